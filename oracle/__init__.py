@@ -1,0 +1,273 @@
+"""CPU oracle of the seeding stage (SMEM finding, max-occurrence filter, locate).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py``'s CPU-baseline / reference leg may import this package.  It shares
+no code with the CUDA library (``paper_2606_15357_gb300``) and never imports
+it.  The arithmetic lives in ``oracle.cpp`` (plain C++, compiled with g++ on
+first use); this module only marshals numpy arrays.
+
+What each function follows (arxiv 2606.15357):
+  Index            Section 2.1: T = R . revcomp(R) . $, suffix array S, B[i] = T[S(i)-1];
+                   Section 2.8: bisulfite mode indexes CT(R) . GA(R).
+  ds_interval      Section 2.1, the ds-interval (lo(P), lo(revcomp P), occ(P)) by binary
+                   search over the sorted suffixes.
+  pi / backward_ext / forward_ext
+                   Section 2.1 LF-mapping and Algorithm 1.
+  smem(method="def")   Section 2.1 definition of (l,c)-SMEMs (the published answer).
+  smem(method="alg3")  Algorithm 3 BatchFindSMEM with one FIFO queue.
+  smem_brute       the definition by scanning T (tiny texts only).
+  locate           {S(x) : k <= x < k+s} from the full suffix array (Section 2.3).
+  locate_slow / batch_locate   Algorithm 2 with the sampled suffix array, modulo n.
+  seed             the whole stage: SMEMs, max-occ filter, hits in SA-row order.
+
+Parity pins (tests/test_oracle_*.py): brute force on tiny texts, the suffix
+array as a sorted permutation, hand-derived values for short texts, closed
+forms (empty pattern, N), invariants (non-containment, maximality, strand
+mirror, hit positions spell the SMEM), Algorithm 3 = definition,
+LocateSlow = BatchLocate = full suffix array.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+SMEM_DTYPE = np.dtype([("read", np.uint64), ("qbeg", np.uint64), ("qend", np.uint64),
+                       ("k", np.uint64), ("kr", np.uint64), ("s", np.uint64)])
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.cpp into _build/liboracle.so (g++, OpenMP)."""
+    src = os.path.join(_HERE, "oracle.cpp")
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(src):
+        return _SO
+    os.makedirs(os.path.dirname(_SO), exist_ok=True)
+    tmp = _SO + f".{os.getpid()}.tmp"
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-fopenmp", "-shared", "-fPIC", src,
+                           "-o", tmp])
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            P, U64, U32, U8, I = (ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32,
+                                  ctypes.c_uint8, ctypes.c_int)
+            sig = {
+                "orc_index_build": ([P, U64, U64, I, U32, I], P),
+                "orc_index_free": ([P], None),
+                "orc_n": ([P], U64), "orc_rlen": ([P], U64), "orc_primary": ([P], U64),
+                "orc_C": ([P, P], None), "orc_text": ([P, P], None), "orc_sa": ([P, P], None),
+                "orc_bwt": ([P, P], None), "orc_ssa": ([P, P], None),
+                "orc_pi": ([P, U8, U64], U64),
+                "orc_ds_def": ([P, P, U64, P], None),
+                "orc_ds_def_batch": ([P, P, U64, U64, P, I], None),
+                "orc_backward_ext": ([P, P, U8, P], None),
+                "orc_forward_ext": ([P, P, U8, P], None),
+                "orc_smem": ([P, P, P, U32, U32, U32, I, I], P),
+                "orc_smem_brute": ([P, U64, P, P, U32, U32, U32, I], P),
+                "orc_result_nsmem": ([P], U64), "orc_result_smem": ([P, P], None),
+                "orc_result_free": ([P], None),
+                "orc_locate_sa": ([P, P, U64, P, I], None),
+                "orc_locate_slow": ([P, P, U64, P, I], None),
+                "orc_batch_locate": ([P, P, U64, P], None),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _u8(a):
+    return np.ascontiguousarray(a, dtype=np.uint8)
+
+
+def _u64(a):
+    return np.ascontiguousarray(a, dtype=np.uint64)
+
+
+def _take_smem(h) -> np.ndarray:
+    L = lib()
+    m = L.orc_result_nsmem(h)
+    raw = np.empty(6 * m, dtype=np.uint64)
+    if m:
+        L.orc_result_smem(h, _p(raw))
+    L.orc_result_free(h)
+    return raw.view(SMEM_DTYPE).reshape(m)
+
+
+class Index:
+    """FMD-index of R (Section 2.1) built on the host by sorting suffixes."""
+
+    def __init__(self, ref: np.ndarray, n_seed: int = 0, bs3: bool = False, sa_rate: int = 32,
+                 threads: int = 0):
+        self._ref = _u8(ref)
+        self.sa_rate = sa_rate
+        self.bs3 = bs3
+        self._h = lib().orc_index_build(_p(self._ref), len(self._ref), n_seed, int(bs3), sa_rate,
+                                        threads)
+        self.n = int(lib().orc_n(self._h))
+        self.rlen = int(lib().orc_rlen(self._h))
+        self.primary = int(lib().orc_primary(self._h))
+        C = np.empty(5, dtype=np.uint64)
+        lib().orc_C(self._h, _p(C))
+        self.C = C
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().orc_index_free(h)
+            self._h = None
+
+    # raw arrays (oracle coding: $=0, A=1, C=2, G=3, T=4)
+    def text(self) -> np.ndarray:
+        out = np.empty(self.n, dtype=np.uint8)
+        lib().orc_text(self._h, _p(out))
+        return out
+
+    def sa(self) -> np.ndarray:
+        out = np.empty(self.n, dtype=np.uint32)
+        lib().orc_sa(self._h, _p(out))
+        return out
+
+    def bwt(self) -> np.ndarray:
+        out = np.empty(self.n, dtype=np.uint8)
+        lib().orc_bwt(self._h, _p(out))
+        return out
+
+    def ssa(self) -> np.ndarray:
+        out = np.empty((self.n + self.sa_rate - 1) // self.sa_rate, dtype=np.uint32)
+        lib().orc_ssa(self._h, _p(out))
+        return out
+
+    def pi(self, a: int, k: int) -> int:
+        """pi(a,k) with a in oracle coding (0 = $)."""
+        return int(lib().orc_pi(self._h, a, k))
+
+    def ds_interval(self, P) -> tuple:
+        """ds-interval of P (read codes 0..3, 4 = N) by the definition."""
+        P = _u8(P)
+        out = np.empty(3, dtype=np.uint64)
+        lib().orc_ds_def(self._h, _p(P), len(P), _p(out))
+        return tuple(int(v) for v in out)
+
+    def ds_intervals(self, pats: np.ndarray, threads: int = 0) -> np.ndarray:
+        """ds-intervals of the rows of a 2-D uint8 array of patterns; shape (npat, 3)."""
+        pats = np.ascontiguousarray(pats, dtype=np.uint8)
+        out = np.empty((pats.shape[0], 3), dtype=np.uint64)
+        if pats.shape[0]:
+            lib().orc_ds_def_batch(self._h, _p(pats), pats.shape[0], pats.shape[1], _p(out), threads)
+        return out
+
+    def backward_ext(self, iv, a: int) -> tuple:
+        inp = np.asarray(iv, dtype=np.uint64)
+        out = np.empty(3, dtype=np.uint64)
+        lib().orc_backward_ext(self._h, _p(inp), a, _p(out))
+        return tuple(int(v) for v in out)
+
+    def forward_ext(self, iv, a: int) -> tuple:
+        inp = np.asarray(iv, dtype=np.uint64)
+        out = np.empty(3, dtype=np.uint64)
+        lib().orc_forward_ext(self._h, _p(inp), a, _p(out))
+        return tuple(int(v) for v in out)
+
+    def smem(self, seq, off, min_len: int = 19, min_occ: int = 1, method: str = "def",
+             threads: int = 0) -> np.ndarray:
+        seq, off = _u8(seq), _u64(off)
+        h = lib().orc_smem(self._h, _p(seq), _p(off), len(off) - 1, min_len, min_occ,
+                           {"def": 0, "alg3": 1}[method], threads)
+        return _take_smem(h)
+
+    def locate(self, rows, threads: int = 0) -> np.ndarray:
+        rows = _u64(rows)
+        out = np.empty(len(rows), dtype=np.uint64)
+        if len(rows):
+            lib().orc_locate_sa(self._h, _p(rows), len(rows), _p(out), threads)
+        return out
+
+    def locate_slow(self, rows, threads: int = 0) -> np.ndarray:
+        rows = _u64(rows)
+        out = np.empty(len(rows), dtype=np.uint64)
+        if len(rows):
+            lib().orc_locate_slow(self._h, _p(rows), len(rows), _p(out), threads)
+        return out
+
+    def batch_locate(self, rows) -> np.ndarray:
+        rows = _u64(rows)
+        out = np.empty(len(rows), dtype=np.uint64)
+        if len(rows):
+            lib().orc_batch_locate(self._h, _p(rows), len(rows), _p(out))
+        return out
+
+    def seed(self, seq, off, min_len: int = 19, min_occ: int = 1, max_occ: int = 500,
+             threads: int = 0, method: str = "def"):
+        """The whole seeding stage.  Returns (smem, over, hit_off, hits):
+        over[m] = s > max_occ (not located); hit_off = exclusive prefix sum of
+        the located hit counts; hits = S(x) for x in [k, k+s) of each kept SMEM,
+        in SMEM order then SA-row order."""
+        sm = self.smem(seq, off, min_len, min_occ, method, threads)
+        over = sm["s"] > max_occ
+        cnt = np.where(over, 0, sm["s"]).astype(np.uint64)
+        hit_off = np.zeros(len(sm), dtype=np.uint64)
+        if len(sm):
+            np.cumsum(cnt[:-1], out=hit_off[1:])
+        total = int(cnt.sum())
+        rows = np.empty(total, dtype=np.uint64)
+        keep = np.nonzero(~over)[0]
+        for q in keep:
+            b = int(hit_off[q])
+            rows[b:b + int(cnt[q])] = np.arange(int(sm["k"][q]), int(sm["k"][q] + cnt[q]),
+                                                dtype=np.uint64)
+        hits = self.locate(rows, threads)
+        return sm, over, hit_off, hits
+
+
+def smem_brute(text: np.ndarray, seq, off, min_len: int = 19, min_occ: int = 1,
+               threads: int = 0) -> np.ndarray:
+    """(l,c)-SMEMs and their ds-intervals by scanning the text (oracle coding, ends with $)."""
+    text, seq, off = _u8(text), _u8(seq), _u64(off)
+    h = lib().orc_smem_brute(_p(text), len(text), _p(seq), _p(off), len(off) - 1, min_len,
+                             min_occ, threads)
+    return _take_smem(h)
+
+
+def bs_convert_reads(seq, off, mate) -> np.ndarray:
+    """Section 2.8: every C of read 1 becomes T and every G of read 2 becomes A."""
+    seq = np.array(seq, dtype=np.uint8, copy=True)
+    rid = np.repeat(np.arange(len(off) - 1), np.diff(np.asarray(off, dtype=np.int64)))
+    m = np.asarray(mate)[rid]
+    seq[(m == 1) & (seq == 1)] = 3
+    seq[(m == 2) & (seq == 2)] = 0
+    return seq
+
+
+def bs_keep(pos, qlen, read_mate, rlen: int) -> np.ndarray:
+    """Section 2.8 strand filter on the 3-base index T = CT(R) GA(R) rc(GA(R)) rc(CT(R)) $:
+    a read-1 hit is kept only inside the forward C-to-T or the reverse G-to-A copy, a read-2
+    hit only inside the forward G-to-A or the reverse C-to-T copy.  rlen = |R|; a hit that
+    crosses a copy boundary is dropped."""
+    pos = np.asarray(pos, dtype=np.int64)
+    qlen = np.asarray(qlen, dtype=np.int64)
+    seg = pos // rlen
+    whole = (pos + qlen - 1) // rlen == seg
+    m = np.asarray(read_mate)
+    ok1 = (seg == 0) | (seg == 2)
+    ok2 = (seg == 1) | (seg == 3)
+    return whole & np.where(m == 1, ok1, np.where(m == 2, ok2, True))

@@ -1,0 +1,295 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU).
+
+Section 2.1 definitions: brute force on tiny texts, a hand-derived fixture,
+the suffix array as a sorted permutation, invariants of (l,c)-SMEMs;
+Algorithm 1 and 3 against the definition; Algorithm 2 against the full suffix
+array; the bisulfite index layout of Section 2.8.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+COMP = np.array([3, 2, 1, 0, 4], dtype=np.uint8)
+
+
+def revcomp(x):
+    return COMP[np.asarray(x, dtype=np.uint8)][::-1]
+
+
+def parse_golden(name):
+    rows = []
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            rows.append(line.split())
+    return rows
+
+
+def test_hand_derived_tiny_text():
+    X = oracle.Index(np.array([0, 1, 2], np.uint8))
+    assert X.n == 7
+    for row in parse_golden("tiny_acg.txt"):
+        tag, vals = row[0], row[1:]
+        if tag == "SA":
+            assert X.sa().tolist() == [int(v) for v in vals]
+        elif tag == "BWT":
+            assert X.bwt().tolist() == [int(v) for v in vals]
+        elif tag == "PRIMARY":
+            assert X.primary == int(vals[0])
+        elif tag == "C":
+            assert X.C.tolist() == [int(v) for v in vals]
+        elif tag == "DS":
+            pat = [] if vals[0] == "-" else [int(v) for v in vals[0].split(",")]
+            assert X.ds_interval(np.array(pat, np.uint8)) == tuple(int(v) for v in vals[1:]), pat
+
+
+def suffix_sorted_check(T, SA):
+    """SA is a permutation of [0,n) and adjacent suffixes are in strictly increasing order."""
+    n = len(T)
+    assert np.array_equal(np.sort(SA), np.arange(n, dtype=SA.dtype))
+    Tb = T.tobytes()
+    for x in range(n - 1):
+        assert Tb[SA[x]:] < Tb[SA[x + 1]:]
+
+
+@pytest.mark.parametrize("length,seed", [(1, 1), (2, 2), (7, 3), (64, 4), (300, 5), (2500, 6)])
+def test_suffix_array_sorted_permutation(length, seed):
+    ref = synth.reference(length, seed)
+    X = oracle.Index(ref)
+    T, SA, B = X.text(), X.sa(), X.bwt()
+    assert X.n == 2 * length + 1
+    # T = R . revcomp(R) . $ in oracle coding
+    assert np.array_equal(T[:length], ref + 1)
+    assert np.array_equal(T[length:2 * length], revcomp(ref) + 1)
+    assert T[-1] == 0
+    suffix_sorted_check(T, SA)
+    # B[i] = T[S(i) - 1], T[-1] = $
+    assert np.array_equal(B, T[(SA.astype(np.int64) - 1) % X.n])
+    assert SA[X.primary] == 0
+    # C[a] = #{B < a}
+    for a in range(5):
+        assert X.C[a] == int((B < a).sum())
+    # sampled SA
+    assert np.array_equal(X.ssa(), SA[::32])
+
+
+def test_suffix_array_repeats():
+    # tandem and segmental repeats give long common prefixes
+    ref = synth.repeat_rich_reference(20000, 77, 0.5)
+    X = oracle.Index(ref, n_seed=3)
+    suffix_sorted_check(X.text(), X.sa())
+
+
+def test_ambiguous_bases_become_seeded_random_bases():
+    ref = np.array([0, 4, 4, 1, 4, 2, 3] * 50, np.uint8)
+    X1, X2, X3 = oracle.Index(ref, n_seed=5), oracle.Index(ref, n_seed=5), oracle.Index(ref, n_seed=6)
+    T1 = X1.text()[:len(ref)]
+    assert np.array_equal(T1, X2.text()[:len(ref)])
+    assert T1.max() <= 4 and T1.min() >= 1          # no N left in T
+    assert np.array_equal(T1[ref < 4], ref[ref < 4] + 1)
+    assert not np.array_equal(T1, X3.text()[:len(ref)])
+    counts = np.bincount(T1[ref == 4], minlength=5)[1:]
+    assert counts.min() > 0                          # all four bases drawn
+
+
+def brute_ds(T, P):
+    """ds-interval straight from Section 2.1 by scanning T (oracle coding)."""
+    n = len(T)
+    Tb = T.tobytes()
+    f = bytes((np.asarray(P, np.uint8) + 1).tolist())
+    rc = bytes((revcomp(P) + 1).tolist())
+    lo = sum(1 for i in range(n) if Tb[i:] < f and not Tb[i:].startswith(f))
+    lor = sum(1 for i in range(n) if Tb[i:] < rc and not Tb[i:].startswith(rc))
+    occ = sum(1 for i in range(n) if Tb[i:i + len(f)] == f)
+    return lo, lor, occ
+
+
+def test_ds_interval_by_scanning():
+    rng = np.random.default_rng(1)
+    ref = synth.reference(150, 11)
+    X = oracle.Index(ref)
+    T = X.text()
+    for _ in range(300):
+        m = int(rng.integers(1, 7))
+        if rng.random() < 0.5:
+            s = int(rng.integers(0, 2 * len(ref) - m))
+            P = (T[s:s + m] - 1).astype(np.uint8)
+            if (T[s:s + m] == 0).any():
+                continue
+        else:
+            P = rng.integers(0, 4, m).astype(np.uint8)
+        assert X.ds_interval(P) == brute_ds(T, P)
+
+
+def test_backward_forward_ext_match_definition():
+    """Algorithm 1 extends the ds-interval of P to that of aP / Pa."""
+    rng = np.random.default_rng(2)
+    ref = synth.repeat_rich_reference(3000, 12, 0.3)
+    X = oracle.Index(ref)
+    for _ in range(400):
+        m = int(rng.integers(0, 12))
+        P = rng.integers(0, 4, m).astype(np.uint8)
+        a = int(rng.integers(0, 4))
+        iv = X.ds_interval(P)
+        assert X.backward_ext(iv, a) == X.ds_interval(np.concatenate([[a], P]).astype(np.uint8))
+        assert X.forward_ext(iv, a) == X.ds_interval(np.concatenate([P, [a]]).astype(np.uint8))
+    # N ends every match
+    assert X.backward_ext((0, 0, X.n), 4) == (0, 0, 0)
+    assert X.ds_interval(np.array([0, 4, 1], np.uint8)) == (0, 0, 0)
+
+
+def test_pi_definition():
+    ref = synth.reference(500, 13)
+    X = oracle.Index(ref)
+    B = X.bwt()
+    for k in list(range(0, 70)) + list(range(X.n - 70, X.n + 1)):
+        for a in range(5):
+            assert X.pi(a, k) == int((B < a).sum() + (B[:k] == a).sum())
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_smem_three_ways_tiny(seed):
+    """Definition (SA binary search) = Algorithm 3 = brute force over T."""
+    rng = np.random.default_rng(seed)
+    kind = seed % 3
+    if kind == 0:
+        ref = synth.reference(int(rng.integers(50, 2000)), 100 + seed)
+    elif kind == 1:
+        ref = synth.repeat_rich_reference(int(rng.integers(2000, 6000)), 100 + seed, 0.6)
+    else:
+        ref = np.tile(synth.reference(int(rng.integers(3, 40)), 100 + seed), 40)
+    X = oracle.Index(ref, n_seed=seed)
+    rd = synth.reads(ref, 30, 200 + seed, mode=0, read_len=int(rng.integers(20, 90)),
+                     sub_lo=0.03, indel=0.01)
+    # some reads with N and some from nowhere
+    seq = rd.seq.copy()
+    seq[rng.integers(0, len(seq), 5)] = 4
+    rnd = synth.reads(synth.reference(5000, 300 + seed), 6, 400 + seed, mode=0, read_len=40)
+    seq = np.concatenate([seq, rnd.seq])
+    off = np.concatenate([rd.off, rd.off[-1] + rnd.off[1:]])
+    T = X.text()
+    for c in (1, 2, 3):
+        for l in (1, 4, 9, 19, 25):
+            a = oracle.smem_brute(T, seq, off, l, c)
+            b = X.smem(seq, off, l, c, "def")
+            d = X.smem(seq, off, l, c, "alg3")
+            assert np.array_equal(a, b), (c, l)
+            assert np.array_equal(b, d), (c, l)
+
+
+def check_smem_invariants(X, seq, off, sm, l, c):
+    by_read = {}
+    for rec in sm:
+        by_read.setdefault(int(rec["read"]), []).append(rec)
+    for r, recs in by_read.items():
+        P = seq[off[r]:off[r + 1]]
+        qb = [int(x["qbeg"]) for x in recs]
+        qe = [int(x["qend"]) for x in recs]
+        # no SMEM contains another: both ends strictly ascending
+        assert all(a < b for a, b in zip(qb, qb[1:])) and all(a < b for a, b in zip(qe, qe[1:]))
+        for x in recs:
+            i, j = int(x["qbeg"]), int(x["qend"])
+            assert j - i >= l and int(x["s"]) >= c
+            assert (int(x["k"]), int(x["kr"]), int(x["s"])) == X.ds_interval(P[i:j])
+            # maximal on both sides
+            if i > 0:
+                assert X.ds_interval(P[i - 1:j])[2] < c
+            if j < len(P):
+                assert X.ds_interval(P[i:j + 1])[2] < c
+
+
+def test_smem_invariants_workload1_sample():
+    ref, rd, p = synth.workload(1, scale=0.05)
+    X = oracle.Index(ref)
+    sub = rd.subset(range(0, 200))
+    sm = X.smem(sub.seq, sub.off, 19, 1)
+    check_smem_invariants(X, sub.seq, sub.off, sm, 19, 1)
+    # strand mirror: SMEMs of revcomp(P) are [|P|-j, |P|-i) with (k', k, s)
+    rc_seq = np.concatenate([revcomp(sub.read(i)) for i in range(sub.n)])
+    sm_rc = X.smem(rc_seq, sub.off, 19, 1)
+    for r in range(sub.n):
+        L = int(sub.off[r + 1] - sub.off[r])
+        a = sorted((L - int(x["qend"]), L - int(x["qbeg"]), int(x["kr"]), int(x["k"]), int(x["s"]))
+                   for x in sm[sm["read"] == r])
+        b = sorted((int(x["qbeg"]), int(x["qend"]), int(x["k"]), int(x["kr"]), int(x["s"]))
+                   for x in sm_rc[sm_rc["read"] == r])
+        assert a == b
+
+
+def test_error_free_read_single_smem_and_origin():
+    ref = synth.reference(200_000, 21)
+    X = oracle.Index(ref)
+    rd = synth.reads(ref, 50, 22, mode=0, read_len=150)
+    sm, over, hoff, hits = X.seed(rd.seq, rd.off)
+    assert len(sm) == rd.n
+    assert np.all(sm["qbeg"] == 0) and np.all(sm["qend"] == 150)
+    for r in range(rd.n):
+        st, s = int(rd.origin[r]) >> 63, int(rd.origin[r]) & ((1 << 63) - 1)
+        h = hits[int(hoff[r]):int(hoff[r]) + int(sm["s"][r])]
+        # forward reads start at s; reverse reads are revcomp(ref[s+16 .. s+166)) -> T position
+        want = s if st == 0 else 2 * len(ref) - (s + 166)
+        assert want in h.tolist()
+
+
+def test_locate_three_ways_and_spelling():
+    ref, rd, p = synth.workload(2, scale=0.002)
+    X = oracle.Index(ref, n_seed=9)
+    T = X.text()
+    sub = rd.subset(range(0, 300))
+    sm, over, hoff, hits = X.seed(sub.seq, sub.off, max_occ=20)
+    assert len(hits) == int(np.where(over, 0, sm["s"]).sum())
+    rows = np.concatenate([np.arange(int(x["k"]), int(x["k"] + x["s"]), dtype=np.uint64)
+                           for x, o in zip(sm, over) if not o])
+    assert np.array_equal(X.locate_slow(rows), hits)
+    assert np.array_equal(X.batch_locate(rows), hits)
+    for x, o, h0 in zip(sm, over, hoff):
+        if o:
+            continue
+        P = sub.seq[sub.off[x["read"]] + x["qbeg"]:sub.off[x["read"]] + x["qend"]] + 1
+        for t in hits[int(h0):int(h0) + int(x["s"])]:
+            assert np.array_equal(T[int(t):int(t) + len(P)], P)
+    # every SA row, and the walk through the $ row
+    allrows = np.arange(X.n, dtype=np.uint64)
+    assert np.array_equal(X.locate_slow(allrows), X.sa().astype(np.uint64))
+
+
+def test_max_occ_flag_and_hit_offsets():
+    ref = np.tile(synth.reference(37, 5), 700)   # every 19-mer occurs hundreds of times
+    X = oracle.Index(ref)
+    rd = synth.reads(ref, 20, 6, mode=0, read_len=60)
+    sm, over, hoff, hits = X.seed(rd.seq, rd.off, max_occ=500)
+    assert np.array_equal(over, sm["s"] > 500)
+    assert over.any()
+    kept = np.where(over, 0, sm["s"])
+    assert np.array_equal(hoff, np.concatenate([[0], np.cumsum(kept)[:-1]]).astype(np.uint64))
+
+
+def test_bisulfite_index_and_filter():
+    ref = synth.reference(3000, 31)
+    X = oracle.Index(ref, bs3=True)
+    m = len(ref)
+    T = X.text()
+    assert X.n == 4 * m + 1 and X.rlen == 2 * m
+    ct = np.where(ref == 1, 3, ref)
+    ga = np.where(ref == 2, 0, ref)
+    assert np.array_equal(T[:m], ct + 1)
+    assert np.array_equal(T[m:2 * m], ga + 1)
+    assert np.array_equal(T[2 * m:3 * m], revcomp(ga) + 1)
+    assert np.array_equal(T[3 * m:4 * m], revcomp(ct) + 1)
+    suffix_sorted_check(T, X.sa())
+    # bisulfite pairs: the read's true segment is among the kept hits
+    rd = synth.reads(ref, 40, 32, mode=1, read_len=100, bisulfite=True)
+    seq = oracle.bs_convert_reads(rd.seq, rd.off, rd.mate)
+    sm, over, hoff, hits = X.seed(seq, rd.off)
+    qlen = np.repeat((sm["qend"] - sm["qbeg"]).astype(np.int64), np.where(over, 0, sm["s"]).astype(np.int64))
+    rmate = np.repeat(rd.mate[sm["read"].astype(np.int64)], np.where(over, 0, sm["s"]).astype(np.int64))
+    keep = oracle.bs_keep(hits, qlen, rmate, m)
+    segs = (hits // m)[keep]
+    assert set(segs[rmate[keep] == 1].tolist()) <= {0, 2}
+    assert set(segs[rmate[keep] == 2].tolist()) <= {1, 3}
+    assert keep.sum() > 0
