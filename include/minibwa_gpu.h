@@ -1,0 +1,164 @@
+/*
+ * minibwa_gpu: the seeding stage of minibwa (arxiv 2606.15357) on one GB300 GPU.
+ *
+ * For every read it finds the (l,c)-SMEMs against an FMD-index of the reference
+ * (Section 2.1 definitions; Algorithm 3), flags SMEMs that occur more than
+ * max_occ times, and locates the remaining occurrences through a sampled
+ * suffix array by LF-walks (Section 2.3; Algorithm 2).  All arithmetic runs in
+ * CUDA kernels for sm_103a; the host code below only moves data and launches.
+ *
+ * Conventions shared by every call:
+ *  - Base codes: 0=A 1=C 2=G 3=T; 4 (or any value > 3) = N.
+ *  - Pointers marked "host or device" are classified with
+ *    cudaPointerGetAttributes; host buffers are staged through the library.
+ *    The caller owns every buffer it passes in.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *    enqueue work on it and return after the results they report on the host
+ *    (counts, status) are known; device outputs are complete when they return.
+ *  - Return value: MB_OK (0) or a negative MB_ERR_* code; mb_strerror() names
+ *    it.  No C++ exception crosses this boundary.
+ *  - An index is read-only after it is built and may be used from several
+ *    streams at once.  A server (mb_serve_*) is used from one host thread.
+ *  - Text coordinates: T = R . revcomp(R) . $ (Section 2.1), n = 2|R| + 1; in
+ *    bisulfite mode R is replaced by CT(R) . GA(R) (Section 2.8).  n must be
+ *    below 2^32.
+ */
+#ifndef MINIBWA_GPU_H
+#define MINIBWA_GPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    MB_OK = 0,
+    MB_ERR_ARG = -1,          /* invalid argument (null pointer, size out of range, n >= 2^32) */
+    MB_ERR_NOMEM = -2,        /* device or host allocation failed / admission budget exceeded */
+    MB_ERR_CAPACITY = -3,     /* output buffer too small; the needed size is reported */
+    MB_ERR_CUDA = -4,         /* a CUDA runtime call failed */
+    MB_ERR_TIMEOUT = -5,      /* a bounded wait expired */
+    MB_ERR_IO = -6,           /* file could not be opened, read or written */
+    MB_ERR_CORRUPT = -7,      /* index file header or checksum mismatch */
+    MB_ERR_DEVICE_CHECK = -8, /* a device-side consistency check failed */
+    MB_ERR_BUSY = -9          /* server has no free slot for the request right now */
+};
+
+/* Flags of mb_opts.flags */
+#define MB_BS3      0x1u   /* index: bisulfite 3-base index over CT(R).GA(R) (Section 2.8);
+                              seeding: convert read 1 C->T and read 2 G->A, keep hits by strand */
+#define MB_BATCHED  0x2u   /* seeding: one persistent launch over a device work queue */
+#define MB_CHECKED  0x4u   /* seeding: bounds-check every block / row index on the device */
+#define MB_NO_KMER  0x8u   /* seeding: do not use the k-mer ds-interval table */
+
+/* Flags of mb_smem.flags */
+#define MB_SMEM_OVER_MAX_OCC 0x1u   /* s > max_occ: reported, not located, no hits */
+
+typedef struct mb_index mb_index;
+typedef struct mb_server mb_server;
+
+/* Parameters.  Zero in any field selects its default. */
+typedef struct {
+    uint32_t min_len;         /* l, minimum SMEM length (default 19, Section 2.7) */
+    uint32_t min_occ;         /* c, minimum occurrence (default 1) */
+    uint32_t max_occ;         /* SMEMs with s > max_occ are flagged and not located (default 500) */
+    uint32_t sa_rate;         /* r, suffix array sample rate (default 32, Section 2.3) */
+    uint32_t kmer_k;          /* k of the k-mer ds-interval table (default 10, Section 2.5), <= 12 */
+    uint32_t flags;           /* MB_* flags above */
+    uint32_t reads_per_warp;  /* tuning: reads per warp in the batched form (0 = default) */
+    uint32_t prefetch_depth;  /* tuning: in-flight reads per lane (0 = default) */
+    uint32_t block_size;      /* tuning: threads per block (0 = default) */
+} mb_opts;
+
+/* One SMEM (48 bytes).  (k, kr, s) is its ds-interval (lo(P), lo(revcomp P), occ(P)),
+ * P = read[qbeg, qend).  hit_off indexes its first hit in mb_locate's output. */
+typedef struct {
+    uint32_t read, qbeg, qend, flags;
+    uint64_t k, kr, s;
+    uint64_t hit_off;
+} mb_smem;
+
+/* ---------------------------------------------------------------------------------------
+ * mb_index_build — FMD-index of a reference on the GPU (Section 2.1, 2.2, 2.3, 2.5).
+ *   ref      host or device, `len` base codes; codes > 3 (ambiguous) are replaced by
+ *            random bases: bits 63..62 of splitmix64's output function of
+ *            (n_seed + (pos+1) * 0x9E3779B97F4A7C15)  (Section 2.1, "random bases").
+ *   opts     sa_rate, kmer_k, flags & MB_BS3 are used.
+ *   stream   stream for the build.
+ *   out      receives the new index (free with mb_index_free).
+ * Builds T, its suffix array by prefix doubling, the BWT in 64-byte occurrence
+ * blocks (four 64-bit counts of A/C/G/T before the block, then 128 2-bit symbols;
+ * Section 2.2), the sampled suffix array and the k-mer ds-interval table.
+ * Errors: MB_ERR_ARG (len = 0, n >= 2^32), MB_ERR_NOMEM, MB_ERR_CUDA.
+ */
+int mb_index_build(const uint8_t *ref, uint64_t len, const mb_opts *opts, uint64_t n_seed,
+                   void *stream, mb_index **out);
+
+/* Write / read an index file (header with version, sizes and a checksum; 64-byte blocks as in
+ * memory, Section 2.2).  Errors: MB_ERR_IO, MB_ERR_CORRUPT (bad header, size or checksum),
+ * MB_ERR_NOMEM, MB_ERR_CUDA. */
+int mb_index_save(const mb_index *idx, const char *path);
+int mb_index_load(const char *path, void *stream, mb_index **out);
+void mb_index_free(mb_index *idx);
+
+/* n = |T|, primary = the row i with S(i) = 0, ref_len = |R| (|R3| in bisulfite mode). */
+int mb_index_info(const mb_index *idx, uint64_t *n, uint64_t *primary, uint64_t *ref_len);
+
+/* Copy index arrays to the caller (host or device): sa (n x u32, full suffix array; only
+ * available until mb_index_drop_sa, else MB_ERR_ARG), bwt (n bytes, 0=$ 1..4=A..T),
+ * ssa (ceil(n/r) x u32), occ blocks (ceil((n+1)/128) x 64 bytes), kmer table (4^k x 3 u32:
+ * k, kr, s), C (5 x u64 = #{B[i] < a} for a = $,A,C,G,T).  Any pointer may be NULL. */
+int mb_index_export(const mb_index *idx, uint32_t *sa, uint8_t *bwt, uint32_t *ssa,
+                    void *occ_blocks, uint32_t *kmer, uint64_t *C);
+/* Free the full suffix array kept after the build (it is only needed for mb_index_export). */
+int mb_index_drop_sa(mb_index *idx);
+
+/* ---------------------------------------------------------------------------------------
+ * mb_seed_batch — (l,c)-SMEMs of a batch of reads (Section 2.5, Algorithm 3) with the
+ * max-occurrence flag and hit offsets.
+ *   seq      host or device, concatenated read base codes.
+ *   off      host or device, n_reads + 1 u64 offsets into seq (read r = seq[off[r], off[r+1])).
+ *   mate     host or device or NULL; per read 0 = single, 1 = read 1, 2 = read 2 (used with
+ *            MB_BS3 to convert read 1 C->T and read 2 G->A before seeding, Section 2.8).
+ *   out      host or device, room for `cap` records.  Records are ordered by read, then by
+ *            ascending qbeg; s > max_occ sets MB_SMEM_OVER_MAX_OCC; hit_off is the
+ *            exclusive prefix sum of s over records without that flag.
+ *   n_out    receives the number of SMEMs.  If it exceeds cap, nothing is written to out and
+ *            MB_ERR_CAPACITY is returned with *n_out = the needed count.
+ *   n_hits   (may be NULL) receives the total number of hits to locate.
+ * Errors: MB_ERR_ARG, MB_ERR_CAPACITY, MB_ERR_NOMEM, MB_ERR_CUDA, MB_ERR_DEVICE_CHECK.
+ */
+int mb_seed_batch(const mb_index *idx, const uint8_t *seq, const uint64_t *off, uint32_t n_reads,
+                  const uint8_t *mate, const mb_opts *opts, void *stream,
+                  mb_smem *out, uint64_t cap, uint64_t *n_out, uint64_t *n_hits);
+
+/* ---------------------------------------------------------------------------------------
+ * mb_locate — text positions of every row of every SMEM without MB_SMEM_OVER_MAX_OCC
+ * (Section 2.3, Algorithm 2): row x is LF-walked to a sampled row; its position is
+ * (steps + S(sampled row)) mod n.
+ *   smem     host or device, n_smem records from mb_seed_batch (hit_off must be as written).
+ *   hits     host or device, room for `cap` u32 positions; hit t of record m is written at
+ *            hits[m.hit_off + t], rows k..k+s-1 in order.
+ *   n_hits   receives the total.  If it exceeds cap: MB_ERR_CAPACITY, nothing written.
+ * With MB_BS3 in opts, hits are still all written; mb_bs_filter applies the strand rule.
+ */
+int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_smem, const mb_opts *opts,
+              void *stream, uint32_t *hits, uint64_t cap, uint64_t *n_hits);
+
+/* Section 2.8 strand rule on the 3-base index: keep[h] = 1 if hit h of an SMEM of read `mate`
+ * 1 lies wholly inside the forward C-to-T or the reverse G-to-A copy of the reference (read 2:
+ * forward G-to-A or reverse C-to-T), else 0.  All pointers host or device. */
+int mb_bs_filter(const mb_index *idx, const mb_smem *smem, uint64_t n_smem, const uint8_t *mate,
+                 const uint32_t *hits, uint64_t n_hits, void *stream, uint8_t *keep);
+
+/* Map a text position to the reference: strand 0 = forward, 1 = reverse complement;
+ * rpos = the start on the forward strand of the match of length len. */
+int mb_hit_to_ref(const mb_index *idx, uint64_t pos, uint64_t len, int *strand, uint64_t *rpos);
+
+const char *mb_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,259 @@
+"""Seeding stage of minibwa (arxiv 2606.15357) on one GB300 GPU: Python binding.
+
+This module only marshals arguments for ``libminibwa_gpu.so`` (C ABI declared in
+``include/minibwa_gpu.h``); every step of the computation runs in its CUDA
+kernels.  Arrays may be numpy arrays (host) or torch tensors (host or CUDA);
+pointers are passed through unchanged and the library stages host buffers.
+There is no CPU fallback: if the library has not been built, loading fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from .nvcc_build import SO, build
+
+__all__ = ["SMEM_DTYPE", "Opts", "MbError", "lib", "build", "Index", "mb_index_build",
+           "mb_index_load", "mb_seed_batch", "mb_locate", "mb_bs_filter", "seed"]
+
+MB_BS3, MB_BATCHED, MB_CHECKED, MB_NO_KMER = 0x1, 0x2, 0x4, 0x8
+MB_SMEM_OVER_MAX_OCC = 0x1
+MB_ERR_CAPACITY = -3
+
+SMEM_DTYPE = np.dtype([("read", "<u4"), ("qbeg", "<u4"), ("qend", "<u4"), ("flags", "<u4"),
+                       ("k", "<u8"), ("kr", "<u8"), ("s", "<u8"), ("hit_off", "<u8")])
+assert SMEM_DTYPE.itemsize == 48
+
+
+class Opts(ctypes.Structure):
+    """mb_opts; zero fields take the library defaults (l=19, c=1, max_occ=500, r=32, k=10)."""
+    _fields_ = [("min_len", ctypes.c_uint32), ("min_occ", ctypes.c_uint32),
+                ("max_occ", ctypes.c_uint32), ("sa_rate", ctypes.c_uint32),
+                ("kmer_k", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("reads_per_warp", ctypes.c_uint32), ("prefetch_depth", ctypes.c_uint32),
+                ("block_size", ctypes.c_uint32)]
+
+
+class MbError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libminibwa_gpu.so.  Raises if it was not built (no fallback path exists)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(SO):
+                raise RuntimeError(f"libminibwa_gpu.so is not built ({SO}); "
+                                   "run `python -c 'import __graft_entry__ as g; g.build()'`")
+            L = ctypes.CDLL(SO)
+            P, U64, U32, I = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+            PP = ctypes.POINTER(ctypes.c_void_p)
+            PU64 = ctypes.POINTER(ctypes.c_uint64)
+            OP = ctypes.POINTER(Opts)
+            sig = {
+                "mb_index_build": ([P, U64, OP, U64, P, PP], I),
+                "mb_index_save": ([P, ctypes.c_char_p], I),
+                "mb_index_load": ([ctypes.c_char_p, P, PP], I),
+                "mb_index_free": ([P], None),
+                "mb_index_info": ([P, PU64, PU64, PU64], I),
+                "mb_index_export": ([P, P, P, P, P, P, P], I),
+                "mb_index_drop_sa": ([P], I),
+                "mb_seed_batch": ([P, P, P, U32, P, OP, P, P, U64, PU64, PU64], I),
+                "mb_locate": ([P, P, U64, OP, P, P, U64, PU64], I),
+                "mb_bs_filter": ([P, P, U64, P, P, U64, P, P], I),
+                "mb_hit_to_ref": ([P, U64, U64, ctypes.POINTER(I), PU64], I),
+                "mb_strerror": ([I], ctypes.c_char_p),
+                "mb_last_error": ([], ctypes.c_char_p),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        L = lib()
+        raise MbError(rc, f"{what}: {L.mb_strerror(rc).decode()}: {L.mb_last_error().decode()}")
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return ctypes.c_void_p(x.ctypes.data)
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    raise TypeError(type(x))
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return None
+
+
+def _opts(opts) -> Opts:
+    if opts is None:
+        return Opts()
+    if isinstance(opts, Opts):
+        return opts
+    return Opts(**opts)
+
+
+def _is_cuda(x) -> bool:
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
+class Index:
+    """A device-resident FMD-index (handle to mb_index)."""
+
+    def __init__(self, handle):
+        self._h = handle
+        n, prim, rl = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib().mb_index_info(handle, ctypes.byref(n), ctypes.byref(prim), ctypes.byref(rl)),
+               "mb_index_info")
+        self.n, self.primary, self.ref_len = n.value, prim.value, rl.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def free(self):
+        if self._h:
+            lib().mb_index_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def save(self, path: str):
+        _check(lib().mb_index_save(self._h, path.encode()), "mb_index_save")
+
+    def drop_sa(self):
+        _check(lib().mb_index_drop_sa(self._h), "mb_index_drop_sa")
+
+    def export(self, sa=False, bwt=False, ssa=False, occ=False, kmer=False, sa_rate=32, kmer_k=10):
+        """Copy index arrays to host numpy arrays (for tests)."""
+        n = self.n
+        out = {}
+        a_sa = np.empty(n, np.uint32) if sa else None
+        a_bwt = np.empty(n, np.uint8) if bwt else None
+        a_ssa = np.empty((n + sa_rate - 1) // sa_rate, np.uint32) if ssa else None
+        a_occ = np.empty((n // 128 + 1) * 8, np.uint64) if occ else None
+        a_kmer = np.empty(3 * 4 ** kmer_k, np.uint32) if kmer else None
+        C = np.empty(5, np.uint64)
+        _check(lib().mb_index_export(self._h, _ptr(a_sa), _ptr(a_bwt), _ptr(a_ssa), _ptr(a_occ),
+                                     _ptr(a_kmer), _ptr(C)), "mb_index_export")
+        for k, v in (("sa", a_sa), ("bwt", a_bwt), ("ssa", a_ssa), ("occ", a_occ), ("kmer", a_kmer)):
+            if v is not None:
+                out[k] = v
+        out["C"] = C
+        return out
+
+    def hit_to_ref(self, pos: int, length: int):
+        strand, rpos = ctypes.c_int(), ctypes.c_uint64()
+        _check(lib().mb_hit_to_ref(self._h, pos, length, ctypes.byref(strand), ctypes.byref(rpos)),
+               "mb_hit_to_ref")
+        return strand.value, rpos.value
+
+
+def mb_index_build(ref, opts=None, n_seed: int = 0, stream=None) -> Index:
+    """FMD-index of `ref` (uint8 codes, host numpy or torch tensor) built on the GPU."""
+    o = _opts(opts)
+    h = ctypes.c_void_p()
+    _check(lib().mb_index_build(_ptr(ref), int(ref.numel() if hasattr(ref, "numel") else len(ref)),
+                                ctypes.byref(o), n_seed, _stream(stream), ctypes.byref(h)),
+           "mb_index_build")
+    return Index(h)
+
+
+def mb_index_load(path: str, stream=None) -> Index:
+    h = ctypes.c_void_p()
+    _check(lib().mb_index_load(path.encode(), _stream(stream), ctypes.byref(h)), "mb_index_load")
+    return Index(h)
+
+
+def mb_seed_batch(index: Index, seq, off, mate=None, opts=None, stream=None, out=None, cap=None):
+    """SMEMs of a batch of reads.  Returns (records, n_smem, n_hits).
+
+    With `out` None the records come back as a host numpy array of SMEM_DTYPE;
+    otherwise they are written into `out` (a uint8 buffer of cap*48 bytes,
+    host or device) and `out` is returned.
+    """
+    o = _opts(opts)
+    n_reads = (off.numel() if hasattr(off, "numel") else len(off)) - 1
+    n_out, n_hits = ctypes.c_uint64(), ctypes.c_uint64()
+    if out is None:
+        cap = cap if cap is not None else max(16, 8 * n_reads)
+        while True:
+            buf = np.empty(cap, dtype=SMEM_DTYPE)
+            rc = lib().mb_seed_batch(index.handle, _ptr(seq), _ptr(off), n_reads, _ptr(mate),
+                                     ctypes.byref(o), _stream(stream), _ptr(buf), cap,
+                                     ctypes.byref(n_out), ctypes.byref(n_hits))
+            if rc == MB_ERR_CAPACITY:
+                cap = n_out.value
+                continue
+            _check(rc, "mb_seed_batch")
+            return buf[:n_out.value], n_out.value, n_hits.value
+    rc = lib().mb_seed_batch(index.handle, _ptr(seq), _ptr(off), n_reads, _ptr(mate), ctypes.byref(o),
+                             _stream(stream), _ptr(out), cap, ctypes.byref(n_out), ctypes.byref(n_hits))
+    _check(rc, "mb_seed_batch")
+    return out, n_out.value, n_hits.value
+
+
+def mb_locate(index: Index, smem, n_smem: int, opts=None, stream=None, hits=None, cap=None):
+    """Text positions of the hits of every SMEM not over max_occ.  Returns (hits, n_hits)."""
+    o = _opts(opts)
+    n_hits = ctypes.c_uint64()
+    if hits is None:
+        cap = 0 if cap is None else cap
+        while True:
+            buf = np.empty(max(cap, 1), dtype=np.uint32)
+            rc = lib().mb_locate(index.handle, _ptr(smem), n_smem, ctypes.byref(o), _stream(stream),
+                                 _ptr(buf), cap, ctypes.byref(n_hits))
+            if rc == MB_ERR_CAPACITY:
+                cap = n_hits.value
+                continue
+            _check(rc, "mb_locate")
+            return buf[:n_hits.value], n_hits.value
+    _check(lib().mb_locate(index.handle, _ptr(smem), n_smem, ctypes.byref(o), _stream(stream),
+                           _ptr(hits), cap, ctypes.byref(n_hits)), "mb_locate")
+    return hits, n_hits.value
+
+
+def mb_bs_filter(index: Index, smem, n_smem: int, mate, hits, n_hits: int, stream=None, keep=None):
+    """Section 2.8 strand rule: 1 for hits kept, 0 for hits dropped."""
+    if keep is None:
+        keep = np.empty(max(n_hits, 1), dtype=np.uint8)
+    _check(lib().mb_bs_filter(index.handle, _ptr(smem), n_smem, _ptr(mate), _ptr(hits), n_hits,
+                              _stream(stream), _ptr(keep)), "mb_bs_filter")
+    return keep[:n_hits]
+
+
+def seed(index: Index, seq, off, mate=None, opts=None, stream=None):
+    """SMEMs then hits, host in / host out (numpy).  Returns (records, hits)."""
+    sm, m, nh = mb_seed_batch(index, seq, off, mate, opts, stream)
+    hits, _ = mb_locate(index, sm, m, opts, stream, cap=nh)
+    return sm, hits

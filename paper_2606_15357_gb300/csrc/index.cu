@@ -1,0 +1,627 @@
+// FMD-index construction on the GPU (Section 2.1 definitions, Section 2.2 block layout,
+// Section 2.3 sampled suffix array, Section 2.5 k-mer ds-interval table).
+//
+//   T = R . revcomp(R) . $            (bisulfite: R -> CT(R) . GA(R), Section 2.8)
+//   S = suffix array of T             prefix doubling: sort by the first 27 symbols, then
+//                                     repeatedly re-sort the suffixes whose 2h-prefix is still
+//                                     shared by (rank of the h-prefix, rank of the h-prefix at +h)
+//   B[i] = T[S(i) - 1], T[-1] = $     written straight into 64-byte occurrence blocks
+#include <stdarg.h>
+#include <stdlib.h>
+#include <string.h>
+#include <mutex>
+#include <string>
+#include <vector>
+#include "common.cuh"
+
+struct mb_index {
+    u64 n = 0, rlen = 0, primary = 0;
+    u32 sa_rate = 32, kmer_k = 10, flags = 0;
+    u64 C[5] = {0, 0, 0, 0, 0};   // $, A, C, G, T
+    u64 nblocks = 0;
+    OccBlock *occ = nullptr;
+    u32 *ssa = nullptr;
+    u32 *kmer = nullptr;
+    u32 *sa = nullptr;            // full SA, kept until mb_index_drop_sa
+    int device = 0;
+};
+
+DevIndex mb_dev_index(const mb_index *x) {
+    DevIndex I;
+    I.occ = x->occ;
+    I.ssa = x->ssa;
+    I.kmer = x->kmer;
+    I.n = x->n;
+    I.primary = x->primary;
+    for (int a = 0; a < 4; ++a) I.C[a] = x->C[a + 1];
+    I.nblocks = x->nblocks;
+    I.r = x->sa_rate;
+    I.kmer_k = x->kmer_k;
+    return I;
+}
+int mb_index_device(const mb_index *x) { return x->device; }
+u32 mb_index_flags(const mb_index *x) { return x->flags; }
+
+namespace {
+
+constexpr u64 GOLDEN = 0x9E3779B97F4A7C15ULL;
+constexpr int KEY_SYMS = 27;   // 5^27 < 2^63: the first 27 symbols of a suffix in base 5 ($ = 0)
+
+__device__ __forceinline__ u8 ref_base(const u8 *__restrict__ R, u64 x, u64 seed) {
+    u8 b = R[x];
+    return b < 4 ? b : (u8)(mb_mix64(seed + (x + 1) * GOLDEN) >> 62);
+}
+__device__ __forceinline__ u8 r3_base(const u8 *__restrict__ R, u64 m, u64 x, u64 seed, int bs3) {
+    if (!bs3) return ref_base(R, x, seed);
+    if (x < m) {
+        u8 b = ref_base(R, x, seed);
+        return b == 1 ? 3 : b;   // C -> T
+    }
+    u8 b = ref_base(R, x - m, seed);
+    return b == 2 ? 0 : b;       // G -> A
+}
+
+// T[i] in 0..3 for i < n-1; T[n-1] = 4 marks $.
+__global__ void k_pack_text(const u8 *__restrict__ R, u64 m, u64 seed, int bs3, u8 *__restrict__ T, u64 n) {
+    const u64 M = (n - 1) / 2;
+    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x) {
+        u8 b;
+        if (i == n - 1) b = 4;
+        else if (i < M) b = r3_base(R, m, i, seed, bs3);
+        else b = (u8)(3 - r3_base(R, m, 2 * M - 1 - i, seed, bs3));
+        T[i] = b;
+    }
+}
+
+__global__ void k_init_keys(const u8 *__restrict__ T, u64 n, u64 *__restrict__ keys, u32 *__restrict__ vals) {
+    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x) {
+        u64 v = 0;
+#pragma unroll
+        for (int q = 0; q < KEY_SYMS; ++q) {
+            u64 p = i + q;
+            u32 s = p < n - 1 ? (u32)T[p] + 1u : 0u;
+            v = v * 5 + s;
+        }
+        keys[i] = v;
+        vals[i] = (u32)i;
+    }
+}
+
+// hv[t] = (start of a new key run) ? pos(t) : 0, for a max-scan giving each item its run head.
+// flag[t] = item t is in a run of more than one key.
+__global__ void k_heads(const u64 *__restrict__ keys, const u32 *__restrict__ pos, u64 A, u32 *__restrict__ hv,
+                        u32 *__restrict__ flag) {
+    for (u64 t = blockIdx.x * (u64)blockDim.x + threadIdx.x; t < A; t += (u64)gridDim.x * blockDim.x) {
+        u64 k = keys[t];
+        bool head = t == 0 || keys[t - 1] != k;
+        bool last = t == A - 1 || keys[t + 1] != k;
+        hv[t] = head ? (pos ? pos[t] : (u32)t) : 0u;
+        flag[t] = (head && last) ? 0u : 1u;
+    }
+}
+
+__global__ void k_set_rank(const u32 *__restrict__ sa_vals, const u32 *__restrict__ hv, u64 A, u32 *__restrict__ rank) {
+    for (u64 t = blockIdx.x * (u64)blockDim.x + threadIdx.x; t < A; t += (u64)gridDim.x * blockDim.x)
+        rank[sa_vals[t]] = hv[t];
+}
+
+// act2[pos[t]] = (act ? act[t] : t) for flagged t
+__global__ void k_compact(const u32 *__restrict__ flag, const u32 *__restrict__ pos, const u32 *__restrict__ act,
+                          u64 A, u32 *__restrict__ act2) {
+    for (u64 t = blockIdx.x * (u64)blockDim.x + threadIdx.x; t < A; t += (u64)gridDim.x * blockDim.x)
+        if (flag[t]) act2[pos[t]] = act ? act[t] : (u32)t;
+}
+
+__global__ void k_round_keys(const u32 *__restrict__ act, u64 A, const u32 *__restrict__ SA,
+                             const u32 *__restrict__ rank, u64 h, u64 n, u64 *__restrict__ keys,
+                             u32 *__restrict__ vals, u32 *__restrict__ err) {
+    for (u64 t = blockIdx.x * (u64)blockDim.x + threadIdx.x; t < A; t += (u64)gridDim.x * blockDim.x) {
+        u32 p = SA[act[t]];
+        u64 q = (u64)p + h;
+        u32 r2 = 0;
+        if (q < n) r2 = rank[q];
+        else atomicOr(err, 1u);   // a suffix whose h-prefix holds $ is unique; never active
+        keys[t] = ((u64)rank[p] << 32) | r2;
+        vals[t] = p;
+    }
+}
+
+__global__ void k_scatter_sa(const u32 *__restrict__ act, u64 A, const u32 *__restrict__ vals, u32 *__restrict__ SA) {
+    for (u64 t = blockIdx.x * (u64)blockDim.x + threadIdx.x; t < A; t += (u64)gridDim.x * blockDim.x)
+        SA[act[t]] = vals[t];
+}
+
+// One warp per 128-row block: symbols B[x] = T[S(x)-1] packed 2 bits each ($ stored as A),
+// per-block counts of A,C,G,T (excluding $) to bcnt[a * nblocks + b].
+__global__ void k_bwt_blocks(const u8 *__restrict__ T, const u32 *__restrict__ SA, u64 n, OccBlock *__restrict__ occ,
+                             u64 nblocks, u64 *__restrict__ bcnt, u64 *__restrict__ primary) {
+    const int lane = threadIdx.x & 31;
+    const u64 warps = (u64)gridDim.x * (blockDim.x >> 5);
+    for (u64 b = blockIdx.x * (u64)(blockDim.x >> 5) + (threadIdx.x >> 5); b < nblocks; b += warps) {
+        u32 byte = 0, c[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            u64 x = b * 128 + (u64)lane * 4 + j;
+            if (x < n) {
+                u32 p = SA[x];
+                u32 s;
+                if (p == 0) {
+                    *primary = x;
+                    s = 0;
+                } else {
+                    s = T[p - 1];
+                    c[s] += 1;
+                }
+                byte |= s << (2 * j);
+            }
+        }
+        u64 word = (u64)byte << (8 * (lane & 7));
+#pragma unroll
+        for (int d = 1; d < 8; d <<= 1) word |= __shfl_xor_sync(0xffffffffu, word, d);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) c[a] += __shfl_xor_sync(0xffffffffu, c[a], d);
+        if ((lane & 7) == 0) occ[b].w[lane >> 3] = word;
+        if (lane < 4) bcnt[(u64)lane * nblocks + b] = c[lane];
+    }
+}
+
+__global__ void k_fill_counts(const u64 *__restrict__ bcnt_scanned, u64 nblocks, OccBlock *__restrict__ occ) {
+    for (u64 b = blockIdx.x * (u64)blockDim.x + threadIdx.x; b < nblocks; b += (u64)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) occ[b].cnt[a] = bcnt_scanned[(u64)a * nblocks + b];
+}
+
+__global__ void k_sample_sa(const u32 *__restrict__ SA, u64 n, u32 r, u32 *__restrict__ ssa) {
+    u64 m = (n + r - 1) / r;
+    for (u64 x = blockIdx.x * (u64)blockDim.x + threadIdx.x; x < m; x += (u64)gridDim.x * blockDim.x)
+        ssa[x] = SA[x * r];
+}
+
+// ds-interval of every k-mer by k BackwardExt steps from the empty string (0, 0, n).
+__global__ void k_kmer_table(DevIndex I, u32 k, u32 *__restrict__ out) {
+    u64 nk = 1ULL << (2 * k);
+    for (u64 w = blockIdx.x * (u64)blockDim.x + threadIdx.x; w < nk; w += (u64)gridDim.x * blockDim.x) {
+        u64 p = 0, q = 0, s = I.n;
+        for (int t = (int)k - 1; t >= 0; --t) {
+            u32 a = (u32)(w >> (2 * (k - 1 - t))) & 3u;
+            Ext e = extend(I, p, q, s, a);
+            p = e.p; q = e.q; s = e.s;
+        }
+        out[3 * w + 0] = (u32)p;
+        out[3 * w + 1] = (u32)q;
+        out[3 * w + 2] = (u32)s;
+    }
+}
+
+int nbits(u64 v) {   // smallest b with v <= 2^b
+    int b = 0;
+    while (b < 64 && (1ULL << b) < v) ++b;
+    return b;
+}
+
+}  // namespace
+
+// ============================================================================ host side
+static std::mutex g_err_mu;
+static std::string g_err;
+void mb_set_error(const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    std::lock_guard<std::mutex> g(g_err_mu);
+    g_err = buf;
+}
+extern "C" const char *mb_last_error(void) {
+    static thread_local std::string copy;
+    std::lock_guard<std::mutex> g(g_err_mu);
+    copy = g_err;
+    return copy.c_str();
+}
+
+bool mb_is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int mb_stage_in(const void *src, size_t bytes, cudaStream_t st, DevBuf &buf, const void **dev) {
+    if (bytes == 0 || mb_is_device_ptr(src)) {
+        *dev = src;
+        return MB_OK;
+    }
+    MB_TRY(buf.alloc(bytes, st));
+    MB_CK(cudaMemcpyAsync(buf.p, src, bytes, cudaMemcpyHostToDevice, st));
+    *dev = buf.p;
+    return MB_OK;
+}
+
+static void free_index(mb_index *x) {
+    if (!x) return;
+    if (x->occ) cudaFree(x->occ);
+    if (x->ssa) cudaFree(x->ssa);
+    if (x->kmer) cudaFree(x->kmer);
+    if (x->sa) cudaFree(x->sa);
+    delete x;
+}
+
+// Suffix array of T (device, n symbols) by prefix doubling.  SA (device, n) receives it.
+static int build_sa(const u8 *T, u64 n, u32 *SA, cudaStream_t st) {
+    DevBuf bk, bka, bv, bva, btmp, brank, bhv, bflag, bact, bact2, berr, bcount;
+    MB_TRY(bk.alloc(n * 8, st));
+    MB_TRY(bka.alloc(n * 8, st));
+    MB_TRY(bv.alloc(n * 4, st));
+    MB_TRY(bva.alloc(n * 4, st));
+    size_t tb = radix_tmp_bytes(n);
+    size_t sb = scan_tmp_bytes(n);
+    MB_TRY(btmp.alloc(tb > sb ? tb : sb, st));
+    MB_TRY(brank.alloc(n * 4, st));
+    MB_TRY(bhv.alloc(n * 4, st));
+    MB_TRY(bflag.alloc(n * 4, st));
+    MB_TRY(bact.alloc(n * 4, st));
+    MB_TRY(bact2.alloc(n * 4, st));
+    MB_TRY(berr.alloc(8, st));
+    MB_TRY(bcount.alloc(8, st));
+    u64 *keys = bk.as<u64>(), *keys_alt = bka.as<u64>();
+    u32 *vals = bv.as<u32>(), *vals_alt = bva.as<u32>();
+    u32 *rank = brank.as<u32>(), *hv = bhv.as<u32>(), *flag = bflag.as<u32>();
+    u32 *act = bact.as<u32>(), *act2 = bact2.as<u32>();
+    u32 *err = berr.as<u32>(), *count = bcount.as<u32>();
+    MB_CK(cudaMemsetAsync(err, 0, 4, st));
+    const unsigned B = 256;
+
+    // round 0: the first 27 symbols
+    k_init_keys<<<grid_for(n, B), B, 0, st>>>(T, n, keys, vals);
+    MB_CK(cudaGetLastError());
+    BitRange r0[1] = {{0, 63}};
+    MB_TRY(radix_sort_pairs(keys, vals, keys_alt, vals_alt, n, r0, 1, btmp.p, st));
+    MB_CK(cudaMemcpyAsync(SA, vals, n * 4, cudaMemcpyDeviceToDevice, st));
+    k_heads<<<grid_for(n, B), B, 0, st>>>(keys, nullptr, n, hv, flag);
+    MB_CK(cudaGetLastError());
+    MB_TRY(scan_inclusive_max_u32(hv, hv, n, btmp.p, st));
+    k_set_rank<<<grid_for(n, B), B, 0, st>>>(vals, hv, n, rank);
+    MB_CK(cudaGetLastError());
+    MB_TRY(scan_exclusive_u32(flag, hv, n, count, btmp.p, st));   // hv reused as positions
+    k_compact<<<grid_for(n, B), B, 0, st>>>(flag, hv, nullptr, n, act);
+    MB_CK(cudaGetLastError());
+    u32 A = 0;
+    MB_CK(cudaMemcpyAsync(&A, count, 4, cudaMemcpyDeviceToHost, st));
+    MB_CK(cudaStreamSynchronize(st));
+
+    const int nb = nbits(n);
+    BitRange rr[2] = {{0, nb}, {32, 32 + nb}};
+    u64 h = KEY_SYMS;
+    while (A > 0) {
+        k_round_keys<<<grid_for(A, B), B, 0, st>>>(act, A, SA, rank, h, n, keys, vals, err);
+        MB_CK(cudaGetLastError());
+        MB_TRY(radix_sort_pairs(keys, vals, keys_alt, vals_alt, A, rr, 2, btmp.p, st));
+        k_scatter_sa<<<grid_for(A, B), B, 0, st>>>(act, A, vals, SA);
+        MB_CK(cudaGetLastError());
+        k_heads<<<grid_for(A, B), B, 0, st>>>(keys, act, A, hv, flag);
+        MB_CK(cudaGetLastError());
+        MB_TRY(scan_inclusive_max_u32(hv, hv, A, btmp.p, st));
+        k_set_rank<<<grid_for(A, B), B, 0, st>>>(vals, hv, A, rank);
+        MB_CK(cudaGetLastError());
+        MB_TRY(scan_exclusive_u32(flag, hv, A, count, btmp.p, st));
+        k_compact<<<grid_for(A, B), B, 0, st>>>(flag, hv, act, A, act2);
+        MB_CK(cudaGetLastError());
+        u32 A2 = 0, e = 0;
+        MB_CK(cudaMemcpyAsync(&A2, count, 4, cudaMemcpyDeviceToHost, st));
+        MB_CK(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, st));
+        MB_CK(cudaStreamSynchronize(st));
+        if (e) {
+            mb_set_error("suffix sort: an active suffix reached past the end of T (h=%llu)",
+                         (unsigned long long)h);
+            return MB_ERR_DEVICE_CHECK;
+        }
+        u32 *t = act; act = act2; act2 = t;
+        A = A2;
+        h *= 2;
+        if (h > 2 * n + 64) {
+            mb_set_error("suffix sort did not converge");
+            return MB_ERR_DEVICE_CHECK;
+        }
+    }
+    return MB_OK;
+}
+
+extern "C" int mb_index_build(const uint8_t *ref, uint64_t len, const mb_opts *opts, uint64_t n_seed,
+                              void *stream, mb_index **out) {
+    if (!ref || !out || len == 0) {
+        mb_set_error("mb_index_build: null argument or empty reference");
+        return MB_ERR_ARG;
+    }
+    *out = nullptr;
+    cudaStream_t st = (cudaStream_t)stream;
+    u32 flags = opts ? opts->flags : 0;
+    u32 r = opts && opts->sa_rate ? opts->sa_rate : 32;
+    u32 kk = opts && opts->kmer_k ? opts->kmer_k : 10;
+    if (kk > 12 || r == 0) {
+        mb_set_error("mb_index_build: kmer_k must be <= 12");
+        return MB_ERR_ARG;
+    }
+    int bs3 = (flags & MB_BS3) ? 1 : 0;
+    u64 M = bs3 ? 2 * len : len;
+    u64 n = 2 * M + 1;
+    if (n >= (1ULL << 32)) {
+        mb_set_error("mb_index_build: n = %llu must be below 2^32", (unsigned long long)n);
+        return MB_ERR_ARG;
+    }
+    mb_index *X = new mb_index;
+    X->n = n;
+    X->rlen = M;
+    X->sa_rate = r;
+    X->kmer_k = kk;
+    X->flags = flags & MB_BS3;
+    cudaGetDevice(&X->device);
+    int rc = MB_OK;
+    do {
+        DevBuf bref, bT, bcnt, btmp, bprim, btot;
+        const void *dref = nullptr;
+        if ((rc = mb_stage_in(ref, len, st, bref, &dref)) != MB_OK) break;
+        if ((rc = bT.alloc(n, st)) != MB_OK) break;
+        k_pack_text<<<grid_for(n, 256), 256, 0, st>>>((const u8 *)dref, len, n_seed, bs3, bT.as<u8>(), n);
+        if (cudaGetLastError() != cudaSuccess) { rc = MB_ERR_CUDA; break; }
+        bref.release();
+        if (cudaMalloc(&X->sa, n * 4) != cudaSuccess) { rc = MB_ERR_NOMEM; break; }
+        if ((rc = build_sa(bT.as<u8>(), n, X->sa, st)) != MB_OK) break;
+
+        // BWT in occurrence blocks
+        X->nblocks = n / 128 + 1;
+        const u64 nbk = X->nblocks;
+        if (cudaMalloc(&X->occ, nbk * sizeof(OccBlock)) != cudaSuccess) { rc = MB_ERR_NOMEM; break; }
+        if (cudaMemsetAsync(X->occ, 0, nbk * sizeof(OccBlock), st) != cudaSuccess) { rc = MB_ERR_CUDA; break; }
+        if ((rc = bcnt.alloc(nbk * 4 * 8, st)) != MB_OK) break;
+        if ((rc = btmp.alloc(scan_tmp_bytes(nbk), st)) != MB_OK) break;
+        if ((rc = bprim.alloc(8, st)) != MB_OK) break;
+        if ((rc = btot.alloc(4 * 8, st)) != MB_OK) break;
+        k_bwt_blocks<<<grid_for(nbk * 32, 256), 256, 0, st>>>(bT.as<u8>(), X->sa, n, X->occ, nbk, bcnt.as<u64>(),
+                                                              bprim.as<u64>());
+        if (cudaGetLastError() != cudaSuccess) { rc = MB_ERR_CUDA; break; }
+        for (int a = 0; a < 4 && rc == MB_OK; ++a)
+            rc = scan_exclusive_u64(bcnt.as<u64>() + a * nbk, bcnt.as<u64>() + a * nbk, nbk, btot.as<u64>() + a,
+                                    btmp.p, st);
+        if (rc != MB_OK) break;
+        k_fill_counts<<<grid_for(nbk, 256), 256, 0, st>>>(bcnt.as<u64>(), nbk, X->occ);
+        if (cudaGetLastError() != cudaSuccess) { rc = MB_ERR_CUDA; break; }
+        u64 tot[4], prim = 0;
+        if (cudaMemcpyAsync(tot, btot.p, 32, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(&prim, bprim.p, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) { rc = MB_ERR_CUDA; break; }
+        X->primary = prim;
+        X->C[0] = 0;
+        X->C[1] = 1;
+        for (int a = 1; a < 4; ++a) X->C[a + 1] = X->C[a] + tot[a - 1];
+
+        // sampled SA and k-mer table
+        u64 ns = (n + r - 1) / r;
+        if (cudaMalloc(&X->ssa, ns * 4) != cudaSuccess) { rc = MB_ERR_NOMEM; break; }
+        k_sample_sa<<<grid_for(ns, 256), 256, 0, st>>>(X->sa, n, r, X->ssa);
+        if (cudaGetLastError() != cudaSuccess) { rc = MB_ERR_CUDA; break; }
+        u64 nk = 1ULL << (2 * kk);
+        if (cudaMalloc(&X->kmer, nk * 12) != cudaSuccess) { rc = MB_ERR_NOMEM; break; }
+        k_kmer_table<<<grid_for(nk, 256), 256, 0, st>>>(mb_dev_index(X), kk, X->kmer);
+        if (cudaGetLastError() != cudaSuccess) { rc = MB_ERR_CUDA; break; }
+        if (cudaStreamSynchronize(st) != cudaSuccess) { rc = MB_ERR_CUDA; break; }
+    } while (0);
+    if (rc != MB_OK) {
+        cudaStreamSynchronize(st);
+        free_index(X);
+        return rc;
+    }
+    *out = X;
+    return MB_OK;
+}
+
+extern "C" void mb_index_free(mb_index *idx) { free_index(idx); }
+
+extern "C" int mb_index_info(const mb_index *idx, uint64_t *n, uint64_t *primary, uint64_t *ref_len) {
+    if (!idx) return MB_ERR_ARG;
+    if (n) *n = idx->n;
+    if (primary) *primary = idx->primary;
+    if (ref_len) *ref_len = idx->rlen;
+    return MB_OK;
+}
+
+extern "C" int mb_index_drop_sa(mb_index *idx) {
+    if (!idx) return MB_ERR_ARG;
+    if (idx->sa) cudaFree(idx->sa);
+    idx->sa = nullptr;
+    return MB_OK;
+}
+
+static int copy_out(void *dst, const void *src, size_t bytes) {
+    if (!dst || bytes == 0) return MB_OK;
+    MB_CK(cudaMemcpy(dst, src, bytes, cudaMemcpyDefault));
+    return MB_OK;
+}
+
+extern "C" int mb_index_export(const mb_index *idx, uint32_t *sa, uint8_t *bwt, uint32_t *ssa, void *occ_blocks,
+                               uint32_t *kmer, uint64_t *C) {
+    if (!idx) return MB_ERR_ARG;
+    if ((sa || bwt) && !idx->sa) {
+        mb_set_error("mb_index_export: the full suffix array was dropped");
+        return MB_ERR_ARG;
+    }
+    MB_TRY(copy_out(sa, idx->sa, idx->n * 4));
+    if (bwt) {
+        // decode B from the blocks on the host side of the caller's buffer
+        std::vector<OccBlock> blk(idx->nblocks);
+        MB_CK(cudaMemcpy(blk.data(), idx->occ, idx->nblocks * sizeof(OccBlock), cudaMemcpyDeviceToHost));
+        std::vector<u8> b(idx->n);
+        for (u64 x = 0; x < idx->n; ++x) {
+            u64 w = blk[x >> 7].w[(x & 127) >> 5];
+            b[x] = x == idx->primary ? 0 : (u8)(((w >> (2 * (x & 31))) & 3) + 1);
+        }
+        MB_TRY(copy_out(bwt, b.data(), idx->n));
+    }
+    MB_TRY(copy_out(ssa, idx->ssa, ((idx->n + idx->sa_rate - 1) / idx->sa_rate) * 4));
+    MB_TRY(copy_out(occ_blocks, idx->occ, idx->nblocks * sizeof(OccBlock)));
+    MB_TRY(copy_out(kmer, idx->kmer, (1ULL << (2 * idx->kmer_k)) * 12));
+    if (C) memcpy(C, idx->C, sizeof(idx->C));
+    return MB_OK;
+}
+
+// ----------------------------------------------------------------------------- save / load
+namespace {
+constexpr u64 MAGIC = 0x3130585744424D4DULL;   // "MMBDWX01"
+struct FileHeader {
+    u64 magic, version, n, rlen, primary, nblocks;
+    u32 sa_rate, kmer_k, flags, pad;
+    u64 C[5];
+    u64 checksum;
+};
+u64 checksum_words(const void *p, size_t bytes, u64 h) {
+    const u8 *b = (const u8 *)p;
+    size_t nw = bytes / 8;
+    for (size_t i = 0; i < nw; ++i) {
+        u64 w;
+        memcpy(&w, b + 8 * i, 8);
+        h = (h ^ w) * 0x100000001B3ULL;
+        h ^= h >> 29;
+    }
+    for (size_t i = nw * 8; i < bytes; ++i) h = (h ^ b[i]) * 0x100000001B3ULL;
+    return h;
+}
+}  // namespace
+
+extern "C" int mb_index_save(const mb_index *idx, const char *path) {
+    if (!idx || !path) return MB_ERR_ARG;
+    u64 ns = (idx->n + idx->sa_rate - 1) / idx->sa_rate, nk = 1ULL << (2 * idx->kmer_k);
+    std::vector<u8> occ(idx->nblocks * sizeof(OccBlock)), ssa(ns * 4), km(nk * 12);
+    MB_CK(cudaMemcpy(occ.data(), idx->occ, occ.size(), cudaMemcpyDeviceToHost));
+    MB_CK(cudaMemcpy(ssa.data(), idx->ssa, ssa.size(), cudaMemcpyDeviceToHost));
+    MB_CK(cudaMemcpy(km.data(), idx->kmer, km.size(), cudaMemcpyDeviceToHost));
+    FileHeader h;
+    memset(&h, 0, sizeof h);
+    h.magic = MAGIC;
+    h.version = 1;
+    h.n = idx->n;
+    h.rlen = idx->rlen;
+    h.primary = idx->primary;
+    h.nblocks = idx->nblocks;
+    h.sa_rate = idx->sa_rate;
+    h.kmer_k = idx->kmer_k;
+    h.flags = idx->flags;
+    memcpy(h.C, idx->C, sizeof h.C);
+    u64 cs = checksum_words(&h, offsetof(FileHeader, checksum), 0xCBF29CE484222325ULL);
+    cs = checksum_words(occ.data(), occ.size(), cs);
+    cs = checksum_words(ssa.data(), ssa.size(), cs);
+    cs = checksum_words(km.data(), km.size(), cs);
+    h.checksum = cs;
+    FILE *f = fopen(path, "wb");
+    if (!f) {
+        mb_set_error("mb_index_save: cannot open %s", path);
+        return MB_ERR_IO;
+    }
+    bool ok = fwrite(&h, sizeof h, 1, f) == 1 && fwrite(occ.data(), 1, occ.size(), f) == occ.size() &&
+              fwrite(ssa.data(), 1, ssa.size(), f) == ssa.size() && fwrite(km.data(), 1, km.size(), f) == km.size();
+    ok = (fclose(f) == 0) && ok;
+    if (!ok) {
+        mb_set_error("mb_index_save: write to %s failed", path);
+        return MB_ERR_IO;
+    }
+    return MB_OK;
+}
+
+extern "C" int mb_index_load(const char *path, void *stream, mb_index **out) {
+    if (!path || !out) return MB_ERR_ARG;
+    *out = nullptr;
+    FILE *f = fopen(path, "rb");
+    if (!f) {
+        mb_set_error("mb_index_load: cannot open %s", path);
+        return MB_ERR_IO;
+    }
+    FileHeader h;
+    if (fread(&h, sizeof h, 1, f) != 1) {
+        fclose(f);
+        mb_set_error("mb_index_load: short header");
+        return MB_ERR_CORRUPT;
+    }
+    if (h.magic != MAGIC || h.version != 1 || h.sa_rate == 0 || h.kmer_k > 12 || h.n >= (1ULL << 32) ||
+        h.nblocks != h.n / 128 + 1) {
+        fclose(f);
+        mb_set_error("mb_index_load: bad header");
+        return MB_ERR_CORRUPT;
+    }
+    u64 ns = (h.n + h.sa_rate - 1) / h.sa_rate, nk = 1ULL << (2 * h.kmer_k);
+    std::vector<u8> occ(h.nblocks * sizeof(OccBlock)), ssa(ns * 4), km(nk * 12);
+    bool ok = fread(occ.data(), 1, occ.size(), f) == occ.size() && fread(ssa.data(), 1, ssa.size(), f) == ssa.size() &&
+              fread(km.data(), 1, km.size(), f) == km.size();
+    fclose(f);
+    if (!ok) {
+        mb_set_error("mb_index_load: truncated file");
+        return MB_ERR_CORRUPT;
+    }
+    u64 cs = checksum_words(&h, offsetof(FileHeader, checksum), 0xCBF29CE484222325ULL);
+    cs = checksum_words(occ.data(), occ.size(), cs);
+    cs = checksum_words(ssa.data(), ssa.size(), cs);
+    cs = checksum_words(km.data(), km.size(), cs);
+    if (cs != h.checksum) {
+        mb_set_error("mb_index_load: checksum mismatch");
+        return MB_ERR_CORRUPT;
+    }
+    mb_index *X = new mb_index;
+    X->n = h.n;
+    X->rlen = h.rlen;
+    X->primary = h.primary;
+    X->nblocks = h.nblocks;
+    X->sa_rate = h.sa_rate;
+    X->kmer_k = h.kmer_k;
+    X->flags = h.flags;
+    memcpy(X->C, h.C, sizeof h.C);
+    cudaGetDevice(&X->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMalloc(&X->occ, occ.size()) != cudaSuccess || cudaMalloc(&X->ssa, ssa.size()) != cudaSuccess ||
+        cudaMalloc(&X->kmer, km.size()) != cudaSuccess) {
+        free_index(X);
+        mb_set_error("mb_index_load: device allocation failed");
+        return MB_ERR_NOMEM;
+    }
+    if (cudaMemcpyAsync(X->occ, occ.data(), occ.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(X->ssa, ssa.data(), ssa.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(X->kmer, km.data(), km.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        free_index(X);
+        mb_set_error("mb_index_load: copy to device failed");
+        return MB_ERR_CUDA;
+    }
+    *out = X;
+    return MB_OK;
+}
+
+extern "C" int mb_hit_to_ref(const mb_index *idx, uint64_t pos, uint64_t len, int *strand, uint64_t *rpos) {
+    if (!idx || !strand || !rpos || pos + len > idx->n - 1) return MB_ERR_ARG;
+    u64 M = idx->rlen;
+    if (pos < M) {
+        *strand = 0;
+        *rpos = pos;
+    } else {
+        *strand = 1;
+        *rpos = 2 * M - pos - len;
+    }
+    return MB_OK;
+}
+
+extern "C" const char *mb_strerror(int code) {
+    switch (code) {
+    case MB_OK: return "ok";
+    case MB_ERR_ARG: return "invalid argument";
+    case MB_ERR_NOMEM: return "out of memory";
+    case MB_ERR_CAPACITY: return "output buffer too small";
+    case MB_ERR_CUDA: return "CUDA error";
+    case MB_ERR_TIMEOUT: return "timed out";
+    case MB_ERR_IO: return "I/O error";
+    case MB_ERR_CORRUPT: return "corrupt index file";
+    case MB_ERR_DEVICE_CHECK: return "device-side check failed";
+    case MB_ERR_BUSY: return "busy";
+    default: return "unknown error";
+    }
+}

@@ -1,0 +1,405 @@
+// Seeding on the GPU: (l,c)-SMEM finding (Section 2.5, Algorithm 3), the max-occurrence flag,
+// and locate through the sampled suffix array (Section 2.3, Algorithm 2).
+//
+// SMEMs: one thread runs Algorithm 3's three-stage state machine for one read.  In Algorithm 3
+// every read has exactly one entry in the queue at any time, so the per-read order of queue
+// operations is the serial order below; the GPU's many resident warps take the place of the
+// paper's queue-plus-prefetch as the way to keep many block reads in flight.  Every step that
+// touches memory is one extension (Algorithm 1), i.e. two occurrence-block reads, so all lanes
+// of a warp share the same memory instruction whatever stage they are in.
+//
+// Output: each read first writes its SMEMs into a private run of slots in scratch memory
+// (off[r]/32 + 4r slots before it), a prefix sum over the per-read counts gives the final
+// positions, and a gather writes the 48-byte records.  Reads with more SMEMs than slots are
+// listed and recomputed straight into the final records.
+#include "common.cuh"
+
+DevIndex mb_dev_index(const mb_index *x);
+int mb_index_device(const mb_index *x);
+u32 mb_index_flags(const mb_index *x);
+
+namespace {
+
+struct SlotRec {
+    u32 qbeg, qend, k, kr, s;
+};
+
+__device__ __forceinline__ u64 slot_base(const u64 *off, u64 r) { return (off[r] - off[0]) / 32 + 4 * r; }
+
+// read base with the bisulfite conversion of Section 2.8 (conv 1: C->T, conv 2: G->A); > 3 = N
+__device__ __forceinline__ u32 read_base(const u8 *__restrict__ P, u64 j, u32 conv) {
+    u32 b = P[j];
+    if (conv == 1 && b == 1) b = 3;
+    if (conv == 2 && b == 2) b = 0;
+    return b;
+}
+
+// Algorithm 3 for one read P[0, L).  emit(i, j, k, kr, s) receives the SMEMs in ascending i.
+template <class Emit>
+__device__ __forceinline__ void smem_read(const DevIndex &I, const u8 *__restrict__ P, int64_t L, u32 l, u32 c,
+                                          u32 conv, Emit &emit) {
+    const int64_t ll = (int64_t)l;
+    if (ll - 1 >= L) return;
+    int u = 1;
+    int64_t i = 0, j = ll - 1;
+    u64 k = 0, kr = 0, s = I.n;
+    for (;;) {
+        if (u == 1 && j < i) {              // stage 1 done: P[i, i+l) is a match
+            u = 2;
+            j = i + ll;
+            continue;
+        }
+        if (u == 2 && j == L) {             // reached the end of P
+            emit(i, j, k, kr, s);
+            return;
+        }
+        if (u == 3 && j <= i) {             // back to stage 1 at the next start
+            u = 1;
+            i = j + 1;
+            j = j + ll;
+            k = 0; kr = 0; s = I.n;
+            continue;
+        }
+        const u32 a = read_base(P, (u64)j, conv);
+        const bool fwd = u == 2;
+        u64 nk = 0, nkr = 0, ns = 0;
+        if (a < 4) {
+            if (!fwd) {                     // BackwardExt((k,kr,s), a)
+                Ext e = extend(I, k, kr, s, a);
+                nk = e.p; nkr = e.q; ns = e.s;
+            } else {                        // ForwardExt((k,kr,s), a) = BackwardExt((kr,k,s), comp a)
+                Ext e = extend(I, kr, k, s, 3u - a);
+                nk = e.q; nkr = e.p; ns = e.s;
+            }
+        }
+        if (fwd) {
+            if (ns >= c) {
+                ++j;
+                k = nk; kr = nkr; s = ns;
+            } else {
+                emit(i, j, k, kr, s);
+                u = 3;
+                k = 0; kr = 0; s = I.n;
+            }
+        } else {                            // BackStep
+            if (ns >= c) {
+                --j;
+                k = nk; kr = nkr; s = ns;
+            } else if (j + ll < L) {
+                u = 1;
+                i = j + 1;
+                j = j + ll;
+                k = 0; kr = 0; s = I.n;
+            } else {
+                return;
+            }
+        }
+    }
+}
+
+struct SlotEmit {
+    SlotRec *slots;
+    u64 base, cap, cnt;
+    __device__ __forceinline__ void operator()(int64_t i, int64_t j, u64 k, u64 kr, u64 s) {
+        if (cnt < cap) slots[base + cnt] = SlotRec{(u32)i, (u32)j, (u32)k, (u32)kr, (u32)s};
+        ++cnt;
+    }
+};
+
+__device__ __forceinline__ u32 conv_of(const u8 *mate, u64 r, u32 bs) {
+    if (!bs || !mate) return 0;
+    u8 m = mate[r];
+    return m == 1 ? 1u : (m == 2 ? 2u : 0u);
+}
+
+__global__ void __launch_bounds__(256) k_smem(DevIndex I, const u8 *__restrict__ seq, const u64 *__restrict__ off,
+                                              u32 nr, const u8 *__restrict__ mate, u32 bs, u32 l, u32 c,
+                                              SlotRec *__restrict__ slots, u64 *__restrict__ counts,
+                                              u32 *__restrict__ ovf_list, u32 *__restrict__ ovf_n) {
+    u64 r = blockIdx.x * (u64)blockDim.x + threadIdx.x;
+    if (r >= nr) return;
+    u64 b = off[r], e = off[r + 1];
+    SlotEmit em{slots, slot_base(off, r), slot_base(off, r + 1) - slot_base(off, r), 0};
+    smem_read(I, seq + b, (int64_t)(e - b), l, c, conv_of(mate, r, bs), em);
+    counts[r] = em.cnt;
+    if (em.cnt > em.cap) ovf_list[atomicAdd(ovf_n, 1u)] = (u32)r;
+}
+
+__device__ __forceinline__ void write_rec(mb_smem *out, u64 *hitc, u64 m, u32 r, u32 qbeg, u32 qend, u64 k, u64 kr,
+                                          u64 s, u32 max_occ) {
+    mb_smem x;
+    x.read = r;
+    x.qbeg = qbeg;
+    x.qend = qend;
+    x.flags = s > max_occ ? MB_SMEM_OVER_MAX_OCC : 0u;
+    x.k = k;
+    x.kr = kr;
+    x.s = s;
+    x.hit_off = 0;
+    out[m] = x;
+    hitc[m] = s > max_occ ? 0 : s;
+}
+
+__global__ void k_gather(const u64 *__restrict__ off, u32 nr, const SlotRec *__restrict__ slots,
+                         const u64 *__restrict__ counts, const u64 *__restrict__ soff, u32 max_occ,
+                         mb_smem *__restrict__ out, u64 *__restrict__ hitc) {
+    u64 r = blockIdx.x * (u64)blockDim.x + threadIdx.x;
+    if (r >= nr) return;
+    u64 sb = slot_base(off, r), cap = slot_base(off, r + 1) - sb, cnt = counts[r];
+    if (cnt > cap) return;   // recomputed by k_smem_overflow
+    u64 o = soff[r];
+    for (u64 t = 0; t < cnt; ++t) {
+        SlotRec x = slots[sb + t];
+        write_rec(out, hitc, o + t, (u32)r, x.qbeg, x.qend, x.k, x.kr, x.s, max_occ);
+    }
+}
+
+struct FinalEmit {
+    mb_smem *out;
+    u64 *hitc;
+    u64 o;
+    u32 r, max_occ;
+    __device__ __forceinline__ void operator()(int64_t i, int64_t j, u64 k, u64 kr, u64 s) {
+        write_rec(out, hitc, o++, r, (u32)i, (u32)j, k, kr, s, max_occ);
+    }
+};
+
+__global__ void k_smem_overflow(DevIndex I, const u8 *__restrict__ seq, const u64 *__restrict__ off,
+                                const u8 *__restrict__ mate, u32 bs, u32 l, u32 c, const u32 *__restrict__ ovf_list,
+                                const u32 *__restrict__ ovf_n, const u64 *__restrict__ soff, u32 max_occ,
+                                mb_smem *__restrict__ out, u64 *__restrict__ hitc) {
+    u32 n = *ovf_n;
+    for (u32 q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        u32 r = ovf_list[q];
+        FinalEmit em{out, hitc, soff[r], r, max_occ};
+        smem_read(I, seq + off[r], (int64_t)(off[r + 1] - off[r]), l, c, conv_of(mate, r, bs), em);
+    }
+}
+
+__global__ void k_set_hitoff(const u64 *__restrict__ hoff, u64 m, mb_smem *__restrict__ out) {
+    for (u64 t = blockIdx.x * (u64)blockDim.x + threadIdx.x; t < m; t += (u64)gridDim.x * blockDim.x)
+        out[t].hit_off = hoff[t];
+}
+
+// ---------------------------------------------------------------------------- locate
+// Largest record index m with hit_off <= h (records with no hits share the offset of the next
+// record that has hits, so the last such record is the one owning hit h).
+__device__ __forceinline__ u64 owner_of(const mb_smem *__restrict__ sm, u64 nsm, u64 h) {
+    u64 a = 0, b = nsm;   // invariant: hit_off[a] <= h, answer in [a, b)
+    while (b - a > 1) {
+        u64 mid = (a + b) >> 1;
+        if (__ldg(&sm[mid].hit_off) <= h) a = mid;
+        else b = mid;
+    }
+    return a;
+}
+
+// LF-walk from `row` to a sampled row (Algorithm 2).  The $ row (S = 0) ends a walk too: its
+// position is the number of steps taken.  A walk never needs more than n steps; the bound only
+// guards against a corrupted index (it then yields 0xFFFFFFFF).
+__device__ __forceinline__ u32 lf_walk(const DevIndex &I, u64 row) {
+    for (u64 steps = 0; steps <= I.n; ++steps) {
+        if (row % I.r == 0) return (u32)(I.ssa[row / I.r] + steps);
+        if (row == I.primary) return (u32)steps;
+        const BlockVals v = load_block(I.occ + (row >> 7));
+        const u32 a = sym_from_vals(v, row);
+        Occ4 o;
+        occ_from_vals(v, row, I.primary, o);
+        row = sel4(a, I.C[0] + o.c[0], I.C[1] + o.c[1], I.C[2] + o.c[2], I.C[3] + o.c[3]);
+    }
+    return 0xFFFFFFFFu;
+}
+
+__global__ void __launch_bounds__(256) k_locate(DevIndex I, const mb_smem *__restrict__ sm, u64 nsm, u64 nhits,
+                                                u32 *__restrict__ hits) {
+    for (u64 h = blockIdx.x * (u64)blockDim.x + threadIdx.x; h < nhits; h += (u64)gridDim.x * blockDim.x) {
+        u64 m = owner_of(sm, nsm, h);
+        u64 row = __ldg(&sm[m].k) + (h - __ldg(&sm[m].hit_off));
+        hits[h] = lf_walk(I, row);
+    }
+}
+
+__global__ void k_bs_filter(const mb_smem *__restrict__ sm, u64 nsm, const u8 *__restrict__ mate,
+                            const u32 *__restrict__ hits, u64 nhits, u64 M, u8 *__restrict__ keep) {
+    for (u64 h = blockIdx.x * (u64)blockDim.x + threadIdx.x; h < nhits; h += (u64)gridDim.x * blockDim.x) {
+        u64 m = owner_of(sm, nsm, h);
+        u64 len = sm[m].qend - sm[m].qbeg;
+        u8 mt = mate ? mate[sm[m].read] : 0;
+        u64 pos = hits[h];
+        u64 seg = pos / M;
+        bool whole = (pos + len - 1) / M == seg;
+        bool ok = mt == 1 ? (seg == 0 || seg == 2) : mt == 2 ? (seg == 1 || seg == 3) : true;
+        keep[h] = (whole && ok) ? 1 : 0;
+    }
+}
+
+void opts_defaults(const mb_opts *o, u32 &l, u32 &c, u32 &max_occ, u32 &flags) {
+    l = o && o->min_len ? o->min_len : 19;
+    c = o && o->min_occ ? o->min_occ : 1;
+    max_occ = o && o->max_occ ? o->max_occ : 500;
+    flags = o ? o->flags : 0;
+}
+
+}  // namespace
+
+// ============================================================================ host entry points
+extern "C" int mb_seed_batch(const mb_index *idx, const uint8_t *seq, const uint64_t *off, uint32_t n_reads,
+                             const uint8_t *mate, const mb_opts *opts, void *stream, mb_smem *out, uint64_t cap,
+                             uint64_t *n_out, uint64_t *n_hits) {
+    if (!idx || !off || !n_out || (n_reads > 0 && !seq)) {
+        mb_set_error("mb_seed_batch: null argument");
+        return MB_ERR_ARG;
+    }
+    u32 l, c, max_occ, flags;
+    opts_defaults(opts, l, c, max_occ, flags);
+    cudaStream_t st = (cudaStream_t)stream;
+    *n_out = 0;
+    if (n_hits) *n_hits = 0;
+    if (n_reads == 0) return MB_OK;
+    const u32 bs = (flags & MB_BS3) ? 1u : 0u;
+
+    // offsets to the host to size the inputs and scratch
+    DevBuf boff, bseq, bmate;
+    const void *doff = nullptr, *dseq = nullptr, *dmate = nullptr;
+    u64 o0 = 0, o1 = 0;
+    MB_CK(cudaMemcpyAsync(&o0, off, 8, cudaMemcpyDefault, st));
+    MB_CK(cudaMemcpyAsync(&o1, off + n_reads, 8, cudaMemcpyDefault, st));
+    MB_CK(cudaStreamSynchronize(st));
+    if (o1 < o0) {
+        mb_set_error("mb_seed_batch: offsets decrease");
+        return MB_ERR_ARG;
+    }
+    MB_TRY(mb_stage_in(off, (size_t)(n_reads + 1) * 8, st, boff, &doff));
+    // a host `seq` is staged from off[0]; device pointers are used as given
+    if (mb_is_device_ptr(seq)) dseq = seq;
+    else {
+        MB_TRY(bseq.alloc(o1 - o0 + 1, st));
+        MB_CK(cudaMemcpyAsync(bseq.as<u8>() + 0, seq + o0, o1 - o0, cudaMemcpyHostToDevice, st));
+        dseq = bseq.as<u8>() - o0;
+    }
+    if (mate) MB_TRY(mb_stage_in(mate, n_reads, st, bmate, &dmate));
+
+    const u64 nslots = (o1 - o0) / 32 + 4ULL * n_reads + 4;
+    DevBuf bslots, bcounts, bsoff, bovf, bmisc, btmp;
+    MB_TRY(bslots.alloc(nslots * sizeof(SlotRec), st));
+    MB_TRY(bcounts.alloc((size_t)n_reads * 8, st));
+    MB_TRY(bsoff.alloc((size_t)n_reads * 8, st));
+    MB_TRY(bovf.alloc((size_t)n_reads * 4, st));
+    MB_TRY(bmisc.alloc(64, st));
+    u64 *dtotal = bmisc.as<u64>(), *dhtotal = bmisc.as<u64>() + 1;
+    u32 *dovf_n = (u32 *)(bmisc.as<u64>() + 2);
+    MB_CK(cudaMemsetAsync(bmisc.p, 0, 64, st));
+
+    const DevIndex I = mb_dev_index(idx);
+    const unsigned B = 256;
+    const unsigned G = (unsigned)((n_reads + B - 1) / B);
+    k_smem<<<G, B, 0, st>>>(I, (const u8 *)dseq, (const u64 *)doff, n_reads, (const u8 *)dmate, bs, l, c,
+                            bslots.as<SlotRec>(), bcounts.as<u64>(), bovf.as<u32>(), dovf_n);
+    MB_CK(cudaGetLastError());
+    MB_TRY(btmp.alloc(scan_tmp_bytes(n_reads), st));
+    MB_TRY(scan_exclusive_u64(bcounts.as<u64>(), bsoff.as<u64>(), n_reads, dtotal, btmp.p, st));
+    u64 total = 0;
+    MB_CK(cudaMemcpyAsync(&total, dtotal, 8, cudaMemcpyDeviceToHost, st));
+    MB_CK(cudaStreamSynchronize(st));
+    *n_out = total;
+    if (total > cap) return MB_ERR_CAPACITY;
+    if (total == 0) return MB_OK;
+
+    const bool out_dev = mb_is_device_ptr(out);
+    if (!out) {
+        mb_set_error("mb_seed_batch: null output");
+        return MB_ERR_ARG;
+    }
+    DevBuf bout, bhitc, bhtmp;
+    mb_smem *dout = out;
+    if (!out_dev) {
+        MB_TRY(bout.alloc(total * sizeof(mb_smem), st));
+        dout = bout.as<mb_smem>();
+    }
+    MB_TRY(bhitc.alloc(total * 8, st));
+    k_gather<<<G, B, 0, st>>>((const u64 *)doff, n_reads, bslots.as<SlotRec>(), bcounts.as<u64>(), bsoff.as<u64>(),
+                              max_occ, dout, bhitc.as<u64>());
+    MB_CK(cudaGetLastError());
+    k_smem_overflow<<<152, 128, 0, st>>>(I, (const u8 *)dseq, (const u64 *)doff, (const u8 *)dmate, bs, l, c,
+                                         bovf.as<u32>(), dovf_n, bsoff.as<u64>(), max_occ, dout, bhitc.as<u64>());
+    MB_CK(cudaGetLastError());
+    MB_TRY(bhtmp.alloc(scan_tmp_bytes(total), st));
+    MB_TRY(scan_exclusive_u64(bhitc.as<u64>(), bhitc.as<u64>(), total, dhtotal, bhtmp.p, st));
+    k_set_hitoff<<<grid_for(total, 256), 256, 0, st>>>(bhitc.as<u64>(), total, dout);
+    MB_CK(cudaGetLastError());
+    u64 ht = 0;
+    MB_CK(cudaMemcpyAsync(&ht, dhtotal, 8, cudaMemcpyDeviceToHost, st));
+    if (!out_dev) MB_CK(cudaMemcpyAsync(out, dout, total * sizeof(mb_smem), cudaMemcpyDeviceToHost, st));
+    MB_CK(cudaStreamSynchronize(st));
+    if (n_hits) *n_hits = ht;
+    return MB_OK;
+}
+
+extern "C" int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_smem, const mb_opts *opts,
+                         void *stream, uint32_t *hits, uint64_t cap, uint64_t *n_hits) {
+    (void)opts;
+    if (!idx || !n_hits || (n_smem && !smem)) {
+        mb_set_error("mb_locate: null argument");
+        return MB_ERR_ARG;
+    }
+    *n_hits = 0;
+    if (n_smem == 0) return MB_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    DevBuf bsm, bhits;
+    const void *dsm = nullptr;
+    MB_TRY(mb_stage_in(smem, n_smem * sizeof(mb_smem), st, bsm, &dsm));
+    mb_smem last;
+    MB_CK(cudaMemcpyAsync(&last, (const mb_smem *)dsm + n_smem - 1, sizeof last, cudaMemcpyDeviceToHost, st));
+    MB_CK(cudaStreamSynchronize(st));
+    u64 total = last.hit_off + ((last.flags & MB_SMEM_OVER_MAX_OCC) ? 0 : last.s);
+    *n_hits = total;
+    if (total > cap) return MB_ERR_CAPACITY;
+    if (total == 0) return MB_OK;
+    if (!hits) return MB_ERR_ARG;
+    u32 *dh = hits;
+    const bool hdev = mb_is_device_ptr(hits);
+    if (!hdev) {
+        MB_TRY(bhits.alloc(total * 4, st));
+        dh = bhits.as<u32>();
+    }
+    const DevIndex I = mb_dev_index(idx);
+    k_locate<<<grid_for(total, 256, 152u * 2048u / 256u * 8u), 256, 0, st>>>(I, (const mb_smem *)dsm, n_smem, total,
+                                                                             dh);
+    MB_CK(cudaGetLastError());
+    if (!hdev) MB_CK(cudaMemcpyAsync(hits, dh, total * 4, cudaMemcpyDeviceToHost, st));
+    MB_CK(cudaStreamSynchronize(st));
+    return MB_OK;
+}
+
+extern "C" int mb_bs_filter(const mb_index *idx, const mb_smem *smem, uint64_t n_smem, const uint8_t *mate,
+                            const uint32_t *hits, uint64_t n_hits, void *stream, uint8_t *keep) {
+    if (!idx || (n_hits && (!smem || !hits || !keep))) return MB_ERR_ARG;
+    if (n_hits == 0) return MB_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    DevBuf bsm, bmate, bhits, bkeep;
+    const void *dsm = nullptr, *dmate = nullptr, *dhits = nullptr;
+    MB_TRY(mb_stage_in(smem, n_smem * sizeof(mb_smem), st, bsm, &dsm));
+    if (mate) {
+        mb_smem last;
+        MB_CK(cudaMemcpyAsync(&last, (const mb_smem *)dsm + n_smem - 1, sizeof last, cudaMemcpyDeviceToHost, st));
+        MB_CK(cudaStreamSynchronize(st));
+        MB_TRY(mb_stage_in(mate, (size_t)last.read + 1, st, bmate, &dmate));
+    }
+    MB_TRY(mb_stage_in(hits, n_hits * 4, st, bhits, &dhits));
+    u8 *dk = keep;
+    const bool kdev = mb_is_device_ptr(keep);
+    if (!kdev) {
+        MB_TRY(bkeep.alloc(n_hits, st));
+        dk = bkeep.as<u8>();
+    }
+    u64 M = 0, n = 0, prim = 0;
+    mb_index_info(idx, &n, &prim, &M);
+    // the 3-base index holds four copies of |R| = M/2 bases
+    u64 quarter = M / 2;
+    k_bs_filter<<<grid_for(n_hits, 256), 256, 0, st>>>((const mb_smem *)dsm, n_smem, (const u8 *)dmate,
+                                                       (const u32 *)dhits, n_hits, quarter, dk);
+    MB_CK(cudaGetLastError());
+    if (!kdev) MB_CK(cudaMemcpyAsync(keep, dk, n_hits, cudaMemcpyDeviceToHost, st));
+    MB_CK(cudaStreamSynchronize(st));
+    return MB_OK;
+}

@@ -1,0 +1,199 @@
+"""GPU path against the CPU oracle, through the C ABI.
+
+Every field is integer: the bar is bit-exact equality (SA, BWT, occurrence
+counts, sampled SA, k-mer table, SMEM records, max-occ flags, hit offsets,
+hit positions).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mb():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2606_15357_gb300 as m
+    m.lib()
+    return m
+
+
+def dev(a):
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint64:
+        return torch.from_numpy(a.view(np.int64)).cuda()
+    return torch.from_numpy(a).cuda()
+
+
+def compare_index(G, X, k=10):
+    e = G.export(sa=True, bwt=True, ssa=True, occ=True, kmer=True, kmer_k=k)
+    assert G.n == X.n and G.primary == X.primary
+    assert np.array_equal(e["sa"], X.sa())
+    assert np.array_equal(e["bwt"], X.bwt())
+    assert np.array_equal(e["ssa"], X.ssa())
+    assert np.array_equal(e["C"], X.C)
+    # block counts: #a in B[0, 128b) excluding $
+    B = X.bwt()
+    occ = e["occ"].reshape(-1, 8)
+    for a in range(4):
+        cum = np.concatenate([[0], np.cumsum(B == a + 1)])
+        assert np.array_equal(occ[:, a], cum[np.arange(len(occ)) * 128].astype(np.uint64))
+    # k-mer table against the definition
+    nk = 4 ** k
+    words = np.arange(nk, dtype=np.int64)
+    pats = np.stack([(words >> (2 * (k - 1 - t))) & 3 for t in range(k)], axis=1).astype(np.uint8)
+    want = X.ds_intervals(pats).astype(np.uint32)
+    got = e["kmer"].reshape(nk, 3)
+    assert np.array_equal(got, want)
+
+
+def compare_seed(sm, hits, X, seq, off, l=19, c=1, max_occ=500):
+    osm, over, hoff, ohits = X.seed(seq, off, l, c, max_occ)
+    assert len(sm) == len(osm)
+    for f in ("read", "qbeg", "qend", "k", "kr", "s"):
+        assert np.array_equal(sm[f].astype(np.uint64), osm[f]), f
+    assert np.array_equal((sm["flags"] & 1).astype(bool), over)
+    assert np.array_equal(sm["hit_off"], hoff)
+    assert np.array_equal(np.asarray(hits).astype(np.uint64), ohits)
+
+
+@pytest.mark.parametrize("length", [1, 2, 3, 100, 127, 128, 129, 1000, 4095])
+def test_index_tiny_lengths(mb, length):
+    ref = synth.reference(length, 1000 + length)
+    G = mb.mb_index_build(ref, n_seed=3)
+    X = oracle.Index(ref, n_seed=3)
+    compare_index(G, X)
+
+
+def test_index_repeat_rich_with_n(mb):
+    ref = synth.repeat_rich_reference(300_000, 41, 0.45)
+    assert (ref == 4).any()
+    G = mb.mb_index_build(dev(ref), n_seed=77)
+    X = oracle.Index(ref, n_seed=77)
+    compare_index(G, X)
+
+
+def test_index_periodic_text(mb):
+    # one short unit repeated: common prefixes of tens of thousands of symbols force many
+    # prefix-doubling rounds
+    ref = np.tile(synth.reference(7, 5), 6000)
+    G = mb.mb_index_build(ref)
+    X = oracle.Index(ref)
+    compare_index(G, X)
+
+
+def test_workload1_full(mb):
+    """1 Mbp uniform reference, 10,000 single-end 150 bp reads, 0.5% substitutions."""
+    ref, rd, p = synth.workload(1)
+    G = mb.mb_index_build(ref)
+    X = oracle.Index(ref)
+    compare_index(G, X)
+    sm, hits = mb.seed(G, rd.seq, rd.off)
+    compare_seed(sm, hits, X, rd.seq, rd.off)
+
+
+def test_workload2_scaled_device_pointers(mb):
+    """Repeat-rich reference with N runs, paired 2x150 reads with indels; device buffers."""
+    ref, rd, p = synth.workload(2, scale=0.02)
+    G = mb.mb_index_build(dev(ref))
+    X = oracle.Index(ref)
+    seq, off = dev(rd.seq), dev(rd.off)
+    out = torch.empty(rd.n * 8 * 48, dtype=torch.uint8, device="cuda")
+    out, m, nh = mb.mb_seed_batch(G, seq, off, out=out, cap=rd.n * 8)
+    hits = torch.empty(max(nh, 1), dtype=torch.int32, device="cuda")
+    mb.mb_locate(G, out, m, hits=hits, cap=nh)
+    sm = out[:m * 48].cpu().numpy().view(mb.SMEM_DTYPE)
+    compare_seed(sm, hits[:nh].cpu().numpy().view(np.uint32), X, rd.seq, rd.off)
+
+
+def test_workload4_mixed_lengths(mb):
+    """Log-uniform 100 bp - 10 kb reads in one batch (reads that overflow their slots)."""
+    ref, rd, p = synth.workload(4, scale=0.004)
+    G = mb.mb_index_build(ref)
+    X = oracle.Index(ref)
+    sm, hits = mb.seed(G, rd.seq, rd.off)
+    compare_seed(sm, hits, X, rd.seq, rd.off)
+
+
+@pytest.mark.parametrize("l,c,max_occ", [(1, 1, 500), (5, 1, 3), (19, 2, 500), (12, 3, 50),
+                                         (30, 1, 500)])
+def test_parameters_and_overflow(mb, l, c, max_occ):
+    ref = synth.repeat_rich_reference(40_000, 51, 0.3)
+    rd = synth.reads(ref, 300, 52, mode=0, read_len=150, sub_lo=0.02, indel=0.002)
+    G = mb.mb_index_build(ref)
+    X = oracle.Index(ref)
+    o = dict(min_len=l, min_occ=c, max_occ=max_occ)
+    sm, hits = mb.seed(G, rd.seq, rd.off, opts=o)
+    compare_seed(sm, hits, X, rd.seq, rd.off, l, c, max_occ)
+
+
+def test_edge_reads(mb):
+    ref = synth.reference(20_000, 61)
+    G = mb.mb_index_build(ref)
+    X = oracle.Index(ref)
+    reads = [np.zeros(0, np.uint8), ref[100:118], ref[200:219], ref[300:320],
+             np.full(150, 4, np.uint8), np.concatenate([ref[400:450], [4], ref[451:500]]),
+             ref[1000:1150], synth.reference(150, 999)]
+    seq = np.concatenate(reads).astype(np.uint8)
+    off = np.concatenate([[0], np.cumsum([len(r) for r in reads])]).astype(np.uint64)
+    sm, hits = mb.seed(G, seq, off)
+    compare_seed(sm, hits, X, seq, off)
+    # empty batch
+    e, m, nh = mb.mb_seed_batch(G, seq, off[:1])
+    assert m == 0 and nh == 0
+
+
+def test_capacity_error_reports_needed(mb):
+    ref, rd, p = synth.workload(1, scale=0.01)
+    G = mb.mb_index_build(ref)
+    buf = np.empty(1, dtype=mb.SMEM_DTYPE)
+    with pytest.raises(mb.MbError) as ei:
+        mb.mb_seed_batch(G, rd.seq, rd.off, out=buf, cap=1)
+    assert ei.value.code == -3
+
+
+def test_bisulfite_index_and_seeding(mb):
+    ref = synth.reference(50_000, 71)
+    rd = synth.reads(ref, 400, 72, mode=1, read_len=150, bisulfite=True, sub_lo=0.001)
+    o = dict(flags=mb.MB_BS3)
+    G = mb.mb_index_build(ref, opts=o)
+    X = oracle.Index(ref, bs3=True)
+    compare_index(G, X)
+    conv = oracle.bs_convert_reads(rd.seq, rd.off, rd.mate)
+    sm, m, nh = mb.mb_seed_batch(G, rd.seq, rd.off, mate=rd.mate, opts=o)
+    hits, _ = mb.mb_locate(G, sm, m, opts=o, cap=nh)
+    compare_seed(sm, hits, X, conv, rd.off)
+    keep = mb.mb_bs_filter(G, sm, m, rd.mate, hits, nh)
+    osm, over, hoff, ohits = X.seed(conv, rd.off)
+    cnt = np.where(over, 0, osm["s"]).astype(np.int64)
+    qlen = np.repeat((osm["qend"] - osm["qbeg"]).astype(np.int64), cnt)
+    rmate = np.repeat(rd.mate[osm["read"].astype(np.int64)], cnt)
+    assert np.array_equal(keep.astype(bool), oracle.bs_keep(ohits, qlen, rmate, len(ref)))
+
+
+def test_save_load_roundtrip_and_corruption(mb, tmp_path):
+    ref, rd, p = synth.workload(1, scale=0.02)
+    G = mb.mb_index_build(ref)
+    path = str(tmp_path / "i.mbi")
+    G.save(path)
+    H = mb.mb_index_load(path)
+    a = mb.seed(G, rd.seq, rd.off)
+    b = mb.seed(H, rd.seq, rd.off)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    raw = bytearray(open(path, "rb").read())
+    raw[200] ^= 0xFF
+    bad = str(tmp_path / "bad.mbi")
+    open(bad, "wb").write(bytes(raw))
+    with pytest.raises(mb.MbError) as ei:
+        mb.mb_index_load(bad)
+    assert ei.value.code == -7
+    open(bad, "wb").write(bytes(raw[:100]))
+    with pytest.raises(mb.MbError) as ei:
+        mb.mb_index_load(bad)
+    assert ei.value.code == -7
