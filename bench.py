@@ -1,0 +1,383 @@
+#!/usr/bin/env python3
+"""Seeding-stage benchmark: reads/s seeded + located on one GB300 (or N replicas).
+
+One step = SMEM finding + max-occ flag + locate (mb_seed_batch then mb_locate) over one
+batch of reads.  Default workload: 1 Gbp repeat-rich synthetic reference (45% repeats,
+0.5% N runs) and 10M 2x150 bp pairs (20M reads), min_len 19, max_occ 500, SA rate 32.
+The index build is timed separately and is not part of the step.
+
+Prints one JSON line.  `--impl reference` times the CPU oracle (the plain reference
+implementation of the same stage) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOADS = {
+    3: "1 Gbp repeat-rich reference (45% repeats: tandem/segdup/satellite 5:2:1, 0.5% N runs), "
+       "10M 2x150 bp pairs, insert N(400,50), subst 0.1%->1% along the read, 0.01% indels",
+    2: "100 Mbp repeat-rich reference (8% repeats, 0.5% N runs), 1M 2x150 bp pairs",
+    1: "1 Mbp uniform reference, 10,000 single-end 150 bp reads, 0.5% substitutions",
+}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("seed.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2606_15357_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current
+    kernel source (profiles/<kernel>_<workload>.txt lines 'source_hash:' and
+    'dram_bytes_per_launch:')."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    mh = re.search(r"source_hash:\s*(\w+)", txt)
+    mb = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not mh or not mb or mh.group(1) != kernel_source_hash():
+        return None
+    return float(mb.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_inputs(workload: int, scale: float, rank: int):
+    t = time.time()
+    ref, rd, params = synth.workload(workload, scale)
+    if rank:
+        # weak scaling: every rank seeds its own batch of the same size
+        o = rd.n
+        kw = dict(mode=1, read_len=150, sub_lo=0.001, sub_hi=0.01, indel=0.0001)
+        if workload == 1:
+            kw = dict(mode=0, read_len=150, sub_lo=0.005)
+        rd = synth.reads(ref, o, synth.SEED[workload] + 1000 * rank, **kw)
+    log(f"inputs: |R|={len(ref)} reads={rd.n} bases={len(rd.seq)} ({time.time() - t:.1f}s)")
+    return ref, rd, params
+
+
+# --------------------------------------------------------------------------------- oracle side
+def oracle_rate(ref, rd, params, target_s: float, threads: int, min_reads: int = 64):
+    """Time the CPU oracle (index built first, untimed) on a bounded sample of the reads."""
+    import oracle
+    t = time.time()
+    X = oracle.Index(ref, n_seed=0, threads=threads)
+    build_s = time.time() - t
+    rng = np.random.default_rng(12345)
+    n_probe = min(rd.n, min_reads)
+    sample = rd.subset(np.sort(rng.choice(rd.n, n_probe, replace=False)))
+    t = time.time()
+    X.seed(sample.seq, sample.off, params["min_len"], params["min_occ"], params["max_occ"], threads=threads)
+    dt = max(time.time() - t, 1e-3)
+    n = int(min(rd.n, max(n_probe, n_probe * target_s / dt)))
+    sample = rd.subset(np.sort(rng.choice(rd.n, n, replace=False)))
+    return X, build_s, sample
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    threads = os.cpu_count() or 1
+    ref, rd, params = make_inputs(args.workload, args.scale, 0)
+    X, build_s, sample = oracle_rate(ref, rd, params, args.ref_step_s, threads)
+    times = []
+    for it in range(args.warmup + args.steps):
+        t = time.time()
+        X.seed(sample.seq, sample.off, params["min_len"], params["min_occ"], params["max_occ"], threads=threads)
+        dt = time.time() - t
+        if it >= args.warmup:
+            times.append(dt)
+    T = float(np.sum(times))
+    value = args.steps * sample.n / T
+    desc = f"{sample.n} reads drawn (seed 12345) from the {rd.n}-read batch, oracle index built first " \
+           f"({build_s:.0f}s, untimed)"
+    line = {
+        "impl": "reference", "metric": "reads/s seeded+located", "value": value, "unit": "reads/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * T / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "scale": args.scale, "min_len": params["min_len"],
+                   "max_occ": params["max_occ"], "sa_rate": params["sa_rate"]},
+        "cpu_baseline": {"value": value, "unit": "reads/s", "cores": threads, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "reads/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------------- GPU side
+def run_gpu(args):
+    import torch
+    import paper_2606_15357_gb300 as mb
+    ws, rank, local = dist_env()
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        pg = dist
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    st = torch.cuda.current_stream()
+
+    ref, rd, params = make_inputs(args.workload, args.scale, rank)
+    opts = dict(min_len=params["min_len"], min_occ=params["min_occ"], max_occ=params["max_occ"],
+                sa_rate=params["sa_rate"])
+    torch.cuda.synchronize()
+    t = time.time()
+    idx = mb.mb_index_build(torch.from_numpy(ref).to(dev), opts=opts, n_seed=0)
+    torch.cuda.synchronize()
+    build_s = time.time() - t
+    idx.drop_sa()
+    log(f"index: n={idx.n} built in {build_s:.1f}s")
+
+    seq = torch.from_numpy(rd.seq).to(dev)
+    off = torch.from_numpy(rd.off.view(np.int64)).to(dev)
+    n_reads = rd.n
+
+    # first call sizes the outputs
+    cap = 4 * n_reads
+    out = torch.empty(cap * 48, dtype=torch.uint8, device=dev)
+    try:
+        _, m, nh = mb.mb_seed_batch(idx, seq, off, opts=opts, out=out, cap=cap)
+    except mb.MbError as e:
+        if e.code != mb.MB_ERR_CAPACITY:
+            raise
+        raise
+    hits = torch.empty(max(nh, 1), dtype=torch.int32, device=dev)
+
+    def step():
+        _, m_, nh_ = mb.mb_seed_batch(idx, seq, off, opts=opts, out=out, cap=cap)
+        mb.mb_locate(idx, out, m_, opts=opts, hits=hits, cap=nh_)
+        return m_, nh_
+
+    # work counters (untimed pass with counting kernels)
+    mb.profile_reset()
+    copts = dict(opts, flags=mb.MB_COUNT)
+    _, m, nh = mb.mb_seed_batch(idx, seq, off, opts=copts, out=out, cap=cap)
+    mb.mb_locate(idx, out, m, opts=copts, hits=hits, cap=nh)
+    wc = mb.work_counters()
+    log(f"work: {m} SMEMs, {nh} hits, {wc}")
+
+    for _ in range(args.warmup):
+        step()
+    mb.profile_reset()
+    mb.profile_enable(True)
+    l0 = mb.launch_count()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(st)
+        for _ in range(args.steps):
+            step()
+        e1.record(st)
+        torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    mb.profile_enable(False)
+    launches = mb.launch_count() - l0
+    ms = e0.elapsed_time(e1)
+    if pg:
+        tt = torch.tensor([ms], dtype=torch.float64)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = ws * args.steps * n_reads / (ms / 1000.0)
+    smem_ms, smem_n = mb.profile_get("smem")
+    loc_ms, loc_n = mb.profile_get("locate")
+    log(f"timed: {ms / args.steps:.1f} ms/step; smem {smem_ms / max(smem_n, 1):.1f} ms, "
+        f"locate {loc_ms / max(loc_n, 1):.1f} ms per launch")
+
+    # roofline of the dominant kernel: algorithmic bytes / its event-timed duration
+    peak, peak_kind = measured_peaks()
+    smem_bytes = 64 * wc["ext_blocks"] + 12 * wc["kmer_lookups"]
+    loc_bytes = 64 * wc["lf_steps"] + 4 * wc["sa_reads"]
+    if loc_ms / max(loc_n, 1) >= smem_ms / max(smem_n, 1):
+        kname, kbytes, kms = "locate", loc_bytes, loc_ms / max(loc_n, 1)
+    else:
+        kname, kbytes, kms = "smem", smem_bytes, smem_ms / max(smem_n, 1)
+    achieved = kbytes / (kms / 1000.0) / 1e9
+    wl_tag = {3: "1gbp", 2: "100mbp", 1: "1mbp"}[args.workload]
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth",
+                "traffic": ncu_traffic(kname, wl_tag),
+                "algorithmic_bytes_per_launch": kbytes,
+                "kernels": {"smem": {"ms_per_launch": smem_ms / max(smem_n, 1), "bytes": smem_bytes,
+                                     "GBps": smem_bytes / max(smem_ms / max(smem_n, 1), 1e-9) / 1e6},
+                            "locate": {"ms_per_launch": loc_ms / max(loc_n, 1), "bytes": loc_bytes,
+                                       "GBps": loc_bytes / max(loc_ms / max(loc_n, 1), 1e-9) / 1e6}}}
+
+    # end to end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        seq_h = torch.from_numpy(rd.seq).pin_memory()
+        off_h = torch.from_numpy(rd.off.view(np.int64)).pin_memory()
+        out_h = torch.empty(m * 48, dtype=torch.uint8).pin_memory()
+        hits_h = torch.empty(max(nh, 1), dtype=torch.int32).pin_memory()
+        k2 = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        t0 = time.time()
+        for _ in range(k2):
+            _, m2, nh2 = mb.mb_seed_batch(idx, seq_h, off_h, opts=opts, out=out_h, cap=m)
+            mb.mb_locate(idx, out_h, m2, opts=opts, hits=hits_h, cap=nh2)
+        torch.cuda.synchronize()
+        dt = time.time() - t0
+        if pg:
+            tt = torch.tensor([dt], dtype=torch.float64)
+            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+            dt = float(tt.item())
+        e2e = {"value": ws * k2 * n_reads / dt, "unit": "reads/s",
+               "h2d_bytes_per_step": int(seq_h.numel() + off_h.numel() * 8 + m * 48),
+               "d2h_bytes_per_step": int(m * 48 + nh * 4),
+               "note": "host pinned buffers; the locate call re-stages the SMEM records"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        X, obuild_s, sample = oracle_rate(ref, rd, params, args.cpu_s, threads)
+        t = time.time()
+        X.seed(sample.seq, sample.off, params["min_len"], params["min_occ"], params["max_occ"], threads=threads)
+        dt = time.time() - t
+        cpu = {"value": sample.n / dt, "unit": "reads/s", "cores": threads, "kind": "oracle",
+               "sample": f"{sample.n} reads drawn from the {rd.n}-read batch; oracle index build "
+                         f"({obuild_s:.0f}s) untimed", "seconds": dt}
+        del X
+
+    if rank != 0:
+        return 0
+    line = {
+        "metric": "reads/s seeded+located", "value": value, "unit": "reads/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "scale": args.scale, "reads_per_step": n_reads,
+                   "pairs_per_step": n_reads // 2, "min_len": params["min_len"], "max_occ": params["max_occ"],
+                   "sa_rate": params["sa_rate"], "parallelism": f"replicas{ws}",
+                   "l2": "inputs larger than L2 (reads 3 GB, index 1.25 GB)",
+                   "smem_per_step": m, "hits_per_step": nh, "index_build_s": build_s},
+        "smems_per_s": ws * args.steps * m / (ms / 1000.0),
+        "hits_per_s": ws * args.steps * nh / (ms / 1000.0),
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", type=int, default=3, choices=[1, 2, 3])
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--cpu-s", type=float, default=15.0, help="target seconds of oracle work")
+    ap.add_argument("--ref-step-s", type=float, default=8.0, help="reference arm: seconds per step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -51,6 +51,7 @@ enum {
 #define MB_BATCHED  0x2u   /* seeding: one persistent launch over a device work queue */
 #define MB_CHECKED  0x4u   /* seeding: bounds-check every block / row index on the device */
 #define MB_NO_KMER  0x8u   /* seeding: do not use the k-mer ds-interval table */
+#define MB_COUNT    0x10u  /* seeding/locate: also count the work done (mb_work_counters) */
 
 /* Flags of mb_smem.flags */
 #define MB_SMEM_OVER_MAX_OCC 0x1u   /* s > max_occ: reported, not located, no hits */
@@ -157,6 +158,25 @@ int mb_bs_filter(const mb_index *idx, const mb_smem *smem, uint64_t n_smem, cons
 int mb_hit_to_ref(const mb_index *idx, uint64_t pos, uint64_t len, int *strand, uint64_t *rpos);
 
 const char *mb_strerror(int code);
+/* Detail of the last error of this library (host-side message), for diagnostics. */
+const char *mb_last_error(void);
+
+/* ---------------------------------------------------------------------------------------
+ * Measurement hooks (no effect on results).
+ * mb_profile_enable(1): CUDA events are recorded on the launching stream around the SMEM
+ * kernel ("smem") and the locate kernel ("locate"); mb_profile_get returns the summed
+ * device time in ms and the number of timed launches since the last reset.
+ * mb_launch_count: number of kernels this library has launched since it was loaded.
+ * mb_work_counters: work done by calls made with MB_COUNT in opts, summed since the last
+ * reset: extension steps of Algorithm 3, distinct occurrence blocks they read, k-mer table
+ * lookups, LF steps of Algorithm 2 and sampled-SA reads.
+ */
+void mb_profile_enable(int on);
+int mb_profile_get(const char *kernel, double *ms, uint64_t *launches);
+void mb_profile_reset(void);
+uint64_t mb_launch_count(void);
+void mb_work_counters(uint64_t *ext_steps, uint64_t *ext_blocks, uint64_t *kmer_lookups,
+                      uint64_t *lf_steps, uint64_t *sa_reads);
 
 #ifdef __cplusplus
 }

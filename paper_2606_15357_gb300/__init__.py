@@ -19,7 +19,7 @@ from .nvcc_build import SO, build
 __all__ = ["SMEM_DTYPE", "Opts", "MbError", "lib", "build", "Index", "mb_index_build",
            "mb_index_load", "mb_seed_batch", "mb_locate", "mb_bs_filter", "seed"]
 
-MB_BS3, MB_BATCHED, MB_CHECKED, MB_NO_KMER = 0x1, 0x2, 0x4, 0x8
+MB_BS3, MB_BATCHED, MB_CHECKED, MB_NO_KMER, MB_COUNT = 0x1, 0x2, 0x4, 0x8, 0x10
 MB_SMEM_OVER_MAX_OCC = 0x1
 MB_ERR_CAPACITY = -3
 
@@ -74,6 +74,11 @@ def lib():
                 "mb_hit_to_ref": ([P, U64, U64, ctypes.POINTER(I), PU64], I),
                 "mb_strerror": ([I], ctypes.c_char_p),
                 "mb_last_error": ([], ctypes.c_char_p),
+                "mb_profile_enable": ([I], None),
+                "mb_profile_get": ([ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), PU64], I),
+                "mb_profile_reset": ([], None),
+                "mb_launch_count": ([], U64),
+                "mb_work_counters": ([PU64, PU64, PU64, PU64, PU64], None),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -257,3 +262,30 @@ def seed(index: Index, seq, off, mate=None, opts=None, stream=None):
     sm, m, nh = mb_seed_batch(index, seq, off, mate, opts, stream)
     hits, _ = mb_locate(index, sm, m, opts, stream, cap=nh)
     return sm, hits
+
+
+# ---------------------------------------------------------------------------- measurement hooks
+def profile_enable(on: bool = True):
+    lib().mb_profile_enable(int(on))
+
+
+def profile_reset():
+    lib().mb_profile_reset()
+
+
+def profile_get(kernel: str):
+    """(summed device ms, launches) of a timed kernel ("smem", "locate")."""
+    ms, n = ctypes.c_double(), ctypes.c_uint64()
+    _check(lib().mb_profile_get(kernel.encode(), ctypes.byref(ms), ctypes.byref(n)), "mb_profile_get")
+    return ms.value, n.value
+
+
+def launch_count() -> int:
+    return int(lib().mb_launch_count())
+
+
+def work_counters() -> dict:
+    v = [ctypes.c_uint64() for _ in range(5)]
+    lib().mb_work_counters(*[ctypes.byref(x) for x in v])
+    return dict(zip(("ext_steps", "ext_blocks", "kmer_lookups", "lf_steps", "sa_reads"),
+                    (x.value for x in v)))

@@ -57,6 +57,29 @@ struct DevBuf {
 
 bool mb_is_device_ptr(const void *p);
 
+// launch bookkeeping: every kernel launch site calls MB_KCHECK() right after <<<...>>>
+void mb_count_launch();
+#define MB_KCHECK()                  \
+    do {                             \
+        MB_CK(cudaGetLastError());   \
+        mb_count_launch();           \
+    } while (0)
+
+// CUDA-event timing of one kernel launch when profiling is on (see mb_profile_enable)
+struct KTimer {
+    const char *name;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr, b = nullptr;
+    KTimer(const char *n, cudaStream_t s);
+    void start();
+    void stop();
+    ~KTimer();   // after the stream was synchronized: accumulates the elapsed time
+};
+
+// device-side work counters (index into the array handed to kernels in counting mode)
+enum { WC_EXT_STEPS = 0, WC_EXT_BLOCKS = 1, WC_KMER = 2, WC_LF_STEPS = 3, WC_SA_READS = 4, WC_N = 5 };
+u64 *mb_work_counter_buf(cudaStream_t st);   // device array of WC_N u64 (zeroed on first use)
+
 // Stage a host-or-device input on the device: returns a device pointer (the input itself when
 // it already is one, else a copy in `buf`).
 int mb_stage_in(const void *src, size_t bytes, cudaStream_t st, DevBuf &buf, const void **dev);

@@ -9,6 +9,8 @@
 #include <stdarg.h>
 #include <stdlib.h>
 #include <string.h>
+#include <atomic>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -222,6 +224,89 @@ extern "C" const char *mb_last_error(void) {
     return copy.c_str();
 }
 
+// ----------------------------------------------------------------------------- measurement hooks
+static std::atomic<u64> g_launches{0};
+static std::atomic<int> g_prof{0};
+struct KStat {
+    double ms = 0;
+    u64 launches = 0;
+};
+static std::map<std::string, KStat> g_kstat;
+void mb_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+KTimer::KTimer(const char *n, cudaStream_t s) : name(n), st(s) {
+    if (g_prof.load()) {
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+    }
+}
+void KTimer::start() {
+    if (a) cudaEventRecord(a, st);
+}
+void KTimer::stop() {
+    if (b) cudaEventRecord(b, st);
+}
+KTimer::~KTimer() {
+    if (!a) return;
+    float ms = 0;
+    if (cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess) {
+        std::lock_guard<std::mutex> g(g_err_mu);
+        KStat &k = g_kstat[name];
+        k.ms += ms;
+        k.launches += 1;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+}
+
+static u64 *g_wc = nullptr;
+static int g_wc_dev = -1;
+u64 *mb_work_counter_buf(cudaStream_t st) {
+    int d = 0;
+    cudaGetDevice(&d);
+    std::lock_guard<std::mutex> g(g_err_mu);
+    if (!g_wc || g_wc_dev != d) {
+        if (cudaMalloc(&g_wc, WC_N * sizeof(u64)) != cudaSuccess) return nullptr;
+        cudaMemsetAsync(g_wc, 0, WC_N * sizeof(u64), st);
+        g_wc_dev = d;
+    }
+    return g_wc;
+}
+
+extern "C" void mb_profile_enable(int on) { g_prof.store(on ? 1 : 0); }
+extern "C" int mb_profile_get(const char *kernel, double *ms, uint64_t *launches) {
+    if (!kernel) return MB_ERR_ARG;
+    std::lock_guard<std::mutex> g(g_err_mu);
+    auto it = g_kstat.find(kernel);
+    if (ms) *ms = it == g_kstat.end() ? 0.0 : it->second.ms;
+    if (launches) *launches = it == g_kstat.end() ? 0 : it->second.launches;
+    return MB_OK;
+}
+extern "C" void mb_profile_reset(void) {
+    {
+        std::lock_guard<std::mutex> g(g_err_mu);
+        g_kstat.clear();
+    }
+    if (g_wc) {
+        cudaDeviceSynchronize();
+        cudaMemset(g_wc, 0, WC_N * sizeof(u64));
+    }
+}
+extern "C" uint64_t mb_launch_count(void) { return g_launches.load(); }
+extern "C" void mb_work_counters(uint64_t *ext_steps, uint64_t *ext_blocks, uint64_t *kmer_lookups,
+                                 uint64_t *lf_steps, uint64_t *sa_reads) {
+    u64 v[WC_N] = {0, 0, 0, 0, 0};
+    if (g_wc) {
+        cudaDeviceSynchronize();
+        cudaMemcpy(v, g_wc, sizeof v, cudaMemcpyDeviceToHost);
+    }
+    if (ext_steps) *ext_steps = v[WC_EXT_STEPS];
+    if (ext_blocks) *ext_blocks = v[WC_EXT_BLOCKS];
+    if (kmer_lookups) *kmer_lookups = v[WC_KMER];
+    if (lf_steps) *lf_steps = v[WC_LF_STEPS];
+    if (sa_reads) *sa_reads = v[WC_SA_READS];
+}
+
 bool mb_is_device_ptr(const void *p) {
     if (!p) return false;
     cudaPointerAttributes a;
@@ -279,18 +364,18 @@ static int build_sa(const u8 *T, u64 n, u32 *SA, cudaStream_t st) {
 
     // round 0: the first 27 symbols
     k_init_keys<<<grid_for(n, B), B, 0, st>>>(T, n, keys, vals);
-    MB_CK(cudaGetLastError());
+    MB_KCHECK();
     BitRange r0[1] = {{0, 63}};
     MB_TRY(radix_sort_pairs(keys, vals, keys_alt, vals_alt, n, r0, 1, btmp.p, st));
     MB_CK(cudaMemcpyAsync(SA, vals, n * 4, cudaMemcpyDeviceToDevice, st));
     k_heads<<<grid_for(n, B), B, 0, st>>>(keys, nullptr, n, hv, flag);
-    MB_CK(cudaGetLastError());
+    MB_KCHECK();
     MB_TRY(scan_inclusive_max_u32(hv, hv, n, btmp.p, st));
     k_set_rank<<<grid_for(n, B), B, 0, st>>>(vals, hv, n, rank);
-    MB_CK(cudaGetLastError());
+    MB_KCHECK();
     MB_TRY(scan_exclusive_u32(flag, hv, n, count, btmp.p, st));   // hv reused as positions
     k_compact<<<grid_for(n, B), B, 0, st>>>(flag, hv, nullptr, n, act);
-    MB_CK(cudaGetLastError());
+    MB_KCHECK();
     u32 A = 0;
     MB_CK(cudaMemcpyAsync(&A, count, 4, cudaMemcpyDeviceToHost, st));
     MB_CK(cudaStreamSynchronize(st));
@@ -300,18 +385,18 @@ static int build_sa(const u8 *T, u64 n, u32 *SA, cudaStream_t st) {
     u64 h = KEY_SYMS;
     while (A > 0) {
         k_round_keys<<<grid_for(A, B), B, 0, st>>>(act, A, SA, rank, h, n, keys, vals, err);
-        MB_CK(cudaGetLastError());
+        MB_KCHECK();
         MB_TRY(radix_sort_pairs(keys, vals, keys_alt, vals_alt, A, rr, 2, btmp.p, st));
         k_scatter_sa<<<grid_for(A, B), B, 0, st>>>(act, A, vals, SA);
-        MB_CK(cudaGetLastError());
+        MB_KCHECK();
         k_heads<<<grid_for(A, B), B, 0, st>>>(keys, act, A, hv, flag);
-        MB_CK(cudaGetLastError());
+        MB_KCHECK();
         MB_TRY(scan_inclusive_max_u32(hv, hv, A, btmp.p, st));
         k_set_rank<<<grid_for(A, B), B, 0, st>>>(vals, hv, A, rank);
-        MB_CK(cudaGetLastError());
+        MB_KCHECK();
         MB_TRY(scan_exclusive_u32(flag, hv, A, count, btmp.p, st));
         k_compact<<<grid_for(A, B), B, 0, st>>>(flag, hv, act, A, act2);
-        MB_CK(cudaGetLastError());
+        MB_KCHECK();
         u32 A2 = 0, e = 0;
         MB_CK(cudaMemcpyAsync(&A2, count, 4, cudaMemcpyDeviceToHost, st));
         MB_CK(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, st));

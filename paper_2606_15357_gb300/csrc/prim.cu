@@ -94,17 +94,17 @@ int scan_impl(const T *in, T *out, size_t n, void *tmp, cudaStream_t st, Op op) 
     size_t nb = level_blocks(n);
     if (nb == 1) {
         k_scan_apply<T, Op, INCL><<<1, SCAN_T, 0, st>>>(in, out, n, nullptr, nullptr, op);
-        MB_CK(cudaGetLastError());
+        MB_KCHECK();
         return MB_OK;
     }
     T *part = (T *)tmp;
     void *rest = (void *)((char *)tmp + ((nb * sizeof(u64) + 255) & ~(size_t)255));
     k_scan_reduce<T, Op><<<(unsigned)nb, SCAN_T, 0, st>>>(in, n, part, op);
-    MB_CK(cudaGetLastError());
+    MB_KCHECK();
     // exclusive scan of the tile sums gives each tile's carry
     MB_TRY((scan_impl<T, Op, false>(part, part, nb, rest, st, op)));
     k_scan_apply<T, Op, INCL><<<(unsigned)nb, SCAN_T, 0, st>>>(in, out, n, part, nullptr, op);
-    MB_CK(cudaGetLastError());
+    MB_KCHECK();
     return MB_OK;
 }
 
@@ -123,12 +123,12 @@ int scan_excl_total(const T *in, T *out, size_t n, T *total, void *tmp, cudaStre
     }
     if (total) {
         k_copy_one<T><<<1, 1, 0, st>>>(in + n - 1, total);
-        MB_CK(cudaGetLastError());
+        MB_KCHECK();
     }
     MB_TRY((scan_impl<T, OpSum, false>(in, out, n, tmp, st, OpSum())));
     if (total) {
         k_add_one<T><<<1, 1, 0, st>>>(out + n - 1, total);
-        MB_CK(cudaGetLastError());
+        MB_KCHECK();
     }
     return MB_OK;
 }
@@ -254,10 +254,10 @@ int radix_sort_pairs(u64 *keys, u32 *vals, u64 *keys_alt, u32 *vals_alt, size_t 
             int w = ranges[r].hi - sh < 8 ? ranges[r].hi - sh : 8;
             u32 mask = (1u << w) - 1u;
             k_radix_up<<<(unsigned)tiles, RS_T, 0, st>>>(ka, n, sh, mask, hist, tiles);
-            MB_CK(cudaGetLastError());
+            MB_KCHECK();
             MB_TRY(scan_exclusive_u32(hist, hist, 256 * tiles, nullptr, stmp, st));
             k_radix_down<<<(unsigned)tiles, RS_T, 0, st>>>(ka, va, kb, vb, n, sh, mask, hist, tiles);
-            MB_CK(cudaGetLastError());
+            MB_KCHECK();
             u64 *tk = ka; ka = kb; kb = tk;
             u32 *tv = va; va = vb; vb = tv;
             ++passes;

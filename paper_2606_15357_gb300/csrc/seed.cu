@@ -34,10 +34,31 @@ __device__ __forceinline__ u32 read_base(const u8 *__restrict__ P, u64 j, u32 co
     return b;
 }
 
+// Work counters of the measurement mode (MB_COUNT); compiled out otherwise.
+template <bool ON>
+struct Work {
+    u64 steps = 0, blocks = 0, kmer = 0, lf = 0, sa = 0;
+    __device__ __forceinline__ void ext(u64 p, u64 s) {
+        if (ON) {
+            ++steps;
+            blocks += (p >> 7) == ((p + s) >> 7) ? 1 : 2;
+        }
+    }
+    __device__ __forceinline__ void flush(u64 *wc) {
+        if (ON) {
+            if (steps) atomicAdd((unsigned long long *)&wc[WC_EXT_STEPS], (unsigned long long)steps);
+            if (blocks) atomicAdd((unsigned long long *)&wc[WC_EXT_BLOCKS], (unsigned long long)blocks);
+            if (kmer) atomicAdd((unsigned long long *)&wc[WC_KMER], (unsigned long long)kmer);
+            if (lf) atomicAdd((unsigned long long *)&wc[WC_LF_STEPS], (unsigned long long)lf);
+            if (sa) atomicAdd((unsigned long long *)&wc[WC_SA_READS], (unsigned long long)sa);
+        }
+    }
+};
+
 // Algorithm 3 for one read P[0, L).  emit(i, j, k, kr, s) receives the SMEMs in ascending i.
-template <class Emit>
+template <class Emit, class W>
 __device__ __forceinline__ void smem_read(const DevIndex &I, const u8 *__restrict__ P, int64_t L, u32 l, u32 c,
-                                          u32 conv, Emit &emit) {
+                                          u32 conv, Emit &emit, W &work) {
     const int64_t ll = (int64_t)l;
     if (ll - 1 >= L) return;
     int u = 1;
@@ -64,6 +85,7 @@ __device__ __forceinline__ void smem_read(const DevIndex &I, const u8 *__restric
         const bool fwd = u == 2;
         u64 nk = 0, nkr = 0, ns = 0;
         if (a < 4) {
+            work.ext(fwd ? kr : k, s);
             if (!fwd) {                     // BackwardExt((k,kr,s), a)
                 Ext e = extend(I, k, kr, s, a);
                 nk = e.p; nkr = e.q; ns = e.s;
@@ -112,15 +134,18 @@ __device__ __forceinline__ u32 conv_of(const u8 *mate, u64 r, u32 bs) {
     return m == 1 ? 1u : (m == 2 ? 2u : 0u);
 }
 
+template <bool COUNT>
 __global__ void __launch_bounds__(256) k_smem(DevIndex I, const u8 *__restrict__ seq, const u64 *__restrict__ off,
                                               u32 nr, const u8 *__restrict__ mate, u32 bs, u32 l, u32 c,
                                               SlotRec *__restrict__ slots, u64 *__restrict__ counts,
-                                              u32 *__restrict__ ovf_list, u32 *__restrict__ ovf_n) {
+                                              u32 *__restrict__ ovf_list, u32 *__restrict__ ovf_n, u64 *wc) {
     u64 r = blockIdx.x * (u64)blockDim.x + threadIdx.x;
     if (r >= nr) return;
     u64 b = off[r], e = off[r + 1];
     SlotEmit em{slots, slot_base(off, r), slot_base(off, r + 1) - slot_base(off, r), 0};
-    smem_read(I, seq + b, (int64_t)(e - b), l, c, conv_of(mate, r, bs), em);
+    Work<COUNT> work;
+    smem_read(I, seq + b, (int64_t)(e - b), l, c, conv_of(mate, r, bs), em, work);
+    work.flush(wc);
     counts[r] = em.cnt;
     if (em.cnt > em.cap) ovf_list[atomicAdd(ovf_n, 1u)] = (u32)r;
 }
@@ -172,7 +197,8 @@ __global__ void k_smem_overflow(DevIndex I, const u8 *__restrict__ seq, const u6
     for (u32 q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
         u32 r = ovf_list[q];
         FinalEmit em{out, hitc, soff[r], r, max_occ};
-        smem_read(I, seq + off[r], (int64_t)(off[r + 1] - off[r]), l, c, conv_of(mate, r, bs), em);
+        Work<false> work;
+        smem_read(I, seq + off[r], (int64_t)(off[r + 1] - off[r]), l, c, conv_of(mate, r, bs), em, work);
     }
 }
 
@@ -197,10 +223,18 @@ __device__ __forceinline__ u64 owner_of(const mb_smem *__restrict__ sm, u64 nsm,
 // LF-walk from `row` to a sampled row (Algorithm 2).  The $ row (S = 0) ends a walk too: its
 // position is the number of steps taken.  A walk never needs more than n steps; the bound only
 // guards against a corrupted index (it then yields 0xFFFFFFFF).
-__device__ __forceinline__ u32 lf_walk(const DevIndex &I, u64 row) {
+template <class W>
+__device__ __forceinline__ u32 lf_walk(const DevIndex &I, u64 row, W &work) {
     for (u64 steps = 0; steps <= I.n; ++steps) {
-        if (row % I.r == 0) return (u32)(I.ssa[row / I.r] + steps);
-        if (row == I.primary) return (u32)steps;
+        if (row % I.r == 0) {
+            work.lf += steps;
+            work.sa += 1;
+            return (u32)(I.ssa[row / I.r] + steps);
+        }
+        if (row == I.primary) {
+            work.lf += steps;
+            return (u32)steps;
+        }
         const BlockVals v = load_block(I.occ + (row >> 7));
         const u32 a = sym_from_vals(v, row);
         Occ4 o;
@@ -210,13 +244,16 @@ __device__ __forceinline__ u32 lf_walk(const DevIndex &I, u64 row) {
     return 0xFFFFFFFFu;
 }
 
+template <bool COUNT>
 __global__ void __launch_bounds__(256) k_locate(DevIndex I, const mb_smem *__restrict__ sm, u64 nsm, u64 nhits,
-                                                u32 *__restrict__ hits) {
+                                                u32 *__restrict__ hits, u64 *wc) {
+    Work<COUNT> work;
     for (u64 h = blockIdx.x * (u64)blockDim.x + threadIdx.x; h < nhits; h += (u64)gridDim.x * blockDim.x) {
         u64 m = owner_of(sm, nsm, h);
         u64 row = __ldg(&sm[m].k) + (h - __ldg(&sm[m].hit_off));
-        hits[h] = lf_walk(I, row);
+        hits[h] = lf_walk(I, row, work);
     }
+    work.flush(wc);
 }
 
 __global__ void k_bs_filter(const mb_smem *__restrict__ sm, u64 nsm, const u8 *__restrict__ mate,
@@ -293,9 +330,21 @@ extern "C" int mb_seed_batch(const mb_index *idx, const uint8_t *seq, const uint
     const DevIndex I = mb_dev_index(idx);
     const unsigned B = 256;
     const unsigned G = (unsigned)((n_reads + B - 1) / B);
-    k_smem<<<G, B, 0, st>>>(I, (const u8 *)dseq, (const u64 *)doff, n_reads, (const u8 *)dmate, bs, l, c,
-                            bslots.as<SlotRec>(), bcounts.as<u64>(), bovf.as<u32>(), dovf_n);
-    MB_CK(cudaGetLastError());
+    KTimer kt("smem", st);   // reported after the stream is synchronized below
+    {
+        const bool count = (flags & MB_COUNT) != 0;
+        u64 *wc = count ? mb_work_counter_buf(st) : nullptr;
+        kt.start();
+        if (count)
+            k_smem<true><<<G, B, 0, st>>>(I, (const u8 *)dseq, (const u64 *)doff, n_reads, (const u8 *)dmate, bs, l,
+                                          c, bslots.as<SlotRec>(), bcounts.as<u64>(), bovf.as<u32>(), dovf_n, wc);
+        else
+            k_smem<false><<<G, B, 0, st>>>(I, (const u8 *)dseq, (const u64 *)doff, n_reads, (const u8 *)dmate, bs,
+                                           l, c, bslots.as<SlotRec>(), bcounts.as<u64>(), bovf.as<u32>(), dovf_n,
+                                           nullptr);
+        kt.stop();
+        MB_KCHECK();
+    }
     MB_TRY(btmp.alloc(scan_tmp_bytes(n_reads), st));
     MB_TRY(scan_exclusive_u64(bcounts.as<u64>(), bsoff.as<u64>(), n_reads, dtotal, btmp.p, st));
     u64 total = 0;
@@ -319,14 +368,14 @@ extern "C" int mb_seed_batch(const mb_index *idx, const uint8_t *seq, const uint
     MB_TRY(bhitc.alloc(total * 8, st));
     k_gather<<<G, B, 0, st>>>((const u64 *)doff, n_reads, bslots.as<SlotRec>(), bcounts.as<u64>(), bsoff.as<u64>(),
                               max_occ, dout, bhitc.as<u64>());
-    MB_CK(cudaGetLastError());
+    MB_KCHECK();
     k_smem_overflow<<<152, 128, 0, st>>>(I, (const u8 *)dseq, (const u64 *)doff, (const u8 *)dmate, bs, l, c,
                                          bovf.as<u32>(), dovf_n, bsoff.as<u64>(), max_occ, dout, bhitc.as<u64>());
-    MB_CK(cudaGetLastError());
+    MB_KCHECK();
     MB_TRY(bhtmp.alloc(scan_tmp_bytes(total), st));
     MB_TRY(scan_exclusive_u64(bhitc.as<u64>(), bhitc.as<u64>(), total, dhtotal, bhtmp.p, st));
     k_set_hitoff<<<grid_for(total, 256), 256, 0, st>>>(bhitc.as<u64>(), total, dout);
-    MB_CK(cudaGetLastError());
+    MB_KCHECK();
     u64 ht = 0;
     MB_CK(cudaMemcpyAsync(&ht, dhtotal, 8, cudaMemcpyDeviceToHost, st));
     if (!out_dev) MB_CK(cudaMemcpyAsync(out, dout, total * sizeof(mb_smem), cudaMemcpyDeviceToHost, st));
@@ -337,7 +386,6 @@ extern "C" int mb_seed_batch(const mb_index *idx, const uint8_t *seq, const uint
 
 extern "C" int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_smem, const mb_opts *opts,
                          void *stream, uint32_t *hits, uint64_t cap, uint64_t *n_hits) {
-    (void)opts;
     if (!idx || !n_hits || (n_smem && !smem)) {
         mb_set_error("mb_locate: null argument");
         return MB_ERR_ARG;
@@ -363,9 +411,16 @@ extern "C" int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_sm
         dh = bhits.as<u32>();
     }
     const DevIndex I = mb_dev_index(idx);
-    k_locate<<<grid_for(total, 256, 152u * 2048u / 256u * 8u), 256, 0, st>>>(I, (const mb_smem *)dsm, n_smem, total,
-                                                                             dh);
-    MB_CK(cudaGetLastError());
+    const bool count = opts && (opts->flags & MB_COUNT);
+    const unsigned G = grid_for(total, 256, 152u * 2048u / 256u * 8u);
+    KTimer kt("locate", st);
+    kt.start();
+    if (count)
+        k_locate<true><<<G, 256, 0, st>>>(I, (const mb_smem *)dsm, n_smem, total, dh, mb_work_counter_buf(st));
+    else
+        k_locate<false><<<G, 256, 0, st>>>(I, (const mb_smem *)dsm, n_smem, total, dh, nullptr);
+    kt.stop();
+    MB_KCHECK();
     if (!hdev) MB_CK(cudaMemcpyAsync(hits, dh, total * 4, cudaMemcpyDeviceToHost, st));
     MB_CK(cudaStreamSynchronize(st));
     return MB_OK;
@@ -398,7 +453,7 @@ extern "C" int mb_bs_filter(const mb_index *idx, const mb_smem *smem, uint64_t n
     u64 quarter = M / 2;
     k_bs_filter<<<grid_for(n_hits, 256), 256, 0, st>>>((const mb_smem *)dsm, n_smem, (const u8 *)dmate,
                                                        (const u32 *)dhits, n_hits, quarter, dk);
-    MB_CK(cudaGetLastError());
+    MB_KCHECK();
     if (!kdev) MB_CK(cudaMemcpyAsync(keep, dk, n_hits, cudaMemcpyDeviceToHost, st));
     MB_CK(cudaStreamSynchronize(st));
     return MB_OK;
