@@ -135,6 +135,28 @@ int mb_seed_batch(const mb_index *idx, const uint8_t *seq, const uint64_t *off, 
                   mb_smem *out, uint64_t cap, uint64_t *n_out, uint64_t *n_hits);
 
 /* ---------------------------------------------------------------------------------------
+ * mb_seed_batch_noalloc — mb_seed_batch for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is an interface of this library only.  Some callers
+ * cannot call cudaMalloc: a process whose device memory is reserved in full by another
+ * allocator (a framework's caching allocator, a serving runtime that pre-reserves HBM), or a
+ * latency-critical caller for which an allocation, which may synchronize the device, is not
+ * acceptable.  This entry point allocates nothing: its scratch is a fixed 64 MiB device array
+ * inside the library (every GPU that loads the library holds it until the process exits).
+ *   seq, off, mate (or NULL) and out must be DEVICE pointers; the other arguments, the results
+ *   and the errors are those of mb_seed_batch (same records, same order).
+ *   A batch whose scratch need exceeds 64 MiB (about 300,000 reads of 150 bases, less with many
+ *   SMEMs) is rejected with MB_ERR_ARG and a message naming the need; split the batch.
+ *   The first call on a device looks up the array's device address (cudaGetSymbolAddress) for
+ *   that device; make that first call before any stream capture.
+ *   All calls share the one array and it keeps the last call's contents: calls whose work
+ *   overlaps on the GPU (from other streams or host threads) race and must not be issued;
+ *   calls on one stream are ordered.
+ */
+int mb_seed_batch_noalloc(const mb_index *idx, const uint8_t *seq, const uint64_t *off,
+                          uint32_t n_reads, const uint8_t *mate, const mb_opts *opts, void *stream,
+                          mb_smem *out, uint64_t cap, uint64_t *n_out, uint64_t *n_hits);
+
+/* ---------------------------------------------------------------------------------------
  * mb_locate — text positions of every row of every SMEM without MB_SMEM_OVER_MAX_OCC
  * (Section 2.3, Algorithm 2): row x is LF-walked to a sampled row; its position is
  * (steps + S(sampled row)) mod n.

@@ -458,3 +458,135 @@ extern "C" int mb_bs_filter(const mb_index *idx, const mb_smem *smem, uint64_t n
     MB_CK(cudaStreamSynchronize(st));
     return MB_OK;
 }
+
+// ============================================================================ no-allocation variant
+// mb_seed_batch_noalloc is for callers that cannot allocate device memory: a host process whose
+// device memory is already reserved in full by another allocator (a framework's caching
+// allocator, a serving runtime that pre-reserves HBM), or a latency-critical caller for which a
+// cudaMalloc / cudaFree (which may synchronize the device) is not acceptable.  Its scratch is
+// the fixed array below; the caller still provides the inputs and the output records.
+//
+// The array is part of this library's device image: every GPU on which the library is loaded
+// holds these MB_NOALLOC_SCRATCH_BYTES until the process exits.  All calls share it and it keeps
+// the contents of the last call, so calls whose work overlaps on the GPU (other streams or
+// threads) race; calls on one stream are ordered.
+#define MB_NOALLOC_SCRATCH_BYTES (64ull << 20)
+static __device__ __align__(256) unsigned char g_noalloc_scratch[MB_NOALLOC_SCRATCH_BYTES];
+
+#include <mutex>
+
+namespace {
+constexpr int NOALLOC_MAX_DEV = 128;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[NOALLOC_MAX_DEV] = {};
+
+// Device address of the scratch array on the current device.  In host code the array's name is
+// only a host-side stand-in, so the address is looked up once per device, with that device
+// current, and cached.  The first call on a device does this set-up; make that first call before
+// any stream capture.
+int noalloc_scratch(unsigned char **p) {
+    int d = 0;
+    MB_CK(cudaGetDevice(&d));
+    if (d < 0 || d >= NOALLOC_MAX_DEV) {
+        mb_set_error("mb_seed_batch_noalloc: device ordinal %d out of range", d);
+        return MB_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_ptr[d]) {
+        void *q = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&q, g_noalloc_scratch);
+        if (e != cudaSuccess || !q) {
+            mb_set_error("mb_seed_batch_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+            return MB_ERR_CUDA;
+        }
+        g_noalloc_ptr[d] = q;
+    }
+    *p = (unsigned char *)g_noalloc_ptr[d];
+    return MB_OK;
+}
+
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+}  // namespace
+
+extern "C" int mb_seed_batch_noalloc(const mb_index *idx, const uint8_t *seq, const uint64_t *off,
+                                     uint32_t n_reads, const uint8_t *mate, const mb_opts *opts, void *stream,
+                                     mb_smem *out, uint64_t cap, uint64_t *n_out, uint64_t *n_hits) {
+    if (!idx || !off || !n_out || (n_reads > 0 && (!seq || !out))) {
+        mb_set_error("mb_seed_batch_noalloc: null argument");
+        return MB_ERR_ARG;
+    }
+    *n_out = 0;
+    if (n_hits) *n_hits = 0;
+    if (n_reads == 0) return MB_OK;
+    if (!mb_is_device_ptr(seq) || !mb_is_device_ptr(off) || !mb_is_device_ptr(out) ||
+        (mate && !mb_is_device_ptr(mate))) {
+        mb_set_error("mb_seed_batch_noalloc: seq, off, mate and out must be device pointers");
+        return MB_ERR_ARG;
+    }
+    u32 l, c, max_occ, flags;
+    opts_defaults(opts, l, c, max_occ, flags);
+    const u32 bs = (flags & MB_BS3) ? 1u : 0u;
+    cudaStream_t st = (cudaStream_t)stream;
+    u64 o0 = 0, o1 = 0;
+    MB_CK(cudaMemcpyAsync(&o0, off, 8, cudaMemcpyDeviceToHost, st));
+    MB_CK(cudaMemcpyAsync(&o1, off + n_reads, 8, cudaMemcpyDeviceToHost, st));
+    MB_CK(cudaStreamSynchronize(st));
+    if (o1 < o0) {
+        mb_set_error("mb_seed_batch_noalloc: offsets decrease");
+        return MB_ERR_ARG;
+    }
+    // scratch layout: [totals][counts][soff][overflow list][scan tmp][slots][hit counts][scan tmp]
+    const size_t nr = n_reads;
+    const size_t nslots = (o1 - o0) / 32 + 4 * nr + 4;
+    const size_t o_cnt = 256, o_soff = o_cnt + al256(nr * 8), o_ovf = o_soff + al256(nr * 8);
+    const size_t o_tmp = o_ovf + al256(nr * 4), o_slots = o_tmp + al256(scan_tmp_bytes(nr));
+    const size_t fixed = o_slots + al256(nslots * sizeof(SlotRec));
+    if (fixed > MB_NOALLOC_SCRATCH_BYTES) {
+        mb_set_error("mb_seed_batch_noalloc: batch of %zu reads / %llu bases needs %zu bytes of scratch, "
+                     "more than the fixed %llu; split the batch",
+                     nr, (unsigned long long)(o1 - o0), fixed, (unsigned long long)MB_NOALLOC_SCRATCH_BYTES);
+        return MB_ERR_ARG;
+    }
+    unsigned char *S = nullptr;
+    MB_TRY(noalloc_scratch(&S));
+    u64 *dtotal = (u64 *)S, *dhtotal = (u64 *)S + 1;
+    u32 *dovf_n = (u32 *)((u64 *)S + 2);
+    u64 *counts = (u64 *)(S + o_cnt), *soff = (u64 *)(S + o_soff);
+    u32 *ovf = (u32 *)(S + o_ovf);
+    SlotRec *slots = (SlotRec *)(S + o_slots);
+    MB_CK(cudaMemsetAsync(S, 0, 256, st));   // totals and the overflow count start at zero
+
+    const DevIndex I = mb_dev_index(idx);
+    const unsigned B = 256, G = (unsigned)((nr + B - 1) / B);
+    k_smem<false><<<G, B, 0, st>>>(I, seq, off, n_reads, mate, bs, l, c, slots, counts, ovf, dovf_n, nullptr);
+    MB_KCHECK();
+    MB_TRY(scan_exclusive_u64(counts, soff, nr, dtotal, S + o_tmp, st));
+    u64 total = 0;
+    MB_CK(cudaMemcpyAsync(&total, dtotal, 8, cudaMemcpyDeviceToHost, st));
+    MB_CK(cudaStreamSynchronize(st));
+    *n_out = total;
+    if (total > cap) return MB_ERR_CAPACITY;
+    if (total == 0) return MB_OK;
+    const size_t o_hitc = fixed, o_htmp = o_hitc + al256(total * 8);
+    const size_t need = o_htmp + al256(scan_tmp_bytes(total));
+    if (need > MB_NOALLOC_SCRATCH_BYTES) {
+        mb_set_error("mb_seed_batch_noalloc: %llu SMEMs need %zu bytes of scratch, more than the fixed %llu; "
+                     "split the batch",
+                     (unsigned long long)total, need, (unsigned long long)MB_NOALLOC_SCRATCH_BYTES);
+        *n_out = 0;
+        return MB_ERR_ARG;
+    }
+    u64 *hitc = (u64 *)(S + o_hitc);
+    k_gather<<<G, B, 0, st>>>(off, n_reads, slots, counts, soff, max_occ, out, hitc);
+    MB_KCHECK();
+    k_smem_overflow<<<152, 128, 0, st>>>(I, seq, off, mate, bs, l, c, ovf, dovf_n, soff, max_occ, out, hitc);
+    MB_KCHECK();
+    MB_TRY(scan_exclusive_u64(hitc, hitc, total, dhtotal, S + o_htmp, st));
+    k_set_hitoff<<<grid_for(total, 256), 256, 0, st>>>(hitc, total, out);
+    MB_KCHECK();
+    u64 ht = 0;
+    MB_CK(cudaMemcpyAsync(&ht, dhtotal, 8, cudaMemcpyDeviceToHost, st));
+    MB_CK(cudaStreamSynchronize(st));
+    if (n_hits) *n_hits = ht;
+    return MB_OK;
+}
