@@ -110,65 +110,88 @@ struct DevIndex {
 struct mb_index_impl;
 
 // ----------------------------------------------------------------------------- device helpers
-// Counts of A,C,G,T and of $ in B[0, x), from the block of row x.
-struct Occ4 {
-    u64 c[4];
-    u32 dollar;
+// Every row, count and interval bound is below n < 2^32, so the kernels work in u32.
+// A block as loaded: the low halves of the four u64 counts and the four 2-bit words.
+struct Blk {
+    u32 c[4];
+    u64 w[4];
 };
-
-struct BlockVals {
-    ulonglong2 c01, c23, w01, w23;
-};
-__device__ __forceinline__ BlockVals load_block(const OccBlock *__restrict__ blk) {
-    const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(blk);
-    BlockVals v;
-    v.c01 = __ldg(p + 0);
-    v.c23 = __ldg(p + 1);
-    v.w01 = __ldg(p + 2);
-    v.w23 = __ldg(p + 3);
-    return v;
+__device__ __forceinline__ Blk load_blk(const OccBlock *__restrict__ blk) {
+    const uint4 *p = reinterpret_cast<const uint4 *>(blk);
+    const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(blk);
+    uint4 c01 = __ldg(p), c23 = __ldg(p + 1);
+    ulonglong2 w01 = __ldg(q + 2), w23 = __ldg(q + 3);
+    Blk b;
+    b.c[0] = c01.x; b.c[1] = c01.z; b.c[2] = c23.x; b.c[3] = c23.z;
+    b.w[0] = w01.x; b.w[1] = w01.y; b.w[2] = w23.x; b.w[3] = w23.y;
+    return b;
 }
 
-__device__ __forceinline__ void occ_from_vals(const BlockVals &v, u64 x, u64 primary, Occ4 &o) {
-    u32 m = (u32)(x & 127);
-    u64 w[4] = {v.w01.x, v.w01.y, v.w23.x, v.w23.y};
+// Counts of A,C,G,T and of $ in B[0, x), x in the block b.
+struct Occ4 {
+    u32 c[4];
+    u32 dollar;
+};
+__device__ __forceinline__ Occ4 occ_blk(const Blk &b, u32 x, u32 primary) {
+    const u32 m = x & 127;
     u32 nl = 0, nh = 0, nt = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         int take = (int)m - 32 * q;
         take = take < 0 ? 0 : (take > 32 ? 32 : take);
         u64 mask = take == 32 ? ~0ULL : ((1ULL << (2 * take)) - 1);
-        u64 y = w[q] & mask;
+        u64 y = b.w[q] & mask;
         u64 lo = y & 0x5555555555555555ULL, hi = (y >> 1) & 0x5555555555555555ULL;
         nl += __popcll(lo);
         nh += __popcll(hi);
         nt += __popcll(lo & hi);
     }
-    // symbol codes: A=00 C=01 G=10 T=11 (low bit first)
-    u32 cT = nt, cC = nl - nt, cG = nh - nt, cA = m - cC - cG - cT;
-    u64 bstart = x & ~127ULL;
-    u32 d = (primary >= bstart && primary < x) ? 1u : 0u;
-    o.c[0] = v.c01.x + cA - d;
-    o.c[1] = v.c01.y + cC;
-    o.c[2] = v.c23.x + cG;
-    o.c[3] = v.c23.y + cT;
+    // symbol codes: A=00 C=01 G=10 T=11 (low bit first); the $ row is stored as A
+    const u32 cT = nt, cC = nl - nt, cG = nh - nt, cA = m - cC - cG - cT;
+    const u32 bstart = x & ~127u;
+    const u32 d = (primary >= bstart && primary < x) ? 1u : 0u;
+    Occ4 o;
+    o.c[0] = b.c[0] + cA - d;
+    o.c[1] = b.c[1] + cC;
+    o.c[2] = b.c[2] + cG;
+    o.c[3] = b.c[3] + cT;
     o.dollar = primary < x ? 1u : 0u;
+    return o;
 }
 
 // symbol (0..3) stored at row x of its block ($ reads as A)
-__device__ __forceinline__ u32 sym_from_vals(const BlockVals &v, u64 x) {
-    u32 q = (u32)(x & 127);
-    u64 w = q < 64 ? ((q & 32) ? v.w01.y : v.w01.x) : ((q & 32) ? v.w23.y : v.w23.x);
+__device__ __forceinline__ u32 sym_blk(const Blk &b, u32 x) {
+    const u32 q = x & 127;
+    const u64 w = q < 64 ? (q < 32 ? b.w[0] : b.w[1]) : (q < 96 ? b.w[2] : b.w[3]);
     return (u32)(w >> (2 * (q & 31))) & 3u;
 }
 
-__device__ __forceinline__ void occ_from_block(const OccBlock *__restrict__ blk, u64 x, u64 primary, Occ4 &o) {
-    occ_from_vals(load_block(blk), x, primary, o);
+// x[a] for a in 0..3 without dynamic indexing (which would go through local memory)
+__device__ __forceinline__ u32 sel4(u32 a, u32 x0, u32 x1, u32 x2, u32 x3) {
+    return a < 2 ? (a == 0 ? x0 : x1) : (a == 2 ? x2 : x3);
 }
 
-__device__ __forceinline__ void occ_at(const DevIndex &I, u64 x, Occ4 &o) {
-    occ_from_block(I.occ + (x >> 7), x, I.primary, o);
+// One LF step of Algorithm 2 from row x (x is not the $ row): a = B[x], result C[a] + #a in
+// B[0, x), counting only symbol a (one popcount per word).
+__device__ __forceinline__ u32 lf_blk(const Blk &b, u32 x, u32 primary, u32 C0, u32 C1, u32 C2, u32 C3) {
+    const u32 m = x & 127;
+    const u64 wx = m < 64 ? (m < 32 ? b.w[0] : b.w[1]) : (m < 96 ? b.w[2] : b.w[3]);
+    const u32 a = (u32)(wx >> (2 * (m & 31))) & 3u;
+    const u64 pat = (u64)a * 0x5555555555555555ULL;   // a repeated in every 2-bit slot
+    u32 cnt = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        int take = (int)m - 32 * q;
+        take = take < 0 ? 0 : (take > 32 ? 32 : take);
+        const u64 mask = take == 32 ? ~0ULL : ((1ULL << (2 * take)) - 1);
+        const u64 y = ~(b.w[q] ^ pat);                    // 11 where the slot holds a
+        cnt += __popcll(y & (y >> 1) & 0x5555555555555555ULL & mask);
+    }
+    const u32 bstart = x & ~127u;
+    if (a == 0 && primary >= bstart && primary < x) cnt -= 1;   // the $ row is stored as A
+    return sel4(a, C0 + b.c[0], C1 + b.c[1], C2 + b.c[2], C3 + b.c[3]) + cnt;
 }
+
 
 // Algorithm 1 in one step.  Extends the interval (p, q, s) of P on the side of p by symbol a
 // (0..3): p is lo of the strand being extended backwards, q is lo of the other strand.
@@ -178,29 +201,27 @@ __device__ __forceinline__ void occ_at(const DevIndex &I, u64 x, Occ4 &o) {
 // BackwardExt((k,k',s), a) is (p,q) = (k,k'); ForwardExt((k,k',s), a) is (p,q) = (k',k) with
 // the complement of a.
 struct Ext {
-    u64 p, q, s;
+    u32 p, q, s;
 };
-// x[a] for a in 0..3 without dynamic indexing (which would go through local memory)
-__device__ __forceinline__ u64 sel4(u32 a, u64 x0, u64 x1, u64 x2, u64 x3) {
-    return a < 2 ? (a == 0 ? x0 : x1) : (a == 2 ? x2 : x3);
-}
-__device__ __forceinline__ Ext extend_from(const DevIndex &I, const Occ4 &lo, const Occ4 &hi, u64 q,
-                                           u32 a) {
-    u64 d0 = hi.c[0] - lo.c[0], d1 = hi.c[1] - lo.c[1], d2 = hi.c[2] - lo.c[2], d3 = hi.c[3] - lo.c[3];
-    u64 dd = hi.dollar - lo.dollar;
-    u64 gt = dd + (a < 3 ? d3 : 0) + (a < 2 ? d2 : 0) + (a < 1 ? d1 : 0);
+__device__ __forceinline__ Ext extend_from(const DevIndex &I, const Occ4 &lo, const Occ4 &hi, u32 q, u32 a) {
+    const u32 d0 = hi.c[0] - lo.c[0], d1 = hi.c[1] - lo.c[1], d2 = hi.c[2] - lo.c[2], d3 = hi.c[3] - lo.c[3];
+    const u32 gt = (hi.dollar - lo.dollar) + (a < 3 ? d3 : 0) + (a < 2 ? d2 : 0) + (a < 1 ? d1 : 0);
     Ext e;
     e.s = sel4(a, d0, d1, d2, d3);
-    e.p = sel4(a, I.C[0] + lo.c[0], I.C[1] + lo.c[1], I.C[2] + lo.c[2], I.C[3] + lo.c[3]);
+    e.p = sel4(a, (u32)I.C[0] + lo.c[0], (u32)I.C[1] + lo.c[1], (u32)I.C[2] + lo.c[2], (u32)I.C[3] + lo.c[3]);
     e.q = q + gt;
     return e;
 }
 
-__device__ __forceinline__ Ext extend(const DevIndex &I, u64 p, u64 q, u64 s, u32 a) {
-    Occ4 lo, hi;
-    occ_at(I, p, lo);
-    occ_at(I, p + s, hi);
-    return extend_from(I, lo, hi, q, a);
+// One extension: the blocks of rows p and p+s are read once each (once in all when they are the
+// same block).
+__device__ __forceinline__ Ext extend(const DevIndex &I, u32 p, u32 q, u32 s, u32 a) {
+    const u32 e = p + s;
+    const Blk b0 = load_blk(I.occ + (p >> 7));
+    Blk b1 = b0;
+    if ((e >> 7) != (p >> 7)) b1 = load_blk(I.occ + (e >> 7));
+    const u32 prim = (u32)I.primary;
+    return extend_from(I, occ_blk(b0, p, prim), occ_blk(b1, e, prim), q, a);
 }
 
 // splitmix64 output function; bits 63..62 give the base replacing an ambiguous reference base.

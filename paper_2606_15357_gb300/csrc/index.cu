@@ -185,15 +185,15 @@ __global__ void k_sample_sa(const u32 *__restrict__ SA, u64 n, u32 r, u32 *__res
 __global__ void k_kmer_table(DevIndex I, u32 k, u32 *__restrict__ out) {
     u64 nk = 1ULL << (2 * k);
     for (u64 w = blockIdx.x * (u64)blockDim.x + threadIdx.x; w < nk; w += (u64)gridDim.x * blockDim.x) {
-        u64 p = 0, q = 0, s = I.n;
+        u32 p = 0, q = 0, s = (u32)I.n;
         for (int t = (int)k - 1; t >= 0; --t) {
             u32 a = (u32)(w >> (2 * (k - 1 - t))) & 3u;
             Ext e = extend(I, p, q, s, a);
             p = e.p; q = e.q; s = e.s;
         }
-        out[3 * w + 0] = (u32)p;
-        out[3 * w + 1] = (u32)q;
-        out[3 * w + 2] = (u32)s;
+        out[3 * w + 0] = p;
+        out[3 * w + 1] = q;
+        out[3 * w + 2] = s;
     }
 }
 

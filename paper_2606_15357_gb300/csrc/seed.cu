@@ -55,75 +55,184 @@ struct Work {
     }
 };
 
-// Algorithm 3 for one read P[0, L).  emit(i, j, k, kr, s) receives the SMEMs in ascending i.
-template <class Emit, class W>
-__device__ __forceinline__ void smem_read(const DevIndex &I, const u8 *__restrict__ P, int64_t L, u32 l, u32 c,
-                                          u32 conv, Emit &emit, W &work) {
-    const int64_t ll = (int64_t)l;
-    if (ll - 1 >= L) return;
-    int u = 1;
-    int64_t i = 0, j = ll - 1;
-    u64 k = 0, kr = 0, s = I.n;
+// Per-read state of Algorithm 3.  In Algorithm 3 a read has exactly one queue entry at any time,
+// so one read's queue operations happen in the serial order kept here.
+struct SmemState {
+    const u8 *P;
+    int L;       // read length
+    u32 conv;    // bisulfite conversion (0 none, 1 C->T, 2 G->A)
+    int u;       // stage 1, 2, 3; 0 = finished
+    int i, j;
+    u32 k, kr, s;
+    bool tried;  // stage 3: the k-mer table was already consulted for this entry
+};
+
+__device__ __forceinline__ void smem_begin(SmemState &S, const u8 *P, int L, u32 conv, u32 l, u32 n) {
+    S.P = P;
+    S.L = L;
+    S.conv = conv;
+    S.u = (int)l - 1 < L ? 1 : 0;   // Algorithm 3 queues a read only if l - 1 < |P|
+    S.i = 0;
+    S.j = (int)l - 1;
+    S.k = 0; S.kr = 0; S.s = n;
+    S.tried = false;
+}
+
+// k-mer code of P[j-K+1 .. j] (first base most significant); false if it holds an N
+__device__ __forceinline__ bool kmer_code(const SmemState &S, int j, u32 K, u32 &code) {
+    u32 v = 0;
+    for (u32 t = 0; t < K; ++t) {
+        u32 b = read_base(S.P, (u64)(j - (int)K + 1 + (int)t), S.conv);
+        if (b > 3) return false;
+        v = (v << 2) | b;
+    }
+    code = v;
+    return true;
+}
+
+// Moves through the steps of Algorithm 3 that need no occurrence block.  Returns true when the
+// next step is an extension of P[j] (backward in stages 1 and 3, forward in stage 2), false when
+// the read is finished.  SMEMs found on the way go to emit.
+//
+// With the k-mer table (Section 2.5), the first K backward steps from the empty string are one
+// table lookup: the table holds exactly the interval those K BackwardExt steps give.  In stage 1
+// a failing k-mer P[x, x+K) restarts the scan at x+1, no further than Algorithm 3's own restart
+// (every window starting at or before x contains that k-mer, so none is a match); in stage 3 the
+// restart point must be exact, so a failing k-mer falls back to single steps.
+template <bool KMER, class Emit, class W>
+__device__ __forceinline__ bool smem_advance(SmemState &S, const DevIndex &I, u32 l, u32 c, Emit &emit, W &work) {
+    const u32 n = (u32)I.n, K = I.kmer_k;
     for (;;) {
-        if (u == 1 && j < i) {              // stage 1 done: P[i, i+l) is a match
-            u = 2;
-            j = i + ll;
-            continue;
-        }
-        if (u == 2 && j == L) {             // reached the end of P
-            emit(i, j, k, kr, s);
-            return;
-        }
-        if (u == 3 && j <= i) {             // back to stage 1 at the next start
-            u = 1;
-            i = j + 1;
-            j = j + ll;
-            k = 0; kr = 0; s = I.n;
-            continue;
-        }
-        const u32 a = read_base(P, (u64)j, conv);
-        const bool fwd = u == 2;
-        u64 nk = 0, nkr = 0, ns = 0;
-        if (a < 4) {
-            work.ext(fwd ? kr : k, s);
-            if (!fwd) {                     // BackwardExt((k,kr,s), a)
-                Ext e = extend(I, k, kr, s, a);
-                nk = e.p; nkr = e.q; ns = e.s;
-            } else {                        // ForwardExt((k,kr,s), a) = BackwardExt((kr,k,s), comp a)
-                Ext e = extend(I, kr, k, s, 3u - a);
-                nk = e.q; nkr = e.p; ns = e.s;
+        if (S.u == 2) {
+            if (S.j == S.L) {                       // reached the end of P
+                emit(S.i, S.j, S.k, S.kr, S.s);
+                S.u = 0;
+                return false;
             }
+            return true;
         }
-        if (fwd) {
-            if (ns >= c) {
-                ++j;
-                k = nk; kr = nkr; s = ns;
-            } else {
-                emit(i, j, k, kr, s);
-                u = 3;
-                k = 0; kr = 0; s = I.n;
+        if (S.u == 1) {
+            if (S.j < S.i) {                        // P[i, i+l) is a match: stage 2
+                S.u = 2;
+                S.j = S.i + (int)l;
+                continue;
             }
-        } else {                            // BackStep
-            if (ns >= c) {
-                --j;
-                k = nk; kr = nkr; s = ns;
-            } else if (j + ll < L) {
-                u = 1;
-                i = j + 1;
-                j = j + ll;
-                k = 0; kr = 0; s = I.n;
-            } else {
-                return;
+            u32 code;
+            if (KMER && l >= K && S.s == n && kmer_code(S, S.j, K, code)) {
+                const u32 *e = I.kmer + 3 * (u64)code;
+                u32 tk = __ldg(e), tkr = __ldg(e + 1), ts = __ldg(e + 2);
+                work.kmer += 1;
+                if (ts >= c) {
+                    S.k = tk; S.kr = tkr; S.s = ts;
+                    S.j -= (int)K;
+                    continue;
+                }
+                const int x = S.j - (int)K + 1;
+                if (x + (int)l < S.L) {
+                    S.i = x + 1;
+                    S.j = x + (int)l;
+                    continue;
+                }
+                S.u = 0;
+                return false;
             }
+            return true;
         }
+        if (S.u == 3) {
+            if (S.j <= S.i) {                       // back to stage 1 at the next start
+                S.u = 1;
+                S.i = S.j + 1;
+                S.j = S.j + (int)l;
+                S.k = 0; S.kr = 0; S.s = n;
+                continue;
+            }
+            u32 code;
+            if (KMER && !S.tried && S.s == n && S.j - (int)K + 1 > S.i && kmer_code(S, S.j, K, code)) {
+                S.tried = true;
+                const u32 *e = I.kmer + 3 * (u64)code;
+                u32 tk = __ldg(e), tkr = __ldg(e + 1), ts = __ldg(e + 2);
+                work.kmer += 1;
+                if (ts >= c) {
+                    S.k = tk; S.kr = tkr; S.s = ts;
+                    S.j -= (int)K;
+                    continue;
+                }
+            }
+            return true;
+        }
+        return false;
+    }
+}
+
+// Applies the result (nk, nkr, ns) of the pending extension.  Returns false when the read is
+// finished.
+template <class Emit>
+__device__ __forceinline__ bool smem_apply(SmemState &S, u32 nk, u32 nkr, u32 ns, u32 l, u32 c, u32 n, Emit &emit) {
+    if (S.u == 2) {
+        if (ns >= c) {
+            ++S.j;
+            S.k = nk; S.kr = nkr; S.s = ns;
+        } else {                                    // SMEM ends before P[j]: stage 3
+            emit(S.i, S.j, S.k, S.kr, S.s);
+            S.u = 3;
+            S.k = 0; S.kr = 0; S.s = n;
+            S.tried = false;
+        }
+        return true;
+    }
+    if (ns >= c) {                                  // BackStep succeeded
+        --S.j;
+        S.k = nk; S.kr = nkr; S.s = ns;
+        return true;
+    }
+    if (S.j + (int)l < S.L) {                       // BackStep failed: restart after P[j]
+        S.u = 1;
+        S.i = S.j + 1;
+        S.j = S.j + (int)l;
+        S.k = 0; S.kr = 0; S.s = n;
+        return true;
+    }
+    S.u = 0;
+    return false;
+}
+
+// The pending extension of P[j]: BackwardExt((k,kr,s), a) in stages 1/3, ForwardExt in stage 2
+// (= BackwardExt((kr,k,s), comp a)).  An N gives the empty interval without a memory access.
+template <class W>
+__device__ __forceinline__ void smem_extend(const SmemState &S, const DevIndex &I, u32 &nk, u32 &nkr, u32 &ns,
+                                            W &work) {
+    const u32 a = read_base(S.P, (u64)S.j, S.conv);
+    nk = 0; nkr = 0; ns = 0;
+    if (a < 4) {
+        const bool fwd = S.u == 2;
+        const u32 p = fwd ? S.kr : S.k, q = fwd ? S.k : S.kr;
+        work.ext(p, S.s);
+        Ext e = extend(I, p, q, S.s, fwd ? 3u - a : a);
+        nk = fwd ? e.q : e.p;
+        nkr = fwd ? e.p : e.q;
+        ns = e.s;
+    }
+}
+
+// Algorithm 3 for one read, start to end (used by the overflow pass).
+template <bool KMER, class Emit, class W>
+__device__ __forceinline__ void smem_read(const DevIndex &I, const u8 *__restrict__ P, int L, u32 l, u32 c, u32 conv,
+                                          Emit &emit, W &work) {
+    SmemState S;
+    smem_begin(S, P, L, conv, l, (u32)I.n);
+    while (smem_advance<KMER>(S, I, l, c, emit, work)) {
+        u32 nk, nkr, ns;
+        smem_extend(S, I, nk, nkr, ns, work);
+        if (!smem_apply(S, nk, nkr, ns, l, c, (u32)I.n, emit)) break;
     }
 }
 
 struct SlotEmit {
     SlotRec *slots;
-    u64 base, cap, cnt;
-    __device__ __forceinline__ void operator()(int64_t i, int64_t j, u64 k, u64 kr, u64 s) {
-        if (cnt < cap) slots[base + cnt] = SlotRec{(u32)i, (u32)j, (u32)k, (u32)kr, (u32)s};
+    u64 base;
+    u32 cap, cnt;
+    __device__ __forceinline__ void operator()(int i, int j, u32 k, u32 kr, u32 s) {
+        if (cnt < cap) slots[base + cnt] = SlotRec{(u32)i, (u32)j, k, kr, s};
         ++cnt;
     }
 };
@@ -134,20 +243,46 @@ __device__ __forceinline__ u32 conv_of(const u8 *mate, u64 r, u32 bs) {
     return m == 1 ? 1u : (m == 2 ? 2u : 0u);
 }
 
-template <bool COUNT>
+// One lane keeps one read in flight; when it finishes, the lane takes the next read
+// (r += total threads) inside the same loop, so lanes never wait for the slowest read of
+// their warp.  Each loop iteration performs at most one extension.
+template <bool COUNT, bool KMER>
 __global__ void __launch_bounds__(256) k_smem(DevIndex I, const u8 *__restrict__ seq, const u64 *__restrict__ off,
                                               u32 nr, const u8 *__restrict__ mate, u32 bs, u32 l, u32 c,
                                               SlotRec *__restrict__ slots, u64 *__restrict__ counts,
                                               u32 *__restrict__ ovf_list, u32 *__restrict__ ovf_n, u64 *wc) {
-    u64 r = blockIdx.x * (u64)blockDim.x + threadIdx.x;
-    if (r >= nr) return;
-    u64 b = off[r], e = off[r + 1];
-    SlotEmit em{slots, slot_base(off, r), slot_base(off, r + 1) - slot_base(off, r), 0};
+    const u32 stride = gridDim.x * blockDim.x;
+    const u32 n = (u32)I.n;
+    const u64 o0 = off[0];
     Work<COUNT> work;
-    smem_read(I, seq + b, (int64_t)(e - b), l, c, conv_of(mate, r, bs), em, work);
+    SmemState S;
+    SlotEmit em;
+    u32 r = blockIdx.x * blockDim.x + threadIdx.x;
+    auto start = [&](u32 rr) {
+        const u64 b = off[rr], e = off[rr + 1];
+        const u64 sb = (b - o0) / 32 + 4 * (u64)rr, se = (e - o0) / 32 + 4 * (u64)(rr + 1);
+        em.slots = slots;
+        em.base = sb;
+        em.cap = (u32)(se - sb);
+        em.cnt = 0;
+        smem_begin(S, seq + b, (int)(e - b), conv_of(mate, rr, bs), l, n);
+    };
+    if (r < nr) start(r);
+    while (r < nr) {
+        bool go = smem_advance<KMER>(S, I, l, c, em, work);
+        if (go) {
+            u32 nk, nkr, ns;
+            smem_extend(S, I, nk, nkr, ns, work);
+            go = smem_apply(S, nk, nkr, ns, l, c, n, em);
+        }
+        if (!go) {
+            counts[r] = em.cnt;
+            if (em.cnt > em.cap) ovf_list[atomicAdd(ovf_n, 1u)] = r;
+            r += stride;
+            if (r < nr) start(r);
+        }
+    }
     work.flush(wc);
-    counts[r] = em.cnt;
-    if (em.cnt > em.cap) ovf_list[atomicAdd(ovf_n, 1u)] = (u32)r;
 }
 
 __device__ __forceinline__ void write_rec(mb_smem *out, u64 *hitc, u64 m, u32 r, u32 qbeg, u32 qend, u64 k, u64 kr,
@@ -184,11 +319,12 @@ struct FinalEmit {
     u64 *hitc;
     u64 o;
     u32 r, max_occ;
-    __device__ __forceinline__ void operator()(int64_t i, int64_t j, u64 k, u64 kr, u64 s) {
+    __device__ __forceinline__ void operator()(int i, int j, u32 k, u32 kr, u32 s) {
         write_rec(out, hitc, o++, r, (u32)i, (u32)j, k, kr, s, max_occ);
     }
 };
 
+template <bool KMER>
 __global__ void k_smem_overflow(DevIndex I, const u8 *__restrict__ seq, const u64 *__restrict__ off,
                                 const u8 *__restrict__ mate, u32 bs, u32 l, u32 c, const u32 *__restrict__ ovf_list,
                                 const u32 *__restrict__ ovf_n, const u64 *__restrict__ soff, u32 max_occ,
@@ -198,7 +334,7 @@ __global__ void k_smem_overflow(DevIndex I, const u8 *__restrict__ seq, const u6
         u32 r = ovf_list[q];
         FinalEmit em{out, hitc, soff[r], r, max_occ};
         Work<false> work;
-        smem_read(I, seq + off[r], (int64_t)(off[r + 1] - off[r]), l, c, conv_of(mate, r, bs), em, work);
+        smem_read<KMER>(I, seq + off[r], (int)(off[r + 1] - off[r]), l, c, conv_of(mate, r, bs), em, work);
     }
 }
 
@@ -220,38 +356,55 @@ __device__ __forceinline__ u64 owner_of(const mb_smem *__restrict__ sm, u64 nsm,
     return a;
 }
 
-// LF-walk from `row` to a sampled row (Algorithm 2).  The $ row (S = 0) ends a walk too: its
-// position is the number of steps taken.  A walk never needs more than n steps; the bound only
-// guards against a corrupted index (it then yields 0xFFFFFFFF).
-template <class W>
-__device__ __forceinline__ u32 lf_walk(const DevIndex &I, u64 row, W &work) {
-    for (u64 steps = 0; steps <= I.n; ++steps) {
-        if (row % I.r == 0) {
-            work.lf += steps;
-            work.sa += 1;
-            return (u32)(I.ssa[row / I.r] + steps);
-        }
-        if (row == I.primary) {
-            work.lf += steps;
-            return (u32)steps;
-        }
-        const BlockVals v = load_block(I.occ + (row >> 7));
-        const u32 a = sym_from_vals(v, row);
-        Occ4 o;
-        occ_from_vals(v, row, I.primary, o);
-        row = sel4(a, I.C[0] + o.c[0], I.C[1] + o.c[1], I.C[2] + o.c[2], I.C[3] + o.c[3]);
-    }
-    return 0xFFFFFFFFu;
+__device__ __forceinline__ u64 hits_of(const mb_smem *__restrict__ sm, u64 m) {
+    return (__ldg(&sm[m].flags) & MB_SMEM_OVER_MAX_OCC) ? 0 : __ldg(&sm[m].s);
 }
 
+// Locate (Algorithm 2).  Every lane owns one contiguous range of hits; it LF-walks one row at a
+// time, one step per loop iteration, and starts its next row inside the same loop as soon as a
+// walk ends, so lanes never wait for the longest walk of their warp.  A walk ends on a sampled
+// row (position = steps + S(row)) or on the $ row (S = 0, position = steps).  A walk needs fewer
+// than n steps; the bound only guards against a corrupted index (it then writes 0xFFFFFFFF).
 template <bool COUNT>
 __global__ void __launch_bounds__(256) k_locate(DevIndex I, const mb_smem *__restrict__ sm, u64 nsm, u64 nhits,
                                                 u32 *__restrict__ hits, u64 *wc) {
+    const u64 nt = (u64)gridDim.x * blockDim.x;
+    const u64 tid = blockIdx.x * (u64)blockDim.x + threadIdx.x;
+    const u64 per = (nhits + nt - 1) / nt;
+    u64 h = tid * per;
+    const u64 h1 = h + per < nhits ? h + per : nhits;
+    if (h >= h1) return;
     Work<COUNT> work;
-    for (u64 h = blockIdx.x * (u64)blockDim.x + threadIdx.x; h < nhits; h += (u64)gridDim.x * blockDim.x) {
-        u64 m = owner_of(sm, nsm, h);
-        u64 row = __ldg(&sm[m].k) + (h - __ldg(&sm[m].hit_off));
-        hits[h] = lf_walk(I, row, work);
+    const u32 r = I.r, prim = (u32)I.primary, n = (u32)I.n;
+    const u32 C0 = (u32)I.C[0], C1 = (u32)I.C[1], C2 = (u32)I.C[2], C3 = (u32)I.C[3];
+    u64 m = owner_of(sm, nsm, h);
+    u64 moff = __ldg(&sm[m].hit_off), mend = moff + hits_of(sm, m);
+    u32 mk = (u32)__ldg(&sm[m].k);
+    u32 row = mk + (u32)(h - moff), steps = 0;
+    for (;;) {
+        const bool sampled = row % r == 0;
+        if (sampled || row == prim || steps > n) {
+            u32 pos = sampled ? __ldg(&I.ssa[row / r]) + steps : steps;
+            if (steps > n) pos = 0xFFFFFFFFu;
+            hits[h] = pos;
+            work.lf += steps;
+            work.sa += sampled ? 1 : 0;
+            if (++h >= h1) break;
+            while (h >= mend) {                 // next record that has hits
+                if (++m >= nsm) {               // inconsistent hit_off values: stop this range
+                    work.flush(wc);
+                    return;
+                }
+                moff = __ldg(&sm[m].hit_off);
+                mend = moff + hits_of(sm, m);
+                mk = (u32)__ldg(&sm[m].k);
+            }
+            row = mk + (u32)(h - moff);
+            steps = 0;
+            continue;
+        }
+        row = lf_blk(load_blk(I.occ + (row >> 7)), row, prim, C0, C1, C2, C3);
+        ++steps;
     }
     work.flush(wc);
 }
@@ -275,6 +428,28 @@ void opts_defaults(const mb_opts *o, u32 &l, u32 &c, u32 &max_occ, u32 &flags) {
     c = o && o->min_occ ? o->min_occ : 1;
     max_occ = o && o->max_occ ? o->max_occ : 500;
     flags = o ? o->flags : 0;
+}
+
+// Grid of as many blocks as are resident at once (per-lane refill loops need no more), capped by
+// the work available.
+unsigned resident_grid(const void *kernel, int block, u64 work_items) {
+    int dev = 0, sms = 152, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    u64 g = (u64)sms * (u64)per_sm;
+    u64 need = (work_items + block - 1) / block;
+    if (need < g) g = need;
+    return (unsigned)(g ? g : 1);
+}
+
+unsigned smem_grid(u32 n_reads, bool count, bool kmer) {
+    const void *k = count ? (kmer ? (const void *)k_smem<true, true> : (const void *)k_smem<true, false>)
+                          : (kmer ? (const void *)k_smem<false, true> : (const void *)k_smem<false, false>);
+    return resident_grid(k, 256, n_reads);
 }
 
 }  // namespace
@@ -331,17 +506,28 @@ extern "C" int mb_seed_batch(const mb_index *idx, const uint8_t *seq, const uint
     const unsigned B = 256;
     const unsigned G = (unsigned)((n_reads + B - 1) / B);
     KTimer kt("smem", st);   // reported after the stream is synchronized below
+    const bool kmer = !(flags & MB_NO_KMER) && l >= mb_dev_index(idx).kmer_k;
     {
         const bool count = (flags & MB_COUNT) != 0;
         u64 *wc = count ? mb_work_counter_buf(st) : nullptr;
+        const unsigned Gs = smem_grid(n_reads, count, kmer);
         kt.start();
-        if (count)
-            k_smem<true><<<G, B, 0, st>>>(I, (const u8 *)dseq, (const u64 *)doff, n_reads, (const u8 *)dmate, bs, l,
-                                          c, bslots.as<SlotRec>(), bcounts.as<u64>(), bovf.as<u32>(), dovf_n, wc);
+        if (count && kmer)
+            k_smem<true, true><<<Gs, B, 0, st>>>(I, (const u8 *)dseq, (const u64 *)doff, n_reads, (const u8 *)dmate,
+                                                 bs, l, c, bslots.as<SlotRec>(), bcounts.as<u64>(), bovf.as<u32>(),
+                                                 dovf_n, wc);
+        else if (count)
+            k_smem<true, false><<<Gs, B, 0, st>>>(I, (const u8 *)dseq, (const u64 *)doff, n_reads,
+                                                  (const u8 *)dmate, bs, l, c, bslots.as<SlotRec>(),
+                                                  bcounts.as<u64>(), bovf.as<u32>(), dovf_n, wc);
+        else if (kmer)
+            k_smem<false, true><<<Gs, B, 0, st>>>(I, (const u8 *)dseq, (const u64 *)doff, n_reads,
+                                                  (const u8 *)dmate, bs, l, c, bslots.as<SlotRec>(),
+                                                  bcounts.as<u64>(), bovf.as<u32>(), dovf_n, nullptr);
         else
-            k_smem<false><<<G, B, 0, st>>>(I, (const u8 *)dseq, (const u64 *)doff, n_reads, (const u8 *)dmate, bs,
-                                           l, c, bslots.as<SlotRec>(), bcounts.as<u64>(), bovf.as<u32>(), dovf_n,
-                                           nullptr);
+            k_smem<false, false><<<Gs, B, 0, st>>>(I, (const u8 *)dseq, (const u64 *)doff, n_reads,
+                                                   (const u8 *)dmate, bs, l, c, bslots.as<SlotRec>(),
+                                                   bcounts.as<u64>(), bovf.as<u32>(), dovf_n, nullptr);
         kt.stop();
         MB_KCHECK();
     }
@@ -369,8 +555,14 @@ extern "C" int mb_seed_batch(const mb_index *idx, const uint8_t *seq, const uint
     k_gather<<<G, B, 0, st>>>((const u64 *)doff, n_reads, bslots.as<SlotRec>(), bcounts.as<u64>(), bsoff.as<u64>(),
                               max_occ, dout, bhitc.as<u64>());
     MB_KCHECK();
-    k_smem_overflow<<<152, 128, 0, st>>>(I, (const u8 *)dseq, (const u64 *)doff, (const u8 *)dmate, bs, l, c,
-                                         bovf.as<u32>(), dovf_n, bsoff.as<u64>(), max_occ, dout, bhitc.as<u64>());
+    if (kmer)
+        k_smem_overflow<true><<<152, 128, 0, st>>>(I, (const u8 *)dseq, (const u64 *)doff, (const u8 *)dmate, bs, l,
+                                                   c, bovf.as<u32>(), dovf_n, bsoff.as<u64>(), max_occ, dout,
+                                                   bhitc.as<u64>());
+    else
+        k_smem_overflow<false><<<152, 128, 0, st>>>(I, (const u8 *)dseq, (const u64 *)doff, (const u8 *)dmate, bs,
+                                                    l, c, bovf.as<u32>(), dovf_n, bsoff.as<u64>(), max_occ, dout,
+                                                    bhitc.as<u64>());
     MB_KCHECK();
     MB_TRY(bhtmp.alloc(scan_tmp_bytes(total), st));
     MB_TRY(scan_exclusive_u64(bhitc.as<u64>(), bhitc.as<u64>(), total, dhtotal, bhtmp.p, st));
@@ -412,7 +604,7 @@ extern "C" int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_sm
     }
     const DevIndex I = mb_dev_index(idx);
     const bool count = opts && (opts->flags & MB_COUNT);
-    const unsigned G = grid_for(total, 256, 152u * 2048u / 256u * 8u);
+    const unsigned G = resident_grid((const void *)k_locate<false>, 256, total);
     KTimer kt("locate", st);
     kt.start();
     if (count)
@@ -558,7 +750,13 @@ extern "C" int mb_seed_batch_noalloc(const mb_index *idx, const uint8_t *seq, co
 
     const DevIndex I = mb_dev_index(idx);
     const unsigned B = 256, G = (unsigned)((nr + B - 1) / B);
-    k_smem<false><<<G, B, 0, st>>>(I, seq, off, n_reads, mate, bs, l, c, slots, counts, ovf, dovf_n, nullptr);
+    const bool kmer = !(flags & MB_NO_KMER) && l >= I.kmer_k;
+    if (kmer)
+        k_smem<false, true><<<smem_grid(n_reads, false, true), B, 0, st>>>(I, seq, off, n_reads, mate, bs, l, c,
+                                                                          slots, counts, ovf, dovf_n, nullptr);
+    else
+        k_smem<false, false><<<smem_grid(n_reads, false, false), B, 0, st>>>(I, seq, off, n_reads, mate, bs, l, c,
+                                                                            slots, counts, ovf, dovf_n, nullptr);
     MB_KCHECK();
     MB_TRY(scan_exclusive_u64(counts, soff, nr, dtotal, S + o_tmp, st));
     u64 total = 0;
@@ -579,7 +777,11 @@ extern "C" int mb_seed_batch_noalloc(const mb_index *idx, const uint8_t *seq, co
     u64 *hitc = (u64 *)(S + o_hitc);
     k_gather<<<G, B, 0, st>>>(off, n_reads, slots, counts, soff, max_occ, out, hitc);
     MB_KCHECK();
-    k_smem_overflow<<<152, 128, 0, st>>>(I, seq, off, mate, bs, l, c, ovf, dovf_n, soff, max_occ, out, hitc);
+    if (kmer)
+        k_smem_overflow<true><<<152, 128, 0, st>>>(I, seq, off, mate, bs, l, c, ovf, dovf_n, soff, max_occ, out, hitc);
+    else
+        k_smem_overflow<false><<<152, 128, 0, st>>>(I, seq, off, mate, bs, l, c, ovf, dovf_n, soff, max_occ, out,
+                                                    hitc);
     MB_KCHECK();
     MB_TRY(scan_exclusive_u64(hitc, hitc, total, dhtotal, S + o_htmp, st));
     k_set_hitoff<<<grid_for(total, 256), 256, 0, st>>>(hitc, total, out);

@@ -1,0 +1,119 @@
+"""Parity at full workload sizes, in the launch configuration bench.py times.
+
+The GPU builds the whole index and seeds the whole read batch (device buffers, one
+mb_seed_batch + one mb_locate call); the CPU oracle builds its own index by sorting
+suffixes and checks the full suffix array, the block counts, the k-mer table, and a
+seeded random sample of the reads (every SMEM record and every hit of each sampled
+read).  Minutes per test: marked slow as well as gpu.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mb():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2606_15357_gb300 as m
+    m.lib()
+    return m
+
+
+def dev(a):
+    a = np.ascontiguousarray(a)
+    return torch.from_numpy(a.view(np.int64) if a.dtype == np.uint64 else a).cuda()
+
+
+def gpu_seed_all(mb, G, rd, opts=None):
+    seq, off = dev(rd.seq), dev(rd.off)
+    cap = 4 * rd.n
+    out = torch.empty(cap * 48, dtype=torch.uint8, device="cuda")
+    _, m, nh = mb.mb_seed_batch(G, seq, off, opts=opts, out=out, cap=cap)
+    hits = torch.empty(max(nh, 1), dtype=torch.int32, device="cuda")
+    mb.mb_locate(G, out, m, opts=opts, hits=hits, cap=nh)
+    sm = out[:m * 48].cpu().numpy().view(mb.SMEM_DTYPE)
+    h = hits[:nh].cpu().numpy().view(np.uint32)
+    return sm, h
+
+
+def check_index(G, X, k=10, sample_kmers=None):
+    e = G.export(sa=True, ssa=True, occ=True, kmer=True, kmer_k=k)
+    assert G.n == X.n and G.primary == X.primary
+    osa = X.sa()
+    assert np.array_equal(e["sa"], osa)
+    del osa
+    assert np.array_equal(e["ssa"], X.ssa())
+    assert np.array_equal(e["C"], X.C)
+    B = X.bwt()
+    occ = e["occ"].reshape(-1, 8)
+    for a in range(4):
+        blk = np.add.reduceat((B == a + 1).view(np.uint8), np.arange(0, len(B), 128), dtype=np.uint64)
+        cum = np.concatenate([[0], np.cumsum(blk)]).astype(np.uint64)[:len(occ)]
+        assert np.array_equal(occ[:, a], cum), a
+    del B
+    nk = 4 ** k
+    words = np.arange(nk, dtype=np.int64)
+    if sample_kmers:
+        words = np.sort(np.random.default_rng(7).choice(nk, sample_kmers, replace=False))
+    pats = np.stack([(words >> (2 * (k - 1 - t))) & 3 for t in range(k)], axis=1).astype(np.uint8)
+    want = X.ds_intervals(pats).astype(np.uint32)
+    got = e["kmer"].reshape(nk, 3)[words]
+    assert np.array_equal(got, want)
+
+
+def check_sampled_reads(sm, hits, X, rd, frac, seed, params):
+    rng = np.random.default_rng(seed)
+    pick = np.sort(rng.choice(rd.n, max(1, int(rd.n * frac)), replace=False))
+    sub = rd.subset(pick)
+    osm, over, hoff, ohits = X.seed(sub.seq, sub.off, params["min_len"], params["min_occ"],
+                                    params["max_occ"])
+    reads = sm["read"].astype(np.int64)
+    lo = np.searchsorted(reads, pick, side="left")
+    hi = np.searchsorted(reads, pick, side="right")
+    o_lo = np.searchsorted(osm["read"].astype(np.int64), np.arange(len(pick)), side="left")
+    o_hi = np.searchsorted(osm["read"].astype(np.int64), np.arange(len(pick)), side="right")
+    assert np.array_equal(hi - lo, o_hi - o_lo)
+    g_idx = np.concatenate([np.arange(a, b) for a, b in zip(lo, hi)]) if len(pick) else np.zeros(0, int)
+    g = sm[g_idx]
+    for f in ("qbeg", "qend", "k", "kr", "s"):
+        assert np.array_equal(g[f].astype(np.uint64), osm[f]), f
+    assert np.array_equal(pick[osm["read"].astype(np.int64)], g["read"].astype(np.int64))
+    assert np.array_equal((g["flags"] & 1).astype(bool), over)
+    # hits of the sampled reads, in record order then SA-row order
+    cnt = np.where(g["flags"] & 1, 0, g["s"]).astype(np.int64)
+    starts = g["hit_off"].astype(np.int64)
+    gh = np.concatenate([hits[s:s + c] for s, c in zip(starts, cnt)]) if len(g) else np.zeros(0)
+    assert np.array_equal(gh.astype(np.uint64), ohits)
+    return len(pick), len(g), len(gh)
+
+
+def test_workload3_1gbp_full_index_and_sampled_reads(mb):
+    """1 Gbp repeat-rich reference, 10M pairs: full SA / blocks / k-mer sample and 1% of reads."""
+    ref, rd, params = synth.workload(3)
+    G = mb.mb_index_build(dev(ref))
+    X = oracle.Index(ref, threads=os.cpu_count())
+    check_index(G, X, sample_kmers=200_000)
+    G.drop_sa()
+    sm, hits = gpu_seed_all(mb, G, rd)
+    n, m, h = check_sampled_reads(sm, hits, X, rd, 0.01, 0x6D62, params)
+    print(f"checked {n} reads, {m} SMEMs, {h} hits")
+
+
+def test_workload2_100mbp_full_index_and_sampled_reads(mb):
+    """100 Mbp repeat-rich reference, 1M pairs: full index and 10% of reads."""
+    ref, rd, params = synth.workload(2)
+    G = mb.mb_index_build(dev(ref))
+    X = oracle.Index(ref, threads=os.cpu_count())
+    check_index(G, X)
+    G.drop_sa()
+    sm, hits = gpu_seed_all(mb, G, rd)
+    check_sampled_reads(sm, hits, X, rd, 0.10, 0x6D63, params)
