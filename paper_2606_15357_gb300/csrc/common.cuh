@@ -127,43 +127,38 @@ __device__ __forceinline__ Blk load_blk(const OccBlock *__restrict__ blk) {
     return b;
 }
 
-// Counts of A,C,G,T and of $ in B[0, x), x in the block b.
-struct Occ4 {
-    u32 c[4];
-    u32 dollar;
-};
-__device__ __forceinline__ Occ4 occ_blk(const Blk &b, u32 x, u32 primary) {
-    const u32 m = x & 127;
-    u32 nl = 0, nh = 0, nt = 0;
+// Bit mask of the 2-bit slots of word q (0..3) that lie before slot m (0..128) of the block.
+__device__ __forceinline__ u64 slot_mask(u32 m, int q) {
+    int take = (int)m - 32 * q;
+    take = take < 0 ? 0 : (take > 32 ? 32 : take);
+    return take == 32 ? ~0ULL : ((1ULL << (2 * take)) - 1);
+}
+// Two words of even-position bits folded into one word, so one popcount covers both.
+__device__ __forceinline__ u32 popc_pair(u64 z0, u64 z1) { return __popcll(z0 | (z1 << 1)); }
+
+constexpr u64 EVEN = 0x5555555555555555ULL;
+
+// #{slots before m holding code a}; the $ row (stored as A) is not corrected here.
+__device__ __forceinline__ u32 cnt_sym(const Blk &b, u32 m, u32 a) {
+    const u64 pat = (u64)a * EVEN;   // a in every 2-bit slot
+    u64 z[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        int take = (int)m - 32 * q;
-        take = take < 0 ? 0 : (take > 32 ? 32 : take);
-        u64 mask = take == 32 ? ~0ULL : ((1ULL << (2 * take)) - 1);
-        u64 y = b.w[q] & mask;
-        u64 lo = y & 0x5555555555555555ULL, hi = (y >> 1) & 0x5555555555555555ULL;
-        nl += __popcll(lo);
-        nh += __popcll(hi);
-        nt += __popcll(lo & hi);
+        const u64 y = ~(b.w[q] ^ pat);   // 11 where the slot holds a
+        z[q] = y & (y >> 1) & EVEN & slot_mask(m, q);
     }
-    // symbol codes: A=00 C=01 G=10 T=11 (low bit first); the $ row is stored as A
-    const u32 cT = nt, cC = nl - nt, cG = nh - nt, cA = m - cC - cG - cT;
-    const u32 bstart = x & ~127u;
-    const u32 d = (primary >= bstart && primary < x) ? 1u : 0u;
-    Occ4 o;
-    o.c[0] = b.c[0] + cA - d;
-    o.c[1] = b.c[1] + cC;
-    o.c[2] = b.c[2] + cG;
-    o.c[3] = b.c[3] + cT;
-    o.dollar = primary < x ? 1u : 0u;
-    return o;
+    return popc_pair(z[0], z[1]) + popc_pair(z[2], z[3]);
 }
-
-// symbol (0..3) stored at row x of its block ($ reads as A)
-__device__ __forceinline__ u32 sym_blk(const Blk &b, u32 x) {
-    const u32 q = x & 127;
-    const u64 w = q < 64 ? (q < 32 ? b.w[0] : b.w[1]) : (q < 96 ? b.w[2] : b.w[3]);
-    return (u32)(w >> (2 * (q & 31))) & 3u;
+// #{slots before m holding a code <= a}; the $ row (stored as A) is not corrected here.
+__device__ __forceinline__ u32 cnt_le(const Blk &b, u32 m, u32 a) {
+    u64 z[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const u64 lo = b.w[q] & EVEN, hi = (b.w[q] >> 1) & EVEN;
+        const u64 e = a == 0 ? (~lo & ~hi) : a == 1 ? ~hi : a == 2 ? ~(lo & hi) : ~0ULL;
+        z[q] = e & EVEN & slot_mask(m, q);
+    }
+    return popc_pair(z[0], z[1]) + popc_pair(z[2], z[3]);
 }
 
 // x[a] for a in 0..3 without dynamic indexing (which would go through local memory)
@@ -171,57 +166,56 @@ __device__ __forceinline__ u32 sel4(u32 a, u32 x0, u32 x1, u32 x2, u32 x3) {
     return a < 2 ? (a == 0 ? x0 : x1) : (a == 2 ? x2 : x3);
 }
 
+// [the $ row lies in the block of x, before x]
+__device__ __forceinline__ u32 dollar_before(u32 x, u32 primary) {
+    const u32 bstart = x & ~127u;
+    return (primary >= bstart && primary < x) ? 1u : 0u;
+}
+
 // One LF step of Algorithm 2 from row x (x is not the $ row): a = B[x], result C[a] + #a in
-// B[0, x), counting only symbol a (one popcount per word).
+// B[0, x).
 __device__ __forceinline__ u32 lf_blk(const Blk &b, u32 x, u32 primary, u32 C0, u32 C1, u32 C2, u32 C3) {
     const u32 m = x & 127;
     const u64 wx = m < 64 ? (m < 32 ? b.w[0] : b.w[1]) : (m < 96 ? b.w[2] : b.w[3]);
     const u32 a = (u32)(wx >> (2 * (m & 31))) & 3u;
-    const u64 pat = (u64)a * 0x5555555555555555ULL;   // a repeated in every 2-bit slot
-    u32 cnt = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        int take = (int)m - 32 * q;
-        take = take < 0 ? 0 : (take > 32 ? 32 : take);
-        const u64 mask = take == 32 ? ~0ULL : ((1ULL << (2 * take)) - 1);
-        const u64 y = ~(b.w[q] ^ pat);                    // 11 where the slot holds a
-        cnt += __popcll(y & (y >> 1) & 0x5555555555555555ULL & mask);
-    }
-    const u32 bstart = x & ~127u;
-    if (a == 0 && primary >= bstart && primary < x) cnt -= 1;   // the $ row is stored as A
+    u32 cnt = cnt_sym(b, m, a);
+    if (a == 0) cnt -= dollar_before(x, primary);
     return sel4(a, C0 + b.c[0], C1 + b.c[1], C2 + b.c[2], C3 + b.c[3]) + cnt;
 }
-
 
 // Algorithm 1 in one step.  Extends the interval (p, q, s) of P on the side of p by symbol a
 // (0..3): p is lo of the strand being extended backwards, q is lo of the other strand.
 //   s'  = #a in B[p, p+s)
 //   p'  = C[a] + #a in B[0, p)
-//   q'  = q + #{ $ or symbols > a } in B[p, p+s)
+//   q'  = q + #{ $ or symbols > a } in B[p, p+s) = q + s - #{symbols <= a} in B[p, p+s)
 // BackwardExt((k,k',s), a) is (p,q) = (k,k'); ForwardExt((k,k',s), a) is (p,q) = (k',k) with
 // the complement of a.
 struct Ext {
     u32 p, q, s;
 };
-__device__ __forceinline__ Ext extend_from(const DevIndex &I, const Occ4 &lo, const Occ4 &hi, u32 q, u32 a) {
-    const u32 d0 = hi.c[0] - lo.c[0], d1 = hi.c[1] - lo.c[1], d2 = hi.c[2] - lo.c[2], d3 = hi.c[3] - lo.c[3];
-    const u32 gt = (hi.dollar - lo.dollar) + (a < 3 ? d3 : 0) + (a < 2 ? d2 : 0) + (a < 1 ? d1 : 0);
-    Ext e;
-    e.s = sel4(a, d0, d1, d2, d3);
-    e.p = sel4(a, (u32)I.C[0] + lo.c[0], (u32)I.C[1] + lo.c[1], (u32)I.C[2] + lo.c[2], (u32)I.C[3] + lo.c[3]);
-    e.q = q + gt;
-    return e;
+// #a and #{symbols <= a} in B[0, x), $ excluded
+__device__ __forceinline__ void occ_a_le(const Blk &b, u32 x, u32 a, u32 primary, u32 &na, u32 &nle) {
+    const u32 m = x & 127, d = dollar_before(x, primary);
+    na = sel4(a, b.c[0], b.c[1], b.c[2], b.c[3]) + cnt_sym(b, m, a) - (a == 0 ? d : 0u);
+    const u32 c01 = b.c[0] + b.c[1], c012 = c01 + b.c[2];
+    nle = sel4(a, b.c[0], c01, c012, c012 + b.c[3]) + cnt_le(b, m, a) - d;
 }
 
 // One extension: the blocks of rows p and p+s are read once each (once in all when they are the
 // same block).
 __device__ __forceinline__ Ext extend(const DevIndex &I, u32 p, u32 q, u32 s, u32 a) {
-    const u32 e = p + s;
+    const u32 e = p + s, prim = (u32)I.primary;
     const Blk b0 = load_blk(I.occ + (p >> 7));
     Blk b1 = b0;
     if ((e >> 7) != (p >> 7)) b1 = load_blk(I.occ + (e >> 7));
-    const u32 prim = (u32)I.primary;
-    return extend_from(I, occ_blk(b0, p, prim), occ_blk(b1, e, prim), q, a);
+    u32 na0, nle0, na1, nle1;
+    occ_a_le(b0, p, a, prim, na0, nle0);
+    occ_a_le(b1, e, a, prim, na1, nle1);
+    Ext r;
+    r.s = na1 - na0;
+    r.p = sel4(a, (u32)I.C[0], (u32)I.C[1], (u32)I.C[2], (u32)I.C[3]) + na0;
+    r.q = q + s - (nle1 - nle0);
+    return r;
 }
 
 // splitmix64 output function; bits 63..62 give the base replacing an ambiguous reference base.

@@ -243,43 +243,72 @@ __device__ __forceinline__ u32 conv_of(const u8 *mate, u64 r, u32 bs) {
     return m == 1 ? 1u : (m == 2 ? 2u : 0u);
 }
 
-// One lane keeps one read in flight; when it finishes, the lane takes the next read
-// (r += total threads) inside the same loop, so lanes never wait for the slowest read of
-// their warp.  Each loop iteration performs at most one extension.
+// Work distribution shared by the seeding kernels: each warp owns one contiguous range of items
+// and hands the next item of its range to each lane that finishes, in lane order (ballot rank).
+// The loop is warp-uniform: every iteration starts with all 32 lanes converged, so one memory
+// instruction serves every lane that has work.
+struct WarpRange {
+    u64 next, end;
+    __device__ __forceinline__ void init(u64 total) {
+        const u64 gw = (blockIdx.x * (u64)blockDim.x + threadIdx.x) >> 5;
+        const u64 nw = ((u64)gridDim.x * blockDim.x) >> 5;
+        const u64 per = (total + nw - 1) / nw;
+        next = gw * per < total ? gw * per : total;
+        end = next + per < total ? next + per : total;
+    }
+};
+
+// One lane keeps one read in flight; each loop iteration performs at most one extension per lane.
 template <bool COUNT, bool KMER>
-__global__ void __launch_bounds__(256) k_smem(DevIndex I, const u8 *__restrict__ seq, const u64 *__restrict__ off,
+__global__ void __launch_bounds__(256, 4) k_smem(DevIndex I, const u8 *__restrict__ seq, const u64 *__restrict__ off,
                                               u32 nr, const u8 *__restrict__ mate, u32 bs, u32 l, u32 c,
                                               SlotRec *__restrict__ slots, u64 *__restrict__ counts,
                                               u32 *__restrict__ ovf_list, u32 *__restrict__ ovf_n, u64 *wc) {
-    const u32 stride = gridDim.x * blockDim.x;
+    const u32 lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
     const u32 n = (u32)I.n;
     const u64 o0 = off[0];
     Work<COUNT> work;
     SmemState S;
     SlotEmit em;
-    u32 r = blockIdx.x * blockDim.x + threadIdx.x;
-    auto start = [&](u32 rr) {
+    WarpRange wr;
+    wr.init(nr);
+    auto start = [&](u64 rr) {
         const u64 b = off[rr], e = off[rr + 1];
-        const u64 sb = (b - o0) / 32 + 4 * (u64)rr, se = (e - o0) / 32 + 4 * (u64)(rr + 1);
+        const u64 sb = (b - o0) / 32 + 4 * rr, se = (e - o0) / 32 + 4 * (rr + 1);
         em.slots = slots;
         em.base = sb;
         em.cap = (u32)(se - sb);
         em.cnt = 0;
         smem_begin(S, seq + b, (int)(e - b), conv_of(mate, rr, bs), l, n);
     };
-    if (r < nr) start(r);
-    while (r < nr) {
-        bool go = smem_advance<KMER>(S, I, l, c, em, work);
-        if (go) {
-            u32 nk, nkr, ns;
-            smem_extend(S, I, nk, nkr, ns, work);
-            go = smem_apply(S, nk, nkr, ns, l, c, n, em);
+    u64 r = wr.next + lane;
+    bool live = r < wr.end;
+    wr.next += 32;
+    if (live) start(r);
+    for (;;) {
+        if (__all_sync(0xffffffffu, !live)) break;
+        bool fin = false;
+        if (live) {
+            bool go = smem_advance<KMER>(S, I, l, c, em, work);
+            if (go) {
+                u32 nk, nkr, ns;
+                smem_extend(S, I, nk, nkr, ns, work);
+                go = smem_apply(S, nk, nkr, ns, l, c, n, em);
+            }
+            if (!go) {
+                counts[r] = em.cnt;
+                if (em.cnt > em.cap) ovf_list[atomicAdd(ovf_n, 1u)] = (u32)r;
+                fin = true;
+            }
         }
-        if (!go) {
-            counts[r] = em.cnt;
-            if (em.cnt > em.cap) ovf_list[atomicAdd(ovf_n, 1u)] = r;
-            r += stride;
-            if (r < nr) start(r);
+        const u32 fm = __ballot_sync(0xffffffffu, fin);
+        if (fm) {
+            if (fin) {
+                r = wr.next + __popc(fm & lt);
+                live = r < wr.end;
+                if (live) start(r);
+            }
+            wr.next += __popc(fm);
         }
     }
     work.flush(wc);
@@ -360,51 +389,89 @@ __device__ __forceinline__ u64 hits_of(const mb_smem *__restrict__ sm, u64 m) {
     return (__ldg(&sm[m].flags) & MB_SMEM_OVER_MAX_OCC) ? 0 : __ldg(&sm[m].s);
 }
 
-// Locate (Algorithm 2).  Every lane owns one contiguous range of hits; it LF-walks one row at a
-// time, one step per loop iteration, and starts its next row inside the same loop as soon as a
-// walk ends, so lanes never wait for the longest walk of their warp.  A walk ends on a sampled
-// row (position = steps + S(row)) or on the $ row (S = 0, position = steps).  A walk needs fewer
+// rows[hit_off + t] = k + t for the hits of every record without MB_SMEM_OVER_MAX_OCC: one warp
+// per 32 records, writing each record's rows with the whole warp.
+__global__ void k_expand_rows(const mb_smem *__restrict__ sm, u64 nsm, u32 *__restrict__ rows) {
+    const u32 lane = threadIdx.x & 31;
+    const u64 nw = ((u64)gridDim.x * blockDim.x) >> 5;
+    for (u64 base = ((blockIdx.x * (u64)blockDim.x + threadIdx.x) >> 5) * 32; base < nsm; base += nw * 32) {
+        u64 m = base + lane;
+        u64 ho = 0, cnt = 0;
+        u32 k = 0;
+        if (m < nsm) {
+            ho = __ldg(&sm[m].hit_off);
+            cnt = hits_of(sm, m);
+            k = (u32)__ldg(&sm[m].k);
+        }
+        for (int q = 0; q < 32; ++q) {
+            const u64 hq = __shfl_sync(0xffffffffu, ho, q), cq = __shfl_sync(0xffffffffu, cnt, q);
+            const u32 kq = __shfl_sync(0xffffffffu, k, q);
+            for (u64 t = lane; t < cq; t += 32) rows[hq + t] = kq + (u32)t;
+        }
+    }
+}
+
+// Locate (Algorithm 2).  Each lane LF-walks one row at a time, one step per loop iteration; a
+// lane whose walk ends takes the next row of its warp's range at once (rows are prefetched 64
+// ahead, two coalesced buffers, and handed over by shuffle).  A walk ends on a sampled row
+// (position = steps + S(row)) or on the $ row (S = 0, position = steps).  The sampled-SA read
+// and the block read of the other lanes are issued in the same iteration.  A walk needs fewer
 // than n steps; the bound only guards against a corrupted index (it then writes 0xFFFFFFFF).
-template <bool COUNT>
-__global__ void __launch_bounds__(256) k_locate(DevIndex I, const mb_smem *__restrict__ sm, u64 nsm, u64 nhits,
+template <bool COUNT, bool POW2>
+__global__ void __launch_bounds__(256) k_locate(DevIndex I, const u32 *__restrict__ rows, u64 nhits,
                                                 u32 *__restrict__ hits, u64 *wc) {
-    const u64 nt = (u64)gridDim.x * blockDim.x;
-    const u64 tid = blockIdx.x * (u64)blockDim.x + threadIdx.x;
-    const u64 per = (nhits + nt - 1) / nt;
-    u64 h = tid * per;
-    const u64 h1 = h + per < nhits ? h + per : nhits;
-    if (h >= h1) return;
+    const u32 lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
     Work<COUNT> work;
-    const u32 r = I.r, prim = (u32)I.primary, n = (u32)I.n;
+    const u32 r = I.r, rmask = I.r - 1, rshift = __ffs(I.r) - 1, prim = (u32)I.primary, n = (u32)I.n;
     const u32 C0 = (u32)I.C[0], C1 = (u32)I.C[1], C2 = (u32)I.C[2], C3 = (u32)I.C[3];
-    u64 m = owner_of(sm, nsm, h);
-    u64 moff = __ldg(&sm[m].hit_off), mend = moff + hits_of(sm, m);
-    u32 mk = (u32)__ldg(&sm[m].k);
-    u32 row = mk + (u32)(h - moff), steps = 0;
+    WarpRange wr;
+    wr.init(nhits);
+    // rows of the range, 64 ahead: buf0 holds rows[bufbase + lane], buf1 rows[bufbase + 32 + lane];
+    // at the top of every iteration bufbase <= wr.next < bufbase + 32.
+    u64 bufbase = wr.next;
+    u32 buf0 = bufbase + lane < wr.end ? __ldg(&rows[bufbase + lane]) : 0u;
+    u32 buf1 = bufbase + 32 + lane < wr.end ? __ldg(&rows[bufbase + 32 + lane]) : 0u;
+    u64 h = wr.next + lane;
+    bool live = h < wr.end;
+    u32 row = buf0, steps = 0;
+    wr.next += 32;
+    bufbase += 32;
+    buf0 = buf1;
+    buf1 = bufbase + 32 + lane < wr.end ? __ldg(&rows[bufbase + 32 + lane]) : 0u;
     for (;;) {
-        const bool sampled = row % r == 0;
-        if (sampled || row == prim || steps > n) {
-            u32 pos = sampled ? __ldg(&I.ssa[row / r]) + steps : steps;
-            if (steps > n) pos = 0xFFFFFFFFu;
-            hits[h] = pos;
+        if (__all_sync(0xffffffffu, !live)) break;
+        const bool sampled = POW2 ? (row & rmask) == 0 : row % r == 0;
+        const bool stop = live && (sampled || row == prim || steps > n);
+        u32 sv = 0;
+        if (stop && sampled) sv = __ldg(&I.ssa[POW2 ? (row >> rshift) : row / r]);
+        Blk b;
+        if (live && !stop) b = load_blk(I.occ + (row >> 7));
+        if (stop) {
+            hits[h] = steps > n ? 0xFFFFFFFFu : (sampled ? sv + steps : steps);
             work.lf += steps;
             work.sa += sampled ? 1 : 0;
-            if (++h >= h1) break;
-            while (h >= mend) {                 // next record that has hits
-                if (++m >= nsm) {               // inconsistent hit_off values: stop this range
-                    work.flush(wc);
-                    return;
-                }
-                moff = __ldg(&sm[m].hit_off);
-                mend = moff + hits_of(sm, m);
-                mk = (u32)__ldg(&sm[m].k);
-            }
-            row = mk + (u32)(h - moff);
-            steps = 0;
-            continue;
+        } else if (live) {
+            row = lf_blk(b, row, prim, C0, C1, C2, C3);
+            ++steps;
         }
-        row = lf_blk(load_blk(I.occ + (row >> 7)), row, prim, C0, C1, C2, C3);
-        ++steps;
+        const u32 fm = __ballot_sync(0xffffffffu, stop);
+        if (fm) {
+            const u64 idx = wr.next + __popc(fm & lt);
+            const u32 o = (u32)(idx - bufbase);   // < 64 while both buffers cover wr.next..+63
+            const u32 v0 = __shfl_sync(0xffffffffu, buf0, o & 31), v1 = __shfl_sync(0xffffffffu, buf1, o & 31);
+            if (stop) {
+                h = idx;
+                live = h < wr.end;
+                row = o < 32 ? v0 : v1;
+                steps = 0;
+            }
+            wr.next += __popc(fm);
+            if (wr.next >= bufbase + 32) {     // first buffer used up: slide by 32
+                bufbase += 32;
+                buf0 = buf1;
+                buf1 = bufbase + 32 + lane < wr.end ? __ldg(&rows[bufbase + 32 + lane]) : 0u;
+            }
+        }
     }
     work.flush(wc);
 }
@@ -604,13 +671,21 @@ extern "C" int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_sm
     }
     const DevIndex I = mb_dev_index(idx);
     const bool count = opts && (opts->flags & MB_COUNT);
-    const unsigned G = resident_grid((const void *)k_locate<false>, 256, total);
+    const bool pow2 = (I.r & (I.r - 1)) == 0;
+    DevBuf brows;
+    MB_TRY(brows.alloc(total * 4, st));
+    k_expand_rows<<<grid_for(n_smem, 256), 256, 0, st>>>((const mb_smem *)dsm, n_smem, brows.as<u32>());
+    MB_KCHECK();
+    const void *kfn = count ? (pow2 ? (const void *)k_locate<true, true> : (const void *)k_locate<true, false>)
+                            : (pow2 ? (const void *)k_locate<false, true> : (const void *)k_locate<false, false>);
+    const unsigned G = resident_grid(kfn, 256, (total + 63) / 64 * 32);
+    u64 *wc = count ? mb_work_counter_buf(st) : nullptr;
     KTimer kt("locate", st);
     kt.start();
-    if (count)
-        k_locate<true><<<G, 256, 0, st>>>(I, (const mb_smem *)dsm, n_smem, total, dh, mb_work_counter_buf(st));
-    else
-        k_locate<false><<<G, 256, 0, st>>>(I, (const mb_smem *)dsm, n_smem, total, dh, nullptr);
+    if (count && pow2) k_locate<true, true><<<G, 256, 0, st>>>(I, brows.as<u32>(), total, dh, wc);
+    else if (count) k_locate<true, false><<<G, 256, 0, st>>>(I, brows.as<u32>(), total, dh, wc);
+    else if (pow2) k_locate<false, true><<<G, 256, 0, st>>>(I, brows.as<u32>(), total, dh, nullptr);
+    else k_locate<false, false><<<G, 256, 0, st>>>(I, brows.as<u32>(), total, dh, nullptr);
     kt.stop();
     MB_KCHECK();
     if (!hdev) MB_CK(cudaMemcpyAsync(hits, dh, total * 4, cudaMemcpyDeviceToHost, st));
