@@ -116,14 +116,14 @@ struct Blk {
     u32 c[4];
     u64 w[4];
 };
+// Two 256-bit loads per block: one for the counts, one for the symbols.
 __device__ __forceinline__ Blk load_blk(const OccBlock *__restrict__ blk) {
-    const uint4 *p = reinterpret_cast<const uint4 *>(blk);
-    const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(blk);
-    uint4 c01 = __ldg(p), c23 = __ldg(p + 1);
-    ulonglong2 w01 = __ldg(q + 2), w23 = __ldg(q + 3);
+    u64 c0, c1, c2, c3, w0, w1, w2, w3;
+    asm("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];" : "=l"(c0), "=l"(c1), "=l"(c2), "=l"(c3) : "l"(blk->cnt));
+    asm("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];" : "=l"(w0), "=l"(w1), "=l"(w2), "=l"(w3) : "l"(blk->w));
     Blk b;
-    b.c[0] = c01.x; b.c[1] = c01.z; b.c[2] = c23.x; b.c[3] = c23.z;
-    b.w[0] = w01.x; b.w[1] = w01.y; b.w[2] = w23.x; b.w[3] = w23.y;
+    b.c[0] = (u32)c0; b.c[1] = (u32)c1; b.c[2] = (u32)c2; b.c[3] = (u32)c3;
+    b.w[0] = w0; b.w[1] = w1; b.w[2] = w2; b.w[3] = w3;
     return b;
 }
 

@@ -287,13 +287,35 @@ __global__ void __launch_bounds__(256, 4) k_smem(DevIndex I, const u8 *__restric
     if (live) start(r);
     for (;;) {
         if (__all_sync(0xffffffffu, !live)) break;
+        // phase 1 (divergent, no block reads): move through stage changes up to the next extension
+        bool need = false;
+        u32 p = 0, q = 0, ss = 0, sym = 4;
+        if (live) {
+            need = smem_advance<KMER>(S, I, l, c, em, work);
+            if (need) {
+                const u32 a = read_base(S.P, (u64)S.j, S.conv);
+                const bool fwd = S.u == 2;   // ForwardExt((k,kr,s), a) = BackwardExt((kr,k,s), comp a)
+                p = fwd ? S.kr : S.k;
+                q = fwd ? S.k : S.kr;
+                ss = S.s;
+                sym = a > 3 ? 4u : (fwd ? 3u - a : a);
+            }
+        }
+        __syncwarp();
+        // phase 2 (converged): one extension for every lane that has one; an N reads nothing
+        u32 np = 0, nq = 0, ns = 0;
+        if (sym < 4) {
+            work.ext(p, ss);
+            const Ext e = extend(I, p, q, ss, sym);
+            np = e.p; nq = e.q; ns = e.s;
+        }
+        // phase 3: apply, finish, refill
         bool fin = false;
         if (live) {
-            bool go = smem_advance<KMER>(S, I, l, c, em, work);
-            if (go) {
-                u32 nk, nkr, ns;
-                smem_extend(S, I, nk, nkr, ns, work);
-                go = smem_apply(S, nk, nkr, ns, l, c, n, em);
+            bool go = need;
+            if (need) {
+                const bool fwd = S.u == 2;
+                go = smem_apply(S, fwd ? nq : np, fwd ? np : nq, ns, l, c, n, em);
             }
             if (!go) {
                 counts[r] = em.cnt;
