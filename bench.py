@@ -55,6 +55,24 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def gather_ceiling(gib: int = 4):
+    """Random 64-/32-byte block reads over a buffer far above L2 (probe library): independent
+    reads (bandwidth ceiling) and dependent chains (LF-walk pattern), GB/s of bytes requested."""
+    import ctypes
+    from paper_2606_15357_gb300.nvcc_build import build_probe
+    L = ctypes.CDLL(build_probe())
+    L.mb_probe_gather.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_uint,
+                                  ctypes.POINTER(ctypes.c_float)]
+    L.mb_probe_gather.restype = ctypes.c_double
+    out = {}
+    ms = ctypes.c_float()
+    for mode, name, iters in ((0, "indep", 2048), (1, "chain", 512)):
+        for bb in (64, 32):
+            out[f"random{bb}_{name}_GBps"] = L.mb_probe_gather(gib << 30, mode, bb, iters, ctypes.byref(ms))
+    out["buffer_GiB"] = gib
+    return out
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     for f in ("seed.cu", "common.cuh"):
@@ -134,9 +152,11 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def make_inputs(workload: int, scale: float, rank: int):
+def make_inputs(workload: int, scale: float, rank: int, reads: int = 0):
     t = time.time()
     ref, rd, params = synth.workload(workload, scale)
+    if reads and reads < rd.n:   # a subset of the batch (profiling captures only)
+        rd = rd.subset(np.arange(reads))
     if rank:
         # weak scaling: every rank seeds its own batch of the same size
         o = rd.n
@@ -213,7 +233,7 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     st = torch.cuda.current_stream()
 
-    ref, rd, params = make_inputs(args.workload, args.scale, rank)
+    ref, rd, params = make_inputs(args.workload, args.scale, rank, args.reads)
     opts = dict(min_len=params["min_len"], min_occ=params["min_occ"], max_occ=params["max_occ"],
                 sa_rate=params["sa_rate"])
     torch.cuda.synchronize()
@@ -301,6 +321,14 @@ def run_gpu(args):
                             "locate": {"ms_per_launch": loc_ms / max(loc_n, 1), "bytes": loc_bytes,
                                        "GBps": loc_bytes / max(loc_ms / max(loc_n, 1), 1e-9) / 1e6}}}
 
+    if not args.no_probe:
+        gc = gather_ceiling()
+        roofline["gather_ceiling"] = gc
+        g = gc.get("random64_chain_GBps", 0)
+        if g and g > 0:
+            roofline["frac_of_chain_ceiling"] = achieved / g
+        log(f"gather ceiling: {gc}")
+
     # end to end through the public API with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -373,6 +401,9 @@ def main():
     ap.add_argument("--ref-step-s", type=float, default=8.0, help="reference arm: seconds per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-probe", action="store_true", help="skip the random-gather ceiling probe")
+    ap.add_argument("--reads", type=int, default=0,
+                    help="seed only the first N reads of the batch (for ncu captures of the full index)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -169,6 +169,43 @@ int mb_seed_batch_noalloc(const mb_index *idx, const uint8_t *seq, const uint64_
 int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_smem, const mb_opts *opts,
               void *stream, uint32_t *hits, uint64_t cap, uint64_t *n_hits);
 
+/* ---------------------------------------------------------------------------------------
+ * Batched form: a reusable seeding plan.
+ * mb_plan_create allocates, once, all device workspace for batches of at most max_reads reads
+ * and max_bases bases yielding at most max_smem SMEMs and max_hits hits.  mb_plan_run enqueues
+ * the whole stage on `stream` (SMEMs by Algorithm 3, the max-occ flag, hit offsets, locate by
+ * Algorithm 2) with no host synchronization and no allocation, so the call can be captured into
+ * a CUDA graph and the graph replayed for new batches written into the same input buffers.
+ * With MB_BATCHED in opts->flags the SMEM kernel takes reads from a device work queue in
+ * order of decreasing length (one persistent launch for reads of very different lengths);
+ * opts->block_size (128, 256 or 512) selects the launch shape.
+ *   seq, off, mate (or NULL): DEVICE pointers, as in mb_seed_batch.
+ * mb_plan_result waits for the stream and returns the plan-owned DEVICE arrays of the last
+ * run (valid until the next run): records as mb_seed_batch writes them, and hits as mb_locate
+ * writes them.  MB_ERR_CAPACITY (with the needed counts in *n_smem / *n_hits) if a limit was
+ * exceeded; nothing beyond the limits was written.
+ * mb_autotune times mb_plan_run on the given batch for every launch shape it supports
+ * (block size x work queue on/off) and writes the fastest into *best (same output for all).
+ */
+typedef struct mb_plan mb_plan;
+int mb_plan_create(const mb_index *idx, const mb_opts *opts, uint32_t max_reads, uint64_t max_bases,
+                   uint64_t max_smem, uint64_t max_hits, mb_plan **out);
+int mb_plan_run(mb_plan *plan, const uint8_t *seq, const uint64_t *off, uint32_t n_reads,
+                const uint8_t *mate, void *stream);
+int mb_plan_result(mb_plan *plan, void *stream, const mb_smem **smem, uint64_t *n_smem,
+                   const uint32_t **hits, uint64_t *n_hits);
+void mb_plan_free(mb_plan *plan);
+/* Copy the last run's records / hits (counts from mb_plan_result) into caller buffers, host or
+ * device; either pointer may be NULL.  MB_ERR_CAPACITY if a buffer is too small. */
+int mb_plan_copy(mb_plan *plan, void *stream, mb_smem *out, uint64_t cap, uint32_t *hits, uint64_t hits_cap);
+/* Capture one mb_plan_run with these inputs into a CUDA graph kept by the plan; mb_plan_replay
+ * launches that graph on `stream` (the inputs are read again from the same device buffers). */
+int mb_plan_capture(mb_plan *plan, const uint8_t *seq, const uint64_t *off, uint32_t n_reads,
+                    const uint8_t *mate);
+int mb_plan_replay(mb_plan *plan, void *stream);
+int mb_autotune(const mb_index *idx, const uint8_t *seq, const uint64_t *off, uint32_t n_reads,
+                const mb_opts *opts, void *stream, mb_opts *best, double *best_ms);
+
 /* Section 2.8 strand rule on the 3-base index: keep[h] = 1 if hit h of an SMEM of read `mate`
  * 1 lies wholly inside the forward C-to-T or the reverse G-to-A copy of the reference (read 2:
  * forward G-to-A or reverse C-to-T), else 0.  All pointers host or device. */

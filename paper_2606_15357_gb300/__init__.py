@@ -74,6 +74,15 @@ def lib():
                 "mb_hit_to_ref": ([P, U64, U64, ctypes.POINTER(I), PU64], I),
                 "mb_strerror": ([I], ctypes.c_char_p),
                 "mb_last_error": ([], ctypes.c_char_p),
+                "mb_seed_batch_noalloc": ([P, P, P, U32, P, OP, P, P, U64, PU64, PU64], I),
+                "mb_plan_create": ([P, OP, U32, U64, U64, U64, PP], I),
+                "mb_plan_run": ([P, P, P, U32, P, P], I),
+                "mb_plan_result": ([P, P, PP, PU64, PP, PU64], I),
+                "mb_plan_free": ([P], None),
+                "mb_plan_copy": ([P, P, P, U64, P, U64], I),
+                "mb_plan_capture": ([P, P, P, U32, P], I),
+                "mb_plan_replay": ([P, P], I),
+                "mb_autotune": ([P, P, P, U32, OP, P, OP, ctypes.POINTER(ctypes.c_double)], I),
                 "mb_profile_enable": ([I], None),
                 "mb_profile_get": ([ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), PU64], I),
                 "mb_profile_reset": ([], None),
@@ -289,3 +298,69 @@ def work_counters() -> dict:
     lib().mb_work_counters(*[ctypes.byref(x) for x in v])
     return dict(zip(("ext_steps", "ext_blocks", "kmer_lookups", "lf_steps", "sa_reads"),
                     (x.value for x in v)))
+
+
+# ---------------------------------------------------------------------------- batched form
+class Plan:
+    """A reusable seeding plan (mb_plan_*): fixed device workspace, no host synchronization
+    inside a run, capturable into a CUDA graph."""
+
+    def __init__(self, index: Index, max_reads: int, max_bases: int, max_smem: int, max_hits: int,
+                 opts=None):
+        self.index = index
+        self.opts = _opts(opts)
+        h = ctypes.c_void_p()
+        _check(lib().mb_plan_create(index.handle, ctypes.byref(self.opts), max_reads, max_bases,
+                                    max_smem, max_hits, ctypes.byref(h)), "mb_plan_create")
+        self._h = h
+
+    def run(self, seq, off, mate=None, stream=None):
+        n = (off.numel() if hasattr(off, "numel") else len(off)) - 1
+        _check(lib().mb_plan_run(self._h, _ptr(seq), _ptr(off), n, _ptr(mate), _stream(stream)),
+               "mb_plan_run")
+
+    def capture(self, seq, off, mate=None):
+        n = (off.numel() if hasattr(off, "numel") else len(off)) - 1
+        _check(lib().mb_plan_capture(self._h, _ptr(seq), _ptr(off), n, _ptr(mate)), "mb_plan_capture")
+
+    def replay(self, stream=None):
+        _check(lib().mb_plan_replay(self._h, _stream(stream)), "mb_plan_replay")
+
+    def result_ptrs(self, stream=None):
+        """(smem device ptr, n_smem, hits device ptr, n_hits); raises on capacity overflow."""
+        sp, hp = ctypes.c_void_p(), ctypes.c_void_p()
+        ns, nh = ctypes.c_uint64(), ctypes.c_uint64()
+        rc = lib().mb_plan_result(self._h, _stream(stream), ctypes.byref(sp), ctypes.byref(ns),
+                                  ctypes.byref(hp), ctypes.byref(nh))
+        _check(rc, "mb_plan_result")
+        return sp.value, ns.value, hp.value, nh.value
+
+    def result(self, stream=None):
+        """Records and hits of the last run as host numpy arrays."""
+        sp, ns, hp, nh = self.result_ptrs(stream)
+        sm = np.empty(max(ns, 1), dtype=SMEM_DTYPE)
+        hits = np.empty(max(nh, 1), dtype=np.uint32)
+        _check(lib().mb_plan_copy(self._h, _stream(stream), _ptr(sm), ns, _ptr(hits), nh), "mb_plan_copy")
+        return sm[:ns], hits[:nh]
+
+    def free(self):
+        if getattr(self, "_h", None):
+            lib().mb_plan_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def autotune(index: Index, seq, off, opts=None, stream=None):
+    """Fastest launch shape on this batch: (Opts, ms)."""
+    o = _opts(opts)
+    best = Opts()
+    ms = ctypes.c_double()
+    n = (off.numel() if hasattr(off, "numel") else len(off)) - 1
+    _check(lib().mb_autotune(index.handle, _ptr(seq), _ptr(off), n, ctypes.byref(o), _stream(stream),
+                             ctypes.byref(best), ctypes.byref(ms)), "mb_autotune")
+    return best, ms.value

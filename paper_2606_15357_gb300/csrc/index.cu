@@ -496,6 +496,15 @@ extern "C" int mb_index_build(const uint8_t *ref, uint64_t len, const mb_opts *o
         if (cudaGetLastError() != cudaSuccess) { rc = MB_ERR_CUDA; break; }
         if (cudaStreamSynchronize(st) != cudaSuccess) { rc = MB_ERR_CUDA; break; }
     } while (0);
+    {
+        // give the build's temporaries (tens of GB at 1 Gbp) back to the device
+        cudaStreamSynchronize(st);
+        int dev = 0;
+        cudaMemPool_t pool;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess)
+            cudaMemPoolTrimTo(pool, 0);
+        cudaGetLastError();
+    }
     if (rc != MB_OK) {
         cudaStreamSynchronize(st);
         free_index(X);

@@ -99,8 +99,9 @@ __device__ __forceinline__ bool kmer_code(const SmemState &S, int j, u32 K, u32 
 // a failing k-mer P[x, x+K) restarts the scan at x+1, no further than Algorithm 3's own restart
 // (every window starting at or before x contains that k-mer, so none is a match); in stage 3 the
 // restart point must be exact, so a failing k-mer falls back to single steps.
-template <bool KMER, class Emit, class W>
-__device__ __forceinline__ bool smem_advance(SmemState &S, const DevIndex &I, u32 l, u32 c, Emit &emit, W &work) {
+template <class Emit, class W>
+__device__ __forceinline__ bool smem_advance(SmemState &S, const DevIndex &I, u32 l, u32 c, bool kmer, Emit &emit,
+                                             W &work) {
     const u32 n = (u32)I.n, K = I.kmer_k;
     for (;;) {
         if (S.u == 2) {
@@ -118,7 +119,7 @@ __device__ __forceinline__ bool smem_advance(SmemState &S, const DevIndex &I, u3
                 continue;
             }
             u32 code;
-            if (KMER && l >= K && S.s == n && kmer_code(S, S.j, K, code)) {
+            if (kmer && l >= K && S.s == n && kmer_code(S, S.j, K, code)) {
                 const u32 *e = I.kmer + 3 * (u64)code;
                 u32 tk = __ldg(e), tkr = __ldg(e + 1), ts = __ldg(e + 2);
                 work.kmer += 1;
@@ -147,7 +148,7 @@ __device__ __forceinline__ bool smem_advance(SmemState &S, const DevIndex &I, u3
                 continue;
             }
             u32 code;
-            if (KMER && !S.tried && S.s == n && S.j - (int)K + 1 > S.i && kmer_code(S, S.j, K, code)) {
+            if (kmer && !S.tried && S.s == n && S.j - (int)K + 1 > S.i && kmer_code(S, S.j, K, code)) {
                 S.tried = true;
                 const u32 *e = I.kmer + 3 * (u64)code;
                 u32 tk = __ldg(e), tkr = __ldg(e + 1), ts = __ldg(e + 2);
@@ -215,12 +216,12 @@ __device__ __forceinline__ void smem_extend(const SmemState &S, const DevIndex &
 }
 
 // Algorithm 3 for one read, start to end (used by the overflow pass).
-template <bool KMER, class Emit, class W>
+template <class Emit, class W>
 __device__ __forceinline__ void smem_read(const DevIndex &I, const u8 *__restrict__ P, int L, u32 l, u32 c, u32 conv,
-                                          Emit &emit, W &work) {
+                                          bool kmer, Emit &emit, W &work) {
     SmemState S;
     smem_begin(S, P, L, conv, l, (u32)I.n);
-    while (smem_advance<KMER>(S, I, l, c, emit, work)) {
+    while (smem_advance(S, I, l, c, kmer, emit, work)) {
         u32 nk, nkr, ns;
         smem_extend(S, I, nk, nkr, ns, work);
         if (!smem_apply(S, nk, nkr, ns, l, c, (u32)I.n, emit)) break;
@@ -259,11 +260,36 @@ struct WarpRange {
 };
 
 // One lane keeps one read in flight; each loop iteration performs at most one extension per lane.
-template <bool COUNT, bool KMER>
-__global__ void __launch_bounds__(256, 4) k_smem(DevIndex I, const u8 *__restrict__ seq, const u64 *__restrict__ off,
-                                              u32 nr, const u8 *__restrict__ mate, u32 bs, u32 l, u32 c,
-                                              SlotRec *__restrict__ slots, u64 *__restrict__ counts,
-                                              u32 *__restrict__ ovf_list, u32 *__restrict__ ovf_n, u64 *wc) {
+// QUEUE = false: reads are dealt out in warp ranges (WarpRange).  QUEUE = true: warps take the
+// next reads from a device work queue (perm[*qhead ...], an atomic head), so long and short reads
+// balance across the whole GPU in one launch.  A read whose slots would pass slot_total writes
+// none (it is recomputed by the overflow pass).
+struct SmemArgs {
+    DevIndex I;
+    const u8 *seq;
+    const u64 *off;
+    u32 nr;
+    const u8 *mate;
+    u32 bs, l, c;
+    bool kmer;
+    SlotRec *slots;
+    u64 slot_total;
+    u64 *counts;
+    u32 *ovf_list, *ovf_n;
+    const u32 *perm;
+    u32 *qhead;
+    u64 *wc;
+};
+
+template <bool COUNT, bool QUEUE, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_smem(DevIndex I, const u8 *__restrict__ seq,
+                                                               const u64 *__restrict__ off, u32 nr,
+                                                               const u8 *__restrict__ mate, u32 bs, u32 l, u32 c,
+                                                               bool kmer,
+                                                               SlotRec *__restrict__ slots, u64 slot_total,
+                                                               u64 *__restrict__ counts, u32 *__restrict__ ovf_list,
+                                                               u32 *__restrict__ ovf_n, const u32 *__restrict__ perm,
+                                                               u32 *qhead, u64 *wc) {
     const u32 lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
     const u32 n = (u32)I.n;
     const u64 o0 = off[0];
@@ -271,27 +297,44 @@ __global__ void __launch_bounds__(256, 4) k_smem(DevIndex I, const u8 *__restric
     SmemState S;
     SlotEmit em;
     WarpRange wr;
-    wr.init(nr);
+    if (!QUEUE) wr.init(nr);
     auto start = [&](u64 rr) {
         const u64 b = off[rr], e = off[rr + 1];
         const u64 sb = (b - o0) / 32 + 4 * rr, se = (e - o0) / 32 + 4 * (rr + 1);
         em.slots = slots;
         em.base = sb;
-        em.cap = (u32)(se - sb);
+        em.cap = se <= slot_total ? (u32)(se - sb) : 0u;
         em.cnt = 0;
         smem_begin(S, seq + b, (int)(e - b), conv_of(mate, rr, bs), l, n);
     };
-    u64 r = wr.next + lane;
-    bool live = r < wr.end;
-    wr.next += 32;
-    if (live) start(r);
+    // next `k` items of this warp's work; lane gets item base + rank
+    auto take = [&](u32 k, u32 rank, u64 &item, bool &ok) {
+        if (QUEUE) {
+            u32 base = 0;
+            if (lane == 0) base = atomicAdd(qhead, k);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            item = (u64)base + rank;
+            ok = item < nr;
+        } else {
+            item = wr.next + rank;
+            ok = item < wr.end;
+            wr.next += k;
+        }
+    };
+    u64 item, r = 0;
+    bool live;
+    take(32, lane, item, live);
+    if (live) {
+        r = QUEUE ? perm[item] : item;
+        start(r);
+    }
     for (;;) {
         if (__all_sync(0xffffffffu, !live)) break;
         // phase 1 (divergent, no block reads): move through stage changes up to the next extension
         bool need = false;
         u32 p = 0, q = 0, ss = 0, sym = 4;
         if (live) {
-            need = smem_advance<KMER>(S, I, l, c, em, work);
+            need = smem_advance(S, I, l, c, kmer, em, work);
             if (need) {
                 const u32 a = read_base(S.P, (u64)S.j, S.conv);
                 const bool fwd = S.u == 2;   // ForwardExt((k,kr,s), a) = BackwardExt((kr,k,s), comp a)
@@ -325,19 +368,24 @@ __global__ void __launch_bounds__(256, 4) k_smem(DevIndex I, const u8 *__restric
         }
         const u32 fm = __ballot_sync(0xffffffffu, fin);
         if (fm) {
+            u64 it2;
+            bool ok2;
+            take(__popc(fm), __popc(fm & lt), it2, ok2);
             if (fin) {
-                r = wr.next + __popc(fm & lt);
-                live = r < wr.end;
-                if (live) start(r);
+                live = ok2;
+                if (live) {
+                    r = QUEUE ? perm[it2] : it2;
+                    start(r);
+                }
             }
-            wr.next += __popc(fm);
         }
     }
     work.flush(wc);
 }
 
 __device__ __forceinline__ void write_rec(mb_smem *out, u64 *hitc, u64 m, u32 r, u32 qbeg, u32 qend, u64 k, u64 kr,
-                                          u64 s, u32 max_occ) {
+                                          u64 s, u32 max_occ, u64 cap) {
+    if (m >= cap) return;   // past the caller's capacity (reported, not written)
     mb_smem x;
     x.read = r;
     x.qbeg = qbeg;
@@ -351,45 +399,50 @@ __device__ __forceinline__ void write_rec(mb_smem *out, u64 *hitc, u64 m, u32 r,
     hitc[m] = s > max_occ ? 0 : s;
 }
 
-__global__ void k_gather(const u64 *__restrict__ off, u32 nr, const SlotRec *__restrict__ slots,
+// Copies each read's SMEMs from its slots to the records; reads with more SMEMs than slots (or
+// whose slots lie past slot_total) are skipped here and recomputed by k_smem_overflow.
+__global__ void k_gather(const u64 *__restrict__ off, u32 nr, const SlotRec *__restrict__ slots, u64 slot_total,
                          const u64 *__restrict__ counts, const u64 *__restrict__ soff, u32 max_occ,
-                         mb_smem *__restrict__ out, u64 *__restrict__ hitc) {
+                         mb_smem *__restrict__ out, u64 *__restrict__ hitc, u64 out_cap) {
     u64 r = blockIdx.x * (u64)blockDim.x + threadIdx.x;
     if (r >= nr) return;
-    u64 sb = slot_base(off, r), cap = slot_base(off, r + 1) - sb, cnt = counts[r];
-    if (cnt > cap) return;   // recomputed by k_smem_overflow
-    u64 o = soff[r];
+    const u64 sb = slot_base(off, r), se = slot_base(off, r + 1), cnt = counts[r];
+    if (se > slot_total || cnt > se - sb) return;
+    const u64 o = soff[r];
     for (u64 t = 0; t < cnt; ++t) {
         SlotRec x = slots[sb + t];
-        write_rec(out, hitc, o + t, (u32)r, x.qbeg, x.qend, x.k, x.kr, x.s, max_occ);
+        write_rec(out, hitc, o + t, (u32)r, x.qbeg, x.qend, x.k, x.kr, x.s, max_occ, out_cap);
     }
 }
 
 struct FinalEmit {
     mb_smem *out;
     u64 *hitc;
-    u64 o;
+    u64 o, cap;
     u32 r, max_occ;
     __device__ __forceinline__ void operator()(int i, int j, u32 k, u32 kr, u32 s) {
-        write_rec(out, hitc, o++, r, (u32)i, (u32)j, k, kr, s, max_occ);
+        write_rec(out, hitc, o++, r, (u32)i, (u32)j, k, kr, s, max_occ, cap);
     }
 };
 
-template <bool KMER>
 __global__ void k_smem_overflow(DevIndex I, const u8 *__restrict__ seq, const u64 *__restrict__ off,
-                                const u8 *__restrict__ mate, u32 bs, u32 l, u32 c, const u32 *__restrict__ ovf_list,
+                                const u8 *__restrict__ mate, u32 bs, u32 l, u32 c, bool kmer,
+                                const u32 *__restrict__ ovf_list,
                                 const u32 *__restrict__ ovf_n, const u64 *__restrict__ soff, u32 max_occ,
-                                mb_smem *__restrict__ out, u64 *__restrict__ hitc) {
+                                mb_smem *__restrict__ out, u64 *__restrict__ hitc, u64 cap) {
     u32 n = *ovf_n;
     for (u32 q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
         u32 r = ovf_list[q];
-        FinalEmit em{out, hitc, soff[r], r, max_occ};
+        FinalEmit em{out, hitc, soff[r], cap, r, max_occ};
         Work<false> work;
-        smem_read<KMER>(I, seq + off[r], (int)(off[r + 1] - off[r]), l, c, conv_of(mate, r, bs), em, work);
+        smem_read(I, seq + off[r], (int)(off[r + 1] - off[r]), l, c, conv_of(mate, r, bs), kmer, em, work);
     }
 }
 
-__global__ void k_set_hitoff(const u64 *__restrict__ hoff, u64 m, mb_smem *__restrict__ out) {
+// m records, or min(*mdev, m) when mdev is given (count known only on the device)
+__global__ void k_set_hitoff(const u64 *__restrict__ hoff, u64 m, const u64 *__restrict__ mdev,
+                             mb_smem *__restrict__ out) {
+    if (mdev && *mdev < m) m = *mdev;
     for (u64 t = blockIdx.x * (u64)blockDim.x + threadIdx.x; t < m; t += (u64)gridDim.x * blockDim.x)
         out[t].hit_off = hoff[t];
 }
@@ -413,8 +466,10 @@ __device__ __forceinline__ u64 hits_of(const mb_smem *__restrict__ sm, u64 m) {
 
 // rows[hit_off + t] = k + t for the hits of every record without MB_SMEM_OVER_MAX_OCC: one warp
 // per 32 records, writing each record's rows with the whole warp.
-__global__ void k_expand_rows(const mb_smem *__restrict__ sm, u64 nsm, u32 *__restrict__ rows) {
+__global__ void k_expand_rows(const mb_smem *__restrict__ sm, u64 nsm, const u64 *__restrict__ nsm_dev,
+                              u32 *__restrict__ rows, u64 rows_cap) {
     const u32 lane = threadIdx.x & 31;
+    if (nsm_dev && *nsm_dev < nsm) nsm = *nsm_dev;
     const u64 nw = ((u64)gridDim.x * blockDim.x) >> 5;
     for (u64 base = ((blockIdx.x * (u64)blockDim.x + threadIdx.x) >> 5) * 32; base < nsm; base += nw * 32) {
         u64 m = base + lane;
@@ -428,7 +483,7 @@ __global__ void k_expand_rows(const mb_smem *__restrict__ sm, u64 nsm, u32 *__re
         for (int q = 0; q < 32; ++q) {
             const u64 hq = __shfl_sync(0xffffffffu, ho, q), cq = __shfl_sync(0xffffffffu, cnt, q);
             const u32 kq = __shfl_sync(0xffffffffu, k, q);
-            for (u64 t = lane; t < cq; t += 32) rows[hq + t] = kq + (u32)t;
+            for (u64 t = lane; t < cq && hq + t < rows_cap; t += 32) rows[hq + t] = kq + (u32)t;
         }
     }
 }
@@ -441,8 +496,9 @@ __global__ void k_expand_rows(const mb_smem *__restrict__ sm, u64 nsm, u32 *__re
 // than n steps; the bound only guards against a corrupted index (it then writes 0xFFFFFFFF).
 template <bool COUNT, bool POW2>
 __global__ void __launch_bounds__(256) k_locate(DevIndex I, const u32 *__restrict__ rows, u64 nhits,
-                                                u32 *__restrict__ hits, u64 *wc) {
+                                                const u64 *__restrict__ nhits_dev, u32 *__restrict__ hits, u64 *wc) {
     const u32 lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+    if (nhits_dev && *nhits_dev < nhits) nhits = *nhits_dev;
     Work<COUNT> work;
     const u32 r = I.r, rmask = I.r - 1, rshift = __ffs(I.r) - 1, prim = (u32)I.primary, n = (u32)I.n;
     const u32 C0 = (u32)I.C[0], C1 = (u32)I.C[1], C2 = (u32)I.C[2], C3 = (u32)I.C[3];
@@ -535,10 +591,27 @@ unsigned resident_grid(const void *kernel, int block, u64 work_items) {
     return (unsigned)(g ? g : 1);
 }
 
-unsigned smem_grid(u32 n_reads, bool count, bool kmer) {
-    const void *k = count ? (kmer ? (const void *)k_smem<true, true> : (const void *)k_smem<true, false>)
-                          : (kmer ? (const void *)k_smem<false, true> : (const void *)k_smem<false, false>);
-    return resident_grid(k, 256, n_reads);
+template <bool COUNT, bool QUEUE, int BLOCK>
+int launch_smem_t(const SmemArgs &a, cudaStream_t st) {
+    const unsigned g = resident_grid((const void *)k_smem<COUNT, QUEUE, BLOCK>, BLOCK, a.nr);
+    k_smem<COUNT, QUEUE, BLOCK><<<g, BLOCK, 0, st>>>(a.I, a.seq, a.off, a.nr, a.mate, a.bs, a.l, a.c, a.kmer, a.slots,
+                                                     a.slot_total, a.counts, a.ovf_list, a.ovf_n, a.perm, a.qhead,
+                                                     a.wc);
+    MB_KCHECK();
+    return MB_OK;
+}
+
+// The SMEM kernel in the requested shape: work counters, work queue, threads per block.
+int launch_smem(const SmemArgs &a, bool count, bool queue, int block, cudaStream_t st) {
+    if (count) return launch_smem_t<true, false, 256>(a, st);
+    if (queue) {
+        if (block == 128) return launch_smem_t<false, true, 128>(a, st);
+        if (block == 512) return launch_smem_t<false, true, 512>(a, st);
+        return launch_smem_t<false, true, 256>(a, st);
+    }
+    if (block == 128) return launch_smem_t<false, false, 128>(a, st);
+    if (block == 512) return launch_smem_t<false, false, 512>(a, st);
+    return launch_smem_t<false, false, 256>(a, st);
 }
 
 }  // namespace
@@ -598,27 +671,12 @@ extern "C" int mb_seed_batch(const mb_index *idx, const uint8_t *seq, const uint
     const bool kmer = !(flags & MB_NO_KMER) && l >= mb_dev_index(idx).kmer_k;
     {
         const bool count = (flags & MB_COUNT) != 0;
-        u64 *wc = count ? mb_work_counter_buf(st) : nullptr;
-        const unsigned Gs = smem_grid(n_reads, count, kmer);
+        SmemArgs sa{I, (const u8 *)dseq, (const u64 *)doff, n_reads, (const u8 *)dmate, bs, l, c, kmer,
+                    bslots.as<SlotRec>(), nslots, bcounts.as<u64>(), bovf.as<u32>(), dovf_n, nullptr, nullptr,
+                    count ? mb_work_counter_buf(st) : nullptr};
         kt.start();
-        if (count && kmer)
-            k_smem<true, true><<<Gs, B, 0, st>>>(I, (const u8 *)dseq, (const u64 *)doff, n_reads, (const u8 *)dmate,
-                                                 bs, l, c, bslots.as<SlotRec>(), bcounts.as<u64>(), bovf.as<u32>(),
-                                                 dovf_n, wc);
-        else if (count)
-            k_smem<true, false><<<Gs, B, 0, st>>>(I, (const u8 *)dseq, (const u64 *)doff, n_reads,
-                                                  (const u8 *)dmate, bs, l, c, bslots.as<SlotRec>(),
-                                                  bcounts.as<u64>(), bovf.as<u32>(), dovf_n, wc);
-        else if (kmer)
-            k_smem<false, true><<<Gs, B, 0, st>>>(I, (const u8 *)dseq, (const u64 *)doff, n_reads,
-                                                  (const u8 *)dmate, bs, l, c, bslots.as<SlotRec>(),
-                                                  bcounts.as<u64>(), bovf.as<u32>(), dovf_n, nullptr);
-        else
-            k_smem<false, false><<<Gs, B, 0, st>>>(I, (const u8 *)dseq, (const u64 *)doff, n_reads,
-                                                   (const u8 *)dmate, bs, l, c, bslots.as<SlotRec>(),
-                                                   bcounts.as<u64>(), bovf.as<u32>(), dovf_n, nullptr);
+        MB_TRY(launch_smem(sa, count, false, 256, st));
         kt.stop();
-        MB_KCHECK();
     }
     MB_TRY(btmp.alloc(scan_tmp_bytes(n_reads), st));
     MB_TRY(scan_exclusive_u64(bcounts.as<u64>(), bsoff.as<u64>(), n_reads, dtotal, btmp.p, st));
@@ -641,21 +699,16 @@ extern "C" int mb_seed_batch(const mb_index *idx, const uint8_t *seq, const uint
         dout = bout.as<mb_smem>();
     }
     MB_TRY(bhitc.alloc(total * 8, st));
-    k_gather<<<G, B, 0, st>>>((const u64 *)doff, n_reads, bslots.as<SlotRec>(), bcounts.as<u64>(), bsoff.as<u64>(),
-                              max_occ, dout, bhitc.as<u64>());
+    k_gather<<<G, B, 0, st>>>((const u64 *)doff, n_reads, bslots.as<SlotRec>(), nslots, bcounts.as<u64>(),
+                              bsoff.as<u64>(), max_occ, dout, bhitc.as<u64>(), total);
     MB_KCHECK();
-    if (kmer)
-        k_smem_overflow<true><<<152, 128, 0, st>>>(I, (const u8 *)dseq, (const u64 *)doff, (const u8 *)dmate, bs, l,
-                                                   c, bovf.as<u32>(), dovf_n, bsoff.as<u64>(), max_occ, dout,
-                                                   bhitc.as<u64>());
-    else
-        k_smem_overflow<false><<<152, 128, 0, st>>>(I, (const u8 *)dseq, (const u64 *)doff, (const u8 *)dmate, bs,
-                                                    l, c, bovf.as<u32>(), dovf_n, bsoff.as<u64>(), max_occ, dout,
-                                                    bhitc.as<u64>());
+    k_smem_overflow<<<152, 128, 0, st>>>(I, (const u8 *)dseq, (const u64 *)doff, (const u8 *)dmate, bs, l, c, kmer,
+                                         bovf.as<u32>(), dovf_n, bsoff.as<u64>(), max_occ, dout, bhitc.as<u64>(),
+                                         total);
     MB_KCHECK();
     MB_TRY(bhtmp.alloc(scan_tmp_bytes(total), st));
     MB_TRY(scan_exclusive_u64(bhitc.as<u64>(), bhitc.as<u64>(), total, dhtotal, bhtmp.p, st));
-    k_set_hitoff<<<grid_for(total, 256), 256, 0, st>>>(bhitc.as<u64>(), total, dout);
+    k_set_hitoff<<<grid_for(total, 256), 256, 0, st>>>(bhitc.as<u64>(), total, nullptr, dout);
     MB_KCHECK();
     u64 ht = 0;
     MB_CK(cudaMemcpyAsync(&ht, dhtotal, 8, cudaMemcpyDeviceToHost, st));
@@ -696,7 +749,8 @@ extern "C" int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_sm
     const bool pow2 = (I.r & (I.r - 1)) == 0;
     DevBuf brows;
     MB_TRY(brows.alloc(total * 4, st));
-    k_expand_rows<<<grid_for(n_smem, 256), 256, 0, st>>>((const mb_smem *)dsm, n_smem, brows.as<u32>());
+    k_expand_rows<<<grid_for(n_smem, 256), 256, 0, st>>>((const mb_smem *)dsm, n_smem, nullptr, brows.as<u32>(),
+                                                         total);
     MB_KCHECK();
     const void *kfn = count ? (pow2 ? (const void *)k_locate<true, true> : (const void *)k_locate<true, false>)
                             : (pow2 ? (const void *)k_locate<false, true> : (const void *)k_locate<false, false>);
@@ -704,10 +758,10 @@ extern "C" int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_sm
     u64 *wc = count ? mb_work_counter_buf(st) : nullptr;
     KTimer kt("locate", st);
     kt.start();
-    if (count && pow2) k_locate<true, true><<<G, 256, 0, st>>>(I, brows.as<u32>(), total, dh, wc);
-    else if (count) k_locate<true, false><<<G, 256, 0, st>>>(I, brows.as<u32>(), total, dh, wc);
-    else if (pow2) k_locate<false, true><<<G, 256, 0, st>>>(I, brows.as<u32>(), total, dh, nullptr);
-    else k_locate<false, false><<<G, 256, 0, st>>>(I, brows.as<u32>(), total, dh, nullptr);
+    if (count && pow2) k_locate<true, true><<<G, 256, 0, st>>>(I, brows.as<u32>(), total, nullptr, dh, wc);
+    else if (count) k_locate<true, false><<<G, 256, 0, st>>>(I, brows.as<u32>(), total, nullptr, dh, wc);
+    else if (pow2) k_locate<false, true><<<G, 256, 0, st>>>(I, brows.as<u32>(), total, nullptr, dh, nullptr);
+    else k_locate<false, false><<<G, 256, 0, st>>>(I, brows.as<u32>(), total, nullptr, dh, nullptr);
     kt.stop();
     MB_KCHECK();
     if (!hdev) MB_CK(cudaMemcpyAsync(hits, dh, total * 4, cudaMemcpyDeviceToHost, st));
@@ -848,13 +902,11 @@ extern "C" int mb_seed_batch_noalloc(const mb_index *idx, const uint8_t *seq, co
     const DevIndex I = mb_dev_index(idx);
     const unsigned B = 256, G = (unsigned)((nr + B - 1) / B);
     const bool kmer = !(flags & MB_NO_KMER) && l >= I.kmer_k;
-    if (kmer)
-        k_smem<false, true><<<smem_grid(n_reads, false, true), B, 0, st>>>(I, seq, off, n_reads, mate, bs, l, c,
-                                                                          slots, counts, ovf, dovf_n, nullptr);
-    else
-        k_smem<false, false><<<smem_grid(n_reads, false, false), B, 0, st>>>(I, seq, off, n_reads, mate, bs, l, c,
-                                                                            slots, counts, ovf, dovf_n, nullptr);
-    MB_KCHECK();
+    {
+        SmemArgs sa{I, seq, off, n_reads, mate, bs, l, c, kmer, slots, nslots, counts, ovf, dovf_n, nullptr, nullptr,
+                    nullptr};
+        MB_TRY(launch_smem(sa, false, false, 256, st));
+    }
     MB_TRY(scan_exclusive_u64(counts, soff, nr, dtotal, S + o_tmp, st));
     u64 total = 0;
     MB_CK(cudaMemcpyAsync(&total, dtotal, 8, cudaMemcpyDeviceToHost, st));
@@ -872,20 +924,271 @@ extern "C" int mb_seed_batch_noalloc(const mb_index *idx, const uint8_t *seq, co
         return MB_ERR_ARG;
     }
     u64 *hitc = (u64 *)(S + o_hitc);
-    k_gather<<<G, B, 0, st>>>(off, n_reads, slots, counts, soff, max_occ, out, hitc);
+    k_gather<<<G, B, 0, st>>>(off, n_reads, slots, nslots, counts, soff, max_occ, out, hitc, total);
     MB_KCHECK();
-    if (kmer)
-        k_smem_overflow<true><<<152, 128, 0, st>>>(I, seq, off, mate, bs, l, c, ovf, dovf_n, soff, max_occ, out, hitc);
-    else
-        k_smem_overflow<false><<<152, 128, 0, st>>>(I, seq, off, mate, bs, l, c, ovf, dovf_n, soff, max_occ, out,
-                                                    hitc);
+    k_smem_overflow<<<152, 128, 0, st>>>(I, seq, off, mate, bs, l, c, kmer, ovf, dovf_n, soff, max_occ, out, hitc,
+                                         total);
     MB_KCHECK();
     MB_TRY(scan_exclusive_u64(hitc, hitc, total, dhtotal, S + o_htmp, st));
-    k_set_hitoff<<<grid_for(total, 256), 256, 0, st>>>(hitc, total, out);
+    k_set_hitoff<<<grid_for(total, 256), 256, 0, st>>>(hitc, total, nullptr, out);
     MB_KCHECK();
     u64 ht = 0;
     MB_CK(cudaMemcpyAsync(&ht, dhtotal, 8, cudaMemcpyDeviceToHost, st));
     MB_CK(cudaStreamSynchronize(st));
     if (n_hits) *n_hits = ht;
+    return MB_OK;
+}
+
+// ============================================================================ batched form: plans
+namespace {
+// lengths as sort keys, longest first (key = 2^32 - 1 - length), values = read ids
+__global__ void k_len_keys(const u64 *__restrict__ off, u32 nr, u64 *__restrict__ keys, u32 *__restrict__ ids) {
+    for (u64 r = blockIdx.x * (u64)blockDim.x + threadIdx.x; r < nr; r += (u64)gridDim.x * blockDim.x) {
+        const u64 len = off[r + 1] - off[r];
+        keys[r] = 0xFFFFFFFFull - (len < 0xFFFFFFFFull ? len : 0xFFFFFFFFull);
+        ids[r] = (u32)r;
+    }
+}
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+}  // namespace
+
+struct mb_plan {
+    const mb_index *idx = nullptr;
+    u32 l = 19, c = 1, max_occ = 500, flags = 0;
+    bool kmer = true, queue = false;
+    int block = 256;
+    u32 max_reads = 0;
+    u64 max_bases = 0, max_smem = 0, max_hits = 0, nslots = 0;
+    void *mem = nullptr;
+    SlotRec *slots = nullptr;
+    u64 *counts = nullptr, *soff = nullptr, *misc = nullptr, *hitc = nullptr;
+    u32 *ovf = nullptr, *rows = nullptr, *hits = nullptr;
+    mb_smem *out = nullptr;
+    u64 *skeys = nullptr, *skeys_alt = nullptr;
+    u32 *perm = nullptr, *perm_alt = nullptr;
+    void *tmp = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" int mb_plan_create(const mb_index *idx, const mb_opts *opts, uint32_t max_reads, uint64_t max_bases,
+                              uint64_t max_smem, uint64_t max_hits, mb_plan **out) {
+    if (!idx || !out || max_reads == 0) return MB_ERR_ARG;
+    *out = nullptr;
+    mb_plan *P = new mb_plan;
+    P->idx = idx;
+    opts_defaults(opts, P->l, P->c, P->max_occ, P->flags);
+    P->kmer = !(P->flags & MB_NO_KMER) && P->l >= mb_dev_index(idx).kmer_k;
+    P->queue = (P->flags & MB_BATCHED) != 0;
+    P->block = opts && (opts->block_size == 128 || opts->block_size == 512) ? (int)opts->block_size : 256;
+    P->max_reads = max_reads;
+    P->max_bases = max_bases;
+    P->max_smem = max_smem ? max_smem : 1;
+    P->max_hits = max_hits ? max_hits : 1;
+    P->nslots = max_bases / 32 + 4ULL * max_reads + 4;
+    const size_t nr = max_reads;
+    size_t tb = scan_tmp_bytes(nr > P->max_smem ? nr : P->max_smem);
+    const size_t rb = radix_tmp_bytes(nr);
+    if (rb > tb) tb = rb;
+    size_t sizes[] = {P->nslots * sizeof(SlotRec), nr * 8, nr * 8, 256, P->max_smem * 8, nr * 4, P->max_hits * 4,
+                      P->max_hits * 4, P->max_smem * sizeof(mb_smem), P->queue ? nr * 8 : 0, P->queue ? nr * 8 : 0,
+                      P->queue ? nr * 4 : 0, P->queue ? nr * 4 : 0, tb};
+    size_t total = 0;
+    for (size_t z : sizes) total += align_up(z);
+    if (cudaMalloc(&P->mem, total) != cudaSuccess) {
+        cudaGetLastError();
+        delete P;
+        mb_set_error("mb_plan_create: cannot allocate %zu bytes of device workspace", total);
+        return MB_ERR_NOMEM;
+    }
+    char *m = (char *)P->mem;
+    void **ptrs[] = {(void **)&P->slots, (void **)&P->counts, (void **)&P->soff, (void **)&P->misc, (void **)&P->hitc,
+                     (void **)&P->ovf, (void **)&P->rows, (void **)&P->hits, (void **)&P->out, (void **)&P->skeys,
+                     (void **)&P->skeys_alt, (void **)&P->perm, (void **)&P->perm_alt, (void **)&P->tmp};
+    for (size_t i = 0; i < sizeof(sizes) / sizeof(sizes[0]); ++i) {
+        *ptrs[i] = sizes[i] ? (void *)m : nullptr;
+        m += align_up(sizes[i]);
+    }
+    *out = P;
+    return MB_OK;
+}
+
+extern "C" void mb_plan_free(mb_plan *P) {
+    if (!P) return;
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    if (P->graph) cudaGraphDestroy(P->graph);
+    if (P->mem) cudaFree(P->mem);
+    delete P;
+}
+
+// The whole stage on `stream`, with no host synchronization and no allocation.
+extern "C" int mb_plan_run(mb_plan *P, const uint8_t *seq, const uint64_t *off, uint32_t n_reads, const uint8_t *mate,
+                           void *stream) {
+    if (!P || (n_reads && (!seq || !off))) return MB_ERR_ARG;
+    if (n_reads > P->max_reads) {
+        mb_set_error("mb_plan_run: %u reads exceed the plan's %u", n_reads, P->max_reads);
+        return MB_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    MB_CK(cudaMemsetAsync(P->misc, 0, 256, st));
+    if (n_reads == 0) return MB_OK;
+    const DevIndex I = mb_dev_index(P->idx);
+    const u32 bs = (P->flags & MB_BS3) ? 1u : 0u;
+    u64 *n_smem = P->misc, *n_hits = P->misc + 1;
+    u32 *ovf_n = (u32 *)(P->misc + 2), *qhead = (u32 *)(P->misc + 3);
+    MB_CK(cudaMemsetAsync(P->hitc, 0, P->max_smem * 8, st));   // zero tail for the fixed-length scan
+    const u32 *perm = nullptr;
+    if (P->queue) {   // work queue in order of decreasing read length
+        k_len_keys<<<grid_for(n_reads, 256), 256, 0, st>>>(off, n_reads, P->skeys, P->perm);
+        MB_KCHECK();
+        BitRange r0[1] = {{0, 32}};
+        MB_TRY(radix_sort_pairs(P->skeys, P->perm, P->skeys_alt, P->perm_alt, n_reads, r0, 1, P->tmp, st));
+        perm = P->perm;
+    }
+    SmemArgs sa{I, seq, off, n_reads, mate, bs, P->l, P->c, P->kmer, P->slots, P->nslots, P->counts, P->ovf, ovf_n,
+                perm, qhead, nullptr};
+    MB_TRY(launch_smem(sa, false, P->queue, P->block, st));
+    MB_TRY(scan_exclusive_u64(P->counts, P->soff, n_reads, n_smem, P->tmp, st));
+    const unsigned G = (unsigned)((n_reads + 255) / 256);
+    k_gather<<<G, 256, 0, st>>>(off, n_reads, P->slots, P->nslots, P->counts, P->soff, P->max_occ, P->out, P->hitc,
+                                P->max_smem);
+    MB_KCHECK();
+    k_smem_overflow<<<152, 128, 0, st>>>(I, seq, off, mate, bs, P->l, P->c, P->kmer, P->ovf, ovf_n, P->soff,
+                                         P->max_occ, P->out, P->hitc, P->max_smem);
+    MB_KCHECK();
+    MB_TRY(scan_exclusive_u64(P->hitc, P->hitc, P->max_smem, n_hits, P->tmp, st));
+    k_set_hitoff<<<grid_for(P->max_smem, 256), 256, 0, st>>>(P->hitc, P->max_smem, n_smem, P->out);
+    MB_KCHECK();
+    k_expand_rows<<<grid_for(P->max_smem, 256), 256, 0, st>>>(P->out, P->max_smem, n_smem, P->rows, P->max_hits);
+    MB_KCHECK();
+    const bool pow2 = (I.r & (I.r - 1)) == 0;
+    const void *kfn = pow2 ? (const void *)k_locate<false, true> : (const void *)k_locate<false, false>;
+    const unsigned GL = resident_grid(kfn, 256, (P->max_hits + 63) / 64 * 32);
+    if (pow2) k_locate<false, true><<<GL, 256, 0, st>>>(I, P->rows, P->max_hits, n_hits, P->hits, nullptr);
+    else k_locate<false, false><<<GL, 256, 0, st>>>(I, P->rows, P->max_hits, n_hits, P->hits, nullptr);
+    MB_KCHECK();
+    return MB_OK;
+}
+
+extern "C" int mb_plan_result(mb_plan *P, void *stream, const mb_smem **smem, uint64_t *n_smem, const uint32_t **hits,
+                              uint64_t *n_hits) {
+    if (!P) return MB_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    u64 v[2] = {0, 0};
+    MB_CK(cudaMemcpyAsync(v, P->misc, 16, cudaMemcpyDeviceToHost, st));
+    MB_CK(cudaStreamSynchronize(st));
+    if (n_smem) *n_smem = v[0];
+    if (n_hits) *n_hits = v[1];
+    if (smem) *smem = P->out;
+    if (hits) *hits = P->hits;
+    if (v[0] > P->max_smem || v[1] > P->max_hits) {
+        mb_set_error("mb_plan_result: %llu SMEMs / %llu hits exceed the plan's %llu / %llu",
+                     (unsigned long long)v[0], (unsigned long long)v[1], (unsigned long long)P->max_smem,
+                     (unsigned long long)P->max_hits);
+        return MB_ERR_CAPACITY;
+    }
+    return MB_OK;
+}
+
+extern "C" int mb_plan_copy(mb_plan *P, void *stream, mb_smem *out, uint64_t cap, uint32_t *hits, uint64_t hits_cap) {
+    if (!P) return MB_ERR_ARG;
+    u64 ns = 0, nh = 0;
+    const mb_smem *sp = nullptr;
+    const uint32_t *hp = nullptr;
+    MB_TRY(mb_plan_result(P, stream, &sp, &ns, &hp, &nh));
+    if ((out && ns > cap) || (hits && nh > hits_cap)) return MB_ERR_CAPACITY;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (out && ns) MB_CK(cudaMemcpyAsync(out, sp, ns * sizeof(mb_smem), cudaMemcpyDefault, st));
+    if (hits && nh) MB_CK(cudaMemcpyAsync(hits, hp, nh * 4, cudaMemcpyDefault, st));
+    MB_CK(cudaStreamSynchronize(st));
+    return MB_OK;
+}
+
+extern "C" int mb_plan_capture(mb_plan *P, const uint8_t *seq, const uint64_t *off, uint32_t n_reads,
+                               const uint8_t *mate) {
+    if (!P) return MB_ERR_ARG;
+    cudaStream_t s;
+    MB_CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    if (P->exec) { cudaGraphExecDestroy(P->exec); P->exec = nullptr; }
+    if (P->graph) { cudaGraphDestroy(P->graph); P->graph = nullptr; }
+    int rc = MB_OK;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = MB_ERR_CUDA;
+    else {
+        rc = mb_plan_run(P, seq, off, n_reads, mate, s);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(s, &g);
+        if (rc == MB_OK && e != cudaSuccess) rc = MB_ERR_CUDA;
+        if (rc == MB_OK && cudaGraphInstantiate(&P->exec, g, 0) != cudaSuccess) rc = MB_ERR_CUDA;
+        if (rc == MB_OK) P->graph = g;
+        else if (g) cudaGraphDestroy(g);
+    }
+    cudaStreamDestroy(s);
+    if (rc != MB_OK) mb_set_error("mb_plan_capture: graph capture failed");
+    return rc;
+}
+
+extern "C" int mb_plan_replay(mb_plan *P, void *stream) {
+    if (!P || !P->exec) return MB_ERR_ARG;
+    MB_CK(cudaGraphLaunch(P->exec, (cudaStream_t)stream));
+    mb_count_launch();
+    return MB_OK;
+}
+
+// Times every launch shape on this batch; all give the same output (tests check that).
+extern "C" int mb_autotune(const mb_index *idx, const uint8_t *seq, const uint64_t *off, uint32_t n_reads,
+                           const mb_opts *opts, void *stream, mb_opts *best, double *best_ms) {
+    if (!idx || !best || !seq || !off || n_reads == 0) return MB_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    // sizes from one run of the allocating path
+    u64 n_smem = 0, n_hits = 0;
+    {
+        mb_opts o = opts ? *opts : mb_opts{};
+        DevBuf tmp;
+        int rc = mb_seed_batch(idx, seq, off, n_reads, nullptr, &o, stream, nullptr, 0, &n_smem, &n_hits);
+        if (rc != MB_OK && rc != MB_ERR_CAPACITY) return rc;
+        MB_TRY(tmp.alloc(n_smem * sizeof(mb_smem) + 64, st));
+        MB_TRY(mb_seed_batch(idx, seq, off, n_reads, nullptr, &o, stream, tmp.as<mb_smem>(), n_smem, &n_smem,
+                             &n_hits));
+    }
+    u64 o0 = 0, o1 = 0;
+    MB_CK(cudaMemcpyAsync(&o0, off, 8, cudaMemcpyDefault, st));
+    MB_CK(cudaMemcpyAsync(&o1, off + n_reads, 8, cudaMemcpyDefault, st));
+    MB_CK(cudaStreamSynchronize(st));
+    const int blocks[3] = {128, 256, 512};
+    double bms = 1e30;
+    mb_opts bo = opts ? *opts : mb_opts{};
+    cudaEvent_t a, b;
+    MB_CK(cudaEventCreate(&a));
+    MB_CK(cudaEventCreate(&b));
+    int rc = MB_OK;
+    for (int q = 0; q < 2 && rc == MB_OK; ++q)
+        for (int bi = 0; bi < 3 && rc == MB_OK; ++bi) {
+            mb_opts o = opts ? *opts : mb_opts{};
+            o.flags = (o.flags & ~MB_BATCHED) | (q ? MB_BATCHED : 0u);
+            o.block_size = (u32)blocks[bi];
+            mb_plan *P = nullptr;
+            rc = mb_plan_create(idx, &o, n_reads, o1 - o0, n_smem, n_hits, &P);
+            if (rc != MB_OK) break;
+            double t_best = 1e30;
+            for (int rep = 0; rep < 3 && rc == MB_OK; ++rep) {
+                cudaEventRecord(a, st);
+                rc = mb_plan_run(P, seq, off, n_reads, nullptr, st);
+                cudaEventRecord(b, st);
+                if (cudaEventSynchronize(b) != cudaSuccess) rc = MB_ERR_CUDA;
+                float ms = 0;
+                cudaEventElapsedTime(&ms, a, b);
+                if (rep > 0 && ms < t_best) t_best = ms;   // first run warms up
+            }
+            mb_plan_free(P);
+            if (rc == MB_OK && t_best < bms) {
+                bms = t_best;
+                bo = o;
+            }
+        }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (rc != MB_OK) return rc;
+    *best = bo;
+    if (best_ms) *best_ms = bms;
     return MB_OK;
 }

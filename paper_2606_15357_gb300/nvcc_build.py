@@ -12,6 +12,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 SO = os.path.join(OUT_DIR, "libminibwa_gpu.so")
+PROBE_SRC = os.path.join(HERE, "probe", "gather.cu")
+PROBE_SO = os.path.join(OUT_DIR, "libmb_probe.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -40,8 +42,21 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
+def build_probe(force: bool = False) -> str:
+    """The random-gather probe used by bench.py (a separate library, not part of the C ABI)."""
+    if not force and os.path.exists(PROBE_SO) and os.path.getmtime(PROBE_SO) >= os.path.getmtime(PROBE_SRC):
+        return PROBE_SO
+    os.makedirs(OUT_DIR, exist_ok=True)
+    tmp = PROBE_SO + f".{os.getpid()}.tmp"
+    subprocess.check_call([nvcc()] + ARCH + ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+                                             PROBE_SRC, "-o", tmp])
+    os.replace(tmp, PROBE_SO)
+    return PROBE_SO
+
+
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
     if not force and up_to_date():
+        build_probe()
         return SO
     os.makedirs(OUT_DIR, exist_ok=True)
     procs = []
@@ -65,6 +80,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     tmp = SO + f".{os.getpid()}.tmp"
     subprocess.check_call([nvcc()] + ARCH + ["-shared", "-o", tmp] + objs)
     os.replace(tmp, SO)
+    build_probe(force)
     return SO
 
 
