@@ -219,6 +219,160 @@ def run_reference(args):
     return 0
 
 
+# --------------------------------------------------------------------------------- batched / served
+def bench_batched(mb, torch, dev, reps: int = 3):
+    """Mixed-length workload (100 Mbp repeat-rich reference, 200,000 reads of 100 bp-10 kb):
+    one plain mb_seed_batch + mb_locate launch per length bucket, against the batched form
+    (autotuned plan, device work queue, replayed CUDA graph).  Output compared for identity."""
+    ref, rd, params = synth.workload(4)
+    G = mb.mb_index_build(torch.from_numpy(ref).to(dev))
+    G.drop_sa()
+    lens = np.diff(rd.off.astype(np.int64))
+    edges = [100 * 2 ** i for i in range(8)] + [10001]
+    buckets = []
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        ids = np.nonzero((lens >= lo) & (lens < hi))[0]
+        if len(ids):
+            sub = rd.subset(ids)
+            buckets.append((ids, torch.from_numpy(sub.seq).to(dev),
+                            torch.from_numpy(sub.off.view(np.int64)).to(dev)))
+    outs = []
+    for ids, s, o in buckets:   # sizes
+        _, m, nh = mb.mb_seed_batch(G, s, o, out=torch.empty(8 * len(ids) * 64 * 48, dtype=torch.uint8, device=dev),
+                                    cap=8 * len(ids) * 64)
+        outs.append((torch.empty(max(m, 1) * 48, dtype=torch.uint8, device=dev), m,
+                     torch.empty(max(nh, 1), dtype=torch.int32, device=dev), nh))
+
+    def plain():
+        for (ids, s, o), (ob, m, hb, nh) in zip(buckets, outs):
+            _, m2, nh2 = mb.mb_seed_batch(G, s, o, out=ob, cap=m)
+            mb.mb_locate(G, ob, m2, hits=hb, cap=nh2)
+
+    plain()
+    torch.cuda.synchronize()
+    t = time.time()
+    for _ in range(reps):
+        plain()
+    torch.cuda.synchronize()
+    plain_s = (time.time() - t) / reps
+    seq, off = torch.from_numpy(rd.seq).to(dev), torch.from_numpy(rd.off.view(np.int64)).to(dev)
+    best, tune_ms = mb.autotune(G, seq, off)
+    n_smem = sum(x[1] for x in outs)
+    n_hits = sum(x[3] for x in outs)
+    P = mb.Plan(G, rd.n, len(rd.seq), n_smem + 64, n_hits + 64, opts=best)
+    P.capture(seq, off)
+    P.replay()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        P.replay()
+    e1.record(st)
+    torch.cuda.synchronize()
+    batched_s = e0.elapsed_time(e1) / 1000 / reps
+    bsm, bhits = P.result()
+    # identity with the per-bucket launches, put back in read order
+    rec, hl = [], []
+    for (ids, s, o), (ob, m, hb, nh) in zip(buckets, outs):
+        x = ob[:m * 48].cpu().numpy().view(mb.SMEM_DTYPE)
+        h = hb[:nh].cpu().numpy().view(np.uint32)
+        for r in x:
+            c = 0 if r["flags"] & 1 else int(r["s"])
+            rec.append((int(ids[r["read"]]), int(r["qbeg"]), int(r["qend"]), int(r["k"]), int(r["kr"]), int(r["s"])))
+            hl.append(h[int(r["hit_off"]):int(r["hit_off"]) + c])
+    order = sorted(range(len(rec)), key=lambda i: (rec[i][0], rec[i][1]))
+    same = [rec[i] for i in order] == [tuple(int(v) for v in (r["read"], r["qbeg"], r["qend"], r["k"], r["kr"],
+                                                                 r["s"])) for r in bsm]
+    same = same and np.array_equal(np.concatenate([hl[i] for i in order]), bhits)
+    return {"workload": "100 Mbp repeat-rich reference, 200,000 SE reads log-uniform 100 bp-10 kb",
+            "reads": rd.n, "bases": int(len(rd.seq)), "smems": n_smem, "hits": n_hits,
+            "plain_per_bucket_reads_per_s": rd.n / plain_s, "batched_graph_reads_per_s": rd.n / batched_s,
+            "speedup": plain_s / batched_s, "identical_output": bool(same),
+            "autotuned": {"block_size": best.block_size, "work_queue": bool(best.flags & mb.MB_BATCHED)},
+            "plain_ms": plain_s * 1000, "batched_ms": batched_s * 1000}
+
+
+def serve_requests(ref, n, seed):
+    """Request stream: 80% short (log-uniform 1-4,096 pairs of 2x150), 20% long (log-uniform
+    1-4,096 single reads of log-uniform 1-10 kb)."""
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for q in range(n):
+        k = int(np.exp(rng.uniform(0, np.log(4096))))
+        if rng.random() < 0.8:
+            rd = synth.reads(ref, 2 * k, seed * 7919 + q, mode=1, read_len=150, sub_lo=0.001, sub_hi=0.01,
+                             indel=0.0001)
+        else:
+            rd = synth.reads(ref, k, seed * 7919 + q, mode=2, len_lo=1000, len_hi=10000, sub_lo=0.001,
+                             indel=0.0002)
+        reqs.append(rd)
+    return reqs
+
+
+def bench_served(mb, G, ref, n_requests: int, load: float = 0.7):
+    """Served form on the resident index: capacity (all requests at once), then Poisson arrivals at
+    `load` x capacity; latency per request from submit to results on the host.  The same arrivals
+    served by sequential plain launches (one request at a time) for comparison."""
+    import threading as th
+    reqs = serve_requests(ref, n_requests, 4242)
+    total_reads = sum(r.n for r in reqs)
+    srv = mb.Server(G, hbm_budget=8 << 30)
+    t = time.time()
+    tickets = [srv.submit(r.seq, r.off) for r in reqs]
+    for tk in tickets:
+        srv.wait(tk)
+    cap_s = time.time() - t
+    cap_rps = n_requests / cap_s
+    rate = load * cap_rps
+    gaps = np.random.default_rng(17).exponential(1.0 / rate, n_requests)
+    arrivals = np.cumsum(gaps)
+    lat = [0.0] * n_requests
+    tk = [0] * n_requests
+    done_ev = th.Event()
+
+    def collect():
+        for i in range(n_requests):
+            while tk[i] == 0:
+                time.sleep(0.0002)
+            _, _, lat[i] = srv.wait(tk[i])
+        done_ev.set()
+
+    col = th.Thread(target=collect)
+    col.start()
+    t0 = time.time()
+    for i, r in enumerate(reqs):
+        d = t0 + arrivals[i] - time.time()
+        if d > 0:
+            time.sleep(d)
+        tk[i] = srv.submit(r.seq, r.off)
+    col.join()
+    wall = time.time() - t0
+    stats = srv.stats()
+    srv.close()
+    # sequential plain launches on the same arrival times
+    seq_lat = []
+    t0 = time.time()
+    for i, r in enumerate(reqs):
+        d = t0 + arrivals[i] - time.time()
+        if d > 0:
+            time.sleep(d)
+        mb.seed(G, r.seq, r.off)
+        seq_lat.append((time.time() - t0 - arrivals[i]) * 1000)
+    seq_wall = time.time() - t0
+    q = lambda a, p: float(np.percentile(np.asarray(a), p))
+    return {"requests": n_requests, "reads": total_reads,
+            "mix": "80% short (1-4,096 pairs of 2x150), 20% long (1-4,096 reads of 1-10 kb), log-uniform sizes",
+            "capacity_requests_per_s": cap_rps, "capacity_reads_per_s": total_reads / cap_s,
+            "offered_load": load, "arrival_rate_per_s": rate,
+            "served_reads_per_s": total_reads / wall,
+            "served_p50_ms": q(lat, 50), "served_p95_ms": q(lat, 95), "served_p99_ms": q(lat, 99),
+            "sequential_plain_reads_per_s": total_reads / seq_wall,
+            "sequential_plain_p50_ms": q(seq_lat, 50), "sequential_plain_p95_ms": q(seq_lat, 95),
+            "sequential_plain_p99_ms": q(seq_lat, 99),
+            "slots": stats["slots"], "launch_groups": stats["groups"], "merged_requests": stats["merged"]}
+
+
 # --------------------------------------------------------------------------------- GPU side
 def run_gpu(args):
     import torch
@@ -272,6 +426,12 @@ def run_gpu(args):
     wc = mb.work_counters()
     log(f"work: {m} SMEMs, {nh} hits, {wc}")
 
+    # autotune the launch shape on a sample of the batch, then use it for both forms
+    ns = min(n_reads, 1_000_000)
+    best, tune_ms = mb.autotune(idx, seq[:int(rd.off[ns])], off[:ns + 1], opts=opts)
+    opts["block_size"] = best.block_size
+    log(f"autotuned on {ns} reads: block {best.block_size}, work queue {bool(best.flags & mb.MB_BATCHED)}")
+
     for _ in range(args.warmup):
         step()
     mb.profile_reset()
@@ -281,17 +441,47 @@ def run_gpu(args):
         pg.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    mb.profile_enable(False)
+    plain_ms = e0.elapsed_time(e1)
+    plain_launches = mb.launch_count() - l0
+
+    # the same stage as one captured CUDA graph of an autotuned plan (no host sync inside a step)
+    popts = dict(opts, flags=best.flags)
+    P = mb.Plan(idx, n_reads, len(rd.seq), m + 1024, nh + 1024, opts=popts)
+    P.capture(seq, off)
+    for _ in range(args.warmup):
+        P.replay()
+    _, gm, _, gnh = P.result_ptrs()
+    assert (gm, gnh) == (m, nh), "graph form disagrees with the plain launches"
+    psm, phits = P.result()
+    same = psm.tobytes() == out[:m * 48].cpu().numpy().tobytes() and \
+        np.array_equal(phits, hits[:nh].cpu().numpy().view(np.uint32))
+    l1 = mb.launch_count()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         e0.record(st)
         for _ in range(args.steps):
-            step()
+            P.replay()
         e1.record(st)
         torch.cuda.synchronize()
     if pg:
         pg.barrier()
-    mb.profile_enable(False)
-    launches = mb.launch_count() - l0
-    ms = e0.elapsed_time(e1)
+    graph_ms = e0.elapsed_time(e1)
+    graph_launches = mb.launch_count() - l1
+    del psm, phits
+    P.free()
+    use_graph = same and graph_ms < plain_ms
+    ms = graph_ms if use_graph else plain_ms
+    launches = graph_launches if use_graph else plain_launches
     if pg:
         tt = torch.tensor([ms], dtype=torch.float64)
         pg.all_reduce(tt, op=pg.ReduceOp.MAX)
@@ -299,8 +489,15 @@ def run_gpu(args):
     value = ws * args.steps * n_reads / (ms / 1000.0)
     smem_ms, smem_n = mb.profile_get("smem")
     loc_ms, loc_n = mb.profile_get("locate")
-    log(f"timed: {ms / args.steps:.1f} ms/step; smem {smem_ms / max(smem_n, 1):.1f} ms, "
-        f"locate {loc_ms / max(loc_n, 1):.1f} ms per launch")
+    log(f"timed: plain {plain_ms / args.steps:.1f} ms/step, graph {graph_ms / args.steps:.1f} ms/step "
+        f"(identical: {same}); smem {smem_ms / max(smem_n, 1):.1f} ms, locate {loc_ms / max(loc_n, 1):.1f} ms per launch")
+    forms = {"plain_launch": {"reads_per_s": ws * args.steps * n_reads / (plain_ms / 1000.0),
+                              "ms_per_step": plain_ms / args.steps, "gpu_launches": plain_launches},
+             "graph_plan": {"reads_per_s": ws * args.steps * n_reads / (graph_ms / 1000.0),
+                            "ms_per_step": graph_ms / args.steps, "identical_output": bool(same),
+                            "gpu_launches_note": "one graph launch per step; counted as the kernels it holds",
+                            "block_size": best.block_size, "work_queue": bool(best.flags & mb.MB_BATCHED)},
+             "reported": "graph_plan" if use_graph else "plain_launch"}
 
     # roofline of the dominant kernel: algorithmic bytes / its event-timed duration
     peak, peak_kind = measured_peaks()
@@ -322,7 +519,7 @@ def run_gpu(args):
                                        "GBps": loc_bytes / max(loc_ms / max(loc_n, 1), 1e-9) / 1e6}}}
 
     if not args.no_probe:
-        gc = gather_ceiling()
+        gc = gather_ceiling(args.probe_gib)
         roofline["gather_ceiling"] = gc
         g = gc.get("random64_chain_GBps", 0)
         if g and g > 0:
@@ -352,6 +549,17 @@ def run_gpu(args):
                "h2d_bytes_per_step": int(seq_h.numel() + off_h.numel() * 8 + m * 48),
                "d2h_bytes_per_step": int(m * 48 + nh * 4),
                "note": "host pinned buffers; the locate call re-stages the SMEM records"}
+
+    served = None
+    if rank == 0 and not args.no_serve:
+        served = bench_served(mb, idx, ref, args.serve_requests)
+        log(f"served: {served}")
+    del out, hits
+    torch.cuda.empty_cache()
+    batched = None
+    if rank == 0 and not args.no_batched:
+        batched = bench_batched(mb, torch, dev)
+        log(f"batched: {batched}")
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -383,6 +591,9 @@ def run_gpu(args):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
+        "forms": forms,
+        "batched": batched,
+        "served": served,
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
@@ -402,6 +613,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-probe", action="store_true", help="skip the random-gather ceiling probe")
+    ap.add_argument("--no-batched", action="store_true", help="skip the mixed-length batched comparison")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served-form measurement")
+    ap.add_argument("--serve-requests", type=int, default=600)
+    ap.add_argument("--probe-gib", type=int, default=1, help="buffer of the random-gather probe (GiB)")
     ap.add_argument("--reads", type=int, default=0,
                     help="seed only the first N reads of the batch (for ncu captures of the full index)")
     args = ap.parse_args()

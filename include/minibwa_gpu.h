@@ -206,6 +206,37 @@ int mb_plan_replay(mb_plan *plan, void *stream);
 int mb_autotune(const mb_index *idx, const uint8_t *seq, const uint64_t *off, uint32_t n_reads,
                 const mb_opts *opts, void *stream, mb_opts *best, double *best_ms);
 
+/* ---------------------------------------------------------------------------------------
+ * Served form: continuous batching of seeding requests on one GPU.
+ * mb_serve_create starts a worker thread.  It preallocates as many execution slots (a stream
+ * and a seeding plan for up to 65,536 reads / 64M bases / 2M SMEMs / 32M hits each) as fit in
+ * hbm_budget bytes of device memory (at least one).  Requests wait in arrival order; whenever
+ * a slot is free, every waiting request that still fits the slot's limits is merged into one
+ * launch group, so requests arriving while others are on the GPU are admitted as soon as a slot
+ * frees, and groups run concurrently on their own streams.  Each request's results are exactly
+ * those of mb_seed_batch + mb_locate on that request alone (read numbers and hit offsets are
+ * relative to the request).
+ *   mb_serve_submit  copies the request (host buffers) and returns a ticket at once.
+ *                    MB_ERR_ARG if the request alone exceeds a slot's limits.
+ *   mb_serve_poll    *done = 1 when the ticket's results are ready.
+ *   mb_serve_wait    waits up to timeout_ms (0 = no limit; MB_ERR_TIMEOUT after it) and returns
+ *                    server-owned host arrays valid until mb_serve_release(ticket), plus the
+ *                    request's latency from submit to results ready, in ms.
+ *   mb_serve_destroy finishes every request already submitted, then stops and frees the server;
+ *                    no call may use the server afterwards.
+ */
+int mb_serve_create(const mb_index *idx, const mb_opts *opts, uint64_t hbm_budget, mb_server **out);
+int mb_serve_submit(mb_server *srv, const uint8_t *seq, const uint64_t *off, uint32_t n_reads,
+                    uint64_t *ticket);
+int mb_serve_poll(mb_server *srv, uint64_t ticket, int *done);
+int mb_serve_wait(mb_server *srv, uint64_t ticket, uint32_t timeout_ms, const mb_smem **smem,
+                  uint64_t *n_smem, const uint32_t **hits, uint64_t *n_hits, double *latency_ms);
+int mb_serve_release(mb_server *srv, uint64_t ticket);
+int mb_serve_destroy(mb_server *srv);
+/* slots = execution slots created; groups = launch groups run; merged = requests that shared a
+ * group with another request (the continuous-batching count). */
+int mb_serve_stats(mb_server *srv, uint32_t *slots, uint64_t *groups, uint64_t *merged);
+
 /* Section 2.8 strand rule on the 3-base index: keep[h] = 1 if hit h of an SMEM of read `mate`
  * 1 lies wholly inside the forward C-to-T or the reverse G-to-A copy of the reference (read 2:
  * forward G-to-A or reverse C-to-T), else 0.  All pointers host or device. */

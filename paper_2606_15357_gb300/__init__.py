@@ -83,6 +83,13 @@ def lib():
                 "mb_plan_capture": ([P, P, P, U32, P], I),
                 "mb_plan_replay": ([P, P], I),
                 "mb_autotune": ([P, P, P, U32, OP, P, OP, ctypes.POINTER(ctypes.c_double)], I),
+                "mb_serve_create": ([P, OP, U64, PP], I),
+                "mb_serve_submit": ([P, P, P, U32, PU64], I),
+                "mb_serve_poll": ([P, U64, ctypes.POINTER(I)], I),
+                "mb_serve_wait": ([P, U64, U32, PP, PU64, PP, PU64, ctypes.POINTER(ctypes.c_double)], I),
+                "mb_serve_release": ([P, U64], I),
+                "mb_serve_destroy": ([P], I),
+                "mb_serve_stats": ([P, ctypes.POINTER(U32), PU64, PU64], I),
                 "mb_profile_enable": ([I], None),
                 "mb_profile_get": ([ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), PU64], I),
                 "mb_profile_reset": ([], None),
@@ -364,3 +371,62 @@ def autotune(index: Index, seq, off, opts=None, stream=None):
     _check(lib().mb_autotune(index.handle, _ptr(seq), _ptr(off), n, ctypes.byref(o), _stream(stream),
                              ctypes.byref(best), ctypes.byref(ms)), "mb_autotune")
     return best, ms.value
+
+
+# ---------------------------------------------------------------------------- served form
+class Server:
+    """Continuous-batching seeding server (mb_serve_*): submit host read batches, get tickets."""
+
+    def __init__(self, index: Index, hbm_budget: int = 4 << 30, opts=None):
+        self.index = index
+        self.opts = _opts(opts)
+        h = ctypes.c_void_p()
+        _check(lib().mb_serve_create(index.handle, ctypes.byref(self.opts), hbm_budget, ctypes.byref(h)),
+               "mb_serve_create")
+        self._h = h
+
+    def submit(self, seq: np.ndarray, off: np.ndarray) -> int:
+        seq = np.ascontiguousarray(seq, dtype=np.uint8)
+        off = np.ascontiguousarray(off, dtype=np.uint64)
+        t = ctypes.c_uint64()
+        _check(lib().mb_serve_submit(self._h, _ptr(seq), _ptr(off), len(off) - 1, ctypes.byref(t)),
+               "mb_serve_submit")
+        return t.value
+
+    def poll(self, ticket: int) -> bool:
+        d = ctypes.c_int()
+        _check(lib().mb_serve_poll(self._h, ticket, ctypes.byref(d)), "mb_serve_poll")
+        return bool(d.value)
+
+    def wait(self, ticket: int, timeout_ms: int = 0, release: bool = True):
+        """(records, hits, latency_ms) as host numpy arrays (copied)."""
+        sp, hp = ctypes.c_void_p(), ctypes.c_void_p()
+        ns, nh, lat = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_double()
+        _check(lib().mb_serve_wait(self._h, ticket, timeout_ms, ctypes.byref(sp), ctypes.byref(ns),
+                                   ctypes.byref(hp), ctypes.byref(nh), ctypes.byref(lat)), "mb_serve_wait")
+        sm = np.empty(ns.value, dtype=SMEM_DTYPE)
+        hits = np.empty(nh.value, dtype=np.uint32)
+        if ns.value:
+            ctypes.memmove(sm.ctypes.data, sp.value, ns.value * 48)
+        if nh.value:
+            ctypes.memmove(hits.ctypes.data, hp.value, nh.value * 4)
+        if release:
+            _check(lib().mb_serve_release(self._h, ticket), "mb_serve_release")
+        return sm, hits, lat.value
+
+    def stats(self):
+        sl, g, m = ctypes.c_uint32(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib().mb_serve_stats(self._h, ctypes.byref(sl), ctypes.byref(g), ctypes.byref(m)),
+               "mb_serve_stats")
+        return dict(slots=sl.value, groups=g.value, merged=m.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(lib().mb_serve_destroy(self._h), "mb_serve_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

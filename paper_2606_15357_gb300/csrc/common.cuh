@@ -244,6 +244,12 @@ size_t radix_tmp_bytes(size_t n);
 int radix_sort_pairs(u64 *keys, u32 *vals, u64 *keys_alt, u32 *vals_alt, size_t n, const BitRange *ranges,
                      int nranges, void *tmp, cudaStream_t st);
 
+// plan internals used by the server: device bytes of a plan, asynchronous copy of its two
+// result counts (n_smem, n_hits) to host memory, and its device result arrays
+size_t mb_plan_bytes(const mb_plan *p);
+int mb_plan_counts_async(mb_plan *p, u64 *host_counts, cudaStream_t st);
+void mb_plan_arrays(const mb_plan *p, const mb_smem **smem, const u32 **hits, u64 *max_smem, u64 *max_hits);
+
 inline unsigned grid_for(size_t n, unsigned block, unsigned cap = 152u * 64u) {
     size_t g = (n + block - 1) / block;
     if (g > cap) g = cap;

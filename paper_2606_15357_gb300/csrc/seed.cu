@@ -12,6 +12,7 @@
 // (off[r]/32 + 4r slots before it), a prefix sum over the per-read counts gives the final
 // positions, and a gather writes the 48-byte records.  Reads with more SMEMs than slots are
 // listed and recomputed straight into the final records.
+#include <climits>
 #include "common.cuh"
 
 DevIndex mb_dev_index(const mb_index *x);
@@ -59,6 +60,9 @@ struct Work {
 // so one read's queue operations happen in the serial order kept here.
 struct SmemState {
     const u8 *P;
+    int lim;             // chunk loads must end by P + lim (the end of the batch, capped)
+    int cj;              // P + cj is the 16-byte aligned start of the cached chunk (INT_MIN: none)
+    uint4 chunk;         // the read's bases around the current position
     int L;       // read length
     u32 conv;    // bisulfite conversion (0 none, 1 C->T, 2 G->A)
     int u;       // stage 1, 2, 3; 0 = finished
@@ -67,8 +71,12 @@ struct SmemState {
     bool tried;  // stage 3: the k-mer table was already consulted for this entry
 };
 
-__device__ __forceinline__ void smem_begin(SmemState &S, const u8 *P, int L, u32 conv, u32 l, u32 n) {
+__device__ __forceinline__ void smem_begin(SmemState &S, const u8 *P, int L, u32 conv, u32 l, u32 n,
+                                           const u8 *end) {
     S.P = P;
+    const u64 room = (u64)(end - P);
+    S.lim = room > 0x7FFFFFF0ull ? 0x7FFFFFF0 : (int)room;
+    S.cj = INT_MIN;
     S.L = L;
     S.conv = conv;
     S.u = (int)l - 1 < L ? 1 : 0;   // Algorithm 3 queues a read only if l - 1 < |P|
@@ -78,11 +86,34 @@ __device__ __forceinline__ void smem_begin(SmemState &S, const u8 *P, int L, u32
     S.tried = false;
 }
 
+// Base j of the read through a one-chunk cache: the steps of Algorithm 3 move j by one, so the
+// 16 bytes around j are loaded once per 16 steps instead of one byte per step (a byte load at
+// the end of the batch, where a whole chunk would pass the buffer).
+__device__ __forceinline__ u32 cached_base(SmemState &S, int j) {
+    const int mis = (int)((uintptr_t)S.P & 15);   // P's offset inside its 16-byte chunk
+    const int cj = ((j + mis) & ~15) - mis;       // read index at which j's chunk starts
+    u32 b;
+    if (cj != S.cj && cj + 16 <= S.lim) {
+        S.chunk = __ldg(reinterpret_cast<const uint4 *>(S.P + cj));
+        S.cj = cj;
+    }
+    if (cj == S.cj) {
+        const u32 o = (u32)(j - cj);
+        const u32 w = o < 8 ? (o < 4 ? S.chunk.x : S.chunk.y) : (o < 12 ? S.chunk.z : S.chunk.w);
+        b = (w >> (8 * (o & 3))) & 0xFFu;
+    } else {
+        b = S.P[j];
+    }
+    if (S.conv == 1 && b == 1) b = 3;
+    if (S.conv == 2 && b == 2) b = 0;
+    return b;
+}
+
 // k-mer code of P[j-K+1 .. j] (first base most significant); false if it holds an N
-__device__ __forceinline__ bool kmer_code(const SmemState &S, int j, u32 K, u32 &code) {
+__device__ __forceinline__ bool kmer_code(SmemState &S, int j, u32 K, u32 &code) {
     u32 v = 0;
     for (u32 t = 0; t < K; ++t) {
-        u32 b = read_base(S.P, (u64)(j - (int)K + 1 + (int)t), S.conv);
+        u32 b = cached_base(S, j - (int)K + 1 + (int)t);
         if (b > 3) return false;
         v = (v << 2) | b;
     }
@@ -200,9 +231,9 @@ __device__ __forceinline__ bool smem_apply(SmemState &S, u32 nk, u32 nkr, u32 ns
 // The pending extension of P[j]: BackwardExt((k,kr,s), a) in stages 1/3, ForwardExt in stage 2
 // (= BackwardExt((kr,k,s), comp a)).  An N gives the empty interval without a memory access.
 template <class W>
-__device__ __forceinline__ void smem_extend(const SmemState &S, const DevIndex &I, u32 &nk, u32 &nkr, u32 &ns,
+__device__ __forceinline__ void smem_extend(SmemState &S, const DevIndex &I, u32 &nk, u32 &nkr, u32 &ns,
                                             W &work) {
-    const u32 a = read_base(S.P, (u64)S.j, S.conv);
+    const u32 a = cached_base(S, S.j);
     nk = 0; nkr = 0; ns = 0;
     if (a < 4) {
         const bool fwd = S.u == 2;
@@ -218,9 +249,9 @@ __device__ __forceinline__ void smem_extend(const SmemState &S, const DevIndex &
 // Algorithm 3 for one read, start to end (used by the overflow pass).
 template <class Emit, class W>
 __device__ __forceinline__ void smem_read(const DevIndex &I, const u8 *__restrict__ P, int L, u32 l, u32 c, u32 conv,
-                                          bool kmer, Emit &emit, W &work) {
+                                          bool kmer, const u8 *end, Emit &emit, W &work) {
     SmemState S;
-    smem_begin(S, P, L, conv, l, (u32)I.n);
+    smem_begin(S, P, L, conv, l, (u32)I.n, end);
     while (smem_advance(S, I, l, c, kmer, emit, work)) {
         u32 nk, nkr, ns;
         smem_extend(S, I, nk, nkr, ns, work);
@@ -281,8 +312,10 @@ struct SmemArgs {
     u64 *wc;
 };
 
+// Launch bounds per shape: 128 threads allow 85 registers (6 blocks, 24 warps per SM); 256 and
+// 512 threads cap registers at 64 (32 warps per SM).
 template <bool COUNT, bool QUEUE, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_smem(DevIndex I, const u8 *__restrict__ seq,
+__global__ void __launch_bounds__(BLOCK, BLOCK == 128 ? 6 : 1024 / BLOCK) k_smem(DevIndex I, const u8 *__restrict__ seq,
                                                                const u64 *__restrict__ off, u32 nr,
                                                                const u8 *__restrict__ mate, u32 bs, u32 l, u32 c,
                                                                bool kmer,
@@ -293,6 +326,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_smem(DevIndex I, const 
     const u32 lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
     const u32 n = (u32)I.n;
     const u64 o0 = off[0];
+    const u8 *const end = seq + off[nr];
     Work<COUNT> work;
     SmemState S;
     SlotEmit em;
@@ -305,7 +339,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_smem(DevIndex I, const 
         em.base = sb;
         em.cap = se <= slot_total ? (u32)(se - sb) : 0u;
         em.cnt = 0;
-        smem_begin(S, seq + b, (int)(e - b), conv_of(mate, rr, bs), l, n);
+        smem_begin(S, seq + b, (int)(e - b), conv_of(mate, rr, bs), l, n, end);
     };
     // next `k` items of this warp's work; lane gets item base + rank
     auto take = [&](u32 k, u32 rank, u64 &item, bool &ok) {
@@ -336,7 +370,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_smem(DevIndex I, const 
         if (live) {
             need = smem_advance(S, I, l, c, kmer, em, work);
             if (need) {
-                const u32 a = read_base(S.P, (u64)S.j, S.conv);
+                const u32 a = cached_base(S, S.j);
                 const bool fwd = S.u == 2;   // ForwardExt((k,kr,s), a) = BackwardExt((kr,k,s), comp a)
                 p = fwd ? S.kr : S.k;
                 q = fwd ? S.k : S.kr;
@@ -425,7 +459,7 @@ struct FinalEmit {
     }
 };
 
-__global__ void k_smem_overflow(DevIndex I, const u8 *__restrict__ seq, const u64 *__restrict__ off,
+__global__ void k_smem_overflow(DevIndex I, const u8 *__restrict__ seq, const u64 *__restrict__ off, u32 nr,
                                 const u8 *__restrict__ mate, u32 bs, u32 l, u32 c, bool kmer,
                                 const u32 *__restrict__ ovf_list,
                                 const u32 *__restrict__ ovf_n, const u64 *__restrict__ soff, u32 max_occ,
@@ -435,7 +469,8 @@ __global__ void k_smem_overflow(DevIndex I, const u8 *__restrict__ seq, const u6
         u32 r = ovf_list[q];
         FinalEmit em{out, hitc, soff[r], cap, r, max_occ};
         Work<false> work;
-        smem_read(I, seq + off[r], (int)(off[r + 1] - off[r]), l, c, conv_of(mate, r, bs), kmer, em, work);
+        smem_read(I, seq + off[r], (int)(off[r + 1] - off[r]), l, c, conv_of(mate, r, bs), kmer, seq + off[nr], em,
+                  work);
     }
 }
 
@@ -674,8 +709,9 @@ extern "C" int mb_seed_batch(const mb_index *idx, const uint8_t *seq, const uint
         SmemArgs sa{I, (const u8 *)dseq, (const u64 *)doff, n_reads, (const u8 *)dmate, bs, l, c, kmer,
                     bslots.as<SlotRec>(), nslots, bcounts.as<u64>(), bovf.as<u32>(), dovf_n, nullptr, nullptr,
                     count ? mb_work_counter_buf(st) : nullptr};
+        const int blk = opts && (opts->block_size == 128 || opts->block_size == 512) ? (int)opts->block_size : 256;
         kt.start();
-        MB_TRY(launch_smem(sa, count, false, 256, st));
+        MB_TRY(launch_smem(sa, count, false, blk, st));
         kt.stop();
     }
     MB_TRY(btmp.alloc(scan_tmp_bytes(n_reads), st));
@@ -702,7 +738,8 @@ extern "C" int mb_seed_batch(const mb_index *idx, const uint8_t *seq, const uint
     k_gather<<<G, B, 0, st>>>((const u64 *)doff, n_reads, bslots.as<SlotRec>(), nslots, bcounts.as<u64>(),
                               bsoff.as<u64>(), max_occ, dout, bhitc.as<u64>(), total);
     MB_KCHECK();
-    k_smem_overflow<<<152, 128, 0, st>>>(I, (const u8 *)dseq, (const u64 *)doff, (const u8 *)dmate, bs, l, c, kmer,
+    k_smem_overflow<<<152, 128, 0, st>>>(I, (const u8 *)dseq, (const u64 *)doff, n_reads, (const u8 *)dmate, bs, l,
+                                         c, kmer,
                                          bovf.as<u32>(), dovf_n, bsoff.as<u64>(), max_occ, dout, bhitc.as<u64>(),
                                          total);
     MB_KCHECK();
@@ -926,7 +963,8 @@ extern "C" int mb_seed_batch_noalloc(const mb_index *idx, const uint8_t *seq, co
     u64 *hitc = (u64 *)(S + o_hitc);
     k_gather<<<G, B, 0, st>>>(off, n_reads, slots, nslots, counts, soff, max_occ, out, hitc, total);
     MB_KCHECK();
-    k_smem_overflow<<<152, 128, 0, st>>>(I, seq, off, mate, bs, l, c, kmer, ovf, dovf_n, soff, max_occ, out, hitc,
+    k_smem_overflow<<<152, 128, 0, st>>>(I, seq, off, n_reads, mate, bs, l, c, kmer, ovf, dovf_n, soff, max_occ, out,
+                                         hitc,
                                          total);
     MB_KCHECK();
     MB_TRY(scan_exclusive_u64(hitc, hitc, total, dhtotal, S + o_htmp, st));
@@ -967,9 +1005,22 @@ struct mb_plan {
     u64 *skeys = nullptr, *skeys_alt = nullptr;
     u32 *perm = nullptr, *perm_alt = nullptr;
     void *tmp = nullptr;
+    size_t bytes = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
+
+size_t mb_plan_bytes(const mb_plan *p) { return p ? p->bytes : 0; }
+int mb_plan_counts_async(mb_plan *p, u64 *host_counts, cudaStream_t st) {
+    MB_CK(cudaMemcpyAsync(host_counts, p->misc, 16, cudaMemcpyDeviceToHost, st));
+    return MB_OK;
+}
+void mb_plan_arrays(const mb_plan *p, const mb_smem **smem, const u32 **hits, u64 *max_smem, u64 *max_hits) {
+    *smem = p->out;
+    *hits = p->hits;
+    *max_smem = p->max_smem;
+    *max_hits = p->max_hits;
+}
 
 extern "C" int mb_plan_create(const mb_index *idx, const mb_opts *opts, uint32_t max_reads, uint64_t max_bases,
                               uint64_t max_smem, uint64_t max_hits, mb_plan **out) {
@@ -1001,6 +1052,7 @@ extern "C" int mb_plan_create(const mb_index *idx, const mb_opts *opts, uint32_t
         mb_set_error("mb_plan_create: cannot allocate %zu bytes of device workspace", total);
         return MB_ERR_NOMEM;
     }
+    P->bytes = total;
     char *m = (char *)P->mem;
     void **ptrs[] = {(void **)&P->slots, (void **)&P->counts, (void **)&P->soff, (void **)&P->misc, (void **)&P->hitc,
                      (void **)&P->ovf, (void **)&P->rows, (void **)&P->hits, (void **)&P->out, (void **)&P->skeys,
@@ -1053,7 +1105,7 @@ extern "C" int mb_plan_run(mb_plan *P, const uint8_t *seq, const uint64_t *off, 
     k_gather<<<G, 256, 0, st>>>(off, n_reads, P->slots, P->nslots, P->counts, P->soff, P->max_occ, P->out, P->hitc,
                                 P->max_smem);
     MB_KCHECK();
-    k_smem_overflow<<<152, 128, 0, st>>>(I, seq, off, mate, bs, P->l, P->c, P->kmer, P->ovf, ovf_n, P->soff,
+    k_smem_overflow<<<152, 128, 0, st>>>(I, seq, off, n_reads, mate, bs, P->l, P->c, P->kmer, P->ovf, ovf_n, P->soff,
                                          P->max_occ, P->out, P->hitc, P->max_smem);
     MB_KCHECK();
     MB_TRY(scan_exclusive_u64(P->hitc, P->hitc, P->max_smem, n_hits, P->tmp, st));
