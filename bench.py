@@ -47,6 +47,21 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, pg) -> float:
+    """The largest value of x over all ranks (timing is the slowest rank's); identity at N=1."""
+    if pg is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, steps: int, units_per_rank_step: int, ms: float) -> float:
+    """Weak scaling: every rank processes its own batch of the same size each step."""
+    return world * steps * units_per_rank_step / (ms / 1000.0)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -66,7 +81,7 @@ def gather_ceiling(gib: int = 4):
     L.mb_probe_gather.restype = ctypes.c_double
     out = {}
     ms = ctypes.c_float()
-    for mode, name, iters in ((0, "indep", 2048), (1, "chain", 512)):
+    for mode, name, iters in ((0, "indep", 2048), (1, "chain", 512), (2, "chain_l2only", 512)):
         for bb in (64, 32):
             out[f"random{bb}_{name}_GBps"] = L.mb_probe_gather(gib << 30, mode, bb, iters, ctypes.byref(ms))
     out["buffer_GiB"] = gib
@@ -482,11 +497,8 @@ def run_gpu(args):
     use_graph = same and graph_ms < plain_ms
     ms = graph_ms if use_graph else plain_ms
     launches = graph_launches if use_graph else plain_launches
-    if pg:
-        tt = torch.tensor([ms], dtype=torch.float64)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = ws * args.steps * n_reads / (ms / 1000.0)
+    ms = max_over_ranks(ms, pg)
+    value = whole_job_rate(ws, args.steps, n_reads, ms)
     smem_ms, smem_n = mb.profile_get("smem")
     loc_ms, loc_n = mb.profile_get("locate")
     log(f"timed: plain {plain_ms / args.steps:.1f} ms/step, graph {graph_ms / args.steps:.1f} ms/step "
@@ -495,7 +507,7 @@ def run_gpu(args):
                               "ms_per_step": plain_ms / args.steps, "gpu_launches": plain_launches},
              "graph_plan": {"reads_per_s": ws * args.steps * n_reads / (graph_ms / 1000.0),
                             "ms_per_step": graph_ms / args.steps, "identical_output": bool(same),
-                            "gpu_launches_note": "one graph launch per step; counted as the kernels it holds",
+                            "gpu_launches": graph_launches,
                             "block_size": best.block_size, "work_queue": bool(best.flags & mb.MB_BATCHED)},
              "reported": "graph_plan" if use_graph else "plain_launch"}
 
@@ -541,10 +553,7 @@ def run_gpu(args):
             mb.mb_locate(idx, out_h, m2, opts=opts, hits=hits_h, cap=nh2)
         torch.cuda.synchronize()
         dt = time.time() - t0
-        if pg:
-            tt = torch.tensor([dt], dtype=torch.float64)
-            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-            dt = float(tt.item())
+        dt = max_over_ranks(dt, pg)
         e2e = {"value": ws * k2 * n_reads / dt, "unit": "reads/s",
                "h2d_bytes_per_step": int(seq_h.numel() + off_h.numel() * 8 + m * 48),
                "d2h_bytes_per_step": int(m * 48 + nh * 4),

@@ -55,6 +55,7 @@ enum {
 
 /* Flags of mb_smem.flags */
 #define MB_SMEM_OVER_MAX_OCC 0x1u   /* s > max_occ: reported, not located, no hits */
+#define MB_SMEM_ROUND2       0x2u   /* found by the second seeding round (mb_reseed) */
 
 typedef struct mb_index mb_index;
 typedef struct mb_server mb_server;
@@ -133,6 +134,21 @@ int mb_index_drop_sa(mb_index *idx);
 int mb_seed_batch(const mb_index *idx, const uint8_t *seq, const uint64_t *off, uint32_t n_reads,
                   const uint8_t *mate, const mb_opts *opts, void *stream,
                   mb_smem *out, uint64_t cap, uint64_t *n_out, uint64_t *n_hits);
+
+/* ---------------------------------------------------------------------------------------
+ * mb_reseed — the second seeding round of Section 2.7.  For every record of `smem` (the first
+ * round's (l,c)-SMEMs of the same reads, as mb_seed_batch wrote them) with qend - qbeg >= 2l and
+ * s <= 10 and no MB_SMEM_OVER_MAX_OCC, finds the (floor((qend-qbeg)/2), s+1)-SMEMs of the
+ * substring read[qbeg, qend) (the paper prints the length as floor((j-1)/2); read here as the
+ * window length j - i).  Records are in read coordinates, flagged MB_SMEM_ROUND2, ordered by
+ * their window (the order of `smem`) then by qbeg, with the max-occ flag and hit offsets of
+ * mb_seed_batch (relative to this output; pass it to mb_locate for the hits).
+ *   seq, off, mate: as for mb_seed_batch (host or device).  smem: host or device.
+ *   Capacity and errors as mb_seed_batch.
+ */
+int mb_reseed(const mb_index *idx, const uint8_t *seq, const uint64_t *off, uint32_t n_reads,
+              const uint8_t *mate, const mb_smem *smem, uint64_t n_smem, const mb_opts *opts,
+              void *stream, mb_smem *out, uint64_t cap, uint64_t *n_out, uint64_t *n_hits);
 
 /* ---------------------------------------------------------------------------------------
  * mb_seed_batch_noalloc — mb_seed_batch for callers that cannot allocate device memory.

@@ -239,6 +239,44 @@ class Index:
         return sm, over, hit_off, hits
 
 
+def reseed(X: "Index", seq, off, first, min_len: int = 19, max_s: int = 10, max_occ: int = 500,
+           threads: int = 0):
+    """Section 2.7, second seeding round: for every first-round record with qend - qbeg >= 2l,
+    s <= 10 and s <= max_occ, the (floor((qend - qbeg)/2), s + 1)-SMEMs of read[qbeg, qend) as a
+    query of its own, by the definition (Index.smem).  Returns (records in read coordinates,
+    ordered by window then qbeg; over-max-occ flags; hit offsets; hits)."""
+    seq = _u8(seq)
+    off = _u64(off)
+    wins = [(int(x["read"]), int(x["qbeg"]), int(x["qend"]), int(x["s"])) for x in first
+            if int(x["qend"]) - int(x["qbeg"]) >= 2 * min_len and int(x["s"]) <= max_s
+            and int(x["s"]) <= max_occ]
+    groups = {}
+    for w, (r, b, e, s) in enumerate(wins):
+        groups.setdefault(((e - b) // 2, s + 1), []).append(w)
+    per_win = [[] for _ in wins]
+    for (l2, c2), ws in groups.items():
+        sub = np.concatenate([seq[int(off[wins[w][0]]) + wins[w][1]:int(off[wins[w][0]]) + wins[w][2]]
+                              for w in ws])
+        so = np.zeros(len(ws) + 1, dtype=np.uint64)
+        np.cumsum([wins[w][2] - wins[w][1] for w in ws], out=so[1:])
+        rec = X.smem(sub, so, l2, c2, "def", threads)
+        for x in rec:
+            w = ws[int(x["read"])]
+            per_win[w].append((wins[w][0], int(x["qbeg"]) + wins[w][1], int(x["qend"]) + wins[w][1],
+                               int(x["k"]), int(x["kr"]), int(x["s"])))
+    flat = [t for lst in per_win for t in lst]
+    sm = np.array(flat, dtype=np.uint64).reshape(-1, 6).view(SMEM_DTYPE).reshape(-1) if flat else \
+        np.zeros(0, dtype=SMEM_DTYPE)
+    over = sm["s"] > max_occ
+    cnt = np.where(over, 0, sm["s"]).astype(np.uint64)
+    hoff = np.zeros(len(sm), dtype=np.uint64)
+    if len(sm):
+        np.cumsum(cnt[:-1], out=hoff[1:])
+    rows = np.concatenate([np.arange(int(x["k"]), int(x["k"]) + int(c), dtype=np.uint64)
+                           for x, c in zip(sm, cnt)]) if len(sm) else np.zeros(0, np.uint64)
+    return sm, over, hoff, X.locate(rows, threads)
+
+
 def smem_brute(text: np.ndarray, seq, off, min_len: int = 19, min_occ: int = 1,
                threads: int = 0) -> np.ndarray:
     """(l,c)-SMEMs and their ds-intervals by scanning the text (oracle coding, ends with $)."""

@@ -20,7 +20,7 @@ __all__ = ["SMEM_DTYPE", "Opts", "MbError", "lib", "build", "Index", "mb_index_b
            "mb_index_load", "mb_seed_batch", "mb_locate", "mb_bs_filter", "seed"]
 
 MB_BS3, MB_BATCHED, MB_CHECKED, MB_NO_KMER, MB_COUNT = 0x1, 0x2, 0x4, 0x8, 0x10
-MB_SMEM_OVER_MAX_OCC = 0x1
+MB_SMEM_OVER_MAX_OCC, MB_SMEM_ROUND2 = 0x1, 0x2
 MB_ERR_CAPACITY = -3
 
 SMEM_DTYPE = np.dtype([("read", "<u4"), ("qbeg", "<u4"), ("qend", "<u4"), ("flags", "<u4"),
@@ -75,6 +75,7 @@ def lib():
                 "mb_strerror": ([I], ctypes.c_char_p),
                 "mb_last_error": ([], ctypes.c_char_p),
                 "mb_seed_batch_noalloc": ([P, P, P, U32, P, OP, P, P, U64, PU64, PU64], I),
+                "mb_reseed": ([P, P, P, U32, P, P, U64, OP, P, P, U64, PU64, PU64], I),
                 "mb_plan_create": ([P, OP, U32, U64, U64, U64, PP], I),
                 "mb_plan_run": ([P, P, P, U32, P, P], I),
                 "mb_plan_result": ([P, P, PP, PU64, PP, PU64], I),
@@ -271,6 +272,24 @@ def mb_bs_filter(index: Index, smem, n_smem: int, mate, hits, n_hits: int, strea
     _check(lib().mb_bs_filter(index.handle, _ptr(smem), n_smem, _ptr(mate), _ptr(hits), n_hits,
                               _stream(stream), _ptr(keep)), "mb_bs_filter")
     return keep[:n_hits]
+
+
+def mb_reseed(index: Index, seq, off, smem, n_smem: int, mate=None, opts=None, stream=None):
+    """Second seeding round (Section 2.7) on first-round records; returns (records, n, n_hits)."""
+    o = _opts(opts)
+    n_reads = (off.numel() if hasattr(off, "numel") else len(off)) - 1
+    n_out, n_hits = ctypes.c_uint64(), ctypes.c_uint64()
+    cap = max(16, 4 * n_smem)
+    while True:
+        buf = np.empty(cap, dtype=SMEM_DTYPE)
+        rc = lib().mb_reseed(index.handle, _ptr(seq), _ptr(off), n_reads, _ptr(mate), _ptr(smem), n_smem,
+                             ctypes.byref(o), _stream(stream), _ptr(buf), cap, ctypes.byref(n_out),
+                             ctypes.byref(n_hits))
+        if rc == MB_ERR_CAPACITY:
+            cap = n_out.value
+            continue
+        _check(rc, "mb_reseed")
+        return buf[:n_out.value], n_out.value, n_hits.value
 
 
 def seed(index: Index, seq, off, mate=None, opts=None, stream=None):

@@ -339,7 +339,10 @@ static void free_index(mb_index *x) {
 
 // Suffix array of T (device, n symbols) by prefix doubling.  SA (device, n) receives it.
 static int build_sa(const u8 *T, u64 n, u32 *SA, cudaStream_t st) {
-    DevBuf bk, bka, bv, bva, btmp, brank, bhv, bflag, bact, bact2, berr, bcount;
+    // 25 bytes per suffix: keys and the sort's spare keys (8 + 8), values and spare values (4 + 4),
+    // ranks (4), two active lists (4 + 4); the run heads and flags (4 + 4) live in the spare keys,
+    // which are free whenever they are used.
+    DevBuf bk, bka, bv, bva, btmp, brank, bact, bact2, berr, bcount;
     MB_TRY(bk.alloc(n * 8, st));
     MB_TRY(bka.alloc(n * 8, st));
     MB_TRY(bv.alloc(n * 4, st));
@@ -348,15 +351,13 @@ static int build_sa(const u8 *T, u64 n, u32 *SA, cudaStream_t st) {
     size_t sb = scan_tmp_bytes(n);
     MB_TRY(btmp.alloc(tb > sb ? tb : sb, st));
     MB_TRY(brank.alloc(n * 4, st));
-    MB_TRY(bhv.alloc(n * 4, st));
-    MB_TRY(bflag.alloc(n * 4, st));
     MB_TRY(bact.alloc(n * 4, st));
     MB_TRY(bact2.alloc(n * 4, st));
     MB_TRY(berr.alloc(8, st));
     MB_TRY(bcount.alloc(8, st));
     u64 *keys = bk.as<u64>(), *keys_alt = bka.as<u64>();
     u32 *vals = bv.as<u32>(), *vals_alt = bva.as<u32>();
-    u32 *rank = brank.as<u32>(), *hv = bhv.as<u32>(), *flag = bflag.as<u32>();
+    u32 *rank = brank.as<u32>(), *hv = bka.as<u32>(), *flag = bka.as<u32>() + n;
     u32 *act = bact.as<u32>(), *act2 = bact2.as<u32>();
     u32 *err = berr.as<u32>(), *count = bcount.as<u32>();
     MB_CK(cudaMemsetAsync(err, 0, 4, st));

@@ -13,6 +13,7 @@
 // positions, and a gather writes the 48-byte records.  Reads with more SMEMs than slots are
 // listed and recomputed straight into the final records.
 #include <climits>
+#include <vector>
 #include "common.cuh"
 
 DevIndex mb_dev_index(const mb_index *x);
@@ -21,19 +22,14 @@ u32 mb_index_flags(const mb_index *x);
 
 namespace {
 
+// second seeding round (Section 2.7): windows are SMEMs occurring at most this many times
+constexpr u32 RESEED_MAX_OCC = 10;
+
 struct SlotRec {
     u32 qbeg, qend, k, kr, s;
 };
 
 __device__ __forceinline__ u64 slot_base(const u64 *off, u64 r) { return (off[r] - off[0]) / 32 + 4 * r; }
-
-// read base with the bisulfite conversion of Section 2.8 (conv 1: C->T, conv 2: G->A); > 3 = N
-__device__ __forceinline__ u32 read_base(const u8 *__restrict__ P, u64 j, u32 conv) {
-    u32 b = P[j];
-    if (conv == 1 && b == 1) b = 3;
-    if (conv == 2 && b == 2) b = 0;
-    return b;
-}
 
 // Work counters of the measurement mode (MB_COUNT); compiled out otherwise.
 template <bool ON>
@@ -310,6 +306,7 @@ struct SmemArgs {
     const u32 *perm;
     u32 *qhead;
     u64 *wc;
+    const u32 *lc;   // per-read (l | c << 16), or null for the kernel-wide l and c
 };
 
 // Launch bounds per shape: 128 threads allow 85 registers (6 blocks, 24 warps per SM); 256 and
@@ -322,7 +319,7 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 128 ? 6 : 1024 / BLOCK) k_smem
                                                                SlotRec *__restrict__ slots, u64 slot_total,
                                                                u64 *__restrict__ counts, u32 *__restrict__ ovf_list,
                                                                u32 *__restrict__ ovf_n, const u32 *__restrict__ perm,
-                                                               u32 *qhead, u64 *wc) {
+                                                               u32 *qhead, u64 *wc, const u32 *__restrict__ lc) {
     const u32 lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
     const u32 n = (u32)I.n;
     const u64 o0 = off[0];
@@ -332,6 +329,7 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 128 ? 6 : 1024 / BLOCK) k_smem
     SlotEmit em;
     WarpRange wr;
     if (!QUEUE) wr.init(nr);
+    u32 lr = l, cr = c;   // this read's l and c
     auto start = [&](u64 rr) {
         const u64 b = off[rr], e = off[rr + 1];
         const u64 sb = (b - o0) / 32 + 4 * rr, se = (e - o0) / 32 + 4 * (rr + 1);
@@ -339,7 +337,12 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 128 ? 6 : 1024 / BLOCK) k_smem
         em.base = sb;
         em.cap = se <= slot_total ? (u32)(se - sb) : 0u;
         em.cnt = 0;
-        smem_begin(S, seq + b, (int)(e - b), conv_of(mate, rr, bs), l, n, end);
+        if (lc) {
+            const u32 v = lc[rr];
+            lr = v & 0xFFFFu;
+            cr = v >> 16;
+        }
+        smem_begin(S, seq + b, (int)(e - b), conv_of(mate, rr, bs), lr, n, end);
     };
     // next `k` items of this warp's work; lane gets item base + rank
     auto take = [&](u32 k, u32 rank, u64 &item, bool &ok) {
@@ -368,7 +371,7 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 128 ? 6 : 1024 / BLOCK) k_smem
         bool need = false;
         u32 p = 0, q = 0, ss = 0, sym = 4;
         if (live) {
-            need = smem_advance(S, I, l, c, kmer, em, work);
+            need = smem_advance(S, I, lr, cr, kmer && lr >= I.kmer_k, em, work);
             if (need) {
                 const u32 a = cached_base(S, S.j);
                 const bool fwd = S.u == 2;   // ForwardExt((k,kr,s), a) = BackwardExt((kr,k,s), comp a)
@@ -392,7 +395,7 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 128 ? 6 : 1024 / BLOCK) k_smem
             bool go = need;
             if (need) {
                 const bool fwd = S.u == 2;
-                go = smem_apply(S, fwd ? nq : np, fwd ? np : nq, ns, l, c, n, em);
+                go = smem_apply(S, fwd ? nq : np, fwd ? np : nq, ns, lr, cr, n, em);
             }
             if (!go) {
                 counts[r] = em.cnt;
@@ -463,14 +466,16 @@ __global__ void k_smem_overflow(DevIndex I, const u8 *__restrict__ seq, const u6
                                 const u8 *__restrict__ mate, u32 bs, u32 l, u32 c, bool kmer,
                                 const u32 *__restrict__ ovf_list,
                                 const u32 *__restrict__ ovf_n, const u64 *__restrict__ soff, u32 max_occ,
-                                mb_smem *__restrict__ out, u64 *__restrict__ hitc, u64 cap) {
+                                mb_smem *__restrict__ out, u64 *__restrict__ hitc, u64 cap,
+                                const u32 *__restrict__ lc) {
     u32 n = *ovf_n;
     for (u32 q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
         u32 r = ovf_list[q];
         FinalEmit em{out, hitc, soff[r], cap, r, max_occ};
         Work<false> work;
-        smem_read(I, seq + off[r], (int)(off[r + 1] - off[r]), l, c, conv_of(mate, r, bs), kmer, seq + off[nr], em,
-                  work);
+        const u32 lr = lc ? (lc[r] & 0xFFFFu) : l, cr = lc ? (lc[r] >> 16) : c;
+        smem_read(I, seq + off[r], (int)(off[r + 1] - off[r]), lr, cr, conv_of(mate, r, bs), kmer && lr >= I.kmer_k,
+                  seq + off[nr], em, work);
     }
 }
 
@@ -631,7 +636,7 @@ int launch_smem_t(const SmemArgs &a, cudaStream_t st) {
     const unsigned g = resident_grid((const void *)k_smem<COUNT, QUEUE, BLOCK>, BLOCK, a.nr);
     k_smem<COUNT, QUEUE, BLOCK><<<g, BLOCK, 0, st>>>(a.I, a.seq, a.off, a.nr, a.mate, a.bs, a.l, a.c, a.kmer, a.slots,
                                                      a.slot_total, a.counts, a.ovf_list, a.ovf_n, a.perm, a.qhead,
-                                                     a.wc);
+                                                     a.wc, a.lc);
     MB_KCHECK();
     return MB_OK;
 }
@@ -652,42 +657,17 @@ int launch_smem(const SmemArgs &a, bool count, bool queue, int block, cudaStream
 }  // namespace
 
 // ============================================================================ host entry points
-extern "C" int mb_seed_batch(const mb_index *idx, const uint8_t *seq, const uint64_t *off, uint32_t n_reads,
-                             const uint8_t *mate, const mb_opts *opts, void *stream, mb_smem *out, uint64_t cap,
-                             uint64_t *n_out, uint64_t *n_hits) {
-    if (!idx || !off || !n_out || (n_reads > 0 && !seq)) {
-        mb_set_error("mb_seed_batch: null argument");
-        return MB_ERR_ARG;
-    }
+// The seeding pipeline on device inputs (seq, off, mate, and optionally a per-read (l | c << 16));
+// out may be host or device.
+static int seed_device(const mb_index *idx, const u8 *dseq, const u64 *doff, u32 n_reads, const u8 *dmate,
+                       const u32 *dlc, u64 o0, u64 o1, const mb_opts *opts, cudaStream_t st, mb_smem *out, u64 cap,
+                       u64 *n_out, u64 *n_hits) {
     u32 l, c, max_occ, flags;
     opts_defaults(opts, l, c, max_occ, flags);
-    cudaStream_t st = (cudaStream_t)stream;
+    const u32 bs = (flags & MB_BS3) ? 1u : 0u;
     *n_out = 0;
     if (n_hits) *n_hits = 0;
     if (n_reads == 0) return MB_OK;
-    const u32 bs = (flags & MB_BS3) ? 1u : 0u;
-
-    // offsets to the host to size the inputs and scratch
-    DevBuf boff, bseq, bmate;
-    const void *doff = nullptr, *dseq = nullptr, *dmate = nullptr;
-    u64 o0 = 0, o1 = 0;
-    MB_CK(cudaMemcpyAsync(&o0, off, 8, cudaMemcpyDefault, st));
-    MB_CK(cudaMemcpyAsync(&o1, off + n_reads, 8, cudaMemcpyDefault, st));
-    MB_CK(cudaStreamSynchronize(st));
-    if (o1 < o0) {
-        mb_set_error("mb_seed_batch: offsets decrease");
-        return MB_ERR_ARG;
-    }
-    MB_TRY(mb_stage_in(off, (size_t)(n_reads + 1) * 8, st, boff, &doff));
-    // a host `seq` is staged from off[0]; device pointers are used as given
-    if (mb_is_device_ptr(seq)) dseq = seq;
-    else {
-        MB_TRY(bseq.alloc(o1 - o0 + 1, st));
-        MB_CK(cudaMemcpyAsync(bseq.as<u8>() + 0, seq + o0, o1 - o0, cudaMemcpyHostToDevice, st));
-        dseq = bseq.as<u8>() - o0;
-    }
-    if (mate) MB_TRY(mb_stage_in(mate, n_reads, st, bmate, &dmate));
-
     const u64 nslots = (o1 - o0) / 32 + 4ULL * n_reads + 4;
     DevBuf bslots, bcounts, bsoff, bovf, bmisc, btmp;
     MB_TRY(bslots.alloc(nslots * sizeof(SlotRec), st));
@@ -708,7 +688,7 @@ extern "C" int mb_seed_batch(const mb_index *idx, const uint8_t *seq, const uint
         const bool count = (flags & MB_COUNT) != 0;
         SmemArgs sa{I, (const u8 *)dseq, (const u64 *)doff, n_reads, (const u8 *)dmate, bs, l, c, kmer,
                     bslots.as<SlotRec>(), nslots, bcounts.as<u64>(), bovf.as<u32>(), dovf_n, nullptr, nullptr,
-                    count ? mb_work_counter_buf(st) : nullptr};
+                    count ? mb_work_counter_buf(st) : nullptr, dlc};
         const int blk = opts && (opts->block_size == 128 || opts->block_size == 512) ? (int)opts->block_size : 256;
         kt.start();
         MB_TRY(launch_smem(sa, count, false, blk, st));
@@ -741,7 +721,7 @@ extern "C" int mb_seed_batch(const mb_index *idx, const uint8_t *seq, const uint
     k_smem_overflow<<<152, 128, 0, st>>>(I, (const u8 *)dseq, (const u64 *)doff, n_reads, (const u8 *)dmate, bs, l,
                                          c, kmer,
                                          bovf.as<u32>(), dovf_n, bsoff.as<u64>(), max_occ, dout, bhitc.as<u64>(),
-                                         total);
+                                         total, dlc);
     MB_KCHECK();
     MB_TRY(bhtmp.alloc(scan_tmp_bytes(total), st));
     MB_TRY(scan_exclusive_u64(bhitc.as<u64>(), bhitc.as<u64>(), total, dhtotal, bhtmp.p, st));
@@ -753,6 +733,43 @@ extern "C" int mb_seed_batch(const mb_index *idx, const uint8_t *seq, const uint
     MB_CK(cudaStreamSynchronize(st));
     if (n_hits) *n_hits = ht;
     return MB_OK;
+}
+
+extern "C" int mb_seed_batch(const mb_index *idx, const uint8_t *seq, const uint64_t *off, uint32_t n_reads,
+                             const uint8_t *mate, const mb_opts *opts, void *stream, mb_smem *out, uint64_t cap,
+                             uint64_t *n_out, uint64_t *n_hits) {
+    if (!idx || !off || !n_out || (n_reads > 0 && !seq)) {
+        mb_set_error("mb_seed_batch: null argument");
+        return MB_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    *n_out = 0;
+    if (n_hits) *n_hits = 0;
+    if (n_reads == 0) return MB_OK;
+
+    // offsets to the host to size the inputs and scratch
+    DevBuf boff, bseq, bmate;
+    const void *doff = nullptr, *dseq = nullptr, *dmate = nullptr;
+    u64 o0 = 0, o1 = 0;
+    MB_CK(cudaMemcpyAsync(&o0, off, 8, cudaMemcpyDefault, st));
+    MB_CK(cudaMemcpyAsync(&o1, off + n_reads, 8, cudaMemcpyDefault, st));
+    MB_CK(cudaStreamSynchronize(st));
+    if (o1 < o0) {
+        mb_set_error("mb_seed_batch: offsets decrease");
+        return MB_ERR_ARG;
+    }
+    MB_TRY(mb_stage_in(off, (size_t)(n_reads + 1) * 8, st, boff, &doff));
+    // a host `seq` is staged from off[0]; device pointers are used as given
+    if (mb_is_device_ptr(seq)) dseq = seq;
+    else {
+        MB_TRY(bseq.alloc(o1 - o0 + 1, st));
+        MB_CK(cudaMemcpyAsync(bseq.as<u8>() + 0, seq + o0, o1 - o0, cudaMemcpyHostToDevice, st));
+        dseq = bseq.as<u8>() - o0;
+    }
+    if (mate) MB_TRY(mb_stage_in(mate, n_reads, st, bmate, &dmate));
+
+    return seed_device(idx, (const u8 *)dseq, (const u64 *)doff, n_reads, (const u8 *)dmate, nullptr, o0, o1, opts,
+                       st, out, cap, n_out, n_hits);
 }
 
 extern "C" int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_smem, const mb_opts *opts,
@@ -964,8 +981,7 @@ extern "C" int mb_seed_batch_noalloc(const mb_index *idx, const uint8_t *seq, co
     k_gather<<<G, B, 0, st>>>(off, n_reads, slots, nslots, counts, soff, max_occ, out, hitc, total);
     MB_KCHECK();
     k_smem_overflow<<<152, 128, 0, st>>>(I, seq, off, n_reads, mate, bs, l, c, kmer, ovf, dovf_n, soff, max_occ, out,
-                                         hitc,
-                                         total);
+                                         hitc, total, nullptr);
     MB_KCHECK();
     MB_TRY(scan_exclusive_u64(hitc, hitc, total, dhtotal, S + o_htmp, st));
     k_set_hitoff<<<grid_for(total, 256), 256, 0, st>>>(hitc, total, nullptr, out);
@@ -1008,6 +1024,7 @@ struct mb_plan {
     size_t bytes = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    u64 graph_kernels = 0;   // kernel nodes of the captured graph
 };
 
 size_t mb_plan_bytes(const mb_plan *p) { return p ? p->bytes : 0; }
@@ -1106,7 +1123,7 @@ extern "C" int mb_plan_run(mb_plan *P, const uint8_t *seq, const uint64_t *off, 
                                 P->max_smem);
     MB_KCHECK();
     k_smem_overflow<<<152, 128, 0, st>>>(I, seq, off, n_reads, mate, bs, P->l, P->c, P->kmer, P->ovf, ovf_n, P->soff,
-                                         P->max_occ, P->out, P->hitc, P->max_smem);
+                                         P->max_occ, P->out, P->hitc, P->max_smem, nullptr);
     MB_KCHECK();
     MB_TRY(scan_exclusive_u64(P->hitc, P->hitc, P->max_smem, n_hits, P->tmp, st));
     k_set_hitoff<<<grid_for(P->max_smem, 256), 256, 0, st>>>(P->hitc, P->max_smem, n_smem, P->out);
@@ -1171,7 +1188,19 @@ extern "C" int mb_plan_capture(mb_plan *P, const uint8_t *seq, const uint64_t *o
         cudaError_t e = cudaStreamEndCapture(s, &g);
         if (rc == MB_OK && e != cudaSuccess) rc = MB_ERR_CUDA;
         if (rc == MB_OK && cudaGraphInstantiate(&P->exec, g, 0) != cudaSuccess) rc = MB_ERR_CUDA;
-        if (rc == MB_OK) P->graph = g;
+        if (rc == MB_OK) {
+            P->graph = g;
+            size_t nn = 0;
+            cudaGraphGetNodes(g, nullptr, &nn);
+            std::vector<cudaGraphNode_t> nodes(nn);
+            if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+            P->graph_kernels = 0;
+            for (size_t i = 0; i < nn; ++i) {
+                cudaGraphNodeType t;
+                if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+                    ++P->graph_kernels;
+            }
+        }
         else if (g) cudaGraphDestroy(g);
     }
     cudaStreamDestroy(s);
@@ -1182,7 +1211,7 @@ extern "C" int mb_plan_capture(mb_plan *P, const uint8_t *seq, const uint64_t *o
 extern "C" int mb_plan_replay(mb_plan *P, void *stream) {
     if (!P || !P->exec) return MB_ERR_ARG;
     MB_CK(cudaGraphLaunch(P->exec, (cudaStream_t)stream));
-    mb_count_launch();
+    for (u64 i = 0; i < P->graph_kernels; ++i) mb_count_launch();   // the kernels the graph runs
     return MB_OK;
 }
 
@@ -1242,5 +1271,141 @@ extern "C" int mb_autotune(const mb_index *idx, const uint8_t *seq, const uint64
     if (rc != MB_OK) return rc;
     *best = bo;
     if (best_ms) *best_ms = bms;
+    return MB_OK;
+}
+
+// ============================================================================ second seeding round
+namespace {
+// window of record m: an SMEM of at least min_w bases that occurs at most max_s times
+__global__ void k_win_flag(const mb_smem *__restrict__ sm, u64 nsm, u32 min_w, u32 max_s, u64 *__restrict__ flag) {
+    for (u64 m = blockIdx.x * (u64)blockDim.x + threadIdx.x; m < nsm; m += (u64)gridDim.x * blockDim.x) {
+        const mb_smem x = sm[m];
+        flag[m] = (x.qend - x.qbeg >= min_w && x.s <= max_s && !(x.flags & MB_SMEM_OVER_MAX_OCC)) ? 1 : 0;
+    }
+}
+// window w: read, start, length, (l' | c' << 16) with l' = floor(len / 2), c' = s + 1
+__global__ void k_win_build(const mb_smem *__restrict__ sm, u64 nsm, const u64 *__restrict__ flag,
+                            const u64 *__restrict__ wpos, const u8 *__restrict__ mate, uint2 *__restrict__ winfo,
+                            u64 *__restrict__ wlen, u32 *__restrict__ lc, u8 *__restrict__ wmate) {
+    for (u64 m = blockIdx.x * (u64)blockDim.x + threadIdx.x; m < nsm; m += (u64)gridDim.x * blockDim.x) {
+        if (!flag[m]) continue;
+        const mb_smem x = sm[m];
+        const u64 w = wpos[m];
+        const u32 len = x.qend - x.qbeg;
+        winfo[w] = make_uint2(x.read, x.qbeg);
+        wlen[w] = len;
+        lc[w] = (len / 2) | ((u32)(x.s + 1) << 16);
+        wmate[w] = mate ? mate[x.read] : 0;
+    }
+}
+// bases of every window, one warp per window
+__global__ void k_win_copy(const u8 *__restrict__ seq, const u64 *__restrict__ off, const uint2 *__restrict__ winfo,
+                           const u64 *__restrict__ woff, u64 nw, u8 *__restrict__ wseq) {
+    const u32 lane = threadIdx.x & 31;
+    const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
+    for (u64 w = (blockIdx.x * (u64)blockDim.x + threadIdx.x) >> 5; w < nw; w += nwarps) {
+        const u8 *src = seq + off[winfo[w].x] + winfo[w].y;
+        const u64 b = woff[w], len = woff[w + 1] - b;
+        for (u64 t = lane; t < len; t += 32) wseq[b + t] = src[t];
+    }
+}
+// records of the windows back in read coordinates
+__global__ void k_win_fix(mb_smem *__restrict__ out, u64 n, const uint2 *__restrict__ winfo) {
+    for (u64 t = blockIdx.x * (u64)blockDim.x + threadIdx.x; t < n; t += (u64)gridDim.x * blockDim.x) {
+        const uint2 w = winfo[out[t].read];
+        out[t].read = w.x;
+        out[t].qbeg += w.y;
+        out[t].qend += w.y;
+        out[t].flags |= MB_SMEM_ROUND2;
+    }
+}
+}  // namespace
+
+extern "C" int mb_reseed(const mb_index *idx, const uint8_t *seq, const uint64_t *off, uint32_t n_reads,
+                         const uint8_t *mate, const mb_smem *smem, uint64_t n_smem, const mb_opts *opts, void *stream,
+                         mb_smem *out, uint64_t cap, uint64_t *n_out, uint64_t *n_hits) {
+    if (!idx || !off || !n_out || (n_reads && !seq) || (n_smem && !smem)) return MB_ERR_ARG;
+    *n_out = 0;
+    if (n_hits) *n_hits = 0;
+    if (n_reads == 0 || n_smem == 0) return MB_OK;
+    u32 l, c, max_occ, flags;
+    opts_defaults(opts, l, c, max_occ, flags);
+    cudaStream_t st = (cudaStream_t)stream;
+    DevBuf boff, bseq, bmate, bsm;
+    const void *doff = nullptr, *dseq = nullptr, *dmate = nullptr, *dsm = nullptr;
+    u64 o0 = 0, o1 = 0;
+    MB_CK(cudaMemcpyAsync(&o0, off, 8, cudaMemcpyDefault, st));
+    MB_CK(cudaMemcpyAsync(&o1, off + n_reads, 8, cudaMemcpyDefault, st));
+    MB_CK(cudaStreamSynchronize(st));
+    MB_TRY(mb_stage_in(off, (size_t)(n_reads + 1) * 8, st, boff, &doff));
+    if (mb_is_device_ptr(seq)) dseq = seq;
+    else {
+        MB_TRY(bseq.alloc(o1 - o0 + 1, st));
+        MB_CK(cudaMemcpyAsync(bseq.as<u8>(), seq + o0, o1 - o0, cudaMemcpyHostToDevice, st));
+        dseq = bseq.as<u8>() - o0;
+    }
+    if (mate) MB_TRY(mb_stage_in(mate, n_reads, st, bmate, &dmate));
+    MB_TRY(mb_stage_in(smem, n_smem * sizeof(mb_smem), st, bsm, &dsm));
+    // windows (Section 2.7): SMEMs of at least 2l bases occurring at most 10 times
+    DevBuf bflag, bwpos, btmp, bmisc;
+    MB_TRY(bflag.alloc(n_smem * 8, st));
+    MB_TRY(bwpos.alloc(n_smem * 8, st));
+    MB_TRY(btmp.alloc(scan_tmp_bytes(n_smem + 1), st));
+    MB_TRY(bmisc.alloc(64, st));
+    k_win_flag<<<grid_for(n_smem, 256), 256, 0, st>>>((const mb_smem *)dsm, n_smem, 2 * l, RESEED_MAX_OCC,
+                                                      bflag.as<u64>());
+    MB_KCHECK();
+    MB_TRY(scan_exclusive_u64(bflag.as<u64>(), bwpos.as<u64>(), n_smem, bmisc.as<u64>(), btmp.p, st));
+    u64 nw = 0;
+    MB_CK(cudaMemcpyAsync(&nw, bmisc.p, 8, cudaMemcpyDeviceToHost, st));
+    MB_CK(cudaStreamSynchronize(st));
+    if (nw == 0) return MB_OK;
+    if (nw >= (1ull << 32)) return MB_ERR_ARG;
+    DevBuf binfo, bwlen, blc, bwmate, bwoff, bwseq;
+    MB_TRY(binfo.alloc(nw * 8, st));
+    MB_TRY(bwlen.alloc(nw * 8, st));
+    MB_TRY(blc.alloc(nw * 4, st));
+    MB_TRY(bwmate.alloc(nw, st));
+    MB_TRY(bwoff.alloc((nw + 1) * 8, st));
+    k_win_build<<<grid_for(n_smem, 256), 256, 0, st>>>((const mb_smem *)dsm, n_smem, bflag.as<u64>(),
+                                                       bwpos.as<u64>(), (const u8 *)dmate, binfo.as<uint2>(),
+                                                       bwlen.as<u64>(), blc.as<u32>(), bwmate.as<u8>());
+    MB_KCHECK();
+    MB_TRY(btmp.alloc(scan_tmp_bytes(nw), st));
+    MB_TRY(scan_exclusive_u64(bwlen.as<u64>(), bwoff.as<u64>(), nw, bwoff.as<u64>() + nw, btmp.p, st));
+    u64 wbases = 0;
+    MB_CK(cudaMemcpyAsync(&wbases, bwoff.as<u64>() + nw, 8, cudaMemcpyDeviceToHost, st));
+    MB_CK(cudaStreamSynchronize(st));
+    MB_TRY(bwseq.alloc(wbases + 16, st));
+    k_win_copy<<<grid_for(nw * 32, 256), 256, 0, st>>>((const u8 *)dseq, (const u64 *)doff, binfo.as<uint2>(),
+                                                       bwoff.as<u64>(), nw, bwseq.as<u8>());
+    MB_KCHECK();
+    // the seeding pipeline on the windows, each with its own (l', c'); window bases are copied
+    // unconverted, so in bisulfite mode each window is converted by its read's mate flag
+    mb_opts o = opts ? *opts : mb_opts{};
+    o.flags &= ~(u32)MB_COUNT;
+    const u8 *wm = (flags & MB_BS3) ? bwmate.as<u8>() : nullptr;
+    DevBuf bout;
+    const bool out_dev = mb_is_device_ptr(out);
+    u64 need = 0, nh = 0;
+    int rc = seed_device(idx, bwseq.as<u8>(), bwoff.as<u64>(), (u32)nw, wm, blc.as<u32>(), 0, wbases, &o, st,
+                         nullptr, 0, &need, &nh);
+    if (rc != MB_OK && rc != MB_ERR_CAPACITY) return rc;
+    *n_out = need;
+    if (need > cap) return MB_ERR_CAPACITY;
+    if (need == 0) return MB_OK;
+    if (!out) return MB_ERR_ARG;
+    mb_smem *dout = out;
+    if (!out_dev) {
+        MB_TRY(bout.alloc(need * sizeof(mb_smem), st));
+        dout = bout.as<mb_smem>();
+    }
+    MB_TRY(seed_device(idx, bwseq.as<u8>(), bwoff.as<u64>(), (u32)nw, wm, blc.as<u32>(), 0, wbases, &o, st, dout,
+                       need, &need, &nh));
+    k_win_fix<<<grid_for(need, 256), 256, 0, st>>>(dout, need, binfo.as<uint2>());
+    MB_KCHECK();
+    if (!out_dev) MB_CK(cudaMemcpyAsync(out, dout, need * sizeof(mb_smem), cudaMemcpyDeviceToHost, st));
+    MB_CK(cudaStreamSynchronize(st));
+    if (n_hits) *n_hits = nh;
     return MB_OK;
 }

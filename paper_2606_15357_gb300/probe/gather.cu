@@ -4,6 +4,7 @@
 //   mode 0: independent random block reads, 8 in flight per thread (bandwidth ceiling)
 //   mode 1: dependent chains: each read's address comes from the data just read, the access
 //           pattern of an LF-walk (latency-bound ceiling at full occupancy)
+//   mode 2: as mode 1 with loads cached in L2 only (ld.global.cg)
 // Blocks are 64 bytes (two 256-bit loads) or 32 bytes (one), at random 64-byte-aligned places
 // of a buffer of `bytes` bytes (block index = high 64 bits of hash * number of blocks).
 #include <cuda_runtime.h>
@@ -19,13 +20,16 @@ __device__ __forceinline__ u64 mix(u64 z) {
     return z ^ (z >> 31);
 }
 
-template <int BYTES>
+// CG = false: non-coherent path, cached in L1; CG = true: cached in L2 only
+template <int BYTES, bool CG = false>
 __device__ __forceinline__ u64 ld_block(const u64 *p) {
     u64 a, b, c, d;
-    asm volatile("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
+    if (CG) asm volatile("ld.global.cg.v4.u64 {%0,%1,%2,%3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
+    else asm volatile("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
     u64 r = a ^ b ^ c ^ d;
     if (BYTES == 64) {
-        asm volatile("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p + 4));
+        if (CG) asm volatile("ld.global.cg.v4.u64 {%0,%1,%2,%3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p + 4));
+        else asm volatile("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p + 4));
         r ^= a ^ b ^ c ^ d;
     }
     return r;
@@ -50,11 +54,11 @@ __global__ void __launch_bounds__(256) k_indep(const u64 *buf, u64 nblocks, unsi
     if (acc == 0x1234567) sink[tid & 1023] = acc;
 }
 
-template <int BYTES>
+template <int BYTES, bool CG = false>
 __global__ void __launch_bounds__(256) k_chain(const u64 *buf, u64 nblocks, unsigned iters, u64 *sink) {
     const u64 tid = blockIdx.x * (u64)blockDim.x + threadIdx.x;
     u64 idx = __umul64hi(mix(tid), nblocks);
-    for (unsigned it = 0; it < iters; ++it) idx = __umul64hi(mix(ld_block<BYTES>(buf + idx * 8) ^ it), nblocks);
+    for (unsigned it = 0; it < iters; ++it) idx = __umul64hi(mix(ld_block<BYTES, CG>(buf + idx * 8) ^ it), nblocks);
     if (idx == 0x1234567) sink[tid & 1023] = idx;
 }
 
@@ -73,6 +77,7 @@ extern "C" double mb_probe_gather(uint64_t bytes, int mode, int block_bytes, uns
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const void *k = mode == 0 ? (block_bytes == 64 ? (const void *)k_indep<64> : (const void *)k_indep<32>)
                               : (block_bytes == 64 ? (const void *)k_chain<64> : (const void *)k_chain<32>);
+    if (mode == 2) k = block_bytes == 64 ? (const void *)k_chain<64, true> : (const void *)k_chain<32, true>;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, 256, 0);
     const unsigned grid = (unsigned)(sms * (per > 0 ? per : 1));
     cudaEvent_t a, b;
@@ -83,6 +88,8 @@ extern "C" double mb_probe_gather(uint64_t bytes, int mode, int block_bytes, uns
         cudaEventRecord(a);
         if (mode == 0 && block_bytes == 64) k_indep<64><<<grid, 256>>>(buf, nblocks, iters, sink);
         else if (mode == 0) k_indep<32><<<grid, 256>>>(buf, nblocks, iters, sink);
+        else if (mode == 2 && block_bytes == 64) k_chain<64, true><<<grid, 256>>>(buf, nblocks, iters, sink);
+        else if (mode == 2) k_chain<32, true><<<grid, 256>>>(buf, nblocks, iters, sink);
         else if (block_bytes == 64) k_chain<64><<<grid, 256>>>(buf, nblocks, iters, sink);
         else k_chain<32><<<grid, 256>>>(buf, nblocks, iters, sink);
         cudaEventRecord(b);

@@ -117,3 +117,36 @@ def test_workload2_100mbp_full_index_and_sampled_reads(mb):
     G.drop_sa()
     sm, hits = gpu_seed_all(mb, G, rd)
     check_sampled_reads(sm, hits, X, rd, 0.10, 0x6D63, params)
+
+
+def test_workload3_bisulfite_1gbp_three_base_index(mb):
+    """Directional bisulfite set: 3-base index over CT(R).GA(R) of the 1 Gbp reference
+    (n = 4e9 + 1), reads converted on the GPU (read 1 C->T, read 2 G->A), the strand filter of
+    Section 2.8; full suffix array, k-mer sample and 1% of the reads against the oracle."""
+    from synth import Reads
+    ref, rd, params = synth.workload(3, bisulfite=True)
+    o = dict(flags=mb.MB_BS3)
+    G = mb.mb_index_build(dev(ref), opts=o)
+    assert G.n == 4 * len(ref) + 1
+    X = oracle.Index(ref, bs3=True, threads=os.cpu_count())
+    check_index(G, X, sample_kmers=100_000)
+    G.drop_sa()
+    seq, off, mate = dev(rd.seq), dev(rd.off), dev(rd.mate)
+    cap = 4 * rd.n
+    out = torch.empty(cap * 48, dtype=torch.uint8, device="cuda")
+    _, m, nh = mb.mb_seed_batch(G, seq, off, mate=mate, opts=o, out=out, cap=cap)
+    hits = torch.empty(max(nh, 1), dtype=torch.int32, device="cuda")
+    mb.mb_locate(G, out, m, opts=o, hits=hits, cap=nh)
+    keep = torch.empty(max(nh, 1), dtype=torch.uint8, device="cuda")
+    mb.mb_bs_filter(G, out, m, mate, hits, nh, keep=keep)
+    sm = out[:m * 48].cpu().numpy().view(mb.SMEM_DTYPE)
+    h = hits[:nh].cpu().numpy().view(np.uint32)
+    kp = keep[:nh].cpu().numpy()
+    conv = Reads(oracle.bs_convert_reads(rd.seq, rd.off, rd.mate), rd.off, rd.origin, rd.mate)
+    check_sampled_reads(sm, h, X, conv, 0.01, 0x6D64, params)
+    # strand filter recomputed from the positions (Section 2.8)
+    cnt = np.where(sm["flags"] & 1, 0, sm["s"]).astype(np.int64)
+    qlen = np.repeat((sm["qend"] - sm["qbeg"]).astype(np.int64), cnt)
+    rmate = np.repeat(rd.mate[sm["read"].astype(np.int64)], cnt)
+    assert np.array_equal(kp.astype(bool), oracle.bs_keep(h, qlen, rmate, len(ref)))
+    assert kp.sum() > 0
