@@ -36,6 +36,9 @@ WORKLOADS = {
 }
 
 
+BLOCK_BYTES = 32   # one occurrence block (64 BWT rows) per 32-byte sector
+
+
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
@@ -443,7 +446,10 @@ def run_gpu(args):
 
     # autotune the launch shape on a sample of the batch, then use it for both forms
     ns = min(n_reads, 1_000_000)
-    best, tune_ms = mb.autotune(idx, seq[:int(rd.off[ns])], off[:ns + 1], opts=opts)
+    if args.no_autotune:
+        best = mb.Opts(block_size=256)
+    else:
+        best, tune_ms = mb.autotune(idx, seq[:int(rd.off[ns])], off[:ns + 1], opts=opts)
     opts["block_size"] = best.block_size
     log(f"autotuned on {ns} reads: block {best.block_size}, work queue {bool(best.flags & mb.MB_BATCHED)}")
 
@@ -513,8 +519,8 @@ def run_gpu(args):
 
     # roofline of the dominant kernel: algorithmic bytes / its event-timed duration
     peak, peak_kind = measured_peaks()
-    smem_bytes = 64 * wc["ext_blocks"] + 12 * wc["kmer_lookups"]
-    loc_bytes = 64 * wc["lf_steps"] + 4 * wc["sa_reads"]
+    smem_bytes = BLOCK_BYTES * wc["ext_blocks"] + 12 * wc["kmer_lookups"]
+    loc_bytes = BLOCK_BYTES * wc["lf_steps"] + 4 * wc["sa_reads"]
     if loc_ms / max(loc_n, 1) >= smem_ms / max(smem_n, 1):
         kname, kbytes, kms = "locate", loc_bytes, loc_ms / max(loc_n, 1)
     else:
@@ -593,6 +599,7 @@ def run_gpu(args):
                    "pairs_per_step": n_reads // 2, "min_len": params["min_len"], "max_occ": params["max_occ"],
                    "sa_rate": params["sa_rate"], "parallelism": f"replicas{ws}",
                    "l2": "inputs larger than L2 (reads 3 GB, index 1.25 GB)",
+                   "occ_block_bytes": BLOCK_BYTES,
                    "smem_per_step": m, "hits_per_step": nh, "index_build_s": build_s},
         "smems_per_s": ws * args.steps * m / (ms / 1000.0),
         "hits_per_s": ws * args.steps * nh / (ms / 1000.0),
@@ -626,6 +633,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the served-form measurement")
     ap.add_argument("--serve-requests", type=int, default=600)
     ap.add_argument("--probe-gib", type=int, default=1, help="buffer of the random-gather probe (GiB)")
+    ap.add_argument("--no-autotune", action="store_true", help="default launch shape (profiling captures)")
     ap.add_argument("--reads", type=int, default=0,
                     help="seed only the first N reads of the batch (for ncu captures of the full index)")
     args = ap.parse_args()

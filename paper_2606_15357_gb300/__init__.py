@@ -183,7 +183,7 @@ class Index:
         a_sa = np.empty(n, np.uint32) if sa else None
         a_bwt = np.empty(n, np.uint8) if bwt else None
         a_ssa = np.empty((n + sa_rate - 1) // sa_rate, np.uint32) if ssa else None
-        a_occ = np.empty((n // 128 + 1) * 8, np.uint64) if occ else None
+        a_occ = np.empty((n // 64 + 1) * 4, np.uint64) if occ else None
         a_kmer = np.empty(3 * 4 ** kmer_k, np.uint32) if kmer else None
         C = np.empty(5, np.uint64)
         _check(lib().mb_index_export(self._h, _ptr(a_sa), _ptr(a_bwt), _ptr(a_ssa), _ptr(a_occ),

@@ -85,14 +85,20 @@ u64 *mb_work_counter_buf(cudaStream_t st);   // device array of WC_N u64 (zeroed
 int mb_stage_in(const void *src, size_t bytes, cudaStream_t st, DevBuf &buf, const void **dev);
 
 // ----------------------------------------------------------------------------- index layout
-// One occurrence block per 128 BWT rows (Section 2.2): the counts of A, C, G, T in B[0, 128b)
-// as four u64, then the 128 symbols of B[128b, 128b+128) as four u64 words of 2-bit codes,
-// row q of the block in word q/32 at bits 2*(q%32).  The $ row (primary) is stored as A and
-// excluded from the counts.
-struct __align__(64) OccBlock {
-    u64 cnt[4];
-    u64 w[4];
+// One occurrence block per 64 BWT rows, 32 bytes: the counts of A, C, G, T in B[0, 64b) as four
+// u32 (n < 2^32), then the 64 symbols of B[64b, 64b+64) as two u64 words of 2-bit codes, row q of
+// the block in word q/32 at bits 2*(q%32).  The $ row (primary) is stored as A and excluded from
+// the counts.  The paper (Section 2.2) uses 64-byte blocks of 128 rows sized for a CPU cache
+// line; on this GPU a random read costs one 32-byte DRAM sector, so a block is one sector and
+// every LF step or block access reads exactly one.
+constexpr u32 BLK_SHIFT = 6;
+constexpr u32 BLK_ROWS = 1u << BLK_SHIFT;
+constexpr u32 BLK_MASK = BLK_ROWS - 1;
+struct __align__(32) OccBlock {
+    u32 cnt[4];
+    u64 w[2];
 };
+static_assert(sizeof(OccBlock) == 32, "one block per 32-byte sector");
 
 // Index view passed to kernels by value.
 struct DevIndex {
@@ -111,23 +117,21 @@ struct mb_index_impl;
 
 // ----------------------------------------------------------------------------- device helpers
 // Every row, count and interval bound is below n < 2^32, so the kernels work in u32.
-// A block as loaded: the low halves of the four u64 counts and the four 2-bit words.
 struct Blk {
     u32 c[4];
-    u64 w[4];
+    u64 w[2];
 };
-// Two 256-bit loads per block: one for the counts, one for the symbols.
+// The whole block in one 256-bit load.
 __device__ __forceinline__ Blk load_blk(const OccBlock *__restrict__ blk) {
-    u64 c0, c1, c2, c3, w0, w1, w2, w3;
-    asm("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];" : "=l"(c0), "=l"(c1), "=l"(c2), "=l"(c3) : "l"(blk->cnt));
-    asm("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];" : "=l"(w0), "=l"(w1), "=l"(w2), "=l"(w3) : "l"(blk->w));
+    u64 c01, c23, w0, w1;
+    asm("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];" : "=l"(c01), "=l"(c23), "=l"(w0), "=l"(w1) : "l"(blk));
     Blk b;
-    b.c[0] = (u32)c0; b.c[1] = (u32)c1; b.c[2] = (u32)c2; b.c[3] = (u32)c3;
-    b.w[0] = w0; b.w[1] = w1; b.w[2] = w2; b.w[3] = w3;
+    b.c[0] = (u32)c01; b.c[1] = (u32)(c01 >> 32); b.c[2] = (u32)c23; b.c[3] = (u32)(c23 >> 32);
+    b.w[0] = w0; b.w[1] = w1;
     return b;
 }
 
-// Bit mask of the 2-bit slots of word q (0..3) that lie before slot m (0..128) of the block.
+// Bit mask of the 2-bit slots of word q (0..1) that lie before slot m (0..64) of the block.
 __device__ __forceinline__ u64 slot_mask(u32 m, int q) {
     int take = (int)m - 32 * q;
     take = take < 0 ? 0 : (take > 32 ? 32 : take);
@@ -141,24 +145,19 @@ constexpr u64 EVEN = 0x5555555555555555ULL;
 // #{slots before m holding code a}; the $ row (stored as A) is not corrected here.
 __device__ __forceinline__ u32 cnt_sym(const Blk &b, u32 m, u32 a) {
     const u64 pat = (u64)a * EVEN;   // a in every 2-bit slot
-    u64 z[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const u64 y = ~(b.w[q] ^ pat);   // 11 where the slot holds a
-        z[q] = y & (y >> 1) & EVEN & slot_mask(m, q);
-    }
-    return popc_pair(z[0], z[1]) + popc_pair(z[2], z[3]);
+    const u64 y0 = ~(b.w[0] ^ pat), y1 = ~(b.w[1] ^ pat);   // 11 where the slot holds a
+    return popc_pair(y0 & (y0 >> 1) & EVEN & slot_mask(m, 0), y1 & (y1 >> 1) & EVEN & slot_mask(m, 1));
 }
 // #{slots before m holding a code <= a}; the $ row (stored as A) is not corrected here.
 __device__ __forceinline__ u32 cnt_le(const Blk &b, u32 m, u32 a) {
-    u64 z[4];
+    u64 z[2];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 2; ++q) {
         const u64 lo = b.w[q] & EVEN, hi = (b.w[q] >> 1) & EVEN;
         const u64 e = a == 0 ? (~lo & ~hi) : a == 1 ? ~hi : a == 2 ? ~(lo & hi) : ~0ULL;
         z[q] = e & EVEN & slot_mask(m, q);
     }
-    return popc_pair(z[0], z[1]) + popc_pair(z[2], z[3]);
+    return popc_pair(z[0], z[1]);
 }
 
 // x[a] for a in 0..3 without dynamic indexing (which would go through local memory)
@@ -168,16 +167,15 @@ __device__ __forceinline__ u32 sel4(u32 a, u32 x0, u32 x1, u32 x2, u32 x3) {
 
 // [the $ row lies in the block of x, before x]
 __device__ __forceinline__ u32 dollar_before(u32 x, u32 primary) {
-    const u32 bstart = x & ~127u;
+    const u32 bstart = x & ~BLK_MASK;
     return (primary >= bstart && primary < x) ? 1u : 0u;
 }
 
 // One LF step of Algorithm 2 from row x (x is not the $ row): a = B[x], result C[a] + #a in
 // B[0, x).
 __device__ __forceinline__ u32 lf_blk(const Blk &b, u32 x, u32 primary, u32 C0, u32 C1, u32 C2, u32 C3) {
-    const u32 m = x & 127;
-    const u64 wx = m < 64 ? (m < 32 ? b.w[0] : b.w[1]) : (m < 96 ? b.w[2] : b.w[3]);
-    const u32 a = (u32)(wx >> (2 * (m & 31))) & 3u;
+    const u32 m = x & BLK_MASK;
+    const u32 a = (u32)((m < 32 ? b.w[0] : b.w[1]) >> (2 * (m & 31))) & 3u;
     u32 cnt = cnt_sym(b, m, a);
     if (a == 0) cnt -= dollar_before(x, primary);
     return sel4(a, C0 + b.c[0], C1 + b.c[1], C2 + b.c[2], C3 + b.c[3]) + cnt;
@@ -195,7 +193,7 @@ struct Ext {
 };
 // #a and #{symbols <= a} in B[0, x), $ excluded
 __device__ __forceinline__ void occ_a_le(const Blk &b, u32 x, u32 a, u32 primary, u32 &na, u32 &nle) {
-    const u32 m = x & 127, d = dollar_before(x, primary);
+    const u32 m = x & BLK_MASK, d = dollar_before(x, primary);
     na = sel4(a, b.c[0], b.c[1], b.c[2], b.c[3]) + cnt_sym(b, m, a) - (a == 0 ? d : 0u);
     const u32 c01 = b.c[0] + b.c[1], c012 = c01 + b.c[2];
     nle = sel4(a, b.c[0], c01, c012, c012 + b.c[3]) + cnt_le(b, m, a) - d;
@@ -205,9 +203,9 @@ __device__ __forceinline__ void occ_a_le(const Blk &b, u32 x, u32 a, u32 primary
 // same block).
 __device__ __forceinline__ Ext extend(const DevIndex &I, u32 p, u32 q, u32 s, u32 a) {
     const u32 e = p + s, prim = (u32)I.primary;
-    const Blk b0 = load_blk(I.occ + (p >> 7));
+    const Blk b0 = load_blk(I.occ + (p >> BLK_SHIFT));
     Blk b1 = b0;
-    if ((e >> 7) != (p >> 7)) b1 = load_blk(I.occ + (e >> 7));
+    if ((e >> BLK_SHIFT) != (p >> BLK_SHIFT)) b1 = load_blk(I.occ + (e >> BLK_SHIFT));
     u32 na0, nle0, na1, nle1;
     occ_a_le(b0, p, a, prim, na0, nle0);
     occ_a_le(b1, e, a, prim, na1, nle1);

@@ -1,11 +1,12 @@
-// FMD-index construction on the GPU (Section 2.1 definitions, Section 2.2 block layout,
+// FMD-index construction on the GPU (Section 2.1 definitions, Section 2.2 block layout (here one
+// 32-byte block per 64 rows),
 // Section 2.3 sampled suffix array, Section 2.5 k-mer ds-interval table).
 //
 //   T = R . revcomp(R) . $            (bisulfite: R -> CT(R) . GA(R), Section 2.8)
 //   S = suffix array of T             prefix doubling: sort by the first 27 symbols, then
 //                                     repeatedly re-sort the suffixes whose 2h-prefix is still
 //                                     shared by (rank of the h-prefix, rank of the h-prefix at +h)
-//   B[i] = T[S(i) - 1], T[-1] = $     written straight into 64-byte occurrence blocks
+//   B[i] = T[S(i) - 1], T[-1] = $     written straight into 32-byte occurrence blocks
 #include <stdarg.h>
 #include <stdlib.h>
 #include <string.h>
@@ -133,17 +134,18 @@ __global__ void k_scatter_sa(const u32 *__restrict__ act, u64 A, const u32 *__re
         SA[act[t]] = vals[t];
 }
 
-// One warp per 128-row block: symbols B[x] = T[S(x)-1] packed 2 bits each ($ stored as A),
-// per-block counts of A,C,G,T (excluding $) to bcnt[a * nblocks + b].
+// One warp per 128 rows, i.e. two 64-row blocks: symbols B[x] = T[S(x)-1] packed 2 bits each
+// ($ stored as A), per-block counts of A,C,G,T (excluding $) to bcnt[a * nblocks + b].
 __global__ void k_bwt_blocks(const u8 *__restrict__ T, const u32 *__restrict__ SA, u64 n, OccBlock *__restrict__ occ,
                              u64 nblocks, u64 *__restrict__ bcnt, u64 *__restrict__ primary) {
     const int lane = threadIdx.x & 31;
     const u64 warps = (u64)gridDim.x * (blockDim.x >> 5);
-    for (u64 b = blockIdx.x * (u64)(blockDim.x >> 5) + (threadIdx.x >> 5); b < nblocks; b += warps) {
+    const u64 ngroups = (nblocks + 1) / 2;
+    for (u64 g = blockIdx.x * (u64)(blockDim.x >> 5) + (threadIdx.x >> 5); g < ngroups; g += warps) {
         u32 byte = 0, c[4] = {0, 0, 0, 0};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            u64 x = b * 128 + (u64)lane * 4 + j;
+            u64 x = g * 128 + (u64)lane * 4 + j;
             if (x < n) {
                 u32 p = SA[x];
                 u32 s;
@@ -163,16 +165,20 @@ __global__ void k_bwt_blocks(const u8 *__restrict__ T, const u32 *__restrict__ S
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int d = 16; d > 0; d >>= 1) c[a] += __shfl_xor_sync(0xffffffffu, c[a], d);
-        if ((lane & 7) == 0) occ[b].w[lane >> 3] = word;
-        if (lane < 4) bcnt[(u64)lane * nblocks + b] = c[lane];
+            for (int d = 8; d > 0; d >>= 1) c[a] += __shfl_xor_sync(0xffffffffu, c[a], d);   // per 16-lane half
+        const u64 b = 2 * g + (u64)(lane >> 4);
+        if (b < nblocks) {
+            if ((lane & 7) == 0) occ[b].w[(lane >> 3) & 1] = word;
+            const u32 a = (u32)(lane & 15);
+            if (a < 4) bcnt[(u64)a * nblocks + b] = a < 2 ? (a == 0 ? c[0] : c[1]) : (a == 2 ? c[2] : c[3]);
+        }
     }
 }
 
 __global__ void k_fill_counts(const u64 *__restrict__ bcnt_scanned, u64 nblocks, OccBlock *__restrict__ occ) {
     for (u64 b = blockIdx.x * (u64)blockDim.x + threadIdx.x; b < nblocks; b += (u64)gridDim.x * blockDim.x)
 #pragma unroll
-        for (int a = 0; a < 4; ++a) occ[b].cnt[a] = bcnt_scanned[(u64)a * nblocks + b];
+        for (int a = 0; a < 4; ++a) occ[b].cnt[a] = (u32)bcnt_scanned[(u64)a * nblocks + b];
 }
 
 __global__ void k_sample_sa(const u32 *__restrict__ SA, u64 n, u32 r, u32 *__restrict__ ssa) {
@@ -460,7 +466,7 @@ extern "C" int mb_index_build(const uint8_t *ref, uint64_t len, const mb_opts *o
         if ((rc = build_sa(bT.as<u8>(), n, X->sa, st)) != MB_OK) break;
 
         // BWT in occurrence blocks
-        X->nblocks = n / 128 + 1;
+        X->nblocks = n / BLK_ROWS + 1;
         const u64 nbk = X->nblocks;
         if (cudaMalloc(&X->occ, nbk * sizeof(OccBlock)) != cudaSuccess) { rc = MB_ERR_NOMEM; break; }
         if (cudaMemsetAsync(X->occ, 0, nbk * sizeof(OccBlock), st) != cudaSuccess) { rc = MB_ERR_CUDA; break; }
@@ -468,7 +474,7 @@ extern "C" int mb_index_build(const uint8_t *ref, uint64_t len, const mb_opts *o
         if ((rc = btmp.alloc(scan_tmp_bytes(nbk), st)) != MB_OK) break;
         if ((rc = bprim.alloc(8, st)) != MB_OK) break;
         if ((rc = btot.alloc(4 * 8, st)) != MB_OK) break;
-        k_bwt_blocks<<<grid_for(nbk * 32, 256), 256, 0, st>>>(bT.as<u8>(), X->sa, n, X->occ, nbk, bcnt.as<u64>(),
+        k_bwt_blocks<<<grid_for((nbk + 1) / 2 * 32, 256), 256, 0, st>>>(bT.as<u8>(), X->sa, n, X->occ, nbk, bcnt.as<u64>(),
                                                               bprim.as<u64>());
         if (cudaGetLastError() != cudaSuccess) { rc = MB_ERR_CUDA; break; }
         for (int a = 0; a < 4 && rc == MB_OK; ++a)
@@ -552,7 +558,7 @@ extern "C" int mb_index_export(const mb_index *idx, uint32_t *sa, uint8_t *bwt, 
         MB_CK(cudaMemcpy(blk.data(), idx->occ, idx->nblocks * sizeof(OccBlock), cudaMemcpyDeviceToHost));
         std::vector<u8> b(idx->n);
         for (u64 x = 0; x < idx->n; ++x) {
-            u64 w = blk[x >> 7].w[(x & 127) >> 5];
+            u64 w = blk[x >> BLK_SHIFT].w[(x & BLK_MASK) >> 5];
             b[x] = x == idx->primary ? 0 : (u8)(((w >> (2 * (x & 31))) & 3) + 1);
         }
         MB_TRY(copy_out(bwt, b.data(), idx->n));
@@ -597,7 +603,7 @@ extern "C" int mb_index_save(const mb_index *idx, const char *path) {
     FileHeader h;
     memset(&h, 0, sizeof h);
     h.magic = MAGIC;
-    h.version = 1;
+    h.version = 2;
     h.n = idx->n;
     h.rlen = idx->rlen;
     h.primary = idx->primary;
@@ -640,8 +646,8 @@ extern "C" int mb_index_load(const char *path, void *stream, mb_index **out) {
         mb_set_error("mb_index_load: short header");
         return MB_ERR_CORRUPT;
     }
-    if (h.magic != MAGIC || h.version != 1 || h.sa_rate == 0 || h.kmer_k > 12 || h.n >= (1ULL << 32) ||
-        h.nblocks != h.n / 128 + 1) {
+    if (h.magic != MAGIC || h.version != 2 || h.sa_rate == 0 || h.kmer_k > 12 || h.n >= (1ULL << 32) ||
+        h.nblocks != h.n / BLK_ROWS + 1) {
         fclose(f);
         mb_set_error("mb_index_load: bad header");
         return MB_ERR_CORRUPT;

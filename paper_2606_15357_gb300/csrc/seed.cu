@@ -38,7 +38,7 @@ struct Work {
     __device__ __forceinline__ void ext(u64 p, u64 s) {
         if (ON) {
             ++steps;
-            blocks += (p >> 7) == ((p + s) >> 7) ? 1 : 2;
+            blocks += (p >> BLK_SHIFT) == ((p + s) >> BLK_SHIFT) ? 1 : 2;
         }
     }
     __device__ __forceinline__ void flush(u64 *wc) {
@@ -563,7 +563,7 @@ __global__ void __launch_bounds__(256) k_locate(DevIndex I, const u32 *__restric
         u32 sv = 0;
         if (stop && sampled) sv = __ldg(&I.ssa[POW2 ? (row >> rshift) : row / r]);
         Blk b;
-        if (live && !stop) b = load_blk(I.occ + (row >> 7));
+        if (live && !stop) b = load_blk(I.occ + (row >> BLK_SHIFT));
         if (stop) {
             hits[h] = steps > n ? 0xFFFFFFFFu : (sampled ? sv + steps : steps);
             work.lf += steps;

@@ -38,12 +38,13 @@ def compare_index(G, X, k=10):
     assert np.array_equal(e["bwt"], X.bwt())
     assert np.array_equal(e["ssa"], X.ssa())
     assert np.array_equal(e["C"], X.C)
-    # block counts: #a in B[0, 128b) excluding $
+    # block counts: #a in B[0, 64b) excluding $ (32-byte blocks: four u32 counts, two u64 words)
     B = X.bwt()
-    occ = e["occ"].reshape(-1, 8)
+    occ = e["occ"].view(np.uint32).reshape(-1, 8)
+    assert len(occ) == X.n // 64 + 1
     for a in range(4):
         cum = np.concatenate([[0], np.cumsum(B == a + 1)])
-        assert np.array_equal(occ[:, a], cum[np.arange(len(occ)) * 128].astype(np.uint64))
+        assert np.array_equal(occ[:, a].astype(np.uint64), cum[np.arange(len(occ)) * 64].astype(np.uint64))
     # k-mer table against the definition
     nk = 4 ** k
     words = np.arange(nk, dtype=np.int64)
