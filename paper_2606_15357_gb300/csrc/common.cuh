@@ -25,6 +25,10 @@ void mb_set_error(const char *fmt, ...);
         if (r_ != MB_OK) return r_;  \
     } while (0)
 
+// Keep freed stream-ordered memory in the device's pool between calls (the default threshold of 0
+// hands it back to the driver at every synchronization, so each call would map its scratch again).
+void mb_keep_pool_memory();
+
 // Stream-ordered device buffer owned by host code.  Freed on the stream it was made on.
 struct DevBuf {
     void *p = nullptr;
@@ -39,6 +43,7 @@ struct DevBuf {
         st = s;
         bytes = b;
         if (b == 0) return MB_OK;
+        mb_keep_pool_memory();
         cudaError_t e = cudaMallocAsync(&p, b, s);
         if (e != cudaSuccess) {
             p = nullptr;

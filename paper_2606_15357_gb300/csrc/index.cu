@@ -313,6 +313,19 @@ extern "C" void mb_work_counters(uint64_t *ext_steps, uint64_t *ext_blocks, uint
     if (sa_reads) *sa_reads = v[WC_SA_READS];
 }
 
+void mb_keep_pool_memory() {
+    static thread_local int done_dev = -1;
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || d == done_dev) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, d) == cudaSuccess) {
+        u64 thr = ~0ULL;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    done_dev = d;
+}
+
 bool mb_is_device_ptr(const void *p) {
     if (!p) return false;
     cudaPointerAttributes a;

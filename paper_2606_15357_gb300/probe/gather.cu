@@ -6,7 +6,7 @@
 //           pattern of an LF-walk (latency-bound ceiling at full occupancy)
 //   mode 2: as mode 1 with loads cached in L2 only (ld.global.cg)
 // Blocks are 64 bytes (two 256-bit loads) or 32 bytes (one), at random 64-byte-aligned places
-// of a buffer of `bytes` bytes (block index = high 64 bits of hash * number of blocks).
+// of a buffer of `bytes` bytes (fewer than 2^32 blocks).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -14,10 +14,19 @@ typedef uint64_t u64;
 
 namespace {
 
-__device__ __forceinline__ u64 mix(u64 z) {
+__device__ __forceinline__ u64 mix(u64 z) {   // 64-bit hash: only used to fill the buffer
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
     return z ^ (z >> 31);
+}
+// 32-bit hash (a few integer ops) and block index = high half of hash * number of blocks, so the
+// probe's own arithmetic stays far below its memory traffic
+__device__ __forceinline__ uint32_t h32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7FEB352Du;
+    x ^= x >> 15;
+    x *= 0x846CA68Bu;
+    return x ^ (x >> 16);
 }
 
 // CG = false: non-coherent path, cached in L1; CG = true: cached in L2 only
@@ -47,7 +56,7 @@ __global__ void __launch_bounds__(256) k_indep(const u64 *buf, u64 nblocks, unsi
     for (unsigned it = 0; it < iters; it += 8) {
         u64 idx[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) idx[u] = __umul64hi(mix(tid * 0x9E3779B97F4A7C15ULL + it + u), nblocks);
+        for (int u = 0; u < 8; ++u) idx[u] = __umulhi(h32((uint32_t)tid * 0x9E3779B9u + it * 8 + u), (uint32_t)nblocks);
 #pragma unroll
         for (int u = 0; u < 8; ++u) acc ^= ld_block<BYTES>(buf + idx[u] * 8);
     }
@@ -57,8 +66,9 @@ __global__ void __launch_bounds__(256) k_indep(const u64 *buf, u64 nblocks, unsi
 template <int BYTES, bool CG = false>
 __global__ void __launch_bounds__(256) k_chain(const u64 *buf, u64 nblocks, unsigned iters, u64 *sink) {
     const u64 tid = blockIdx.x * (u64)blockDim.x + threadIdx.x;
-    u64 idx = __umul64hi(mix(tid), nblocks);
-    for (unsigned it = 0; it < iters; ++it) idx = __umul64hi(mix(ld_block<BYTES, CG>(buf + idx * 8) ^ it), nblocks);
+    u64 idx = __umulhi(h32((uint32_t)tid), (uint32_t)nblocks);
+    for (unsigned it = 0; it < iters; ++it)
+        idx = __umulhi(h32((uint32_t)ld_block<BYTES, CG>(buf + idx * 8) ^ it), (uint32_t)nblocks);
     if (idx == 0x1234567) sink[tid & 1023] = idx;
 }
 
@@ -67,6 +77,7 @@ __global__ void __launch_bounds__(256) k_chain(const u64 *buf, u64 nblocks, unsi
 // Returns the achieved rate in GB/s (bytes actually requested: BYTES per read), or a negative
 // value on a CUDA error.  `ms` receives the kernel time.
 extern "C" double mb_probe_gather(uint64_t bytes, int mode, int block_bytes, unsigned iters, float *ms) {
+    if (bytes / 64 >= (1ull << 32)) return -3;
     u64 *buf = nullptr, *sink = nullptr;
     if (cudaMalloc(&buf, bytes) != cudaSuccess) return -1;
     if (cudaMalloc(&sink, 1024 * 8) != cudaSuccess) { cudaFree(buf); return -1; }

@@ -293,3 +293,24 @@ def test_bisulfite_index_and_filter():
     assert set(segs[rmate[keep] == 1].tolist()) <= {0, 2}
     assert set(segs[rmate[keep] == 2].tolist()) <= {1, 3}
     assert keep.sum() > 0
+
+
+def test_second_round_windows_by_brute_force():
+    """Section 2.7: the second round's SMEMs of each window equal brute force on that window."""
+    ref = synth.repeat_rich_reference(6000, 41, 0.5)
+    X = oracle.Index(ref)
+    T = X.text()
+    rd = synth.reads(ref, 40, 42, mode=0, read_len=120, sub_lo=0.01)
+    sm1 = X.smem(rd.seq, rd.off, 19, 1)
+    sm2, over, hoff, hits = oracle.reseed(X, rd.seq, rd.off, sm1)
+    wins = [x for x in sm1 if int(x["qend"]) - int(x["qbeg"]) >= 38 and int(x["s"]) <= 10]
+    assert wins
+    want = []
+    for x in wins:
+        r, b, e, s = int(x["read"]), int(x["qbeg"]), int(x["qend"]), int(x["s"])
+        w = rd.seq[int(rd.off[r]) + b:int(rd.off[r]) + e]
+        got = oracle.smem_brute(T, w, np.array([0, len(w)], np.uint64), (e - b) // 2, s + 1)
+        want += [(r, int(y["qbeg"]) + b, int(y["qend"]) + b, int(y["k"]), int(y["kr"]), int(y["s"])) for y in got]
+    have = [tuple(int(y[f]) for f in ("read", "qbeg", "qend", "k", "kr", "s")) for y in sm2]
+    assert have == want
+    assert all(int(y["s"]) >= 2 for y in sm2)
