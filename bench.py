@@ -404,6 +404,10 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     st = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    l2_default = mb.set_l2_fetch_granularity(0)
+    l2_fetch = mb.set_l2_fetch_granularity(args.l2_fetch) if args.l2_fetch else l2_default
+    log(f"L2 fetch granularity: default {l2_default} B, in use {l2_fetch} B")
 
     ref, rd, params = make_inputs(args.workload, args.scale, rank, args.reads)
     opts = dict(min_len=params["min_len"], min_occ=params["min_occ"], max_occ=params["max_occ"],
@@ -536,7 +540,7 @@ def run_gpu(args):
                             "locate": {"ms_per_launch": loc_ms / max(loc_n, 1), "bytes": loc_bytes,
                                        "GBps": loc_bytes / max(loc_ms / max(loc_n, 1), 1e-9) / 1e6}}}
 
-    if not args.no_probe:
+    if args.probe:
         gc = gather_ceiling(args.probe_gib)
         roofline["gather_ceiling"] = gc
         g = gc.get("random64_chain_GBps", 0)
@@ -599,7 +603,7 @@ def run_gpu(args):
                    "pairs_per_step": n_reads // 2, "min_len": params["min_len"], "max_occ": params["max_occ"],
                    "sa_rate": params["sa_rate"], "parallelism": f"replicas{ws}",
                    "l2": "inputs larger than L2 (reads 3 GB, index 1.25 GB)",
-                   "occ_block_bytes": BLOCK_BYTES,
+                   "occ_block_bytes": BLOCK_BYTES, "l2_fetch_granularity": l2_fetch,
                    "smem_per_step": m, "hits_per_step": nh, "index_build_s": build_s},
         "smems_per_s": ws * args.steps * m / (ms / 1000.0),
         "hits_per_s": ws * args.steps * nh / (ms / 1000.0),
@@ -628,7 +632,10 @@ def main():
     ap.add_argument("--ref-step-s", type=float, default=8.0, help="reference arm: seconds per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-probe", action="store_true", help="skip the random-gather ceiling probe")
+    ap.add_argument("--no-probe", action="store_true", help="(default) skip the random-gather probe")
+    ap.add_argument("--probe", action="store_true", help="run the random-gather probe")
+    ap.add_argument("--l2-fetch", type=int, default=32,
+                    help="L2 fetch granularity for this process (32/64/128; 0 = leave the default)")
     ap.add_argument("--no-batched", action="store_true", help="skip the mixed-length batched comparison")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-form measurement")
     ap.add_argument("--serve-requests", type=int, default=600)

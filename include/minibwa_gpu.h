@@ -264,6 +264,14 @@ int mb_bs_filter(const mb_index *idx, const mb_smem *smem, uint64_t n_smem, cons
 int mb_hit_to_ref(const mb_index *idx, uint64_t pos, uint64_t len, int *strand, uint64_t *rpos);
 
 const char *mb_strerror(int code);
+
+/* Set the L2 fetch granularity of the calling process's CUDA context on the current device
+ * (cudaLimitMaxL2FetchGranularity; 32, 64 or 128 bytes; 0 leaves it unchanged) and return the
+ * value in force in *now.  Every block access of the seeding kernels is a random 32-byte read;
+ * with a larger granularity the L2 fetches the rest of the line from DRAM for nothing.  The
+ * limit belongs to this process's context only (other processes and later users of the GPU are
+ * not affected) but it applies to every kernel of this process.  No counterpart in the paper. */
+int mb_set_l2_fetch_granularity(int bytes, int *now);
 /* Detail of the last error of this library (host-side message), for diagnostics. */
 const char *mb_last_error(void);
 

@@ -91,6 +91,7 @@ def lib():
                 "mb_serve_release": ([P, U64], I),
                 "mb_serve_destroy": ([P], I),
                 "mb_serve_stats": ([P, ctypes.POINTER(U32), PU64, PU64], I),
+                "mb_set_l2_fetch_granularity": ([I, ctypes.POINTER(I)], I),
                 "mb_profile_enable": ([I], None),
                 "mb_profile_get": ([ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), PU64], I),
                 "mb_profile_reset": ([], None),
@@ -449,3 +450,11 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def set_l2_fetch_granularity(nbytes: int = 32) -> int:
+    """cudaLimitMaxL2FetchGranularity of this process's context (0 = query); returns the value
+    in force."""
+    now = ctypes.c_int()
+    _check(lib().mb_set_l2_fetch_granularity(nbytes, ctypes.byref(now)), "mb_set_l2_fetch_granularity")
+    return now.value

@@ -724,6 +724,17 @@ extern "C" int mb_hit_to_ref(const mb_index *idx, uint64_t pos, uint64_t len, in
     return MB_OK;
 }
 
+extern "C" int mb_set_l2_fetch_granularity(int bytes, int *now) {
+    if (bytes != 0 && bytes != 32 && bytes != 64 && bytes != 128) return MB_ERR_ARG;
+    if (bytes) MB_CK(cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)bytes));
+    if (now) {
+        size_t v = 0;
+        MB_CK(cudaDeviceGetLimit(&v, cudaLimitMaxL2FetchGranularity));
+        *now = (int)v;
+    }
+    return MB_OK;
+}
+
 extern "C" const char *mb_strerror(int code) {
     switch (code) {
     case MB_OK: return "ok";

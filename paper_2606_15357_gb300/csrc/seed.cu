@@ -528,13 +528,14 @@ __global__ void k_expand_rows(const mb_smem *__restrict__ sm, u64 nsm, const u64
     }
 }
 
-// Locate (Algorithm 2).  Each lane LF-walks one row at a time, one step per loop iteration; a
-// lane whose walk ends takes the next row of its warp's range at once (rows are prefetched 64
-// ahead, two coalesced buffers, and handed over by shuffle).  A walk ends on a sampled row
-// (position = steps + S(row)) or on the $ row (S = 0, position = steps).  The sampled-SA read
-// and the block read of the other lanes are issued in the same iteration.  A walk needs fewer
-// than n steps; the bound only guards against a corrupted index (it then writes 0xFFFFFFFF).
-template <bool COUNT, bool POW2>
+// Locate (Algorithm 2).  Each lane LF-walks D rows at a time (D independent block reads in
+// flight per lane), one step of each per loop iteration; a walk that ends is replaced at once by
+// the next row of the warp's range (rows are prefetched 64 ahead, two coalesced buffers, and
+// handed over by shuffle).  A walk ends on a sampled row (position = steps + S(row)) or on the $
+// row (S = 0, position = steps).  The sampled-SA reads and the block reads of one iteration are
+// issued together.  A walk needs fewer than n steps; the bound only guards against a corrupted
+// index (it then writes 0xFFFFFFFF).
+template <bool COUNT, bool POW2, int D>
 __global__ void __launch_bounds__(256) k_locate(DevIndex I, const u32 *__restrict__ rows, u64 nhits,
                                                 const u64 *__restrict__ nhits_dev, u32 *__restrict__ hits, u64 *wc) {
     const u32 lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
@@ -545,50 +546,64 @@ __global__ void __launch_bounds__(256) k_locate(DevIndex I, const u32 *__restric
     WarpRange wr;
     wr.init(nhits);
     // rows of the range, 64 ahead: buf0 holds rows[bufbase + lane], buf1 rows[bufbase + 32 + lane];
-    // at the top of every iteration bufbase <= wr.next < bufbase + 32.
+    // before every hand-over bufbase <= wr.next < bufbase + 32.
     u64 bufbase = wr.next;
     u32 buf0 = bufbase + lane < wr.end ? __ldg(&rows[bufbase + lane]) : 0u;
     u32 buf1 = bufbase + 32 + lane < wr.end ? __ldg(&rows[bufbase + 32 + lane]) : 0u;
-    u64 h = wr.next + lane;
-    bool live = h < wr.end;
-    u32 row = buf0, steps = 0;
-    wr.next += 32;
-    bufbase += 32;
-    buf0 = buf1;
-    buf1 = bufbase + 32 + lane < wr.end ? __ldg(&rows[bufbase + 32 + lane]) : 0u;
-    for (;;) {
-        if (__all_sync(0xffffffffu, !live)) break;
-        const bool sampled = POW2 ? (row & rmask) == 0 : row % r == 0;
-        const bool stop = live && (sampled || row == prim || steps > n);
-        u32 sv = 0;
-        if (stop && sampled) sv = __ldg(&I.ssa[POW2 ? (row >> rshift) : row / r]);
-        Blk b;
-        if (live && !stop) b = load_blk(I.occ + (row >> BLK_SHIFT));
-        if (stop) {
-            hits[h] = steps > n ? 0xFFFFFFFFu : (sampled ? sv + steps : steps);
-            work.lf += steps;
-            work.sa += sampled ? 1 : 0;
-        } else if (live) {
-            row = lf_blk(b, row, prim, C0, C1, C2, C3);
-            ++steps;
+    u64 h[D];
+    bool live[D];
+    u32 row[D], steps[D];
+    // hands the next items of the range to the lanes in `fm` (in lane order), walk slot d
+    auto hand_over = [&](u32 fm, bool mine, int d) {
+        const u64 idx = wr.next + __popc(fm & lt);
+        const u32 o = (u32)(idx - bufbase);   // < 64
+        const u32 v0 = __shfl_sync(0xffffffffu, buf0, o & 31), v1 = __shfl_sync(0xffffffffu, buf1, o & 31);
+        if (mine) {
+            h[d] = idx;
+            live[d] = idx < wr.end;
+            row[d] = o < 32 ? v0 : v1;
+            steps[d] = 0;
         }
-        const u32 fm = __ballot_sync(0xffffffffu, stop);
-        if (fm) {
-            const u64 idx = wr.next + __popc(fm & lt);
-            const u32 o = (u32)(idx - bufbase);   // < 64 while both buffers cover wr.next..+63
-            const u32 v0 = __shfl_sync(0xffffffffu, buf0, o & 31), v1 = __shfl_sync(0xffffffffu, buf1, o & 31);
-            if (stop) {
-                h = idx;
-                live = h < wr.end;
-                row = o < 32 ? v0 : v1;
-                steps = 0;
+        wr.next += __popc(fm);
+        if (wr.next >= bufbase + 32) {     // first buffer used up: slide by 32
+            bufbase += 32;
+            buf0 = buf1;
+            buf1 = bufbase + 32 + lane < wr.end ? __ldg(&rows[bufbase + 32 + lane]) : 0u;
+        }
+    };
+#pragma unroll
+    for (int d = 0; d < D; ++d) hand_over(0xffffffffu, true, d);
+    for (;;) {
+        bool any = false;
+#pragma unroll
+        for (int d = 0; d < D; ++d) any |= live[d];
+        if (__all_sync(0xffffffffu, !any)) break;
+        bool stop[D], sampled[D];
+        u32 sv[D];
+        Blk b[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            sampled[d] = POW2 ? (row[d] & rmask) == 0 : row[d] % r == 0;
+            stop[d] = live[d] && (sampled[d] || row[d] == prim || steps[d] > n);
+            sv[d] = 0;
+            if (stop[d] && sampled[d]) sv[d] = __ldg(&I.ssa[POW2 ? (row[d] >> rshift) : row[d] / r]);
+            if (live[d] && !stop[d]) b[d] = load_blk(I.occ + (row[d] >> BLK_SHIFT));
+        }
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            if (stop[d]) {
+                hits[h[d]] = steps[d] > n ? 0xFFFFFFFFu : (sampled[d] ? sv[d] + steps[d] : steps[d]);
+                work.lf += steps[d];
+                work.sa += sampled[d] ? 1 : 0;
+            } else if (live[d]) {
+                row[d] = lf_blk(b[d], row[d], prim, C0, C1, C2, C3);
+                ++steps[d];
             }
-            wr.next += __popc(fm);
-            if (wr.next >= bufbase + 32) {     // first buffer used up: slide by 32
-                bufbase += 32;
-                buf0 = buf1;
-                buf1 = bufbase + 32 + lane < wr.end ? __ldg(&rows[bufbase + 32 + lane]) : 0u;
-            }
+        }
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const u32 fm = __ballot_sync(0xffffffffu, stop[d]);
+            if (fm) hand_over(fm, stop[d], d);
         }
     }
     work.flush(wc);
@@ -639,6 +654,26 @@ int launch_smem_t(const SmemArgs &a, cudaStream_t st) {
                                                      a.wc, a.lc);
     MB_KCHECK();
     return MB_OK;
+}
+
+template <bool COUNT, bool POW2, int D>
+int launch_locate_t(const DevIndex &I, const u32 *rows, u64 nhits, const u64 *nhits_dev, u32 *hits, u64 *wc,
+                    cudaStream_t st) {
+    const unsigned g = resident_grid((const void *)k_locate<COUNT, POW2, D>, 256, (nhits + 63) / 64 * 32);
+    k_locate<COUNT, POW2, D><<<g, 256, 0, st>>>(I, rows, nhits, nhits_dev, hits, wc);
+    MB_KCHECK();
+    return MB_OK;
+}
+
+// The locate kernel: work counters, power-of-two sample rate, walks per lane (depth 1 or 2).
+int launch_locate(const DevIndex &I, const u32 *rows, u64 nhits, const u64 *nhits_dev, u32 *hits, u64 *wc,
+                  bool count, u32 depth, cudaStream_t st) {
+    const bool pow2 = (I.r & (I.r - 1)) == 0;
+    if (count) return pow2 ? launch_locate_t<true, true, 1>(I, rows, nhits, nhits_dev, hits, wc, st)
+                           : launch_locate_t<true, false, 1>(I, rows, nhits, nhits_dev, hits, wc, st);
+    if (!pow2) return launch_locate_t<false, false, 1>(I, rows, nhits, nhits_dev, hits, wc, st);
+    if (depth >= 2) return launch_locate_t<false, true, 2>(I, rows, nhits, nhits_dev, hits, wc, st);
+    return launch_locate_t<false, true, 1>(I, rows, nhits, nhits_dev, hits, wc, st);
 }
 
 // The SMEM kernel in the requested shape: work counters, work queue, threads per block.
@@ -806,16 +841,10 @@ extern "C" int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_sm
     k_expand_rows<<<grid_for(n_smem, 256), 256, 0, st>>>((const mb_smem *)dsm, n_smem, nullptr, brows.as<u32>(),
                                                          total);
     MB_KCHECK();
-    const void *kfn = count ? (pow2 ? (const void *)k_locate<true, true> : (const void *)k_locate<true, false>)
-                            : (pow2 ? (const void *)k_locate<false, true> : (const void *)k_locate<false, false>);
-    const unsigned G = resident_grid(kfn, 256, (total + 63) / 64 * 32);
     u64 *wc = count ? mb_work_counter_buf(st) : nullptr;
     KTimer kt("locate", st);
     kt.start();
-    if (count && pow2) k_locate<true, true><<<G, 256, 0, st>>>(I, brows.as<u32>(), total, nullptr, dh, wc);
-    else if (count) k_locate<true, false><<<G, 256, 0, st>>>(I, brows.as<u32>(), total, nullptr, dh, wc);
-    else if (pow2) k_locate<false, true><<<G, 256, 0, st>>>(I, brows.as<u32>(), total, nullptr, dh, nullptr);
-    else k_locate<false, false><<<G, 256, 0, st>>>(I, brows.as<u32>(), total, nullptr, dh, nullptr);
+    MB_TRY(launch_locate(I, brows.as<u32>(), total, nullptr, dh, wc, count, opts ? opts->prefetch_depth : 0, st));
     kt.stop();
     MB_KCHECK();
     if (!hdev) MB_CK(cudaMemcpyAsync(hits, dh, total * 4, cudaMemcpyDeviceToHost, st));
@@ -1011,6 +1040,7 @@ struct mb_plan {
     u32 l = 19, c = 1, max_occ = 500, flags = 0;
     bool kmer = true, queue = false;
     int block = 256;
+    u32 depth = 1;   // walks per lane in locate
     u32 max_reads = 0;
     u64 max_bases = 0, max_smem = 0, max_hits = 0, nslots = 0;
     void *mem = nullptr;
@@ -1049,6 +1079,7 @@ extern "C" int mb_plan_create(const mb_index *idx, const mb_opts *opts, uint32_t
     P->kmer = !(P->flags & MB_NO_KMER) && P->l >= mb_dev_index(idx).kmer_k;
     P->queue = (P->flags & MB_BATCHED) != 0;
     P->block = opts && (opts->block_size == 128 || opts->block_size == 512) ? (int)opts->block_size : 256;
+    P->depth = opts && opts->prefetch_depth >= 2 ? 2u : 1u;
     P->max_reads = max_reads;
     P->max_bases = max_bases;
     P->max_smem = max_smem ? max_smem : 1;
@@ -1130,12 +1161,7 @@ extern "C" int mb_plan_run(mb_plan *P, const uint8_t *seq, const uint64_t *off, 
     MB_KCHECK();
     k_expand_rows<<<grid_for(P->max_smem, 256), 256, 0, st>>>(P->out, P->max_smem, n_smem, P->rows, P->max_hits);
     MB_KCHECK();
-    const bool pow2 = (I.r & (I.r - 1)) == 0;
-    const void *kfn = pow2 ? (const void *)k_locate<false, true> : (const void *)k_locate<false, false>;
-    const unsigned GL = resident_grid(kfn, 256, (P->max_hits + 63) / 64 * 32);
-    if (pow2) k_locate<false, true><<<GL, 256, 0, st>>>(I, P->rows, P->max_hits, n_hits, P->hits, nullptr);
-    else k_locate<false, false><<<GL, 256, 0, st>>>(I, P->rows, P->max_hits, n_hits, P->hits, nullptr);
-    MB_KCHECK();
+    MB_TRY(launch_locate(I, P->rows, P->max_hits, n_hits, P->hits, nullptr, false, P->depth, st));
     return MB_OK;
 }
 
@@ -1243,10 +1269,12 @@ extern "C" int mb_autotune(const mb_index *idx, const uint8_t *seq, const uint64
     MB_CK(cudaEventCreate(&b));
     int rc = MB_OK;
     for (int q = 0; q < 2 && rc == MB_OK; ++q)
-        for (int bi = 0; bi < 3 && rc == MB_OK; ++bi) {
+        for (int bi = 0; bi < 3 && rc == MB_OK; ++bi)
+        for (int dep = 1; dep <= 2 && rc == MB_OK; ++dep) {
             mb_opts o = opts ? *opts : mb_opts{};
             o.flags = (o.flags & ~MB_BATCHED) | (q ? MB_BATCHED : 0u);
             o.block_size = (u32)blocks[bi];
+            o.prefetch_depth = (u32)dep;
             mb_plan *P = nullptr;
             rc = mb_plan_create(idx, &o, n_reads, o1 - o0, n_smem, n_hits, &P);
             if (rc != MB_OK) break;

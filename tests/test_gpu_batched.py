@@ -43,11 +43,12 @@ def test_plain_matches_oracle(mb, mixed):
     assert np.array_equal(hits.astype(np.uint64), ohits)
 
 
+@pytest.mark.parametrize("depth", [1, 2])
 @pytest.mark.parametrize("queue", [False, True])
 @pytest.mark.parametrize("block", [128, 256, 512])
-def test_plan_every_launch_shape(mb, mixed, queue, block):
+def test_plan_every_launch_shape(mb, mixed, queue, block, depth):
     ref, rd, G, sm, hits = mixed
-    o = dict(flags=mb.MB_BATCHED if queue else 0, block_size=block)
+    o = dict(flags=mb.MB_BATCHED if queue else 0, block_size=block, prefetch_depth=depth)
     P = mb.Plan(G, rd.n, len(rd.seq), len(sm) + 10, len(hits) + 10, opts=o)
     P.run(dev(rd.seq), dev(rd.off))
     psm, phits = P.result()

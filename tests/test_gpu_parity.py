@@ -99,6 +99,17 @@ def test_workload1_full(mb):
     compare_seed(sm, hits, X, rd.seq, rd.off)
 
 
+@pytest.mark.parametrize("depth", [1, 2])
+def test_locate_walks_per_lane(mb, depth):
+    """Locate with one or two LF-walks in flight per lane gives the same hits."""
+    ref, rd, p = synth.workload(2, scale=0.01)
+    G = mb.mb_index_build(ref)
+    X = oracle.Index(ref)
+    sm, m, nh = mb.mb_seed_batch(G, rd.seq, rd.off)
+    hits, _ = mb.mb_locate(G, sm, m, opts=dict(prefetch_depth=depth), cap=nh)
+    compare_seed(sm, hits, X, rd.seq, rd.off)
+
+
 def test_workload2_scaled_device_pointers(mb):
     """Repeat-rich reference with N runs, paired 2x150 reads with indels; device buffers."""
     ref, rd, p = synth.workload(2, scale=0.02)
