@@ -307,7 +307,8 @@ def bench_batched(mb, torch, dev, reps: int = 3):
             "reads": rd.n, "bases": int(len(rd.seq)), "smems": n_smem, "hits": n_hits,
             "plain_per_bucket_reads_per_s": rd.n / plain_s, "batched_graph_reads_per_s": rd.n / batched_s,
             "speedup": plain_s / batched_s, "identical_output": bool(same),
-            "autotuned": {"block_size": best.block_size, "work_queue": bool(best.flags & mb.MB_BATCHED)},
+            "autotuned": {"block_size": best.block_size, "work_queue": bool(best.flags & mb.MB_BATCHED),
+                          "locate_walks_per_lane": best.prefetch_depth},
             "plain_ms": plain_s * 1000, "batched_ms": batched_s * 1000}
 
 
@@ -451,11 +452,13 @@ def run_gpu(args):
     # autotune the launch shape on a sample of the batch, then use it for both forms
     ns = min(n_reads, 1_000_000)
     if args.no_autotune:
-        best = mb.Opts(block_size=256)
+        best = mb.Opts(block_size=256, prefetch_depth=1)
     else:
         best, tune_ms = mb.autotune(idx, seq[:int(rd.off[ns])], off[:ns + 1], opts=opts)
     opts["block_size"] = best.block_size
-    log(f"autotuned on {ns} reads: block {best.block_size}, work queue {bool(best.flags & mb.MB_BATCHED)}")
+    opts["prefetch_depth"] = best.prefetch_depth
+    log(f"autotuned on {ns} reads: block {best.block_size}, work queue {bool(best.flags & mb.MB_BATCHED)}, "
+        f"locate walks per lane {best.prefetch_depth}")
 
     for _ in range(args.warmup):
         step()
@@ -518,7 +521,8 @@ def run_gpu(args):
              "graph_plan": {"reads_per_s": ws * args.steps * n_reads / (graph_ms / 1000.0),
                             "ms_per_step": graph_ms / args.steps, "identical_output": bool(same),
                             "gpu_launches": graph_launches,
-                            "block_size": best.block_size, "work_queue": bool(best.flags & mb.MB_BATCHED)},
+                            "block_size": best.block_size, "work_queue": bool(best.flags & mb.MB_BATCHED),
+                            "locate_walks_per_lane": best.prefetch_depth},
              "reported": "graph_plan" if use_graph else "plain_launch"}
 
     # roofline of the dominant kernel: algorithmic bytes / its event-timed duration

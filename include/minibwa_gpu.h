@@ -89,16 +89,16 @@ typedef struct {
  *   opts     sa_rate, kmer_k, flags & MB_BS3 are used.
  *   stream   stream for the build.
  *   out      receives the new index (free with mb_index_free).
- * Builds T, its suffix array by prefix doubling, the BWT in 64-byte occurrence
- * blocks (four 64-bit counts of A/C/G/T before the block, then 128 2-bit symbols;
- * Section 2.2), the sampled suffix array and the k-mer ds-interval table.
+ * Builds T, its suffix array by prefix doubling, the BWT in occurrence blocks (Section 2.2;
+ * here 32 bytes per 64 rows: four u32 counts of A/C/G/T before the block, then 64 2-bit
+ * symbols), the sampled suffix array and the k-mer ds-interval table.
  * Errors: MB_ERR_ARG (len = 0, n >= 2^32), MB_ERR_NOMEM, MB_ERR_CUDA.
  */
 int mb_index_build(const uint8_t *ref, uint64_t len, const mb_opts *opts, uint64_t n_seed,
                    void *stream, mb_index **out);
 
-/* Write / read an index file (header with version, sizes and a checksum; 64-byte blocks as in
- * memory, Section 2.2).  Errors: MB_ERR_IO, MB_ERR_CORRUPT (bad header, size or checksum),
+/* Write / read an index file (header with version, sizes and a checksum; the blocks as in
+ * memory).  Errors: MB_ERR_IO, MB_ERR_CORRUPT (bad header, size or checksum),
  * MB_ERR_NOMEM, MB_ERR_CUDA. */
 int mb_index_save(const mb_index *idx, const char *path);
 int mb_index_load(const char *path, void *stream, mb_index **out);
@@ -109,8 +109,10 @@ int mb_index_info(const mb_index *idx, uint64_t *n, uint64_t *primary, uint64_t 
 
 /* Copy index arrays to the caller (host or device): sa (n x u32, full suffix array; only
  * available until mb_index_drop_sa, else MB_ERR_ARG), bwt (n bytes, 0=$ 1..4=A..T),
- * ssa (ceil(n/r) x u32), occ blocks (ceil((n+1)/128) x 64 bytes), kmer table (4^k x 3 u32:
- * k, kr, s), C (5 x u64 = #{B[i] < a} for a = $,A,C,G,T).  Any pointer may be NULL. */
+ * ssa (ceil(n/r) x u32), occ blocks (n/64 + 1 blocks of 32 bytes: four u32 counts of A,C,G,T
+ * before the block, then two u64 words of 2-bit symbols of its 64 rows), kmer table (4^k x 3 u32:
+ * k, kr, s of the k-mer whose base t is in bits 2t..2t+1 of the entry number), C (5 x u64 =
+ * #{B[i] < a} for a = $,A,C,G,T).  Any pointer may be NULL. */
 int mb_index_export(const mb_index *idx, uint32_t *sa, uint8_t *bwt, uint32_t *ssa,
                     void *occ_blocks, uint32_t *kmer, uint64_t *C);
 /* Free the full suffix array kept after the build (it is only needed for mb_index_export). */

@@ -109,7 +109,7 @@ static_assert(sizeof(OccBlock) == 32, "one block per 32-byte sector");
 struct DevIndex {
     const OccBlock *occ;
     const u32 *ssa;     // S(x*r)
-    const u32 *kmer;    // (k, kr, s) of every k-mer, first symbol most significant
+    const u32 *kmer;    // (k, kr, s) of every k-mer, base t of the k-mer in bits 2t..2t+1
     u64 n;              // |T|
     u64 primary;        // row with S = 0
     u64 C[4];           // C[a] = #{i : B[i] < a}, a = A,C,G,T

@@ -187,13 +187,14 @@ __global__ void k_sample_sa(const u32 *__restrict__ SA, u64 n, u32 r, u32 *__res
         ssa[x] = SA[x * r];
 }
 
-// ds-interval of every k-mer by k BackwardExt steps from the empty string (0, 0, n).
+// ds-interval of every k-mer by k BackwardExt steps from the empty string (0, 0, n).  The
+// k-mer of entry w has its t-th base (t = 0 first) in bits 2t..2t+1 of w.
 __global__ void k_kmer_table(DevIndex I, u32 k, u32 *__restrict__ out) {
     u64 nk = 1ULL << (2 * k);
     for (u64 w = blockIdx.x * (u64)blockDim.x + threadIdx.x; w < nk; w += (u64)gridDim.x * blockDim.x) {
         u32 p = 0, q = 0, s = (u32)I.n;
         for (int t = (int)k - 1; t >= 0; --t) {
-            u32 a = (u32)(w >> (2 * (k - 1 - t))) & 3u;
+            u32 a = (u32)(w >> (2 * t)) & 3u;
             Ext e = extend(I, p, q, s, a);
             p = e.p; q = e.q; s = e.s;
         }

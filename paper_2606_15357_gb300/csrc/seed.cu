@@ -105,13 +105,47 @@ __device__ __forceinline__ u32 cached_base(SmemState &S, int j) {
     return b;
 }
 
-// k-mer code of P[j-K+1 .. j] (first base most significant); false if it holds an N
+// Eight bases (bytes 0..3) to their 2-bit codes, first base in the lowest bits (16 bits).
+__device__ __forceinline__ u32 pack8(u64 x) {
+    x = (x | (x >> 6)) & 0x000F000F000F000FULL;
+    x = (x | (x >> 12)) & 0x000000FF000000FFULL;
+    return (u32)((x | (x >> 24)) & 0xFFFFULL);
+}
+// Bisulfite conversion of eight bases at once (conv 1: C(1) -> T(3); conv 2: G(2) -> A(0)).
+__device__ __forceinline__ u64 convert8(u64 x, u32 conv) {
+    const u64 ONES = 0x0101010101010101ULL;
+    if (conv == 1) return x | ((x & ~(x >> 1) & ONES) << 1);
+    if (conv == 2) return x & ~((((x >> 1) & ~x) & ONES) << 1);
+    return x;
+}
+
+// k-mer code of P[j-K+1 .. j] (K <= 12), first base in the lowest bits; false if it holds an N.
+// The K bytes lie in two aligned 16-byte chunks: both are loaded, the K bytes shifted out, and
+// tested, converted and packed eight at a time.  Next to the end of the batch it goes byte by
+// byte.
 __device__ __forceinline__ bool kmer_code(SmemState &S, int j, u32 K, u32 &code) {
+    const int st = j - (int)K + 1;
+    const u8 *a = S.P + st;
+    const u8 *A = (const u8 *)((uintptr_t)a & ~(uintptr_t)15);
+    const u32 o = (u32)(a - A);
+    if ((long long)(A + 32 - S.P) <= (long long)S.lim) {
+        const ulonglong2 c0 = __ldg(reinterpret_cast<const ulonglong2 *>(A));
+        const ulonglong2 c1 = __ldg(reinterpret_cast<const ulonglong2 *>(A + 16));
+        const u64 w0 = o < 8 ? c0.x : c0.y, w1 = o < 8 ? c0.y : c1.x, w2 = o < 8 ? c1.x : c1.y;
+        const u32 sh = 8 * (o & 7);
+        u64 lo = sh ? (w0 >> sh) | (w1 << (64 - sh)) : w0;
+        u64 hi = sh ? (w1 >> sh) | (w2 << (64 - sh)) : w1;
+        lo &= K >= 8 ? ~0ULL : ((1ULL << (8 * K)) - 1);
+        hi &= K > 8 ? ((1ULL << (8 * (K - 8))) - 1) : 0ULL;
+        if (((lo | hi) & 0xFCFCFCFCFCFCFCFCULL) != 0) return false;   // an N (any code > 3)
+        code = pack8(convert8(lo, S.conv)) | (pack8(convert8(hi, S.conv)) << 16);
+        return true;
+    }
     u32 v = 0;
     for (u32 t = 0; t < K; ++t) {
-        u32 b = cached_base(S, j - (int)K + 1 + (int)t);
+        const u32 b = cached_base(S, st + (int)t);
         if (b > 3) return false;
-        v = (v << 2) | b;
+        v |= b << (2 * t);
     }
     code = v;
     return true;

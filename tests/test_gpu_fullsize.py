@@ -64,7 +64,7 @@ def check_index(G, X, k=10, sample_kmers=None):
     words = np.arange(nk, dtype=np.int64)
     if sample_kmers:
         words = np.sort(np.random.default_rng(7).choice(nk, sample_kmers, replace=False))
-    pats = np.stack([(words >> (2 * (k - 1 - t))) & 3 for t in range(k)], axis=1).astype(np.uint8)
+    pats = np.stack([(words >> (2 * t)) & 3 for t in range(k)], axis=1).astype(np.uint8)   # base t in bits 2t
     want = X.ds_intervals(pats).astype(np.uint32)
     got = e["kmer"].reshape(nk, 3)[words]
     assert np.array_equal(got, want)

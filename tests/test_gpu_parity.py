@@ -48,7 +48,7 @@ def compare_index(G, X, k=10):
     # k-mer table against the definition
     nk = 4 ** k
     words = np.arange(nk, dtype=np.int64)
-    pats = np.stack([(words >> (2 * (k - 1 - t))) & 3 for t in range(k)], axis=1).astype(np.uint8)
+    pats = np.stack([(words >> (2 * t)) & 3 for t in range(k)], axis=1).astype(np.uint8)   # base t in bits 2t
     want = X.ds_intervals(pats).astype(np.uint32)
     got = e["kmer"].reshape(nk, 3)
     assert np.array_equal(got, want)
