@@ -204,13 +204,10 @@ __device__ __forceinline__ void occ_a_le(const Blk &b, u32 x, u32 a, u32 primary
     nle = sel4(a, b.c[0], c01, c012, c012 + b.c[3]) + cnt_le(b, m, a) - d;
 }
 
-// One extension: the blocks of rows p and p+s are read once each (once in all when they are the
-// same block).
-__device__ __forceinline__ Ext extend(const DevIndex &I, u32 p, u32 q, u32 s, u32 a) {
+// One extension from the already loaded blocks b0 (of row p) and b1 (of row p+s).
+__device__ __forceinline__ Ext extend_blocks(const DevIndex &I, const Blk &b0, const Blk &b1, u32 p, u32 q, u32 s,
+                                             u32 a) {
     const u32 e = p + s, prim = (u32)I.primary;
-    const Blk b0 = load_blk(I.occ + (p >> BLK_SHIFT));
-    Blk b1 = b0;
-    if ((e >> BLK_SHIFT) != (p >> BLK_SHIFT)) b1 = load_blk(I.occ + (e >> BLK_SHIFT));
     u32 na0, nle0, na1, nle1;
     occ_a_le(b0, p, a, prim, na0, nle0);
     occ_a_le(b1, e, a, prim, na1, nle1);
@@ -219,6 +216,16 @@ __device__ __forceinline__ Ext extend(const DevIndex &I, u32 p, u32 q, u32 s, u3
     r.p = sel4(a, (u32)I.C[0], (u32)I.C[1], (u32)I.C[2], (u32)I.C[3]) + na0;
     r.q = q + s - (nle1 - nle0);
     return r;
+}
+
+// One extension: the blocks of rows p and p+s are read once each (once in all when they are the
+// same block).
+__device__ __forceinline__ Ext extend(const DevIndex &I, u32 p, u32 q, u32 s, u32 a) {
+    const u32 e = p + s;
+    const Blk b0 = load_blk(I.occ + (p >> BLK_SHIFT));
+    Blk b1 = b0;
+    if ((e >> BLK_SHIFT) != (p >> BLK_SHIFT)) b1 = load_blk(I.occ + (e >> BLK_SHIFT));
+    return extend_blocks(I, b0, b1, p, q, s, a);
 }
 
 // splitmix64 output function; bits 63..62 give the base replacing an ambiguous reference base.

@@ -151,27 +151,30 @@ __device__ __forceinline__ bool kmer_code(SmemState &S, int j, u32 K, u32 &code)
     return true;
 }
 
-// Moves through the steps of Algorithm 3 that need no occurrence block.  Returns true when the
-// next step is an extension of P[j] (backward in stages 1 and 3, forward in stage 2), false when
-// the read is finished.  SMEMs found on the way go to emit.
+// What a lane does with memory in one step of Algorithm 3.
+enum { ACT_NONE = 0, ACT_EXT = 1, ACT_KMER = 2 };
+
+// Moves through the steps of Algorithm 3 that need no memory and picks the next memory action:
+// ACT_EXT, an extension of P[j] (backward in stages 1 and 3, forward in stage 2); ACT_KMER, a
+// k-mer table lookup (its code in `code`); ACT_NONE, the read is finished.  SMEMs found on the
+// way go to emit.
 //
 // With the k-mer table (Section 2.5), the first K backward steps from the empty string are one
 // table lookup: the table holds exactly the interval those K BackwardExt steps give.  In stage 1
 // a failing k-mer P[x, x+K) restarts the scan at x+1, no further than Algorithm 3's own restart
 // (every window starting at or before x contains that k-mer, so none is a match); in stage 3 the
 // restart point must be exact, so a failing k-mer falls back to single steps.
-template <class Emit, class W>
-__device__ __forceinline__ bool smem_advance(SmemState &S, const DevIndex &I, u32 l, u32 c, bool kmer, Emit &emit,
-                                             W &work) {
+template <class Emit>
+__device__ __forceinline__ int smem_next(SmemState &S, const DevIndex &I, u32 l, bool kmer, Emit &emit, u32 &code) {
     const u32 n = (u32)I.n, K = I.kmer_k;
     for (;;) {
         if (S.u == 2) {
             if (S.j == S.L) {                       // reached the end of P
                 emit(S.i, S.j, S.k, S.kr, S.s);
                 S.u = 0;
-                return false;
+                return ACT_NONE;
             }
-            return true;
+            return ACT_EXT;
         }
         if (S.u == 1) {
             if (S.j < S.i) {                        // P[i, i+l) is a match: stage 2
@@ -179,26 +182,8 @@ __device__ __forceinline__ bool smem_advance(SmemState &S, const DevIndex &I, u3
                 S.j = S.i + (int)l;
                 continue;
             }
-            u32 code;
-            if (kmer && l >= K && S.s == n && kmer_code(S, S.j, K, code)) {
-                const u32 *e = I.kmer + 3 * (u64)code;
-                u32 tk = __ldg(e), tkr = __ldg(e + 1), ts = __ldg(e + 2);
-                work.kmer += 1;
-                if (ts >= c) {
-                    S.k = tk; S.kr = tkr; S.s = ts;
-                    S.j -= (int)K;
-                    continue;
-                }
-                const int x = S.j - (int)K + 1;
-                if (x + (int)l < S.L) {
-                    S.i = x + 1;
-                    S.j = x + (int)l;
-                    continue;
-                }
-                S.u = 0;
-                return false;
-            }
-            return true;
+            if (kmer && l >= K && S.s == n && kmer_code(S, S.j, K, code)) return ACT_KMER;
+            return ACT_EXT;
         }
         if (S.u == 3) {
             if (S.j <= S.i) {                       // back to stage 1 at the next start
@@ -208,22 +193,33 @@ __device__ __forceinline__ bool smem_advance(SmemState &S, const DevIndex &I, u3
                 S.k = 0; S.kr = 0; S.s = n;
                 continue;
             }
-            u32 code;
             if (kmer && !S.tried && S.s == n && S.j - (int)K + 1 > S.i && kmer_code(S, S.j, K, code)) {
                 S.tried = true;
-                const u32 *e = I.kmer + 3 * (u64)code;
-                u32 tk = __ldg(e), tkr = __ldg(e + 1), ts = __ldg(e + 2);
-                work.kmer += 1;
-                if (ts >= c) {
-                    S.k = tk; S.kr = tkr; S.s = ts;
-                    S.j -= (int)K;
-                    continue;
-                }
+                return ACT_KMER;
             }
-            return true;
+            return ACT_EXT;
         }
-        return false;
+        return ACT_NONE;
     }
+}
+
+// Applies a k-mer table entry (tk, tkr, ts) looked up in stage 1 or 3.  Returns false when the
+// read is finished.
+__device__ __forceinline__ bool smem_apply_kmer(SmemState &S, u32 tk, u32 tkr, u32 ts, u32 l, u32 c, u32 K) {
+    if (ts >= c) {                                  // the K steps all succeed
+        S.k = tk; S.kr = tkr; S.s = ts;
+        S.j -= (int)K;
+        return true;
+    }
+    if (S.u == 3) return true;                      // stage 3: step one base at a time instead
+    const int x = S.j - (int)K + 1;                 // stage 1: restart after the k-mer's first base
+    if (x + (int)l < S.L) {
+        S.i = x + 1;
+        S.j = x + (int)l;
+        return true;
+    }
+    S.u = 0;
+    return false;
 }
 
 // Applies the result (nk, nkr, ns) of the pending extension.  Returns false when the read is
@@ -259,20 +255,25 @@ __device__ __forceinline__ bool smem_apply(SmemState &S, u32 nk, u32 nkr, u32 ns
 }
 
 // The pending extension of P[j]: BackwardExt((k,kr,s), a) in stages 1/3, ForwardExt in stage 2
-// (= BackwardExt((kr,k,s), comp a)).  An N gives the empty interval without a memory access.
+// (= BackwardExt((kr,k,s), comp a)).  The block reads are issued before the read base is fetched
+// (the base is only needed for the counting), so their latencies overlap.  An N gives the empty
+// interval.
 template <class W>
 __device__ __forceinline__ void smem_extend(SmemState &S, const DevIndex &I, u32 &nk, u32 &nkr, u32 &ns,
                                             W &work) {
+    const bool fwd = S.u == 2;
+    const u32 p = fwd ? S.kr : S.k, q = fwd ? S.k : S.kr, e = p + S.s;
+    const Blk b0 = load_blk(I.occ + (p >> BLK_SHIFT));
+    Blk b1 = b0;
+    if ((e >> BLK_SHIFT) != (p >> BLK_SHIFT)) b1 = load_blk(I.occ + (e >> BLK_SHIFT));
     const u32 a = cached_base(S, S.j);
     nk = 0; nkr = 0; ns = 0;
     if (a < 4) {
-        const bool fwd = S.u == 2;
-        const u32 p = fwd ? S.kr : S.k, q = fwd ? S.k : S.kr;
         work.ext(p, S.s);
-        Ext e = extend(I, p, q, S.s, fwd ? 3u - a : a);
-        nk = fwd ? e.q : e.p;
-        nkr = fwd ? e.p : e.q;
-        ns = e.s;
+        const Ext x = extend_blocks(I, b0, b1, p, q, S.s, fwd ? 3u - a : a);
+        nk = fwd ? x.q : x.p;
+        nkr = fwd ? x.p : x.q;
+        ns = x.s;
     }
 }
 
@@ -281,11 +282,21 @@ template <class Emit, class W>
 __device__ __forceinline__ void smem_read(const DevIndex &I, const u8 *__restrict__ P, int L, u32 l, u32 c, u32 conv,
                                           bool kmer, const u8 *end, Emit &emit, W &work) {
     SmemState S;
-    smem_begin(S, P, L, conv, l, (u32)I.n, end);
-    while (smem_advance(S, I, l, c, kmer, emit, work)) {
+    const u32 n = (u32)I.n;
+    smem_begin(S, P, L, conv, l, n, end);
+    for (;;) {
+        u32 code = 0;
+        const int act = smem_next(S, I, l, kmer, emit, code);
+        if (act == ACT_NONE) break;
+        if (act == ACT_KMER) {
+            const u32 *t = I.kmer + 3 * (u64)code;
+            work.kmer += 1;
+            if (!smem_apply_kmer(S, __ldg(t), __ldg(t + 1), __ldg(t + 2), l, c, I.kmer_k)) break;
+            continue;
+        }
         u32 nk, nkr, ns;
         smem_extend(S, I, nk, nkr, ns, work);
-        if (!smem_apply(S, nk, nkr, ns, l, c, (u32)I.n, emit)) break;
+        if (!smem_apply(S, nk, nkr, ns, l, c, n, emit)) break;
     }
 }
 
@@ -401,41 +412,50 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 128 ? 6 : 1024 / BLOCK) k_smem
     }
     for (;;) {
         if (__all_sync(0xffffffffu, !live)) break;
-        // phase 1 (divergent, no block reads): move through stage changes up to the next extension
-        bool need = false;
-        u32 p = 0, q = 0, ss = 0, sym = 4;
-        if (live) {
-            need = smem_advance(S, I, lr, cr, kmer && lr >= I.kmer_k, em, work);
-            if (need) {
-                const u32 a = cached_base(S, S.j);
-                const bool fwd = S.u == 2;   // ForwardExt((k,kr,s), a) = BackwardExt((kr,k,s), comp a)
-                p = fwd ? S.kr : S.k;
-                q = fwd ? S.k : S.kr;
-                ss = S.s;
-                sym = a > 3 ? 4u : (fwd ? 3u - a : a);
-            }
-        }
+        // phase 1 (divergent, no memory): stage changes, then this lane's one memory action
+        int act = ACT_NONE;
+        u32 code = 0;
+        if (live) act = smem_next(S, I, lr, kmer && lr >= I.kmer_k, em, code);
         __syncwarp();
-        // phase 2 (converged): one extension for every lane that has one; an N reads nothing
-        u32 np = 0, nq = 0, ns = 0;
-        if (sym < 4) {
-            work.ext(p, ss);
-            const Ext e = extend(I, p, q, ss, sym);
-            np = e.p; nq = e.q; ns = e.s;
+        // phase 2 (converged): every lane's loads are issued before any is used, so the table
+        // lookups, the block reads and the read-chunk reloads of one iteration overlap
+        u32 tk = 0, tkr = 0, ts = 0;
+        if (act == ACT_KMER) {
+            const u32 *t = I.kmer + 3 * (u64)code;
+            tk = __ldg(t);
+            tkr = __ldg(t + 1);
+            ts = __ldg(t + 2);
         }
-        // phase 3: apply, finish, refill
+        const bool fwd = S.u == 2;
+        const u32 p = fwd ? S.kr : S.k, q = fwd ? S.k : S.kr, e = p + S.s;
+        Blk b0, b1;
+        if (act == ACT_EXT) {
+            b0 = load_blk(I.occ + (p >> BLK_SHIFT));
+            b1 = b0;
+            if ((e >> BLK_SHIFT) != (p >> BLK_SHIFT)) b1 = load_blk(I.occ + (e >> BLK_SHIFT));
+        }
+        const u32 a = act == ACT_EXT ? cached_base(S, S.j) : 0u;
+        // phase 3: apply the results
         bool fin = false;
-        if (live) {
-            bool go = need;
-            if (need) {
-                const bool fwd = S.u == 2;
-                go = smem_apply(S, fwd ? nq : np, fwd ? np : nq, ns, lr, cr, n, em);
+        if (act == ACT_KMER) {
+            work.kmer += 1;
+            fin = !smem_apply_kmer(S, tk, tkr, ts, lr, cr, I.kmer_k);
+        } else if (act == ACT_EXT) {
+            u32 nk = 0, nkr = 0, ns = 0;
+            if (a < 4) {   // an N gives the empty interval
+                work.ext(p, S.s);
+                const Ext x = extend_blocks(I, b0, b1, p, q, S.s, fwd ? 3u - a : a);
+                nk = fwd ? x.q : x.p;
+                nkr = fwd ? x.p : x.q;
+                ns = x.s;
             }
-            if (!go) {
-                counts[r] = em.cnt;
-                if (em.cnt > em.cap) ovf_list[atomicAdd(ovf_n, 1u)] = (u32)r;
-                fin = true;
-            }
+            fin = !smem_apply(S, nk, nkr, ns, lr, cr, n, em);
+        } else if (live) {
+            fin = true;
+        }
+        if (fin) {
+            counts[r] = em.cnt;
+            if (em.cnt > em.cap) ovf_list[atomicAdd(ovf_n, 1u)] = (u32)r;
         }
         const u32 fm = __ballot_sync(0xffffffffu, fin);
         if (fm) {
