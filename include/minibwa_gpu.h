@@ -69,7 +69,7 @@ typedef struct {
     uint32_t kmer_k;          /* k of the k-mer ds-interval table (default 10, Section 2.5), <= 12 */
     uint32_t flags;           /* MB_* flags above */
     uint32_t reads_per_warp;  /* tuning: reads per warp in the batched form (0 = default) */
-    uint32_t prefetch_depth;  /* tuning: in-flight reads per lane (0 = default) */
+    uint32_t prefetch_depth;  /* tuning: LF-walks in flight per lane in locate, 1, 2 or 4 (0 = 1) */
     uint32_t block_size;      /* tuning: threads per block (0 = default) */
 } mb_opts;
 
@@ -203,7 +203,8 @@ int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_smem, const m
  * writes them.  MB_ERR_CAPACITY (with the needed counts in *n_smem / *n_hits) if a limit was
  * exceeded; nothing beyond the limits was written.
  * mb_autotune times mb_plan_run on the given batch for every launch shape it supports
- * (block size x work queue on/off) and writes the fastest into *best (same output for all).
+ * (block size 128/256/512 x work queue on/off x locate walks per lane 1/2/4) and writes the
+ * fastest into *best (same output for all).
  */
 typedef struct mb_plan mb_plan;
 int mb_plan_create(const mb_index *idx, const mb_opts *opts, uint32_t max_reads, uint64_t max_bases,

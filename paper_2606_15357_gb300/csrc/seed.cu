@@ -719,13 +719,14 @@ int launch_locate_t(const DevIndex &I, const u32 *rows, u64 nhits, const u64 *nh
     return MB_OK;
 }
 
-// The locate kernel: work counters, power-of-two sample rate, walks per lane (depth 1 or 2).
+// The locate kernel: work counters, power-of-two sample rate, walks per lane (depth 1, 2 or 4).
 int launch_locate(const DevIndex &I, const u32 *rows, u64 nhits, const u64 *nhits_dev, u32 *hits, u64 *wc,
                   bool count, u32 depth, cudaStream_t st) {
     const bool pow2 = (I.r & (I.r - 1)) == 0;
     if (count) return pow2 ? launch_locate_t<true, true, 1>(I, rows, nhits, nhits_dev, hits, wc, st)
                            : launch_locate_t<true, false, 1>(I, rows, nhits, nhits_dev, hits, wc, st);
     if (!pow2) return launch_locate_t<false, false, 1>(I, rows, nhits, nhits_dev, hits, wc, st);
+    if (depth >= 4) return launch_locate_t<false, true, 4>(I, rows, nhits, nhits_dev, hits, wc, st);
     if (depth >= 2) return launch_locate_t<false, true, 2>(I, rows, nhits, nhits_dev, hits, wc, st);
     return launch_locate_t<false, true, 1>(I, rows, nhits, nhits_dev, hits, wc, st);
 }
@@ -1133,7 +1134,7 @@ extern "C" int mb_plan_create(const mb_index *idx, const mb_opts *opts, uint32_t
     P->kmer = !(P->flags & MB_NO_KMER) && P->l >= mb_dev_index(idx).kmer_k;
     P->queue = (P->flags & MB_BATCHED) != 0;
     P->block = opts && (opts->block_size == 128 || opts->block_size == 512) ? (int)opts->block_size : 256;
-    P->depth = opts && opts->prefetch_depth >= 2 ? 2u : 1u;
+    P->depth = opts && opts->prefetch_depth >= 4 ? 4u : (opts && opts->prefetch_depth >= 2 ? 2u : 1u);
     P->max_reads = max_reads;
     P->max_bases = max_bases;
     P->max_smem = max_smem ? max_smem : 1;
@@ -1324,7 +1325,7 @@ extern "C" int mb_autotune(const mb_index *idx, const uint8_t *seq, const uint64
     int rc = MB_OK;
     for (int q = 0; q < 2 && rc == MB_OK; ++q)
         for (int bi = 0; bi < 3 && rc == MB_OK; ++bi)
-        for (int dep = 1; dep <= 2 && rc == MB_OK; ++dep) {
+        for (int dep = 1; dep <= 4 && rc == MB_OK; dep *= 2) {
             mb_opts o = opts ? *opts : mb_opts{};
             o.flags = (o.flags & ~MB_BATCHED) | (q ? MB_BATCHED : 0u);
             o.block_size = (u32)blocks[bi];

@@ -99,7 +99,7 @@ def test_workload1_full(mb):
     compare_seed(sm, hits, X, rd.seq, rd.off)
 
 
-@pytest.mark.parametrize("depth", [1, 2])
+@pytest.mark.parametrize("depth", [1, 2, 4])
 def test_locate_walks_per_lane(mb, depth):
     """Locate with one or two LF-walks in flight per lane gives the same hits."""
     ref, rd, p = synth.workload(2, scale=0.01)
