@@ -162,7 +162,7 @@ int mb_reseed(const mb_index *idx, const uint8_t *seq, const uint64_t *off, uint
  * inside the library (every GPU that loads the library holds it until the process exits).
  *   seq, off, mate (or NULL) and out must be DEVICE pointers; the other arguments, the results
  *   and the errors are those of mb_seed_batch (same records, same order).
- *   A batch whose scratch need exceeds 64 MiB (about 300,000 reads of 150 bases, less with many
+ *   A batch whose scratch need exceeds 64 MiB (about 170,000 reads of 150 bases, less with many
  *   SMEMs) is rejected with MB_ERR_ARG and a message naming the need; split the batch.
  *   The first call on a device looks up the array's device address (cudaGetSymbolAddress) for
  *   that device; make that first call before any stream capture.

@@ -9,7 +9,7 @@
 // of a warp share the same memory instruction whatever stage they are in.
 //
 // Output: each read first writes its SMEMs into a private run of slots in scratch memory
-// (off[r]/32 + 4r slots before it), a prefix sum over the per-read counts gives the final
+// (off[r]/16 + 8r slots before it), a prefix sum over the per-read counts gives the final
 // positions, and a gather writes the 48-byte records.  Reads with more SMEMs than slots are
 // listed and recomputed straight into the final records.
 #include <climits>
@@ -29,7 +29,15 @@ struct SlotRec {
     u32 qbeg, qend, k, kr, s;
 };
 
-__device__ __forceinline__ u64 slot_base(const u64 *off, u64 r) { return (off[r] - off[0]) / 32 + 4 * r; }
+// Scratch slots: a read of len bases owns len/16 + 8 slots (about 17 for 150 bases).
+constexpr u64 SLOT_DIV = 16, SLOT_EXTRA = 8;
+__host__ __device__ __forceinline__ u64 slots_before(u64 bases_before, u64 r) {
+    return bases_before / SLOT_DIV + SLOT_EXTRA * r;
+}
+__host__ __device__ __forceinline__ u64 slots_total(u64 bases, u64 n_reads) {
+    return bases / SLOT_DIV + SLOT_EXTRA * n_reads + SLOT_EXTRA;
+}
+__device__ __forceinline__ u64 slot_base(const u64 *off, u64 r) { return slots_before(off[r] - off[0], r); }
 
 // Work counters of the measurement mode (MB_COUNT); compiled out otherwise.
 template <bool ON>
@@ -377,7 +385,7 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 128 ? 6 : 1024 / BLOCK) k_smem
     u32 lr = l, cr = c;   // this read's l and c
     auto start = [&](u64 rr) {
         const u64 b = off[rr], e = off[rr + 1];
-        const u64 sb = (b - o0) / 32 + 4 * rr, se = (e - o0) / 32 + 4 * (rr + 1);
+        const u64 sb = slots_before(b - o0, rr), se = slots_before(e - o0, rr + 1);
         em.slots = slots;
         em.base = sb;
         em.cap = se <= slot_total ? (u32)(se - sb) : 0u;
@@ -758,7 +766,7 @@ static int seed_device(const mb_index *idx, const u8 *dseq, const u64 *doff, u32
     *n_out = 0;
     if (n_hits) *n_hits = 0;
     if (n_reads == 0) return MB_OK;
-    const u64 nslots = (o1 - o0) / 32 + 4ULL * n_reads + 4;
+    const u64 nslots = slots_total(o1 - o0, n_reads);
     DevBuf bslots, bcounts, bsoff, bovf, bmisc, btmp;
     MB_TRY(bslots.alloc(nslots * sizeof(SlotRec), st));
     MB_TRY(bcounts.alloc((size_t)n_reads * 8, st));
@@ -808,7 +816,7 @@ static int seed_device(const mb_index *idx, const u8 *dseq, const u64 *doff, u32
     k_gather<<<G, B, 0, st>>>((const u64 *)doff, n_reads, bslots.as<SlotRec>(), nslots, bcounts.as<u64>(),
                               bsoff.as<u64>(), max_occ, dout, bhitc.as<u64>(), total);
     MB_KCHECK();
-    k_smem_overflow<<<152, 128, 0, st>>>(I, (const u8 *)dseq, (const u64 *)doff, n_reads, (const u8 *)dmate, bs, l,
+    k_smem_overflow<<<resident_grid((const void *)k_smem_overflow, 128, 1ull << 40), 128, 0, st>>>(I, (const u8 *)dseq, (const u64 *)doff, n_reads, (const u8 *)dmate, bs, l,
                                          c, kmer,
                                          bovf.as<u32>(), dovf_n, bsoff.as<u64>(), max_occ, dout, bhitc.as<u64>(),
                                          total, dlc);
@@ -1018,7 +1026,7 @@ extern "C" int mb_seed_batch_noalloc(const mb_index *idx, const uint8_t *seq, co
     }
     // scratch layout: [totals][counts][soff][overflow list][scan tmp][slots][hit counts][scan tmp]
     const size_t nr = n_reads;
-    const size_t nslots = (o1 - o0) / 32 + 4 * nr + 4;
+    const size_t nslots = slots_total(o1 - o0, nr);
     const size_t o_cnt = 256, o_soff = o_cnt + al256(nr * 8), o_ovf = o_soff + al256(nr * 8);
     const size_t o_tmp = o_ovf + al256(nr * 4), o_slots = o_tmp + al256(scan_tmp_bytes(nr));
     const size_t fixed = o_slots + al256(nslots * sizeof(SlotRec));
@@ -1064,7 +1072,7 @@ extern "C" int mb_seed_batch_noalloc(const mb_index *idx, const uint8_t *seq, co
     u64 *hitc = (u64 *)(S + o_hitc);
     k_gather<<<G, B, 0, st>>>(off, n_reads, slots, nslots, counts, soff, max_occ, out, hitc, total);
     MB_KCHECK();
-    k_smem_overflow<<<152, 128, 0, st>>>(I, seq, off, n_reads, mate, bs, l, c, kmer, ovf, dovf_n, soff, max_occ, out,
+    k_smem_overflow<<<resident_grid((const void *)k_smem_overflow, 128, 1ull << 40), 128, 0, st>>>(I, seq, off, n_reads, mate, bs, l, c, kmer, ovf, dovf_n, soff, max_occ, out,
                                          hitc, total, nullptr);
     MB_KCHECK();
     MB_TRY(scan_exclusive_u64(hitc, hitc, total, dhtotal, S + o_htmp, st));
@@ -1139,7 +1147,7 @@ extern "C" int mb_plan_create(const mb_index *idx, const mb_opts *opts, uint32_t
     P->max_bases = max_bases;
     P->max_smem = max_smem ? max_smem : 1;
     P->max_hits = max_hits ? max_hits : 1;
-    P->nslots = max_bases / 32 + 4ULL * max_reads + 4;
+    P->nslots = slots_total(max_bases, max_reads);
     const size_t nr = max_reads;
     size_t tb = scan_tmp_bytes(nr > P->max_smem ? nr : P->max_smem);
     const size_t rb = radix_tmp_bytes(nr);
@@ -1208,7 +1216,7 @@ extern "C" int mb_plan_run(mb_plan *P, const uint8_t *seq, const uint64_t *off, 
     k_gather<<<G, 256, 0, st>>>(off, n_reads, P->slots, P->nslots, P->counts, P->soff, P->max_occ, P->out, P->hitc,
                                 P->max_smem);
     MB_KCHECK();
-    k_smem_overflow<<<152, 128, 0, st>>>(I, seq, off, n_reads, mate, bs, P->l, P->c, P->kmer, P->ovf, ovf_n, P->soff,
+    k_smem_overflow<<<resident_grid((const void *)k_smem_overflow, 128, 1ull << 40), 128, 0, st>>>(I, seq, off, n_reads, mate, bs, P->l, P->c, P->kmer, P->ovf, ovf_n, P->soff,
                                          P->max_occ, P->out, P->hitc, P->max_smem, nullptr);
     MB_KCHECK();
     MB_TRY(scan_exclusive_u64(P->hitc, P->hitc, P->max_smem, n_hits, P->tmp, st));
