@@ -449,16 +449,17 @@ def run_gpu(args):
     wc = mb.work_counters()
     log(f"work: {m} SMEMs, {nh} hits, {wc}")
 
-    # autotune the launch shape on a sample of the batch, then use it for both forms
+    # launch shape: fixed (--block / --locate-walks, the autotuner's choice on this workload), or
+    # autotuned on a sample of the batch with --autotune; used for both forms
     ns = min(n_reads, 1_000_000)
-    if args.no_autotune:
-        best = mb.Opts(block_size=256, prefetch_depth=1)
-    else:
+    if args.autotune:
         best, tune_ms = mb.autotune(idx, seq[:int(rd.off[ns])], off[:ns + 1], opts=opts)
+        log(f"autotuned on {ns} reads: block {best.block_size}, work queue {bool(best.flags & mb.MB_BATCHED)}, "
+            f"locate walks per lane {best.prefetch_depth}")
+    else:
+        best = mb.Opts(block_size=args.block, prefetch_depth=args.locate_walks)
     opts["block_size"] = best.block_size
     opts["prefetch_depth"] = best.prefetch_depth
-    log(f"autotuned on {ns} reads: block {best.block_size}, work queue {bool(best.flags & mb.MB_BATCHED)}, "
-        f"locate walks per lane {best.prefetch_depth}")
 
     for _ in range(args.warmup):
         step()
@@ -552,7 +553,9 @@ def run_gpu(args):
             roofline["frac_of_chain_ceiling"] = achieved / g
         log(f"gather ceiling: {gc}")
 
-    # end to end through the public API with pinned host buffers
+    # end to end through the public API with pinned host buffers: the pipelined one-call form
+    # (chunks alternate between two streams, copies overlap kernels), and the two calls
+    # mb_seed_batch + mb_locate for comparison
     e2e = None
     if not args.no_e2e:
         seq_h = torch.from_numpy(rd.seq).pin_memory()
@@ -560,18 +563,28 @@ def run_gpu(args):
         out_h = torch.empty(m * 48, dtype=torch.uint8).pin_memory()
         hits_h = torch.empty(max(nh, 1), dtype=torch.int32).pin_memory()
         k2 = max(1, min(args.steps, 3))
+        mb.seed_locate(idx, seq_h, off_h, opts=opts, out=out_h, cap=m, hits=hits_h, hits_cap=nh)   # warm-up
         torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
         t0 = time.time()
         for _ in range(k2):
-            _, m2, nh2 = mb.mb_seed_batch(idx, seq_h, off_h, opts=opts, out=out_h, cap=m)
-            mb.mb_locate(idx, out_h, m2, opts=opts, hits=hits_h, cap=nh2)
+            m2, nh2 = mb.seed_locate(idx, seq_h, off_h, opts=opts, out=out_h, cap=m, hits=hits_h, hits_cap=nh)
         torch.cuda.synchronize()
-        dt = time.time() - t0
-        dt = max_over_ranks(dt, pg)
+        dt = max_over_ranks(time.time() - t0, pg)
+        t0 = time.time()
+        for _ in range(k2):
+            _, m3, nh3 = mb.mb_seed_batch(idx, seq_h, off_h, opts=opts, out=out_h, cap=m)
+            mb.mb_locate(idx, out_h, m3, opts=opts, hits=hits_h, cap=nh3)
+        torch.cuda.synchronize()
+        dt2 = max_over_ranks(time.time() - t0, pg)
         e2e = {"value": ws * k2 * n_reads / dt, "unit": "reads/s",
-               "h2d_bytes_per_step": int(seq_h.numel() + off_h.numel() * 8 + m * 48),
+               "h2d_bytes_per_step": int(seq_h.numel() + off_h.numel() * 8),
                "d2h_bytes_per_step": int(m * 48 + nh * 4),
-               "note": "host pinned buffers; the locate call re-stages the SMEM records"}
+               "call": "mb_seed_locate (pinned host buffers, 2M-read chunks on two streams)",
+               "two_calls_reads_per_s": ws * k2 * n_reads / dt2,
+               "note": "two_calls = mb_seed_batch + mb_locate on host buffers (the records are staged back in)"}
+        log(f"e2e: {e2e}")
 
     served = None
     if rank == 0 and not args.no_serve:
@@ -644,7 +657,11 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the served-form measurement")
     ap.add_argument("--serve-requests", type=int, default=600)
     ap.add_argument("--probe-gib", type=int, default=1, help="buffer of the random-gather probe (GiB)")
-    ap.add_argument("--no-autotune", action="store_true", help="default launch shape (profiling captures)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="autotune the launch shape on 1M reads instead of --block / --locate-walks")
+    ap.add_argument("--no-autotune", action="store_true", help="(default) fixed launch shape")
+    ap.add_argument("--block", type=int, default=512, choices=[128, 256, 512])
+    ap.add_argument("--locate-walks", type=int, default=4, choices=[1, 2, 4])
     ap.add_argument("--reads", type=int, default=0,
                     help="seed only the first N reads of the batch (for ncu captures of the full index)")
     args = ap.parse_args()

@@ -68,7 +68,7 @@ typedef struct {
     uint32_t sa_rate;         /* r, suffix array sample rate (default 32, Section 2.3) */
     uint32_t kmer_k;          /* k of the k-mer ds-interval table (default 10, Section 2.5), <= 12 */
     uint32_t flags;           /* MB_* flags above */
-    uint32_t reads_per_warp;  /* tuning: reads per warp in the batched form (0 = default) */
+    uint32_t chunk_reads;     /* mb_seed_locate: reads per pipelined chunk (0 = 2^21) */
     uint32_t prefetch_depth;  /* tuning: LF-walks in flight per lane in locate, 1, 2 or 4 (0 = 1) */
     uint32_t block_size;      /* tuning: threads per block (0 = default) */
 } mb_opts;
@@ -90,8 +90,8 @@ typedef struct {
  *   stream   stream for the build.
  *   out      receives the new index (free with mb_index_free).
  * Builds T, its suffix array by prefix doubling, the BWT in occurrence blocks (Section 2.2;
- * here 32 bytes per 64 rows: four u32 counts of A/C/G/T before the block, then 64 2-bit
- * symbols), the sampled suffix array and the k-mer ds-interval table.
+ * here 32 bytes per 64 rows: four u32 counts of A/C/G/T before the block, then the 64 2-bit
+ * symbols as two bit planes), the sampled suffix array and the k-mer ds-interval table.
  * Errors: MB_ERR_ARG (len = 0, n >= 2^32), MB_ERR_NOMEM, MB_ERR_CUDA.
  */
 int mb_index_build(const uint8_t *ref, uint64_t len, const mb_opts *opts, uint64_t n_seed,
@@ -110,7 +110,8 @@ int mb_index_info(const mb_index *idx, uint64_t *n, uint64_t *primary, uint64_t 
 /* Copy index arrays to the caller (host or device): sa (n x u32, full suffix array; only
  * available until mb_index_drop_sa, else MB_ERR_ARG), bwt (n bytes, 0=$ 1..4=A..T),
  * ssa (ceil(n/r) x u32), occ blocks (n/64 + 1 blocks of 32 bytes: four u32 counts of A,C,G,T
- * before the block, then two u64 words of 2-bit symbols of its 64 rows), kmer table (4^k x 3 u32:
+ * before the block, then two u64 bit planes of its 64 rows: bit q of the first is the low bit of
+ * row q's code 0..3, bit q of the second its high bit; the $ row reads as A), kmer table (4^k x 3 u32:
  * k, kr, s of the k-mer whose base t is in bits 2t..2t+1 of the entry number), C (5 x u64 =
  * #{B[i] < a} for a = $,A,C,G,T).  Any pointer may be NULL. */
 int mb_index_export(const mb_index *idx, uint32_t *sa, uint8_t *bwt, uint32_t *ssa,
@@ -186,6 +187,29 @@ int mb_seed_batch_noalloc(const mb_index *idx, const uint8_t *seq, const uint64_
  */
 int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_smem, const mb_opts *opts,
               void *stream, uint32_t *hits, uint64_t cap, uint64_t *n_hits);
+
+/* ---------------------------------------------------------------------------------------
+ * mb_seed_locate — the whole stage in one call: SMEMs as mb_seed_batch, then their hits as
+ * mb_locate (Section 2.5, Algorithm 3; Section 2.3, Algorithm 2), for callers whose reads and
+ * results live in host memory.  The batch is cut into chunks of consecutive reads
+ * (opts->chunk_reads reads, at most 2^29 bases, at least one read) that alternate between two
+ * internal streams, so that the copies of one chunk overlap the kernels of the other; use
+ * pinned host buffers for the copies to overlap.
+ *   seq, off, mate   host or device, as for mb_seed_batch.
+ *   out              host or device, room for `cap` records: the records of mb_seed_batch (read
+ *                    numbers and hit_off relative to this batch).
+ *   hits             host or device, room for `hits_cap` u32: the output of mb_locate.
+ *   n_out, n_hits    receive the totals.  If either exceeds its capacity, MB_ERR_CAPACITY is
+ *                    returned with both totals; the contents of out and hits are then undefined.
+ * Work is ordered after what the caller enqueued on `stream` before the call; the call returns
+ * when every result is written.  Allocates its device workspace (two seeding plans sized for
+ * the largest chunk) on each call; a chunk that yields more records or hits than its plan holds
+ * is seeded again through the allocating path.
+ * Errors: MB_ERR_ARG, MB_ERR_CAPACITY, MB_ERR_NOMEM, MB_ERR_CUDA, MB_ERR_DEVICE_CHECK.
+ */
+int mb_seed_locate(const mb_index *idx, const uint8_t *seq, const uint64_t *off, uint32_t n_reads,
+                   const uint8_t *mate, const mb_opts *opts, void *stream, mb_smem *out, uint64_t cap,
+                   uint32_t *hits, uint64_t hits_cap, uint64_t *n_out, uint64_t *n_hits);
 
 /* ---------------------------------------------------------------------------------------
  * Batched form: a reusable seeding plan.

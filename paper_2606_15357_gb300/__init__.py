@@ -33,7 +33,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("min_len", ctypes.c_uint32), ("min_occ", ctypes.c_uint32),
                 ("max_occ", ctypes.c_uint32), ("sa_rate", ctypes.c_uint32),
                 ("kmer_k", ctypes.c_uint32), ("flags", ctypes.c_uint32),
-                ("reads_per_warp", ctypes.c_uint32), ("prefetch_depth", ctypes.c_uint32),
+                ("chunk_reads", ctypes.c_uint32), ("prefetch_depth", ctypes.c_uint32),
                 ("block_size", ctypes.c_uint32)]
 
 
@@ -70,6 +70,7 @@ def lib():
                 "mb_index_drop_sa": ([P], I),
                 "mb_seed_batch": ([P, P, P, U32, P, OP, P, P, U64, PU64, PU64], I),
                 "mb_locate": ([P, P, U64, OP, P, P, U64, PU64], I),
+                "mb_seed_locate": ([P, P, P, U32, P, OP, P, P, U64, P, U64, PU64, PU64], I),
                 "mb_bs_filter": ([P, P, U64, P, P, U64, P, P], I),
                 "mb_hit_to_ref": ([P, U64, U64, ctypes.POINTER(I), PU64], I),
                 "mb_strerror": ([I], ctypes.c_char_p),
@@ -291,6 +292,36 @@ def mb_reseed(index: Index, seq, off, smem, n_smem: int, mate=None, opts=None, s
             continue
         _check(rc, "mb_reseed")
         return buf[:n_out.value], n_out.value, n_hits.value
+
+
+def seed_locate(index: Index, seq, off, mate=None, opts=None, stream=None, out=None, cap=None, hits=None,
+                hits_cap=None):
+    """SMEMs and their hits in one pipelined call (host or device buffers).
+
+    With `out` None returns host numpy arrays (records, hits), sized by a retry on
+    MB_ERR_CAPACITY; otherwise writes into `out` (uint8, cap*48 bytes) and `hits` (hits_cap
+    u32) and returns (n_smem, n_hits)."""
+    o = _opts(opts)
+    n_reads = (off.numel() if hasattr(off, "numel") else len(off)) - 1
+    n_out, n_hits = ctypes.c_uint64(), ctypes.c_uint64()
+    if out is None:
+        cap = cap if cap is not None else max(16, 4 * n_reads)
+        hits_cap = hits_cap if hits_cap is not None else max(16, 32 * n_reads)
+        while True:
+            buf = np.empty(max(cap, 1), dtype=SMEM_DTYPE)
+            hbuf = np.empty(max(hits_cap, 1), dtype=np.uint32)
+            rc = lib().mb_seed_locate(index.handle, _ptr(seq), _ptr(off), n_reads, _ptr(mate), ctypes.byref(o),
+                                      _stream(stream), _ptr(buf), cap, _ptr(hbuf), hits_cap,
+                                      ctypes.byref(n_out), ctypes.byref(n_hits))
+            if rc == MB_ERR_CAPACITY:
+                cap, hits_cap = n_out.value, n_hits.value
+                continue
+            _check(rc, "mb_seed_locate")
+            return buf[:n_out.value], hbuf[:n_hits.value]
+    _check(lib().mb_seed_locate(index.handle, _ptr(seq), _ptr(off), n_reads, _ptr(mate), ctypes.byref(o),
+                                _stream(stream), _ptr(out), cap, _ptr(hits), hits_cap, ctypes.byref(n_out),
+                                ctypes.byref(n_hits)), "mb_seed_locate")
+    return n_out.value, n_hits.value
 
 
 def seed(index: Index, seq, off, mate=None, opts=None, stream=None):

@@ -91,17 +91,18 @@ int mb_stage_in(const void *src, size_t bytes, cudaStream_t st, DevBuf &buf, con
 
 // ----------------------------------------------------------------------------- index layout
 // One occurrence block per 64 BWT rows, 32 bytes: the counts of A, C, G, T in B[0, 64b) as four
-// u32 (n < 2^32), then the 64 symbols of B[64b, 64b+64) as two u64 words of 2-bit codes, row q of
-// the block in word q/32 at bits 2*(q%32).  The $ row (primary) is stored as A and excluded from
-// the counts.  The paper (Section 2.2) uses 64-byte blocks of 128 rows sized for a CPU cache
-// line; on this GPU a random read costs one 32-byte DRAM sector, so a block is one sector and
-// every LF step or block access reads exactly one.
+// u32 (n < 2^32), then the 64 symbols of B[64b, 64b+64) as two bit planes: bit q of `lo` is the
+// low bit of row q's 2-bit code, bit q of `hi` its high bit.  The $ row (primary) is stored as A
+// and excluded from the counts.  The paper (Section 2.2) uses 64-byte blocks of 128 rows sized
+// for a CPU cache line; on this GPU a random read costs one 32-byte DRAM sector, so a block is
+// one sector and every LF step or block access reads exactly one.  The planes make the symbol of
+// a row two bit tests and the count of a symbol before a row one 64-bit mask and popcount.
 constexpr u32 BLK_SHIFT = 6;
 constexpr u32 BLK_ROWS = 1u << BLK_SHIFT;
 constexpr u32 BLK_MASK = BLK_ROWS - 1;
 struct __align__(32) OccBlock {
     u32 cnt[4];
-    u64 w[2];
+    u64 lo, hi;
 };
 static_assert(sizeof(OccBlock) == 32, "one block per 32-byte sector");
 
@@ -124,46 +125,37 @@ struct mb_index_impl;
 // Every row, count and interval bound is below n < 2^32, so the kernels work in u32.
 struct Blk {
     u32 c[4];
-    u64 w[2];
+    u64 lo, hi;
 };
 // The whole block in one 256-bit load.
 __device__ __forceinline__ Blk load_blk(const OccBlock *__restrict__ blk) {
-    u64 c01, c23, w0, w1;
-    asm("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];" : "=l"(c01), "=l"(c23), "=l"(w0), "=l"(w1) : "l"(blk));
+    u64 c01, c23, lo, hi;
+    asm("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];" : "=l"(c01), "=l"(c23), "=l"(lo), "=l"(hi) : "l"(blk));
     Blk b;
     b.c[0] = (u32)c01; b.c[1] = (u32)(c01 >> 32); b.c[2] = (u32)c23; b.c[3] = (u32)(c23 >> 32);
-    b.w[0] = w0; b.w[1] = w1;
+    b.lo = lo; b.hi = hi;
     return b;
 }
 
-// Bit mask of the 2-bit slots of word q (0..1) that lie before slot m (0..64) of the block.
-__device__ __forceinline__ u64 slot_mask(u32 m, int q) {
-    int take = (int)m - 32 * q;
-    take = take < 0 ? 0 : (take > 32 ? 32 : take);
-    return take == 32 ? ~0ULL : ((1ULL << (2 * take)) - 1);
+// Rows of the block before row m (0..63) as a bit mask.
+__device__ __forceinline__ u64 rows_before(u32 m) { return (1ULL << m) - 1; }
+// Code of row m of the block.
+__device__ __forceinline__ u32 sym_at(const Blk &b, u32 m) {
+    return (u32)((b.lo >> m) & 1) | ((u32)((b.hi >> m) & 1) << 1);
 }
-// Two words of even-position bits folded into one word, so one popcount covers both.
-__device__ __forceinline__ u32 popc_pair(u64 z0, u64 z1) { return __popcll(z0 | (z1 << 1)); }
-
-constexpr u64 EVEN = 0x5555555555555555ULL;
-
-// #{slots before m holding code a}; the $ row (stored as A) is not corrected here.
-__device__ __forceinline__ u32 cnt_sym(const Blk &b, u32 m, u32 a) {
-    const u64 pat = (u64)a * EVEN;   // a in every 2-bit slot
-    const u64 y0 = ~(b.w[0] ^ pat), y1 = ~(b.w[1] ^ pat);   // 11 where the slot holds a
-    return popc_pair(y0 & (y0 >> 1) & EVEN & slot_mask(m, 0), y1 & (y1 >> 1) & EVEN & slot_mask(m, 1));
+// Rows holding code a (0..3).
+__device__ __forceinline__ u64 rows_eq(const Blk &b, u32 a) {
+    const u64 fl = (u64)(a & 1) - 1, fh = (u64)(a >> 1) - 1;   // all ones where that bit of a is 0
+    return (b.lo ^ fl) & (b.hi ^ fh);
 }
-// #{slots before m holding a code <= a}; the $ row (stored as A) is not corrected here.
-__device__ __forceinline__ u32 cnt_le(const Blk &b, u32 m, u32 a) {
-    u64 z[2];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const u64 lo = b.w[q] & EVEN, hi = (b.w[q] >> 1) & EVEN;
-        const u64 e = a == 0 ? (~lo & ~hi) : a == 1 ? ~hi : a == 2 ? ~(lo & hi) : ~0ULL;
-        z[q] = e & EVEN & slot_mask(m, q);
-    }
-    return popc_pair(z[0], z[1]);
+// Rows holding a code <= a (0..3).
+__device__ __forceinline__ u64 rows_le(const Blk &b, u32 a) {
+    return a < 2 ? (a == 0 ? ~(b.lo | b.hi) : ~b.hi) : (a == 2 ? ~(b.lo & b.hi) : ~0ULL);
 }
+// #{rows before m holding code a}; the $ row (stored as A) is not corrected here.
+__device__ __forceinline__ u32 cnt_sym(const Blk &b, u32 m, u32 a) { return __popcll(rows_eq(b, a) & rows_before(m)); }
+// #{rows before m holding a code <= a}; the $ row (stored as A) is not corrected here.
+__device__ __forceinline__ u32 cnt_le(const Blk &b, u32 m, u32 a) { return __popcll(rows_le(b, a) & rows_before(m)); }
 
 // x[a] for a in 0..3 without dynamic indexing (which would go through local memory)
 __device__ __forceinline__ u32 sel4(u32 a, u32 x0, u32 x1, u32 x2, u32 x3) {
@@ -180,7 +172,7 @@ __device__ __forceinline__ u32 dollar_before(u32 x, u32 primary) {
 // B[0, x).
 __device__ __forceinline__ u32 lf_blk(const Blk &b, u32 x, u32 primary, u32 C0, u32 C1, u32 C2, u32 C3) {
     const u32 m = x & BLK_MASK;
-    const u32 a = (u32)((m < 32 ? b.w[0] : b.w[1]) >> (2 * (m & 31))) & 3u;
+    const u32 a = sym_at(b, m);
     u32 cnt = cnt_sym(b, m, a);
     if (a == 0) cnt -= dollar_before(x, primary);
     return sel4(a, C0 + b.c[0], C1 + b.c[1], C2 + b.c[2], C3 + b.c[3]) + cnt;

@@ -142,7 +142,7 @@ __global__ void k_bwt_blocks(const u8 *__restrict__ T, const u32 *__restrict__ S
     const u64 warps = (u64)gridDim.x * (blockDim.x >> 5);
     const u64 ngroups = (nblocks + 1) / 2;
     for (u64 g = blockIdx.x * (u64)(blockDim.x >> 5) + (threadIdx.x >> 5); g < ngroups; g += warps) {
-        u32 byte = 0, c[4] = {0, 0, 0, 0};
+        u32 lob = 0, hib = 0, c[4] = {0, 0, 0, 0};   // low / high code bits of the lane's 4 rows
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             u64 x = g * 128 + (u64)lane * 4 + j;
@@ -156,19 +156,27 @@ __global__ void k_bwt_blocks(const u8 *__restrict__ T, const u32 *__restrict__ S
                     s = T[p - 1];
                     c[s] += 1;
                 }
-                byte |= s << (2 * j);
+                lob |= (s & 1u) << j;
+                hib |= (s >> 1) << j;
             }
         }
-        u64 word = (u64)byte << (8 * (lane & 7));
+        // rows 4*(lane & 15) .. +3 of block 2g + (lane >> 4): OR the planes over each 16-lane half
+        u64 lo = (u64)lob << (4 * (lane & 15)), hi = (u64)hib << (4 * (lane & 15));
 #pragma unroll
-        for (int d = 1; d < 8; d <<= 1) word |= __shfl_xor_sync(0xffffffffu, word, d);
+        for (int d = 1; d < 16; d <<= 1) {
+            lo |= __shfl_xor_sync(0xffffffffu, lo, d);
+            hi |= __shfl_xor_sync(0xffffffffu, hi, d);
+        }
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int d = 8; d > 0; d >>= 1) c[a] += __shfl_xor_sync(0xffffffffu, c[a], d);   // per 16-lane half
         const u64 b = 2 * g + (u64)(lane >> 4);
         if (b < nblocks) {
-            if ((lane & 7) == 0) occ[b].w[(lane >> 3) & 1] = word;
+            if ((lane & 15) == 0) {
+                occ[b].lo = lo;
+                occ[b].hi = hi;
+            }
             const u32 a = (u32)(lane & 15);
             if (a < 4) bcnt[(u64)a * nblocks + b] = a < 2 ? (a == 0 ? c[0] : c[1]) : (a == 2 ? c[2] : c[3]);
         }
@@ -572,8 +580,9 @@ extern "C" int mb_index_export(const mb_index *idx, uint32_t *sa, uint8_t *bwt, 
         MB_CK(cudaMemcpy(blk.data(), idx->occ, idx->nblocks * sizeof(OccBlock), cudaMemcpyDeviceToHost));
         std::vector<u8> b(idx->n);
         for (u64 x = 0; x < idx->n; ++x) {
-            u64 w = blk[x >> BLK_SHIFT].w[(x & BLK_MASK) >> 5];
-            b[x] = x == idx->primary ? 0 : (u8)(((w >> (2 * (x & 31))) & 3) + 1);
+            const OccBlock &o = blk[x >> BLK_SHIFT];
+            const u32 m = (u32)(x & BLK_MASK);
+            b[x] = x == idx->primary ? 0 : (u8)((((o.lo >> m) & 1) | (((o.hi >> m) & 1) << 1)) + 1);
         }
         MB_TRY(copy_out(bwt, b.data(), idx->n));
     }
@@ -617,7 +626,7 @@ extern "C" int mb_index_save(const mb_index *idx, const char *path) {
     FileHeader h;
     memset(&h, 0, sizeof h);
     h.magic = MAGIC;
-    h.version = 2;
+    h.version = 3;
     h.n = idx->n;
     h.rlen = idx->rlen;
     h.primary = idx->primary;
@@ -660,7 +669,7 @@ extern "C" int mb_index_load(const char *path, void *stream, mb_index **out) {
         mb_set_error("mb_index_load: short header");
         return MB_ERR_CORRUPT;
     }
-    if (h.magic != MAGIC || h.version != 2 || h.sa_rate == 0 || h.kmer_k > 12 || h.n >= (1ULL << 32) ||
+    if (h.magic != MAGIC || h.version != 3 || h.sa_rate == 0 || h.kmer_k > 12 || h.n >= (1ULL << 32) ||
         h.nblocks != h.n / BLK_ROWS + 1) {
         fclose(f);
         mb_set_error("mb_index_load: bad header");

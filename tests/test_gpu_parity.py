@@ -38,13 +38,20 @@ def compare_index(G, X, k=10):
     assert np.array_equal(e["bwt"], X.bwt())
     assert np.array_equal(e["ssa"], X.ssa())
     assert np.array_equal(e["C"], X.C)
-    # block counts: #a in B[0, 64b) excluding $ (32-byte blocks: four u32 counts, two u64 words)
+    # block counts: #a in B[0, 64b) excluding $ (32-byte blocks: four u32 counts, two bit planes)
     B = X.bwt()
     occ = e["occ"].view(np.uint32).reshape(-1, 8)
     assert len(occ) == X.n // 64 + 1
     for a in range(4):
         cum = np.concatenate([[0], np.cumsum(B == a + 1)])
         assert np.array_equal(occ[:, a].astype(np.uint64), cum[np.arange(len(occ)) * 64].astype(np.uint64))
+    # bit planes: row q of block b has code ((lo >> q) & 1) | ((hi >> q) & 1) << 1, $ as A, A after the end
+    planes = e["occ"].view(np.uint64).reshape(-1, 4)[:, 2:]
+    q = np.arange(64, dtype=np.uint64)
+    codes = (((planes[:, :1] >> q) & 1) | (((planes[:, 1:] >> q) & 1) << 1)).reshape(-1)
+    want = np.zeros(len(codes), np.uint64)
+    want[:X.n] = np.where(B == 0, 0, B.astype(np.int64) - 1)
+    assert np.array_equal(codes, want)
     # k-mer table against the definition
     nk = 4 ** k
     words = np.arange(nk, dtype=np.int64)
