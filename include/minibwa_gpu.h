@@ -66,10 +66,11 @@ typedef struct {
     uint32_t min_occ;         /* c, minimum occurrence (default 1) */
     uint32_t max_occ;         /* SMEMs with s > max_occ are flagged and not located (default 500) */
     uint32_t sa_rate;         /* r, suffix array sample rate (default 32, Section 2.3) */
-    uint32_t kmer_k;          /* k of the k-mer ds-interval table (default 10, Section 2.5), <= 12 */
+    uint32_t kmer_k;          /* k of the k-mer ds-interval table (default 10, Section 2.5), <= 14;
+                                 the table takes 12 * 4^k bytes (3.2 GB at k = 14) */
     uint32_t flags;           /* MB_* flags above */
     uint32_t chunk_reads;     /* mb_seed_locate: reads per pipelined chunk (0 = 2^21) */
-    uint32_t prefetch_depth;  /* tuning: LF-walks in flight per lane in locate, 1, 2 or 4 (0 = 1) */
+    uint32_t prefetch_depth;  /* tuning: LF-walks in flight per lane in locate, 1/2/4/8/16 (0 = 1) */
     uint32_t block_size;      /* tuning: threads per block (0 = default) */
 } mb_opts;
 
@@ -202,9 +203,12 @@ int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_smem, const m
  *   n_out, n_hits    receive the totals.  If either exceeds its capacity, MB_ERR_CAPACITY is
  *                    returned with both totals; the contents of out and hits are then undefined.
  * Work is ordered after what the caller enqueued on `stream` before the call; the call returns
- * when every result is written.  Allocates its device workspace (two seeding plans sized for
- * the largest chunk) on each call; a chunk that yields more records or hits than its plan holds
- * is seeded again through the allocating path.
+ * when every result is written.  Its device workspace (two seeding plans sized for the largest
+ * chunk, two streams, staging buffers) is allocated on first use and kept for later calls with
+ * the same index, device and seeding options whose chunks fit it (at most two such sets are
+ * kept; mb_index_free releases them), so repeated calls allocate nothing.  Calls from several
+ * host threads are allowed: each takes its own workspace.  A chunk that yields more records or
+ * hits than its plan holds is seeded again through the allocating path.
  * Errors: MB_ERR_ARG, MB_ERR_CAPACITY, MB_ERR_NOMEM, MB_ERR_CUDA, MB_ERR_DEVICE_CHECK.
  */
 int mb_seed_locate(const mb_index *idx, const uint8_t *seq, const uint64_t *off, uint32_t n_reads,
@@ -227,7 +231,7 @@ int mb_seed_locate(const mb_index *idx, const uint8_t *seq, const uint64_t *off,
  * writes them.  MB_ERR_CAPACITY (with the needed counts in *n_smem / *n_hits) if a limit was
  * exceeded; nothing beyond the limits was written.
  * mb_autotune times mb_plan_run on the given batch for every launch shape it supports
- * (block size 128/256/512 x work queue on/off x locate walks per lane 1/2/4) and writes the
+ * (block size 128/256/512 x work queue on/off x locate walks per lane 1/2/4/8/16) and writes the
  * fastest into *best (same output for all).
  */
 typedef struct mb_plan mb_plan;

@@ -457,8 +457,8 @@ extern "C" int mb_index_build(const uint8_t *ref, uint64_t len, const mb_opts *o
     u32 flags = opts ? opts->flags : 0;
     u32 r = opts && opts->sa_rate ? opts->sa_rate : 32;
     u32 kk = opts && opts->kmer_k ? opts->kmer_k : 10;
-    if (kk > 12 || r == 0) {
-        mb_set_error("mb_index_build: kmer_k must be <= 12");
+    if (kk > 14 || r == 0) {
+        mb_set_error("mb_index_build: kmer_k must be <= 14 and sa_rate > 0");
         return MB_ERR_ARG;
     }
     int bs3 = (flags & MB_BS3) ? 1 : 0;
@@ -543,7 +543,10 @@ extern "C" int mb_index_build(const uint8_t *ref, uint64_t len, const mb_opts *o
     return MB_OK;
 }
 
-extern "C" void mb_index_free(mb_index *idx) { free_index(idx); }
+extern "C" void mb_index_free(mb_index *idx) {
+    mb_pipeline_forget(idx);
+    free_index(idx);
+}
 
 extern "C" int mb_index_info(const mb_index *idx, uint64_t *n, uint64_t *primary, uint64_t *ref_len) {
     if (!idx) return MB_ERR_ARG;
@@ -669,7 +672,7 @@ extern "C" int mb_index_load(const char *path, void *stream, mb_index **out) {
         mb_set_error("mb_index_load: short header");
         return MB_ERR_CORRUPT;
     }
-    if (h.magic != MAGIC || h.version != 3 || h.sa_rate == 0 || h.kmer_k > 12 || h.n >= (1ULL << 32) ||
+    if (h.magic != MAGIC || h.version != 3 || h.sa_rate == 0 || h.kmer_k > 14 || h.n >= (1ULL << 32) ||
         h.nblocks != h.n / BLK_ROWS + 1) {
         fclose(f);
         mb_set_error("mb_index_load: bad header");

@@ -6,6 +6,12 @@
 // max-occ flag, Algorithm 2) and copies its records and hits out, the other stream's chunk is on
 // the GPU.  Read numbers and hit offsets of a chunk are made global by a small kernel before the
 // copy out, so the call returns exactly what mb_seed_batch followed by mb_locate return.
+//
+// The streams, plans and staging buffers of a call are kept for the next call with the same index,
+// device and seeding options whose chunks fit them (at most two sets are kept; they are released
+// with the index), so steady-state calls allocate nothing.
+#include <memory>
+#include <mutex>
 #include <vector>
 #include "common.cuh"
 
@@ -39,6 +45,12 @@ struct Stage {
 };
 
 struct Pipeline {
+    const mb_index *idx = nullptr;
+    int device = -1;
+    mb_opts opts{};                // options the plans were made with
+    u32 max_nr = 0;                // capacity: reads and bases per chunk
+    u64 max_nb = 0;
+    bool own_seq = false, own_off = false, own_mate = false;   // staging buffers present
     Stage s[PIPE_STAGES];
     cudaEvent_t start = nullptr;   // recorded on the caller's stream
     ~Pipeline() {
@@ -56,7 +68,57 @@ struct Pipeline {
     }
 };
 
+// the options that shape a plan (chunk_reads only sizes the chunks)
+bool same_plan_opts(const mb_opts &a, const mb_opts &b) {
+    return a.min_len == b.min_len && a.min_occ == b.min_occ && a.max_occ == b.max_occ && a.flags == b.flags &&
+           a.prefetch_depth == b.prefetch_depth && a.block_size == b.block_size;
+}
+
+constexpr size_t KEEP = 2;
+std::mutex g_mu;
+std::vector<std::unique_ptr<Pipeline>> g_idle;
+
+std::unique_ptr<Pipeline> take_pipeline(const mb_index *idx, int device, const mb_opts &o, u32 nr, u64 nb,
+                                        bool seq, bool off, bool mate) {
+    std::lock_guard<std::mutex> g(g_mu);
+    for (size_t i = 0; i < g_idle.size(); ++i) {
+        Pipeline &p = *g_idle[i];
+        if (p.idx == idx && p.device == device && same_plan_opts(p.opts, o) && p.max_nr >= nr && p.max_nb >= nb &&
+            (p.own_seq || !seq) && (p.own_off || !off) && (p.own_mate || !mate)) {
+            std::unique_ptr<Pipeline> r = std::move(g_idle[i]);
+            g_idle.erase(g_idle.begin() + i);
+            return r;
+        }
+    }
+    return nullptr;
+}
+
+void keep_pipeline(std::unique_ptr<Pipeline> p) {
+    std::unique_ptr<Pipeline> drop;
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        g_idle.push_back(std::move(p));
+        if (g_idle.size() > KEEP) {
+            drop = std::move(g_idle.front());
+            g_idle.erase(g_idle.begin());
+        }
+    }
+}
+
 }  // namespace
+
+void mb_pipeline_forget(const mb_index *idx) {
+    std::vector<std::unique_ptr<Pipeline>> drop;
+    std::lock_guard<std::mutex> g(g_mu);
+    for (size_t i = 0; i < g_idle.size();) {
+        if (g_idle[i]->idx == idx) {
+            drop.push_back(std::move(g_idle[i]));
+            g_idle.erase(g_idle.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+}
 
 extern "C" int mb_seed_locate(const mb_index *idx, const uint8_t *seq, const uint64_t *off, uint32_t n_reads,
                               const uint8_t *mate, const mb_opts *opts, void *stream, mb_smem *out, uint64_t cap,
@@ -103,22 +165,39 @@ extern "C" int mb_seed_locate(const mb_index *idx, const uint8_t *seq, const uin
         r = e;
     }
 
-    // per-stage resources, sized for the largest chunk
-    Pipeline pl;
-    const u64 max_smem = 4ull * max_nr + max_nb / 32 + 64;
-    const u64 max_hits = 16ull * max_smem;
-    MB_CK(cudaEventCreateWithFlags(&pl.start, cudaEventDisableTiming));
-    MB_CK(cudaEventRecord(pl.start, ust));
-    for (Stage &x : pl.s) {
-        MB_CK(cudaStreamCreateWithFlags(&x.st, cudaStreamNonBlocking));
-        MB_CK(cudaEventCreateWithFlags(&x.ev, cudaEventDisableTiming));
-        MB_CK(cudaMallocHost(&x.hcnt, 16));
-        MB_CK(cudaStreamWaitEvent(x.st, pl.start, 0));   // ordered after the caller's earlier work
-        MB_TRY(mb_plan_create(idx, opts, max_nr, max_nb, max_smem, max_hits, &x.plan));
-        if (!seq_dev) MB_CK(cudaMalloc(&x.dseq, max_nb + 16));
-        if (!off_dev) MB_CK(cudaMalloc(&x.doff, ((size_t)max_nr + 1) * 8));
-        if (mate && !mate_dev) MB_CK(cudaMalloc(&x.dmate, max_nr));
+    // per-stage resources, sized for the largest chunk (a kept set when one fits)
+    int device = 0;
+    MB_CK(cudaGetDevice(&device));
+    const mb_opts o = opts ? *opts : mb_opts{};
+    std::unique_ptr<Pipeline> keep =
+        take_pipeline(idx, device, o, max_nr, max_nb, !seq_dev, !off_dev, mate && !mate_dev);
+    if (!keep) {
+        keep.reset(new Pipeline);
+        Pipeline &p = *keep;
+        p.idx = idx;
+        p.device = device;
+        p.opts = o;
+        p.max_nr = max_nr;
+        p.max_nb = max_nb;
+        p.own_seq = !seq_dev;
+        p.own_off = !off_dev;
+        p.own_mate = mate && !mate_dev;
+        const u64 max_smem = 4ull * max_nr + max_nb / 32 + 64;
+        const u64 max_hits = 4ull * max_smem;
+        MB_CK(cudaEventCreateWithFlags(&p.start, cudaEventDisableTiming));
+        for (Stage &x : p.s) {
+            MB_CK(cudaStreamCreateWithFlags(&x.st, cudaStreamNonBlocking));
+            MB_CK(cudaEventCreateWithFlags(&x.ev, cudaEventDisableTiming));
+            MB_CK(cudaMallocHost(&x.hcnt, 16));
+            MB_TRY(mb_plan_create(idx, opts, max_nr, max_nb, max_smem, max_hits, &x.plan));
+            if (p.own_seq) MB_CK(cudaMalloc(&x.dseq, max_nb + 16));
+            if (p.own_off) MB_CK(cudaMalloc(&x.doff, ((size_t)max_nr + 1) * 8));
+            if (p.own_mate) MB_CK(cudaMalloc(&x.dmate, max_nr));
+        }
     }
+    Pipeline &pl = *keep;
+    MB_CK(cudaEventRecord(pl.start, ust));
+    for (Stage &x : pl.s) MB_CK(cudaStreamWaitEvent(x.st, pl.start, 0));   // after the caller's earlier work
 
     // inputs of chunk i in, then its whole stage, then its two counts to the host
     auto enqueue = [&](int i, Stage &x) -> int {
@@ -193,6 +272,7 @@ extern "C" int mb_seed_locate(const mb_index *idx, const uint8_t *seq, const uin
         if (i + PIPE_STAGES < nc) MB_TRY(enqueue(i + PIPE_STAGES, x));
     }
     for (Stage &x : pl.s) MB_CK(cudaStreamSynchronize(x.st));
+    keep_pipeline(std::move(keep));
     *n_out = m_tot;
     *n_hits = h_tot;
     if (over) {

@@ -127,7 +127,7 @@ __device__ __forceinline__ u64 convert8(u64 x, u32 conv) {
     return x;
 }
 
-// k-mer code of P[j-K+1 .. j] (K <= 12), first base in the lowest bits; false if it holds an N.
+// k-mer code of P[j-K+1 .. j] (K <= 14), first base in the lowest bits; false if it holds an N.
 // The K bytes lie in two aligned 16-byte chunks: both are loaded, the K bytes shifted out, and
 // tested, converted and packed eight at a time.  Next to the end of the batch it goes byte by
 // byte.
@@ -591,81 +591,92 @@ __global__ void k_expand_rows(const mb_smem *__restrict__ sm, u64 nsm, const u64
 }
 
 // Locate (Algorithm 2).  Each lane LF-walks D rows at a time (D independent block reads in
-// flight per lane), one step of each per loop iteration; a walk that ends is replaced at once by
-// the next row of the warp's range (rows are prefetched 64 ahead, two coalesced buffers, and
-// handed over by shuffle).  A walk ends on a sampled row (position = steps + S(row)) or on the $
-// row (S = 0, position = steps).  The sampled-SA reads and the block reads of one iteration are
-// issued together.  A walk needs fewer than n steps; the bound only guards against a corrupted
-// index (it then writes 0xFFFFFFFF).
+// flight per lane), one step of each per loop iteration.  The walks that end in an iteration are
+// replaced by the next rows of the warp's range in one hand-out: the lanes' counts of ended walks
+// are scanned across the warp, each ended walk takes the next offset in lane order, then slot
+// order, and loads its row directly (the range's rows are prefetched into L1 about 128 ahead).  A
+// walk ends on a sampled row (position = steps + S(row)) or on the $ row (S = 0, position =
+// steps).  The sampled-SA reads and the block reads of one iteration are issued together.  A walk
+// needs fewer than n steps; the bound only guards against a corrupted index (it then writes
+// 0xFFFFFFFF).  Offsets within a warp's range are u32 (the host keeps ranges below 2^32 - 2^12).
+// Launch bounds: 16 walks per lane fit one block of 8 warps per SM, 8 walks two blocks, fewer
+// walks three.
 template <bool COUNT, bool POW2, int D>
-__global__ void __launch_bounds__(256) k_locate(DevIndex I, const u32 *__restrict__ rows, u64 nhits,
+__global__ void __launch_bounds__(256, D == 8 ? 2 : 1) k_locate(DevIndex I, const u32 *__restrict__ rows, u64 nhits,
                                                 const u64 *__restrict__ nhits_dev, u32 *__restrict__ hits, u64 *wc) {
-    const u32 lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+    const u32 lane = threadIdx.x & 31;
     if (nhits_dev && *nhits_dev < nhits) nhits = *nhits_dev;
     Work<COUNT> work;
     const u32 r = I.r, rmask = I.r - 1, rshift = __ffs(I.r) - 1, prim = (u32)I.primary, n = (u32)I.n;
     const u32 C0 = (u32)I.C[0], C1 = (u32)I.C[1], C2 = (u32)I.C[2], C3 = (u32)I.C[3];
     WarpRange wr;
     wr.init(nhits);
-    // rows of the range, 64 ahead: buf0 holds rows[bufbase + lane], buf1 rows[bufbase + 32 + lane];
-    // before every hand-over bufbase <= wr.next < bufbase + 32.
-    u64 bufbase = wr.next;
-    u32 buf0 = bufbase + lane < wr.end ? __ldg(&rows[bufbase + lane]) : 0u;
-    u32 buf1 = bufbase + 32 + lane < wr.end ? __ldg(&rows[bufbase + 32 + lane]) : 0u;
-    u64 h[D];
-    bool live[D];
-    u32 row[D], steps[D];
-    // hands the next items of the range to the lanes in `fm` (in lane order), walk slot d
-    auto hand_over = [&](u32 fm, bool mine, int d) {
-        const u64 idx = wr.next + __popc(fm & lt);
-        const u32 o = (u32)(idx - bufbase);   // < 64
-        const u32 v0 = __shfl_sync(0xffffffffu, buf0, o & 31), v1 = __shfl_sync(0xffffffffu, buf1, o & 31);
-        if (mine) {
-            h[d] = idx;
-            live[d] = idx < wr.end;
-            row[d] = o < 32 ? v0 : v1;
-            steps[d] = 0;
-        }
-        wr.next += __popc(fm);
-        if (wr.next >= bufbase + 32) {     // first buffer used up: slide by 32
-            bufbase += 32;
-            buf0 = buf1;
-            buf1 = bufbase + 32 + lane < wr.end ? __ldg(&rows[bufbase + 32 + lane]) : 0u;
-        }
-    };
+    const u64 wbase = wr.next;
+    const u32 wlen = (u32)(wr.end - wr.next);
+    const u32 *__restrict__ wrows = rows + wbase;
+    u32 *__restrict__ whits = hits + wbase;
+    u32 h[D], row[D], steps[D];
+    u32 live = 0;   // bit d: slot d holds a walk
+    u32 next = 0;   // next offset of the range to hand out (warp-uniform)
 #pragma unroll
-    for (int d = 0; d < D; ++d) hand_over(0xffffffffu, true, d);
+    for (int d = 0; d < D; ++d) {
+        const u32 o = next + lane;
+        h[d] = o;
+        steps[d] = 0;
+        row[d] = 0;
+        if (o < wlen) {
+            live |= 1u << d;
+            row[d] = __ldg(&wrows[o]);
+        }
+        next += 32;
+    }
     for (;;) {
-        bool any = false;
-#pragma unroll
-        for (int d = 0; d < D; ++d) any |= live[d];
-        if (__all_sync(0xffffffffu, !any)) break;
-        bool stop[D], sampled[D];
+        if (__all_sync(0xffffffffu, live == 0)) break;
+        if (next + 128 + lane < wlen) asm volatile("prefetch.global.L1 [%0];" ::"l"(wrows + next + 128 + lane));
+        u32 stop = 0, smp = 0;
         u32 sv[D];
         Blk b[D];
 #pragma unroll
         for (int d = 0; d < D; ++d) {
-            sampled[d] = POW2 ? (row[d] & rmask) == 0 : row[d] % r == 0;
-            stop[d] = live[d] && (sampled[d] || row[d] == prim || steps[d] > n);
+            const bool on = (live >> d) & 1u;
+            const bool sampled = POW2 ? (row[d] & rmask) == 0 : row[d] % r == 0;
+            const bool st = on && (sampled || row[d] == prim || steps[d] > n);
             sv[d] = 0;
-            if (stop[d] && sampled[d]) sv[d] = __ldg(&I.ssa[POW2 ? (row[d] >> rshift) : row[d] / r]);
-            if (live[d] && !stop[d]) b[d] = load_blk(I.occ + (row[d] >> BLK_SHIFT));
+            if (st) {
+                stop |= 1u << d;
+                if (sampled) {
+                    smp |= 1u << d;
+                    sv[d] = __ldg(&I.ssa[POW2 ? (row[d] >> rshift) : row[d] / r]);
+                }
+            } else if (on) {
+                b[d] = load_blk(I.occ + (row[d] >> BLK_SHIFT));
+            }
         }
+        // offsets for this iteration's ended walks: exclusive scan of the per-lane counts
+        const u32 cnt = __popc(stop);
+        u32 incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const u32 v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (u32)o) incl += v;
+        }
+        u32 give = next + incl - cnt;
+        next += __shfl_sync(0xffffffffu, incl, 31);
 #pragma unroll
         for (int d = 0; d < D; ++d) {
-            if (stop[d]) {
-                hits[h[d]] = steps[d] > n ? 0xFFFFFFFFu : (sampled[d] ? sv[d] + steps[d] : steps[d]);
+            if ((stop >> d) & 1u) {
+                whits[h[d]] = steps[d] > n ? 0xFFFFFFFFu : (((smp >> d) & 1u) ? sv[d] + steps[d] : steps[d]);
                 work.lf += steps[d];
-                work.sa += sampled[d] ? 1 : 0;
-            } else if (live[d]) {
+                work.sa += (smp >> d) & 1u;
+                h[d] = give;
+                steps[d] = 0;
+                if (give < wlen) row[d] = __ldg(&wrows[give]);
+                else live &= ~(1u << d);
+                ++give;
+            } else if ((live >> d) & 1u) {
                 row[d] = lf_blk(b[d], row[d], prim, C0, C1, C2, C3);
                 ++steps[d];
             }
-        }
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-            const u32 fm = __ballot_sync(0xffffffffu, stop[d]);
-            if (fm) hand_over(fm, stop[d], d);
         }
     }
     work.flush(wc);
@@ -722,18 +733,25 @@ template <bool COUNT, bool POW2, int D>
 int launch_locate_t(const DevIndex &I, const u32 *rows, u64 nhits, const u64 *nhits_dev, u32 *hits, u64 *wc,
                     cudaStream_t st) {
     const unsigned g = resident_grid((const void *)k_locate<COUNT, POW2, D>, 256, (nhits + 63) / 64 * 32);
+    const u64 warps = (u64)g * 8;
+    if ((nhits + warps - 1) / warps >= (1ull << 32) - 4096) {   // offsets within a warp's range are u32
+        mb_set_error("locate: %llu hits over %llu warps", (unsigned long long)nhits, (unsigned long long)warps);
+        return MB_ERR_ARG;
+    }
     k_locate<COUNT, POW2, D><<<g, 256, 0, st>>>(I, rows, nhits, nhits_dev, hits, wc);
     MB_KCHECK();
     return MB_OK;
 }
 
-// The locate kernel: work counters, power-of-two sample rate, walks per lane (depth 1, 2 or 4).
+// The locate kernel: work counters, power-of-two sample rate, walks per lane (depth 1, 2, 4, 8, 16).
 int launch_locate(const DevIndex &I, const u32 *rows, u64 nhits, const u64 *nhits_dev, u32 *hits, u64 *wc,
                   bool count, u32 depth, cudaStream_t st) {
     const bool pow2 = (I.r & (I.r - 1)) == 0;
     if (count) return pow2 ? launch_locate_t<true, true, 1>(I, rows, nhits, nhits_dev, hits, wc, st)
                            : launch_locate_t<true, false, 1>(I, rows, nhits, nhits_dev, hits, wc, st);
     if (!pow2) return launch_locate_t<false, false, 1>(I, rows, nhits, nhits_dev, hits, wc, st);
+    if (depth >= 16) return launch_locate_t<false, true, 16>(I, rows, nhits, nhits_dev, hits, wc, st);
+    if (depth >= 8) return launch_locate_t<false, true, 8>(I, rows, nhits, nhits_dev, hits, wc, st);
     if (depth >= 4) return launch_locate_t<false, true, 4>(I, rows, nhits, nhits_dev, hits, wc, st);
     if (depth >= 2) return launch_locate_t<false, true, 2>(I, rows, nhits, nhits_dev, hits, wc, st);
     return launch_locate_t<false, true, 1>(I, rows, nhits, nhits_dev, hits, wc, st);
@@ -1142,7 +1160,8 @@ extern "C" int mb_plan_create(const mb_index *idx, const mb_opts *opts, uint32_t
     P->kmer = !(P->flags & MB_NO_KMER) && P->l >= mb_dev_index(idx).kmer_k;
     P->queue = (P->flags & MB_BATCHED) != 0;
     P->block = opts && (opts->block_size == 128 || opts->block_size == 512) ? (int)opts->block_size : 256;
-    P->depth = opts && opts->prefetch_depth >= 4 ? 4u : (opts && opts->prefetch_depth >= 2 ? 2u : 1u);
+    const u32 dq = opts ? opts->prefetch_depth : 0;
+    P->depth = dq >= 16 ? 16u : (dq >= 8 ? 8u : (dq >= 4 ? 4u : (dq >= 2 ? 2u : 1u)));
     P->max_reads = max_reads;
     P->max_bases = max_bases;
     P->max_smem = max_smem ? max_smem : 1;
@@ -1333,7 +1352,7 @@ extern "C" int mb_autotune(const mb_index *idx, const uint8_t *seq, const uint64
     int rc = MB_OK;
     for (int q = 0; q < 2 && rc == MB_OK; ++q)
         for (int bi = 0; bi < 3 && rc == MB_OK; ++bi)
-        for (int dep = 1; dep <= 4 && rc == MB_OK; dep *= 2) {
+        for (int dep = 1; dep <= 16 && rc == MB_OK; dep *= 2) {
             mb_opts o = opts ? *opts : mb_opts{};
             o.flags = (o.flags & ~MB_BATCHED) | (q ? MB_BATCHED : 0u);
             o.block_size = (u32)blocks[bi];

@@ -43,7 +43,7 @@ def test_plain_matches_oracle(mb, mixed):
     assert np.array_equal(hits.astype(np.uint64), ohits)
 
 
-@pytest.mark.parametrize("depth", [1, 2, 4])
+@pytest.mark.parametrize("depth", [1, 2, 4, 8, 16])
 @pytest.mark.parametrize("queue", [False, True])
 @pytest.mark.parametrize("block", [128, 256, 512])
 def test_plan_every_launch_shape(mb, mixed, queue, block, depth):

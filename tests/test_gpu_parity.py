@@ -106,15 +106,33 @@ def test_workload1_full(mb):
     compare_seed(sm, hits, X, rd.seq, rd.off)
 
 
-@pytest.mark.parametrize("depth", [1, 2, 4])
+@pytest.mark.parametrize("depth", [1, 2, 4, 8, 16])
 def test_locate_walks_per_lane(mb, depth):
-    """Locate with one or two LF-walks in flight per lane gives the same hits."""
+    """Locate with 1, 2, 4, 8 or 16 LF-walks in flight per lane gives the same hits."""
     ref, rd, p = synth.workload(2, scale=0.01)
     G = mb.mb_index_build(ref)
     X = oracle.Index(ref)
     sm, m, nh = mb.mb_seed_batch(G, rd.seq, rd.off)
     hits, _ = mb.mb_locate(G, sm, m, opts=dict(prefetch_depth=depth), cap=nh)
     compare_seed(sm, hits, X, rd.seq, rd.off)
+
+
+@pytest.mark.parametrize("k", [12, 14])
+def test_larger_kmer_tables(mb, k):
+    """k-mer tables above the paper's k = 10 (12 * 4^k bytes, 3.2 GB at k = 14): sampled entries
+    against the oracle's ds-intervals, and the same SMEMs and hits as without a table."""
+    ref, rd, p = synth.workload(2, scale=0.005)
+    G = mb.mb_index_build(ref, opts=dict(kmer_k=k))
+    X = oracle.Index(ref)
+    e = G.export(kmer=True, kmer_k=k)
+    words = np.sort(np.random.default_rng(k).choice(4 ** k, 50_000, replace=False)).astype(np.int64)
+    pats = np.stack([(words >> (2 * t)) & 3 for t in range(k)], axis=1).astype(np.uint8)
+    assert np.array_equal(e["kmer"].reshape(-1, 3)[words], X.ds_intervals(pats).astype(np.uint32))
+    del e
+    sm, hits = mb.seed(G, rd.seq, rd.off)
+    compare_seed(sm, hits, X, rd.seq, rd.off)
+    nsm, nhits = mb.seed(G, rd.seq, rd.off, opts=dict(flags=mb.MB_NO_KMER))
+    assert sm.tobytes() == nsm.tobytes() and np.array_equal(hits, nhits)
 
 
 def test_workload2_scaled_device_pointers(mb):
