@@ -73,8 +73,8 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def gather_ceiling(gib: int = 4):
-    """Random 64-/32-byte block reads over a buffer far above L2 (probe library): independent
+def gather_ceiling(gib: float = 4, modes=((0, "indep", 2048), (1, "chain", 512), (2, "chain_l2only", 512))):
+    """Random 64-/32-byte block reads over a buffer of `gib` GiB (probe library): independent
     reads (bandwidth ceiling) and dependent chains (LF-walk pattern), GB/s of bytes requested."""
     import ctypes
     from paper_2606_15357_gb300.nvcc_build import build_probe
@@ -84,11 +84,24 @@ def gather_ceiling(gib: int = 4):
     L.mb_probe_gather.restype = ctypes.c_double
     out = {}
     ms = ctypes.c_float()
-    for mode, name, iters in ((0, "indep", 2048), (1, "chain", 512), (2, "chain_l2only", 512)):
+    for mode, name, iters in modes:
         for bb in (64, 32):
-            out[f"random{bb}_{name}_GBps"] = L.mb_probe_gather(gib << 30, mode, bb, iters, ctypes.byref(ms))
+            out[f"random{bb}_{name}_GBps"] = L.mb_probe_gather(int(gib * (1 << 30)), mode, bb, iters,
+                                                                ctypes.byref(ms))
     out["buffer_GiB"] = gib
     return out
+
+
+def probe_sweep():
+    """Random-read rate against buffer size (L2-resident to far above L2): one JSON line per size,
+    with the 32-byte rate also in reads/s."""
+    import torch
+    torch.cuda.init()
+    for gib in (1 / 32, 3 / 32, 1 / 4, 1, 4, 8):
+        gc = gather_ceiling(gib, modes=((0, "indep", 2048), (1, "chain", 512)))
+        gc["random32_indep_Greads_per_s"] = gc["random32_indep_GBps"] / 32
+        print(json.dumps(gc), flush=True)
+    return 0
 
 
 def kernel_source_hash() -> str:
@@ -662,7 +675,9 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the mixed-length batched comparison")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-form measurement")
     ap.add_argument("--serve-requests", type=int, default=600)
-    ap.add_argument("--probe-gib", type=int, default=1, help="buffer of the random-gather probe (GiB)")
+    ap.add_argument("--probe-gib", type=float, default=1, help="buffer of the random-gather probe (GiB)")
+    ap.add_argument("--probe-sweep", action="store_true",
+                    help="only the random-read probe over buffer sizes 1/32 .. 8 GiB (one JSON line each)")
     ap.add_argument("--kmer-k", type=int, default=14, choices=range(1, 15),
                     help="k of the k-mer ds-interval table (Section 2.5 uses 10; same SMEMs for any k)")
     ap.add_argument("--autotune", action="store_true",
@@ -673,6 +688,8 @@ def main():
     ap.add_argument("--reads", type=int, default=0,
                     help="seed only the first N reads of the batch (for ncu captures of the full index)")
     args = ap.parse_args()
+    if args.probe_sweep:
+        return probe_sweep()
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -5,8 +5,8 @@
 //   mode 1: dependent chains: each read's address comes from the data just read, the access
 //           pattern of an LF-walk (latency-bound ceiling at full occupancy)
 //   mode 2: as mode 1 with loads cached in L2 only (ld.global.cg)
-// Blocks are 64 bytes (two 256-bit loads) or 32 bytes (one), at random 64-byte-aligned places
-// of a buffer of `bytes` bytes (fewer than 2^32 blocks).
+// Blocks are 64 bytes (two 256-bit loads) or 32 bytes (one), at random block-aligned places of
+// a buffer of `bytes` bytes (fewer than 2^32 blocks).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(256) k_indep(const u64 *buf, u64 nblocks, unsi
 #pragma unroll
         for (int u = 0; u < 8; ++u) idx[u] = __umulhi(h32((uint32_t)tid * 0x9E3779B9u + it * 8 + u), (uint32_t)nblocks);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) acc ^= ld_block<BYTES>(buf + idx[u] * 8);
+        for (int u = 0; u < 8; ++u) acc ^= ld_block<BYTES>(buf + idx[u] * (BYTES / 8));
     }
     if (acc == 0x1234567) sink[tid & 1023] = acc;
 }
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(256) k_chain(const u64 *buf, u64 nblocks, unsi
     const u64 tid = blockIdx.x * (u64)blockDim.x + threadIdx.x;
     u64 idx = __umulhi(h32((uint32_t)tid), (uint32_t)nblocks);
     for (unsigned it = 0; it < iters; ++it)
-        idx = __umulhi(h32((uint32_t)ld_block<BYTES, CG>(buf + idx * 8) ^ it), (uint32_t)nblocks);
+        idx = __umulhi(h32((uint32_t)ld_block<BYTES, CG>(buf + idx * (BYTES / 8)) ^ it), (uint32_t)nblocks);
     if (idx == 0x1234567) sink[tid & 1023] = idx;
 }
 
@@ -77,11 +77,12 @@ __global__ void __launch_bounds__(256) k_chain(const u64 *buf, u64 nblocks, unsi
 // Returns the achieved rate in GB/s (bytes actually requested: BYTES per read), or a negative
 // value on a CUDA error.  `ms` receives the kernel time.
 extern "C" double mb_probe_gather(uint64_t bytes, int mode, int block_bytes, unsigned iters, float *ms) {
-    if (bytes / 64 >= (1ull << 32)) return -3;
+    if (block_bytes != 32 && block_bytes != 64) return -3;
+    if (bytes / block_bytes >= (1ull << 32)) return -3;
     u64 *buf = nullptr, *sink = nullptr;
     if (cudaMalloc(&buf, bytes) != cudaSuccess) return -1;
     if (cudaMalloc(&sink, 1024 * 8) != cudaSuccess) { cudaFree(buf); return -1; }
-    const u64 words = bytes / 8, nblocks = bytes / 64;
+    const u64 words = bytes / 8, nblocks = bytes / block_bytes;
     k_fill<<<2048, 256>>>(buf, words);
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
