@@ -200,7 +200,7 @@ def make_inputs(workload: int, scale: float, rank: int, reads: int = 0):
 
 
 # --------------------------------------------------------------------------------- oracle side
-def oracle_rate(ref, rd, params, target_s: float, threads: int, min_reads: int = 64):
+def oracle_rate(ref, rd, params, target_s: float, threads: int, min_reads: int = 2048):
     """Time the CPU oracle (index built first, untimed) on a bounded sample of the reads."""
     import oracle
     t = time.time()
@@ -241,7 +241,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "scale": args.scale, "min_len": params["min_len"],
-                   "max_occ": params["max_occ"], "sa_rate": params["sa_rate"]},
+                   "max_occ": params["max_occ"], "sa_rate": params["sa_rate"], "kmer_k": args.kmer_k},
         "cpu_baseline": {"value": value, "unit": "reads/s", "cores": threads, "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": value, "unit": "reads/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -340,6 +340,44 @@ def serve_requests(ref, n, seed):
                              indel=0.0002)
         reqs.append(rd)
     return reqs
+
+
+# Integer lanes of the GB300 (152 SMs x 4 sub-partitions x 32 lanes) at the 2,070 MHz SM clock: the
+# roofline of the mate-rescue prefilter, which counts one compare and one add per q-mer pair.
+INT_LANE_OPS_PER_S = 152 * 128 * 2.07e9
+
+
+def bench_rescue(mb, torch, dev, ref, n_pairs: int, reps: int = 5):
+    """Mate-rescue prefilter (Section 2.6): max_t M_t of 7-mer matches for n_pairs (150 bp read,
+    600 bp window) pairs drawn from the reference, device buffers, kernel timed by CUDA events."""
+    r, ro, w, wo = synth.rescue_pairs(ref, n_pairs, 0x6D620006)
+    dr, dro = torch.from_numpy(r).to(dev), torch.from_numpy(ro.view(np.int64)).to(dev)
+    dw, dwo = torch.from_numpy(w).to(dev), torch.from_numpy(wo.view(np.int64)).to(dev)
+    best = torch.empty(n_pairs, dtype=torch.int32, device=dev)
+    mb.mb_rescue_prefilter(dr, dro, dw, dwo, best=best)   # warm-up
+    mb.profile_reset()
+    mb.profile_enable(True)
+    torch.cuda.synchronize()
+    t = time.time()
+    for _ in range(reps):
+        mb.mb_rescue_prefilter(dr, dro, dw, dwo, best=best)
+    torch.cuda.synchronize()
+    call_s = (time.time() - t) / reps
+    mb.profile_enable(False)
+    kms, kn = mb.profile_get("rescue")
+    kms /= max(kn, 1)
+    q = 7
+    compares = float(np.sum((np.diff(ro.astype(np.int64)) - q + 1).clip(0) *
+                            (np.diff(wo.astype(np.int64)) - q + 1).clip(0)))
+    got = best.cpu().numpy().view(np.uint32)
+    achieved = 2 * compares / (kms / 1000.0)
+    return {"workload": f"{n_pairs:,} pairs of a 150 bp read and a 600 bp window of the 1 Gbp reference, "
+                        "half of them true (read inside the window, 1% substitutions)",
+            "q": q, "pairs_per_s": n_pairs / (kms / 1000.0), "call_pairs_per_s": n_pairs / call_s,
+            "kernel_ms": kms, "pass_frac": float((got >= 10).mean()),
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": INT_LANE_OPS_PER_S / 1e12,
+                         "unit": "T int ops/s", "frac": achieved / INT_LANE_OPS_PER_S,
+                         "ops": "2 per q-mer pair compared (compare, add)", "compares_per_launch": compares}}
 
 
 def bench_served(mb, G, ref, n_requests: int, load: float = 0.7):
@@ -606,6 +644,11 @@ def run_gpu(args):
                "note": "two_calls = mb_seed_batch + mb_locate on host buffers (the records are staged back in)"}
         log(f"e2e: {e2e}")
 
+    rescue = None
+    if rank == 0 and not args.no_rescue:
+        rescue = bench_rescue(mb, torch, dev, ref, args.rescue_pairs)
+        log(f"rescue prefilter: {rescue}")
+
     served = None
     if rank == 0 and not args.no_serve:
         served = bench_served(mb, idx, ref, args.serve_requests)
@@ -624,9 +667,17 @@ def run_gpu(args):
         t = time.time()
         X.seed(sample.seq, sample.off, params["min_len"], params["min_occ"], params["max_occ"], threads=threads)
         dt = time.time() - t
+        # one core, on a smaller sample of the same draw (about a tenth of the time budget)
+        n1 = max(64, min(sample.n, int(sample.n / dt * args.cpu_s / 10 / threads)))
+        one = sample.subset(np.arange(n1))
+        t = time.time()
+        X.seed(one.seq, one.off, params["min_len"], params["min_occ"], params["max_occ"], threads=1)
+        dt1 = time.time() - t
         cpu = {"value": sample.n / dt, "unit": "reads/s", "cores": threads, "kind": "oracle",
                "sample": f"{sample.n} reads drawn from the {rd.n}-read batch; oracle index build "
-                         f"({obuild_s:.0f}s) untimed", "seconds": dt}
+                         f"({obuild_s:.0f}s) untimed", "seconds": dt,
+               "single_core": {"value": one.n / dt1, "unit": "reads/s", "cores": 1,
+                               "sample": f"the first {one.n} reads of that sample", "seconds": dt1}}
         del X
 
     if rank != 0:
@@ -650,6 +701,7 @@ def run_gpu(args):
         "gpu_launches": launches,
         "forms": forms,
         "batched": batched,
+        "rescue_prefilter": rescue,
         "served": served,
         "clocks": clk.summary(),
     }
@@ -674,6 +726,8 @@ def main():
                     help="L2 fetch granularity for this process (32/64/128; 0 = leave the default)")
     ap.add_argument("--no-batched", action="store_true", help="skip the mixed-length batched comparison")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-form measurement")
+    ap.add_argument("--no-rescue", action="store_true", help="skip the mate-rescue prefilter measurement")
+    ap.add_argument("--rescue-pairs", type=int, default=1_000_000)
     ap.add_argument("--serve-requests", type=int, default=600)
     ap.add_argument("--probe-gib", type=float, default=1, help="buffer of the random-gather probe (GiB)")
     ap.add_argument("--probe-sweep", action="store_true",

@@ -290,6 +290,57 @@ int mb_serve_stats(mb_server *srv, uint32_t *slots, uint64_t *groups, uint64_t *
 int mb_bs_filter(const mb_index *idx, const mb_smem *smem, uint64_t n_smem, const uint8_t *mate,
                  const uint32_t *hits, uint64_t n_hits, void *stream, uint8_t *keep);
 
+/* One piece of a split bisulfite seed (24 bytes): read[qbeg, qend) matches the text at pos; hit
+ * is the index of the seed's hit in mb_locate's output. */
+typedef struct {
+    uint64_t hit;
+    uint32_t read, qbeg, qend, pos;
+} mb_piece;
+
+/* ---------------------------------------------------------------------------------------
+ * mb_bs_split — Section 2.8: a seed found on the 3-base index may pair a read C with a
+ * reference T (read 1, C->T converted) or a read G with a reference A (read 2, G->A); such a
+ * T-to-C mismatch is not a bisulfite conversion.  For every hit h with keep[h] != 0 (keep may
+ * be NULL: every hit), the original read bases under the seed are compared with the original
+ * reference bases under the hit: for a hit in copy g = pos / |R| of the text
+ * CT(R) GA(R) rc(GA(R)) rc(CT(R)) $ at offset q = pos - g|R|, copies 0 and 1 give R[q + t],
+ * copies 2 and 3 the complement of R[|R| - 1 - (q + t)].  The seed is cut at every read C over
+ * a reference T (reads with mate 1) or read G over a reference A (mate 2); the cut base belongs
+ * to no piece; reads with mate 0 are not cut.  Pieces of at least opts->min_len (default 19)
+ * bases are written in hit order, then qbeg order; pos is the piece's text position.  A hit that
+ * does not lie inside one copy gives no piece.
+ *   ref          host or device, the |R| original reference codes (0..3; > 3 = N, never cuts)
+ *                the MB_BS3 index was built from.
+ *   seq, off, mate, smem, hits: the original (unconverted) reads and the outputs of
+ *                mb_seed_batch / mb_locate; keep: the output of mb_bs_filter or NULL.
+ *   out          host or device, room for `cap` pieces; *n_out receives the count (if it
+ *                exceeds cap: MB_ERR_CAPACITY, nothing written).
+ * Errors: MB_ERR_ARG (also for an index built without MB_BS3), MB_ERR_CAPACITY, MB_ERR_NOMEM,
+ * MB_ERR_CUDA.
+ */
+int mb_bs_split(const mb_index *idx, const uint8_t *ref, const uint8_t *seq, const uint64_t *off,
+                uint32_t n_reads, const uint8_t *mate, const mb_smem *smem, uint64_t n_smem,
+                const uint32_t *hits, const uint8_t *keep, uint64_t n_hits, const mb_opts *opts,
+                void *stream, mb_piece *out, uint64_t cap, uint64_t *n_out);
+
+/* ---------------------------------------------------------------------------------------
+ * mb_rescue_prefilter — the mate-rescue prefilter of Section 2.6: for each pair p of a read
+ * P = reads[read_off[p], read_off[p+1]) and a reference window R = wins[win_off[p],
+ * win_off[p+1]), best[p] = max over t of M_t = #{(i, j) : P[i, i+q) = R[j, j+q), j - i = t}
+ * (0 when no q-mer matches), over every q-mer start i of P and j of R.  A q-mer holding an N
+ * (code > 3) matches nothing.  The paper starts a Smith-Waterman alignment only when
+ * best >= 10 with q = 7.  Independent of any index.
+ *   reads, wins, read_off, win_off: host or device; offsets non-decreasing.
+ *   q        1..15 (0 = 7).
+ *   best     host or device, n_pairs u32.
+ * The longest read plus the longest window, 4 bytes per base, must fit one block's shared
+ * memory (e.g. reads of 1 kb with windows of 50 kb).
+ * Errors: MB_ERR_ARG, MB_ERR_NOMEM, MB_ERR_CUDA.
+ */
+int mb_rescue_prefilter(const uint8_t *reads, const uint64_t *read_off, const uint8_t *wins,
+                        const uint64_t *win_off, uint32_t n_pairs, uint32_t q, void *stream,
+                        uint32_t *best);
+
 /* Map a text position to the reference: strand 0 = forward, 1 = reverse complement;
  * rpos = the start on the forward strand of the match of length len. */
 int mb_hit_to_ref(const mb_index *idx, uint64_t pos, uint64_t len, int *strand, uint64_t *rpos);

@@ -82,6 +82,8 @@ def lib():
                 "orc_locate_sa": ([P, P, U64, P, I], None),
                 "orc_locate_slow": ([P, P, U64, P, I], None),
                 "orc_batch_locate": ([P, P, U64, P], None),
+                "orc_count_alg3": ([P, P, P, U32, U32, U32, U64, P], None),
+                "orc_count_locate": ([P, P, U64, P, I], None),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -216,6 +218,23 @@ class Index:
             lib().orc_batch_locate(self._h, _p(rows), len(rows), _p(out))
         return out
 
+    def count_alg3(self, seq, off, min_len: int = 19, min_occ: int = 1, block_rows: int = 64) -> tuple:
+        """Work of Algorithm 3 over the reads: (extension steps with a base, blocks of
+        `block_rows` rows those steps read: 1 if rows p and p+s share a block, else 2)."""
+        seq, off = _u8(seq), _u64(off)
+        out = np.zeros(2, dtype=np.uint64)
+        lib().orc_count_alg3(self._h, _p(seq), _p(off), len(off) - 1, min_len, min_occ, block_rows, _p(out))
+        return int(out[0]), int(out[1])
+
+    def count_locate(self, rows, threads: int = 0) -> tuple:
+        """Work of Algorithm 2 over the rows, the $ row counting as sampled with S = 0:
+        (LF steps, sampled-S reads)."""
+        rows = _u64(rows)
+        out = np.zeros(2, dtype=np.uint64)
+        if len(rows):
+            lib().orc_count_locate(self._h, _p(rows), len(rows), _p(out), threads)
+        return int(out[0]), int(out[1])
+
     def seed(self, seq, off, min_len: int = 19, min_occ: int = 1, max_occ: int = 500,
              threads: int = 0, method: str = "def"):
         """The whole seeding stage.  Returns (smem, over, hit_off, hits):
@@ -309,3 +328,114 @@ def bs_keep(pos, qlen, read_mate, rlen: int) -> np.ndarray:
     ok1 = (seg == 0) | (seg == 2)
     ok2 = (seg == 1) | (seg == 3)
     return whole & np.where(m == 1, ok1, np.where(m == 2, ok2, True))
+
+
+PIECE_DTYPE = np.dtype([("hit", np.uint64), ("read", np.uint32), ("qbeg", np.uint32),
+                        ("qend", np.uint32), ("pos", np.uint32)])
+
+
+def bs_split(ref, seq, off, mate, sm, hits, keep, min_len: int = 19, over=None) -> np.ndarray:
+    """Section 2.8, T-to-C split of bisulfite seed matches.  For every kept hit (record m of
+    `sm`, text position p = hits[h]) the original read bases x_t = read[qbeg + t] are compared
+    with the original reference bases under the seed: copy g = p // |R| of the 3-base text, offset
+    q = p - g |R|; copies 0 and 1 read R[q + t], copies 2 and 3 (reverse complements) read
+    comp(R[|R| - 1 - (q + t)]).  A read-1 seed (C->T converted) breaks where the read has C over a
+    reference T; a read-2 seed (G->A) where the read has G over a reference A; other reads do not
+    break.  The seed is cut at every such position (the position itself leaves the seed) and the
+    pieces of at least min_len bases are returned as (hit, read, qbeg, qend, pos), pos = the
+    piece's text position, in hit order then qbeg order.  `over` marks the records over max_occ
+    (no hits); by default bit 0 of sm["flags"]."""
+    ref = np.asarray(ref, dtype=np.uint8)
+    seq = np.asarray(seq, dtype=np.uint8)
+    off = np.asarray(off, dtype=np.int64)
+    mate = np.asarray(mate)
+    M = len(ref)
+    comp = np.array([3, 2, 1, 0, 4], dtype=np.uint8)
+    if over is None:   # records with a flags field (the library's layout): bit 0 = over max_occ
+        over = (sm["flags"] & 1).astype(bool)
+    cnt = np.where(over, 0, sm["s"]).astype(np.int64)
+    out = []
+    h = 0
+    for m in range(len(sm)):
+        rd, qb, qe = int(sm["read"][m]), int(sm["qbeg"][m]), int(sm["qend"][m])
+        for _ in range(int(cnt[m])):
+            if keep is None or keep[h]:
+                p = int(hits[h])
+                g, q = p // M, p - (p // M) * M
+                L = qe - qb
+                if g < 2:
+                    R = ref[q:q + L]
+                else:
+                    R = comp[np.minimum(ref[M - q - L:M - q][::-1], 4)]
+                x = seq[off[rd] + qb:off[rd] + qe]
+                mt = int(mate[rd])
+                if mt == 1:
+                    cut = (x == 1) & (R == 3)
+                elif mt == 2:
+                    cut = (x == 2) & (R == 0)
+                else:
+                    cut = np.zeros(L, dtype=bool)
+                edges = [-1] + np.nonzero(cut)[0].tolist() + [L]
+                for a, b in zip(edges[:-1], edges[1:]):
+                    if b - (a + 1) >= min_len:
+                        out.append((h, rd, qb + a + 1, qb + b, p + a + 1))
+            h += 1
+    arr = np.zeros(len(out), dtype=PIECE_DTYPE)
+    for i, t in enumerate(out):
+        arr[i] = t
+    return arr
+
+
+def qmer_diag_max(P, R, q: int = 7) -> int:
+    """Mate-rescue prefilter (Section 2.6): M_t = |{(i, j) : P[i, i+q) = R[j, j+q), j - i = t}|
+    over every q-mer start i of P and j of R, and the result max_t M_t (0 when no q-mer matches).
+    A q-mer holding an N (code > 3) matches nothing.  Written as the definition: all pairs (i, j)
+    compared, matches counted per diagonal t."""
+    P = np.asarray(P, dtype=np.int64)
+    R = np.asarray(R, dtype=np.int64)
+    if len(P) < q or len(R) < q:
+        return 0
+    counts = {}
+    for i in range(len(P) - q + 1):
+        a = P[i:i + q]
+        if np.any(a > 3):
+            continue
+        for j in range(len(R) - q + 1):
+            b = R[j:j + q]
+            if np.array_equal(a, b):
+                counts[j - i] = counts.get(j - i, 0) + 1
+    return max(counts.values()) if counts else 0
+
+
+def qmer_diag_max_batch(reads, read_off, wins, win_off, q: int = 7) -> np.ndarray:
+    """qmer_diag_max for every (read, window) pair, by q-mer codes (same definition, vectorised
+    per pair: codes compared by broadcasting, matches binned by j - i)."""
+    reads = np.asarray(reads, dtype=np.uint8)
+    wins = np.asarray(wins, dtype=np.uint8)
+    read_off = np.asarray(read_off, dtype=np.int64)
+    win_off = np.asarray(win_off, dtype=np.int64)
+    out = np.zeros(len(read_off) - 1, dtype=np.uint32)
+
+    def codes(x):
+        n = len(x) - q + 1
+        if n <= 0:
+            return np.zeros(0, np.int64)
+        c = np.zeros(n, np.int64)
+        bad = np.zeros(n, bool)
+        for k in range(q):
+            s = x[k:k + n].astype(np.int64)
+            bad |= s > 3
+            c = c * 4 + np.minimum(s, 3)
+        c[bad] = -1
+        return c
+
+    for p in range(len(out)):
+        a = codes(reads[read_off[p]:read_off[p + 1]])
+        b = codes(wins[win_off[p]:win_off[p + 1]])
+        if len(a) == 0 or len(b) == 0:
+            continue
+        eq = (a[:, None] == b[None, :]) & (a[:, None] >= 0)
+        i, j = np.nonzero(eq)
+        if len(i):
+            out[p] = np.bincount(j - i + len(a)).max()
+    return out

@@ -269,8 +269,19 @@ void smem_def_read(const Index &X, const u8 *P, u32 m, u32 rid, u32 l, u32 c, st
  */
 struct QE { u8 u; u32 rd; int64_t i, j; DS v; };
 
+/* Work of Algorithm 1 calls, for the measurement's algorithmic bytes: one step per call with a
+ * base (an N reads nothing); the occurrence values a call needs sit at rows p and p+s of the
+ * strand it extends (p = k backwards, k' forwards), i.e. in one block of `block_rows` rows when
+ * both rows fall in it, else in two. */
+struct Work { u64 steps = 0, blocks = 0; u64 block_rows = 64; };
+void count_ext(Work *w, u64 p, u64 s, u8 a) {
+    if (!w || a > 4) return;
+    w->steps += 1;
+    w->blocks += (p / w->block_rows == (p + s) / w->block_rows) ? 1 : 2;
+}
+
 void smem_alg3(const Index &X, const u8 *seq, const u64 *off, u32 nr, u32 l, u32 c,
-               std::vector<std::vector<Smem>> &out) {
+               std::vector<std::vector<Smem>> &out, Work *work = nullptr) {
     std::deque<QE> Q;
     const DS empty{0, 0, X.n};
     auto P = [&](u32 rd, int64_t j) -> u8 { u8 b = seq[off[rd] + j]; return b < 4 ? (u8)(b + 1) : 5; };
@@ -278,6 +289,7 @@ void smem_alg3(const Index &X, const u8 *seq, const u64 *off, u32 nr, u32 l, u32
     for (u32 rd = 0; rd < nr; ++rd)
         if ((int64_t)l - 1 < len(rd)) Q.push_back(QE{1, rd, 0, (int64_t)l - 1, empty});
     auto back_step = [&](const QE &e) {
+        count_ext(work, e.v.k, e.v.s, P(e.rd, e.j));
         DS w = backward_ext(X, e.v, P(e.rd, e.j));
         if (w.s >= c) Q.push_back(QE{e.u, e.rd, e.i, e.j - 1, w});
         else if (e.j + (int64_t)l < len(e.rd)) Q.push_back(QE{1, e.rd, e.j + 1, e.j + (int64_t)l, empty});
@@ -292,6 +304,7 @@ void smem_alg3(const Index &X, const u8 *seq, const u64 *off, u32 nr, u32 l, u32
                 out[e.rd].push_back(Smem{e.rd, (u32)e.i, (u32)e.j, 0, e.v.k, e.v.kr, e.v.s});
                 continue;
             }
+            count_ext(work, e.v.kr, e.v.s, P(e.rd, e.j));
             DS w = forward_ext(X, e.v, P(e.rd, e.j));
             if (w.s >= c) Q.push_back(QE{2, e.rd, e.i, e.j + 1, w});
             else {
@@ -312,6 +325,13 @@ u64 locate_slow_one(const Index &X, u64 k) {
     u64 i = 0;
     while (k % X.r != 0) { k = pi(X, X.B[k], k); ++i; }
     return (i + X.ssa[k / X.r]) % X.n;
+}
+
+/* Work of one LocateSlow walk under the reading that the $ row counts as sampled with S = 0
+ * (the walk stops there): LF steps taken, and whether it ends by reading a sampled S value. */
+void locate_work(const Index &X, u64 k, u64 &steps, u64 &sa_reads) {
+    while (k % X.r != 0 && k != X.primary) { k = pi(X, X.B[k], k); ++steps; }
+    if (k % X.r == 0) ++sa_reads;
 }
 
 /* BatchLocate: the same walks, advanced level by level over the set E */
@@ -478,5 +498,25 @@ void orc_locate_slow(void *x, const u64 *rows, u64 m, u64 *pos, int threads) {
 }
 /* Algorithm 2, BatchLocate (single thread, one set E) */
 void orc_batch_locate(void *x, const u64 *rows, u64 m, u64 *pos) { batch_locate(*(Index *)x, rows, m, pos); }
+
+/* Work counts for the algorithmic bytes: Algorithm 3 over the reads (out: extension steps,
+ * blocks of `block_rows` rows read), and Algorithm 2 over the rows (out: LF steps, S reads). */
+void orc_count_alg3(void *x, const u8 *seq, const u64 *off, u32 nr, u32 l, u32 c, u64 block_rows, u64 *out) {
+    std::vector<std::vector<Smem>> per(nr);
+    Work w;
+    w.block_rows = block_rows;
+    smem_alg3(*(Index *)x, seq, off, nr, l, c, per, &w);
+    out[0] = w.steps;
+    out[1] = w.blocks;
+}
+void orc_count_locate(void *x, const u64 *rows, u64 m, u64 *out, int threads) {
+    const Index &X = *(Index *)x;
+    u64 steps = 0, sa = 0;
+#pragma omp parallel for num_threads(threads > 0 ? threads : omp_get_max_threads()) schedule(dynamic, 64) \
+    reduction(+ : steps, sa)
+    for (u64 q = 0; q < m; ++q) locate_work(X, rows[q], steps, sa);
+    out[0] = steps;
+    out[1] = sa;
+}
 
 }  // extern "C"

@@ -73,6 +73,8 @@ def lib():
                 "mb_seed_locate": ([P, P, P, U32, P, OP, P, P, U64, P, U64, PU64, PU64], I),
                 "mb_bs_filter": ([P, P, U64, P, P, U64, P, P], I),
                 "mb_hit_to_ref": ([P, U64, U64, ctypes.POINTER(I), PU64], I),
+                "mb_bs_split": ([P, P, P, P, U32, P, P, U64, P, P, U64, OP, P, P, U64, PU64], I),
+                "mb_rescue_prefilter": ([P, P, P, P, U32, U32, P, P], I),
                 "mb_strerror": ([I], ctypes.c_char_p),
                 "mb_last_error": ([], ctypes.c_char_p),
                 "mb_seed_batch_noalloc": ([P, P, P, U32, P, OP, P, P, U64, PU64, PU64], I),
@@ -274,6 +276,39 @@ def mb_bs_filter(index: Index, smem, n_smem: int, mate, hits, n_hits: int, strea
     _check(lib().mb_bs_filter(index.handle, _ptr(smem), n_smem, _ptr(mate), _ptr(hits), n_hits,
                               _stream(stream), _ptr(keep)), "mb_bs_filter")
     return keep[:n_hits]
+
+
+PIECE_DTYPE = np.dtype([("hit", np.uint64), ("read", np.uint32), ("qbeg", np.uint32),
+                        ("qend", np.uint32), ("pos", np.uint32)])
+
+
+def mb_bs_split(index: Index, ref, seq, off, mate, smem, n_smem: int, hits, n_hits: int, keep=None,
+                opts=None, stream=None):
+    """Section 2.8 T-to-C split of bisulfite seed hits; returns a host array of PIECE_DTYPE."""
+    o = _opts(opts)
+    n_reads = (off.numel() if hasattr(off, "numel") else len(off)) - 1
+    n = ctypes.c_uint64()
+    cap = 0
+    while True:
+        buf = np.empty(max(cap, 1), dtype=PIECE_DTYPE)
+        rc = lib().mb_bs_split(index.handle, _ptr(ref), _ptr(seq), _ptr(off), n_reads, _ptr(mate), _ptr(smem),
+                               n_smem, _ptr(hits), _ptr(keep), n_hits, ctypes.byref(o), _stream(stream),
+                               _ptr(buf), cap, ctypes.byref(n))
+        if rc == MB_ERR_CAPACITY:
+            cap = n.value
+            continue
+        _check(rc, "mb_bs_split")
+        return buf[:n.value]
+
+
+def mb_rescue_prefilter(reads, read_off, wins, win_off, q: int = 7, stream=None, best=None):
+    """Section 2.6 mate-rescue prefilter: max_t M_t of q-mer matches per (read, window) pair."""
+    n = (read_off.numel() if hasattr(read_off, "numel") else len(read_off)) - 1
+    if best is None:
+        best = np.empty(max(n, 1), dtype=np.uint32)
+    _check(lib().mb_rescue_prefilter(_ptr(reads), _ptr(read_off), _ptr(wins), _ptr(win_off), n, q,
+                                     _stream(stream), _ptr(best)), "mb_rescue_prefilter")
+    return best[:n]
 
 
 def mb_reseed(index: Index, seq, off, smem, n_smem: int, mate=None, opts=None, stream=None):

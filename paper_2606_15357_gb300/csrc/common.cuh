@@ -251,6 +251,8 @@ int radix_sort_pairs(u64 *keys, u32 *vals, u64 *keys_alt, u32 *vals_alt, size_t 
 size_t mb_plan_bytes(const mb_plan *p);
 int mb_plan_counts_async(mb_plan *p, u64 *host_counts, cudaStream_t st);
 void mb_plan_arrays(const mb_plan *p, const mb_smem **smem, const u32 **hits, u64 *max_smem, u64 *max_hits);
+// build flags of an index (MB_BS3 for the 3-base bisulfite index)
+u32 mb_index_flags(const mb_index *x);
 // drops the host-buffer pipelines kept for an index (called when the index is freed)
 void mb_pipeline_forget(const mb_index *idx);
 

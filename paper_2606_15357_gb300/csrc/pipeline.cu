@@ -10,6 +10,7 @@
 // The streams, plans and staging buffers of a call are kept for the next call with the same index,
 // device and seeding options whose chunks fit them (at most two sets are kept; they are released
 // with the index), so steady-state calls allocate nothing.
+#include <algorithm>
 #include <memory>
 #include <mutex>
 #include <vector>
@@ -17,7 +18,7 @@
 
 namespace {
 
-constexpr u32 PIPE_READS = 1u << 21;      // default reads per chunk
+constexpr u32 PIPE_READS = 1u << 22;      // default reads per chunk
 constexpr u64 PIPE_BASES = 1ull << 29;    // at most this many bases per chunk (at least one read)
 constexpr int PIPE_STAGES = 2;
 
@@ -151,8 +152,12 @@ extern "C" int mb_seed_locate(const mb_index *idx, const uint8_t *seq, const uin
         Chunk c;
         c.r0 = r;
         c.o0 = hoff[r];
-        u32 e = r + 1;
-        while (e < n_reads && e - r < per && hoff[e + 1] - c.o0 <= PIPE_BASES) ++e;
+        // the chunk ends before the first read (after read r) whose end passes o0 + PIPE_BASES, and
+        // after at most `per` reads: a binary search over the offsets (which must not decrease)
+        const u32 emax = (u32)std::min<u64>((u64)n_reads, (u64)r + per);
+        const u64 lim = c.o0 + PIPE_BASES;
+        u32 e = (u32)(std::upper_bound(hoff + r + 2, hoff + emax + 1, lim) - (hoff + 1));
+        if (e < r + 1) e = r + 1;
         c.nr = e - r;
         c.o1 = hoff[e];
         if (c.o1 < c.o0) {

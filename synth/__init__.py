@@ -180,3 +180,36 @@ def workload(cfg: int, scale: float = 1.0, bisulfite: bool = False):
     else:
         raise ValueError(cfg)
     return ref, rd, params
+
+
+def rescue_pairs(ref: np.ndarray, n_pairs: int, seed: int, read_len: int = 150, win_len: int = 600,
+                 true_frac: float = 0.5, sub: float = 0.01):
+    """(read, reference window) pairs shaped like mate rescue: a window of `win_len` bases at a
+    uniform place of `ref`; for a `true_frac` share of pairs the read is a `read_len` substring
+    of the window (substitutions at rate `sub`), otherwise it comes from a uniform place
+    elsewhere; each pair is reverse-complemented as a whole with probability 1/2.
+    Returns (reads, read_off, wins, win_off), bases as codes 0..3 (4 = N, from the reference)."""
+    rng = np.random.default_rng(seed)
+    L = len(ref)
+    comp = np.array([3, 2, 1, 0, 4], dtype=np.uint8)
+    reads_out = np.empty(n_pairs * read_len, np.uint8)
+    wins_out = np.empty(n_pairs * win_len, np.uint8)
+    step = 65536
+    for a in range(0, n_pairs, step):
+        k = min(step, n_pairs - a)
+        w0 = rng.integers(0, L - win_len, k)
+        x = rng.integers(0, win_len - read_len + 1, k)
+        other = rng.integers(0, L - read_len, k)
+        is_true = rng.random(k) < true_frac
+        flip = rng.random(k) < 0.5
+        W = ref[w0[:, None] + np.arange(win_len)[None, :]]
+        R = ref[np.where(is_true, w0 + x, other)[:, None] + np.arange(read_len)[None, :]]
+        mut = rng.random(R.shape) < sub
+        R = np.where(mut & (R < 4), (R + rng.integers(1, 4, R.shape)) % 4, R).astype(np.uint8)
+        W[flip] = comp[np.minimum(W[flip], 4)][:, ::-1]
+        R[flip] = comp[np.minimum(R[flip], 4)][:, ::-1]
+        reads_out[a * read_len:(a + k) * read_len] = R.reshape(-1)
+        wins_out[a * win_len:(a + k) * win_len] = W.reshape(-1)
+    roff = np.arange(n_pairs + 1, dtype=np.uint64) * read_len
+    woff = np.arange(n_pairs + 1, dtype=np.uint64) * win_len
+    return reads_out, roff, wins_out, woff

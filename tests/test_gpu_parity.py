@@ -135,6 +135,26 @@ def test_larger_kmer_tables(mb, k):
     assert sm.tobytes() == nsm.tobytes() and np.array_equal(hits, nhits)
 
 
+def test_work_counters_match_oracle(mb):
+    """The counts behind the bench's algorithmic bytes: the GPU's counting kernels (no k-mer
+    table, so Algorithm 3 runs step by step as in the oracle) report the same extension steps,
+    blocks read, LF steps and sampled-S reads as the oracle's own counts on the same reads."""
+    ref, rd, p = synth.workload(2, scale=0.005)
+    G = mb.mb_index_build(ref)
+    X = oracle.Index(ref)
+    mb.profile_reset()
+    o = dict(flags=mb.MB_COUNT | mb.MB_NO_KMER)
+    sm, m, nh = mb.mb_seed_batch(G, rd.seq, rd.off, opts=o)
+    mb.mb_locate(G, sm, m, opts=o, cap=nh)
+    wc = mb.work_counters()
+    assert wc["kmer_lookups"] == 0
+    assert (wc["ext_steps"], wc["ext_blocks"]) == X.count_alg3(rd.seq, rd.off)
+    keep = (sm["flags"] & 1) == 0
+    rows = np.concatenate([np.arange(int(k), int(k) + int(s), dtype=np.uint64)
+                           for k, s in zip(sm["k"][keep], sm["s"][keep])])
+    assert (wc["lf_steps"], wc["sa_reads"]) == X.count_locate(rows)
+
+
 def test_workload2_scaled_device_pointers(mb):
     """Repeat-rich reference with N runs, paired 2x150 reads with indels; device buffers."""
     ref, rd, p = synth.workload(2, scale=0.02)
@@ -212,6 +232,32 @@ def test_bisulfite_index_and_seeding(mb):
     qlen = np.repeat((osm["qend"] - osm["qbeg"]).astype(np.int64), cnt)
     rmate = np.repeat(rd.mate[osm["read"].astype(np.int64)], cnt)
     assert np.array_equal(keep.astype(bool), oracle.bs_keep(ohits, qlen, rmate, len(ref)))
+
+
+def test_bisulfite_split(mb):
+    """Section 2.8 T-to-C split on the GPU against the oracle: reads with 1-3% substitutions so
+    that read C over reference T (read 1) and read G over reference A (read 2) occur; with the
+    strand filter's keep flags and with every hit, host and device buffers."""
+    ref = synth.reference(60_000, 73)
+    rd = synth.reads(ref, 800, 74, mode=1, read_len=150, bisulfite=True, sub_lo=0.01, sub_hi=0.03)
+    o = dict(flags=mb.MB_BS3)
+    G = mb.mb_index_build(ref, opts=o)
+    sm, m, nh = mb.mb_seed_batch(G, rd.seq, rd.off, mate=rd.mate, opts=o)
+    hits, _ = mb.mb_locate(G, sm, m, opts=o, cap=nh)
+    keep = mb.mb_bs_filter(G, sm, m, rd.mate, hits, nh)
+    for kp in (keep, None):
+        got = mb.mb_bs_split(G, ref, rd.seq, rd.off, rd.mate, sm, m, hits, nh, keep=kp)
+        want = oracle.bs_split(ref, rd.seq, rd.off, rd.mate, sm, hits, kp)
+        owner = np.repeat(np.arange(m), np.where(sm["flags"] & 1, 0, sm["s"]).astype(np.int64))
+        assert len(want) > 0 and np.any(want["qbeg"] != sm["qbeg"][owner[want["hit"].astype(np.int64)]])
+        assert got.tobytes() == want.astype(mb.PIECE_DTYPE).tobytes()
+    dgot = mb.mb_bs_split(G, dev(ref), dev(rd.seq), dev(rd.off), dev(rd.mate), dev(sm.view(np.uint8)), m,
+                          dev(hits), nh, keep=dev(keep))
+    assert dgot.tobytes() == mb.mb_bs_split(G, ref, rd.seq, rd.off, rd.mate, sm, m, hits, nh, keep=keep).tobytes()
+    # a plain index is refused
+    P = mb.mb_index_build(ref)
+    with pytest.raises(mb.MbError):
+        mb.mb_bs_split(P, ref, rd.seq, rd.off, rd.mate, sm, m, hits, nh, keep=keep)
 
 
 def test_save_load_roundtrip_and_corruption(mb, tmp_path):

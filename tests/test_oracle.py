@@ -314,3 +314,160 @@ def test_second_round_windows_by_brute_force():
     have = [tuple(int(y[f]) for f in ("read", "qbeg", "qend", "k", "kr", "s")) for y in sm2]
     assert have == want
     assert all(int(y["s"]) >= 2 for y in sm2)
+
+
+def test_locate_work_counts_by_suffix_array():
+    """LF steps and sampled-S reads of Algorithm 2 (the $ row taken as sampled with S = 0), pinned
+    by the suffix array alone: the walk from row x visits rows ISA[S(x) - j] for j = 0, 1, ...
+    and stops at the first row that is a multiple of r, or at text position 0 (the $ row)."""
+    ref = synth.repeat_rich_reference(30_000, 31, 0.3)
+    X = oracle.Index(ref, sa_rate=8)
+    S = X.sa().astype(np.int64)
+    isa = np.empty_like(S)
+    isa[S] = np.arange(X.n)
+    rows = np.random.default_rng(3).choice(X.n, 3000, replace=False).astype(np.uint64)
+    want_steps = want_sa = 0
+    for x in rows.tolist():
+        t, j = int(S[x]), 0
+        while isa[t - j] % 8 != 0 and t - j != 0:
+            j += 1
+        want_steps += j
+        want_sa += int(isa[t - j] % 8 == 0)
+    assert X.count_locate(rows) == (want_steps, want_sa)
+
+
+def test_alg3_work_counts_exact_unique_read():
+    """An error-free read that occurs in T takes exactly |P| extension steps in Algorithm 3
+    (l backward steps of stage 1, then |P| - l forward steps to the end, no stage 3); the blocks
+    each step reads follow from the intervals of the definition: backward step j extends
+    P[j+1, l) (rows k and k+s), forward step j extends P[0, j) (rows k' and k'+s)."""
+    ref = synth.reference(100_000, 41)
+    X = oracle.Index(ref)
+    l, L = 19, 120
+    for start in (1000, 55_555, 99_000):
+        P = ref[start:start + L].astype(np.uint8)
+        off = np.array([0, L], np.uint64)
+        br = 64
+        blocks = 0
+        for j in range(l - 1, -1, -1):
+            k, kr, s = X.ds_interval(P[j + 1:l]) if j + 1 < l else (0, 0, X.n)
+            blocks += 1 if k // br == (k + s) // br else 2
+        for j in range(l, L):
+            k, kr, s = X.ds_interval(P[0:j])
+            blocks += 1 if kr // br == (kr + s) // br else 2
+        assert X.count_alg3(P, off, l, 1, br) == (L, blocks)
+        # the same with 128-row blocks
+        assert X.count_alg3(P, off, l, 1, 128)[0] == L
+
+
+def _bs_seed_and_split(ref, seq, off, mate):
+    X = oracle.Index(ref, bs3=True)
+    conv = oracle.bs_convert_reads(seq, off, mate)
+    sm, over, hoff, hits = X.seed(conv, off)
+    cnt = np.where(over, 0, sm["s"]).astype(np.int64)
+    qlen = np.repeat((sm["qend"] - sm["qbeg"]).astype(np.int64), cnt)
+    rmate = np.repeat(np.asarray(mate)[sm["read"].astype(np.int64)], cnt)
+    keep = oracle.bs_keep(hits, qlen, rmate, len(ref))
+    return sm, over, hits, keep, oracle.bs_split(ref, seq, off, mate, sm, hits, keep, over=over)
+
+
+def test_bs_split_planted_mismatches():
+    """Section 2.8 split, hand-derived: read-1 C over reference T cuts a forward seed and a
+    reverse seed; read-2 G over reference A cuts a forward G-to-A seed; pieces under 19 go."""
+    ref = synth.reference(50_000, 77)
+    M = len(ref)
+    r1 = ref[100:160].copy()                       # read 1, forward strand
+    t_pos = [t for t in range(25, 40) if r1[t] == 3][0]
+    r1[t_pos] = 1                                  # C over reference T
+    rc = revcomp(ref[200:260]).copy()              # read 1, reverse strand
+    t_rc = [t for t in range(5, 15) if rc[t] == 3][0]
+    rc[t_rc] = 1
+    r2 = ref[300:360].copy()                       # read 2, forward strand (G->A copy)
+    a_pos = [t for t in range(30, 45) if r2[t] == 0][0]
+    r2[a_pos] = 2                                  # G over reference A
+    seq = np.concatenate([r1, rc, r2]).astype(np.uint8)
+    off = np.array([0, 60, 120, 180], np.uint64)
+    mate = np.array([1, 1, 2], np.uint8)
+    sm, over, hits, keep, pc = _bs_seed_and_split(ref, seq, off, mate)
+    got = sorted((int(p["read"]), int(p["qbeg"]), int(p["qend"]), int(p["pos"])) for p in pc)
+    want = [(0, 0, t_pos, 100), (0, t_pos + 1, 60, 100 + t_pos + 1)]
+    q_rc = M - 260                                 # offset in copy 2 = rc(GA(R)) = CT(rc(R))
+    if t_rc >= 19:
+        want.append((1, 0, t_rc, 2 * M + q_rc))
+    want.append((1, t_rc + 1, 60, 2 * M + q_rc + t_rc + 1))
+    want += [(2, 0, a_pos, M + 300), (2, a_pos + 1, 60, M + 300 + a_pos + 1)]
+    assert got == sorted(want)
+
+
+def test_bs_split_invariants():
+    """Pieces lie inside their seed, do not overlap, are at least 19 long, hold no cutting pair,
+    and are maximal: each end is a seed end or next to a cutting position."""
+    ref = synth.reference(40_000, 79)
+    rd = synth.reads(ref, 300, 80, mode=1, read_len=150, bisulfite=True, sub_lo=0.01, sub_hi=0.03)
+    sm, over, hits, keep, pc = _bs_seed_and_split(ref, rd.seq, rd.off, rd.mate)
+    assert len(pc) > 0
+    M = len(ref)
+    comp = np.array([3, 2, 1, 0, 4], np.uint8)
+    owner = np.repeat(np.arange(len(sm)), np.where(over, 0, sm["s"]).astype(np.int64))
+    ncut = 0
+    for p in pc:
+        m = owner[int(p["hit"])]
+        qb, qe = int(sm["qbeg"][m]), int(sm["qend"][m])
+        assert keep[int(p["hit"])] and qb <= p["qbeg"] < p["qend"] <= qe and p["qend"] - p["qbeg"] >= 19
+        hp = int(hits[int(p["hit"])])
+        assert int(p["pos"]) == hp + int(p["qbeg"]) - qb
+        rd_i, mt = int(p["read"]), int(rd.mate[int(p["read"])])
+
+        def cuts(t):   # is read position t (absolute in the read) a cutting position?
+            g, q = hp // M, hp - (hp // M) * M
+            u = q + t - qb
+            R = ref[u] if g < 2 else comp[ref[M - 1 - u]]
+            x = rd.seq[int(rd.off[rd_i]) + t]
+            return (mt == 1 and x == 1 and R == 3) or (mt == 2 and x == 2 and R == 0)
+        assert not any(cuts(t) for t in range(int(p["qbeg"]), int(p["qend"])))
+        assert p["qbeg"] == qb or cuts(int(p["qbeg"]) - 1)
+        assert p["qend"] == qe or cuts(int(p["qend"]))
+        ncut += int(p["qbeg"] != qb)
+    assert ncut > 0
+
+
+def test_qmer_prefilter_closed_forms():
+    """Section 2.6 prefilter: a read copied from the window has every q-mer on one diagonal
+    (max M_t = |P| - q + 1); each substitution at least q bases from the others and from the ends
+    removes exactly q of them; an N removes the q-mers that cover it; a periodic pair keeps the
+    full count on its best diagonal."""
+    q = 7
+    R = synth.reference(400, 91)
+    P = R[120:270].copy()
+    assert oracle.qmer_diag_max(P, R, q) == 150 - q + 1
+    P2 = P.copy()
+    for x in (20, 60, 100):
+        P2[x] = (P2[x] + 1) % 4
+    assert oracle.qmer_diag_max(P2, R, q) == 150 - q + 1 - 3 * q
+    P3 = P.copy()
+    P3[75] = 4
+    assert oracle.qmer_diag_max(P3, R, q) == 150 - q + 1 - q
+    per = np.tile(np.array([0, 1], np.uint8), 75)
+    assert oracle.qmer_diag_max(per, np.tile(np.array([0, 1], np.uint8), 150), q) == 150 - q + 1
+    assert oracle.qmer_diag_max(P[:q - 1], R, q) == 0
+
+
+def test_qmer_prefilter_batch_equals_pairwise_definition():
+    rng = np.random.default_rng(5)
+    reads, wins = [], []
+    for t in range(40):
+        R = rng.integers(0, 4, int(rng.integers(5, 500))).astype(np.uint8)
+        if t % 2 and len(R) > 200:
+            s = int(rng.integers(0, len(R) - 150))
+            P = R[s:s + 150].copy()
+        else:
+            P = rng.integers(0, 4, int(rng.integers(3, 160))).astype(np.uint8)
+        k = min(len(P), 4)
+        P[rng.integers(0, len(P), k)] = rng.integers(0, 5, k)
+        reads.append(P)
+        wins.append(R)
+    ro = np.concatenate([[0], np.cumsum([len(x) for x in reads])])
+    wo = np.concatenate([[0], np.cumsum([len(x) for x in wins])])
+    got = oracle.qmer_diag_max_batch(np.concatenate(reads), ro, np.concatenate(wins), wo)
+    want = [oracle.qmer_diag_max(P, R) for P, R in zip(reads, wins)]
+    assert got.tolist() == want
