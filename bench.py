@@ -508,9 +508,11 @@ def run_gpu(args):
         log(f"autotuned on {ns} reads: block {best.block_size}, work queue {bool(best.flags & mb.MB_BATCHED)}, "
             f"locate walks per lane {best.prefetch_depth}")
     else:
-        best = mb.Opts(block_size=args.block, prefetch_depth=args.locate_walks)
+        best = mb.Opts(block_size=args.block, prefetch_depth=args.locate_walks,
+                       flags=mb.MB_BATCHED if args.queue else 0)
     opts["block_size"] = best.block_size
     opts["prefetch_depth"] = best.prefetch_depth
+    opts["flags"] = best.flags
 
     for _ in range(args.warmup):
         step()
@@ -579,7 +581,8 @@ def run_gpu(args):
 
     # roofline of the dominant kernel: algorithmic bytes / its event-timed duration
     peak, peak_kind = measured_peaks()
-    smem_bytes = BLOCK_BYTES * wc["ext_blocks"] + 12 * wc["kmer_lookups"]
+    smem_bytes = (BLOCK_BYTES * (wc["ext_blocks"] + wc["u_walk_steps"]) + 12 * wc["kmer_lookups"] +
+                  4 * wc["u_samples"] + 8 * wc["u_text_loads"])
     loc_bytes = BLOCK_BYTES * wc["lf_steps"] + 4 * wc["sa_reads"]
     if loc_ms / max(loc_n, 1) >= smem_ms / max(smem_n, 1):
         kname, kbytes, kms = "locate", loc_bytes, loc_ms / max(loc_n, 1)
@@ -621,13 +624,14 @@ def run_gpu(args):
         out_h = torch.empty(m * 48, dtype=torch.uint8).pin_memory()
         hits_h = torch.empty(max(nh, 1), dtype=torch.int32).pin_memory()
         k2 = max(1, min(args.steps, 3))
-        mb.seed_locate(idx, seq_h, off_h, opts=opts, out=out_h, cap=m, hits=hits_h, hits_cap=nh)   # warm-up
+        eopts = dict(opts, flags=best.flags)   # the same launch shape as the graph form
+        mb.seed_locate(idx, seq_h, off_h, opts=eopts, out=out_h, cap=m, hits=hits_h, hits_cap=nh)   # warm-up
         torch.cuda.synchronize()
         if pg:
             pg.barrier()
         t0 = time.time()
         for _ in range(k2):
-            m2, nh2 = mb.seed_locate(idx, seq_h, off_h, opts=opts, out=out_h, cap=m, hits=hits_h, hits_cap=nh)
+            m2, nh2 = mb.seed_locate(idx, seq_h, off_h, opts=eopts, out=out_h, cap=m, hits=hits_h, hits_cap=nh)
         torch.cuda.synchronize()
         dt = max_over_ranks(time.time() - t0, pg)
         t0 = time.time()
@@ -639,7 +643,7 @@ def run_gpu(args):
         e2e = {"value": ws * k2 * n_reads / dt, "unit": "reads/s",
                "h2d_bytes_per_step": int(seq_h.numel() + off_h.numel() * 8),
                "d2h_bytes_per_step": int(m * 48 + nh * 4),
-               "call": "mb_seed_locate (pinned host buffers, 2M-read chunks on two streams)",
+               "call": "mb_seed_locate (pinned host buffers, 4M-read chunks on two streams)",
                "two_calls_reads_per_s": ws * k2 * n_reads / dt2,
                "note": "two_calls = mb_seed_batch + mb_locate on host buffers (the records are staged back in)"}
         log(f"e2e: {e2e}")
@@ -738,6 +742,8 @@ def main():
                     help="autotune the launch shape on 1M reads instead of --block / --locate-walks")
     ap.add_argument("--no-autotune", action="store_true", help="(default) fixed launch shape")
     ap.add_argument("--block", type=int, default=512, choices=[128, 256, 512])
+    ap.add_argument("--no-queue", dest="queue", action="store_false",
+                    help="SMEM kernel walks fixed read ranges per warp instead of a device work queue")
     ap.add_argument("--locate-walks", type=int, default=16, choices=[1, 2, 4, 8, 16])
     ap.add_argument("--reads", type=int, default=0,
                     help="seed only the first N reads of the batch (for ncu captures of the full index)")

@@ -48,10 +48,16 @@ enum {
 /* Flags of mb_opts.flags */
 #define MB_BS3      0x1u   /* index: bisulfite 3-base index over CT(R).GA(R) (Section 2.8);
                               seeding: convert read 1 C->T and read 2 G->A, keep hits by strand */
-#define MB_BATCHED  0x2u   /* seeding: one persistent launch over a device work queue */
+#define MB_BATCHED  0x2u   /* seeding: lanes take reads from a device work queue (a plan orders it
+                              by decreasing read length; mb_seed_batch keeps read order) */
 #define MB_CHECKED  0x4u   /* seeding: bounds-check every block / row index on the device */
 #define MB_NO_KMER  0x8u   /* seeding: do not use the k-mer ds-interval table */
 #define MB_COUNT    0x10u  /* seeding/locate: also count the work done (mb_work_counters) */
+#define MB_NO_AUX   0x20u  /* index: build without the packed text and the rate-8 SA / ISA samples
+                              (2.5 bytes per text position) that let seeding extend unique matches
+                              by comparing text */
+#define MB_STEP_ONLY 0x40u /* seeding: extend every match step by step (Algorithm 1), even where
+                              the auxiliary arrays allow comparing text */
 
 /* Flags of mb_smem.flags */
 #define MB_SMEM_OVER_MAX_OCC 0x1u   /* s > max_occ: reported, not located, no hits */
@@ -117,6 +123,12 @@ int mb_index_info(const mb_index *idx, uint64_t *n, uint64_t *primary, uint64_t 
  * #{B[i] < a} for a = $,A,C,G,T).  Any pointer may be NULL. */
 int mb_index_export(const mb_index *idx, uint32_t *sa, uint8_t *bwt, uint32_t *ssa,
                     void *occ_blocks, uint32_t *kmer, uint64_t *C);
+/* The auxiliary arrays of an index built without MB_NO_AUX (else MB_ERR_ARG when any pointer is
+ * given): text2 ((n - 1 + 15) / 16 + 2 u32: T[0, n-1) at 2 bits per base, base e of word w in
+ * bits 2e..2e+1, zero padding), sa_aux (ceil(n / 8) u32: S(8x)), isa_aux (ceil(n / 8) u32: the
+ * row of the suffix at text position 8p).  No counterpart in the paper: they let seeding extend
+ * a match that occurs once by comparing the read with the text (same SMEMs). */
+int mb_index_export_aux(const mb_index *idx, uint32_t *text2, uint32_t *sa_aux, uint32_t *isa_aux);
 /* Free the full suffix array kept after the build (it is only needed for mb_index_export). */
 int mb_index_drop_sa(mb_index *idx);
 
@@ -164,7 +176,7 @@ int mb_reseed(const mb_index *idx, const uint8_t *seq, const uint64_t *off, uint
  * inside the library (every GPU that loads the library holds it until the process exits).
  *   seq, off, mate (or NULL) and out must be DEVICE pointers; the other arguments, the results
  *   and the errors are those of mb_seed_batch (same records, same order).
- *   A batch whose scratch need exceeds 64 MiB (about 170,000 reads of 150 bases, less with many
+ *   A batch whose scratch need exceeds 64 MiB (about 145,000 reads of 150 bases, less with many
  *   SMEMs) is rejected with MB_ERR_ARG and a message naming the need; split the batch.
  *   The first call on a device looks up the array's device address (cudaGetSymbolAddress) for
  *   that device; make that first call before any stream capture.
@@ -366,6 +378,9 @@ const char *mb_last_error(void);
  * mb_work_counters: work done by calls made with MB_COUNT in opts, summed since the last
  * reset: extension steps of Algorithm 3, distinct occurrence blocks they read, k-mer table
  * lookups, LF steps of Algorithm 2 and sampled-SA reads.
+ * mb_work_counters_all: the same five followed by the work of extending unique matches by text
+ * comparison (LF steps of its walks, SA / ISA sample reads, text loads of 8 bytes), `count`
+ * values at most (8 exist).
  */
 void mb_profile_enable(int on);
 int mb_profile_get(const char *kernel, double *ms, uint64_t *launches);
@@ -373,6 +388,7 @@ void mb_profile_reset(void);
 uint64_t mb_launch_count(void);
 void mb_work_counters(uint64_t *ext_steps, uint64_t *ext_blocks, uint64_t *kmer_lookups,
                       uint64_t *lf_steps, uint64_t *sa_reads);
+void mb_work_counters_all(uint64_t *out, uint32_t count);
 
 #ifdef __cplusplus
 }

@@ -20,6 +20,7 @@ __all__ = ["SMEM_DTYPE", "Opts", "MbError", "lib", "build", "Index", "mb_index_b
            "mb_index_load", "mb_seed_batch", "mb_locate", "mb_bs_filter", "seed"]
 
 MB_BS3, MB_BATCHED, MB_CHECKED, MB_NO_KMER, MB_COUNT = 0x1, 0x2, 0x4, 0x8, 0x10
+MB_NO_AUX, MB_STEP_ONLY = 0x20, 0x40
 MB_SMEM_OVER_MAX_OCC, MB_SMEM_ROUND2 = 0x1, 0x2
 MB_ERR_CAPACITY = -3
 
@@ -68,6 +69,7 @@ def lib():
                 "mb_index_info": ([P, PU64, PU64, PU64], I),
                 "mb_index_export": ([P, P, P, P, P, P, P], I),
                 "mb_index_drop_sa": ([P], I),
+                "mb_index_export_aux": ([P, P, P, P], I),
                 "mb_seed_batch": ([P, P, P, U32, P, OP, P, P, U64, PU64, PU64], I),
                 "mb_locate": ([P, P, U64, OP, P, P, U64, PU64], I),
                 "mb_seed_locate": ([P, P, P, U32, P, OP, P, P, U64, P, U64, PU64, PU64], I),
@@ -100,6 +102,7 @@ def lib():
                 "mb_profile_reset": ([], None),
                 "mb_launch_count": ([], U64),
                 "mb_work_counters": ([PU64, PU64, PU64, PU64, PU64], None),
+                "mb_work_counters_all": ([P, U32], None),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -197,6 +200,15 @@ class Index:
                 out[k] = v
         out["C"] = C
         return out
+
+    def export_aux(self):
+        """(text2, sa_aux, isa_aux) as host arrays (see mb_index_export_aux)."""
+        n = self.n
+        t2 = np.empty((n - 1 + 15) // 16 + 2, np.uint32)
+        sx = np.empty((n + 7) // 8, np.uint32)
+        ix = np.empty((n + 7) // 8, np.uint32)
+        _check(lib().mb_index_export_aux(self._h, _ptr(t2), _ptr(sx), _ptr(ix)), "mb_index_export_aux")
+        return t2, sx, ix
 
     def hit_to_ref(self, pos: int, length: int):
         strand, rpos = ctypes.c_int(), ctypes.c_uint64()
@@ -387,10 +399,10 @@ def launch_count() -> int:
 
 
 def work_counters() -> dict:
-    v = [ctypes.c_uint64() for _ in range(5)]
-    lib().mb_work_counters(*[ctypes.byref(x) for x in v])
-    return dict(zip(("ext_steps", "ext_blocks", "kmer_lookups", "lf_steps", "sa_reads"),
-                    (x.value for x in v)))
+    v = np.zeros(8, dtype=np.uint64)
+    lib().mb_work_counters_all(_ptr(v), 8)
+    return dict(zip(("ext_steps", "ext_blocks", "kmer_lookups", "lf_steps", "sa_reads", "u_walk_steps",
+                     "u_samples", "u_text_loads"), (int(x) for x in v)))
 
 
 # ---------------------------------------------------------------------------- batched form

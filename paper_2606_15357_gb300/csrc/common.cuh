@@ -82,7 +82,10 @@ struct KTimer {
 };
 
 // device-side work counters (index into the array handed to kernels in counting mode)
-enum { WC_EXT_STEPS = 0, WC_EXT_BLOCKS = 1, WC_KMER = 2, WC_LF_STEPS = 3, WC_SA_READS = 4, WC_N = 5 };
+enum {
+    WC_EXT_STEPS = 0, WC_EXT_BLOCKS = 1, WC_KMER = 2, WC_LF_STEPS = 3, WC_SA_READS = 4,
+    WC_U_WALK = 5, WC_U_SAMPLE = 6, WC_U_TEXT = 7, WC_N = 8   // U_*: extension of unique matches by text
+};
 u64 *mb_work_counter_buf(cudaStream_t st);   // device array of WC_N u64 (zeroed on first use)
 
 // Stage a host-or-device input on the device: returns a device pointer (the input itself when
@@ -117,7 +120,12 @@ struct DevIndex {
     u64 nblocks;
     u32 r;              // SA sample rate
     u32 kmer_k;
+    const u32 *text2;   // T[0, n-1), 16 bases per word (null without the auxiliary arrays)
+    const u32 *sa_aux;  // S(x * AUX_RATE)
+    const u32 *isa_aux; // row of the suffix at text position p * AUX_RATE
 };
+// Sample rate of the auxiliary SA / ISA samples used to extend unique matches by comparison.
+constexpr u32 AUX_RATE = 8;
 
 struct mb_index_impl;
 

@@ -26,8 +26,15 @@ struct mb_index {
     u32 *ssa = nullptr;
     u32 *kmer = nullptr;
     u32 *sa = nullptr;            // full SA, kept until mb_index_drop_sa
+    // for extending unique matches by text comparison (absent with MB_NO_AUX)
+    u32 *text2 = nullptr;         // T[0, n-1) at 2 bits per base, 16 per word, first in the low bits
+    u32 *sa_aux = nullptr;        // S(x * AUX_RATE)
+    u32 *isa_aux = nullptr;       // row of the suffix at text position p * AUX_RATE
     int device = 0;
 };
+
+u64 text2_words(u64 n) { return (n - 1 + 15) / 16 + 2; }   // two words of padding for unaligned reads
+u64 aux_count(u64 n) { return (n + AUX_RATE - 1) / AUX_RATE; }
 
 DevIndex mb_dev_index(const mb_index *x) {
     DevIndex I;
@@ -40,6 +47,9 @@ DevIndex mb_dev_index(const mb_index *x) {
     I.nblocks = x->nblocks;
     I.r = x->sa_rate;
     I.kmer_k = x->kmer_k;
+    I.text2 = x->text2;
+    I.sa_aux = x->sa_aux;
+    I.isa_aux = x->isa_aux;
     return I;
 }
 int mb_index_device(const mb_index *x) { return x->device; }
@@ -195,6 +205,26 @@ __global__ void k_sample_sa(const u32 *__restrict__ SA, u64 n, u32 r, u32 *__res
         ssa[x] = SA[x * r];
 }
 
+// T[0, n-1) packed 16 bases per u32 word, base e of word w at bits 2e..2e+1; padding words zero.
+__global__ void k_text2(const u8 *__restrict__ T, u64 n, u32 *__restrict__ t2, u64 words) {
+    for (u64 w = blockIdx.x * (u64)blockDim.x + threadIdx.x; w < words; w += (u64)gridDim.x * blockDim.x) {
+        u32 v = 0;
+        for (u32 e = 0; e < 16; ++e) {
+            const u64 x = 16 * w + e;
+            if (x < n - 1) v |= (u32)(T[x] & 3u) << (2 * e);
+        }
+        t2[w] = v;
+    }
+}
+
+// isa[p / r] = the row of the suffix at text position p, for p a multiple of r
+__global__ void k_sample_isa(const u32 *__restrict__ SA, u64 n, u32 r, u32 *__restrict__ isa) {
+    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x) {
+        const u32 p = SA[i];
+        if (p % r == 0) isa[p / r] = (u32)i;
+    }
+}
+
 // ds-interval of every k-mer by k BackwardExt steps from the empty string (0, 0, n).  The
 // k-mer of entry w has its t-th base (t = 0 first) in bits 2t..2t+1 of w.
 __global__ void k_kmer_table(DevIndex I, u32 k, u32 *__restrict__ out) {
@@ -308,9 +338,18 @@ extern "C" void mb_profile_reset(void) {
     }
 }
 extern "C" uint64_t mb_launch_count(void) { return g_launches.load(); }
+extern "C" void mb_work_counters_all(uint64_t *out, uint32_t count) {
+    u64 v[WC_N] = {};
+    if (g_wc) {
+        cudaDeviceSynchronize();
+        cudaMemcpy(v, g_wc, sizeof v, cudaMemcpyDeviceToHost);
+    }
+    for (u32 i = 0; i < count; ++i) out[i] = i < (u32)WC_N ? v[i] : 0;
+}
+
 extern "C" void mb_work_counters(uint64_t *ext_steps, uint64_t *ext_blocks, uint64_t *kmer_lookups,
                                  uint64_t *lf_steps, uint64_t *sa_reads) {
-    u64 v[WC_N] = {0, 0, 0, 0, 0};
+    u64 v[WC_N] = {};
     if (g_wc) {
         cudaDeviceSynchronize();
         cudaMemcpy(v, g_wc, sizeof v, cudaMemcpyDeviceToHost);
@@ -362,6 +401,9 @@ static void free_index(mb_index *x) {
     if (x->ssa) cudaFree(x->ssa);
     if (x->kmer) cudaFree(x->kmer);
     if (x->sa) cudaFree(x->sa);
+    if (x->text2) cudaFree(x->text2);
+    if (x->sa_aux) cudaFree(x->sa_aux);
+    if (x->isa_aux) cudaFree(x->isa_aux);
     delete x;
 }
 
@@ -523,6 +565,16 @@ extern "C" int mb_index_build(const uint8_t *ref, uint64_t len, const mb_opts *o
         if (cudaMalloc(&X->kmer, nk * 12) != cudaSuccess) { rc = MB_ERR_NOMEM; break; }
         k_kmer_table<<<grid_for(nk, 256), 256, 0, st>>>(mb_dev_index(X), kk, X->kmer);
         if (cudaGetLastError() != cudaSuccess) { rc = MB_ERR_CUDA; break; }
+        if (!(flags & MB_NO_AUX)) {
+            // packed text and dense SA / ISA samples for extending unique matches by comparison
+            const u64 tw = text2_words(n), na = aux_count(n);
+            if (cudaMalloc(&X->text2, tw * 4) != cudaSuccess || cudaMalloc(&X->sa_aux, na * 4) != cudaSuccess ||
+                cudaMalloc(&X->isa_aux, na * 4) != cudaSuccess) { rc = MB_ERR_NOMEM; break; }
+            k_text2<<<grid_for(tw, 256), 256, 0, st>>>(bT.as<u8>(), n, X->text2, tw);
+            k_sample_sa<<<grid_for(na, 256), 256, 0, st>>>(X->sa, n, AUX_RATE, X->sa_aux);
+            k_sample_isa<<<grid_for(n, 256), 256, 0, st>>>(X->sa, n, AUX_RATE, X->isa_aux);
+            if (cudaGetLastError() != cudaSuccess) { rc = MB_ERR_CUDA; break; }
+        }
         if (cudaStreamSynchronize(st) != cudaSuccess) { rc = MB_ERR_CUDA; break; }
     } while (0);
     {
@@ -596,12 +648,25 @@ extern "C" int mb_index_export(const mb_index *idx, uint32_t *sa, uint8_t *bwt, 
     return MB_OK;
 }
 
+extern "C" int mb_index_export_aux(const mb_index *idx, uint32_t *text2, uint32_t *sa_aux, uint32_t *isa_aux) {
+    if (!idx) return MB_ERR_ARG;
+    if (!idx->text2 && (text2 || sa_aux || isa_aux)) {
+        mb_set_error("mb_index_export_aux: the index was built without the auxiliary arrays");
+        return MB_ERR_ARG;
+    }
+    if (!idx->text2) return MB_OK;
+    MB_TRY(copy_out(text2, idx->text2, text2_words(idx->n) * 4));
+    MB_TRY(copy_out(sa_aux, idx->sa_aux, aux_count(idx->n) * 4));
+    MB_TRY(copy_out(isa_aux, idx->isa_aux, aux_count(idx->n) * 4));
+    return MB_OK;
+}
+
 // ----------------------------------------------------------------------------- save / load
 namespace {
 constexpr u64 MAGIC = 0x3130585744424D4DULL;   // "MMBDWX01"
 struct FileHeader {
     u64 magic, version, n, rlen, primary, nblocks;
-    u32 sa_rate, kmer_k, flags, pad;
+    u32 sa_rate, kmer_k, flags, aux;   // aux: 1 when the packed text and SA / ISA samples follow
     u64 C[5];
     u64 checksum;
 };
@@ -622,14 +687,23 @@ u64 checksum_words(const void *p, size_t bytes, u64 h) {
 extern "C" int mb_index_save(const mb_index *idx, const char *path) {
     if (!idx || !path) return MB_ERR_ARG;
     u64 ns = (idx->n + idx->sa_rate - 1) / idx->sa_rate, nk = 1ULL << (2 * idx->kmer_k);
+    const bool aux = idx->text2 != nullptr;
     std::vector<u8> occ(idx->nblocks * sizeof(OccBlock)), ssa(ns * 4), km(nk * 12);
+    std::vector<u8> t2(aux ? text2_words(idx->n) * 4 : 0), sx(aux ? aux_count(idx->n) * 4 : 0), ix(sx.size());
     MB_CK(cudaMemcpy(occ.data(), idx->occ, occ.size(), cudaMemcpyDeviceToHost));
     MB_CK(cudaMemcpy(ssa.data(), idx->ssa, ssa.size(), cudaMemcpyDeviceToHost));
     MB_CK(cudaMemcpy(km.data(), idx->kmer, km.size(), cudaMemcpyDeviceToHost));
+    if (aux) {
+        MB_CK(cudaMemcpy(t2.data(), idx->text2, t2.size(), cudaMemcpyDeviceToHost));
+        MB_CK(cudaMemcpy(sx.data(), idx->sa_aux, sx.size(), cudaMemcpyDeviceToHost));
+        MB_CK(cudaMemcpy(ix.data(), idx->isa_aux, ix.size(), cudaMemcpyDeviceToHost));
+    }
+    std::vector<u8> *sec[] = {&occ, &ssa, &km, &t2, &sx, &ix};
     FileHeader h;
     memset(&h, 0, sizeof h);
     h.magic = MAGIC;
-    h.version = 3;
+    h.version = 4;
+    h.aux = aux ? 1u : 0u;
     h.n = idx->n;
     h.rlen = idx->rlen;
     h.primary = idx->primary;
@@ -639,17 +713,15 @@ extern "C" int mb_index_save(const mb_index *idx, const char *path) {
     h.flags = idx->flags;
     memcpy(h.C, idx->C, sizeof h.C);
     u64 cs = checksum_words(&h, offsetof(FileHeader, checksum), 0xCBF29CE484222325ULL);
-    cs = checksum_words(occ.data(), occ.size(), cs);
-    cs = checksum_words(ssa.data(), ssa.size(), cs);
-    cs = checksum_words(km.data(), km.size(), cs);
+    for (auto *v : sec) cs = checksum_words(v->data(), v->size(), cs);
     h.checksum = cs;
     FILE *f = fopen(path, "wb");
     if (!f) {
         mb_set_error("mb_index_save: cannot open %s", path);
         return MB_ERR_IO;
     }
-    bool ok = fwrite(&h, sizeof h, 1, f) == 1 && fwrite(occ.data(), 1, occ.size(), f) == occ.size() &&
-              fwrite(ssa.data(), 1, ssa.size(), f) == ssa.size() && fwrite(km.data(), 1, km.size(), f) == km.size();
+    bool ok = fwrite(&h, sizeof h, 1, f) == 1;
+    for (auto *v : sec) ok = ok && fwrite(v->data(), 1, v->size(), f) == v->size();
     ok = (fclose(f) == 0) && ok;
     if (!ok) {
         mb_set_error("mb_index_save: write to %s failed", path);
@@ -672,25 +744,25 @@ extern "C" int mb_index_load(const char *path, void *stream, mb_index **out) {
         mb_set_error("mb_index_load: short header");
         return MB_ERR_CORRUPT;
     }
-    if (h.magic != MAGIC || h.version != 3 || h.sa_rate == 0 || h.kmer_k > 14 || h.n >= (1ULL << 32) ||
-        h.nblocks != h.n / BLK_ROWS + 1) {
+    if (h.magic != MAGIC || h.version != 4 || h.sa_rate == 0 || h.kmer_k > 14 || h.n >= (1ULL << 32) ||
+        h.n < 2 || h.aux > 1 || h.nblocks != h.n / BLK_ROWS + 1) {
         fclose(f);
         mb_set_error("mb_index_load: bad header");
         return MB_ERR_CORRUPT;
     }
     u64 ns = (h.n + h.sa_rate - 1) / h.sa_rate, nk = 1ULL << (2 * h.kmer_k);
     std::vector<u8> occ(h.nblocks * sizeof(OccBlock)), ssa(ns * 4), km(nk * 12);
-    bool ok = fread(occ.data(), 1, occ.size(), f) == occ.size() && fread(ssa.data(), 1, ssa.size(), f) == ssa.size() &&
-              fread(km.data(), 1, km.size(), f) == km.size();
+    std::vector<u8> t2(h.aux ? text2_words(h.n) * 4 : 0), sx(h.aux ? aux_count(h.n) * 4 : 0), ix(sx.size());
+    std::vector<u8> *sec[] = {&occ, &ssa, &km, &t2, &sx, &ix};
+    bool ok = true;
+    for (auto *v : sec) ok = ok && fread(v->data(), 1, v->size(), f) == v->size();
     fclose(f);
     if (!ok) {
         mb_set_error("mb_index_load: truncated file");
         return MB_ERR_CORRUPT;
     }
     u64 cs = checksum_words(&h, offsetof(FileHeader, checksum), 0xCBF29CE484222325ULL);
-    cs = checksum_words(occ.data(), occ.size(), cs);
-    cs = checksum_words(ssa.data(), ssa.size(), cs);
-    cs = checksum_words(km.data(), km.size(), cs);
+    for (auto *v : sec) cs = checksum_words(v->data(), v->size(), cs);
     if (cs != h.checksum) {
         mb_set_error("mb_index_load: checksum mismatch");
         return MB_ERR_CORRUPT;
@@ -707,7 +779,9 @@ extern "C" int mb_index_load(const char *path, void *stream, mb_index **out) {
     cudaGetDevice(&X->device);
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMalloc(&X->occ, occ.size()) != cudaSuccess || cudaMalloc(&X->ssa, ssa.size()) != cudaSuccess ||
-        cudaMalloc(&X->kmer, km.size()) != cudaSuccess) {
+        cudaMalloc(&X->kmer, km.size()) != cudaSuccess ||
+        (h.aux && (cudaMalloc(&X->text2, t2.size()) != cudaSuccess || cudaMalloc(&X->sa_aux, sx.size()) != cudaSuccess ||
+                   cudaMalloc(&X->isa_aux, ix.size()) != cudaSuccess))) {
         free_index(X);
         mb_set_error("mb_index_load: device allocation failed");
         return MB_ERR_NOMEM;
@@ -715,6 +789,9 @@ extern "C" int mb_index_load(const char *path, void *stream, mb_index **out) {
     if (cudaMemcpyAsync(X->occ, occ.data(), occ.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(X->ssa, ssa.data(), ssa.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(X->kmer, km.data(), km.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        (h.aux && (cudaMemcpyAsync(X->text2, t2.data(), t2.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+                   cudaMemcpyAsync(X->sa_aux, sx.data(), sx.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+                   cudaMemcpyAsync(X->isa_aux, ix.data(), ix.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)) ||
         cudaStreamSynchronize(st) != cudaSuccess) {
         free_index(X);
         mb_set_error("mb_index_load: copy to device failed");

@@ -27,7 +27,9 @@ constexpr u32 RESEED_MAX_OCC = 10;
 
 struct SlotRec {
     u32 qbeg, qend, k, kr, s;
+    u32 pos;   // the text position of the one occurrence when the kernel found it, else NOPOS
 };
+constexpr u32 NOPOS = 0xFFFFFFFFu;   // no known position (and, in a row list, a row not to walk)
 
 // Scratch slots: a read of len bases owns len/16 + 8 slots (about 17 for 150 bases).
 constexpr u64 SLOT_DIV = 16, SLOT_EXTRA = 8;
@@ -42,7 +44,7 @@ __device__ __forceinline__ u64 slot_base(const u64 *off, u64 r) { return slots_b
 // Work counters of the measurement mode (MB_COUNT); compiled out otherwise.
 template <bool ON>
 struct Work {
-    u64 steps = 0, blocks = 0, kmer = 0, lf = 0, sa = 0;
+    u64 steps = 0, blocks = 0, kmer = 0, lf = 0, sa = 0, uwalk = 0, usample = 0, utext = 0;
     __device__ __forceinline__ void ext(u64 p, u64 s) {
         if (ON) {
             ++steps;
@@ -56,6 +58,9 @@ struct Work {
             if (kmer) atomicAdd((unsigned long long *)&wc[WC_KMER], (unsigned long long)kmer);
             if (lf) atomicAdd((unsigned long long *)&wc[WC_LF_STEPS], (unsigned long long)lf);
             if (sa) atomicAdd((unsigned long long *)&wc[WC_SA_READS], (unsigned long long)sa);
+            if (uwalk) atomicAdd((unsigned long long *)&wc[WC_U_WALK], (unsigned long long)uwalk);
+            if (usample) atomicAdd((unsigned long long *)&wc[WC_U_SAMPLE], (unsigned long long)usample);
+            if (utext) atomicAdd((unsigned long long *)&wc[WC_U_TEXT], (unsigned long long)utext);
         }
     }
 };
@@ -73,6 +78,7 @@ struct SmemState {
     int i, j;
     u32 k, kr, s;
     bool tried;  // stage 3: the k-mer table was already consulted for this entry
+    u32 pos;     // stages 5-6: text position of the one occurrence of P[i, j)
 };
 
 __device__ __forceinline__ void smem_begin(SmemState &S, const u8 *P, int L, u32 conv, u32 l, u32 n,
@@ -159,8 +165,57 @@ __device__ __forceinline__ bool kmer_code(SmemState &S, int j, u32 K, u32 &code)
     return true;
 }
 
+// Up to 16 read bases from P[j] on as 2-bit codes (first in the low bits, bisulfite conversion
+// applied) with a mask of the N among them (bit 2t for base j + t); returns how many (at least 1).
+// The 16-byte chunk holding j is loaded if it is not the cached one; next to the end of the batch
+// it takes one base by a byte load.
+__device__ __forceinline__ u64 byte_flags(u64 x) {   // bit 0 of each byte: the byte is above 3
+    u64 t = x & 0xFCFCFCFCFCFCFCFCULL;
+    t |= t >> 4;
+    t |= t >> 2;
+    t |= t >> 1;
+    return t & 0x0101010101010101ULL;
+}
+__device__ __forceinline__ u32 read_codes16(SmemState &S, int j, u32 &codes, u32 &nmask) {
+    const int mis = (int)((uintptr_t)S.P & 15);
+    const int cj = ((j + mis) & ~15) - mis;
+    if (cj != S.cj && cj + 16 <= S.lim) {
+        S.chunk = __ldg(reinterpret_cast<const uint4 *>(S.P + cj));
+        S.cj = cj;
+    }
+    if (cj == S.cj) {
+        const u32 o = (u32)(j - cj);
+        const u64 lo = ((u64)S.chunk.y << 32) | S.chunk.x, hi = ((u64)S.chunk.w << 32) | S.chunk.z;
+        const u64 M3 = 0x0303030303030303ULL;
+        const u32 nm = pack8(byte_flags(lo)) | (pack8(byte_flags(hi)) << 16);
+        const u32 cd = pack8(convert8(lo & M3, S.conv)) | (pack8(convert8(hi & M3, S.conv)) << 16);
+        codes = cd >> (2 * o);
+        nmask = nm >> (2 * o);
+        return 16 - o;
+    }
+    const u32 b = cached_base(S, j);
+    codes = b & 3u;
+    nmask = b > 3 ? 1u : 0u;
+    return 1;
+}
+
 // What a lane does with memory in one step of Algorithm 3.
-enum { ACT_NONE = 0, ACT_EXT = 1, ACT_KMER = 2 };
+enum { ACT_NONE = 0, ACT_EXT = 1, ACT_KMER = 2, ACT_WALK = 3, ACT_SAMPLE = 4, ACT_TEXT = 5 };
+
+// A match that occurs once (s = 1) in stage 2 can be extended forwards by comparing the read with
+// the text after its one occurrence instead of one ForwardExt per base: P[i, j+1) occurs iff
+// T[pos + j - i] = P[j], where pos is the occurrence of P[i, j), and while s = 1 the row k of
+// P[i, j) stays the row of the suffix at pos.  Stages 4-7 do that, with the same result as
+// Algorithm 3's steps (and the same transitions: emit, then stage 3 or the end of the read):
+//   4  walk from row k to a row that is a multiple of AUX_RATE (or the $ row): pos = S(row) + steps
+//      (kr holds the walking row, s the steps)
+//   5  compare up to 16 bases of the read and the text per memory action
+//   6  kr of the final match = the row of the suffix at y = n - 1 - pos - (j - i) (its reverse
+//      complement's one occurrence): start from the ISA sample at the next multiple of AUX_RATE
+//   7  walk back from there to y (s counts down), then emit (i, j, k, kr, 1)
+// It is used when at least U_MIN bases of the read remain, where the walks cost less than the
+// steps they replace.
+constexpr int U_MIN = 16;
 
 // Moves through the steps of Algorithm 3 that need no memory and picks the next memory action:
 // ACT_EXT, an extension of P[j] (backward in stages 1 and 3, forward in stage 2); ACT_KMER, a
@@ -173,7 +228,8 @@ enum { ACT_NONE = 0, ACT_EXT = 1, ACT_KMER = 2 };
 // (every window starting at or before x contains that k-mer, so none is a match); in stage 3 the
 // restart point must be exact, so a failing k-mer falls back to single steps.
 template <class Emit>
-__device__ __forceinline__ int smem_next(SmemState &S, const DevIndex &I, u32 l, bool kmer, Emit &emit, u32 &code) {
+__device__ __forceinline__ int smem_next(SmemState &S, const DevIndex &I, u32 l, bool kmer, Emit &emit, u32 &code,
+                                         bool uext = false) {
     const u32 n = (u32)I.n, K = I.kmer_k;
     for (;;) {
         if (S.u == 2) {
@@ -182,7 +238,66 @@ __device__ __forceinline__ int smem_next(SmemState &S, const DevIndex &I, u32 l,
                 S.u = 0;
                 return ACT_NONE;
             }
+            if (uext && S.s == 1 && S.L - S.j >= U_MIN) {   // one occurrence: compare text
+                S.u = 4;
+                S.kr = S.k;
+                S.s = 0;
+                continue;
+            }
             return ACT_EXT;
+        }
+        if (S.u == 4) {
+            if (S.kr == (u32)I.primary) {           // the $ row: S = 0
+                S.pos = S.s;
+                S.u = 5;
+                continue;
+            }
+            if ((S.kr & (AUX_RATE - 1)) == 0) {
+                code = S.kr / AUX_RATE;
+                return ACT_SAMPLE;
+            }
+            if (S.s > n) {                          // only on a corrupted index: compare nothing
+                S.pos = n;
+                S.u = 5;
+                continue;
+            }
+            return ACT_WALK;
+        }
+        if (S.u == 5) {
+            if (S.j >= S.L || (u64)S.pos + (u32)(S.j - S.i) >= (u64)n - 1) {
+                S.u = 6;
+                continue;
+            }
+            return ACT_TEXT;
+        }
+        if (S.u == 6) {
+            const u64 end = (u64)S.pos + (u32)(S.j - S.i);
+            const u64 y = end < (u64)n - 1 ? (u64)n - 1 - end : 0;
+            u64 q = (y + AUX_RATE - 1) / AUX_RATE * AUX_RATE;
+            if (q >= (u64)n - 1) {                  // the $ suffix, row 0
+                q = (u64)n - 1;
+                S.kr = 0;
+                S.s = (u32)(q - y);
+                S.u = 7;
+                continue;
+            }
+            S.s = (u32)(q - y);
+            code = (u32)(q / AUX_RATE);
+            return ACT_SAMPLE;
+        }
+        if (S.u == 7) {
+            if (S.s == 0) {
+                emit(S.i, S.j, S.k, S.kr, 1u, S.pos);
+                if (S.j == S.L) {
+                    S.u = 0;
+                    return ACT_NONE;
+                }
+                S.u = 3;                            // as after a failed ForwardExt
+                S.k = 0; S.kr = 0; S.s = n;
+                S.tried = false;
+                continue;
+            }
+            return ACT_WALK;
         }
         if (S.u == 1) {
             if (S.j < S.i) {                        // P[i, i+l) is a match: stage 2
@@ -312,8 +427,8 @@ struct SlotEmit {
     SlotRec *slots;
     u64 base;
     u32 cap, cnt;
-    __device__ __forceinline__ void operator()(int i, int j, u32 k, u32 kr, u32 s) {
-        if (cnt < cap) slots[base + cnt] = SlotRec{(u32)i, (u32)j, k, kr, s};
+    __device__ __forceinline__ void operator()(int i, int j, u32 k, u32 kr, u32 s, u32 pos = NOPOS) {
+        if (cnt < cap) slots[base + cnt] = SlotRec{(u32)i, (u32)j, k, kr, s, pos};
         ++cnt;
     }
 };
@@ -360,6 +475,7 @@ struct SmemArgs {
     u32 *qhead;
     u64 *wc;
     const u32 *lc;   // per-read (l | c << 16), or null for the kernel-wide l and c
+    bool uext;       // extend matches that occur once by comparing text (stages 4-7)
 };
 
 // Launch bounds per shape: 128 threads allow 85 registers (6 blocks, 24 warps per SM); 256 and
@@ -372,7 +488,8 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 128 ? 6 : 1024 / BLOCK) k_smem
                                                                SlotRec *__restrict__ slots, u64 slot_total,
                                                                u64 *__restrict__ counts, u32 *__restrict__ ovf_list,
                                                                u32 *__restrict__ ovf_n, const u32 *__restrict__ perm,
-                                                               u32 *qhead, u64 *wc, const u32 *__restrict__ lc) {
+                                                               u32 *qhead, u64 *wc, const u32 *__restrict__ lc,
+                                                               bool uext) {
     const u32 lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
     const u32 n = (u32)I.n;
     const u64 o0 = off[0];
@@ -415,7 +532,7 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 128 ? 6 : 1024 / BLOCK) k_smem
     bool live;
     take(32, lane, item, live);
     if (live) {
-        r = QUEUE ? perm[item] : item;
+        r = QUEUE && perm ? perm[item] : item;
         start(r);
     }
     for (;;) {
@@ -423,7 +540,7 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 128 ? 6 : 1024 / BLOCK) k_smem
         // phase 1 (divergent, no memory): stage changes, then this lane's one memory action
         int act = ACT_NONE;
         u32 code = 0;
-        if (live) act = smem_next(S, I, lr, kmer && lr >= I.kmer_k, em, code);
+        if (live) act = smem_next(S, I, lr, kmer && lr >= I.kmer_k, em, code, uext);
         __syncwarp();
         // phase 2 (converged): every lane's loads are issued before any is used, so the table
         // lookups, the block reads and the read-chunk reloads of one iteration overlap
@@ -434,13 +551,23 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 128 ? 6 : 1024 / BLOCK) k_smem
             tkr = __ldg(t + 1);
             ts = __ldg(t + 2);
         }
-        const bool fwd = S.u == 2;
-        const u32 p = fwd ? S.kr : S.k, q = fwd ? S.k : S.kr, e = p + S.s;
+        // an LF step of a walk (stages 4 and 7) is Algorithm 1's p' = C[a] + #a in B[0, p) with a = B[p]
+        // and s = 0, so it shares the extension's loads and arithmetic
+        const bool walk = act == ACT_WALK, fwd = S.u == 2;
+        const u32 p = (fwd || walk) ? S.kr : S.k, q = fwd ? S.k : S.kr, sz = walk ? 0u : S.s, e = p + sz;
         Blk b0, b1;
-        if (act == ACT_EXT) {
+        u32 smp = 0, t0 = 0, t1 = 0, rc = 0, rn = 0, rcnt = 0;
+        if (act == ACT_EXT || walk) {
             b0 = load_blk(I.occ + (p >> BLK_SHIFT));
             b1 = b0;
             if ((e >> BLK_SHIFT) != (p >> BLK_SHIFT)) b1 = load_blk(I.occ + (e >> BLK_SHIFT));
+        } else if (act == ACT_SAMPLE) {
+            smp = __ldg((S.u == 4 ? I.sa_aux : I.isa_aux) + code);
+        } else if (act == ACT_TEXT) {
+            const u32 x = S.pos + (u32)(S.j - S.i);
+            t0 = __ldg(I.text2 + (x >> 4));
+            t1 = __ldg(I.text2 + (x >> 4) + 1);
+            rcnt = read_codes16(S, S.j, rc, rn);
         }
         const u32 a = act == ACT_EXT ? cached_base(S, S.j) : 0u;
         // phase 3: apply the results
@@ -448,16 +575,36 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 128 ? 6 : 1024 / BLOCK) k_smem
         if (act == ACT_KMER) {
             work.kmer += 1;
             fin = !smem_apply_kmer(S, tk, tkr, ts, lr, cr, I.kmer_k);
-        } else if (act == ACT_EXT) {
-            u32 nk = 0, nkr = 0, ns = 0;
-            if (a < 4) {   // an N gives the empty interval
-                work.ext(p, S.s);
-                const Ext x = extend_blocks(I, b0, b1, p, q, S.s, fwd ? 3u - a : a);
-                nk = fwd ? x.q : x.p;
-                nkr = fwd ? x.p : x.q;
-                ns = x.s;
+        } else if (act == ACT_EXT || walk) {
+            const u32 sym = walk ? sym_at(b0, p & BLK_MASK) : (fwd ? 3u - a : a);
+            Ext x{0, 0, 0};
+            if (walk || a < 4) x = extend_blocks(I, b0, b1, p, q, sz, sym);   // an N: the empty interval
+            if (walk) {                       // stage 4 counts steps up, stage 7 down
+                work.uwalk += 1;
+                S.kr = x.p;
+                S.s = S.u == 4 ? S.s + 1 : S.s - 1;
+            } else {
+                if (a < 4) work.ext(p, S.s);
+                fin = !smem_apply(S, fwd ? x.q : x.p, fwd ? x.p : x.q, x.s, lr, cr, n, em);
             }
-            fin = !smem_apply(S, nk, nkr, ns, lr, cr, n, em);
+        } else if (act == ACT_SAMPLE) {
+            work.usample += 1;
+            if (S.u == 4) {
+                S.pos = smp + S.s;
+                S.u = 5;
+            } else {
+                S.kr = smp;
+                S.u = 7;
+            }
+        } else if (act == ACT_TEXT) {         // the matching prefix of read and text
+            work.utext += 1;
+            const u32 x = S.pos + (u32)(S.j - S.i);
+            const u32 tc = (u32)((((u64)t1 << 32) | t0) >> (2 * (x & 15)));
+            const u32 lim = min(min(rcnt, (u32)(S.L - S.j)), n - 1 - x);
+            const u32 d = rc ^ tc, m2 = ((d | (d >> 1)) & 0x55555555u) | rn;
+            const u32 first = m2 ? (u32)(__ffs(m2) - 1) >> 1 : 16u;
+            S.j += (int)min(first, lim);
+            if (first < lim) S.u = 6;         // mismatch or N: the match ends here
         } else if (live) {
             fin = true;
         }
@@ -473,7 +620,7 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 128 ? 6 : 1024 / BLOCK) k_smem
             if (fin) {
                 live = ok2;
                 if (live) {
-                    r = QUEUE ? perm[it2] : it2;
+                    r = QUEUE && perm ? perm[it2] : it2;
                     start(r);
                 }
             }
@@ -502,7 +649,8 @@ __device__ __forceinline__ void write_rec(mb_smem *out, u64 *hitc, u64 m, u32 r,
 // whose slots lie past slot_total) are skipped here and recomputed by k_smem_overflow.
 __global__ void k_gather(const u64 *__restrict__ off, u32 nr, const SlotRec *__restrict__ slots, u64 slot_total,
                          const u64 *__restrict__ counts, const u64 *__restrict__ soff, u32 max_occ,
-                         mb_smem *__restrict__ out, u64 *__restrict__ hitc, u64 out_cap) {
+                         mb_smem *__restrict__ out, u64 *__restrict__ hitc, u64 out_cap,
+                         u32 *__restrict__ known = nullptr) {
     u64 r = blockIdx.x * (u64)blockDim.x + threadIdx.x;
     if (r >= nr) return;
     const u64 sb = slot_base(off, r), se = slot_base(off, r + 1), cnt = counts[r];
@@ -511,6 +659,7 @@ __global__ void k_gather(const u64 *__restrict__ off, u32 nr, const SlotRec *__r
     for (u64 t = 0; t < cnt; ++t) {
         SlotRec x = slots[sb + t];
         write_rec(out, hitc, o + t, (u32)r, x.qbeg, x.qend, x.k, x.kr, x.s, max_occ, out_cap);
+        if (known && o + t < out_cap) known[o + t] = x.pos;
     }
 }
 
@@ -519,7 +668,9 @@ struct FinalEmit {
     u64 *hitc;
     u64 o, cap;
     u32 r, max_occ;
-    __device__ __forceinline__ void operator()(int i, int j, u32 k, u32 kr, u32 s) {
+    u32 *known;
+    __device__ __forceinline__ void operator()(int i, int j, u32 k, u32 kr, u32 s, u32 = NOPOS) {
+        if (known && o < cap) known[o] = NOPOS;   // the overflow pass steps; no position is known
         write_rec(out, hitc, o++, r, (u32)i, (u32)j, k, kr, s, max_occ, cap);
     }
 };
@@ -529,11 +680,11 @@ __global__ void k_smem_overflow(DevIndex I, const u8 *__restrict__ seq, const u6
                                 const u32 *__restrict__ ovf_list,
                                 const u32 *__restrict__ ovf_n, const u64 *__restrict__ soff, u32 max_occ,
                                 mb_smem *__restrict__ out, u64 *__restrict__ hitc, u64 cap,
-                                const u32 *__restrict__ lc) {
+                                const u32 *__restrict__ lc, u32 *__restrict__ known = nullptr) {
     u32 n = *ovf_n;
     for (u32 q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
         u32 r = ovf_list[q];
-        FinalEmit em{out, hitc, soff[r], cap, r, max_occ};
+        FinalEmit em{out, hitc, soff[r], cap, r, max_occ, known};
         Work<false> work;
         const u32 lr = lc ? (lc[r] & 0xFFFFu) : l, cr = lc ? (lc[r] >> 16) : c;
         smem_read(I, seq + off[r], (int)(off[r + 1] - off[r]), lr, cr, conv_of(mate, r, bs), kmer && lr >= I.kmer_k,
@@ -568,8 +719,11 @@ __device__ __forceinline__ u64 hits_of(const mb_smem *__restrict__ sm, u64 m) {
 
 // rows[hit_off + t] = k + t for the hits of every record without MB_SMEM_OVER_MAX_OCC: one warp
 // per 32 records, writing each record's rows with the whole warp.
+// With `known` (a position per record, NOPOS when not found while seeding), the hit of a record
+// whose position is known is written to hits here and its row is marked NOPOS (locate skips it).
 __global__ void k_expand_rows(const mb_smem *__restrict__ sm, u64 nsm, const u64 *__restrict__ nsm_dev,
-                              u32 *__restrict__ rows, u64 rows_cap) {
+                              u32 *__restrict__ rows, u64 rows_cap, const u32 *__restrict__ known = nullptr,
+                              u32 *__restrict__ hits = nullptr) {
     const u32 lane = threadIdx.x & 31;
     if (nsm_dev && *nsm_dev < nsm) nsm = *nsm_dev;
     const u64 nw = ((u64)gridDim.x * blockDim.x) >> 5;
@@ -581,11 +735,18 @@ __global__ void k_expand_rows(const mb_smem *__restrict__ sm, u64 nsm, const u64
             ho = __ldg(&sm[m].hit_off);
             cnt = hits_of(sm, m);
             k = (u32)__ldg(&sm[m].k);
+            if (known && cnt == 1 && ho < rows_cap) {
+                const u32 pos = known[m];
+                if (pos != NOPOS) {
+                    hits[ho] = pos;
+                    k = NOPOS;
+                }
+            }
         }
         for (int q = 0; q < 32; ++q) {
             const u64 hq = __shfl_sync(0xffffffffu, ho, q), cq = __shfl_sync(0xffffffffu, cnt, q);
             const u32 kq = __shfl_sync(0xffffffffu, k, q);
-            for (u64 t = lane; t < cq && hq + t < rows_cap; t += 32) rows[hq + t] = kq + (u32)t;
+            for (u64 t = lane; t < cq && hq + t < rows_cap; t += 32) rows[hq + t] = kq == NOPOS ? NOPOS : kq + (u32)t;
         }
     }
 }
@@ -633,17 +794,19 @@ __global__ void __launch_bounds__(256, D == 8 ? 2 : 1) k_locate(DevIndex I, cons
     for (;;) {
         if (__all_sync(0xffffffffu, live == 0)) break;
         if (next + 128 + lane < wlen) asm volatile("prefetch.global.L1 [%0];" ::"l"(wrows + next + 128 + lane));
-        u32 stop = 0, smp = 0;
+        u32 stop = 0, smp = 0, skp = 0;
         u32 sv[D];
         Blk b[D];
 #pragma unroll
         for (int d = 0; d < D; ++d) {
             const bool on = (live >> d) & 1u;
-            const bool sampled = POW2 ? (row[d] & rmask) == 0 : row[d] % r == 0;
-            const bool st = on && (sampled || row[d] == prim || steps[d] > n);
+            const bool skip = row[d] == NOPOS;   // a hit already written (position known)
+            const bool sampled = !skip && (POW2 ? (row[d] & rmask) == 0 : row[d] % r == 0);
+            const bool st = on && (skip || sampled || row[d] == prim || steps[d] > n);
             sv[d] = 0;
             if (st) {
                 stop |= 1u << d;
+                if (skip) skp |= 1u << d;
                 if (sampled) {
                     smp |= 1u << d;
                     sv[d] = __ldg(&I.ssa[POW2 ? (row[d] >> rshift) : row[d] / r]);
@@ -665,7 +828,8 @@ __global__ void __launch_bounds__(256, D == 8 ? 2 : 1) k_locate(DevIndex I, cons
 #pragma unroll
         for (int d = 0; d < D; ++d) {
             if ((stop >> d) & 1u) {
-                whits[h[d]] = steps[d] > n ? 0xFFFFFFFFu : (((smp >> d) & 1u) ? sv[d] + steps[d] : steps[d]);
+                if (!((skp >> d) & 1u))
+                    whits[h[d]] = steps[d] > n ? 0xFFFFFFFFu : (((smp >> d) & 1u) ? sv[d] + steps[d] : steps[d]);
                 work.lf += steps[d];
                 work.sa += (smp >> d) & 1u;
                 h[d] = give;
@@ -724,7 +888,7 @@ int launch_smem_t(const SmemArgs &a, cudaStream_t st) {
     const unsigned g = resident_grid((const void *)k_smem<COUNT, QUEUE, BLOCK>, BLOCK, a.nr);
     k_smem<COUNT, QUEUE, BLOCK><<<g, BLOCK, 0, st>>>(a.I, a.seq, a.off, a.nr, a.mate, a.bs, a.l, a.c, a.kmer, a.slots,
                                                      a.slot_total, a.counts, a.ovf_list, a.ovf_n, a.perm, a.qhead,
-                                                     a.wc, a.lc);
+                                                     a.wc, a.lc, a.uext);
     MB_KCHECK();
     return MB_OK;
 }
@@ -792,7 +956,7 @@ static int seed_device(const mb_index *idx, const u8 *dseq, const u64 *doff, u32
     MB_TRY(bovf.alloc((size_t)n_reads * 4, st));
     MB_TRY(bmisc.alloc(64, st));
     u64 *dtotal = bmisc.as<u64>(), *dhtotal = bmisc.as<u64>() + 1;
-    u32 *dovf_n = (u32 *)(bmisc.as<u64>() + 2);
+    u32 *dovf_n = (u32 *)(bmisc.as<u64>() + 2), *dqhead = (u32 *)(bmisc.as<u64>() + 3);
     MB_CK(cudaMemsetAsync(bmisc.p, 0, 64, st));
 
     const DevIndex I = mb_dev_index(idx);
@@ -802,12 +966,15 @@ static int seed_device(const mb_index *idx, const u8 *dseq, const u64 *doff, u32
     const bool kmer = !(flags & MB_NO_KMER) && l >= mb_dev_index(idx).kmer_k;
     {
         const bool count = (flags & MB_COUNT) != 0;
+        // with MB_BATCHED the reads are taken from a work queue in read order (no sort here)
+        const bool queue = !count && (flags & MB_BATCHED);
         SmemArgs sa{I, (const u8 *)dseq, (const u64 *)doff, n_reads, (const u8 *)dmate, bs, l, c, kmer,
-                    bslots.as<SlotRec>(), nslots, bcounts.as<u64>(), bovf.as<u32>(), dovf_n, nullptr, nullptr,
-                    count ? mb_work_counter_buf(st) : nullptr, dlc};
+                    bslots.as<SlotRec>(), nslots, bcounts.as<u64>(), bovf.as<u32>(), dovf_n, nullptr,
+                    queue ? dqhead : nullptr, count ? mb_work_counter_buf(st) : nullptr, dlc,
+                    I.text2 && !(flags & MB_STEP_ONLY)};
         const int blk = opts && (opts->block_size == 128 || opts->block_size == 512) ? (int)opts->block_size : 256;
         kt.start();
-        MB_TRY(launch_smem(sa, count, false, blk, st));
+        MB_TRY(launch_smem(sa, count, queue, blk, st));
         kt.stop();
     }
     MB_TRY(btmp.alloc(scan_tmp_bytes(n_reads), st));
@@ -1068,7 +1235,7 @@ extern "C" int mb_seed_batch_noalloc(const mb_index *idx, const uint8_t *seq, co
     const bool kmer = !(flags & MB_NO_KMER) && l >= I.kmer_k;
     {
         SmemArgs sa{I, seq, off, n_reads, mate, bs, l, c, kmer, slots, nslots, counts, ovf, dovf_n, nullptr, nullptr,
-                    nullptr};
+                    nullptr, nullptr, I.text2 && !(flags & MB_STEP_ONLY)};
         MB_TRY(launch_smem(sa, false, false, 256, st));
     }
     MB_TRY(scan_exclusive_u64(counts, soff, nr, dtotal, S + o_tmp, st));
@@ -1128,6 +1295,7 @@ struct mb_plan {
     SlotRec *slots = nullptr;
     u64 *counts = nullptr, *soff = nullptr, *misc = nullptr, *hitc = nullptr;
     u32 *ovf = nullptr, *rows = nullptr, *hits = nullptr;
+    u32 *known = nullptr;   // per record: the hit position found while seeding, or NOPOS
     mb_smem *out = nullptr;
     u64 *skeys = nullptr, *skeys_alt = nullptr;
     u32 *perm = nullptr, *perm_alt = nullptr;
@@ -1173,7 +1341,7 @@ extern "C" int mb_plan_create(const mb_index *idx, const mb_opts *opts, uint32_t
     if (rb > tb) tb = rb;
     size_t sizes[] = {P->nslots * sizeof(SlotRec), nr * 8, nr * 8, 256, P->max_smem * 8, nr * 4, P->max_hits * 4,
                       P->max_hits * 4, P->max_smem * sizeof(mb_smem), P->queue ? nr * 8 : 0, P->queue ? nr * 8 : 0,
-                      P->queue ? nr * 4 : 0, P->queue ? nr * 4 : 0, tb};
+                      P->queue ? nr * 4 : 0, P->queue ? nr * 4 : 0, tb, P->max_smem * 4};
     size_t total = 0;
     for (size_t z : sizes) total += align_up(z);
     if (cudaMalloc(&P->mem, total) != cudaSuccess) {
@@ -1186,7 +1354,8 @@ extern "C" int mb_plan_create(const mb_index *idx, const mb_opts *opts, uint32_t
     char *m = (char *)P->mem;
     void **ptrs[] = {(void **)&P->slots, (void **)&P->counts, (void **)&P->soff, (void **)&P->misc, (void **)&P->hitc,
                      (void **)&P->ovf, (void **)&P->rows, (void **)&P->hits, (void **)&P->out, (void **)&P->skeys,
-                     (void **)&P->skeys_alt, (void **)&P->perm, (void **)&P->perm_alt, (void **)&P->tmp};
+                     (void **)&P->skeys_alt, (void **)&P->perm, (void **)&P->perm_alt, (void **)&P->tmp,
+                     (void **)&P->known};
     for (size_t i = 0; i < sizeof(sizes) / sizeof(sizes[0]); ++i) {
         *ptrs[i] = sizes[i] ? (void *)m : nullptr;
         m += align_up(sizes[i]);
@@ -1228,20 +1397,21 @@ extern "C" int mb_plan_run(mb_plan *P, const uint8_t *seq, const uint64_t *off, 
         perm = P->perm;
     }
     SmemArgs sa{I, seq, off, n_reads, mate, bs, P->l, P->c, P->kmer, P->slots, P->nslots, P->counts, P->ovf, ovf_n,
-                perm, qhead, nullptr};
+                perm, qhead, nullptr, nullptr, I.text2 && !(P->flags & MB_STEP_ONLY)};
     MB_TRY(launch_smem(sa, false, P->queue, P->block, st));
     MB_TRY(scan_exclusive_u64(P->counts, P->soff, n_reads, n_smem, P->tmp, st));
     const unsigned G = (unsigned)((n_reads + 255) / 256);
     k_gather<<<G, 256, 0, st>>>(off, n_reads, P->slots, P->nslots, P->counts, P->soff, P->max_occ, P->out, P->hitc,
-                                P->max_smem);
+                                P->max_smem, P->known);
     MB_KCHECK();
     k_smem_overflow<<<resident_grid((const void *)k_smem_overflow, 128, 1ull << 40), 128, 0, st>>>(I, seq, off, n_reads, mate, bs, P->l, P->c, P->kmer, P->ovf, ovf_n, P->soff,
-                                         P->max_occ, P->out, P->hitc, P->max_smem, nullptr);
+                                         P->max_occ, P->out, P->hitc, P->max_smem, nullptr, P->known);
     MB_KCHECK();
     MB_TRY(scan_exclusive_u64(P->hitc, P->hitc, P->max_smem, n_hits, P->tmp, st));
     k_set_hitoff<<<grid_for(P->max_smem, 256), 256, 0, st>>>(P->hitc, P->max_smem, n_smem, P->out);
     MB_KCHECK();
-    k_expand_rows<<<grid_for(P->max_smem, 256), 256, 0, st>>>(P->out, P->max_smem, n_smem, P->rows, P->max_hits);
+    k_expand_rows<<<grid_for(P->max_smem, 256), 256, 0, st>>>(P->out, P->max_smem, n_smem, P->rows, P->max_hits,
+                                                              P->known, P->hits);
     MB_KCHECK();
     MB_TRY(launch_locate(I, P->rows, P->max_hits, n_hits, P->hits, nullptr, false, P->depth, st));
     return MB_OK;

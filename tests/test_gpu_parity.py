@@ -143,16 +143,49 @@ def test_work_counters_match_oracle(mb):
     G = mb.mb_index_build(ref)
     X = oracle.Index(ref)
     mb.profile_reset()
-    o = dict(flags=mb.MB_COUNT | mb.MB_NO_KMER)
+    o = dict(flags=mb.MB_COUNT | mb.MB_NO_KMER | mb.MB_STEP_ONLY)
     sm, m, nh = mb.mb_seed_batch(G, rd.seq, rd.off, opts=o)
     mb.mb_locate(G, sm, m, opts=o, cap=nh)
     wc = mb.work_counters()
-    assert wc["kmer_lookups"] == 0
+    assert wc["kmer_lookups"] == 0 and wc["u_walk_steps"] == wc["u_samples"] == wc["u_text_loads"] == 0
     assert (wc["ext_steps"], wc["ext_blocks"]) == X.count_alg3(rd.seq, rd.off)
     keep = (sm["flags"] & 1) == 0
     rows = np.concatenate([np.arange(int(k), int(k) + int(s), dtype=np.uint64)
                            for k, s in zip(sm["k"][keep], sm["s"][keep])])
     assert (wc["lf_steps"], wc["sa_reads"]) == X.count_locate(rows)
+
+
+def test_auxiliary_arrays_and_text_extension(mb):
+    """The packed text and the rate-8 SA / ISA samples against the oracle's text and suffix array;
+    SMEMs and hits are the same whether unique matches are extended by comparing text, step by
+    step (MB_STEP_ONLY), or on an index without the arrays (MB_NO_AUX)."""
+    ref, rd, p = synth.workload(2, scale=0.01)
+    G = mb.mb_index_build(ref)
+    X = oracle.Index(ref)
+    t2, sx, ix = G.export_aux()
+    T = X.text().astype(np.int64) - 1          # oracle coding $=0, A..T=1..4
+    want = np.zeros(len(t2) * 16, np.int64)
+    want[:X.n - 1] = T[:X.n - 1]
+    packed = (want.reshape(-1, 16) << (2 * np.arange(16))).sum(axis=1).astype(np.uint32)
+    assert np.array_equal(t2, packed)
+    S = X.sa().astype(np.int64)
+    assert np.array_equal(sx, S[::8].astype(np.uint32))
+    isa = np.empty(X.n, np.int64)
+    isa[S] = np.arange(X.n)
+    assert np.array_equal(ix, isa[::8].astype(np.uint32))
+    mb.profile_reset()
+    sm, hits = mb.seed(G, rd.seq, rd.off, opts=dict(flags=mb.MB_COUNT))
+    wc = mb.work_counters()
+    assert wc["u_walk_steps"] > 0 and wc["u_text_loads"] > 0
+    compare_seed(sm, hits, X, rd.seq, rd.off)
+    sm2, hits2 = mb.seed(G, rd.seq, rd.off)
+    sm3, hits3 = mb.seed(G, rd.seq, rd.off, opts=dict(flags=mb.MB_STEP_ONLY))
+    N = mb.mb_index_build(ref, opts=dict(flags=mb.MB_NO_AUX))
+    sm4, hits4 = mb.seed(N, rd.seq, rd.off)
+    for a, b in ((sm2, hits2), (sm3, hits3), (sm4, hits4)):
+        assert a.tobytes() == sm.tobytes() and np.array_equal(b, hits)
+    with pytest.raises(mb.MbError):
+        N.export_aux()
 
 
 def test_workload2_scaled_device_pointers(mb):
@@ -269,6 +302,12 @@ def test_save_load_roundtrip_and_corruption(mb, tmp_path):
     a = mb.seed(G, rd.seq, rd.off)
     b = mb.seed(H, rd.seq, rd.off)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert all(np.array_equal(x, y) for x, y in zip(G.export_aux(), H.export_aux()))
+    # an index without the auxiliary arrays round-trips too
+    N = mb.mb_index_build(ref, opts=dict(flags=mb.MB_NO_AUX))
+    N.save(str(tmp_path / "n.mbi"))
+    c = mb.seed(mb.mb_index_load(str(tmp_path / "n.mbi")), rd.seq, rd.off)
+    assert np.array_equal(a[0], c[0]) and np.array_equal(a[1], c[1])
     raw = bytearray(open(path, "rb").read())
     raw[200] ^= 0xFF
     bad = str(tmp_path / "bad.mbi")
