@@ -75,7 +75,7 @@ typedef struct {
     uint32_t kmer_k;          /* k of the k-mer ds-interval table (default 10, Section 2.5), <= 14;
                                  the table takes 12 * 4^k bytes (3.2 GB at k = 14) */
     uint32_t flags;           /* MB_* flags above */
-    uint32_t chunk_reads;     /* mb_seed_locate: reads per pipelined chunk (0 = 2^21) */
+    uint32_t chunk_reads;     /* mb_seed_locate: reads per pipelined chunk (0 = 2^22) */
     uint32_t prefetch_depth;  /* tuning: LF-walks in flight per lane in locate, 1/2/4/8/16 (0 = 1) */
     uint32_t block_size;      /* tuning: threads per block (0 = default) */
 } mb_opts;
