@@ -217,6 +217,26 @@ def oracle_rate(ref, rd, params, target_s: float, threads: int, min_reads: int =
     return X, build_s, sample
 
 
+def cpu_batched_rate(src, sample, params, threads: int) -> dict:
+    """The paper's CPU design (Algorithm 3 with one queue per batch and prefetching, 64-byte
+    blocks, 10-mer table, BatchLocate) on the host cores, on the oracle's sample: context for the
+    GPU numbers, built from the GPU index's BWT and sampled suffix array."""
+    import cpu_batched
+    bwt, primary, ssa = src
+    t = time.time()
+    Y = cpu_batched.Index(bwt, primary, ssa, threads=threads)
+    build_s = time.time() - t
+    Y.seed(sample.seq[:int(sample.off[min(sample.n, 256)])], sample.off[:min(sample.n, 256) + 1],
+           params["min_len"], params["min_occ"], params["max_occ"], threads=threads)   # warm-up
+    t = time.time()
+    sm, hits = Y.seed(sample.seq, sample.off, params["min_len"], params["min_occ"], params["max_occ"],
+                      threads=threads)
+    dt = time.time() - t
+    return {"value": sample.n / dt, "unit": "reads/s", "cores": threads, "kind": "paper's CPU design",
+            "sample": f"the oracle's {sample.n} reads; index from the BWT ({build_s:.0f}s) untimed",
+            "seconds": dt, "smems": int(len(sm)), "hits": int(len(hits))}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -469,6 +489,11 @@ def run_gpu(args):
     idx = mb.mb_index_build(torch.from_numpy(ref).to(dev), opts=opts, n_seed=0)
     torch.cuda.synchronize()
     build_s = time.time() - t
+    # the BWT and the sampled SA for the CPU comparator (needs the full SA, dropped next)
+    cpu_index_src = None
+    if rank == 0 and not args.no_cpu_baseline:
+        e = idx.export(bwt=True, ssa=True)
+        cpu_index_src = (e["bwt"], idx.primary, e["ssa"])
     idx.drop_sa()
     log(f"index: n={idx.n} built in {build_s:.1f}s")
 
@@ -683,6 +708,9 @@ def run_gpu(args):
                "single_core": {"value": one.n / dt1, "unit": "reads/s", "cores": 1,
                                "sample": f"the first {one.n} reads of that sample", "seconds": dt1}}
         del X
+        cpu["batched_prefetch"] = cpu_batched_rate(cpu_index_src, sample, params, threads)
+        cpu_index_src = None
+        log(f"cpu baseline: {cpu}")
 
     if rank != 0:
         return 0

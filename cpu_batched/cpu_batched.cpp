@@ -1,0 +1,319 @@
+/*
+ * CPU comparator of the seeding stage: the paper's own CPU design (Section 2.4-2.5), built to be
+ * timed next to the GPU path as context.  It is not the oracle and not part of the product path
+ * (the library never calls it); bench.py times it on the host cores.
+ *
+ *  - Occurrence blocks as the paper lays them out for a 64-byte cache line (Section 2.2): per
+ *    128 BWT rows, the counts of A, C, G, T before the block (4 x u64) and the 128 symbols at 2
+ *    bits (4 x u64).  The $ row is stored as A and left out of the counts.
+ *  - Algorithm 3 (BatchFindSMEM) over a batch of reads with one FIFO queue; whenever an entry is
+ *    pushed, the blocks holding the two rows its next extension reads are prefetched
+ *    (Section 2.4: "prefetches memory blocks containing B[l] and B[l']"), so that by the time the
+ *    entry reaches the head of the queue its data is in cache.
+ *  - The ds-intervals of all 10-mers precomputed (Section 2.5); a stage-1 entry that starts from
+ *    the empty interval takes the 10 backward steps as one table lookup.  A failing 10-mer
+ *    restarts stage 1 at its second base; stage 3 tries the table once and steps otherwise.
+ *  - BatchLocate (Algorithm 2) over the rows of every kept SMEM of the batch, level by level,
+ *    prefetching the block of each next row.
+ * OpenMP over batches of reads.
+ */
+#include <stdint.h>
+#include <string.h>
+#include <algorithm>
+#include <vector>
+#include <omp.h>
+
+typedef uint64_t u64;
+typedef uint32_t u32;
+typedef uint8_t u8;
+
+namespace {
+
+struct Block {
+    u64 cnt[4];   // A, C, G, T in B[0, 128 b), $ excluded
+    u64 w[4];     // row q of the block at bits 2 (q % 32) of w[q / 32]; $ as A
+};
+
+struct Index {
+    u64 n = 0, primary = 0;
+    u64 C[4] = {0, 0, 0, 0};   // #{B[i] < a} for a = A, C, G, T ($ counted)
+    std::vector<Block> blk;
+    std::vector<u32> ssa;       // S(x r)
+    u32 r = 32;
+    std::vector<u64> kmer;      // 4^10 x (k, k', s)
+};
+
+constexpr u32 KTAB = 10;
+constexpr u64 M55 = 0x5555555555555555ULL;
+
+inline const Block &block_of(const Index &X, u64 x) { return X.blk[x >> 7]; }
+inline void prefetch_row(const Index &X, u64 x) { __builtin_prefetch(&X.blk[x >> 7], 0, 0); }
+
+// #{rows before m in word w (32 rows) holding code a}, m in 0..32
+inline u32 count_word(u64 w, u32 a, u32 m) {
+    if (m == 0) return 0;
+    const u64 y = ~(w ^ (M55 * a));                 // 11 in every 2-bit field equal to a
+    u64 eq = y & (y >> 1) & M55;
+    if (m < 32) eq &= (1ULL << (2 * m)) - 1;
+    return (u32)__builtin_popcountll(eq);
+}
+// #{rows before m in word w holding a code <= a}
+inline u32 count_le_word(u64 w, u32 a, u32 m) {
+    u32 c = 0;
+    for (u32 b = 0; b <= a; ++b) c += count_word(w, b, m);
+    return c;
+}
+
+// occurrences of code a (and of codes <= a) in B[0, x), $ excluded
+inline void occ2(const Index &X, u64 x, u32 a, u64 &na, u64 &nle) {
+    const Block &B = block_of(X, x);
+    const u32 m = (u32)(x & 127);
+    na = B.cnt[a];
+    nle = 0;
+    for (u32 b = 0; b <= a; ++b) nle += B.cnt[b];
+    for (u32 q = 0; q < 4; ++q) {
+        const int take = (int)m - 32 * (int)q;
+        if (take <= 0) break;
+        const u32 t = take > 32 ? 32u : (u32)take;
+        na += count_word(B.w[q], a, t);
+        nle += count_le_word(B.w[q], a, t);
+    }
+    if (X.primary < x && (X.primary >> 7) == (x >> 7)) {   // the $ row counted as A above
+        if (a == 0) na -= 1;
+        nle -= 1;
+    }
+}
+
+struct DS { u64 k, kr, s; };
+
+// Algorithm 1: BackwardExt by base a (0..3); a > 3 (N) gives the empty interval
+inline DS backward_ext(const Index &X, DS v, u32 a) {
+    if (a > 3) return DS{0, 0, 0};
+    u64 na0, nle0, na1, nle1;
+    occ2(X, v.k, a, na0, nle0);
+    occ2(X, v.k + v.s, a, na1, nle1);
+    return DS{X.C[a] + na0, v.kr + v.s - (nle1 - nle0), na1 - na0};
+}
+inline DS forward_ext(const Index &X, DS v, u32 a) {
+    if (a > 3) return DS{0, 0, 0};
+    const DS w = backward_ext(X, DS{v.kr, v.k, v.s}, 3 - a);
+    return DS{w.kr, w.k, w.s};
+}
+
+inline u64 lf(const Index &X, u64 x) {   // x is not the $ row
+    const Block &B = block_of(X, x);
+    const u32 m = (u32)(x & 127);
+    const u32 a = (u32)((B.w[m >> 5] >> (2 * (m & 31))) & 3);
+    u64 na, nle;
+    occ2(X, x, a, na, nle);
+    return X.C[a] + na;
+}
+
+struct Rec { u32 read, qbeg, qend; u64 k, kr, s; };
+
+// Algorithm 3 over reads [r0, r1) with one FIFO queue and prefetching; records per read in order
+void batch_find_smem(const Index &X, const u8 *seq, const u64 *off, u32 r0, u32 r1, u32 l, u32 c,
+                     std::vector<Rec> &out) {
+    struct E { u8 u, tried; u32 rd; int i, j; DS v; };
+    const DS empty{0, 0, X.n};
+    std::vector<E> ring(r1 - r0 + 1);
+    size_t head = 0, tail = 0, size = 0;
+    const size_t cap = ring.size();
+    auto base = [&](u32 rd, int j) -> u32 { return seq[off[rd] + (u64)j]; };
+    auto len = [&](u32 rd) -> int { return (int)(off[rd + 1] - off[rd]); };
+    auto push = [&](E e) {
+        // prefetch what this entry's next extension reads: rows k, k+s backwards, k', k'+s forwards
+        const u64 p = e.u == 2 ? e.v.kr : e.v.k;
+        if (e.v.s != X.n) {
+            prefetch_row(X, p);
+            prefetch_row(X, p + e.v.s);
+        }
+        ring[tail] = e;
+        tail = tail + 1 == cap ? 0 : tail + 1;
+        ++size;
+    };
+    std::vector<std::vector<Rec>> per(r1 - r0);
+    auto emit = [&](const E &e) { per[e.rd - r0].push_back(Rec{e.rd, (u32)e.i, (u32)e.j, e.v.k, e.v.kr, e.v.s}); };
+    // k-mer code of P[x, x+10), base t in bits 2t; false if it holds an N
+    auto kmer_code = [&](u32 rd, int x, u32 &code) {
+        u32 v = 0;
+        for (u32 t = 0; t < KTAB; ++t) {
+            const u32 b = base(rd, x + (int)t);
+            if (b > 3) return false;
+            v |= b << (2 * t);
+        }
+        code = v;
+        return true;
+    };
+    // Algorithm 3's BackStep, with the table for the first 10 steps from the empty interval
+    auto back_step = [&](E e) {
+        // stage 1 may use all bases down to i; stage 3 stops above i, so its k-mer must end there
+        const bool fits = e.u == 1 ? e.j - (int)KTAB + 1 >= e.i : e.j - (int)KTAB + 1 > e.i;
+        if (e.v.s == X.n && l >= KTAB && fits && (e.u == 1 || !e.tried)) {
+            u32 code;
+            if (kmer_code(e.rd, e.j - (int)KTAB + 1, code)) {
+                const u64 *t = &X.kmer[3 * (u64)code];
+                if (t[2] >= c) {
+                    e.v = DS{t[0], t[1], t[2]};
+                    e.j -= (int)KTAB;
+                    push(e);
+                    return;
+                }
+                if (e.u == 1) {   // no window starting at or before the k-mer's first base matches
+                    const int x = e.j - (int)KTAB + 1;
+                    if (x + (int)l < len(e.rd)) push(E{1, 0, e.rd, x + 1, x + (int)l, empty});
+                    return;
+                }
+                e.tried = 1;      // stage 3: the exact restart needs single steps
+            }
+        }
+        const DS w = backward_ext(X, e.v, base(e.rd, e.j));
+        if (w.s >= c) push(E{e.u, e.tried, e.rd, e.i, e.j - 1, w});
+        else if (e.j + (int)l < len(e.rd)) push(E{1, 0, e.rd, e.j + 1, e.j + (int)l, empty});
+    };
+    for (u32 rd = r0; rd < r1; ++rd)
+        if ((int)l - 1 < len(rd)) push(E{1, 0, rd, 0, (int)l - 1, empty});
+    while (size) {
+        E e = ring[head];
+        head = head + 1 == cap ? 0 : head + 1;
+        --size;
+        if (e.u == 1) {
+            if (e.j < e.i) push(E{2, 0, e.rd, e.i, e.i + (int)l, e.v});
+            else back_step(e);
+        } else if (e.u == 2) {
+            if (e.j == len(e.rd)) {
+                emit(e);
+                continue;
+            }
+            const DS w = forward_ext(X, e.v, base(e.rd, e.j));
+            if (w.s >= c) push(E{2, 0, e.rd, e.i, e.j + 1, w});
+            else {
+                emit(e);
+                push(E{3, 0, e.rd, e.i, e.j, empty});
+            }
+        } else {
+            if (e.j <= e.i) push(E{1, 0, e.rd, e.j + 1, e.j + (int)l, empty});
+            else back_step(e);
+        }
+    }
+    for (auto &v : per) out.insert(out.end(), v.begin(), v.end());
+}
+
+// Algorithm 2, BatchLocate: all rows of the batch advance one level at a time
+void batch_locate(const Index &X, const std::vector<u64> &rows, u32 *pos) {
+    struct W { u64 k; u64 idx; u32 steps; };
+    std::vector<W> E(rows.size()), E2;
+    for (size_t q = 0; q < rows.size(); ++q) E[q] = W{rows[q], q, 0};
+    while (!E.empty()) {
+        E2.clear();
+        for (const W &w : E) {
+            if (w.k % X.r == 0) pos[w.idx] = (u32)(((u64)X.ssa[w.k / X.r] + w.steps) % X.n);
+            else if (w.k == X.primary) pos[w.idx] = w.steps;   // S = 0
+            else {
+                const u64 nk = lf(X, w.k);
+                prefetch_row(X, nk);
+                E2.push_back(W{nk, w.idx, w.steps + 1});
+            }
+        }
+        E.swap(E2);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+/* Index from the BWT (n bytes: 0 = $, 1..4 = A..T), the row of $ and the sampled suffix array
+ * (ceil(n / r) u32 of S(x r)). */
+void *cb_index_build(const u8 *bwt, u64 n, u64 primary, const u32 *ssa, u32 r, int threads) {
+    Index *X = new Index;
+    X->n = n;
+    X->primary = primary;
+    X->r = r;
+    const u64 nb = n / 128 + 1;
+    X->blk.assign(nb, Block{});
+    std::vector<u64> cnt(nb * 4, 0);
+    const int th = threads > 0 ? threads : omp_get_max_threads();
+#pragma omp parallel for num_threads(th) schedule(static)
+    for (u64 b = 0; b < nb; ++b) {
+        Block &B = X->blk[b];
+        for (u32 q = 0; q < 128; ++q) {
+            const u64 x = b * 128 + q;
+            if (x >= n) break;
+            const u8 s = bwt[x];
+            const u32 code = s == 0 ? 0u : (u32)(s - 1);
+            B.w[q >> 5] |= (u64)code << (2 * (q & 31));
+            if (s) ++cnt[b * 4 + code];
+        }
+    }
+    u64 run[4] = {0, 0, 0, 0};
+    for (u64 b = 0; b < nb; ++b)
+        for (u32 a = 0; a < 4; ++a) {
+            X->blk[b].cnt[a] = run[a];
+            run[a] += cnt[b * 4 + a];
+        }
+    X->C[0] = 1;
+    for (u32 a = 1; a < 4; ++a) X->C[a] = X->C[a - 1] + run[a - 1];
+    X->ssa.assign(ssa, ssa + (n + r - 1) / r);
+    // ds-intervals of all 10-mers: 10 BackwardExt steps from (0, 0, n), last base first
+    const u64 nk = 1ULL << (2 * KTAB);
+    X->kmer.assign(nk * 3, 0);
+#pragma omp parallel for num_threads(th) schedule(static)
+    for (u64 w = 0; w < nk; ++w) {
+        DS v{0, 0, n};
+        for (int t = (int)KTAB - 1; t >= 0 && v.s; --t) v = backward_ext(*X, v, (u32)(w >> (2 * t)) & 3u);
+        X->kmer[3 * w] = v.k;
+        X->kmer[3 * w + 1] = v.kr;
+        X->kmer[3 * w + 2] = v.s;
+    }
+    return X;
+}
+
+void cb_index_free(void *x) { delete (Index *)x; }
+
+struct CbResult {
+    std::vector<Rec> smem;
+    std::vector<u32> hits;
+};
+
+/* SMEMs (Algorithm 3, batches of `batch` reads per queue) and their hits (BatchLocate per batch)
+ * for reads with codes 0..3 (4 = N); SMEMs with s > max_occ get no hits.  Returns a handle. */
+void *cb_seed(void *x, const u8 *seq, const u64 *off, u32 nr, u32 l, u32 c, u32 max_occ, u32 batch, int threads) {
+    const Index &X = *(Index *)x;
+    if (batch == 0) batch = 4096;
+    const u32 nbt = (nr + batch - 1) / batch;
+    std::vector<std::vector<Rec>> recs(nbt);
+    std::vector<std::vector<u32>> hits(nbt);
+#pragma omp parallel for num_threads(threads > 0 ? threads : omp_get_max_threads()) schedule(dynamic, 1)
+    for (u32 b = 0; b < nbt; ++b) {
+        const u32 r0 = b * batch, r1 = std::min(nr, r0 + batch);
+        batch_find_smem(X, seq, off, r0, r1, l, c, recs[b]);
+        std::vector<u64> rows;
+        for (const Rec &m : recs[b])
+            if (m.s <= max_occ)
+                for (u64 t = 0; t < m.s; ++t) rows.push_back(m.k + t);
+        hits[b].resize(rows.size());
+        batch_locate(X, rows, hits[b].data());
+    }
+    CbResult *R = new CbResult;
+    for (u32 b = 0; b < nbt; ++b) {
+        R->smem.insert(R->smem.end(), recs[b].begin(), recs[b].end());
+        R->hits.insert(R->hits.end(), hits[b].begin(), hits[b].end());
+    }
+    return R;
+}
+u64 cb_result_nsmem(void *r) { return ((CbResult *)r)->smem.size(); }
+u64 cb_result_nhits(void *r) { return ((CbResult *)r)->hits.size(); }
+/* records as 6 u64 each (read, qbeg, qend, k, kr, s), then the hits */
+void cb_result_get(void *r, u64 *smem, u32 *hits) {
+    const CbResult &R = *(CbResult *)r;
+    for (size_t q = 0; q < R.smem.size(); ++q) {
+        const Rec &m = R.smem[q];
+        u64 *o = smem + 6 * q;
+        o[0] = m.read; o[1] = m.qbeg; o[2] = m.qend; o[3] = m.k; o[4] = m.kr; o[5] = m.s;
+    }
+    if (!R.hits.empty()) memcpy(hits, R.hits.data(), R.hits.size() * 4);
+}
+void cb_result_free(void *r) { delete (CbResult *)r; }
+
+}  // extern "C"
