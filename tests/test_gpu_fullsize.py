@@ -144,3 +144,15 @@ def test_workload3_bisulfite_1gbp_three_base_index(mb):
     rmate = np.repeat(rd.mate[sm["read"].astype(np.int64)], cnt)
     assert np.array_equal(kp.astype(bool), oracle.bs_keep(h, qlen, rmate, len(ref)))
     assert kp.sum() > 0
+    # T-to-C split of every kept hit (Section 2.8), checked against the oracle on the hits of 1% of
+    # the reads
+    pc = mb.mb_bs_split(G, ref, rd.seq, rd.off, rd.mate, sm, m, h, nh, keep=kp)
+    pick = np.random.default_rng(0x6D65).choice(rd.n, rd.n // 100, replace=False)
+    msel = np.nonzero(np.isin(sm["read"].astype(np.int64), pick))[0]
+    hoff = sm["hit_off"].astype(np.int64)
+    hsel = np.concatenate([np.arange(hoff[q], hoff[q] + cnt[q]) for q in msel]).astype(np.int64)
+    want = oracle.bs_split(ref, rd.seq, rd.off, rd.mate, sm[msel], h[hsel], kp[hsel])
+    want["hit"] = hsel[want["hit"].astype(np.int64)]
+    got = pc[np.isin(pc["hit"].astype(np.int64), hsel)]
+    assert len(want) > 0
+    assert got.tobytes() == want.astype(mb.PIECE_DTYPE).tobytes()
