@@ -400,10 +400,11 @@ def bench_rescue(mb, torch, dev, ref, n_pairs: int, reps: int = 5):
                          "ops": "2 per q-mer pair compared (compare, add)", "compares_per_launch": compares}}
 
 
-def bench_served(mb, G, ref, n_requests: int, load: float = 0.7):
+def bench_served(mb, G, ref, n_requests: int, load: float = 0.7, sweep=(0.3, 0.5, 0.9, 0.95)):
     """Served form on the resident index: capacity (all requests at once), then Poisson arrivals at
     `load` x capacity; latency per request from submit to results on the host.  The same arrivals
-    served by sequential plain launches (one request at a time) for comparison."""
+    served by sequential plain launches (one request at a time) for comparison, and the served
+    form's latencies at the other offered loads of `sweep`."""
     import threading as th
     reqs = serve_requests(ref, n_requests, 4242)
     total_reads = sum(r.n for r in reqs)
@@ -414,30 +415,38 @@ def bench_served(mb, G, ref, n_requests: int, load: float = 0.7):
         srv.wait(tk)
     cap_s = time.time() - t
     cap_rps = n_requests / cap_s
+    q = lambda a, p: float(np.percentile(np.asarray(a), p))
+
+    def poisson(rate, seed):
+        """Submit the requests at Poisson arrival times; (latencies in ms, wall seconds)."""
+        arrivals = np.cumsum(np.random.default_rng(seed).exponential(1.0 / rate, n_requests))
+        lat = [0.0] * n_requests
+        tk = [0] * n_requests
+
+        def collect():
+            for i in range(n_requests):
+                while tk[i] == 0:
+                    time.sleep(0.0002)
+                _, _, lat[i] = srv.wait(tk[i])
+
+        col = th.Thread(target=collect)
+        col.start()
+        t0 = time.time()
+        for i, r in enumerate(reqs):
+            d = t0 + arrivals[i] - time.time()
+            if d > 0:
+                time.sleep(d)
+            tk[i] = srv.submit(r.seq, r.off)
+        col.join()
+        return lat, time.time() - t0, arrivals
+
     rate = load * cap_rps
-    gaps = np.random.default_rng(17).exponential(1.0 / rate, n_requests)
-    arrivals = np.cumsum(gaps)
-    lat = [0.0] * n_requests
-    tk = [0] * n_requests
-    done_ev = th.Event()
-
-    def collect():
-        for i in range(n_requests):
-            while tk[i] == 0:
-                time.sleep(0.0002)
-            _, _, lat[i] = srv.wait(tk[i])
-        done_ev.set()
-
-    col = th.Thread(target=collect)
-    col.start()
-    t0 = time.time()
-    for i, r in enumerate(reqs):
-        d = t0 + arrivals[i] - time.time()
-        if d > 0:
-            time.sleep(d)
-        tk[i] = srv.submit(r.seq, r.off)
-    col.join()
-    wall = time.time() - t0
+    lat, wall, arrivals = poisson(rate, 17)
+    points = []
+    for k, ld in enumerate(sweep):
+        sl, sw, _ = poisson(ld * cap_rps, 18 + k)
+        points.append({"offered_load": ld, "arrival_rate_per_s": ld * cap_rps, "served_reads_per_s": total_reads / sw,
+                       "p50_ms": q(sl, 50), "p95_ms": q(sl, 95), "p99_ms": q(sl, 99)})
     stats = srv.stats()
     srv.close()
     # sequential plain launches on the same arrival times
@@ -450,7 +459,6 @@ def bench_served(mb, G, ref, n_requests: int, load: float = 0.7):
         mb.seed(G, r.seq, r.off)
         seq_lat.append((time.time() - t0 - arrivals[i]) * 1000)
     seq_wall = time.time() - t0
-    q = lambda a, p: float(np.percentile(np.asarray(a), p))
     return {"requests": n_requests, "reads": total_reads,
             "mix": "80% short (1-4,096 pairs of 2x150), 20% long (1-4,096 reads of 1-10 kb), log-uniform sizes",
             "capacity_requests_per_s": cap_rps, "capacity_reads_per_s": total_reads / cap_s,
@@ -460,6 +468,7 @@ def bench_served(mb, G, ref, n_requests: int, load: float = 0.7):
             "sequential_plain_reads_per_s": total_reads / seq_wall,
             "sequential_plain_p50_ms": q(seq_lat, 50), "sequential_plain_p95_ms": q(seq_lat, 95),
             "sequential_plain_p99_ms": q(seq_lat, 99),
+            "load_sweep": points,
             "slots": stats["slots"], "launch_groups": stats["groups"], "merged_requests": stats["merged"]}
 
 
@@ -760,7 +769,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the served-form measurement")
     ap.add_argument("--no-rescue", action="store_true", help="skip the mate-rescue prefilter measurement")
     ap.add_argument("--rescue-pairs", type=int, default=1_000_000)
-    ap.add_argument("--serve-requests", type=int, default=600)
+    ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--probe-gib", type=float, default=1, help="buffer of the random-gather probe (GiB)")
     ap.add_argument("--probe-sweep", action="store_true",
                     help="only the random-read probe over buffer sizes 1/32 .. 8 GiB (one JSON line each)")
