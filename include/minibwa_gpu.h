@@ -53,8 +53,8 @@ enum {
 #define MB_CHECKED  0x4u   /* seeding: bounds-check every block / row index on the device */
 #define MB_NO_KMER  0x8u   /* seeding: do not use the k-mer ds-interval table */
 #define MB_COUNT    0x10u  /* seeding/locate: also count the work done (mb_work_counters) */
-#define MB_NO_AUX   0x20u  /* index: build without the packed text and the rate-8 SA / ISA samples
-                              (2.5 bytes per text position) that let seeding extend unique matches
+#define MB_NO_AUX   0x20u  /* index: build without the packed text and the rate-4 SA / ISA samples
+                              (2.25 bytes per text position) that let seeding extend unique matches
                               by comparing text */
 #define MB_STEP_ONLY 0x40u /* seeding: extend every match step by step (Algorithm 1), even where
                               the auxiliary arrays allow comparing text */
@@ -105,8 +105,8 @@ int mb_index_build(const uint8_t *ref, uint64_t len, const mb_opts *opts, uint64
                    void *stream, mb_index **out);
 
 /* Write / read an index file (header with version, sizes and a checksum; the blocks as in
- * memory).  Errors: MB_ERR_IO, MB_ERR_CORRUPT (bad header, size or checksum),
- * MB_ERR_NOMEM, MB_ERR_CUDA. */
+ * memory).  Errors: MB_ERR_IO, MB_ERR_CORRUPT (bad header, size or checksum, or auxiliary samples
+ * at another rate than this library's), MB_ERR_NOMEM, MB_ERR_CUDA. */
 int mb_index_save(const mb_index *idx, const char *path);
 int mb_index_load(const char *path, void *stream, mb_index **out);
 void mb_index_free(mb_index *idx);
@@ -125,8 +125,8 @@ int mb_index_export(const mb_index *idx, uint32_t *sa, uint8_t *bwt, uint32_t *s
                     void *occ_blocks, uint32_t *kmer, uint64_t *C);
 /* The auxiliary arrays of an index built without MB_NO_AUX (else MB_ERR_ARG when any pointer is
  * given): text2 ((n - 1 + 15) / 16 + 2 u32: T[0, n-1) at 2 bits per base, base e of word w in
- * bits 2e..2e+1, zero padding), sa_aux (ceil(n / 8) u32: S(8x)), isa_aux (ceil(n / 8) u32: the
- * row of the suffix at text position 8p).  No counterpart in the paper: they let seeding extend
+ * bits 2e..2e+1, zero padding), sa_aux (ceil(n / 4) u32: S(4x)), isa_aux (ceil(n / 4) u32: the
+ * row of the suffix at text position 4p).  No counterpart in the paper: they let seeding extend
  * a match that occurs once by comparing the read with the text (same SMEMs). */
 int mb_index_export_aux(const mb_index *idx, uint32_t *text2, uint32_t *sa_aux, uint32_t *isa_aux);
 /* Free the full suffix array kept after the build (it is only needed for mb_index_export). */

@@ -21,6 +21,7 @@ __all__ = ["SMEM_DTYPE", "Opts", "MbError", "lib", "build", "Index", "mb_index_b
 
 MB_BS3, MB_BATCHED, MB_CHECKED, MB_NO_KMER, MB_COUNT = 0x1, 0x2, 0x4, 0x8, 0x10
 MB_NO_AUX, MB_STEP_ONLY = 0x20, 0x40
+AUX_RATE = 4   # sample rate of the auxiliary SA / ISA samples (mb_index_export_aux)
 MB_SMEM_OVER_MAX_OCC, MB_SMEM_ROUND2 = 0x1, 0x2
 MB_ERR_CAPACITY = -3
 
@@ -205,8 +206,8 @@ class Index:
         """(text2, sa_aux, isa_aux) as host arrays (see mb_index_export_aux)."""
         n = self.n
         t2 = np.empty((n - 1 + 15) // 16 + 2, np.uint32)
-        sx = np.empty((n + 7) // 8, np.uint32)
-        ix = np.empty((n + 7) // 8, np.uint32)
+        sx = np.empty((n + AUX_RATE - 1) // AUX_RATE, np.uint32)
+        ix = np.empty((n + AUX_RATE - 1) // AUX_RATE, np.uint32)
         _check(lib().mb_index_export_aux(self._h, _ptr(t2), _ptr(sx), _ptr(ix)), "mb_index_export_aux")
         return t2, sx, ix
 

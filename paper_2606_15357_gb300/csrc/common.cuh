@@ -125,7 +125,7 @@ struct DevIndex {
     const u32 *isa_aux; // row of the suffix at text position p * AUX_RATE
 };
 // Sample rate of the auxiliary SA / ISA samples used to extend unique matches by comparison.
-constexpr u32 AUX_RATE = 8;
+constexpr u32 AUX_RATE = 4;
 
 struct mb_index_impl;
 

@@ -666,7 +666,8 @@ namespace {
 constexpr u64 MAGIC = 0x3130585744424D4DULL;   // "MMBDWX01"
 struct FileHeader {
     u64 magic, version, n, rlen, primary, nblocks;
-    u32 sa_rate, kmer_k, flags, aux;   // aux: 1 when the packed text and SA / ISA samples follow
+    u32 sa_rate, kmer_k, flags, aux;   // aux: the SA / ISA sample rate when the packed text and
+                                       // those samples follow, else 0
     u64 C[5];
     u64 checksum;
 };
@@ -703,7 +704,7 @@ extern "C" int mb_index_save(const mb_index *idx, const char *path) {
     memset(&h, 0, sizeof h);
     h.magic = MAGIC;
     h.version = 4;
-    h.aux = aux ? 1u : 0u;
+    h.aux = aux ? AUX_RATE : 0u;
     h.n = idx->n;
     h.rlen = idx->rlen;
     h.primary = idx->primary;
@@ -745,9 +746,15 @@ extern "C" int mb_index_load(const char *path, void *stream, mb_index **out) {
         return MB_ERR_CORRUPT;
     }
     if (h.magic != MAGIC || h.version != 4 || h.sa_rate == 0 || h.kmer_k > 14 || h.n >= (1ULL << 32) ||
-        h.n < 2 || h.aux > 1 || h.nblocks != h.n / BLK_ROWS + 1) {
+        h.n < 2 || h.nblocks != h.n / BLK_ROWS + 1) {
         fclose(f);
         mb_set_error("mb_index_load: bad header");
+        return MB_ERR_CORRUPT;
+    }
+    if (h.aux != 0 && h.aux != AUX_RATE) {
+        fclose(f);
+        mb_set_error("mb_index_load: the file's auxiliary samples are at rate %u, this library reads rate %u "
+                     "(rebuild the index)", h.aux, AUX_RATE);
         return MB_ERR_CORRUPT;
     }
     u64 ns = (h.n + h.sa_rate - 1) / h.sa_rate, nk = 1ULL << (2 * h.kmer_k);

@@ -156,7 +156,7 @@ def test_work_counters_match_oracle(mb):
 
 
 def test_auxiliary_arrays_and_text_extension(mb):
-    """The packed text and the rate-8 SA / ISA samples against the oracle's text and suffix array;
+    """The packed text and the rate-4 SA / ISA samples against the oracle's text and suffix array;
     SMEMs and hits are the same whether unique matches are extended by comparing text, step by
     step (MB_STEP_ONLY), or on an index without the arrays (MB_NO_AUX)."""
     ref, rd, p = synth.workload(2, scale=0.01)
@@ -169,10 +169,10 @@ def test_auxiliary_arrays_and_text_extension(mb):
     packed = (want.reshape(-1, 16) << (2 * np.arange(16))).sum(axis=1).astype(np.uint32)
     assert np.array_equal(t2, packed)
     S = X.sa().astype(np.int64)
-    assert np.array_equal(sx, S[::8].astype(np.uint32))
+    assert np.array_equal(sx, S[::mb.AUX_RATE].astype(np.uint32))
     isa = np.empty(X.n, np.int64)
     isa[S] = np.arange(X.n)
-    assert np.array_equal(ix, isa[::8].astype(np.uint32))
+    assert np.array_equal(ix, isa[::mb.AUX_RATE].astype(np.uint32))
     mb.profile_reset()
     sm, hits = mb.seed(G, rd.seq, rd.off, opts=dict(flags=mb.MB_COUNT))
     wc = mb.work_counters()
