@@ -400,19 +400,31 @@ def bench_rescue(mb, torch, dev, ref, n_pairs: int, reps: int = 5):
                          "ops": "2 per q-mer pair compared (compare, add)", "compares_per_launch": compares}}
 
 
-def bench_served(mb, G, ref, n_requests: int, load: float = 0.7, sweep=(0.3, 0.5, 0.9, 0.95)):
-    """Served form on the resident index: capacity (all requests at once), then Poisson arrivals at
-    `load` x capacity; latency per request from submit to results on the host.  The same arrivals
-    served by sequential plain launches (one request at a time) for comparison, and the served
-    form's latencies at the other offered loads of `sweep`."""
+def bench_served(mb, G, ref, n_requests: int, pool: int = 2000, load: float = 0.7,
+                 sweep=(0.3, 0.5, 0.9, 0.95), window: int = 4096, seq_prefix: int = 2000):
+    """Served form on the resident index: capacity (the whole stream submitted with at most
+    `window` requests outstanding), then Poisson arrivals at `load` x capacity; latency per request
+    from submit to results on the host.  The stream's requests are drawn (seeded) from `pool`
+    generated requests, so host memory stays bounded; every request is copied at submit and
+    seeded in full.  The first `seq_prefix` arrivals served by sequential plain launches (one
+    request at a time) for comparison, and the served form's latencies at the other offered loads
+    of `sweep`."""
+    import collections
     import threading as th
-    reqs = serve_requests(ref, n_requests, 4242)
+    base = serve_requests(ref, min(pool, n_requests), 4242)
+    pick = (np.arange(n_requests) if n_requests <= len(base) else
+            np.random.default_rng(4243).integers(0, len(base), n_requests))
+    reqs = [base[i] for i in pick]
     total_reads = sum(r.n for r in reqs)
     srv = mb.Server(G, hbm_budget=8 << 30)
     t = time.time()
-    tickets = [srv.submit(r.seq, r.off) for r in reqs]
-    for tk in tickets:
-        srv.wait(tk)
+    out = collections.deque()
+    for r in reqs:
+        if len(out) >= window:
+            srv.wait(out.popleft())
+        out.append(srv.submit(r.seq, r.off))
+    while out:
+        srv.wait(out.popleft())
     cap_s = time.time() - t
     cap_rps = n_requests / cap_s
     q = lambda a, p: float(np.percentile(np.asarray(a), p))
@@ -449,23 +461,27 @@ def bench_served(mb, G, ref, n_requests: int, load: float = 0.7, sweep=(0.3, 0.5
                        "p50_ms": q(sl, 50), "p95_ms": q(sl, 95), "p99_ms": q(sl, 99)})
     stats = srv.stats()
     srv.close()
-    # sequential plain launches on the same arrival times
+    # sequential plain launches on the same arrival times (the first seq_prefix arrivals)
+    ns = min(seq_prefix, n_requests)
     seq_lat = []
     t0 = time.time()
-    for i, r in enumerate(reqs):
+    for i, r in enumerate(reqs[:ns]):
         d = t0 + arrivals[i] - time.time()
         if d > 0:
             time.sleep(d)
         mb.seed(G, r.seq, r.off)
         seq_lat.append((time.time() - t0 - arrivals[i]) * 1000)
     seq_wall = time.time() - t0
-    return {"requests": n_requests, "reads": total_reads,
+    return {"requests": n_requests, "reads": total_reads, "distinct_requests": len(base),
+            "stream": f"{n_requests} requests drawn (seeded) from {len(base)} generated ones",
             "mix": "80% short (1-4,096 pairs of 2x150), 20% long (1-4,096 reads of 1-10 kb), log-uniform sizes",
             "capacity_requests_per_s": cap_rps, "capacity_reads_per_s": total_reads / cap_s,
+            "capacity_window": window,
             "offered_load": load, "arrival_rate_per_s": rate,
             "served_reads_per_s": total_reads / wall,
             "served_p50_ms": q(lat, 50), "served_p95_ms": q(lat, 95), "served_p99_ms": q(lat, 99),
-            "sequential_plain_reads_per_s": total_reads / seq_wall,
+            "sequential_plain_requests": ns,
+            "sequential_plain_reads_per_s": sum(r.n for r in reqs[:ns]) / seq_wall,
             "sequential_plain_p50_ms": q(seq_lat, 50), "sequential_plain_p95_ms": q(seq_lat, 95),
             "sequential_plain_p99_ms": q(seq_lat, 99),
             "load_sweep": points,
@@ -657,7 +673,7 @@ def run_gpu(args):
         off_h = torch.from_numpy(rd.off.view(np.int64)).pin_memory()
         out_h = torch.empty(m * 48, dtype=torch.uint8).pin_memory()
         hits_h = torch.empty(max(nh, 1), dtype=torch.int32).pin_memory()
-        k2 = max(1, min(args.steps, 3))
+        k2 = max(1, args.steps)
         eopts = dict(opts, flags=best.flags)   # the same launch shape as the graph form
         mb.seed_locate(idx, seq_h, off_h, opts=eopts, out=out_h, cap=m, hits=hits_h, hits_cap=nh)   # warm-up
         torch.cuda.synchronize()
@@ -689,7 +705,7 @@ def run_gpu(args):
 
     served = None
     if rank == 0 and not args.no_serve:
-        served = bench_served(mb, idx, ref, args.serve_requests)
+        served = bench_served(mb, idx, ref, args.serve_requests, pool=args.serve_pool)
         log(f"served: {served}")
     del out, hits
     torch.cuda.empty_cache()
@@ -769,7 +785,10 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the served-form measurement")
     ap.add_argument("--no-rescue", action="store_true", help="skip the mate-rescue prefilter measurement")
     ap.add_argument("--rescue-pairs", type=int, default=1_000_000)
-    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-requests", type=int, default=50_000,
+                    help="requests in the served stream (Poisson arrivals)")
+    ap.add_argument("--serve-pool", type=int, default=2000,
+                    help="distinct generated requests the stream draws from")
     ap.add_argument("--probe-gib", type=float, default=1, help="buffer of the random-gather probe (GiB)")
     ap.add_argument("--probe-sweep", action="store_true",
                     help="only the random-read probe over buffer sizes 1/32 .. 8 GiB (one JSON line each)")
