@@ -246,13 +246,14 @@ int scan_inclusive_max_u32(const u32 *in, u32 *out, size_t n, void *tmp, cudaStr
 
 // Stable LSD radix sort of (key, val) pairs by the key bits in [lo_bit, hi_bit) of each digit
 // range given.  Sorted output ends in (keys, vals); (keys_alt, vals_alt) are scratch of the
-// same size.
+// same size.  With n_dev (device), only the first min(n, *n_dev) items are sorted (an odd number
+// of passes then still copies all n back).
 struct BitRange {
     int lo, hi;
 };
 size_t radix_tmp_bytes(size_t n);
 int radix_sort_pairs(u64 *keys, u32 *vals, u64 *keys_alt, u32 *vals_alt, size_t n, const BitRange *ranges,
-                     int nranges, void *tmp, cudaStream_t st);
+                     int nranges, void *tmp, cudaStream_t st, const u64 *n_dev = nullptr);
 
 // plan internals used by the server: device bytes of a plan, asynchronous copy of its two
 // result counts (n_smem, n_hits) to host memory, and its device result arrays

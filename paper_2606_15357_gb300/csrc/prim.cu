@@ -163,9 +163,14 @@ constexpr int RS_T = 256;        // threads (8 warps)
 constexpr int RS_I = 32;         // iterations of 32 items per warp
 constexpr size_t RS_TILE = (size_t)RS_T * RS_I;
 
-__global__ void __launch_bounds__(RS_T) k_radix_up(const u64 *__restrict__ keys, size_t n, int shift, u32 mask,
-                                                   u32 *__restrict__ hist, size_t tiles) {
+// n_dev (device, may be null): the number of items to sort when it is below n (the tiles past it
+// count nothing and move nothing).
+__device__ __forceinline__ size_t items(size_t n, const u64 *n_dev) { return n_dev && *n_dev < n ? (size_t)*n_dev : n; }
+
+__global__ void __launch_bounds__(RS_T) k_radix_up(const u64 *__restrict__ keys, size_t n, const u64 *n_dev, int shift,
+                                                   u32 mask, u32 *__restrict__ hist, size_t tiles) {
     __shared__ u32 h[256];
+    n = items(n, n_dev);
     h[threadIdx.x] = 0;
     __syncthreads();
     size_t base = blockIdx.x * RS_TILE;
@@ -183,9 +188,10 @@ __global__ void __launch_bounds__(RS_T) k_radix_up(const u64 *__restrict__ keys,
 // a digit: the scatter is stable.
 __global__ void __launch_bounds__(RS_T) k_radix_down(const u64 *__restrict__ keys, const u32 *__restrict__ vals,
                                                      u64 *__restrict__ okeys, u32 *__restrict__ ovals, size_t n,
-                                                     int shift, u32 mask, const u32 *__restrict__ offs,
-                                                     size_t tiles) {
+                                                     const u64 *n_dev, int shift, u32 mask,
+                                                     const u32 *__restrict__ offs, size_t tiles) {
     __shared__ u32 wh[RS_T / 32][256];
+    n = items(n, n_dev);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < (RS_T / 32) * 256; i += RS_T) (&wh[0][0])[i] = 0;
     __syncthreads();
@@ -237,7 +243,7 @@ size_t radix_tmp_bytes(size_t n) {
 }
 
 int radix_sort_pairs(u64 *keys, u32 *vals, u64 *keys_alt, u32 *vals_alt, size_t n, const BitRange *ranges,
-                     int nranges, void *tmp, cudaStream_t st) {
+                     int nranges, void *tmp, cudaStream_t st, const u64 *n_dev) {
     if (n <= 1) return MB_OK;
     if (n >= (1ULL << 32)) {
         mb_set_error("radix_sort_pairs: %zu items exceed 2^32-1", n);
@@ -253,10 +259,10 @@ int radix_sort_pairs(u64 *keys, u32 *vals, u64 *keys_alt, u32 *vals_alt, size_t 
         for (int sh = ranges[r].lo; sh < ranges[r].hi; sh += 8) {
             int w = ranges[r].hi - sh < 8 ? ranges[r].hi - sh : 8;
             u32 mask = (1u << w) - 1u;
-            k_radix_up<<<(unsigned)tiles, RS_T, 0, st>>>(ka, n, sh, mask, hist, tiles);
+            k_radix_up<<<(unsigned)tiles, RS_T, 0, st>>>(ka, n, n_dev, sh, mask, hist, tiles);
             MB_KCHECK();
             MB_TRY(scan_exclusive_u32(hist, hist, 256 * tiles, nullptr, stmp, st));
-            k_radix_down<<<(unsigned)tiles, RS_T, 0, st>>>(ka, va, kb, vb, n, sh, mask, hist, tiles);
+            k_radix_down<<<(unsigned)tiles, RS_T, 0, st>>>(ka, va, kb, vb, n, n_dev, sh, mask, hist, tiles);
             MB_KCHECK();
             u64 *tk = ka; ka = kb; kb = tk;
             u32 *tv = va; va = vb; vb = tv;

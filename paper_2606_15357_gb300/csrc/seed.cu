@@ -717,36 +717,141 @@ __device__ __forceinline__ u64 hits_of(const mb_smem *__restrict__ sm, u64 m) {
     return (__ldg(&sm[m].flags) & MB_SMEM_OVER_MAX_OCC) ? 0 : __ldg(&sm[m].s);
 }
 
-// rows[hit_off + t] = k + t for the hits of every record without MB_SMEM_OVER_MAX_OCC: one warp
-// per 32 records, writing each record's rows with the whole warp.
-// With `known` (a position per record, NOPOS when not found while seeding), the hit of a record
-// whose position is known is written to hits here and its row is marked NOPOS (locate skips it).
-__global__ void k_expand_rows(const mb_smem *__restrict__ sm, u64 nsm, const u64 *__restrict__ nsm_dev,
-                              u32 *__restrict__ rows, u64 rows_cap, const u32 *__restrict__ known = nullptr,
-                              u32 *__restrict__ hits = nullptr) {
-    const u32 lane = threadIdx.x & 31;
-    if (nsm_dev && *nsm_dev < nsm) nsm = *nsm_dev;
-    const u64 nw = ((u64)gridDim.x * blockDim.x) >> 5;
-    for (u64 base = ((blockIdx.x * (u64)blockDim.x + threadIdx.x) >> 5) * 32; base < nsm; base += nw * 32) {
-        u64 m = base + lane;
-        u64 ho = 0, cnt = 0;
-        u32 k = 0;
-        if (m < nsm) {
-            ho = __ldg(&sm[m].hit_off);
-            cnt = hits_of(sm, m);
-            k = (u32)__ldg(&sm[m].k);
-            if (known && cnt == 1 && ho < rows_cap) {
-                const u32 pos = known[m];
-                if (pos != NOPOS) {
-                    hits[ho] = pos;
-                    k = NOPOS;
-                }
+// ---------------------------------------------------------------------------- shared walks
+// The records of a batch repeat rows: reads that cover the same repeat give the same or nested SA
+// intervals (two strings' intervals are nested when one is a prefix of the other, else
+// disjoint), so on the 1 Gbp workload 331M hits hold 175M distinct rows.  Locate therefore walks
+// each row of the union of the records' intervals once and copies the positions to every hit
+// (Algorithm 2 gives one position per row, so the hits are the same).
+//
+// The records with rows to walk are sorted by (k ascending, s descending).  A record is maximal
+// when its interval ends after every earlier record's; its rows are walked, in sorted order.  Any
+// other record t lies inside the last maximal record before it: the first record that reaches the
+// running maximum of the ends before t is maximal, starts at or before k_t, ends at or after
+// k_t + s_t, and no maximal record can lie between it and t.  This holds for any intervals (the
+// public mb_locate takes records from the caller); nested ones share every repeated row.
+constexpr int SHARE_S_BITS = 9;                                   // s in the low bits of the sort key
+constexpr int SHARE_KEY_BITS = 32 + SHARE_S_BITS;
+constexpr u64 SHARE_NONE = (1ull << SHARE_KEY_BITS) - 1;          // key of a record with no row to walk
+
+__device__ __forceinline__ u64 records_of(u64 cap, const u64 *nsm_dev) {
+    return nsm_dev && *nsm_dev < cap ? *nsm_dev : cap;
+}
+__device__ __forceinline__ u32 end_of(u64 key, u64 s) {   // k + s, saturated to 32 bits
+    const u64 e = (key >> SHARE_S_BITS) + s;
+    return e < 0xFFFFFFFFull ? (u32)e : 0xFFFFFFFFu;
+}
+
+// Sort keys (k << 9 | 511 - min(s, 511)) and record numbers.  A record with a known position (one
+// hit, found while seeding) writes that hit here and walks nothing.
+__global__ void k_share_keys(const mb_smem *__restrict__ sm, u64 cap, const u64 *__restrict__ nsm_dev,
+                             const u32 *__restrict__ known, u32 *__restrict__ hits, u64 hits_cap,
+                             u64 *__restrict__ keys, u32 *__restrict__ vals) {
+    const u64 nsm = records_of(cap, nsm_dev);
+    for (u64 t = blockIdx.x * (u64)blockDim.x + threadIdx.x; t < nsm; t += (u64)gridDim.x * blockDim.x) {
+        const u64 cnt = hits_of(sm, t);
+        u64 key = SHARE_NONE;
+        if (cnt) {
+            const u32 pos = known && cnt == 1 ? known[t] : NOPOS;
+            if (pos != NOPOS) {
+                const u64 ho = __ldg(&sm[t].hit_off);
+                if (ho < hits_cap) hits[ho] = pos;
+            } else {
+                const u64 sb = cnt < (1u << SHARE_S_BITS) ? cnt : (1u << SHARE_S_BITS) - 1;
+                key = ((u64)(u32)__ldg(&sm[t].k) << SHARE_S_BITS) | ((1u << SHARE_S_BITS) - 1 - sb);
             }
         }
+        keys[t] = key;
+        vals[t] = (u32)t;
+    }
+}
+
+// ends[t] = k + s of sorted record t (0 past the records and for records with no rows)
+__global__ void k_share_ends(const mb_smem *__restrict__ sm, const u64 *__restrict__ keys,
+                             const u32 *__restrict__ vals, u64 cap, const u64 *__restrict__ nsm_dev,
+                             u32 *__restrict__ ends) {
+    const u64 nsm = records_of(cap, nsm_dev);
+    for (u64 t = blockIdx.x * (u64)blockDim.x + threadIdx.x; t < cap; t += (u64)gridDim.x * blockDim.x) {
+        u32 e = 0;
+        if (t < nsm && keys[t] != SHARE_NONE) e = end_of(keys[t], __ldg(&sm[vals[t]].s));
+        ends[t] = e;
+    }
+}
+
+// With pmax = the running maximum of the ends: len[t] = s of a maximal record (else 0) and
+// last[t] = t for a maximal record (else 0), to be scanned into row offsets and owners.
+__global__ void k_share_mark(const mb_smem *__restrict__ sm, const u64 *__restrict__ keys,
+                             const u32 *__restrict__ vals, u64 cap, const u64 *__restrict__ nsm_dev,
+                             const u32 *__restrict__ pmax, u64 *__restrict__ len, u32 *__restrict__ last) {
+    const u64 nsm = records_of(cap, nsm_dev);
+    for (u64 t = blockIdx.x * (u64)blockDim.x + threadIdx.x; t < cap; t += (u64)gridDim.x * blockDim.x) {
+        u64 l = 0;
+        u32 lm = 0;
+        if (t < nsm && keys[t] != SHARE_NONE) {
+            const u64 s = __ldg(&sm[vals[t]].s);
+            if (end_of(keys[t], s) > (t ? pmax[t - 1] : 0u)) {
+                l = s;
+                lm = (u32)t;
+            }
+        }
+        len[t] = l;
+        last[t] = lm;
+    }
+}
+
+__device__ __forceinline__ bool is_maximal(const u64 *keys, const u32 *last, u64 t) {
+    return keys[t] != SHARE_NONE && last[t] == (u32)t;   // the first record with rows is maximal
+}
+
+// rows[roff[t] + q] = k + q for every maximal sorted record t: one warp per 32 sorted records,
+// each record's rows written by the whole warp.
+__global__ void k_share_rows(const mb_smem *__restrict__ sm, const u64 *__restrict__ keys,
+                             const u32 *__restrict__ vals, const u32 *__restrict__ last,
+                             const u64 *__restrict__ roff, u64 cap, const u64 *__restrict__ nsm_dev,
+                             u32 *__restrict__ rows, u64 rows_cap) {
+    const u32 lane = threadIdx.x & 31;
+    const u64 nsm = records_of(cap, nsm_dev);
+    const u64 nw = ((u64)gridDim.x * blockDim.x) >> 5;
+    for (u64 base = ((blockIdx.x * (u64)blockDim.x + threadIdx.x) >> 5) * 32; base < nsm; base += nw * 32) {
+        const u64 t = base + lane;
+        u64 o = 0, c = 0;
+        u32 k = 0;
+        if (t < nsm && is_maximal(keys, last, t)) {
+            o = roff[t];
+            c = __ldg(&sm[vals[t]].s);
+            k = (u32)(keys[t] >> SHARE_S_BITS);
+        }
         for (int q = 0; q < 32; ++q) {
-            const u64 hq = __shfl_sync(0xffffffffu, ho, q), cq = __shfl_sync(0xffffffffu, cnt, q);
+            const u64 oq = __shfl_sync(0xffffffffu, o, q), cq = __shfl_sync(0xffffffffu, c, q);
             const u32 kq = __shfl_sync(0xffffffffu, k, q);
-            for (u64 t = lane; t < cq && hq + t < rows_cap; t += 32) rows[hq + t] = kq == NOPOS ? NOPOS : kq + (u32)t;
+            for (u64 u = lane; u < cq && oq + u < rows_cap; u += 32) rows[oq + u] = kq + (u32)u;
+        }
+    }
+}
+
+// hits[hit_off + q] = rpos[roff[o] + (k - k_o) + q] for every sorted record with rows, o being
+// its owner (itself when maximal): one warp per 32 sorted records, copies by the whole warp.
+__global__ void k_share_copy(const mb_smem *__restrict__ sm, const u64 *__restrict__ keys,
+                             const u32 *__restrict__ vals, const u32 *__restrict__ last,
+                             const u64 *__restrict__ roff, u64 cap, const u64 *__restrict__ nsm_dev,
+                             const u32 *__restrict__ rpos, u64 rows_cap, u32 *__restrict__ hits, u64 hits_cap) {
+    const u32 lane = threadIdx.x & 31;
+    const u64 nsm = records_of(cap, nsm_dev);
+    const u64 nw = ((u64)gridDim.x * blockDim.x) >> 5;
+    for (u64 base = ((blockIdx.x * (u64)blockDim.x + threadIdx.x) >> 5) * 32; base < nsm; base += nw * 32) {
+        const u64 t = base + lane;
+        u64 src = 0, dst = 0, c = 0;
+        if (t < nsm && keys[t] != SHARE_NONE) {
+            const u32 r = vals[t], o = last[t];
+            c = __ldg(&sm[r].s);
+            dst = __ldg(&sm[r].hit_off);
+            src = roff[o] + ((keys[t] >> SHARE_S_BITS) - (keys[o] >> SHARE_S_BITS));
+        }
+        for (int q = 0; q < 32; ++q) {
+            const u64 sq = __shfl_sync(0xffffffffu, src, q), dq = __shfl_sync(0xffffffffu, dst, q);
+            const u64 cq = __shfl_sync(0xffffffffu, c, q);
+            for (u64 u = lane; u < cq; u += 32)
+                if (dq + u < hits_cap && sq + u < rows_cap) hits[dq + u] = rpos[sq + u];
         }
     }
 }
@@ -921,6 +1026,50 @@ int launch_locate(const DevIndex &I, const u32 *rows, u64 nhits, const u64 *nhit
     return launch_locate_t<false, true, 1>(I, rows, nhits, nhits_dev, hits, wc, st);
 }
 
+// Device arrays of the shared-walk locate: per record (cap) sort keys and values with their
+// scratch, running maxima, owners, row offsets; per row (rows_cap) the rows and their positions;
+// the row count; scan and sort scratch.
+struct ShareBufs {
+    u64 *keys = nullptr, *keys_alt = nullptr, *roff = nullptr, *nrows = nullptr;
+    u32 *vals = nullptr, *vals_alt = nullptr, *pmax = nullptr, *last = nullptr, *rows = nullptr, *rpos = nullptr;
+    void *tmp = nullptr;
+};
+size_t share_tmp_bytes(u64 cap) {
+    const size_t a = radix_tmp_bytes(cap), b = scan_tmp_bytes(cap);
+    return a > b ? a : b;
+}
+// bytes of the per-record arrays (keys, keys_alt, roff: u64; vals, vals_alt, pmax, last: u32)
+constexpr size_t SHARE_BYTES_PER_RECORD = 3 * 8 + 4 * 4;
+
+// Locate of the records sm[0, nsm), nsm = min(cap, *nsm_dev): every hit of every record without
+// MB_SMEM_OVER_MAX_OCC, written at the record's hit offset (hits_cap bounds every write).  Each
+// distinct row is walked once (see the shared-walk kernels); kt, when given, times the walks.
+int locate_shared(const DevIndex &I, const mb_smem *sm, u64 cap, const u64 *nsm_dev, const u32 *known, u32 *hits,
+                  u64 hits_cap, const ShareBufs &b, u64 *wc, bool count, u32 depth, KTimer *kt, cudaStream_t st) {
+    if (cap == 0) return MB_OK;
+    const unsigned G = grid_for(cap, 256);
+    k_share_keys<<<G, 256, 0, st>>>(sm, cap, nsm_dev, known, hits, hits_cap, b.keys, b.vals);
+    MB_KCHECK();
+    const BitRange r[1] = {{0, SHARE_KEY_BITS}};
+    MB_TRY(radix_sort_pairs(b.keys, b.vals, b.keys_alt, b.vals_alt, cap, r, 1, b.tmp, st, nsm_dev));
+    k_share_ends<<<G, 256, 0, st>>>(sm, b.keys, b.vals, cap, nsm_dev, b.pmax);
+    MB_KCHECK();
+    MB_TRY(scan_inclusive_max_u32(b.pmax, b.pmax, cap, b.tmp, st));
+    k_share_mark<<<G, 256, 0, st>>>(sm, b.keys, b.vals, cap, nsm_dev, b.pmax, b.roff, b.last);
+    MB_KCHECK();
+    MB_TRY(scan_exclusive_u64(b.roff, b.roff, cap, b.nrows, b.tmp, st));
+    MB_TRY(scan_inclusive_max_u32(b.last, b.last, cap, b.tmp, st));
+    k_share_rows<<<G, 256, 0, st>>>(sm, b.keys, b.vals, b.last, b.roff, cap, nsm_dev, b.rows, hits_cap);
+    MB_KCHECK();
+    if (kt) kt->start();
+    MB_TRY(launch_locate(I, b.rows, hits_cap, b.nrows, b.rpos, wc, count, depth, st));
+    if (kt) kt->stop();
+    k_share_copy<<<G, 256, 0, st>>>(sm, b.keys, b.vals, b.last, b.roff, cap, nsm_dev, b.rpos, hits_cap, hits,
+                                    hits_cap);
+    MB_KCHECK();
+    return MB_OK;
+}
+
 // The SMEM kernel in the requested shape: work counters, work queue, threads per block.
 int launch_smem(const SmemArgs &a, bool count, bool queue, int block, cudaStream_t st) {
     if (count) return launch_smem_t<true, false, 256>(a, st);
@@ -1083,18 +1232,30 @@ extern "C" int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_sm
     }
     const DevIndex I = mb_dev_index(idx);
     const bool count = opts && (opts->flags & MB_COUNT);
-    const bool pow2 = (I.r & (I.r - 1)) == 0;
-    DevBuf brows;
-    MB_TRY(brows.alloc(total * 4, st));
-    k_expand_rows<<<grid_for(n_smem, 256), 256, 0, st>>>((const mb_smem *)dsm, n_smem, nullptr, brows.as<u32>(),
-                                                         total);
-    MB_KCHECK();
+    // the shared-walk workspace: per record, per row, scratch
+    DevBuf bw;
+    const size_t rec_bytes = (size_t)n_smem * SHARE_BYTES_PER_RECORD, row_bytes = (size_t)total * 8;
+    MB_TRY(bw.alloc(rec_bytes + row_bytes + 8 + share_tmp_bytes(n_smem) + 12 * 256, st));
+    ShareBufs b;
+    {
+        char *m = (char *)bw.p;
+        auto take = [&](size_t bytes) { void *p = m; m += (bytes + 255) & ~(size_t)255; return p; };
+        b.keys = (u64 *)take(n_smem * 8);
+        b.keys_alt = (u64 *)take(n_smem * 8);
+        b.roff = (u64 *)take(n_smem * 8);
+        b.vals = (u32 *)take(n_smem * 4);
+        b.vals_alt = (u32 *)take(n_smem * 4);
+        b.pmax = (u32 *)take(n_smem * 4);
+        b.last = (u32 *)take(n_smem * 4);
+        b.rows = (u32 *)take(total * 4);
+        b.rpos = (u32 *)take(total * 4);
+        b.nrows = (u64 *)take(8);
+        b.tmp = take(share_tmp_bytes(n_smem));
+    }
     u64 *wc = count ? mb_work_counter_buf(st) : nullptr;
     KTimer kt("locate", st);
-    kt.start();
-    MB_TRY(launch_locate(I, brows.as<u32>(), total, nullptr, dh, wc, count, opts ? opts->prefetch_depth : 0, st));
-    kt.stop();
-    MB_KCHECK();
+    MB_TRY(locate_shared(I, (const mb_smem *)dsm, n_smem, nullptr, nullptr, dh, total, b, wc, count,
+                         opts ? opts->prefetch_depth : 0, &kt, st));
     if (!hdev) MB_CK(cudaMemcpyAsync(hits, dh, total * 4, cudaMemcpyDeviceToHost, st));
     MB_CK(cudaStreamSynchronize(st));
     return MB_OK;
@@ -1296,6 +1457,7 @@ struct mb_plan {
     u64 *counts = nullptr, *soff = nullptr, *misc = nullptr, *hitc = nullptr;
     u32 *ovf = nullptr, *rows = nullptr, *hits = nullptr;
     u32 *known = nullptr;   // per record: the hit position found while seeding, or NOPOS
+    ShareBufs share;        // shared-walk locate: per-record arrays, positions of the walked rows
     mb_smem *out = nullptr;
     u64 *skeys = nullptr, *skeys_alt = nullptr;
     u32 *perm = nullptr, *perm_alt = nullptr;
@@ -1337,11 +1499,14 @@ extern "C" int mb_plan_create(const mb_index *idx, const mb_opts *opts, uint32_t
     P->nslots = slots_total(max_bases, max_reads);
     const size_t nr = max_reads;
     size_t tb = scan_tmp_bytes(nr > P->max_smem ? nr : P->max_smem);
-    const size_t rb = radix_tmp_bytes(nr);
+    const size_t rb = radix_tmp_bytes(nr), sb = share_tmp_bytes(P->max_smem);
     if (rb > tb) tb = rb;
-    size_t sizes[] = {P->nslots * sizeof(SlotRec), nr * 8, nr * 8, 256, P->max_smem * 8, nr * 4, P->max_hits * 4,
-                      P->max_hits * 4, P->max_smem * sizeof(mb_smem), P->queue ? nr * 8 : 0, P->queue ? nr * 8 : 0,
-                      P->queue ? nr * 4 : 0, P->queue ? nr * 4 : 0, tb, P->max_smem * 4};
+    if (sb > tb) tb = sb;
+    const size_t ms = P->max_smem;
+    size_t sizes[] = {P->nslots * sizeof(SlotRec), nr * 8, nr * 8, 256, ms * 8, nr * 4, P->max_hits * 4,
+                      P->max_hits * 4, ms * sizeof(mb_smem), P->queue ? nr * 8 : 0, P->queue ? nr * 8 : 0,
+                      P->queue ? nr * 4 : 0, P->queue ? nr * 4 : 0, tb, ms * 4,
+                      ms * 8, ms * 8, ms * 8, ms * 4, ms * 4, ms * 4, ms * 4, P->max_hits * 4};
     size_t total = 0;
     for (size_t z : sizes) total += align_up(z);
     if (cudaMalloc(&P->mem, total) != cudaSuccess) {
@@ -1355,11 +1520,16 @@ extern "C" int mb_plan_create(const mb_index *idx, const mb_opts *opts, uint32_t
     void **ptrs[] = {(void **)&P->slots, (void **)&P->counts, (void **)&P->soff, (void **)&P->misc, (void **)&P->hitc,
                      (void **)&P->ovf, (void **)&P->rows, (void **)&P->hits, (void **)&P->out, (void **)&P->skeys,
                      (void **)&P->skeys_alt, (void **)&P->perm, (void **)&P->perm_alt, (void **)&P->tmp,
-                     (void **)&P->known};
+                     (void **)&P->known, (void **)&P->share.keys, (void **)&P->share.keys_alt,
+                     (void **)&P->share.roff, (void **)&P->share.vals, (void **)&P->share.vals_alt,
+                     (void **)&P->share.pmax, (void **)&P->share.last, (void **)&P->share.rpos};
     for (size_t i = 0; i < sizeof(sizes) / sizeof(sizes[0]); ++i) {
         *ptrs[i] = sizes[i] ? (void *)m : nullptr;
         m += align_up(sizes[i]);
     }
+    P->share.rows = P->rows;
+    P->share.nrows = P->misc + 4;
+    P->share.tmp = P->tmp;
     *out = P;
     return MB_OK;
 }
@@ -1410,10 +1580,8 @@ extern "C" int mb_plan_run(mb_plan *P, const uint8_t *seq, const uint64_t *off, 
     MB_TRY(scan_exclusive_u64(P->hitc, P->hitc, P->max_smem, n_hits, P->tmp, st));
     k_set_hitoff<<<grid_for(P->max_smem, 256), 256, 0, st>>>(P->hitc, P->max_smem, n_smem, P->out);
     MB_KCHECK();
-    k_expand_rows<<<grid_for(P->max_smem, 256), 256, 0, st>>>(P->out, P->max_smem, n_smem, P->rows, P->max_hits,
-                                                              P->known, P->hits);
-    MB_KCHECK();
-    MB_TRY(launch_locate(I, P->rows, P->max_hits, n_hits, P->hits, nullptr, false, P->depth, st));
+    MB_TRY(locate_shared(I, P->out, P->max_smem, n_smem, P->known, P->hits, P->max_hits, P->share, nullptr, false,
+                         P->depth, nullptr, st));
     return MB_OK;
 }
 

@@ -117,6 +117,58 @@ def test_locate_walks_per_lane(mb, depth):
     compare_seed(sm, hits, X, rd.seq, rd.off)
 
 
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_locate_shared_rows_any_intervals(mb, seed):
+    """Locate walks each distinct row once and copies the position to every hit: records with
+    duplicated, nested, partially overlapping and adjacent intervals, records over max_occ and
+    empty ones, in shuffled order, all get Algorithm 2's positions (the oracle's full suffix
+    array) for every row."""
+    ref, rd, p = synth.workload(2, scale=0.005)
+    G = mb.mb_index_build(ref)
+    X = oracle.Index(ref)
+    S = X.sa()
+    rng = np.random.default_rng(seed)
+    n = X.n
+    recs = []
+    for _ in range(3000):
+        kind = rng.integers(0, 6)
+        k = int(rng.integers(0, n - 1200))          # every row stays below n
+        s = int(rng.integers(1, 400))
+        recs.append((k, s))
+        if kind == 1:                                   # the same interval again
+            recs.append((k, s))
+        elif kind == 2:                                 # nested inside
+            a = int(rng.integers(0, s))
+            recs.append((k + a, int(rng.integers(1, s - a + 1))))
+        elif kind == 3:                                 # overlapping past the end
+            a = int(rng.integers(1, s + 1))
+            recs.append((k + a, s + int(rng.integers(1, 100))))
+        elif kind == 4:                                 # adjacent
+            recs.append((k + s, int(rng.integers(1, 50))))
+        elif kind == 5:                                 # a single row inside
+            recs.append((k + int(rng.integers(0, s)), 1))
+    order = rng.permutation(len(recs))
+    sm = np.zeros(len(recs), dtype=mb.SMEM_DTYPE)
+    sm["k"] = [recs[i][0] for i in order]
+    sm["s"] = [recs[i][1] for i in order]
+    sm["read"] = np.arange(len(recs))
+    over = rng.random(len(recs)) < 0.05
+    sm["flags"][over] = mb.MB_SMEM_OVER_MAX_OCC
+    sm["s"][rng.random(len(recs)) < 0.02] = 0
+    cnt = np.where(over, 0, sm["s"]).astype(np.uint64)
+    sm["hit_off"] = np.concatenate([[0], np.cumsum(cnt)[:-1]])
+    rows = np.concatenate([np.arange(int(k), int(k) + int(c), dtype=np.int64) for k, c in zip(sm["k"], cnt)])
+    assert len(np.unique(rows)) < len(rows)
+    for depth in (1, 16):
+        hits, nh = mb.mb_locate(G, sm, len(sm), opts=dict(prefetch_depth=depth), cap=int(cnt.sum()))
+        assert nh == len(rows)
+        assert np.array_equal(hits.astype(np.int64), S[rows].astype(np.int64))
+    dsm = torch.from_numpy(sm.view(np.uint8)).cuda()
+    out = torch.empty(len(rows), dtype=torch.int32, device="cuda")
+    mb.mb_locate(G, dsm, len(sm), hits=out, cap=len(rows))
+    assert np.array_equal(out.cpu().numpy().view(np.uint32).astype(np.int64), S[rows].astype(np.int64))
+
+
 @pytest.mark.parametrize("k", [12, 14])
 def test_larger_kmer_tables(mb, k):
     """k-mer tables above the paper's k = 10 (12 * 4^k bytes, 3.2 GB at k = 14): sampled entries
@@ -138,7 +190,8 @@ def test_larger_kmer_tables(mb, k):
 def test_work_counters_match_oracle(mb):
     """The counts behind the bench's algorithmic bytes: the GPU's counting kernels (no k-mer
     table, so Algorithm 3 runs step by step as in the oracle) report the same extension steps,
-    blocks read, LF steps and sampled-S reads as the oracle's own counts on the same reads."""
+    blocks read, LF steps and sampled-S reads as the oracle's own counts on the same reads.
+    Locate walks each distinct row once, so its counts are Algorithm 2's over the distinct rows."""
     ref, rd, p = synth.workload(2, scale=0.005)
     G = mb.mb_index_build(ref)
     X = oracle.Index(ref)
@@ -152,7 +205,8 @@ def test_work_counters_match_oracle(mb):
     keep = (sm["flags"] & 1) == 0
     rows = np.concatenate([np.arange(int(k), int(k) + int(s), dtype=np.uint64)
                            for k, s in zip(sm["k"][keep], sm["s"][keep])])
-    assert (wc["lf_steps"], wc["sa_reads"]) == X.count_locate(rows)
+    assert len(np.unique(rows)) < len(rows)   # the repeat-rich reads repeat rows
+    assert (wc["lf_steps"], wc["sa_reads"]) == X.count_locate(np.unique(rows))
 
 
 def test_auxiliary_arrays_and_text_extension(mb):
