@@ -713,9 +713,6 @@ __device__ __forceinline__ u64 owner_of(const mb_smem *__restrict__ sm, u64 nsm,
     return a;
 }
 
-__device__ __forceinline__ u64 hits_of(const mb_smem *__restrict__ sm, u64 m) {
-    return (__ldg(&sm[m].flags) & MB_SMEM_OVER_MAX_OCC) ? 0 : __ldg(&sm[m].s);
-}
 
 // ---------------------------------------------------------------------------- shared walks
 // The records of a batch repeat rows: reads that cover the same repeat give the same or nested SA
@@ -724,73 +721,96 @@ __device__ __forceinline__ u64 hits_of(const mb_smem *__restrict__ sm, u64 m) {
 // each row of the union of the records' intervals once and copies the positions to every hit
 // (Algorithm 2 gives one position per row, so the hits are the same).
 //
-// The records with rows to walk are sorted by (k ascending, s descending).  A record is maximal
-// when its interval ends after every earlier record's; its rows are walked, in sorted order.  Any
-// other record t lies inside the last maximal record before it: the first record that reaches the
-// running maximum of the ends before t is maximal, starts at or before k_t, ends at or after
-// k_t + s_t, and no maximal record can lie between it and t.  This holds for any intervals (the
-// public mb_locate takes records from the caller); nested ones share every repeated row.
+// The records with rows to walk are compacted and sorted by (k ascending, s descending).  A
+// record is maximal when its interval ends after every earlier record's; its rows are walked, in
+// sorted order.  Any other record t lies inside the last maximal record before it: the first
+// record that reaches the running maximum of the ends before t is maximal, starts at or before
+// k_t, ends at or after k_t + s_t, and no maximal record can lie between it and t.  This holds for
+// any intervals (the public mb_locate takes records from the caller); nested ones share every
+// repeated row.
 constexpr int SHARE_S_BITS = 9;                                   // s in the low bits of the sort key
 constexpr int SHARE_KEY_BITS = 32 + SHARE_S_BITS;
-constexpr u64 SHARE_NONE = (1ull << SHARE_KEY_BITS) - 1;          // key of a record with no row to walk
 
-__device__ __forceinline__ u64 records_of(u64 cap, const u64 *nsm_dev) {
-    return nsm_dev && *nsm_dev < cap ? *nsm_dev : cap;
-}
-__device__ __forceinline__ u32 end_of(u64 key, u64 s) {   // k + s, saturated to 32 bits
-    const u64 e = (key >> SHARE_S_BITS) + s;
-    return e < 0xFFFFFFFFull ? (u32)e : 0xFFFFFFFFu;
+__device__ __forceinline__ u64 count_of(u64 cap, const u64 *n_dev) { return n_dev && *n_dev < cap ? *n_dev : cap; }
+__device__ __forceinline__ u64 hits_of(const mb_smem *__restrict__ sm, u64 m) {
+    return (__ldg(&sm[m].flags) & MB_SMEM_OVER_MAX_OCC) ? 0 : __ldg(&sm[m].s);
 }
 
-// Sort keys (k << 9 | 511 - min(s, 511)) and record numbers.  A record with a known position (one
-// hit, found while seeding) writes that hit here and walks nothing.
-__global__ void k_share_keys(const mb_smem *__restrict__ sm, u64 cap, const u64 *__restrict__ nsm_dev,
+// A record walks its rows when it has hits and its position was not found while seeding.
+__device__ __forceinline__ bool walks(u64 cnt, const u32 *known, u64 t) {
+    return cnt && !(known && cnt == 1 && known[t] != NOPOS);
+}
+
+// flag[t] = 1 for a record with rows to walk.  A record with a known position (one hit, found
+// while seeding) writes that hit here and walks nothing.
+__global__ void k_share_flag(const mb_smem *__restrict__ sm, u64 cap, const u64 *__restrict__ nsm_dev,
                              const u32 *__restrict__ known, u32 *__restrict__ hits, u64 hits_cap,
-                             u64 *__restrict__ keys, u32 *__restrict__ vals) {
-    const u64 nsm = records_of(cap, nsm_dev);
-    for (u64 t = blockIdx.x * (u64)blockDim.x + threadIdx.x; t < nsm; t += (u64)gridDim.x * blockDim.x) {
-        const u64 cnt = hits_of(sm, t);
-        u64 key = SHARE_NONE;
-        if (cnt) {
-            const u32 pos = known && cnt == 1 ? known[t] : NOPOS;
-            if (pos != NOPOS) {
+                             u64 *__restrict__ flag) {
+    const u64 nsm = count_of(cap, nsm_dev);
+    for (u64 t = blockIdx.x * (u64)blockDim.x + threadIdx.x; t < cap; t += (u64)gridDim.x * blockDim.x) {
+        u64 f = 0;
+        if (t < nsm) {
+            const u64 cnt = hits_of(sm, t);
+            if (walks(cnt, known, t)) {
+                f = 1;
+            } else if (cnt == 1) {   // known position
                 const u64 ho = __ldg(&sm[t].hit_off);
-                if (ho < hits_cap) hits[ho] = pos;
-            } else {
-                const u64 sb = cnt < (1u << SHARE_S_BITS) ? cnt : (1u << SHARE_S_BITS) - 1;
-                key = ((u64)(u32)__ldg(&sm[t].k) << SHARE_S_BITS) | ((1u << SHARE_S_BITS) - 1 - sb);
+                if (ho < hits_cap) hits[ho] = known[t];
             }
         }
-        keys[t] = key;
-        vals[t] = (u32)t;
+        flag[t] = f;
     }
 }
 
-// ends[t] = k + s of sorted record t (0 past the records and for records with no rows)
-__global__ void k_share_ends(const mb_smem *__restrict__ sm, const u64 *__restrict__ keys,
-                             const u32 *__restrict__ vals, u64 cap, const u64 *__restrict__ nsm_dev,
-                             u32 *__restrict__ ends) {
-    const u64 nsm = records_of(cap, nsm_dev);
+// The flagged records (see k_share_flag) at their scanned places `at`: sort key
+// (k << 9 | 511 - min(s, 511)) and record number.
+__global__ void k_share_compact(const mb_smem *__restrict__ sm, u64 cap, const u64 *__restrict__ nsm_dev,
+                                const u32 *__restrict__ known, const u64 *__restrict__ at, u64 *__restrict__ keys,
+                                u32 *__restrict__ vals) {
+    const u64 nsm = count_of(cap, nsm_dev);
+    for (u64 t = blockIdx.x * (u64)blockDim.x + threadIdx.x; t < nsm; t += (u64)gridDim.x * blockDim.x) {
+        const u64 cnt = hits_of(sm, t);
+        if (!walks(cnt, known, t)) continue;
+        const u64 sb = cnt < (1u << SHARE_S_BITS) ? cnt : (1u << SHARE_S_BITS) - 1;
+        keys[at[t]] = ((u64)(u32)__ldg(&sm[t].k) << SHARE_S_BITS) | ((1u << SHARE_S_BITS) - 1 - sb);
+        vals[at[t]] = (u32)t;
+    }
+}
+
+// For sorted record t < nw: its s and hit offset in sorted order, and ends[t] = k + s (saturated
+// to 32 bits); ends = 0 past the records.
+__global__ void k_share_gather(const mb_smem *__restrict__ sm, const u64 *__restrict__ keys,
+                               const u32 *__restrict__ vals, u64 cap, const u64 *__restrict__ nw_dev,
+                               u32 *__restrict__ ss, u64 *__restrict__ sho, u32 *__restrict__ ends) {
+    const u64 nw = count_of(cap, nw_dev);
     for (u64 t = blockIdx.x * (u64)blockDim.x + threadIdx.x; t < cap; t += (u64)gridDim.x * blockDim.x) {
         u32 e = 0;
-        if (t < nsm && keys[t] != SHARE_NONE) e = end_of(keys[t], __ldg(&sm[vals[t]].s));
+        if (t < nw) {
+            const u32 r = vals[t];
+            const u64 s = __ldg(&sm[r].s);
+            const u64 end = (keys[t] >> SHARE_S_BITS) + s;
+            ss[t] = (u32)s;
+            sho[t] = __ldg(&sm[r].hit_off);
+            e = end < 0xFFFFFFFFull ? (u32)end : 0xFFFFFFFFu;
+        }
         ends[t] = e;
     }
 }
 
 // With pmax = the running maximum of the ends: len[t] = s of a maximal record (else 0) and
 // last[t] = t for a maximal record (else 0), to be scanned into row offsets and owners.
-__global__ void k_share_mark(const mb_smem *__restrict__ sm, const u64 *__restrict__ keys,
-                             const u32 *__restrict__ vals, u64 cap, const u64 *__restrict__ nsm_dev,
-                             const u32 *__restrict__ pmax, u64 *__restrict__ len, u32 *__restrict__ last) {
-    const u64 nsm = records_of(cap, nsm_dev);
+__global__ void k_share_mark(const u64 *__restrict__ keys, const u32 *__restrict__ ss, u64 cap,
+                             const u64 *__restrict__ nw_dev, const u32 *__restrict__ pmax, u64 *__restrict__ len,
+                             u32 *__restrict__ last) {
+    const u64 nw = count_of(cap, nw_dev);
     for (u64 t = blockIdx.x * (u64)blockDim.x + threadIdx.x; t < cap; t += (u64)gridDim.x * blockDim.x) {
         u64 l = 0;
         u32 lm = 0;
-        if (t < nsm && keys[t] != SHARE_NONE) {
-            const u64 s = __ldg(&sm[vals[t]].s);
-            if (end_of(keys[t], s) > (t ? pmax[t - 1] : 0u)) {
-                l = s;
+        if (t < nw) {
+            const u64 end = (keys[t] >> SHARE_S_BITS) + ss[t];
+            const u32 e = end < 0xFFFFFFFFull ? (u32)end : 0xFFFFFFFFu;
+            if (t == 0 || e > pmax[t - 1]) {   // pmax[t - 1] >= 1 here, so the first record is maximal
+                l = ss[t];
                 lm = (u32)t;
             }
         }
@@ -799,26 +819,21 @@ __global__ void k_share_mark(const mb_smem *__restrict__ sm, const u64 *__restri
     }
 }
 
-__device__ __forceinline__ bool is_maximal(const u64 *keys, const u32 *last, u64 t) {
-    return keys[t] != SHARE_NONE && last[t] == (u32)t;   // the first record with rows is maximal
-}
-
-// rows[roff[t] + q] = k + q for every maximal sorted record t: one warp per 32 sorted records,
-// each record's rows written by the whole warp.
-__global__ void k_share_rows(const mb_smem *__restrict__ sm, const u64 *__restrict__ keys,
-                             const u32 *__restrict__ vals, const u32 *__restrict__ last,
-                             const u64 *__restrict__ roff, u64 cap, const u64 *__restrict__ nsm_dev,
+// rows[roff[t] + q] = k + q for every maximal sorted record t (last[t] == t): one warp per 32
+// sorted records, each record's rows written by the whole warp.
+__global__ void k_share_rows(const u64 *__restrict__ keys, const u32 *__restrict__ ss, const u32 *__restrict__ last,
+                             const u64 *__restrict__ roff, u64 cap, const u64 *__restrict__ nw_dev,
                              u32 *__restrict__ rows, u64 rows_cap) {
     const u32 lane = threadIdx.x & 31;
-    const u64 nsm = records_of(cap, nsm_dev);
-    const u64 nw = ((u64)gridDim.x * blockDim.x) >> 5;
-    for (u64 base = ((blockIdx.x * (u64)blockDim.x + threadIdx.x) >> 5) * 32; base < nsm; base += nw * 32) {
+    const u64 nw = count_of(cap, nw_dev);
+    const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
+    for (u64 base = ((blockIdx.x * (u64)blockDim.x + threadIdx.x) >> 5) * 32; base < nw; base += nwarps * 32) {
         const u64 t = base + lane;
         u64 o = 0, c = 0;
         u32 k = 0;
-        if (t < nsm && is_maximal(keys, last, t)) {
+        if (t < nw && last[t] == (u32)t) {
             o = roff[t];
-            c = __ldg(&sm[vals[t]].s);
+            c = ss[t];
             k = (u32)(keys[t] >> SHARE_S_BITS);
         }
         for (int q = 0; q < 32; ++q) {
@@ -829,22 +844,22 @@ __global__ void k_share_rows(const mb_smem *__restrict__ sm, const u64 *__restri
     }
 }
 
-// hits[hit_off + q] = rpos[roff[o] + (k - k_o) + q] for every sorted record with rows, o being
+// hits[hit_off + q] = rpos[roff[o] + (k - k_o) + q] for every sorted record, o = last[t] being
 // its owner (itself when maximal): one warp per 32 sorted records, copies by the whole warp.
-__global__ void k_share_copy(const mb_smem *__restrict__ sm, const u64 *__restrict__ keys,
-                             const u32 *__restrict__ vals, const u32 *__restrict__ last,
-                             const u64 *__restrict__ roff, u64 cap, const u64 *__restrict__ nsm_dev,
-                             const u32 *__restrict__ rpos, u64 rows_cap, u32 *__restrict__ hits, u64 hits_cap) {
+__global__ void k_share_copy(const u64 *__restrict__ keys, const u32 *__restrict__ ss, const u64 *__restrict__ sho,
+                             const u32 *__restrict__ last, const u64 *__restrict__ roff, u64 cap,
+                             const u64 *__restrict__ nw_dev, const u32 *__restrict__ rpos, u64 rows_cap,
+                             u32 *__restrict__ hits, u64 hits_cap) {
     const u32 lane = threadIdx.x & 31;
-    const u64 nsm = records_of(cap, nsm_dev);
-    const u64 nw = ((u64)gridDim.x * blockDim.x) >> 5;
-    for (u64 base = ((blockIdx.x * (u64)blockDim.x + threadIdx.x) >> 5) * 32; base < nsm; base += nw * 32) {
+    const u64 nw = count_of(cap, nw_dev);
+    const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
+    for (u64 base = ((blockIdx.x * (u64)blockDim.x + threadIdx.x) >> 5) * 32; base < nw; base += nwarps * 32) {
         const u64 t = base + lane;
         u64 src = 0, dst = 0, c = 0;
-        if (t < nsm && keys[t] != SHARE_NONE) {
-            const u32 r = vals[t], o = last[t];
-            c = __ldg(&sm[r].s);
-            dst = __ldg(&sm[r].hit_off);
+        if (t < nw) {
+            const u32 o = last[t];
+            c = ss[t];
+            dst = sho[t];
             src = roff[o] + ((keys[t] >> SHARE_S_BITS) - (keys[o] >> SHARE_S_BITS));
         }
         for (int q = 0; q < 32; ++q) {
@@ -1027,10 +1042,11 @@ int launch_locate(const DevIndex &I, const u32 *rows, u64 nhits, const u64 *nhit
 }
 
 // Device arrays of the shared-walk locate: per record (cap) sort keys and values with their
-// scratch, running maxima, owners, row offsets; per row (rows_cap) the rows and their positions;
-// the row count; scan and sort scratch.
+// scratch (which then hold the sorted records' s and hit offsets), running maxima of the ends,
+// owners, row offsets; per row (rows_cap) the rows and their positions; the counts of records
+// that walk and of rows; scan and sort scratch.
 struct ShareBufs {
-    u64 *keys = nullptr, *keys_alt = nullptr, *roff = nullptr, *nrows = nullptr;
+    u64 *keys = nullptr, *keys_alt = nullptr, *roff = nullptr, *nwalk = nullptr, *nrows = nullptr;
     u32 *vals = nullptr, *vals_alt = nullptr, *pmax = nullptr, *last = nullptr, *rows = nullptr, *rpos = nullptr;
     void *tmp = nullptr;
 };
@@ -1048,24 +1064,28 @@ int locate_shared(const DevIndex &I, const mb_smem *sm, u64 cap, const u64 *nsm_
                   u64 hits_cap, const ShareBufs &b, u64 *wc, bool count, u32 depth, KTimer *kt, cudaStream_t st) {
     if (cap == 0) return MB_OK;
     const unsigned G = grid_for(cap, 256);
-    k_share_keys<<<G, 256, 0, st>>>(sm, cap, nsm_dev, known, hits, hits_cap, b.keys, b.vals);
+    k_share_flag<<<G, 256, 0, st>>>(sm, cap, nsm_dev, known, hits, hits_cap, b.roff);
+    MB_KCHECK();
+    MB_TRY(scan_exclusive_u64(b.roff, b.roff, cap, b.nwalk, b.tmp, st));
+    k_share_compact<<<G, 256, 0, st>>>(sm, cap, nsm_dev, known, b.roff, b.keys, b.vals);
     MB_KCHECK();
     const BitRange r[1] = {{0, SHARE_KEY_BITS}};
-    MB_TRY(radix_sort_pairs(b.keys, b.vals, b.keys_alt, b.vals_alt, cap, r, 1, b.tmp, st, nsm_dev));
-    k_share_ends<<<G, 256, 0, st>>>(sm, b.keys, b.vals, cap, nsm_dev, b.pmax);
+    MB_TRY(radix_sort_pairs(b.keys, b.vals, b.keys_alt, b.vals_alt, cap, r, 1, b.tmp, st, b.nwalk));
+    u32 *ss = b.vals_alt;   // the sort's scratch, free again
+    u64 *sho = b.keys_alt;
+    k_share_gather<<<G, 256, 0, st>>>(sm, b.keys, b.vals, cap, b.nwalk, ss, sho, b.pmax);
     MB_KCHECK();
     MB_TRY(scan_inclusive_max_u32(b.pmax, b.pmax, cap, b.tmp, st));
-    k_share_mark<<<G, 256, 0, st>>>(sm, b.keys, b.vals, cap, nsm_dev, b.pmax, b.roff, b.last);
+    k_share_mark<<<G, 256, 0, st>>>(b.keys, ss, cap, b.nwalk, b.pmax, b.roff, b.last);
     MB_KCHECK();
     MB_TRY(scan_exclusive_u64(b.roff, b.roff, cap, b.nrows, b.tmp, st));
     MB_TRY(scan_inclusive_max_u32(b.last, b.last, cap, b.tmp, st));
-    k_share_rows<<<G, 256, 0, st>>>(sm, b.keys, b.vals, b.last, b.roff, cap, nsm_dev, b.rows, hits_cap);
+    k_share_rows<<<G, 256, 0, st>>>(b.keys, ss, b.last, b.roff, cap, b.nwalk, b.rows, hits_cap);
     MB_KCHECK();
     if (kt) kt->start();
     MB_TRY(launch_locate(I, b.rows, hits_cap, b.nrows, b.rpos, wc, count, depth, st));
     if (kt) kt->stop();
-    k_share_copy<<<G, 256, 0, st>>>(sm, b.keys, b.vals, b.last, b.roff, cap, nsm_dev, b.rpos, hits_cap, hits,
-                                    hits_cap);
+    k_share_copy<<<G, 256, 0, st>>>(b.keys, ss, sho, b.last, b.roff, cap, b.nwalk, b.rpos, hits_cap, hits, hits_cap);
     MB_KCHECK();
     return MB_OK;
 }
@@ -1235,7 +1255,7 @@ extern "C" int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_sm
     // the shared-walk workspace: per record, per row, scratch
     DevBuf bw;
     const size_t rec_bytes = (size_t)n_smem * SHARE_BYTES_PER_RECORD, row_bytes = (size_t)total * 8;
-    MB_TRY(bw.alloc(rec_bytes + row_bytes + 8 + share_tmp_bytes(n_smem) + 12 * 256, st));
+    MB_TRY(bw.alloc(rec_bytes + row_bytes + 16 + share_tmp_bytes(n_smem) + 13 * 256, st));
     ShareBufs b;
     {
         char *m = (char *)bw.p;
@@ -1250,6 +1270,7 @@ extern "C" int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_sm
         b.rows = (u32 *)take(total * 4);
         b.rpos = (u32 *)take(total * 4);
         b.nrows = (u64 *)take(8);
+        b.nwalk = (u64 *)take(8);
         b.tmp = take(share_tmp_bytes(n_smem));
     }
     u64 *wc = count ? mb_work_counter_buf(st) : nullptr;
@@ -1529,6 +1550,7 @@ extern "C" int mb_plan_create(const mb_index *idx, const mb_opts *opts, uint32_t
     }
     P->share.rows = P->rows;
     P->share.nrows = P->misc + 4;
+    P->share.nwalk = P->misc + 5;
     P->share.tmp = P->tmp;
     *out = P;
     return MB_OK;
