@@ -693,7 +693,7 @@ def run_gpu(args):
         e2e = {"value": ws * k2 * n_reads / dt, "unit": "reads/s",
                "h2d_bytes_per_step": int(seq_h.numel() + off_h.numel() * 8),
                "d2h_bytes_per_step": int(m * 48 + nh * 4),
-               "call": "mb_seed_locate (pinned host buffers, 4M-read chunks on two streams)",
+               "call": "mb_seed_locate (pinned host buffers, 4M-read chunks seeded on two streams, the batch located at once)",
                "two_calls_reads_per_s": ws * k2 * n_reads / dt2,
                "note": "two_calls = mb_seed_batch + mb_locate on host buffers (the records are staged back in)"}
         log(f"e2e: {e2e}")

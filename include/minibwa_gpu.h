@@ -204,10 +204,12 @@ int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_smem, const m
 /* ---------------------------------------------------------------------------------------
  * mb_seed_locate — the whole stage in one call: SMEMs as mb_seed_batch, then their hits as
  * mb_locate (Section 2.5, Algorithm 3; Section 2.3, Algorithm 2), for callers whose reads and
- * results live in host memory.  The batch is cut into chunks of consecutive reads
- * (opts->chunk_reads reads, at most 2^29 bases, at least one read) that alternate between two
- * internal streams, so that the copies of one chunk overlap the kernels of the other; use
- * pinned host buffers for the copies to overlap.
+ * results live in host memory.  The batch is cut into slices (at most 2^25 reads and 2^33
+ * bases) and a slice into chunks of consecutive reads (opts->chunk_reads reads, at most 2^29
+ * bases, at least one read) that alternate between two internal streams, so that the copies of
+ * one chunk overlap the seeding of the other; each slice is then located at once (its repeated
+ * rows walked once) while its records are copied out.  Use pinned host buffers for the copies
+ * to overlap.
  *   seq, off, mate   host or device, as for mb_seed_batch.
  *   out              host or device, room for `cap` records: the records of mb_seed_batch (read
  *                    numbers and hit_off relative to this batch).

@@ -260,6 +260,14 @@ int radix_sort_pairs(u64 *keys, u32 *vals, u64 *keys_alt, u32 *vals_alt, size_t 
 size_t mb_plan_bytes(const mb_plan *p);
 int mb_plan_counts_async(mb_plan *p, u64 *host_counts, cudaStream_t st);
 void mb_plan_arrays(const mb_plan *p, const mb_smem **smem, const u32 **hits, u64 *max_smem, u64 *max_hits);
+// seeding of a plan's batch without the locate (records with hit offsets), the plan's per-record
+// known positions (NOPOS where seeding did not find one), and the locate of device records with
+// such positions (hits at the records' offsets; every distinct row walked once)
+int mb_plan_run_seed(mb_plan *p, const uint8_t *seq, const uint64_t *off, uint32_t n_reads, const uint8_t *mate,
+                     cudaStream_t st);
+const u32 *mb_plan_known(const mb_plan *p);
+int mb_locate_records(const mb_index *idx, const mb_smem *sm, u64 n_smem, const u32 *known, u32 *hits, u64 n_hits,
+                      u32 depth, cudaStream_t st);
 // build flags of an index (MB_BS3 for the 3-base bisulfite index)
 u32 mb_index_flags(const mb_index *x);
 // drops the host-buffer pipelines kept for an index (called when the index is freed)

@@ -1,15 +1,19 @@
 // Whole seeding stage with host (or device) buffers in one call: mb_seed_locate.
 //
-// The batch is cut into chunks of consecutive reads that alternate between two streams.  Each
-// stream owns a seeding plan (no host synchronization inside, see mb_plan_run) and device copies
-// of its chunk's inputs, so while one stream copies a chunk in, seeds it (Algorithm 3, the
-// max-occ flag, Algorithm 2) and copies its records and hits out, the other stream's chunk is on
-// the GPU.  Read numbers and hit offsets of a chunk are made global by a small kernel before the
-// copy out, so the call returns exactly what mb_seed_batch followed by mb_locate return.
+// The batch is cut into slices of at most 2^25 reads and 2^33 bases, and a slice into chunks of
+// consecutive reads that alternate between two streams.  Each stream owns a seeding plan (no host
+// synchronization inside) and device copies of its chunk's inputs, so while one stream copies a
+// chunk in and seeds it (Algorithm 3 and the max-occ flag, up to the records and their hit
+// offsets), the other stream's chunk is on the GPU.  A chunk's records, with read numbers and hit
+// offsets made slice-wide by a small kernel, and the positions found while seeding are gathered
+// in device arrays of the slice; then the slice is located at once (Algorithm 2, every distinct
+// row walked once, so the repeats of the whole slice share their walks) while its records are
+// copied out on the other stream, and its hits are copied out last.  The call returns exactly
+// what mb_seed_batch followed by mb_locate return.
 //
 // The streams, plans and staging buffers of a call are kept for the next call with the same index,
 // device and seeding options whose chunks fit them (at most two sets are kept; they are released
-// with the index), so steady-state calls allocate nothing.
+// with the index).
 #include <algorithm>
 #include <memory>
 #include <mutex>
@@ -20,6 +24,8 @@ namespace {
 
 constexpr u32 PIPE_READS = 1u << 22;      // default reads per chunk
 constexpr u64 PIPE_BASES = 1ull << 29;    // at most this many bases per chunk (at least one read)
+constexpr u32 SLICE_READS = 1u << 25;     // at most this many reads per slice (located at once)
+constexpr u64 SLICE_BASES = 1ull << 33;   // and this many bases (at least one chunk)
 constexpr int PIPE_STAGES = 2;
 
 // records of one chunk in batch coordinates: read number and first hit
@@ -33,6 +39,10 @@ __global__ void k_rebase(mb_smem *__restrict__ s, u64 n, u32 r0, u64 h0) {
 struct Chunk {
     u32 r0 = 0, nr = 0;
     u64 o0 = 0, o1 = 0;
+};
+struct Slice {
+    int c0 = 0, c1 = 0;   // its chunks [c0, c1)
+    u64 cap = 0;          // records its chunks' plans hold
 };
 
 struct Stage {
@@ -170,7 +180,25 @@ extern "C" int mb_seed_locate(const mb_index *idx, const uint8_t *seq, const uin
         r = e;
     }
 
-    // per-stage resources, sized for the largest chunk (a kept set when one fits)
+    // slices: consecutive chunks up to SLICE_READS reads and SLICE_BASES bases
+    std::vector<Slice> slices;
+    for (int i = 0; i < (int)chunks.size();) {
+        Slice sl;
+        sl.c0 = i;
+        u64 nr = 0, nb = 0;
+        while (i < (int)chunks.size() && (i == sl.c0 || (nr + chunks[i].nr <= SLICE_READS &&
+                                                         nb + (chunks[i].o1 - chunks[i].o0) <= SLICE_BASES))) {
+            nr += chunks[i].nr;
+            nb += chunks[i].o1 - chunks[i].o0;
+            sl.cap += 4ull * chunks[i].nr + (chunks[i].o1 - chunks[i].o0) / 32 + 64;
+            ++i;
+        }
+        sl.c1 = i;
+        slices.push_back(sl);
+    }
+
+    // per-stage resources, sized for the largest chunk (a kept set when one fits); the plans only
+    // seed, so they hold no hits
     int device = 0;
     MB_CK(cudaGetDevice(&device));
     const mb_opts o = opts ? *opts : mb_opts{};
@@ -188,95 +216,155 @@ extern "C" int mb_seed_locate(const mb_index *idx, const uint8_t *seq, const uin
         p.own_off = !off_dev;
         p.own_mate = mate && !mate_dev;
         const u64 max_smem = 4ull * max_nr + max_nb / 32 + 64;
-        const u64 max_hits = 4ull * max_smem;
         MB_CK(cudaEventCreateWithFlags(&p.start, cudaEventDisableTiming));
         for (Stage &x : p.s) {
             MB_CK(cudaStreamCreateWithFlags(&x.st, cudaStreamNonBlocking));
             MB_CK(cudaEventCreateWithFlags(&x.ev, cudaEventDisableTiming));
             MB_CK(cudaMallocHost(&x.hcnt, 16));
-            MB_TRY(mb_plan_create(idx, opts, max_nr, max_nb, max_smem, max_hits, &x.plan));
+            MB_TRY(mb_plan_create(idx, opts, max_nr, max_nb, max_smem, 1, &x.plan));
             if (p.own_seq) MB_CK(cudaMalloc(&x.dseq, max_nb + 16));
             if (p.own_off) MB_CK(cudaMalloc(&x.doff, ((size_t)max_nr + 1) * 8));
             if (p.own_mate) MB_CK(cudaMalloc(&x.dmate, max_nr));
         }
     }
     Pipeline &pl = *keep;
-    MB_CK(cudaEventRecord(pl.start, ust));
-    for (Stage &x : pl.s) MB_CK(cudaStreamWaitEvent(x.st, pl.start, 0));   // after the caller's earlier work
+    Stage &A = pl.s[0], &B = pl.s[1];
+    const bool out_dev = out && mb_is_device_ptr(out), hits_dev = hits && mb_is_device_ptr(hits);
+    const u32 depth = opts ? opts->prefetch_depth : 0;
 
-    // inputs of chunk i in, then its whole stage, then its two counts to the host
-    auto enqueue = [&](int i, Stage &x) -> int {
+    // device inputs of chunk i (the caller's, or the stage's copies)
+    auto inputs = [&](int i, const Stage &x, const u8 *&dseq, const u64 *&doff, const u8 *&dmate) {
         const Chunk &c = chunks[i];
-        const u8 *dseq = seq;
-        const u64 *doff = off + c.r0;
-        const u8 *dmate = mate ? mate + c.r0 : nullptr;
-        if (!seq_dev) {
-            if (c.o1 > c.o0) MB_CK(cudaMemcpyAsync(x.dseq, seq + c.o0, c.o1 - c.o0, cudaMemcpyHostToDevice, x.st));
-            dseq = x.dseq - c.o0;   // read r of the chunk starts at dseq + off[r], as in the caller's buffer
-        }
-        if (!off_dev) {
-            MB_CK(cudaMemcpyAsync(x.doff, off + c.r0, ((size_t)c.nr + 1) * 8, cudaMemcpyHostToDevice, x.st));
-            doff = x.doff;
-        }
-        if (mate && !mate_dev) {
-            MB_CK(cudaMemcpyAsync(x.dmate, mate + c.r0, c.nr, cudaMemcpyHostToDevice, x.st));
-            dmate = x.dmate;
-        }
-        MB_TRY(mb_plan_run(x.plan, dseq, doff, c.nr, dmate, x.st));
-        MB_TRY(mb_plan_counts_async(x.plan, x.hcnt, x.st));
-        MB_CK(cudaEventRecord(x.ev, x.st));
-        x.chunk = i;
-        return MB_OK;
+        dseq = seq_dev ? seq : x.dseq - c.o0;   // read r of the chunk starts at dseq + off[r]
+        doff = off_dev ? off + c.r0 : x.doff;
+        dmate = mate ? (mate_dev ? mate + c.r0 : x.dmate) : nullptr;
     };
 
-    u64 m_tot = 0, h_tot = 0;
+    u64 m_tot = 0, h_tot = 0;   // over the whole batch
     bool over = false;
-    // chunk i's counts are on the host: its records and hits out (no wait on the copies)
-    auto drain = [&](Stage &x) -> int {
-        const Chunk &c = chunks[x.chunk];
-        MB_CK(cudaEventSynchronize(x.ev));
-        u64 ns = x.hcnt[0], nh = x.hcnt[1];
-        const mb_smem *psm;
-        const u32 *ph;
-        u64 ms, mh;
-        mb_plan_arrays(x.plan, &psm, &ph, &ms, &mh);
-        DevBuf fsm, fh;
-        if (ns > ms || nh > mh) {
-            // the chunk outgrew the plan: the allocating path on the chunk's device inputs
-            const u8 *dseq = seq_dev ? seq : x.dseq - c.o0;
-            const u64 *doff = off_dev ? off + c.r0 : x.doff;
-            const u8 *dmate = mate ? (mate_dev ? mate + c.r0 : x.dmate) : nullptr;
-            u64 h = 0;
-            MB_TRY(fsm.alloc(ns * sizeof(mb_smem) + 64, x.st));
-            MB_TRY(mb_seed_batch(idx, dseq, doff, c.nr, dmate, opts, x.st, fsm.as<mb_smem>(), ns, &ns, &h));
-            MB_TRY(fh.alloc(h * 4 + 64, x.st));
-            MB_TRY(mb_locate(idx, fsm.as<mb_smem>(), ns, opts, x.st, fh.as<u32>(), h, &nh));
-            psm = fsm.as<mb_smem>();
-            ph = fh.as<u32>();
-        }
-        if (!over && (m_tot + ns > cap || h_tot + nh > hits_cap || (ns && !out) || (nh && !hits))) over = true;
-        if (!over) {
-            if (ns) {
-                k_rebase<<<grid_for(ns, 256), 256, 0, x.st>>>((mb_smem *)psm, ns, c.r0, h_tot);
-                MB_KCHECK();
-                MB_CK(cudaMemcpyAsync(out + m_tot, psm, ns * sizeof(mb_smem), cudaMemcpyDefault, x.st));
-            }
-            if (nh) MB_CK(cudaMemcpyAsync(hits + h_tot, ph, nh * 4, cudaMemcpyDefault, x.st));
-        }
-        m_tot += ns;
-        h_tot += nh;
-        x.chunk = -1;
-        return MB_OK;   // a fallback's buffers are freed in stream order after the copies
-    };
+    for (const Slice &sl : slices) {
+        // the slice's records and known positions, gathered on the device
+        DevBuf gsm, gknown;
+        u64 gcap = sl.cap;
+        MB_TRY(gsm.alloc(gcap * sizeof(mb_smem), ust));
+        MB_TRY(gknown.alloc(gcap * 4, ust));
+        MB_CK(cudaEventRecord(pl.start, ust));
+        for (Stage &x : pl.s) MB_CK(cudaStreamWaitEvent(x.st, pl.start, 0));   // after the caller's work and the allocations
 
-    const int nc = (int)chunks.size();
-    for (int i = 0; i < nc && i < PIPE_STAGES; ++i) MB_TRY(enqueue(i, pl.s[i]));
-    for (int i = 0; i < nc; ++i) {
-        Stage &x = pl.s[i % PIPE_STAGES];
-        MB_TRY(drain(x));
-        if (i + PIPE_STAGES < nc) MB_TRY(enqueue(i + PIPE_STAGES, x));
+        // inputs of chunk i in, then its seeding, then its two counts to the host
+        auto enqueue = [&](int i, Stage &x) -> int {
+            const Chunk &c = chunks[i];
+            if (!seq_dev && c.o1 > c.o0)
+                MB_CK(cudaMemcpyAsync(x.dseq, seq + c.o0, c.o1 - c.o0, cudaMemcpyHostToDevice, x.st));
+            if (!off_dev)
+                MB_CK(cudaMemcpyAsync(x.doff, off + c.r0, ((size_t)c.nr + 1) * 8, cudaMemcpyHostToDevice, x.st));
+            if (mate && !mate_dev) MB_CK(cudaMemcpyAsync(x.dmate, mate + c.r0, c.nr, cudaMemcpyHostToDevice, x.st));
+            const u8 *dseq, *dmate;
+            const u64 *doff;
+            inputs(i, x, dseq, doff, dmate);
+            MB_TRY(mb_plan_run_seed(x.plan, dseq, doff, c.nr, dmate, x.st));
+            MB_TRY(mb_plan_counts_async(x.plan, x.hcnt, x.st));
+            MB_CK(cudaEventRecord(x.ev, x.st));
+            x.chunk = i;
+            return MB_OK;
+        };
+
+        u64 ms_tot = 0, hs_tot = 0;   // within the slice
+        // chunk i's counts are on the host: its records, slice-wide, and known positions gathered
+        auto drain = [&](Stage &x) -> int {
+            const Chunk &c = chunks[x.chunk];
+            MB_CK(cudaEventSynchronize(x.ev));
+            u64 ns = x.hcnt[0], nh = x.hcnt[1];
+            const mb_smem *psm;
+            const u32 *ph;
+            u64 ms, mh;
+            mb_plan_arrays(x.plan, &psm, &ph, &ms, &mh);
+            const u32 *pknown = mb_plan_known(x.plan);
+            DevBuf fsm;
+            if (ns > ms) {
+                // the chunk outgrew the plan: the allocating path on the chunk's device inputs (no
+                // positions known from seeding)
+                const u8 *dseq, *dmate;
+                const u64 *doff;
+                inputs(x.chunk, x, dseq, doff, dmate);
+                MB_TRY(fsm.alloc(ns * sizeof(mb_smem) + 64, x.st));
+                MB_TRY(mb_seed_batch(idx, dseq, doff, c.nr, dmate, opts, x.st, fsm.as<mb_smem>(), ns, &ns, &nh));
+                psm = fsm.as<mb_smem>();
+                pknown = nullptr;
+            }
+            if (ms_tot + ns > gcap) {   // only after the allocating path: grow the slice's arrays
+                for (Stage &y : pl.s) MB_CK(cudaStreamSynchronize(y.st));
+                const u64 ncap = 2 * (ms_tot + ns);
+                DevBuf nsm, nkn;
+                MB_TRY(nsm.alloc(ncap * sizeof(mb_smem), x.st));
+                MB_TRY(nkn.alloc(ncap * 4, x.st));
+                if (ms_tot) {
+                    MB_CK(cudaMemcpyAsync(nsm.p, gsm.p, ms_tot * sizeof(mb_smem), cudaMemcpyDeviceToDevice, x.st));
+                    MB_CK(cudaMemcpyAsync(nkn.p, gknown.p, ms_tot * 4, cudaMemcpyDeviceToDevice, x.st));
+                }
+                MB_CK(cudaStreamSynchronize(x.st));
+                std::swap(gsm.p, nsm.p);
+                std::swap(gsm.bytes, nsm.bytes);
+                std::swap(gsm.st, nsm.st);
+                std::swap(gknown.p, nkn.p);
+                std::swap(gknown.bytes, nkn.bytes);
+                std::swap(gknown.st, nkn.st);
+                gcap = ncap;
+            }
+            if (ns) {
+                k_rebase<<<grid_for(ns, 256), 256, 0, x.st>>>((mb_smem *)psm, ns, c.r0, hs_tot);
+                MB_KCHECK();
+                MB_CK(cudaMemcpyAsync(gsm.as<mb_smem>() + ms_tot, psm, ns * sizeof(mb_smem), cudaMemcpyDeviceToDevice,
+                                      x.st));
+                if (pknown) MB_CK(cudaMemcpyAsync(gknown.as<u32>() + ms_tot, pknown, ns * 4, cudaMemcpyDeviceToDevice, x.st));
+                else MB_CK(cudaMemsetAsync(gknown.as<u32>() + ms_tot, 0xFF, ns * 4, x.st));
+            }
+            ms_tot += ns;
+            hs_tot += nh;
+            x.chunk = -1;
+            return MB_OK;   // a fallback's buffer is freed in stream order after the copy
+        };
+
+        const int nc = sl.c1 - sl.c0;
+        for (int i = 0; i < nc && i < PIPE_STAGES; ++i) MB_TRY(enqueue(sl.c0 + i, pl.s[i]));
+        for (int i = 0; i < nc; ++i) {
+            Stage &x = pl.s[i % PIPE_STAGES];
+            MB_TRY(drain(x));
+            if (i + PIPE_STAGES < nc) MB_TRY(enqueue(sl.c0 + i + PIPE_STAGES, x));
+        }
+        for (Stage &x : pl.s) MB_CK(cudaStreamSynchronize(x.st));
+
+        // locate the slice at once (stream A) while its records go out (stream B), hits last
+        if (!over && (m_tot + ms_tot > cap || h_tot + hs_tot > hits_cap || (ms_tot && !out) || (hs_tot && !hits)))
+            over = true;
+        if (!over && ms_tot) {
+            DevBuf dh;
+            u32 *dhits = hits_dev ? hits + h_tot : nullptr;
+            if (!hits_dev && hs_tot) {
+                MB_TRY(dh.alloc(hs_tot * 4, A.st));
+                dhits = dh.as<u32>();
+            }
+            if (h_tot == 0)   // hit offsets are already batch-wide: copy the records out now
+                MB_CK(cudaMemcpyAsync(out + m_tot, gsm.p, ms_tot * sizeof(mb_smem), cudaMemcpyDefault, B.st));
+            MB_TRY(mb_locate_records(idx, gsm.as<mb_smem>(), ms_tot, gknown.as<u32>(), dhits, hs_tot, depth, A.st));
+            if (h_tot) {      // later slices: batch-wide hit offsets after the locate
+                k_rebase<<<grid_for(ms_tot, 256), 256, 0, A.st>>>(gsm.as<mb_smem>(), ms_tot, 0, h_tot);
+                MB_KCHECK();
+                MB_CK(cudaMemcpyAsync(out + m_tot, gsm.p, ms_tot * sizeof(mb_smem), cudaMemcpyDefault, A.st));
+            }
+            if (!hits_dev && hs_tot) MB_CK(cudaMemcpyAsync(hits + h_tot, dhits, hs_tot * 4, cudaMemcpyDeviceToHost, A.st));
+            MB_CK(cudaStreamSynchronize(A.st));
+            MB_CK(cudaStreamSynchronize(B.st));
+        }
+        m_tot += ms_tot;
+        h_tot += hs_tot;
+        // the slice's arrays are freed on the caller's stream, after the stage streams' work above
+        MB_CK(cudaEventRecord(A.ev, A.st));
+        MB_CK(cudaStreamWaitEvent(ust, A.ev, 0));
+        MB_CK(cudaEventRecord(B.ev, B.st));
+        MB_CK(cudaStreamWaitEvent(ust, B.ev, 0));
     }
-    for (Stage &x : pl.s) MB_CK(cudaStreamSynchronize(x.st));
+    (void)out_dev;
     keep_pipeline(std::move(keep));
     *n_out = m_tot;
     *n_hits = h_tot;

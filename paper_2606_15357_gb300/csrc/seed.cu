@@ -1224,6 +1224,38 @@ extern "C" int mb_seed_batch(const mb_index *idx, const uint8_t *seq, const uint
                        st, out, cap, n_out, n_hits);
 }
 
+// The shared-walk workspace for n_smem records and total hits, carved from one stream-ordered
+// allocation.
+static int share_alloc(DevBuf &bw, u64 n_smem, u64 total, cudaStream_t st, ShareBufs &b) {
+    const size_t rec_bytes = (size_t)n_smem * SHARE_BYTES_PER_RECORD, row_bytes = (size_t)total * 8;
+    MB_TRY(bw.alloc(rec_bytes + row_bytes + 16 + share_tmp_bytes(n_smem) + 13 * 256, st));
+    char *m = (char *)bw.p;
+    auto take = [&](size_t bytes) { void *p = m; m += (bytes + 255) & ~(size_t)255; return p; };
+    b.keys = (u64 *)take(n_smem * 8);
+    b.keys_alt = (u64 *)take(n_smem * 8);
+    b.roff = (u64 *)take(n_smem * 8);
+    b.vals = (u32 *)take(n_smem * 4);
+    b.vals_alt = (u32 *)take(n_smem * 4);
+    b.pmax = (u32 *)take(n_smem * 4);
+    b.last = (u32 *)take(n_smem * 4);
+    b.rows = (u32 *)take(total * 4);
+    b.rpos = (u32 *)take(total * 4);
+    b.nrows = (u64 *)take(8);
+    b.nwalk = (u64 *)take(8);
+    b.tmp = take(share_tmp_bytes(n_smem));
+    return MB_OK;
+}
+
+int mb_locate_records(const mb_index *idx, const mb_smem *sm, u64 n_smem, const u32 *known, u32 *hits, u64 n_hits,
+                      u32 depth, cudaStream_t st) {
+    if (n_smem == 0 || n_hits == 0) return MB_OK;
+    DevBuf bw;
+    ShareBufs b;
+    MB_TRY(share_alloc(bw, n_smem, n_hits, st, b));
+    return locate_shared(mb_dev_index(idx), sm, n_smem, nullptr, known, hits, n_hits, b, nullptr, false, depth,
+                         nullptr, st);
+}
+
 extern "C" int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_smem, const mb_opts *opts,
                          void *stream, uint32_t *hits, uint64_t cap, uint64_t *n_hits) {
     if (!idx || !n_hits || (n_smem && !smem)) {
@@ -1252,27 +1284,9 @@ extern "C" int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_sm
     }
     const DevIndex I = mb_dev_index(idx);
     const bool count = opts && (opts->flags & MB_COUNT);
-    // the shared-walk workspace: per record, per row, scratch
     DevBuf bw;
-    const size_t rec_bytes = (size_t)n_smem * SHARE_BYTES_PER_RECORD, row_bytes = (size_t)total * 8;
-    MB_TRY(bw.alloc(rec_bytes + row_bytes + 16 + share_tmp_bytes(n_smem) + 13 * 256, st));
     ShareBufs b;
-    {
-        char *m = (char *)bw.p;
-        auto take = [&](size_t bytes) { void *p = m; m += (bytes + 255) & ~(size_t)255; return p; };
-        b.keys = (u64 *)take(n_smem * 8);
-        b.keys_alt = (u64 *)take(n_smem * 8);
-        b.roff = (u64 *)take(n_smem * 8);
-        b.vals = (u32 *)take(n_smem * 4);
-        b.vals_alt = (u32 *)take(n_smem * 4);
-        b.pmax = (u32 *)take(n_smem * 4);
-        b.last = (u32 *)take(n_smem * 4);
-        b.rows = (u32 *)take(total * 4);
-        b.rpos = (u32 *)take(total * 4);
-        b.nrows = (u64 *)take(8);
-        b.nwalk = (u64 *)take(8);
-        b.tmp = take(share_tmp_bytes(n_smem));
-    }
+    MB_TRY(share_alloc(bw, n_smem, total, st, b));
     u64 *wc = count ? mb_work_counter_buf(st) : nullptr;
     KTimer kt("locate", st);
     MB_TRY(locate_shared(I, (const mb_smem *)dsm, n_smem, nullptr, nullptr, dh, total, b, wc, count,
@@ -1564,15 +1578,14 @@ extern "C" void mb_plan_free(mb_plan *P) {
     delete P;
 }
 
-// The whole stage on `stream`, with no host synchronization and no allocation.
-extern "C" int mb_plan_run(mb_plan *P, const uint8_t *seq, const uint64_t *off, uint32_t n_reads, const uint8_t *mate,
-                           void *stream) {
+// Seeding of the plan's batch up to the records with their hit offsets (no locate).
+static int plan_seed(mb_plan *P, const uint8_t *seq, const uint64_t *off, uint32_t n_reads, const uint8_t *mate,
+                     cudaStream_t st) {
     if (!P || (n_reads && (!seq || !off))) return MB_ERR_ARG;
     if (n_reads > P->max_reads) {
         mb_set_error("mb_plan_run: %u reads exceed the plan's %u", n_reads, P->max_reads);
         return MB_ERR_ARG;
     }
-    cudaStream_t st = (cudaStream_t)stream;
     MB_CK(cudaMemsetAsync(P->misc, 0, 256, st));
     if (n_reads == 0) return MB_OK;
     const DevIndex I = mb_dev_index(P->idx);
@@ -1602,8 +1615,23 @@ extern "C" int mb_plan_run(mb_plan *P, const uint8_t *seq, const uint64_t *off, 
     MB_TRY(scan_exclusive_u64(P->hitc, P->hitc, P->max_smem, n_hits, P->tmp, st));
     k_set_hitoff<<<grid_for(P->max_smem, 256), 256, 0, st>>>(P->hitc, P->max_smem, n_smem, P->out);
     MB_KCHECK();
-    MB_TRY(locate_shared(I, P->out, P->max_smem, n_smem, P->known, P->hits, P->max_hits, P->share, nullptr, false,
-                         P->depth, nullptr, st));
+    return MB_OK;
+}
+
+int mb_plan_run_seed(mb_plan *P, const uint8_t *seq, const uint64_t *off, uint32_t n_reads, const uint8_t *mate,
+                     cudaStream_t st) {
+    return plan_seed(P, seq, off, n_reads, mate, st);
+}
+const u32 *mb_plan_known(const mb_plan *P) { return P ? P->known : nullptr; }
+
+// The whole stage on `stream`, with no host synchronization and no allocation.
+extern "C" int mb_plan_run(mb_plan *P, const uint8_t *seq, const uint64_t *off, uint32_t n_reads, const uint8_t *mate,
+                           void *stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    MB_TRY(plan_seed(P, seq, off, n_reads, mate, st));
+    if (n_reads == 0) return MB_OK;
+    MB_TRY(locate_shared(mb_dev_index(P->idx), P->out, P->max_smem, P->misc, P->known, P->hits, P->max_hits,
+                         P->share, nullptr, false, P->depth, nullptr, st));
     return MB_OK;
 }
 

@@ -98,6 +98,25 @@ def test_chunk_outgrows_its_plan(mb):
     check_oracle(sm, hits, oracle.Index(ref), rd.seq, rd.off)
 
 
+def test_records_outgrow_the_plan(mb):
+    """Reads that match nowhere at length 150 but everywhere at length 5: with min_len 5 each read
+    has dozens of SMEMs, more records per chunk than the chunk's plan holds, so every chunk takes
+    the allocating path; the slice is still located at once."""
+    ref = synth.reference(200_000, 81)
+    reads = [synth.reference(150, 8200 + q) for q in range(300)]
+    seq = np.concatenate(reads).astype(np.uint8)
+    off = np.concatenate([[0], np.cumsum([len(r) for r in reads])]).astype(np.uint64)
+    o = dict(min_len=5, max_occ=50)
+    G = mb.mb_index_build(ref)
+    sm, hits = mb.seed_locate(G, seq, off, opts=dict(o, chunk_reads=50))
+    assert len(sm) / (300 / 50) > 4 * (4 * 50 + 7500 // 32 + 64)   # far more per chunk than its plan holds
+    psm, phits = mb.seed(G, seq, off, opts=o)
+    assert sm.tobytes() == psm.tobytes()
+    assert np.array_equal(hits, phits)
+    osm, over, hoff, ohits = oracle.Index(ref).seed(seq, off, min_len=5, max_occ=50)
+    assert np.array_equal(sm["k"].astype(np.uint64), osm["k"]) and np.array_equal(hits.astype(np.uint64), ohits)
+
+
 def test_capacity_reports_both_totals(mb, repeat_rich):
     ref, rd, G = repeat_rich
     psm, phits = mb.seed(G, rd.seq, rd.off)
