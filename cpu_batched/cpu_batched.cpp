@@ -1,5 +1,5 @@
 /*
- * CPU comparator of the seeding stage: the paper's own CPU design (Section 2.4-2.5), built to be
+ * CPU comparator of the seeding stage: the paper's own CPU design (Sections 2.3-2.5), built to be
  * timed next to the GPU path as context.  It is not the oracle and not part of the product path
  * (the library never calls it); bench.py times it on the host cores.
  *
@@ -7,9 +7,9 @@
  *    128 BWT rows, the counts of A, C, G, T before the block (4 x u64) and the 128 symbols at 2
  *    bits (4 x u64).  The $ row is stored as A and left out of the counts.
  *  - Algorithm 3 (BatchFindSMEM) over a batch of reads with one FIFO queue; whenever an entry is
- *    pushed, the blocks holding the two rows its next extension reads are prefetched
- *    (Section 2.4: "prefetches memory blocks containing B[l] and B[l']"), so that by the time the
- *    entry reaches the head of the queue its data is in cache.
+ *    pushed, the blocks holding the two rows its next extension reads are prefetched (the
+ *    prefetch of Section 2.5 for Algorithm 3), so that by the time the entry reaches the head of
+ *    the queue its data is in cache.
  *  - The ds-intervals of all 10-mers precomputed (Section 2.5); a stage-1 entry that starts from
  *    the empty interval takes the 10 backward steps as one table lookup.  A failing 10-mer
  *    restarts stage 1 at its second base; stage 3 tries the table once and steps otherwise.

@@ -4,7 +4,7 @@
  * For every read it finds the (l,c)-SMEMs against an FMD-index of the reference
  * (Section 2.1 definitions; Algorithm 3), flags SMEMs that occur more than
  * max_occ times, and locates the remaining occurrences through a sampled
- * suffix array by LF-walks (Section 2.3; Algorithm 2).  All arithmetic runs in
+ * suffix array by LF-walks (Section 2.4; Algorithm 2).  All arithmetic runs in
  * CUDA kernels for sm_103a; the host code below only moves data and launches.
  *
  * Conventions shared by every call:
@@ -20,7 +20,7 @@
  *  - An index is read-only after it is built and may be used from several
  *    streams at once.  A server (mb_serve_*) is used from one host thread.
  *  - Text coordinates: T = R . revcomp(R) . $ (Section 2.1), n = 2|R| + 1; in
- *    bisulfite mode R is replaced by CT(R) . GA(R) (Section 2.8).  n must be
+ *    bisulfite mode R is replaced by CT(R) . GA(R) (Section 2.9).  n must be
  *    below 2^32.
  */
 #ifndef MINIBWA_GPU_H
@@ -46,7 +46,7 @@ enum {
 };
 
 /* Flags of mb_opts.flags */
-#define MB_BS3      0x1u   /* index: bisulfite 3-base index over CT(R).GA(R) (Section 2.8);
+#define MB_BS3      0x1u   /* index: bisulfite 3-base index over CT(R).GA(R) (Section 2.9);
                               seeding: convert read 1 C->T and read 2 G->A, keep hits by strand */
 #define MB_BATCHED  0x2u   /* seeding: lanes take reads from a device work queue (a plan orders it
                               by decreasing read length; mb_seed_batch keeps read order) */
@@ -68,10 +68,10 @@ typedef struct mb_server mb_server;
 
 /* Parameters.  Zero in any field selects its default. */
 typedef struct {
-    uint32_t min_len;         /* l, minimum SMEM length (default 19, Section 2.7) */
+    uint32_t min_len;         /* l, minimum SMEM length (default 19, Section 2.6) */
     uint32_t min_occ;         /* c, minimum occurrence (default 1) */
     uint32_t max_occ;         /* SMEMs with s > max_occ are flagged and not located (default 500) */
-    uint32_t sa_rate;         /* r, suffix array sample rate (default 32, Section 2.3) */
+    uint32_t sa_rate;         /* r, suffix array sample rate (default 32, Section 2.4) */
     uint32_t kmer_k;          /* k of the k-mer ds-interval table (default 10, Section 2.5), <= 14;
                                  the table takes 12 * 4^k bytes (3.2 GB at k = 14) */
     uint32_t flags;           /* MB_* flags above */
@@ -138,7 +138,7 @@ int mb_index_drop_sa(mb_index *idx);
  *   seq      host or device, concatenated read base codes.
  *   off      host or device, n_reads + 1 u64 offsets into seq (read r = seq[off[r], off[r+1])).
  *   mate     host or device or NULL; per read 0 = single, 1 = read 1, 2 = read 2 (used with
- *            MB_BS3 to convert read 1 C->T and read 2 G->A before seeding, Section 2.8).
+ *            MB_BS3 to convert read 1 C->T and read 2 G->A before seeding, Section 2.9).
  *   out      host or device, room for `cap` records.  Records are ordered by read, then by
  *            ascending qbeg; s > max_occ sets MB_SMEM_OVER_MAX_OCC; hit_off is the
  *            exclusive prefix sum of s over records without that flag.
@@ -152,7 +152,7 @@ int mb_seed_batch(const mb_index *idx, const uint8_t *seq, const uint64_t *off, 
                   mb_smem *out, uint64_t cap, uint64_t *n_out, uint64_t *n_hits);
 
 /* ---------------------------------------------------------------------------------------
- * mb_reseed — the second seeding round of Section 2.7.  For every record of `smem` (the first
+ * mb_reseed — the second seeding round of Section 2.6.  For every record of `smem` (the first
  * round's (l,c)-SMEMs of the same reads, as mb_seed_batch wrote them) with qend - qbeg >= 2l and
  * s <= 10 and no MB_SMEM_OVER_MAX_OCC, finds the (floor((qend-qbeg)/2), s+1)-SMEMs of the
  * substring read[qbeg, qend) (the paper prints the length as floor((j-1)/2); read here as the
@@ -190,7 +190,7 @@ int mb_seed_batch_noalloc(const mb_index *idx, const uint8_t *seq, const uint64_
 
 /* ---------------------------------------------------------------------------------------
  * mb_locate — text positions of every row of every SMEM without MB_SMEM_OVER_MAX_OCC
- * (Section 2.3, Algorithm 2): row x is LF-walked to a sampled row; its position is
+ * (Section 2.4, Algorithm 2): row x is LF-walked to a sampled row; its position is
  * (steps + S(sampled row)) mod n.
  *   smem     host or device, n_smem records from mb_seed_batch (hit_off must be as written).
  *   hits     host or device, room for `cap` u32 positions; hit t of record m is written at
@@ -203,7 +203,7 @@ int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_smem, const m
 
 /* ---------------------------------------------------------------------------------------
  * mb_seed_locate — the whole stage in one call: SMEMs as mb_seed_batch, then their hits as
- * mb_locate (Section 2.5, Algorithm 3; Section 2.3, Algorithm 2), for callers whose reads and
+ * mb_locate (Section 2.5, Algorithm 3; Section 2.4, Algorithm 2), for callers whose reads and
  * results live in host memory.  The batch is cut into slices (at most 2^25 reads and 2^33
  * bases) and a slice into chunks of consecutive reads (opts->chunk_reads reads, at most 2^29
  * bases, at least one read) that alternate between two internal streams, so that the copies of
@@ -298,7 +298,7 @@ int mb_serve_destroy(mb_server *srv);
  * group with another request (the continuous-batching count). */
 int mb_serve_stats(mb_server *srv, uint32_t *slots, uint64_t *groups, uint64_t *merged);
 
-/* Section 2.8 strand rule on the 3-base index: keep[h] = 1 if hit h of an SMEM of read `mate`
+/* Section 2.9 strand rule on the 3-base index: keep[h] = 1 if hit h of an SMEM of read `mate`
  * 1 lies wholly inside the forward C-to-T or the reverse G-to-A copy of the reference (read 2:
  * forward G-to-A or reverse C-to-T), else 0.  All pointers host or device. */
 int mb_bs_filter(const mb_index *idx, const mb_smem *smem, uint64_t n_smem, const uint8_t *mate,
@@ -312,7 +312,7 @@ typedef struct {
 } mb_piece;
 
 /* ---------------------------------------------------------------------------------------
- * mb_bs_split — Section 2.8: a seed found on the 3-base index may pair a read C with a
+ * mb_bs_split — Section 2.9: a seed found on the 3-base index may pair a read C with a
  * reference T (read 1, C->T converted) or a read G with a reference A (read 2, G->A); such a
  * T-to-C mismatch is not a bisulfite conversion.  For every hit h with keep[h] != 0 (keep may
  * be NULL: every hit), the original read bases under the seed are compared with the original
@@ -338,7 +338,7 @@ int mb_bs_split(const mb_index *idx, const uint8_t *ref, const uint8_t *seq, con
                 void *stream, mb_piece *out, uint64_t cap, uint64_t *n_out);
 
 /* ---------------------------------------------------------------------------------------
- * mb_rescue_prefilter — the mate-rescue prefilter of Section 2.6: for each pair p of a read
+ * mb_rescue_prefilter — the mate-rescue prefilter of Section 2.7: for each pair p of a read
  * P = reads[read_off[p], read_off[p+1]) and a reference window R = wins[win_off[p],
  * win_off[p+1]), best[p] = max over t of M_t = #{(i, j) : P[i, i+q) = R[j, j+q), j - i = t}
  * (0 when no q-mer matches), over every q-mer start i of P and j of R.  A q-mer holding an N

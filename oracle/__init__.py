@@ -8,7 +8,7 @@ first use); this module only marshals numpy arrays.
 
 What each function follows (arxiv 2606.15357):
   Index            Section 2.1: T = R . revcomp(R) . $, suffix array S, B[i] = T[S(i)-1];
-                   Section 2.8: bisulfite mode indexes CT(R) . GA(R).
+                   Section 2.9: bisulfite mode indexes CT(R) . GA(R).
   ds_interval      Section 2.1, the ds-interval (lo(P), lo(revcomp P), occ(P)) by binary
                    search over the sorted suffixes.
   pi / backward_ext / forward_ext
@@ -16,7 +16,7 @@ What each function follows (arxiv 2606.15357):
   smem(method="def")   Section 2.1 definition of (l,c)-SMEMs (the published answer).
   smem(method="alg3")  Algorithm 3 BatchFindSMEM with one FIFO queue.
   smem_brute       the definition by scanning T (tiny texts only).
-  locate           {S(x) : k <= x < k+s} from the full suffix array (Section 2.3).
+  locate           {S(x) : k <= x < k+s} from the full suffix array (Section 2.4).
   locate_slow / batch_locate   Algorithm 2 with the sampled suffix array, modulo n.
   seed             the whole stage: SMEMs, max-occ filter, hits in SA-row order.
 
@@ -260,7 +260,7 @@ class Index:
 
 def reseed(X: "Index", seq, off, first, min_len: int = 19, max_s: int = 10, max_occ: int = 500,
            threads: int = 0):
-    """Section 2.7, second seeding round: for every first-round record with qend - qbeg >= 2l,
+    """Section 2.6, second seeding round: for every first-round record with qend - qbeg >= 2l,
     s <= 10 and s <= max_occ, the (floor((qend - qbeg)/2), s + 1)-SMEMs of read[qbeg, qend) as a
     query of its own, by the definition (Index.smem).  Returns (records in read coordinates,
     ordered by window then qbeg; over-max-occ flags; hit offsets; hits)."""
@@ -306,7 +306,7 @@ def smem_brute(text: np.ndarray, seq, off, min_len: int = 19, min_occ: int = 1,
 
 
 def bs_convert_reads(seq, off, mate) -> np.ndarray:
-    """Section 2.8: every C of read 1 becomes T and every G of read 2 becomes A."""
+    """Section 2.9: every C of read 1 becomes T and every G of read 2 becomes A."""
     seq = np.array(seq, dtype=np.uint8, copy=True)
     rid = np.repeat(np.arange(len(off) - 1), np.diff(np.asarray(off, dtype=np.int64)))
     m = np.asarray(mate)[rid]
@@ -316,7 +316,7 @@ def bs_convert_reads(seq, off, mate) -> np.ndarray:
 
 
 def bs_keep(pos, qlen, read_mate, rlen: int) -> np.ndarray:
-    """Section 2.8 strand filter on the 3-base index T = CT(R) GA(R) rc(GA(R)) rc(CT(R)) $:
+    """Section 2.9 strand filter on the 3-base index T = CT(R) GA(R) rc(GA(R)) rc(CT(R)) $:
     a read-1 hit is kept only inside the forward C-to-T or the reverse G-to-A copy, a read-2
     hit only inside the forward G-to-A or the reverse C-to-T copy.  rlen = |R|; a hit that
     crosses a copy boundary is dropped."""
@@ -335,7 +335,7 @@ PIECE_DTYPE = np.dtype([("hit", np.uint64), ("read", np.uint32), ("qbeg", np.uin
 
 
 def bs_split(ref, seq, off, mate, sm, hits, keep, min_len: int = 19, over=None) -> np.ndarray:
-    """Section 2.8, T-to-C split of bisulfite seed matches.  For every kept hit (record m of
+    """Section 2.9, T-to-C split of bisulfite seed matches.  For every kept hit (record m of
     `sm`, text position p = hits[h]) the original read bases x_t = read[qbeg + t] are compared
     with the original reference bases under the seed: copy g = p // |R| of the 3-base text, offset
     q = p - g |R|; copies 0 and 1 read R[q + t], copies 2 and 3 (reverse complements) read
@@ -387,7 +387,7 @@ def bs_split(ref, seq, off, mate, sm, hits, keep, min_len: int = 19, over=None) 
 
 
 def qmer_diag_max(P, R, q: int = 7) -> int:
-    """Mate-rescue prefilter (Section 2.6): M_t = |{(i, j) : P[i, i+q) = R[j, j+q), j - i = t}|
+    """Mate-rescue prefilter (Section 2.7): M_t = |{(i, j) : P[i, i+q) = R[j, j+q), j - i = t}|
     over every q-mer start i of P and j of R, and the result max_t M_t (0 when no q-mer matches).
     A q-mer holding an N (code > 3) matches nothing.  Written as the definition: all pairs (i, j)
     compared, matches counted per diagonal t."""

@@ -29,7 +29,7 @@
  *  - a pattern containing N has ds-interval (0,0,0);
  *  - Algorithm 2's result is taken modulo n (a walk through the $ row lands on
  *    row 0, whose S value is n-1);
- *  - bisulfite mode indexes R3 = CT(R) . GA(R) (Section 2.8) in place of R.
+ *  - bisulfite mode indexes R3 = CT(R) . GA(R) (Section 2.9) in place of R.
  */
 #include <stdint.h>
 #include <string.h>

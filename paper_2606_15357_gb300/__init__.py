@@ -283,7 +283,7 @@ def mb_locate(index: Index, smem, n_smem: int, opts=None, stream=None, hits=None
 
 
 def mb_bs_filter(index: Index, smem, n_smem: int, mate, hits, n_hits: int, stream=None, keep=None):
-    """Section 2.8 strand rule: 1 for hits kept, 0 for hits dropped."""
+    """Section 2.9 strand rule: 1 for hits kept, 0 for hits dropped."""
     if keep is None:
         keep = np.empty(max(n_hits, 1), dtype=np.uint8)
     _check(lib().mb_bs_filter(index.handle, _ptr(smem), n_smem, _ptr(mate), _ptr(hits), n_hits,
@@ -297,7 +297,7 @@ PIECE_DTYPE = np.dtype([("hit", np.uint64), ("read", np.uint32), ("qbeg", np.uin
 
 def mb_bs_split(index: Index, ref, seq, off, mate, smem, n_smem: int, hits, n_hits: int, keep=None,
                 opts=None, stream=None):
-    """Section 2.8 T-to-C split of bisulfite seed hits; returns a host array of PIECE_DTYPE."""
+    """Section 2.9 T-to-C split of bisulfite seed hits; returns a host array of PIECE_DTYPE."""
     o = _opts(opts)
     n_reads = (off.numel() if hasattr(off, "numel") else len(off)) - 1
     n = ctypes.c_uint64()
@@ -315,7 +315,7 @@ def mb_bs_split(index: Index, ref, seq, off, mate, smem, n_smem: int, hits, n_hi
 
 
 def mb_rescue_prefilter(reads, read_off, wins, win_off, q: int = 7, stream=None, best=None):
-    """Section 2.6 mate-rescue prefilter: max_t M_t of q-mer matches per (read, window) pair."""
+    """Section 2.7 mate-rescue prefilter: max_t M_t of q-mer matches per (read, window) pair."""
     n = (read_off.numel() if hasattr(read_off, "numel") else len(read_off)) - 1
     if best is None:
         best = np.empty(max(n, 1), dtype=np.uint32)
@@ -325,7 +325,7 @@ def mb_rescue_prefilter(reads, read_off, wins, win_off, q: int = 7, stream=None,
 
 
 def mb_reseed(index: Index, seq, off, smem, n_smem: int, mate=None, opts=None, stream=None):
-    """Second seeding round (Section 2.7) on first-round records; returns (records, n, n_hits)."""
+    """Second seeding round (Section 2.6) on first-round records; returns (records, n, n_hits)."""
     o = _opts(opts)
     n_reads = (off.numel() if hasattr(off, "numel") else len(off)) - 1
     n_out, n_hits = ctypes.c_uint64(), ctypes.c_uint64()

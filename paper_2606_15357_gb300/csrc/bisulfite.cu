@@ -1,4 +1,4 @@
-// Section 2.8 on the GPU: the T-to-C split of bisulfite seed matches (mb_bs_split).
+// Section 2.9 on the GPU: the T-to-C split of bisulfite seed matches (mb_bs_split).
 //
 // A seed found on the 3-base index matches the converted read against the converted reference,
 // so a read C over a reference T (read 1, C->T) or a read G over a reference A (read 2, G->A)

@@ -1,8 +1,8 @@
 // FMD-index construction on the GPU (Section 2.1 definitions, Section 2.2 block layout (here one
 // 32-byte block per 64 rows),
-// Section 2.3 sampled suffix array, Section 2.5 k-mer ds-interval table).
+// Section 2.4 sampled suffix array, Section 2.5 k-mer ds-interval table).
 //
-//   T = R . revcomp(R) . $            (bisulfite: R -> CT(R) . GA(R), Section 2.8)
+//   T = R . revcomp(R) . $            (bisulfite: R -> CT(R) . GA(R), Section 2.9)
 //   S = suffix array of T             prefix doubling: sort by the first 27 symbols, then
 //                                     repeatedly re-sort the suffixes whose 2h-prefix is still
 //                                     shared by (rank of the h-prefix, rank of the h-prefix at +h)

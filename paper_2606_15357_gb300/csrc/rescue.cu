@@ -1,4 +1,4 @@
-// Mate-rescue prefilter of Section 2.6 (mb_rescue_prefilter): for a read P and a reference window
+// Mate-rescue prefilter of Section 2.7 (mb_rescue_prefilter): for a read P and a reference window
 // R, M_t = #{(i, j) : P[i, i+q) = R[j, j+q), j - i = t}, and the result is max_t M_t.
 //
 // One warp per (read, window) pair, bit-parallel along each diagonal.  The warp writes, for each

@@ -1,5 +1,5 @@
 // Seeding on the GPU: (l,c)-SMEM finding (Section 2.5, Algorithm 3), the max-occurrence flag,
-// and locate through the sampled suffix array (Section 2.3, Algorithm 2).
+// and locate through the sampled suffix array (Section 2.4, Algorithm 2).
 //
 // SMEMs: one thread runs Algorithm 3's three-stage state machine for one read.  In Algorithm 3
 // every read has exactly one entry in the queue at any time, so the per-read order of queue
@@ -22,7 +22,7 @@ u32 mb_index_flags(const mb_index *x);
 
 namespace {
 
-// second seeding round (Section 2.7): windows are SMEMs occurring at most this many times
+// second seeding round (Section 2.6): windows are SMEMs occurring at most this many times
 constexpr u32 RESEED_MAX_OCC = 10;
 
 struct SlotRec {
@@ -1844,7 +1844,7 @@ extern "C" int mb_reseed(const mb_index *idx, const uint8_t *seq, const uint64_t
     }
     if (mate) MB_TRY(mb_stage_in(mate, n_reads, st, bmate, &dmate));
     MB_TRY(mb_stage_in(smem, n_smem * sizeof(mb_smem), st, bsm, &dsm));
-    // windows (Section 2.7): SMEMs of at least 2l bases occurring at most 10 times
+    // windows (Section 2.6): SMEMs of at least 2l bases occurring at most 10 times
     DevBuf bflag, bwpos, btmp, bmisc;
     MB_TRY(bflag.alloc(n_smem * 8, st));
     MB_TRY(bwpos.alloc(n_smem * 8, st));

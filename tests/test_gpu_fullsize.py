@@ -122,7 +122,7 @@ def test_workload2_100mbp_full_index_and_sampled_reads(mb):
 def test_workload3_bisulfite_1gbp_three_base_index(mb):
     """Directional bisulfite set: 3-base index over CT(R).GA(R) of the 1 Gbp reference
     (n = 4e9 + 1), reads converted on the GPU (read 1 C->T, read 2 G->A), the strand filter of
-    Section 2.8; full suffix array, k-mer sample and 1% of the reads against the oracle."""
+    Section 2.9; full suffix array, k-mer sample and 1% of the reads against the oracle."""
     from synth import Reads
     ref, rd, params = synth.workload(3, bisulfite=True)
     o = dict(flags=mb.MB_BS3)
@@ -138,13 +138,13 @@ def test_workload3_bisulfite_1gbp_three_base_index(mb):
     kp = mb.mb_bs_filter(G, sm, m, rd.mate, h, nh)
     conv = Reads(oracle.bs_convert_reads(rd.seq, rd.off, rd.mate), rd.off, rd.origin, rd.mate)
     check_sampled_reads(sm, h, X, conv, 0.01, 0x6D64, params)
-    # strand filter recomputed from the positions (Section 2.8)
+    # strand filter recomputed from the positions (Section 2.9)
     cnt = np.where(sm["flags"] & 1, 0, sm["s"]).astype(np.int64)
     qlen = np.repeat((sm["qend"] - sm["qbeg"]).astype(np.int64), cnt)
     rmate = np.repeat(rd.mate[sm["read"].astype(np.int64)], cnt)
     assert np.array_equal(kp.astype(bool), oracle.bs_keep(h, qlen, rmate, len(ref)))
     assert kp.sum() > 0
-    # T-to-C split of every kept hit (Section 2.8), checked against the oracle on the hits of 1% of
+    # T-to-C split of every kept hit (Section 2.9), checked against the oracle on the hits of 1% of
     # the reads
     pc = mb.mb_bs_split(G, ref, rd.seq, rd.off, rd.mate, sm, m, h, nh, keep=kp)
     pick = np.random.default_rng(0x6D65).choice(rd.n, rd.n // 100, replace=False)

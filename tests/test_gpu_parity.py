@@ -322,7 +322,7 @@ def test_bisulfite_index_and_seeding(mb):
 
 
 def test_bisulfite_split(mb):
-    """Section 2.8 T-to-C split on the GPU against the oracle: reads with 1-3% substitutions so
+    """Section 2.9 T-to-C split on the GPU against the oracle: reads with 1-3% substitutions so
     that read C over reference T (read 1) and read G over reference A (read 2) occur; with the
     strand filter's keep flags and with every hit, host and device buffers."""
     ref = synth.reference(60_000, 73)

@@ -1,4 +1,4 @@
-"""Mate-rescue prefilter (Section 2.6) on the GPU against the oracle's definition: max over
+"""Mate-rescue prefilter (Section 2.7) on the GPU against the oracle's definition: max over
 diagonals t of the number of q-mer matches (i, j) with j - i = t, per (read, window) pair."""
 import numpy as np
 import pytest

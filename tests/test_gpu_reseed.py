@@ -1,4 +1,4 @@
-"""Second seeding round (Section 2.7): (floor(len/2), s+1)-SMEMs inside every first-round SMEM
+"""Second seeding round (Section 2.6): (floor(len/2), s+1)-SMEMs inside every first-round SMEM
 of at least 2l bases occurring at most 10 times, against the oracle's definition."""
 import numpy as np
 import pytest

@@ -3,7 +3,7 @@
 Section 2.1 definitions: brute force on tiny texts, a hand-derived fixture,
 the suffix array as a sorted permutation, invariants of (l,c)-SMEMs;
 Algorithm 1 and 3 against the definition; Algorithm 2 against the full suffix
-array; the bisulfite index layout of Section 2.8.
+array; the bisulfite index layout of Section 2.9.
 """
 import os
 
@@ -296,7 +296,7 @@ def test_bisulfite_index_and_filter():
 
 
 def test_second_round_windows_by_brute_force():
-    """Section 2.7: the second round's SMEMs of each window equal brute force on that window."""
+    """Section 2.6: the second round's SMEMs of each window equal brute force on that window."""
     ref = synth.repeat_rich_reference(6000, 41, 0.5)
     X = oracle.Index(ref)
     T = X.text()
@@ -372,7 +372,7 @@ def _bs_seed_and_split(ref, seq, off, mate):
 
 
 def test_bs_split_planted_mismatches():
-    """Section 2.8 split, hand-derived: read-1 C over reference T cuts a forward seed and a
+    """Section 2.9 split, hand-derived: read-1 C over reference T cuts a forward seed and a
     reverse seed; read-2 G over reference A cuts a forward G-to-A seed; pieces under 19 go."""
     ref = synth.reference(50_000, 77)
     M = len(ref)
@@ -432,7 +432,7 @@ def test_bs_split_invariants():
 
 
 def test_qmer_prefilter_closed_forms():
-    """Section 2.6 prefilter: a read copied from the window has every q-mer on one diagonal
+    """Section 2.7 prefilter: a read copied from the window has every q-mer on one diagonal
     (max M_t = |P| - q + 1); each substitution at least q bases from the others and from the ends
     removes exactly q of them; an N removes the q-mers that cover it; a periodic pair keeps the
     full count on its best diagonal."""
