@@ -26,7 +26,7 @@ void mb_set_error(const char *fmt, ...);
     } while (0)
 
 // Keep freed stream-ordered memory in the device's pool between calls (the default threshold of 0
-// hands it back to the driver at every synchronization, so each call would map its scratch again).
+// returns it to the CUDA driver at every synchronization, so each call would map its scratch again).
 void mb_keep_pool_memory();
 
 // Stream-ordered device buffer owned by host code.  Freed on the stream it was made on.
