@@ -153,6 +153,17 @@ def ncu_traffic(kernel: str, workload: str):
     return float(mb.group(1))
 
 
+def ncu_hit_rates(kernel: str, workload: str):
+    """(L2 hit %, L1 hit %) of the --set full capture in the same committed summary, if it was
+    taken on the current kernel source."""
+    if ncu_traffic(kernel, workload) is None:
+        return None
+    txt = open(os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")).read()
+    l2 = re.search(r"- L2 hit rate %:\s*([0-9.]+)", txt)
+    l1 = re.search(r"- L1 hit rate %:\s*([0-9.]+)", txt)
+    return (float(l2.group(1)), float(l1.group(1))) if l2 and l1 else None
+
+
 class ClockSampler:
     """nvidia-smi samples during the timed region."""
 
@@ -681,6 +692,18 @@ def run_gpu(args):
     # this, not the copy bandwidth, is the ceiling a DRAM-bound gather can reach.
     if roofline["traffic"]:
         roofline["dram_GBps"] = roofline["traffic"] / (kms / 1000.0) / 1e9
+    # per kernel: DRAM bytes of the committed capture, their rate, random 32-byte sectors per
+    # second (every block access is one such sector) and the capture's cache hit rates
+    for kn, kd in roofline["kernels"].items():
+        t = ncu_traffic(kn, wl_tag)
+        if t:
+            sec = kd["ms_per_launch"] / 1000.0
+            kd["dram_bytes"] = t
+            kd["dram_GBps"] = t / sec / 1e9
+            kd["dram_sectors_per_s"] = t / 32 / sec
+        hr = ncu_hit_rates(kn, wl_tag)
+        if hr:
+            kd["l2_hit_pct"], kd["l1_hit_pct"] = hr
     if not args.no_probe:
         gc = gather_ceiling(args.probe_gib)
         roofline["gather_ceiling"] = gc
