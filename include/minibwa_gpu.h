@@ -197,6 +197,9 @@ int mb_seed_batch_noalloc(const mb_index *idx, const uint8_t *seq, const uint64_
  *            hits[m.hit_off + t], rows k..k+s-1 in order.
  *   n_hits   receives the total.  If it exceeds cap: MB_ERR_CAPACITY, nothing written.
  * With MB_BS3 in opts, hits are still all written; mb_bs_filter applies the strand rule.
+ * A row that several records share (the same or nested intervals) is walked once and its
+ * position copied to each of their hits; with MB_COUNT the work counters count those walks.
+ * Device workspace: about 40 bytes per record and 8 per hit, allocated per call.
  */
 int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_smem, const mb_opts *opts,
               void *stream, uint32_t *hits, uint64_t cap, uint64_t *n_hits);
