@@ -15,6 +15,7 @@
 // device and seeding options whose chunks fit them (at most two sets are kept; they are released
 // with the index).
 #include <algorithm>
+#include <cstdlib>
 #include <memory>
 #include <mutex>
 #include <vector>
@@ -25,8 +26,18 @@ namespace {
 constexpr u32 PIPE_READS = 1u << 22;      // default reads per chunk
 constexpr u64 PIPE_BASES = 1ull << 29;    // at most this many bases per chunk (at least one read)
 constexpr u32 SLICE_READS = 1u << 25;     // at most this many reads per slice (located at once)
+                                          // (MB_SLICE_READS in the environment may lower it)
 constexpr u64 SLICE_BASES = 1ull << 33;   // and this many bases (at least one chunk)
 constexpr int PIPE_STAGES = 2;
+
+u32 slice_reads() {
+    const char *e = getenv("MB_SLICE_READS");
+    if (e) {
+        const long v = atol(e);
+        if (v > 0 && v < (long)SLICE_READS) return (u32)v;
+    }
+    return SLICE_READS;
+}
 
 // records of one chunk in batch coordinates: read number and first hit
 __global__ void k_rebase(mb_smem *__restrict__ s, u64 n, u32 r0, u64 h0) {
@@ -180,13 +191,14 @@ extern "C" int mb_seed_locate(const mb_index *idx, const uint8_t *seq, const uin
         r = e;
     }
 
-    // slices: consecutive chunks up to SLICE_READS reads and SLICE_BASES bases
+    // slices: consecutive chunks up to slice_reads() reads and SLICE_BASES bases
+    const u32 max_slice = slice_reads();
     std::vector<Slice> slices;
     for (int i = 0; i < (int)chunks.size();) {
         Slice sl;
         sl.c0 = i;
         u64 nr = 0, nb = 0;
-        while (i < (int)chunks.size() && (i == sl.c0 || (nr + chunks[i].nr <= SLICE_READS &&
+        while (i < (int)chunks.size() && (i == sl.c0 || (nr + chunks[i].nr <= max_slice &&
                                                          nb + (chunks[i].o1 - chunks[i].o0) <= SLICE_BASES))) {
             nr += chunks[i].nr;
             nb += chunks[i].o1 - chunks[i].o0;

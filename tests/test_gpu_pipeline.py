@@ -57,6 +57,24 @@ def test_host_buffers_against_oracle_and_plain(mb, repeat_rich, chunk):
     assert np.array_equal(hits, phits)
 
 
+def test_several_slices(mb, repeat_rich, monkeypatch):
+    """Slices of at most 3,000 reads (MB_SLICE_READS lowers the 2^25 default): each slice is
+    located on its own and its records' hit offsets are made batch-wide after its locate."""
+    ref, rd, G = repeat_rich
+    monkeypatch.setenv("MB_SLICE_READS", "3000")
+    psm, phits = mb.seed(G, rd.seq, rd.off)
+    for chunk in (1000, 2999, 0):
+        sm, hits = mb.seed_locate(G, rd.seq, rd.off, opts=dict(chunk_reads=chunk))
+        assert sm.tobytes() == psm.tobytes()
+        assert np.array_equal(hits, phits)
+    out = torch.empty(len(psm) * 48, dtype=torch.uint8, device="cuda")
+    dh = torch.empty(len(phits), dtype=torch.int32, device="cuda")
+    mb.seed_locate(G, dev(rd.seq), dev(rd.off), opts=dict(chunk_reads=1500), out=out, cap=len(psm), hits=dh,
+                   hits_cap=len(phits))
+    assert out.cpu().numpy().tobytes() == psm.tobytes()
+    assert np.array_equal(dh.cpu().numpy().view(np.uint32), phits)
+
+
 def test_pinned_and_device_buffers(mb, repeat_rich):
     ref, rd, G = repeat_rich
     psm, phits = mb.seed(G, rd.seq, rd.off)
