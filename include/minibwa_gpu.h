@@ -212,7 +212,8 @@ int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_smem, const m
  * bases, at least one read) that alternate between two internal streams, so that the copies of
  * one chunk overlap the seeding of the other; each slice is then located at once (its repeated
  * rows walked once) while its records are copied out.  Use pinned host buffers for the copies
- * to overlap.
+ * to overlap.  The environment variable MB_SLICE_READS, when set below 2^25, lowers the reads
+ * per slice (less device memory, fewer repeated rows shared).
  *   seq, off, mate   host or device, as for mb_seed_batch.
  *   out              host or device, room for `cap` records: the records of mb_seed_batch (read
  *                    numbers and hit_off relative to this batch).
