@@ -288,6 +288,17 @@ def test_edge_reads(mb):
     off = np.concatenate([[0], np.cumsum([len(r) for r in reads])]).astype(np.uint64)
     sm, hits = mb.seed(G, seq, off)
     compare_seed(sm, hits, X, seq, off)
+    # any code above 3 is an N: codes 5..255 in place of 4 give the same records and hits
+    rng = np.random.default_rng(62)
+    odd = seq.copy()
+    ns = odd == 4
+    odd[ns] = rng.integers(5, 256, int(ns.sum())).astype(np.uint8)
+    odd[300:302] = (9, 200)   # two more inside an exact read
+    same = seq.copy()
+    same[300:302] = 4
+    osm, ohits = mb.seed(G, odd, off)
+    ssm, shits = mb.seed(G, same, off)
+    assert osm.tobytes() == ssm.tobytes() and np.array_equal(ohits, shits)
     # empty batch
     e, m, nh = mb.mb_seed_batch(G, seq, off[:1])
     assert m == 0 and nh == 0
