@@ -241,7 +241,7 @@ extern "C" int mb_seed_locate(const mb_index *idx, const uint8_t *seq, const uin
     }
     Pipeline &pl = *keep;
     Stage &A = pl.s[0], &B = pl.s[1];
-    const bool out_dev = out && mb_is_device_ptr(out), hits_dev = hits && mb_is_device_ptr(hits);
+    const bool hits_dev = hits && mb_is_device_ptr(hits);
     const u32 depth = opts ? opts->prefetch_depth : 0;
 
     // device inputs of chunk i (the caller's, or the stage's copies)
@@ -376,7 +376,6 @@ extern "C" int mb_seed_locate(const mb_index *idx, const uint8_t *seq, const uin
         MB_CK(cudaEventRecord(B.ev, B.st));
         MB_CK(cudaStreamWaitEvent(ust, B.ev, 0));
     }
-    (void)out_dev;
     keep_pipeline(std::move(keep));
     *n_out = m_tot;
     *n_hits = h_tot;
