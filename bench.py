@@ -296,7 +296,7 @@ def run_reference(args):
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "reads/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * T / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "scale": args.scale, "min_len": params["min_len"],
                    "max_occ": params["max_occ"], "sa_rate": params["sa_rate"], "kmer_k": args.kmer_k},
@@ -796,7 +796,7 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": value, "unit": "reads/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "scale": args.scale, "reads_per_step": n_reads,
                    "pairs_per_step": n_reads // 2, "min_len": params["min_len"], "max_occ": params["max_occ"],
