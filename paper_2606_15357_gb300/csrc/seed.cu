@@ -29,7 +29,7 @@ struct SlotRec {
     u32 qbeg, qend, k, kr, s;
     u32 pos;   // the text position of the one occurrence when the kernel found it, else NOPOS
 };
-constexpr u32 NOPOS = 0xFFFFFFFFu;   // no known position (and, in a row list, a row not to walk)
+constexpr u32 NOPOS = 0xFFFFFFFFu;   // no known position (and, in a row list given to k_locate, a row to skip)
 
 // Scratch slots: a read of len bases owns len/16 + 8 slots (about 17 for 150 bases).
 constexpr u64 SLOT_DIV = 16, SLOT_EXTRA = 8;
@@ -920,7 +920,7 @@ __global__ void __launch_bounds__(256, D == 8 ? 2 : 1) k_locate(DevIndex I, cons
 #pragma unroll
         for (int d = 0; d < D; ++d) {
             const bool on = (live >> d) & 1u;
-            const bool skip = row[d] == NOPOS;   // a hit already written (position known)
+            const bool skip = row[d] == NOPOS;   // a row to skip (its hit is written elsewhere)
             const bool sampled = !skip && (POW2 ? (row[d] & rmask) == 0 : row[d] % r == 0);
             const bool st = on && (skip || sampled || row[d] == prim || steps[d] > n);
             sv[d] = 0;
