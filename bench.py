@@ -744,12 +744,20 @@ def run_gpu(args):
             mb.mb_locate(idx, out_h, m3, opts=opts, hits=hits_h, cap=nh3)
         torch.cuda.synchronize()
         dt2 = max_over_ranks(time.time() - t0, pg)
+        # the end-to-end call must return exactly what the device-timed forms return (the plain
+        # launches above, which equal the graph form when `same` holds)
+        m2, nh2 = mb.seed_locate(idx, seq_h, off_h, opts=eopts, out=out_h, cap=m, hits=hits_h, hits_cap=nh)
+        e2e_same = (m2, nh2) == (m, nh) and out_h.numpy().tobytes() == out[:m * 48].cpu().numpy().tobytes() and \
+            np.array_equal(hits_h[:nh].numpy(), hits[:nh].cpu().numpy())
+        if not (e2e_same and same):
+            raise SystemExit(f"bench: forms disagree (graph == plain: {same}, mb_seed_locate == plain: {e2e_same})")
         e2e = {"value": ws * k2 * n_reads / dt, "unit": "reads/s",
                "h2d_bytes_per_step": int(seq_h.numel() + off_h.numel() * 8),
                "d2h_bytes_per_step": int(m * 48 + nh * 4),
                "call": "mb_seed_locate (pinned host buffers, 4M-read chunks seeded on two streams, the batch located at once)",
                "two_calls_reads_per_s": ws * k2 * n_reads / dt2,
-               "note": "two_calls = mb_seed_batch + mb_locate on host buffers (the records are staged back in)"}
+               "note": "two_calls = mb_seed_batch + mb_locate on host buffers (the records are staged back in)",
+               "identical_output": bool(e2e_same)}
         log(f"e2e: {e2e}")
 
     rescue = None

@@ -6,10 +6,9 @@
  *  - Occurrence blocks as the paper lays them out for a 64-byte cache line (Section 2.2): per
  *    128 BWT rows, the counts of A, C, G, T before the block (4 x u64) and the 128 symbols at 2
  *    bits (4 x u64).  The $ row is stored as A and left out of the counts.
- *  - Algorithm 3 (BatchFindSMEM) over a batch of reads with one FIFO queue; whenever an entry is
- *    pushed, the blocks holding the two rows its next extension reads are prefetched (the
- *    prefetch of Section 2.5 for Algorithm 3), so that by the time the entry reaches the head of
- *    the queue its data is in cache.
+ *  - Algorithm 3 over a batch of reads that take turns, one memory access per read per turn;
+ *    after its turn a read prefetches the blocks holding the two rows its next extension reads
+ *    (the prefetching of Section 2.5), so that by its next turn the data is in cache.
  *  - The ds-intervals of all 10-mers precomputed (Section 2.5); a stage-1 entry that starts from
  *    the empty interval takes the 10 backward steps as one table lookup.  A failing 10-mer
  *    restarts stage 1 at its second base; stage 3 tries the table once and steps otherwise.
@@ -111,90 +110,123 @@ inline u64 lf(const Index &X, u64 x) {   // x is not the $ row
 
 struct Rec { u32 read, qbeg, qend; u64 k, kr, s; };
 
-// Algorithm 3 over reads [r0, r1) with one FIFO queue and prefetching; records per read in order
-void batch_find_smem(const Index &X, const u8 *seq, const u64 *off, u32 r0, u32 r1, u32 l, u32 c,
-                     std::vector<Rec> &out) {
-    struct E { u8 u, tried; u32 rd; int i, j; DS v; };
-    const DS empty{0, 0, X.n};
-    std::vector<E> ring(r1 - r0 + 1);
-    size_t head = 0, tail = 0, size = 0;
-    const size_t cap = ring.size();
-    auto base = [&](u32 rd, int j) -> u32 { return seq[off[rd] + (u64)j]; };
-    auto len = [&](u32 rd) -> int { return (int)(off[rd + 1] - off[rd]); };
-    auto push = [&](E e) {
-        // prefetch what this entry's next extension reads: rows k, k+s backwards, k', k'+s forwards
-        const u64 p = e.u == 2 ? e.v.kr : e.v.k;
-        if (e.v.s != X.n) {
-            prefetch_row(X, p);
-            prefetch_row(X, p + e.v.s);
-        }
-        ring[tail] = e;
-        tail = tail + 1 == cap ? 0 : tail + 1;
-        ++size;
+// Where one read stands in Algorithm 3: stage u (1: checking the window P[i, j] backwards from
+// j, 2: extending P[i, j) forwards, 3: looking backwards from j for the next start), the bounds
+// and the ds-interval so far.  `tried`: stage 3 already consulted the 10-mer table.
+struct Cursor {
+    u32 rd;
+    u8 u, tried;
+    int i, j;
+    DS v;
+};
+
+// Moves read e through Algorithm 3 up to and including its next memory access (one extension,
+// or one table lookup plus at most one extension) and reports it; returns false when the read
+// has no work left.  SMEMs found on the way go to `out`.
+//
+// The 10-mer table (Section 2.5) replaces the first 10 backward steps from the empty interval.
+// A failing 10-mer in stage 1 restarts the window at its second base (no window starting at or
+// before its first base can match); stage 3 needs the exact failing base, so it tries the table
+// once and steps otherwise.
+bool advance(const Index &X, const u8 *P, int L, u32 l, u32 c, Cursor &e, std::vector<Rec> &out) {
+    const DS whole{0, 0, X.n};
+    const int K = (int)KTAB;
+    auto restart = [&](int x) {   // stage 1 at the window starting at x
+        e.u = 1;
+        e.tried = 0;
+        e.i = x;
+        e.j = x + (int)l - 1;
+        e.v = whole;
     };
-    std::vector<std::vector<Rec>> per(r1 - r0);
-    auto emit = [&](const E &e) { per[e.rd - r0].push_back(Rec{e.rd, (u32)e.i, (u32)e.j, e.v.k, e.v.kr, e.v.s}); };
-    // k-mer code of P[x, x+10), base t in bits 2t; false if it holds an N
-    auto kmer_code = [&](u32 rd, int x, u32 &code) {
-        u32 v = 0;
-        for (u32 t = 0; t < KTAB; ++t) {
-            const u32 b = base(rd, x + (int)t);
-            if (b > 3) return false;
-            v |= b << (2 * t);
+    for (;;) {
+        if (e.u == 1 && e.j < e.i) {            // the window matches: extend it forwards
+            e.u = 2;
+            e.j = e.i + (int)l;
+            continue;
         }
-        code = v;
-        return true;
-    };
-    // Algorithm 3's BackStep, with the table for the first 10 steps from the empty interval
-    auto back_step = [&](E e) {
-        // stage 1 may use all bases down to i; stage 3 stops above i, so its k-mer must end there
-        const bool fits = e.u == 1 ? e.j - (int)KTAB + 1 >= e.i : e.j - (int)KTAB + 1 > e.i;
+        if (e.u == 3 && e.j <= e.i) {           // every base down to i + 1 extends: next start i + 1
+            restart(e.i + 1);
+            continue;
+        }
+        if (e.u == 2) {
+            if (e.j == L) {                     // the match reaches the end of the read
+                out.push_back(Rec{e.rd, (u32)e.i, (u32)e.j, e.v.k, e.v.kr, e.v.s});
+                return false;
+            }
+            const DS w = forward_ext(X, e.v, P[e.j]);
+            if (w.s >= c) {
+                e.v = w;
+                ++e.j;
+            } else {                            // the SMEM is P[i, j); look back from P[j]
+                out.push_back(Rec{e.rd, (u32)e.i, (u32)e.j, e.v.k, e.v.kr, e.v.s});
+                e.u = 3;
+                e.tried = 0;
+                e.v = whole;
+            }
+            return true;
+        }
+        // stages 1 and 3: one backward extension by P[j], the first K of them from the table
+        const bool fits = e.u == 1 ? e.j - K + 1 >= e.i : e.j - K + 1 > e.i;
         if (e.v.s == X.n && l >= KTAB && fits && (e.u == 1 || !e.tried)) {
-            u32 code;
-            if (kmer_code(e.rd, e.j - (int)KTAB + 1, code)) {
+            u32 code = 0;
+            bool ok = true;
+            for (int t = 0; t < K && ok; ++t) {
+                const u32 b = P[e.j - K + 1 + t];
+                ok = b <= 3;
+                code |= (b & 3u) << (2 * t);
+            }
+            if (ok) {
                 const u64 *t = &X.kmer[3 * (u64)code];
                 if (t[2] >= c) {
                     e.v = DS{t[0], t[1], t[2]};
-                    e.j -= (int)KTAB;
-                    push(e);
-                    return;
+                    e.j -= K;
+                    return true;
                 }
-                if (e.u == 1) {   // no window starting at or before the k-mer's first base matches
-                    const int x = e.j - (int)KTAB + 1;
-                    if (x + (int)l < len(e.rd)) push(E{1, 0, e.rd, x + 1, x + (int)l, empty});
-                    return;
+                if (e.u == 1) {
+                    const int x = e.j - K + 1;
+                    if (x + (int)l >= L) return false;
+                    restart(x + 1);
+                    return true;
                 }
-                e.tried = 1;      // stage 3: the exact restart needs single steps
+                e.tried = 1;
             }
         }
-        const DS w = backward_ext(X, e.v, base(e.rd, e.j));
-        if (w.s >= c) push(E{e.u, e.tried, e.rd, e.i, e.j - 1, w});
-        else if (e.j + (int)l < len(e.rd)) push(E{1, 0, e.rd, e.j + 1, e.j + (int)l, empty});
-    };
+        const DS w = backward_ext(X, e.v, P[e.j]);
+        if (w.s >= c) {
+            e.v = w;
+            --e.j;
+            return true;
+        }
+        if (e.j + (int)l >= L) return false;    // no window fits after the failing base
+        restart(e.j + 1);
+        return true;
+    }
+}
+
+// Algorithm 3 over reads [r0, r1), batched as in Section 2.5: the reads take turns, one memory
+// access each per turn, and after its turn a read prefetches the blocks its next extension reads
+// (rows k and k+s backwards, k' and k'+s forwards), so that the data is in cache by its next turn
+// while the other reads work.  Records per read in ascending qbeg.
+void batch_find_smem(const Index &X, const u8 *seq, const u64 *off, u32 r0, u32 r1, u32 l, u32 c,
+                     std::vector<Rec> &out) {
+    std::vector<std::vector<Rec>> per(r1 - r0);
+    std::vector<Cursor> turn;
+    turn.reserve(r1 - r0);
     for (u32 rd = r0; rd < r1; ++rd)
-        if ((int)l - 1 < len(rd)) push(E{1, 0, rd, 0, (int)l - 1, empty});
-    while (size) {
-        E e = ring[head];
-        head = head + 1 == cap ? 0 : head + 1;
-        --size;
-        if (e.u == 1) {
-            if (e.j < e.i) push(E{2, 0, e.rd, e.i, e.i + (int)l, e.v});
-            else back_step(e);
-        } else if (e.u == 2) {
-            if (e.j == len(e.rd)) {
-                emit(e);
-                continue;
+        if ((u64)l <= off[rd + 1] - off[rd]) turn.push_back(Cursor{rd, 1, 0, 0, (int)l - 1, DS{0, 0, X.n}});
+    while (!turn.empty()) {
+        size_t kept = 0;
+        for (size_t q = 0; q < turn.size(); ++q) {
+            Cursor e = turn[q];
+            if (!advance(X, seq + off[e.rd], (int)(off[e.rd + 1] - off[e.rd]), l, c, e, per[e.rd - r0])) continue;
+            if (e.v.s != X.n) {
+                const u64 p = e.u == 2 ? e.v.kr : e.v.k;
+                prefetch_row(X, p);
+                prefetch_row(X, p + e.v.s);
             }
-            const DS w = forward_ext(X, e.v, base(e.rd, e.j));
-            if (w.s >= c) push(E{2, 0, e.rd, e.i, e.j + 1, w});
-            else {
-                emit(e);
-                push(E{3, 0, e.rd, e.i, e.j, empty});
-            }
-        } else {
-            if (e.j <= e.i) push(E{1, 0, e.rd, e.j + 1, e.j + (int)l, empty});
-            else back_step(e);
+            turn[kept++] = e;
         }
+        turn.resize(kept);
     }
     for (auto &v : per) out.insert(out.end(), v.begin(), v.end());
 }

@@ -179,7 +179,9 @@ int mb_reseed(const mb_index *idx, const uint8_t *seq, const uint64_t *off, uint
  *   A batch whose scratch need exceeds 64 MiB (about 145,000 reads of 150 bases, less with many
  *   SMEMs) is rejected with MB_ERR_ARG and a message naming the need; split the batch.
  *   The first call on a device looks up the array's device address (cudaGetSymbolAddress) for
- *   that device; make that first call before any stream capture.
+ *   that device and keeps it for later calls; make that first call before any stream capture.
+ *   The kept address belongs to the device's current context: after cudaDeviceReset on that
+ *   device it is stale, so do not call this entry point again in that process after a reset.
  *   All calls share the one array and it keeps the last call's contents: calls whose work
  *   overlaps on the GPU (from other streams or host threads) race and must not be issued;
  *   calls on one stream are ordered.

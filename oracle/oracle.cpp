@@ -35,7 +35,6 @@
 #include <string.h>
 #include <algorithm>
 #include <atomic>
-#include <deque>
 #include <vector>
 #include <omp.h>
 
@@ -263,12 +262,6 @@ void smem_def_read(const Index &X, const u8 *P, u32 m, u32 rid, u32 l, u32 c, st
     }
 }
 
-/*
- * Algorithm 3, BatchFindSMEM, with one FIFO queue over all reads, and its
- * helper BackStep.  Queue entries (u, read, i, j, (k,k',s)); u = stage.
- */
-struct QE { u8 u; u32 rd; int64_t i, j; DS v; };
-
 /* Work of Algorithm 1 calls, for the measurement's algorithmic bytes: one step per call with a
  * base (an N reads nothing); the occurrence values a call needs sit at rows p and p+s of the
  * strand it extends (p = k backwards, k' forwards), i.e. in one block of `block_rows` rows when
@@ -280,41 +273,88 @@ void count_ext(Work *w, u64 p, u64 s, u8 a) {
     w->blocks += (p / w->block_rows == (p + s) / w->block_rows) ? 1 : 2;
 }
 
-void smem_alg3(const Index &X, const u8 *seq, const u64 *off, u32 nr, u32 l, u32 c,
-               std::vector<std::vector<Smem>> &out, Work *work = nullptr) {
-    std::deque<QE> Q;
-    const DS empty{0, 0, X.n};
-    auto P = [&](u32 rd, int64_t j) -> u8 { u8 b = seq[off[rd] + j]; return b < 4 ? (u8)(b + 1) : 5; };
-    auto len = [&](u32 rd) -> int64_t { return (int64_t)(off[rd + 1] - off[rd]); };
-    for (u32 rd = 0; rd < nr; ++rd)
-        if ((int64_t)l - 1 < len(rd)) Q.push_back(QE{1, rd, 0, (int64_t)l - 1, empty});
-    auto back_step = [&](const QE &e) {
-        count_ext(work, e.v.k, e.v.s, P(e.rd, e.j));
-        DS w = backward_ext(X, e.v, P(e.rd, e.j));
-        if (w.s >= c) Q.push_back(QE{e.u, e.rd, e.i, e.j - 1, w});
-        else if (e.j + (int64_t)l < len(e.rd)) Q.push_back(QE{1, e.rd, e.j + 1, e.j + (int64_t)l, empty});
-    };
-    while (!Q.empty()) {
-        QE e = Q.front(); Q.pop_front();
-        if (e.u == 1) {                       // stage 1: backward extension
-            if (e.j < e.i) Q.push_back(QE{2, e.rd, e.i, e.i + (int64_t)l, e.v});
-            else back_step(e);
-        } else if (e.u == 2) {                // stage 2: forward extension
-            if (e.j == len(e.rd)) {
-                out[e.rd].push_back(Smem{e.rd, (u32)e.i, (u32)e.j, 0, e.v.k, e.v.kr, e.v.s});
-                continue;
-            }
-            count_ext(work, e.v.kr, e.v.s, P(e.rd, e.j));
-            DS w = forward_ext(X, e.v, P(e.rd, e.j));
-            if (w.s >= c) Q.push_back(QE{2, e.rd, e.i, e.j + 1, w});
-            else {
-                out[e.rd].push_back(Smem{e.rd, (u32)e.i, (u32)e.j, 0, e.v.k, e.v.kr, e.v.s});
-                Q.push_back(QE{3, e.rd, e.i, e.j, empty});
-            }
-        } else {                              // stage 3: backward extension again
-            if (e.j <= e.i) Q.push_back(QE{1, e.rd, e.j + 1, e.j + (int64_t)l, empty});
-            else back_step(e);
+/*
+ * Algorithm 3 (Section 2.5) for one read P of m bases (oracle codes, 5 = N).  Algorithm 3 keeps
+ * one queue entry per read at any time, so a read's extensions happen in a fixed order whatever
+ * the other reads do; the batch, the queue and the prefetching only change when they happen.
+ * Here each read runs alone, start to end, as three nested scans over the start i of the next
+ * candidate match:
+ *   - check that the window P[i, i+l) occurs at least c times by extending backwards from its
+ *     last base; at a failing base t no window starting at or before t can match, so the scan
+ *     moves on to i = t + 1 (or the read ends when that window would pass the end of P);
+ *   - extend the match forwards as long as it occurs at least c times and report it as an SMEM
+ *     with the ds-interval of its last successful extension;
+ *   - from the base e where the forward extension failed, extend backwards over P[e], P[e-1], ...
+ *     down to just above i; the base t where this fails (or i itself) bounds the next start:
+ *     every match holding P[e] starts after t, and the scan goes back to the window check at
+ *     t + 1.
+ * The extensions are BackwardExt / ForwardExt of Algorithm 1, in the order Algorithm 3 makes
+ * them for this read, so the work counts are Algorithm 3's.
+ */
+void smem_alg3_read(const Index &X, const u8 *P, int64_t m, u32 rid, u32 l, u32 c, std::vector<Smem> &out,
+                    Work *work) {
+    const DS whole{0, 0, X.n};
+    const int64_t L = (int64_t)l;
+    if (L - 1 >= m) return;                       // the read is shorter than l
+    int64_t i = 0;
+    for (;;) {
+        /* window check of P[i, i+l) */
+        DS v = whole;
+        int64_t t = i + L - 1;
+        for (; t >= i; --t) {
+            count_ext(work, v.k, v.s, P[t]);
+            const DS w = backward_ext(X, v, P[t]);
+            if (w.s < c) break;
+            v = w;
         }
+        if (t >= i) {                             // failed at base t
+            if (t + L < m) { i = t + 1; continue; }
+            return;
+        }
+        /* forward extension of the match P[i, e) */
+        int64_t e = i + L;
+        while (e < m) {
+            count_ext(work, v.kr, v.s, P[e]);
+            const DS w = forward_ext(X, v, P[e]);
+            if (w.s < c) break;
+            v = w;
+            ++e;
+        }
+        out.push_back(Smem{rid, (u32)i, (u32)e, 0, v.k, v.kr, v.s});
+        if (e == m) return;
+        /* the next start: backwards from the failing base e, not below i + 1 */
+        v = whole;
+        for (t = e; t > i; --t) {
+            count_ext(work, v.k, v.s, P[t]);
+            const DS w = backward_ext(X, v, P[t]);
+            if (w.s < c) break;
+            v = w;
+        }
+        if (t > i && t + L >= m) return;          // failed at t, and no window fits after it
+        i = t + 1;
+    }
+}
+
+/* Algorithm 3 over a batch: every read on its own (see smem_alg3_read), reads in parallel. */
+void smem_alg3(const Index &X, const u8 *seq, const u64 *off, u32 nr, u32 l, u32 c,
+               std::vector<std::vector<Smem>> &out, Work *work = nullptr, int threads = 0) {
+    u64 steps = 0, blocks = 0;
+    const u64 br = work ? work->block_rows : 64;
+#pragma omp parallel for num_threads(threads > 0 ? threads : omp_get_max_threads()) schedule(dynamic, 16) \
+    reduction(+ : steps, blocks)
+    for (u32 rd = 0; rd < nr; ++rd) {
+        const int64_t m = (int64_t)(off[rd + 1] - off[rd]);
+        std::vector<u8> P(m);
+        for (int64_t q = 0; q < m; ++q) P[q] = seq[off[rd] + q] < 4 ? (u8)(seq[off[rd] + q] + 1) : 5;
+        Work w;
+        w.block_rows = br;
+        smem_alg3_read(X, P.data(), m, rd, l, c, out[rd], work ? &w : nullptr);
+        steps += w.steps;
+        blocks += w.blocks;
+    }
+    if (work) {
+        work->steps += steps;
+        work->blocks += blocks;
     }
 }
 

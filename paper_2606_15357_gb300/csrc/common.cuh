@@ -266,6 +266,13 @@ void mb_plan_arrays(const mb_plan *p, const mb_smem **smem, const u32 **hits, u6
 int mb_plan_run_seed(mb_plan *p, const uint8_t *seq, const uint64_t *off, uint32_t n_reads, const uint8_t *mate,
                      cudaStream_t st);
 const u32 *mb_plan_known(const mb_plan *p);
+// SMEMs of reads already in device memory (what mb_seed_batch does after staging its inputs):
+// read r is dseq[doff[r], doff[r+1]), o0 = doff[0] and o1 = doff[n_reads] as host values, dlc
+// an optional per-read (l | c << 16); out may be host or device.  No pointer is classified
+// except out.
+int mb_seed_device(const mb_index *idx, const u8 *dseq, const u64 *doff, u32 n_reads, const u8 *dmate,
+                   const u32 *dlc, u64 o0, u64 o1, const mb_opts *opts, cudaStream_t st, mb_smem *out, u64 cap,
+                   u64 *n_out, u64 *n_hits);
 int mb_locate_records(const mb_index *idx, const mb_smem *sm, u64 n_smem, const u32 *known, u32 *hits, u64 n_hits,
                       u32 depth, cudaStream_t st);
 // build flags of an index (MB_BS3 for the 3-base bisulfite index)

@@ -300,7 +300,10 @@ extern "C" int mb_seed_locate(const mb_index *idx, const uint8_t *seq, const uin
                 const u64 *doff;
                 inputs(x.chunk, x, dseq, doff, dmate);
                 MB_TRY(fsm.alloc(ns * sizeof(mb_smem) + 64, x.st));
-                MB_TRY(mb_seed_batch(idx, dseq, doff, c.nr, dmate, opts, x.st, fsm.as<mb_smem>(), ns, &ns, &nh));
+                // the chunk's inputs are device arrays (dseq may point before the stage's copy,
+                // so nothing here is classified by address)
+                MB_TRY(mb_seed_device(idx, dseq, doff, c.nr, dmate, nullptr, c.o0, c.o1, opts, x.st,
+                                      fsm.as<mb_smem>(), ns, &ns, &nh));
                 psm = fsm.as<mb_smem>();
                 pknown = nullptr;
             }

@@ -1108,7 +1108,7 @@ int launch_smem(const SmemArgs &a, bool count, bool queue, int block, cudaStream
 // ============================================================================ host entry points
 // The seeding pipeline on device inputs (seq, off, mate, and optionally a per-read (l | c << 16));
 // out may be host or device.
-static int seed_device(const mb_index *idx, const u8 *dseq, const u64 *doff, u32 n_reads, const u8 *dmate,
+int mb_seed_device(const mb_index *idx, const u8 *dseq, const u64 *doff, u32 n_reads, const u8 *dmate,
                        const u32 *dlc, u64 o0, u64 o1, const mb_opts *opts, cudaStream_t st, mb_smem *out, u64 cap,
                        u64 *n_out, u64 *n_hits) {
     u32 l, c, max_occ, flags;
@@ -1220,7 +1220,7 @@ extern "C" int mb_seed_batch(const mb_index *idx, const uint8_t *seq, const uint
     }
     if (mate) MB_TRY(mb_stage_in(mate, n_reads, st, bmate, &dmate));
 
-    return seed_device(idx, (const u8 *)dseq, (const u64 *)doff, n_reads, (const u8 *)dmate, nullptr, o0, o1, opts,
+    return mb_seed_device(idx, (const u8 *)dseq, (const u64 *)doff, n_reads, (const u8 *)dmate, nullptr, o0, o1, opts,
                        st, out, cap, n_out, n_hits);
 }
 
@@ -1886,7 +1886,7 @@ extern "C" int mb_reseed(const mb_index *idx, const uint8_t *seq, const uint64_t
     DevBuf bout;
     const bool out_dev = mb_is_device_ptr(out);
     u64 need = 0, nh = 0;
-    int rc = seed_device(idx, bwseq.as<u8>(), bwoff.as<u64>(), (u32)nw, wm, blc.as<u32>(), 0, wbases, &o, st,
+    int rc = mb_seed_device(idx, bwseq.as<u8>(), bwoff.as<u64>(), (u32)nw, wm, blc.as<u32>(), 0, wbases, &o, st,
                          nullptr, 0, &need, &nh);
     if (rc != MB_OK && rc != MB_ERR_CAPACITY) return rc;
     *n_out = need;
@@ -1898,7 +1898,7 @@ extern "C" int mb_reseed(const mb_index *idx, const uint8_t *seq, const uint64_t
         MB_TRY(bout.alloc(need * sizeof(mb_smem), st));
         dout = bout.as<mb_smem>();
     }
-    MB_TRY(seed_device(idx, bwseq.as<u8>(), bwoff.as<u64>(), (u32)nw, wm, blc.as<u32>(), 0, wbases, &o, st, dout,
+    MB_TRY(mb_seed_device(idx, bwseq.as<u8>(), bwoff.as<u64>(), (u32)nw, wm, blc.as<u32>(), 0, wbases, &o, st, dout,
                        need, &need, &nh));
     k_win_fix<<<grid_for(need, 256), 256, 0, st>>>(dout, need, binfo.as<uint2>());
     MB_KCHECK();

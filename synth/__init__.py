@@ -213,3 +213,39 @@ def rescue_pairs(ref: np.ndarray, n_pairs: int, seed: int, read_len: int = 150, 
     roff = np.arange(n_pairs + 1, dtype=np.uint64) * read_len
     woff = np.arange(n_pairs + 1, dtype=np.uint64) * win_len
     return reads_out, roff, wins_out, woff
+
+
+def planted_copies(unit_len: int, copies, spacer: int, seed: int):
+    """A reference holding copies[u] exact copies of random unit u (`unit_len` bases each, one
+    unit per entry of `copies`), in random order, separated (and flanked) by random spacers of
+    `spacer` bases, all bases drawn uniformly (numpy, seeded).  Returns (reference, units, starts): units[u] is the u-th unit's bases and
+    starts[u] the sorted reference positions of its copies.  With long random units and spacers
+    no unit occurs anywhere else, or on the other strand, except with negligible probability, so a
+    read equal to unit u occurs exactly copies[u] times in R . revcomp(R)."""
+    rng = np.random.default_rng(seed)
+    n_units = len(copies)
+    units = rng.integers(0, 4, (n_units, unit_len)).astype(np.uint8)
+    order = rng.permutation(np.repeat(np.arange(n_units), copies))
+    parts, starts, pos = [], [[] for _ in range(n_units)], 0
+    for u in order:
+        sp = rng.integers(0, 4, spacer).astype(np.uint8)
+        parts.append(sp)
+        pos += spacer
+        starts[u].append(pos)
+        parts.append(units[u])
+        pos += unit_len
+    parts.append(rng.integers(0, 4, spacer).astype(np.uint8))
+    return np.concatenate(parts), units, [np.array(s, dtype=np.uint64) for s in starts]
+
+
+def junction_read(ref_len: int, half: int, seed: int, filler_len: int = 0):
+    """A reference whose first `half` bases are A/T only, and a 2*half-base read that ends with the
+    reference's last `half` bases and continues with its first `half` bases.  Under the bisulfite
+    conversion of read 1 (C -> T) the read spells the text across the boundary between the
+    C-to-T copy and the G-to-A copy of the 3-base text CT(R) GA(R) ..., so its one occurrence
+    spans two copies.  Returns (reference, read)."""
+    rng = np.random.default_rng(seed)
+    ref = rng.integers(0, 4, ref_len).astype(np.uint8)
+    ref[:half] = np.where(rng.random(half) < 0.5, 0, 3).astype(np.uint8)
+    read = np.concatenate([ref[ref_len - half:], ref[:half]]).astype(np.uint8)
+    return ref, read

@@ -1,10 +1,19 @@
-"""Parity at full workload sizes, in the launch configuration bench.py times.
+"""Parity at full workload sizes.
 
-The GPU builds the whole index and seeds the whole read batch (device buffers, one
-mb_seed_batch + one mb_locate call); the CPU oracle builds its own index by sorting
-suffixes and checks the full suffix array, the block counts, the k-mer table, and a
-seeded random sample of the reads (every SMEM record and every hit of each sampled
-read).  Minutes per test: marked slow as well as gpu.
+The GPU builds the whole index and seeds the whole read batch; the CPU oracle builds its own
+index by sorting suffixes and checks the full suffix array, the block counts, the k-mer table,
+and a seeded random sample of the reads (every SMEM record and every hit of each sampled read).
+
+- The 1 Gbp workload runs twice: with the binding's defaults (10-mer table, fixed read ranges
+  per warp, one locate walk per lane; one mb_seed_batch + one mb_locate call), and in exactly
+  the launch configuration bench.py times (14-mer table, device work queue, 512 threads per
+  block, 16 locate walks per lane) through all three forms the bench runs: the plain calls, the
+  captured CUDA graph of a plan, and mb_seed_locate on pinned host buffers.  The three must be
+  identical byte for byte, and 1% of the reads must match the oracle.
+- The mixed-length workload (100 Mbp, 200,000 reads of 100 bp - 10 kb) runs in the batched
+  form bench.py times (autotuned plan, replayed graph) and in the work-queue shape; 5% of its
+  reads are checked against the oracle.
+Minutes per test: marked slow as well as gpu.
 """
 import os
 
@@ -96,16 +105,108 @@ def check_sampled_reads(sm, hits, X, rd, frac, seed, params):
     return len(pick), len(g), len(gh)
 
 
-def test_workload3_1gbp_full_index_and_sampled_reads(mb):
-    """1 Gbp repeat-rich reference, 10M pairs: full SA / blocks / k-mer sample and 1% of reads."""
+@pytest.fixture(scope="module")
+def w3(mb):
+    """The 1 Gbp workload and the oracle's index of it (built once for both 1 Gbp tests)."""
     ref, rd, params = synth.workload(3)
-    G = mb.mb_index_build(dev(ref))
     X = oracle.Index(ref, threads=os.cpu_count())
+    yield ref, rd, params, X
+    del X
+
+
+def test_workload3_1gbp_full_index_and_sampled_reads(mb, w3):
+    """1 Gbp repeat-rich reference, 10M pairs: full SA / blocks / k-mer sample and 1% of reads."""
+    ref, rd, params, X = w3
+    G = mb.mb_index_build(dev(ref))
     check_index(G, X, sample_kmers=200_000)
     G.drop_sa()
     sm, hits = gpu_seed_all(mb, G, rd)
     n, m, h = check_sampled_reads(sm, hits, X, rd, 0.01, 0x6D62, params)
     print(f"checked {n} reads, {m} SMEMs, {h} hits")
+    G.free()
+    torch.cuda.empty_cache()
+
+
+# the launch configuration bench.py times on the 1 Gbp workload
+BENCH_KMER_K = 14
+BENCH_OPTS = dict(block_size=512, prefetch_depth=16)
+
+
+def test_workload3_1gbp_in_the_bench_configuration(mb, w3):
+    """The bench's exact configuration: 14-mer table, work queue, block 512, 16 walks per lane;
+    plain calls == captured plan graph == mb_seed_locate on pinned host buffers, and 1% of the
+    reads against the oracle."""
+    ref, rd, params, X = w3
+    G = mb.mb_index_build(dev(ref), opts=dict(kmer_k=BENCH_KMER_K))
+    e = G.export(kmer=True, kmer_k=BENCH_KMER_K)
+    words = np.sort(np.random.default_rng(0x6D67).choice(4 ** BENCH_KMER_K, 50_000, replace=False))
+    pats = np.stack([(words >> (2 * t)) & 3 for t in range(BENCH_KMER_K)], axis=1).astype(np.uint8)
+    assert np.array_equal(e["kmer"].reshape(-1, 3)[words], X.ds_intervals(pats).astype(np.uint32))
+    del e
+    G.drop_sa()
+    opts = dict(BENCH_OPTS, flags=mb.MB_BATCHED)
+    seq, off = dev(rd.seq), dev(rd.off)
+    # plain calls in the bench's launch shape
+    cap = 4 * rd.n
+    out = torch.empty(cap * 48, dtype=torch.uint8, device="cuda")
+    _, m, nh = mb.mb_seed_batch(G, seq, off, opts=opts, out=out, cap=cap)
+    hits = torch.empty(max(nh, 1), dtype=torch.int32, device="cuda")
+    mb.mb_locate(G, out, m, opts=opts, hits=hits, cap=nh)
+    plain_sm = out[:m * 48].cpu().numpy()
+    plain_h = hits[:nh].cpu().numpy().view(np.uint32)
+    del out, hits
+    # the captured CUDA graph of a plan, replayed twice
+    P = mb.Plan(G, rd.n, len(rd.seq), m + 1024, nh + 1024, opts=opts)
+    P.capture(seq, off)
+    P.replay()
+    P.replay()
+    gsm, gh = P.result()
+    P.free()
+    assert gsm.tobytes() == plain_sm.tobytes()
+    assert np.array_equal(gh, plain_h)
+    del plain_sm, plain_h, seq, off
+    torch.cuda.empty_cache()
+    # end to end through mb_seed_locate on pinned host buffers
+    seq_h = torch.from_numpy(rd.seq).pin_memory()
+    off_h = torch.from_numpy(rd.off.view(np.int64)).pin_memory()
+    out_h = torch.empty(m * 48, dtype=torch.uint8).pin_memory()
+    hits_h = torch.empty(max(nh, 1), dtype=torch.int32).pin_memory()
+    m2, nh2 = mb.seed_locate(G, seq_h, off_h, opts=opts, out=out_h, cap=m, hits=hits_h, hits_cap=nh)
+    assert (m2, nh2) == (m, nh)
+    assert out_h.numpy().tobytes() == gsm.tobytes()
+    assert np.array_equal(hits_h[:nh].numpy().view(np.uint32), gh)
+    del out_h, hits_h, seq_h, off_h
+    n, ms, h = check_sampled_reads(gsm, gh, X, rd, 0.01, 0x6D66, params)
+    print(f"bench configuration: {m} SMEMs, {nh} hits; checked {n} reads, {ms} SMEMs, {h} hits")
+    G.free()
+    torch.cuda.empty_cache()
+
+
+def test_workload4_full_size_batched_form_sampled_reads(mb):
+    """Mixed lengths at full size (100 Mbp, 200,000 reads of 100 bp - 10 kb): the autotuned plan
+    as a replayed graph and the work-queue shape give the same output, and 5% of the reads match
+    the oracle."""
+    ref, rd, params = synth.workload(4)
+    G = mb.mb_index_build(dev(ref))
+    G.drop_sa()
+    seq, off = dev(rd.seq), dev(rd.off)
+    sm, m, nh = mb.mb_seed_batch(G, seq, off, cap=4 * rd.n)
+    best, _ = mb.autotune(G, seq, off)
+    outs = []
+    for o in (best, mb.Opts(flags=mb.MB_BATCHED, block_size=512, prefetch_depth=16)):
+        P = mb.Plan(G, rd.n, len(rd.seq), m + 64, nh + 64, opts=o)
+        P.capture(seq, off)
+        P.replay()
+        outs.append(P.result())
+        P.free()
+    (a_sm, a_h), (b_sm, b_h) = outs
+    assert a_sm.tobytes() == b_sm.tobytes() and np.array_equal(a_h, b_h)
+    assert a_sm.tobytes() == sm.tobytes()
+    X = oracle.Index(ref, threads=os.cpu_count())
+    n, ms, h = check_sampled_reads(a_sm, a_h, X, rd, 0.05, 0x6D68, params)
+    print(f"mixed lengths: checked {n} reads, {ms} SMEMs, {h} hits")
+    G.free()
+    torch.cuda.empty_cache()
 
 
 def test_workload2_100mbp_full_index_and_sampled_reads(mb):

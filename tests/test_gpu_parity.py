@@ -332,6 +332,46 @@ def test_bisulfite_index_and_seeding(mb):
     assert np.array_equal(keep.astype(bool), oracle.bs_keep(ohits, qlen, rmate, len(ref)))
 
 
+def test_max_occ_boundary_planted(mb):
+    """Units planted exactly 500, 501 and 3 times: the default cap keeps s = 500 (located) and
+    flags s = 501 (no hits), on the GPU as in the oracle and by construction."""
+    ref, units, starts = synth.planted_copies(40, [500, 501, 3], 60, 0x6D6201)
+    G = mb.mb_index_build(ref)
+    X = oracle.Index(ref)
+    seq = units.reshape(-1)
+    off = np.arange(len(units) + 1, dtype=np.uint64) * 40
+    for max_occ in (500, 499, 501):
+        o = dict(max_occ=max_occ)
+        sm, m, nh = mb.mb_seed_batch(G, seq, off, opts=o)
+        hits, _ = mb.mb_locate(G, sm, m, opts=o, cap=nh)
+        compare_seed(sm, hits, X, seq, off, max_occ=max_occ)
+        assert sm["s"].tolist() == [500, 501, 3]
+        assert (sm["flags"] & 1).tolist() == [int(500 > max_occ), int(501 > max_occ), 0]
+    sm, m, nh = mb.mb_seed_batch(G, seq, off)
+    hits, _ = mb.mb_locate(G, sm, m, cap=nh)
+    assert np.array_equal(np.sort(hits[:500]).astype(np.uint64), starts[0])
+    assert np.array_equal(np.sort(hits[500:503]).astype(np.uint64), starts[2])
+
+
+def test_bisulfite_filter_drops_hit_spanning_two_copies(mb):
+    """A read-1 read planted across the C-to-T and G-to-A copies of the 3-base text: its one hit
+    spans both copies and the strand filter drops it; a control read inside the C-to-T copy is
+    kept (Section 2.9)."""
+    m, half = 5000, 20
+    ref, cross = synth.junction_read(m, half, 0x6D6202)
+    seq = np.concatenate([cross, ref[1000:1000 + 2 * half]]).astype(np.uint8)
+    off = np.array([0, 2 * half, 4 * half], dtype=np.uint64)
+    mate = np.array([1, 1], dtype=np.uint8)
+    o = dict(flags=mb.MB_BS3)
+    G = mb.mb_index_build(ref, opts=o)
+    sm, n_sm, nh = mb.mb_seed_batch(G, seq, off, mate=mate, opts=o)
+    hits, _ = mb.mb_locate(G, sm, n_sm, opts=o, cap=nh)
+    assert sm["s"].tolist() == [1, 1]
+    assert hits.tolist() == [m - half, 1000]
+    keep = mb.mb_bs_filter(G, sm, n_sm, mate, hits, nh)
+    assert keep.tolist() == [0, 1]
+
+
 def test_bisulfite_split(mb):
     """Section 2.9 T-to-C split on the GPU against the oracle: reads with 1-3% substitutions so
     that read C over reference T (read 1) and read G over reference A (read 2) occur; with the

@@ -135,6 +135,29 @@ def test_records_outgrow_the_plan(mb):
     assert np.array_equal(sm["k"].astype(np.uint64), osm["k"]) and np.array_equal(hits.astype(np.uint64), ohits)
 
 
+@pytest.mark.slow
+def test_late_chunk_outgrows_its_plan_at_a_large_offset(mb):
+    """Host buffers of 450 MB: five chunks of error-free reads (one SMEM each), then a chunk of
+    random reads with min_len 5 (dozens of SMEMs each, more than its plan holds) starting 375 MB
+    into the batch.  That chunk is seeded again by the allocating path on its device inputs; the
+    output equals mb_seed_batch + mb_locate on the whole batch."""
+    ref = synth.reference(200_000, 83)
+    n_chunk = 500_000
+    filler = synth.reads(ref, 5 * n_chunk, 84, mode=0, read_len=150)
+    rand = synth.reference(150 * n_chunk, 85)
+    seq = np.concatenate([filler.seq, rand]).astype(np.uint8)
+    off = np.concatenate([filler.off, filler.off[-1] + 150 * np.arange(1, n_chunk + 1, dtype=np.uint64)])
+    o = dict(min_len=5, max_occ=50)
+    G = mb.mb_index_build(ref)
+    sm, hits = mb.seed_locate(G, seq, off, opts=dict(o, chunk_reads=n_chunk))
+    last = sm["read"] >= 5 * n_chunk
+    assert int(off[5 * n_chunk]) == 375_000_000
+    assert last.sum() > 4 * n_chunk + 150 * n_chunk // 32 + 64   # more than the chunk's plan holds
+    psm, phits = mb.seed(G, seq, off, opts=o)
+    assert sm.tobytes() == psm.tobytes()
+    assert np.array_equal(hits, phits)
+
+
 def test_capacity_reports_both_totals(mb, repeat_rich):
     ref, rd, G = repeat_rich
     psm, phits = mb.seed(G, rd.seq, rd.off)

@@ -1,9 +1,12 @@
 """Served form: requests of mixed sizes (short pairs and long reads) submitted together are
 merged into launch groups that run concurrently; every request's records and hits must be
-exactly those of the plain entry points on that request alone."""
+exactly those of the plain entry points on that request alone, and those of the CPU oracle."""
+import os
+
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -40,11 +43,35 @@ def requests(ref, n, seed):
 def served(mb):
     ref = synth.repeat_rich_reference(2_000_000, 91, 0.3)
     G = mb.mb_index_build(ref)
-    return ref, G
+    X = oracle.Index(ref)
+    return ref, G, X
+
+
+def same_as_oracle(X, r, sm, hits, frac=1.0, seed=0):
+    """The served records and hits of request r equal the oracle's on r alone (every field of
+    every record, every hit); with frac < 1 only a seeded sample of the request's reads."""
+    pick = np.arange(r.n)
+    if frac < 1.0:
+        pick = np.sort(np.random.default_rng(seed).choice(r.n, max(1, int(r.n * frac)), replace=False))
+    sub = r.subset(pick)
+    osm, over, hoff, ohits = X.seed(sub.seq, sub.off)
+    keep = np.isin(sm["read"].astype(np.int64), pick)
+    g = sm[keep]
+    assert len(g) == len(osm)
+    assert np.array_equal(g["read"].astype(np.int64), pick[osm["read"].astype(np.int64)])
+    for f in ("qbeg", "qend", "k", "kr", "s"):
+        assert np.array_equal(g[f].astype(np.uint64), osm[f]), f
+    assert np.array_equal((g["flags"] & 1).astype(bool), over)
+    cnt = np.where(g["flags"] & 1, 0, g["s"]).astype(np.int64)
+    gh = np.concatenate([hits[int(a):int(a) + int(c)] for a, c in zip(g["hit_off"], cnt)]) if len(g) else \
+        np.zeros(0, np.uint32)
+    assert np.array_equal(gh.astype(np.uint64), ohits)
+    if frac >= 1.0:
+        assert np.array_equal(sm["hit_off"], hoff)
 
 
 def test_each_request_same_alone_and_in_the_mix(mb, served):
-    ref, G = served
+    ref, G, X = served
     reqs = requests(ref, 60, 5)
     srv = mb.Server(G, hbm_budget=2 << 30)
     tickets = [srv.submit(r.seq, r.off) for r in reqs]
@@ -58,10 +85,11 @@ def test_each_request_same_alone_and_in_the_mix(mb, served):
         assert sm.tobytes() == want_sm.tobytes()
         assert np.array_equal(hits, want_hits)
         assert lat > 0
+        same_as_oracle(X, r, sm, hits)
 
 
 def test_requests_arriving_while_others_run(mb, served):
-    ref, G = served
+    ref, G, X = served
     reqs = requests(ref, 30, 6)
     srv = mb.Server(G, hbm_budget=1 << 30)
     got = {}
@@ -79,11 +107,12 @@ def test_requests_arriving_while_others_run(mb, served):
         sm, hits, _ = srv.wait(tt)
         want_sm, want_hits = mb.seed(G, r.seq, r.off)
         assert sm.tobytes() == want_sm.tobytes() and np.array_equal(hits, want_hits)
+        same_as_oracle(X, r, sm, hits)
     srv.close()
 
 
 def test_oversize_request_rejected_and_timeout(mb, served):
-    ref, G = served
+    ref, G, X = served
     srv = mb.Server(G, hbm_budget=1 << 30)
     big_off = np.arange(0, 70000 * 10 + 1, 10, dtype=np.uint64)   # 70,000 reads > one slot
     with pytest.raises(mb.MbError) as ei:
@@ -101,3 +130,43 @@ def test_oversize_request_rejected_and_timeout(mb, served):
     want_sm, want_hits = mb.seed(G, r.seq, r.off)
     assert sm.tobytes() == want_sm.tobytes() and np.array_equal(hits, want_hits)
     srv.close()
+
+
+def config5_requests(ref, n, seed):
+    """Requests shaped like the served workload: 80% short (log-uniform 1-4,096 pairs of 2x150),
+    20% long (log-uniform 1-4,096 single reads of log-uniform 1-10 kb)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for q in range(n):
+        k = int(np.exp(rng.uniform(0, np.log(4096))))
+        if rng.random() < 0.8:
+            rd = synth.reads(ref, 2 * k, seed * 7919 + q, mode=1, read_len=150, sub_lo=0.001, sub_hi=0.01,
+                             indel=0.0001)
+        else:
+            rd = synth.reads(ref, k, seed * 7919 + q, mode=2, len_lo=1000, len_hi=10000, sub_lo=0.001,
+                             indel=0.0002)
+        out.append(rd)
+    return out
+
+
+@pytest.mark.slow
+def test_served_mix_on_100mbp_index_against_oracle(mb):
+    """An index far above L2 (the 100 Mbp repeat-rich reference) serving a stream of requests of
+    the served workload's shape, all submitted at once: every request equals the plain entry
+    points on it alone, and a seeded 5% of each request's reads equal the oracle."""
+    ref, _, _ = synth.workload(2)
+    G = mb.mb_index_build(ref)
+    G.drop_sa()
+    reqs = config5_requests(ref, 120, 0x6D69)
+    srv = mb.Server(G, hbm_budget=16 << 30)
+    tickets = [srv.submit(r.seq, r.off) for r in reqs]
+    results = [srv.wait(t) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    assert st["merged"] > 0
+    X = oracle.Index(ref, threads=os.cpu_count())
+    for q, (r, (sm, hits, _)) in enumerate(zip(reqs, results)):
+        want_sm, want_hits = mb.seed(G, r.seq, r.off)
+        assert sm.tobytes() == want_sm.tobytes(), q
+        assert np.array_equal(hits, want_hits), q
+        same_as_oracle(X, r, sm, hits, frac=0.05, seed=q)

@@ -269,6 +269,55 @@ def test_max_occ_flag_and_hit_offsets():
     assert np.array_equal(hoff, np.concatenate([[0], np.cumsum(kept)[:-1]]).astype(np.uint64))
 
 
+def test_max_occ_boundary_on_planted_copies():
+    """The workload's cap (not in the paper): an SMEM occurring exactly max_occ times is kept and
+    located, one occurring max_occ + 1 times is flagged and gets no hits.  Each read is a unit
+    planted a known number of times in a random reference, so s and the hit positions come from
+    the construction, not from the oracle's own arithmetic."""
+    ref, units, starts = synth.planted_copies(40, [500, 501, 3], 60, 0x6D6201)
+    X = oracle.Index(ref)
+    seq = units.reshape(-1)
+    off = np.arange(len(units) + 1, dtype=np.uint64) * 40
+    for max_occ, flagged in ((500, [False, True, False]), (499, [True, True, False]),
+                             (501, [False, False, False])):
+        sm, over, hoff, hits = X.seed(seq, off, max_occ=max_occ)
+        assert sm["read"].tolist() == [0, 1, 2]
+        assert sm["qbeg"].tolist() == [0, 0, 0] and sm["qend"].tolist() == [40, 40, 40]
+        assert sm["s"].tolist() == [500, 501, 3]
+        assert over.tolist() == flagged
+        kept = [c for c, f in zip((500, 501, 3), flagged) if not f]
+        assert len(hits) == sum(kept)
+        assert hoff.tolist() == [0, 0 if flagged[0] else 500, (0 if flagged[0] else 500) + (0 if flagged[1] else 501)]
+        for u in range(3):
+            if not flagged[u]:
+                h0 = int(hoff[u])
+                assert np.array_equal(np.sort(hits[h0:h0 + [500, 501, 3][u]]), starts[u])
+
+
+def test_bisulfite_filter_drops_hit_spanning_two_copies():
+    """Section 2.9's strand rule keeps a hit only inside one copy of the 3-base text.  A read-1
+    read planted across the end of the C-to-T copy and the start of the G-to-A copy has one
+    occurrence, at a known place, spanning both copies: it is dropped; a control read inside the
+    C-to-T copy is kept."""
+    m, half = 5000, 20
+    ref, cross = synth.junction_read(m, half, 0x6D6202)
+    X = oracle.Index(ref, bs3=True)
+    ctl = ref[1000:1000 + 2 * half]
+    seq = np.concatenate([cross, ctl]).astype(np.uint8)
+    off = np.array([0, 2 * half, 4 * half], dtype=np.uint64)
+    mate = np.array([1, 1], dtype=np.uint8)
+    conv = oracle.bs_convert_reads(seq, off, mate)
+    T = X.text()
+    assert np.array_equal(T[m - half:m + half], conv[:2 * half] + 1)   # the planted span
+    sm, over, hoff, hits = X.seed(conv, off)
+    assert sm["read"].tolist() == [0, 1]
+    assert sm["qbeg"].tolist() == [0, 0] and sm["qend"].tolist() == [2 * half, 2 * half]
+    assert sm["s"].tolist() == [1, 1]
+    assert hits.tolist() == [m - half, 1000]
+    keep = oracle.bs_keep(hits, np.array([2 * half, 2 * half]), mate, m)
+    assert keep.tolist() == [False, True]
+
+
 def test_bisulfite_index_and_filter():
     ref = synth.reference(3000, 31)
     X = oracle.Index(ref, bs3=True)
