@@ -448,28 +448,53 @@ def bench_served(mb, G, ref, n_requests: int, pool: int = 2000, load: float = 0.
     `window` requests outstanding), then Poisson arrivals at `load` x capacity; latency per request
     from submit to results on the host.  The stream's requests are drawn (seeded) from `pool`
     generated requests, so host memory stays bounded; every request is copied at submit and
-    seeded in full.  The first `seq_prefix` arrivals served by sequential plain launches (one
-    request at a time) for comparison, and the served form's latencies at the other offered loads
-    of `sweep`."""
+    seeded in full.  The first `seq_prefix` arrivals are also served by sequential plain launches
+    (one request at a time through one preallocated plan: copy in, run, copy the results out; no
+    allocation per request) for comparison, and the served form's latencies at the other offered
+    loads of `sweep` are reported."""
     import collections
     import threading as th
+    import torch
     base = serve_requests(ref, min(pool, n_requests), 4242)
     pick = (np.arange(n_requests) if n_requests <= len(base) else
             np.random.default_rng(4243).integers(0, len(base), n_requests))
     reqs = [base[i] for i in pick]
     total_reads = sum(r.n for r in reqs)
+    total_bases = sum(int(r.off[-1] - r.off[0]) for r in reqs)
     srv = mb.Server(G, hbm_budget=8 << 30)
+
+    def submit(r, before=None):
+        """Submit; when the staging ring is full (MB_ERR_BUSY), make room first."""
+        while True:
+            try:
+                return srv.submit(r.seq, r.off)
+            except mb.MbError as e:
+                if e.code != -9:
+                    raise
+                if before:
+                    before()
+                else:
+                    time.sleep(0.0005)
+
+    counts = {}
     t = time.time()
     out = collections.deque()
-    for r in reqs:
+
+    def collect_one():
+        q, tk = out.popleft()
+        sm, hits, _ = srv.wait(tk)
+        counts[int(pick[q])] = (len(sm), len(hits))
+
+    for q, r in enumerate(reqs):
         if len(out) >= window:
-            srv.wait(out.popleft())
-        out.append(srv.submit(r.seq, r.off))
+            collect_one()
+        out.append((q, submit(r, collect_one if out else None)))
     while out:
-        srv.wait(out.popleft())
+        collect_one()
     cap_s = time.time() - t
     cap_rps = n_requests / cap_s
-    q = lambda a, p: float(np.percentile(np.asarray(a), p))
+    cap_counters = srv.counters()
+    pct = lambda a, p: float(np.percentile(np.asarray(a), p))
 
     def poisson(rate, seed):
         """Submit the requests at Poisson arrival times; (latencies in ms, wall seconds)."""
@@ -490,7 +515,7 @@ def bench_served(mb, G, ref, n_requests: int, pool: int = 2000, load: float = 0.
             d = t0 + arrivals[i] - time.time()
             if d > 0:
                 time.sleep(d)
-            tk[i] = srv.submit(r.seq, r.off)
+            tk[i] = submit(r)
         col.join()
         return lat, time.time() - t0, arrivals
 
@@ -500,34 +525,50 @@ def bench_served(mb, G, ref, n_requests: int, pool: int = 2000, load: float = 0.
     for k, ld in enumerate(sweep):
         sl, sw, _ = poisson(ld * cap_rps, 18 + k)
         points.append({"offered_load": ld, "arrival_rate_per_s": ld * cap_rps, "served_reads_per_s": total_reads / sw,
-                       "p50_ms": q(sl, 50), "p95_ms": q(sl, 95), "p99_ms": q(sl, 99)})
-    stats = srv.stats()
+                       "p50_ms": pct(sl, 50), "p95_ms": pct(sl, 95), "p99_ms": pct(sl, 99)})
+    stats = srv.counters()
     srv.close()
-    # sequential plain launches on the same arrival times (the first seq_prefix arrivals)
+    # sequential plain launches on the same arrival times (the first seq_prefix arrivals): one plan
+    # sized for the largest request, inputs copied in and results copied out per request
     ns = min(seq_prefix, n_requests)
+    sub = reqs[:ns]
+    mr = max(r.n for r in sub)
+    mbases = max(int(r.off[-1] - r.off[0]) for r in sub)
+    msm = max(counts[int(pick[q])][0] for q in range(ns))
+    mh = max(counts[int(pick[q])][1] for q in range(ns))
+    P = mb.Plan(G, mr, mbases, msm + 64, mh + 64, opts=dict(flags=mb.MB_BATCHED))
+    dseq = torch.empty(mbases + 16, dtype=torch.uint8, device="cuda")
+    doff = torch.empty(mr + 1, dtype=torch.int64, device="cuda")
     seq_lat = []
     t0 = time.time()
-    for i, r in enumerate(reqs[:ns]):
+    for i, r in enumerate(sub):
         d = t0 + arrivals[i] - time.time()
         if d > 0:
             time.sleep(d)
-        mb.seed(G, r.seq, r.off)
+        nb = int(r.off[-1] - r.off[0])
+        dseq[:nb].copy_(torch.from_numpy(r.seq[int(r.off[0]):int(r.off[-1])]))
+        doff[:r.n + 1].copy_(torch.from_numpy((r.off - r.off[0]).view(np.int64)))
+        P.run(dseq[:nb], doff[:r.n + 1])
+        P.result()
         seq_lat.append((time.time() - t0 - arrivals[i]) * 1000)
     seq_wall = time.time() - t0
-    return {"requests": n_requests, "reads": total_reads, "distinct_requests": len(base),
+    P.free()
+    return {"requests": n_requests, "reads": total_reads, "bases": total_bases, "distinct_requests": len(base),
             "stream": f"{n_requests} requests drawn (seeded) from {len(base)} generated ones",
             "mix": "80% short (1-4,096 pairs of 2x150), 20% long (1-4,096 reads of 1-10 kb), log-uniform sizes",
             "capacity_requests_per_s": cap_rps, "capacity_reads_per_s": total_reads / cap_s,
-            "capacity_window": window,
+            "capacity_bases_per_s": total_bases / cap_s, "capacity_window": window,
             "offered_load": load, "arrival_rate_per_s": rate,
-            "served_reads_per_s": total_reads / wall,
-            "served_p50_ms": q(lat, 50), "served_p95_ms": q(lat, 95), "served_p99_ms": q(lat, 99),
+            "served_reads_per_s": total_reads / wall, "served_bases_per_s": total_bases / wall,
+            "served_p50_ms": pct(lat, 50), "served_p95_ms": pct(lat, 95), "served_p99_ms": pct(lat, 99),
             "sequential_plain_requests": ns,
-            "sequential_plain_reads_per_s": sum(r.n for r in reqs[:ns]) / seq_wall,
-            "sequential_plain_p50_ms": q(seq_lat, 50), "sequential_plain_p95_ms": q(seq_lat, 95),
-            "sequential_plain_p99_ms": q(seq_lat, 99),
+            "sequential_plain": "one preallocated plan, one request at a time (copy in, run, copy out)",
+            "sequential_plain_reads_per_s": sum(r.n for r in sub) / seq_wall,
+            "sequential_plain_bases_per_s": sum(int(r.off[-1] - r.off[0]) for r in sub) / seq_wall,
+            "sequential_plain_p50_ms": pct(seq_lat, 50), "sequential_plain_p95_ms": pct(seq_lat, 95),
+            "sequential_plain_p99_ms": pct(seq_lat, 99),
             "load_sweep": points,
-            "slots": stats["slots"], "launch_groups": stats["groups"], "merged_requests": stats["merged"]}
+            "server_counters_after_capacity_run": cap_counters, "server_counters": stats}
 
 
 # --------------------------------------------------------------------------------- GPU side
@@ -662,9 +703,12 @@ def run_gpu(args):
     loc_ms, loc_n = mb.profile_get("locate")
     log(f"timed: plain {plain_ms / args.steps:.1f} ms/step, graph {graph_ms / args.steps:.1f} ms/step "
         f"(identical: {same}); smem {smem_ms / max(smem_n, 1):.1f} ms, locate {loc_ms / max(loc_n, 1):.1f} ms per launch")
+    n_bases = int(len(rd.seq))
     forms = {"plain_launch": {"reads_per_s": ws * args.steps * n_reads / (plain_ms / 1000.0),
+                              "bases_per_s": ws * args.steps * n_bases / (plain_ms / 1000.0),
                               "ms_per_step": plain_ms / args.steps, "gpu_launches": plain_launches},
              "graph_plan": {"reads_per_s": ws * args.steps * n_reads / (graph_ms / 1000.0),
+                            "bases_per_s": ws * args.steps * n_bases / (graph_ms / 1000.0),
                             "ms_per_step": graph_ms / args.steps, "identical_output": bool(same),
                             "gpu_launches": graph_launches,
                             "block_size": best.block_size, "work_queue": bool(best.flags & mb.MB_BATCHED),

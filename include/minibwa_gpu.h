@@ -50,7 +50,12 @@ enum {
                               seeding: convert read 1 C->T and read 2 G->A, keep hits by strand */
 #define MB_BATCHED  0x2u   /* seeding: lanes take reads from a device work queue (a plan orders it
                               by decreasing read length; mb_seed_batch keeps read order) */
-#define MB_CHECKED  0x4u   /* seeding: bounds-check every block / row index on the device */
+#define MB_CHECKED  0x4u   /* seeding / locate: the kernels also check every occurrence row they
+                              read against the text length (only a damaged index can fail it); a
+                              failed check ends that read or walk and the call returns
+                              MB_ERR_DEVICE_CHECK.  Without the flag the kernels still check every
+                              read's offsets and every record's rows (MB_ERR_DEVICE_CHECK), and the
+                              host checks every device buffer against its allocation (MB_ERR_ARG) */
 #define MB_NO_KMER  0x8u   /* seeding: do not use the k-mer ds-interval table */
 #define MB_COUNT    0x10u  /* seeding/locate: also count the work done (mb_work_counters) */
 #define MB_NO_AUX   0x20u  /* index: build without the packed text and the rate-4 SA / ISA samples
@@ -58,6 +63,9 @@ enum {
                               by comparing text */
 #define MB_STEP_ONLY 0x40u /* seeding: extend every match step by step (Algorithm 1), even where
                               the auxiliary arrays allow comparing text */
+#define MB_SMEM_ONE_LOOP 0x80u /* tuning: the SMEM kernel in its one-loop form (every iteration runs
+                              every stage's code) instead of the split form (uniform block steps,
+                              the other actions in service passes); same output */
 
 /* Flags of mb_smem.flags */
 #define MB_SMEM_OVER_MAX_OCC 0x1u   /* s > max_occ: reported, not located, no hits */
@@ -78,6 +86,10 @@ typedef struct {
     uint32_t chunk_reads;     /* mb_seed_locate: reads per pipelined chunk (0 = 2^22) */
     uint32_t prefetch_depth;  /* tuning: LF-walks in flight per lane in locate, 1/2/4/8/16 (0 = 1) */
     uint32_t block_size;      /* tuning: threads per block (0 = default) */
+    uint32_t smem_burst;      /* tuning: SMEM kernel, block steps (extensions, walk steps) a warp runs
+                                 between two service passes of its other actions (0 = default 4) */
+    uint32_t smem_wait;       /* tuning: SMEM kernel, lanes out of the block steps that call a service
+                                 pass early, 1..32 (0 = default 8) */
 } mb_opts;
 
 /* One SMEM (48 bytes).  (k, kr, s) is its ds-interval (lo(P), lo(revcomp P), occ(P)),
@@ -275,22 +287,31 @@ int mb_autotune(const mb_index *idx, const uint8_t *seq, const uint64_t *off, ui
 
 /* ---------------------------------------------------------------------------------------
  * Served form: continuous batching of seeding requests on one GPU.
- * mb_serve_create starts a worker thread.  It preallocates as many execution slots (a stream
- * and a seeding plan for up to 65,536 reads / 64M bases / 2M SMEMs / 32M hits each) as fit in
- * hbm_budget bytes of device memory (at least one).  Requests wait in arrival order; whenever
- * a slot is free, every waiting request that still fits the slot's limits is merged into one
- * launch group, so requests arriving while others are on the GPU are admitted as soon as a slot
- * frees, and groups run concurrently on their own streams.  Each request's results are exactly
- * those of mb_seed_batch + mb_locate on that request alone (read numbers and hit offsets are
- * relative to the request).
- *   mb_serve_submit  copies the request (host buffers) and returns a ticket at once.
- *                    MB_ERR_ARG if the request alone exceeds a slot's limits.
+ * mb_serve_create starts a worker thread and a helper thread and allocates a 1 GiB pinned host
+ * ring in which submitted bases wait.  Device work runs in execution slots (a stream and a seeding
+ * plan for up to 65,536 reads / 64M bases / 2M SMEMs / 32M hits each, about 0.75 GB of device
+ * memory).  Slots are admitted by free device memory: a slot is created only when requests wait
+ * and every slot is busy, and only while cudaMemGetInfo's free bytes minus a reserve left to other
+ * users (2% of the device, at least 1 GiB) hold one more slot and the slots stay within
+ * hbm_budget bytes (0 = no budget; one slot is always allowed by the budget); otherwise requests
+ * wait until a slot frees.  Idle slots are released while free memory is below the reserve.
+ * Whenever a slot is free, every waiting request that still fits the slot's limits is merged into
+ * one launch group, so requests arriving while others are on the GPU are admitted as soon as a
+ * slot frees, and groups run concurrently on their own streams.  A group whose records or hits
+ * exceed its plan is seeded again request by request on the helper thread (allocating entry
+ * points), so the worker keeps serving.  Each request's results are exactly those of
+ * mb_seed_batch + mb_locate on that request alone (read numbers and hit offsets relative to it).
+ *   mb_serve_submit  copies the request's bases into the pinned ring on the calling thread and
+ *                    returns a ticket at once.  MB_ERR_ARG if the request alone exceeds a slot's
+ *                    limits; MB_ERR_BUSY if the ring has no room for it now (too many bases are
+ *                    outstanding: collect results and submit again).
  *   mb_serve_poll    *done = 1 when the ticket's results are ready.
  *   mb_serve_wait    waits up to timeout_ms (0 = no limit; MB_ERR_TIMEOUT after it) and returns
  *                    server-owned host arrays valid until mb_serve_release(ticket), plus the
  *                    request's latency from submit to results ready, in ms.
- *   mb_serve_destroy finishes every request already submitted, then stops and frees the server;
- *                    no call may use the server afterwards.
+ *   mb_serve_destroy finishes every request already submitted, then stops and frees the server.
+ * Every call on a server that was destroyed (or never created) returns MB_ERR_ARG without
+ * touching it.
  */
 int mb_serve_create(const mb_index *idx, const mb_opts *opts, uint64_t hbm_budget, mb_server **out);
 int mb_serve_submit(mb_server *srv, const uint8_t *seq, const uint64_t *off, uint32_t n_reads,
@@ -300,9 +321,18 @@ int mb_serve_wait(mb_server *srv, uint64_t ticket, uint32_t timeout_ms, const mb
                   uint64_t *n_smem, const uint32_t **hits, uint64_t *n_hits, double *latency_ms);
 int mb_serve_release(mb_server *srv, uint64_t ticket);
 int mb_serve_destroy(mb_server *srv);
-/* slots = execution slots created; groups = launch groups run; merged = requests that shared a
- * group with another request (the continuous-batching count). */
+/* slots = execution slots now; groups = launch groups run; merged = requests that shared a group
+ * with another request (the continuous-batching count). */
 int mb_serve_stats(mb_server *srv, uint32_t *slots, uint64_t *groups, uint64_t *merged);
+/* Up to `count` counters, in this order: slots now, groups, merged, slots created, slots released,
+ * slot allocations that failed, groups that outgrew their plan, submits refused with MB_ERR_BUSY,
+ * ms that waiting requests spent with every slot busy and no memory for another, device bytes of
+ * one slot, the free-memory reserve in bytes. */
+int mb_serve_counters(mb_server *srv, uint64_t *out, uint32_t count);
+/* Fault injection for tests of admission (no counterpart in the paper): from now on admission sees
+ * free_bytes of free device memory instead of cudaMemGetInfo's value (free_bytes < 0 restores the
+ * real query), and the next fail_slots slot creations fail as an allocation failure would. */
+int mb_serve_inject(mb_server *srv, int64_t free_bytes, uint32_t fail_slots);
 
 /* Section 2.9 strand rule on the 3-base index: keep[h] = 1 if hit h of an SMEM of read `mate`
  * 1 lies wholly inside the forward C-to-T or the reverse G-to-A copy of the reference (read 2:
@@ -374,6 +404,12 @@ const char *mb_strerror(int code);
  * limit belongs to this process's context only (other processes and later users of the GPU are
  * not affected) but it applies to every kernel of this process.  No counterpart in the paper. */
 int mb_set_l2_fetch_granularity(int bytes, int *now);
+/* The device allocation holding device pointer p: [*base, *base + *size), as the driver reports it.
+ * Every entry point checks its device buffers this way before a kernel touches them (a span that
+ * passes the end of its allocation gives MB_ERR_ARG).  MB_ERR_ARG for host or null pointers,
+ * MB_ERR_CUDA when the driver cannot tell (then those checks are skipped).  No counterpart in the
+ * paper. */
+int mb_device_extent(const void *p, uint64_t *base, uint64_t *size);
 /* Detail of the last error of this library (host-side message), for diagnostics. */
 const char *mb_last_error(void);
 

@@ -20,7 +20,7 @@ __all__ = ["SMEM_DTYPE", "Opts", "MbError", "lib", "build", "Index", "mb_index_b
            "mb_index_load", "mb_seed_batch", "mb_locate", "mb_bs_filter", "seed"]
 
 MB_BS3, MB_BATCHED, MB_CHECKED, MB_NO_KMER, MB_COUNT = 0x1, 0x2, 0x4, 0x8, 0x10
-MB_NO_AUX, MB_STEP_ONLY = 0x20, 0x40
+MB_NO_AUX, MB_STEP_ONLY, MB_SMEM_ONE_LOOP = 0x20, 0x40, 0x80
 AUX_RATE = 4   # sample rate of the auxiliary SA / ISA samples (mb_index_export_aux)
 MB_SMEM_OVER_MAX_OCC, MB_SMEM_ROUND2 = 0x1, 0x2
 MB_ERR_CAPACITY = -3
@@ -36,7 +36,8 @@ class Opts(ctypes.Structure):
                 ("max_occ", ctypes.c_uint32), ("sa_rate", ctypes.c_uint32),
                 ("kmer_k", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                 ("chunk_reads", ctypes.c_uint32), ("prefetch_depth", ctypes.c_uint32),
-                ("block_size", ctypes.c_uint32)]
+                ("block_size", ctypes.c_uint32), ("smem_burst", ctypes.c_uint32),
+                ("smem_wait", ctypes.c_uint32)]
 
 
 class MbError(RuntimeError):
@@ -80,6 +81,7 @@ def lib():
                 "mb_rescue_prefilter": ([P, P, P, P, U32, U32, P, P], I),
                 "mb_strerror": ([I], ctypes.c_char_p),
                 "mb_last_error": ([], ctypes.c_char_p),
+                "mb_device_extent": ([P, PU64, PU64], I),
                 "mb_seed_batch_noalloc": ([P, P, P, U32, P, OP, P, P, U64, PU64, PU64], I),
                 "mb_reseed": ([P, P, P, U32, P, P, U64, OP, P, P, U64, PU64, PU64], I),
                 "mb_plan_create": ([P, OP, U32, U64, U64, U64, PP], I),
@@ -97,6 +99,8 @@ def lib():
                 "mb_serve_release": ([P, U64], I),
                 "mb_serve_destroy": ([P], I),
                 "mb_serve_stats": ([P, ctypes.POINTER(U32), PU64, PU64], I),
+                "mb_serve_counters": ([P, P, U32], I),
+                "mb_serve_inject": ([P, ctypes.c_int64, U32], I),
                 "mb_set_l2_fetch_granularity": ([I, ctypes.POINTER(I)], I),
                 "mb_profile_enable": ([I], None),
                 "mb_profile_get": ([ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), PU64], I),
@@ -518,6 +522,18 @@ class Server:
         _check(lib().mb_serve_stats(self._h, ctypes.byref(sl), ctypes.byref(g), ctypes.byref(m)),
                "mb_serve_stats")
         return dict(slots=sl.value, groups=g.value, merged=m.value)
+
+    COUNTERS = ("slots", "groups", "merged", "slots_created", "slots_released", "alloc_failures",
+                "outgrown_groups", "busy", "memory_wait_ms", "slot_bytes", "reserve_bytes")
+
+    def counters(self):
+        v = np.zeros(len(self.COUNTERS), dtype=np.uint64)
+        _check(lib().mb_serve_counters(self._h, _ptr(v), len(v)), "mb_serve_counters")
+        return dict(zip(self.COUNTERS, (int(x) for x in v)))
+
+    def inject(self, free_bytes: int = -1, fail_slots: int = 0):
+        """Admission fault injection (tests): fake free device memory, failing slot creations."""
+        _check(lib().mb_serve_inject(self._h, free_bytes, fail_slots), "mb_serve_inject")
 
     def close(self):
         if getattr(self, "_h", None):

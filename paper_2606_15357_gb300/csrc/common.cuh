@@ -61,6 +61,13 @@ struct DevBuf {
 };
 
 bool mb_is_device_ptr(const void *p);
+// MB_ERR_ARG (with a message naming `what`) when device memory [p, p + bytes) passes the end of the
+// device allocation holding p; MB_OK for host memory, null or empty spans.
+int mb_check_span(const void *p, u64 bytes, const char *what);
+
+// Device error word: set by kernels whose input fails a check (the access is skipped, never
+// issued); the host returns MB_ERR_DEVICE_CHECK when it is not zero.
+enum { DEVCHK_OFFSETS = 1u, DEVCHK_RECORD = 2u, DEVCHK_BOUNDS = 4u };
 
 // launch bookkeeping: every kernel launch site calls MB_KCHECK() right after <<<...>>>
 void mb_count_launch();
@@ -255,9 +262,12 @@ size_t radix_tmp_bytes(size_t n);
 int radix_sort_pairs(u64 *keys, u32 *vals, u64 *keys_alt, u32 *vals_alt, size_t n, const BitRange *ranges,
                      int nranges, void *tmp, cudaStream_t st, const u64 *n_dev = nullptr);
 
-// plan internals used by the server: device bytes of a plan, asynchronous copy of its two
-// result counts (n_smem, n_hits) to host memory, and its device result arrays
+// plan internals used by the server: device bytes of a plan, asynchronous copy of its result
+// counts to host memory (3 u64: n_smem, n_hits, and the device error word in the upper half of
+// the third), and its device result arrays
 size_t mb_plan_bytes(const mb_plan *p);
+// device bytes mb_plan_create would allocate for these limits (no allocation)
+size_t mb_plan_workspace_bytes(const mb_opts *opts, u32 max_reads, u64 max_bases, u64 max_smem, u64 max_hits);
 int mb_plan_counts_async(mb_plan *p, u64 *host_counts, cudaStream_t st);
 void mb_plan_arrays(const mb_plan *p, const mb_smem **smem, const u32 **hits, u64 *max_smem, u64 *max_hits);
 // seeding of a plan's batch without the locate (records with hit offsets), the plan's per-record

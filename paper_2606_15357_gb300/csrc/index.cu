@@ -384,6 +384,55 @@ bool mb_is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// The device allocation holding p, from the driver's cuMemGetAddressRange (looked up once through
+// the runtime's driver entry points, so the library does not link the driver directly).
+static bool device_range(const void *p, u64 *base, u64 *size) {
+    typedef int (*AddrRange)(unsigned long long *, size_t *, unsigned long long);
+    static AddrRange fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (AddrRange)f;
+        cudaGetLastError();
+    });
+    if (!fn) return false;
+    unsigned long long b = 0;
+    size_t z = 0;
+    if (fn(&b, &z, (unsigned long long)(uintptr_t)p) != 0) return false;
+    *base = b;
+    *size = z;
+    return true;
+}
+
+extern "C" int mb_device_extent(const void *p, uint64_t *base, uint64_t *size) {
+    if (!p || !base || !size || !mb_is_device_ptr(p)) return MB_ERR_ARG;
+    u64 b = 0, z = 0;
+    if (!device_range(p, &b, &z)) {
+        mb_set_error("mb_device_extent: the driver does not report the allocation of %p", p);
+        return MB_ERR_CUDA;
+    }
+    *base = b;
+    *size = z;
+    return MB_OK;
+}
+
+int mb_check_span(const void *p, u64 bytes, const char *what) {
+    if (!p || bytes == 0 || !mb_is_device_ptr(p)) return MB_OK;
+    u64 b = 0, z = 0;
+    if (!device_range(p, &b, &z)) return MB_OK;   // the driver cannot tell: nothing to check
+    const u64 a = (u64)(uintptr_t)p;
+    if (a < b || a - b > z || bytes > z - (a - b)) {
+        mb_set_error("%s: %llu bytes from %p pass the end of its device allocation (%llu bytes from 0x%llx)", what,
+                     (unsigned long long)bytes, p, (unsigned long long)z, (unsigned long long)b);
+        return MB_ERR_ARG;
+    }
+    return MB_OK;
+}
+
 int mb_stage_in(const void *src, size_t bytes, cudaStream_t st, DevBuf &buf, const void **dev) {
     if (bytes == 0 || mb_is_device_ptr(src)) {
         *dev = src;

@@ -93,7 +93,8 @@ struct Pipeline {
 // the options that shape a plan (chunk_reads only sizes the chunks)
 bool same_plan_opts(const mb_opts &a, const mb_opts &b) {
     return a.min_len == b.min_len && a.min_occ == b.min_occ && a.max_occ == b.max_occ && a.flags == b.flags &&
-           a.prefetch_depth == b.prefetch_depth && a.block_size == b.block_size;
+           a.prefetch_depth == b.prefetch_depth && a.block_size == b.block_size && a.smem_burst == b.smem_burst &&
+           a.smem_wait == b.smem_wait;
 }
 
 constexpr size_t KEEP = 2;
@@ -156,6 +157,11 @@ extern "C" int mb_seed_locate(const mb_index *idx, const uint8_t *seq, const uin
     const bool seq_dev = mb_is_device_ptr(seq), off_dev = mb_is_device_ptr(off);
     const bool mate_dev = mate && mb_is_device_ptr(mate);
 
+    // device buffers must hold what the call reads and writes (checked before any access)
+    MB_TRY(mb_check_span(off, ((size_t)n_reads + 1) * 8, "mb_seed_locate: off"));
+    if (mate) MB_TRY(mb_check_span(mate, n_reads, "mb_seed_locate: mate"));
+    if (out) MB_TRY(mb_check_span(out, cap * sizeof(mb_smem), "mb_seed_locate: out"));
+    if (hits) MB_TRY(mb_check_span(hits, hits_cap * 4, "mb_seed_locate: hits"));
     // offsets on the host to cut the chunks
     std::vector<u64> hoff_copy;
     const u64 *hoff = off;
@@ -165,6 +171,11 @@ extern "C" int mb_seed_locate(const mb_index *idx, const uint8_t *seq, const uin
         MB_CK(cudaStreamSynchronize(ust));
         hoff = hoff_copy.data();
     }
+    if (hoff[n_reads] < hoff[0]) {
+        mb_set_error("mb_seed_locate: offsets decrease");
+        return MB_ERR_ARG;
+    }
+    MB_TRY(mb_check_span(seq + hoff[0], hoff[n_reads] - hoff[0], "mb_seed_locate: seq[off[0], off[n_reads])"));
     const u32 per = opts && opts->chunk_reads ? opts->chunk_reads : PIPE_READS;
     std::vector<Chunk> chunks;
     u32 max_nr = 0;
@@ -232,7 +243,7 @@ extern "C" int mb_seed_locate(const mb_index *idx, const uint8_t *seq, const uin
         for (Stage &x : p.s) {
             MB_CK(cudaStreamCreateWithFlags(&x.st, cudaStreamNonBlocking));
             MB_CK(cudaEventCreateWithFlags(&x.ev, cudaEventDisableTiming));
-            MB_CK(cudaMallocHost(&x.hcnt, 16));
+            MB_CK(cudaMallocHost(&x.hcnt, 32));
             MB_TRY(mb_plan_create(idx, opts, max_nr, max_nb, max_smem, 1, &x.plan));
             if (p.own_seq) MB_CK(cudaMalloc(&x.dseq, max_nb + 16));
             if (p.own_off) MB_CK(cudaMalloc(&x.doff, ((size_t)max_nr + 1) * 8));
@@ -286,6 +297,11 @@ extern "C" int mb_seed_locate(const mb_index *idx, const uint8_t *seq, const uin
         auto drain = [&](Stage &x) -> int {
             const Chunk &c = chunks[x.chunk];
             MB_CK(cudaEventSynchronize(x.ev));
+            if (x.hcnt[2] >> 32) {
+                mb_set_error("mb_seed_locate: device check failed (0x%x): read offsets decrease or leave the chunk",
+                             (unsigned)(x.hcnt[2] >> 32));
+                return MB_ERR_DEVICE_CHECK;
+            }
             u64 ns = x.hcnt[0], nh = x.hcnt[1];
             const mb_smem *psm;
             const u32 *ph;

@@ -217,6 +217,13 @@ enum { ACT_NONE = 0, ACT_EXT = 1, ACT_KMER = 2, ACT_WALK = 3, ACT_SAMPLE = 4, AC
 // steps they replace.
 constexpr int U_MIN = 16;
 
+// Tuning of k_smem_split: block steps between two service passes, and lanes out of the block loop
+// that call a service pass early (defaults; mb_opts.smem_burst / smem_wait override them).
+struct SmemTuning {
+    u32 burst, wait;
+};
+constexpr u32 SMEM_BURST = 4, SMEM_WAIT = 8;
+
 // Moves through the steps of Algorithm 3 that need no memory and picks the next memory action:
 // ACT_EXT, an extension of P[j] (backward in stages 1 and 3, forward in stage 2); ACT_KMER, a
 // k-mer table lookup (its code in `code`); ACT_NONE, the read is finished.  SMEMs found on the
@@ -476,6 +483,10 @@ struct SmemArgs {
     u64 *wc;
     const u32 *lc;   // per-read (l | c << 16), or null for the kernel-wide l and c
     bool uext;       // extend matches that occur once by comparing text (stages 4-7)
+    u32 *err = nullptr;                // device error word (always given)
+    u32 *chk = nullptr;                // with MB_CHECKED: the error word, for the per-step bounds checks
+    bool split = true;                 // k_smem_split (else k_smem, one loop for every stage)
+    SmemTuning tune = {SMEM_BURST, SMEM_WAIT};
 };
 
 // Launch bounds per shape: 128 threads allow 85 registers (6 blocks, 24 warps per SM); 256 and
@@ -489,11 +500,12 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 128 ? 6 : 1024 / BLOCK) k_smem
                                                                u64 *__restrict__ counts, u32 *__restrict__ ovf_list,
                                                                u32 *__restrict__ ovf_n, const u32 *__restrict__ perm,
                                                                u32 *qhead, u64 *wc, const u32 *__restrict__ lc,
-                                                               bool uext) {
+                                                               bool uext, u32 *err) {
     const u32 lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
     const u32 n = (u32)I.n;
     const u64 o0 = off[0];
-    const u8 *const end = seq + off[nr];
+    const u64 o1 = off[nr];
+    const u8 *const end = seq + o1;
     Work<COUNT> work;
     SmemState S;
     SlotEmit em;
@@ -501,11 +513,16 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 128 ? 6 : 1024 / BLOCK) k_smem
     if (!QUEUE) wr.init(nr);
     u32 lr = l, cr = c;   // this read's l and c
     auto start = [&](u64 rr) {
-        const u64 b = off[rr], e = off[rr + 1];
+        u64 b = off[rr], e = off[rr + 1];
+        bool bad = b > e || b < o0 || e > o1;
+        if (bad) {   // offsets outside the batch or decreasing: nothing is read, no record written
+            atomicOr(err, (u32)DEVCHK_OFFSETS);
+            b = e = o0;
+        }
         const u64 sb = slots_before(b - o0, rr), se = slots_before(e - o0, rr + 1);
         em.slots = slots;
         em.base = sb;
-        em.cap = se <= slot_total ? (u32)(se - sb) : 0u;
+        em.cap = !bad && se <= slot_total ? (u32)(se - sb) : 0u;
         em.cnt = 0;
         if (lc) {
             const u32 v = lc[rr];
@@ -629,6 +646,201 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 128 ? 6 : 1024 / BLOCK) k_smem
     work.flush(wc);
 }
 
+// The SMEM kernel with the block actions split from the rest.  Its lanes go through Algorithm 3
+// exactly as k_smem's do (same reads, same steps in the same order, same records), but a warp
+// runs two kinds of iteration:
+//  - a block step, uniform code for every lane whose next action reads occurrence blocks: an
+//    extension by P[j] (stages 1-3; Algorithm 1) or one LF step of a walk (stages 4 and 7).  A
+//    lane whose extension succeeds and whose next action is again a block action stays in this
+//    loop; most steps of Algorithm 3 are such extensions;
+//  - a service pass, run when at least `wait` lanes are out of the block loop, when `burst` block
+//    steps ran since the last pass, or when no lane can take a block step: every lane out of the
+//    loop applies a failed extension (a record, a restart), moves through the stage changes that
+//    need no memory, and takes at most one other memory action (k-mer table, SA / ISA sample,
+//    text comparison); finished lanes take new reads.
+// So the branches of the seven stages are executed together once per service pass instead of in
+// every iteration.
+template <bool QUEUE, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, BLOCK == 128 ? 6 : 1024 / BLOCK)
+    k_smem_split(DevIndex I, const u8 *__restrict__ seq, const u64 *__restrict__ off, u32 nr,
+                 const u8 *__restrict__ mate, u32 bs, u32 l, u32 c, bool kmer, SlotRec *__restrict__ slots,
+                 u64 slot_total, u64 *__restrict__ counts, u32 *__restrict__ ovf_list, u32 *__restrict__ ovf_n,
+                 const u32 *__restrict__ perm, u32 *qhead, const u32 *__restrict__ lc, bool uext, SmemTuning tune,
+                 u32 *err, u32 *chk) {
+    const u32 FULL = 0xffffffffu;
+    const u32 lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+    const u32 n = (u32)I.n, prim = (u32)I.primary;
+    const u64 o0 = off[0];
+    const u64 o1 = off[nr];
+    const u8 *const end = seq + o1;
+    Work<false> work;
+    SmemState S;
+    SlotEmit em;
+    WarpRange wr;
+    if (!QUEUE) wr.init(nr);
+    u32 lr = l, cr = c;
+    auto start = [&](u64 rr) {
+        u64 b = off[rr], e = off[rr + 1];
+        bool bad = b > e || b < o0 || e > o1;
+        if (bad) {   // offsets outside the batch or decreasing: nothing is read, no record written
+            atomicOr(err, (u32)DEVCHK_OFFSETS);
+            b = e = o0;
+        }
+        const u64 sb = slots_before(b - o0, rr), se = slots_before(e - o0, rr + 1);
+        em.slots = slots;
+        em.base = sb;
+        em.cap = !bad && se <= slot_total ? (u32)(se - sb) : 0u;
+        em.cnt = 0;
+        if (lc) {
+            const u32 v = lc[rr];
+            lr = v & 0xFFFFu;
+            cr = v >> 16;
+        }
+        smem_begin(S, seq + b, (int)(e - b), conv_of(mate, rr, bs), lr, n, end);
+    };
+    auto take = [&](u32 k, u32 rank, u64 &item, bool &ok) {
+        if (QUEUE) {
+            u32 base = 0;
+            if (lane == 0) base = atomicAdd(qhead, k);
+            base = __shfl_sync(FULL, base, 0);
+            item = (u64)base + rank;
+            ok = item < nr;
+        } else {
+            item = wr.next + rank;
+            ok = item < wr.end;
+            wr.next += k;
+        }
+    };
+    // one service of a lane out of the block loop: its pending failure, the stage changes, and at
+    // most one memory action that is not a block action.  Returns true when the read is finished.
+    bool rdy = false, pend = false;
+    auto service = [&]() -> bool {
+        if (pend) {
+            pend = false;
+            if (!smem_apply(S, 0, 0, 0, lr, cr, n, em)) return true;
+        }
+        u32 code = 0;
+        const int act = smem_next(S, I, lr, kmer && lr >= I.kmer_k, em, code, uext);
+        if (act == ACT_NONE) return true;
+        if (act == ACT_EXT || act == ACT_WALK) {
+            rdy = true;
+            return false;
+        }
+        if (act == ACT_KMER) {
+            const u32 *t = I.kmer + 3 * (u64)code;
+            return !smem_apply_kmer(S, __ldg(t), __ldg(t + 1), __ldg(t + 2), lr, cr, I.kmer_k);
+        }
+        if (act == ACT_SAMPLE) {
+            const u32 smp = __ldg((S.u == 4 ? I.sa_aux : I.isa_aux) + code);
+            if (S.u == 4) {
+                S.pos = smp + S.s;
+                S.u = 5;
+            } else {
+                S.kr = smp;
+                S.u = 7;
+            }
+            return false;
+        }
+        // ACT_TEXT: the matching prefix of read and text, up to 16 bases
+        const u32 x = S.pos + (u32)(S.j - S.i);
+        const u32 t0 = __ldg(I.text2 + (x >> 4)), t1 = __ldg(I.text2 + (x >> 4) + 1);
+        u32 rc = 0, rn = 0;
+        const u32 rcnt = read_codes16(S, S.j, rc, rn);
+        const u32 tc = (u32)((((u64)t1 << 32) | t0) >> (2 * (x & 15)));
+        const u32 lim = min(min(rcnt, (u32)(S.L - S.j)), n - 1 - x);
+        const u32 d = rc ^ tc, m2 = ((d | (d >> 1)) & 0x55555555u) | rn;
+        const u32 first = m2 ? (u32)(__ffs(m2) - 1) >> 1 : 16u;
+        S.j += (int)min(first, lim);
+        if (first < lim) S.u = 6;
+        return false;
+    };
+    u64 item, r = 0;
+    bool live;
+    take(32, lane, item, live);
+    if (live) {
+        r = QUEUE && perm ? perm[item] : item;
+        start(r);
+    }
+    u32 since = 0;
+    for (;;) {
+        if (__all_sync(FULL, !live)) break;
+        const u32 out_mask = __ballot_sync(FULL, live && !rdy);
+        const u32 in_mask = __ballot_sync(FULL, rdy);
+        if (out_mask && (in_mask == 0 || since >= tune.burst || (u32)__popc(out_mask) >= tune.wait)) {
+            since = 0;
+            // ---- service pass (divergent)
+            bool fin = live && !rdy && service();
+            // finished lanes hand in their counts and take new reads, which take their first
+            // action at once (a read shorter than l finishes there and takes the next one)
+            for (;;) {
+                if (fin) {
+                    counts[r] = em.cnt;
+                    if (em.cnt > em.cap) ovf_list[atomicAdd(ovf_n, 1u)] = (u32)r;
+                }
+                const u32 fm = __ballot_sync(FULL, fin);
+                if (!fm) break;
+                u64 it2;
+                bool ok2;
+                take(__popc(fm), __popc(fm & lt), it2, ok2);
+                bool again = false;
+                if (fin) {
+                    live = ok2;
+                    rdy = false;
+                    pend = false;
+                    if (live) {
+                        r = QUEUE && perm ? perm[it2] : it2;
+                        start(r);
+                        again = service();
+                    }
+                }
+                fin = again;
+            }
+        }
+        ++since;
+        // ---- block step (uniform): an extension or an LF step of a walk for every ready lane
+        if (rdy && chk) {   // MB_CHECKED: both rows inside the text (always so on a sound index)
+            const bool walk = S.u >= 4, fwd = S.u == 2;
+            const u64 p = (fwd || walk) ? S.kr : S.k;
+            if (p + (walk ? 0u : S.s) > n) {
+                atomicOr(chk, (u32)DEVCHK_BOUNDS);
+                rdy = false;
+                S.u = 0;   // the read ends here; the next service pass finishes it
+            }
+        }
+        if (rdy) {
+            const bool walk = S.u >= 4, fwd = S.u == 2;
+            const u32 p = (fwd || walk) ? S.kr : S.k, q = fwd ? S.k : S.kr, sz = walk ? 0u : S.s, e = p + sz;
+            const Blk b0 = load_blk(I.occ + (p >> BLK_SHIFT));
+            Blk b1 = b0;
+            if ((e >> BLK_SHIFT) != (p >> BLK_SHIFT)) b1 = load_blk(I.occ + (e >> BLK_SHIFT));
+            const u32 a = walk ? 0u : cached_base(S, S.j);
+            const u32 sym = walk ? sym_at(b0, p & BLK_MASK) : ((fwd ? 3u - a : a) & 3u);
+            const Ext x = extend_blocks(I, b0, b1, p, q, sz, sym);
+            if (walk) {
+                S.kr = x.p;
+                if (S.u == 4) {
+                    ++S.s;
+                    rdy = S.kr != prim && (S.kr & (AUX_RATE - 1)) != 0 && S.s <= n;
+                } else {
+                    --S.s;
+                    rdy = S.s != 0;
+                }
+            } else if (a < 4 && x.s >= cr) {
+                S.k = fwd ? x.q : x.p;
+                S.kr = fwd ? x.p : x.q;
+                S.s = x.s;
+                S.j += fwd ? 1 : -1;
+                rdy = S.u == 1 ? S.j >= S.i
+                               : (S.u == 2 ? (S.j != S.L && !(uext && S.s == 1 && S.L - S.j >= U_MIN)) : S.j > S.i);
+            } else {   // the extension fails: applied at the next service pass
+                rdy = false;
+                pend = true;
+            }
+        }
+    }
+    (void)work;
+}
+
 __device__ __forceinline__ void write_rec(mb_smem *out, u64 *hitc, u64 m, u32 r, u32 qbeg, u32 qend, u64 k, u64 kr,
                                           u64 s, u32 max_occ, u64 cap) {
     if (m >= cap) return;   // past the caller's capacity (reported, not written)
@@ -740,18 +952,26 @@ __device__ __forceinline__ u64 hits_of(const mb_smem *__restrict__ sm, u64 m) {
 __device__ __forceinline__ bool walks(u64 cnt, const u32 *known, u64 t) {
     return cnt && !(known && cnt == 1 && known[t] != NOPOS);
 }
+// A record whose rows [k, k+s) leave the text (only records from a caller can): flagged in the
+// error word and left out of the walks, its hits unwritten.
+__device__ __forceinline__ bool rows_outside(const mb_smem *__restrict__ sm, u64 t, u64 cnt, u64 n) {
+    const u64 k = __ldg(&sm[t].k);
+    return cnt && (k >= n || cnt > n - k);
+}
 
 // flag[t] = 1 for a record with rows to walk.  A record with a known position (one hit, found
 // while seeding) writes that hit here and walks nothing.
 __global__ void k_share_flag(const mb_smem *__restrict__ sm, u64 cap, const u64 *__restrict__ nsm_dev,
                              const u32 *__restrict__ known, u32 *__restrict__ hits, u64 hits_cap,
-                             u64 *__restrict__ flag) {
+                             u64 *__restrict__ flag, u64 n, u32 *err) {
     const u64 nsm = count_of(cap, nsm_dev);
     for (u64 t = blockIdx.x * (u64)blockDim.x + threadIdx.x; t < cap; t += (u64)gridDim.x * blockDim.x) {
         u64 f = 0;
         if (t < nsm) {
             const u64 cnt = hits_of(sm, t);
-            if (walks(cnt, known, t)) {
+            if (rows_outside(sm, t, cnt, n)) {
+                atomicOr(err, (u32)DEVCHK_RECORD);
+            } else if (walks(cnt, known, t)) {
                 f = 1;
             } else if (cnt == 1) {   // known position
                 const u64 ho = __ldg(&sm[t].hit_off);
@@ -766,11 +986,11 @@ __global__ void k_share_flag(const mb_smem *__restrict__ sm, u64 cap, const u64 
 // (k << 9 | 511 - min(s, 511)) and record number.
 __global__ void k_share_compact(const mb_smem *__restrict__ sm, u64 cap, const u64 *__restrict__ nsm_dev,
                                 const u32 *__restrict__ known, const u64 *__restrict__ at, u64 *__restrict__ keys,
-                                u32 *__restrict__ vals) {
+                                u32 *__restrict__ vals, u64 n) {
     const u64 nsm = count_of(cap, nsm_dev);
     for (u64 t = blockIdx.x * (u64)blockDim.x + threadIdx.x; t < nsm; t += (u64)gridDim.x * blockDim.x) {
         const u64 cnt = hits_of(sm, t);
-        if (!walks(cnt, known, t)) continue;
+        if (!walks(cnt, known, t) || rows_outside(sm, t, cnt, n)) continue;
         const u64 sb = cnt < (1u << SHARE_S_BITS) ? cnt : (1u << SHARE_S_BITS) - 1;
         keys[at[t]] = ((u64)(u32)__ldg(&sm[t].k) << SHARE_S_BITS) | ((1u << SHARE_S_BITS) - 1 - sb);
         vals[at[t]] = (u32)t;
@@ -884,7 +1104,8 @@ __global__ void k_share_copy(const u64 *__restrict__ keys, const u32 *__restrict
 // walks three.
 template <bool COUNT, bool POW2, int D>
 __global__ void __launch_bounds__(256, D == 8 ? 2 : 1) k_locate(DevIndex I, const u32 *__restrict__ rows, u64 nhits,
-                                                const u64 *__restrict__ nhits_dev, u32 *__restrict__ hits, u64 *wc) {
+                                                const u64 *__restrict__ nhits_dev, u32 *__restrict__ hits, u64 *wc,
+                                                u32 *chk) {
     const u32 lane = threadIdx.x & 31;
     if (nhits_dev && *nhits_dev < nhits) nhits = *nhits_dev;
     Work<COUNT> work;
@@ -921,8 +1142,10 @@ __global__ void __launch_bounds__(256, D == 8 ? 2 : 1) k_locate(DevIndex I, cons
         for (int d = 0; d < D; ++d) {
             const bool on = (live >> d) & 1u;
             const bool skip = row[d] == NOPOS;   // a row to skip (its hit is written elsewhere)
-            const bool sampled = !skip && (POW2 ? (row[d] & rmask) == 0 : row[d] % r == 0);
-            const bool st = on && (skip || sampled || row[d] == prim || steps[d] > n);
+            const bool bad = chk && on && !skip && row[d] >= n;   // MB_CHECKED: a row outside the text
+            if (bad) atomicOr(chk, (u32)DEVCHK_BOUNDS);
+            const bool sampled = !skip && !bad && (POW2 ? (row[d] & rmask) == 0 : row[d] % r == 0);
+            const bool st = on && (skip || bad || sampled || row[d] == prim || steps[d] > n);
             sv[d] = 0;
             if (st) {
                 stop |= 1u << d;
@@ -949,7 +1172,8 @@ __global__ void __launch_bounds__(256, D == 8 ? 2 : 1) k_locate(DevIndex I, cons
         for (int d = 0; d < D; ++d) {
             if ((stop >> d) & 1u) {
                 if (!((skp >> d) & 1u))
-                    whits[h[d]] = steps[d] > n ? 0xFFFFFFFFu : (((smp >> d) & 1u) ? sv[d] + steps[d] : steps[d]);
+                    whits[h[d]] = (steps[d] > n || row[d] >= n) ? 0xFFFFFFFFu
+                                                                : (((smp >> d) & 1u) ? sv[d] + steps[d] : steps[d]);
                 work.lf += steps[d];
                 work.sa += (smp >> d) & 1u;
                 h[d] = give;
@@ -1005,40 +1229,55 @@ unsigned resident_grid(const void *kernel, int block, u64 work_items) {
 
 template <bool COUNT, bool QUEUE, int BLOCK>
 int launch_smem_t(const SmemArgs &a, cudaStream_t st) {
+    if (!COUNT && a.split) {
+        const unsigned g = resident_grid((const void *)k_smem_split<QUEUE, BLOCK>, BLOCK, a.nr);
+        k_smem_split<QUEUE, BLOCK><<<g, BLOCK, 0, st>>>(a.I, a.seq, a.off, a.nr, a.mate, a.bs, a.l, a.c, a.kmer,
+                                                        a.slots, a.slot_total, a.counts, a.ovf_list, a.ovf_n, a.perm,
+                                                        a.qhead, a.lc, a.uext, a.tune, a.err, a.chk);
+        MB_KCHECK();
+        return MB_OK;
+    }
     const unsigned g = resident_grid((const void *)k_smem<COUNT, QUEUE, BLOCK>, BLOCK, a.nr);
     k_smem<COUNT, QUEUE, BLOCK><<<g, BLOCK, 0, st>>>(a.I, a.seq, a.off, a.nr, a.mate, a.bs, a.l, a.c, a.kmer, a.slots,
                                                      a.slot_total, a.counts, a.ovf_list, a.ovf_n, a.perm, a.qhead,
-                                                     a.wc, a.lc, a.uext);
+                                                     a.wc, a.lc, a.uext, a.err);
     MB_KCHECK();
     return MB_OK;
 }
 
+// The SMEM kernel's form and tuning from the options: k_smem_split unless MB_SMEM_ONE_LOOP.
+void smem_tuning(const mb_opts *o, SmemArgs &a) {
+    a.split = !(o && (o->flags & MB_SMEM_ONE_LOOP));
+    a.tune.burst = o && o->smem_burst ? o->smem_burst : SMEM_BURST;
+    a.tune.wait = o && o->smem_wait ? (o->smem_wait > 32 ? 32u : o->smem_wait) : SMEM_WAIT;
+}
+
 template <bool COUNT, bool POW2, int D>
 int launch_locate_t(const DevIndex &I, const u32 *rows, u64 nhits, const u64 *nhits_dev, u32 *hits, u64 *wc,
-                    cudaStream_t st) {
+                    u32 *chk, cudaStream_t st) {
     const unsigned g = resident_grid((const void *)k_locate<COUNT, POW2, D>, 256, (nhits + 63) / 64 * 32);
     const u64 warps = (u64)g * 8;
     if ((nhits + warps - 1) / warps >= (1ull << 32) - 4096) {   // offsets within a warp's range are u32
         mb_set_error("locate: %llu hits over %llu warps", (unsigned long long)nhits, (unsigned long long)warps);
         return MB_ERR_ARG;
     }
-    k_locate<COUNT, POW2, D><<<g, 256, 0, st>>>(I, rows, nhits, nhits_dev, hits, wc);
+    k_locate<COUNT, POW2, D><<<g, 256, 0, st>>>(I, rows, nhits, nhits_dev, hits, wc, chk);
     MB_KCHECK();
     return MB_OK;
 }
 
 // The locate kernel: work counters, power-of-two sample rate, walks per lane (depth 1, 2, 4, 8, 16).
 int launch_locate(const DevIndex &I, const u32 *rows, u64 nhits, const u64 *nhits_dev, u32 *hits, u64 *wc,
-                  bool count, u32 depth, cudaStream_t st) {
+                  bool count, u32 depth, u32 *chk, cudaStream_t st) {
     const bool pow2 = (I.r & (I.r - 1)) == 0;
-    if (count) return pow2 ? launch_locate_t<true, true, 1>(I, rows, nhits, nhits_dev, hits, wc, st)
-                           : launch_locate_t<true, false, 1>(I, rows, nhits, nhits_dev, hits, wc, st);
-    if (!pow2) return launch_locate_t<false, false, 1>(I, rows, nhits, nhits_dev, hits, wc, st);
-    if (depth >= 16) return launch_locate_t<false, true, 16>(I, rows, nhits, nhits_dev, hits, wc, st);
-    if (depth >= 8) return launch_locate_t<false, true, 8>(I, rows, nhits, nhits_dev, hits, wc, st);
-    if (depth >= 4) return launch_locate_t<false, true, 4>(I, rows, nhits, nhits_dev, hits, wc, st);
-    if (depth >= 2) return launch_locate_t<false, true, 2>(I, rows, nhits, nhits_dev, hits, wc, st);
-    return launch_locate_t<false, true, 1>(I, rows, nhits, nhits_dev, hits, wc, st);
+    if (count) return pow2 ? launch_locate_t<true, true, 1>(I, rows, nhits, nhits_dev, hits, wc, chk, st)
+                           : launch_locate_t<true, false, 1>(I, rows, nhits, nhits_dev, hits, wc, chk, st);
+    if (!pow2) return launch_locate_t<false, false, 1>(I, rows, nhits, nhits_dev, hits, wc, chk, st);
+    if (depth >= 16) return launch_locate_t<false, true, 16>(I, rows, nhits, nhits_dev, hits, wc, chk, st);
+    if (depth >= 8) return launch_locate_t<false, true, 8>(I, rows, nhits, nhits_dev, hits, wc, chk, st);
+    if (depth >= 4) return launch_locate_t<false, true, 4>(I, rows, nhits, nhits_dev, hits, wc, chk, st);
+    if (depth >= 2) return launch_locate_t<false, true, 2>(I, rows, nhits, nhits_dev, hits, wc, chk, st);
+    return launch_locate_t<false, true, 1>(I, rows, nhits, nhits_dev, hits, wc, chk, st);
 }
 
 // Device arrays of the shared-walk locate: per record (cap) sort keys and values with their
@@ -1049,6 +1288,8 @@ struct ShareBufs {
     u64 *keys = nullptr, *keys_alt = nullptr, *roff = nullptr, *nwalk = nullptr, *nrows = nullptr;
     u32 *vals = nullptr, *vals_alt = nullptr, *pmax = nullptr, *last = nullptr, *rows = nullptr, *rpos = nullptr;
     void *tmp = nullptr;
+    u32 *err = nullptr;   // the device error word (records with rows outside the text; MB_CHECKED bounds)
+    bool checked = false; // MB_CHECKED: the locate kernel checks every row it walks
 };
 size_t share_tmp_bytes(u64 cap) {
     const size_t a = radix_tmp_bytes(cap), b = scan_tmp_bytes(cap);
@@ -1064,10 +1305,10 @@ int locate_shared(const DevIndex &I, const mb_smem *sm, u64 cap, const u64 *nsm_
                   u64 hits_cap, const ShareBufs &b, u64 *wc, bool count, u32 depth, KTimer *kt, cudaStream_t st) {
     if (cap == 0) return MB_OK;
     const unsigned G = grid_for(cap, 256);
-    k_share_flag<<<G, 256, 0, st>>>(sm, cap, nsm_dev, known, hits, hits_cap, b.roff);
+    k_share_flag<<<G, 256, 0, st>>>(sm, cap, nsm_dev, known, hits, hits_cap, b.roff, I.n, b.err);
     MB_KCHECK();
     MB_TRY(scan_exclusive_u64(b.roff, b.roff, cap, b.nwalk, b.tmp, st));
-    k_share_compact<<<G, 256, 0, st>>>(sm, cap, nsm_dev, known, b.roff, b.keys, b.vals);
+    k_share_compact<<<G, 256, 0, st>>>(sm, cap, nsm_dev, known, b.roff, b.keys, b.vals, I.n);
     MB_KCHECK();
     const BitRange r[1] = {{0, SHARE_KEY_BITS}};
     MB_TRY(radix_sort_pairs(b.keys, b.vals, b.keys_alt, b.vals_alt, cap, r, 1, b.tmp, st, b.nwalk));
@@ -1083,7 +1324,7 @@ int locate_shared(const DevIndex &I, const mb_smem *sm, u64 cap, const u64 *nsm_
     k_share_rows<<<G, 256, 0, st>>>(b.keys, ss, b.last, b.roff, cap, b.nwalk, b.rows, hits_cap);
     MB_KCHECK();
     if (kt) kt->start();
-    MB_TRY(launch_locate(I, b.rows, hits_cap, b.nrows, b.rpos, wc, count, depth, st));
+    MB_TRY(launch_locate(I, b.rows, hits_cap, b.nrows, b.rpos, wc, count, depth, b.checked ? b.err : nullptr, st));
     if (kt) kt->stop();
     k_share_copy<<<G, 256, 0, st>>>(b.keys, ss, sho, b.last, b.roff, cap, b.nwalk, b.rpos, hits_cap, hits, hits_cap);
     MB_KCHECK();
@@ -1126,6 +1367,7 @@ int mb_seed_device(const mb_index *idx, const u8 *dseq, const u64 *doff, u32 n_r
     MB_TRY(bmisc.alloc(64, st));
     u64 *dtotal = bmisc.as<u64>(), *dhtotal = bmisc.as<u64>() + 1;
     u32 *dovf_n = (u32 *)(bmisc.as<u64>() + 2), *dqhead = (u32 *)(bmisc.as<u64>() + 3);
+    u32 *derr = (u32 *)(bmisc.as<u64>() + 4);
     MB_CK(cudaMemsetAsync(bmisc.p, 0, 64, st));
 
     const DevIndex I = mb_dev_index(idx);
@@ -1141,6 +1383,9 @@ int mb_seed_device(const mb_index *idx, const u8 *dseq, const u64 *doff, u32 n_r
                     bslots.as<SlotRec>(), nslots, bcounts.as<u64>(), bovf.as<u32>(), dovf_n, nullptr,
                     queue ? dqhead : nullptr, count ? mb_work_counter_buf(st) : nullptr, dlc,
                     I.text2 && !(flags & MB_STEP_ONLY)};
+        smem_tuning(opts, sa);
+        sa.err = derr;
+        sa.chk = (flags & MB_CHECKED) ? derr : nullptr;
         const int blk = opts && (opts->block_size == 128 || opts->block_size == 512) ? (int)opts->block_size : 256;
         kt.start();
         MB_TRY(launch_smem(sa, count, queue, blk, st));
@@ -1149,8 +1394,16 @@ int mb_seed_device(const mb_index *idx, const u8 *dseq, const u64 *doff, u32 n_r
     MB_TRY(btmp.alloc(scan_tmp_bytes(n_reads), st));
     MB_TRY(scan_exclusive_u64(bcounts.as<u64>(), bsoff.as<u64>(), n_reads, dtotal, btmp.p, st));
     u64 total = 0;
+    u32 err = 0;
     MB_CK(cudaMemcpyAsync(&total, dtotal, 8, cudaMemcpyDeviceToHost, st));
+    MB_CK(cudaMemcpyAsync(&err, derr, 4, cudaMemcpyDeviceToHost, st));
     MB_CK(cudaStreamSynchronize(st));
+    if (err) {
+        mb_set_error("mb_seed_batch: device check failed (0x%x): %s", err,
+                     (err & DEVCHK_OFFSETS) ? "read offsets decrease or leave [off[0], off[n_reads]]"
+                                            : "an occurrence row outside the text");
+        return MB_ERR_DEVICE_CHECK;
+    }
     *n_out = total;
     if (total > cap) return MB_ERR_CAPACITY;
     if (total == 0) return MB_OK;
@@ -1160,6 +1413,7 @@ int mb_seed_device(const mb_index *idx, const u8 *dseq, const u64 *doff, u32 n_r
         mb_set_error("mb_seed_batch: null output");
         return MB_ERR_ARG;
     }
+    MB_TRY(mb_check_span(out, total * sizeof(mb_smem), "mb_seed_batch: out"));
     DevBuf bout, bhitc, bhtmp;
     mb_smem *dout = out;
     if (!out_dev) {
@@ -1203,6 +1457,7 @@ extern "C" int mb_seed_batch(const mb_index *idx, const uint8_t *seq, const uint
     DevBuf boff, bseq, bmate;
     const void *doff = nullptr, *dseq = nullptr, *dmate = nullptr;
     u64 o0 = 0, o1 = 0;
+    MB_TRY(mb_check_span(off, (size_t)(n_reads + 1) * 8, "mb_seed_batch: off"));
     MB_CK(cudaMemcpyAsync(&o0, off, 8, cudaMemcpyDefault, st));
     MB_CK(cudaMemcpyAsync(&o1, off + n_reads, 8, cudaMemcpyDefault, st));
     MB_CK(cudaStreamSynchronize(st));
@@ -1210,6 +1465,8 @@ extern "C" int mb_seed_batch(const mb_index *idx, const uint8_t *seq, const uint
         mb_set_error("mb_seed_batch: offsets decrease");
         return MB_ERR_ARG;
     }
+    MB_TRY(mb_check_span(seq + o0, o1 - o0, "mb_seed_batch: seq[off[0], off[n_reads])"));
+    if (mate) MB_TRY(mb_check_span(mate, n_reads, "mb_seed_batch: mate"));
     MB_TRY(mb_stage_in(off, (size_t)(n_reads + 1) * 8, st, boff, &doff));
     // a host `seq` is staged from off[0]; device pointers are used as given
     if (mb_is_device_ptr(seq)) dseq = seq;
@@ -1228,7 +1485,7 @@ extern "C" int mb_seed_batch(const mb_index *idx, const uint8_t *seq, const uint
 // allocation.
 static int share_alloc(DevBuf &bw, u64 n_smem, u64 total, cudaStream_t st, ShareBufs &b) {
     const size_t rec_bytes = (size_t)n_smem * SHARE_BYTES_PER_RECORD, row_bytes = (size_t)total * 8;
-    MB_TRY(bw.alloc(rec_bytes + row_bytes + 16 + share_tmp_bytes(n_smem) + 13 * 256, st));
+    MB_TRY(bw.alloc(rec_bytes + row_bytes + 16 + share_tmp_bytes(n_smem) + 14 * 256, st));
     char *m = (char *)bw.p;
     auto take = [&](size_t bytes) { void *p = m; m += (bytes + 255) & ~(size_t)255; return p; };
     b.keys = (u64 *)take(n_smem * 8);
@@ -1242,7 +1499,9 @@ static int share_alloc(DevBuf &bw, u64 n_smem, u64 total, cudaStream_t st, Share
     b.rpos = (u32 *)take(total * 4);
     b.nrows = (u64 *)take(8);
     b.nwalk = (u64 *)take(8);
+    b.err = (u32 *)take(8);
     b.tmp = take(share_tmp_bytes(n_smem));
+    MB_CK(cudaMemsetAsync(b.err, 0, 8, st));
     return MB_OK;
 }
 
@@ -1267,6 +1526,7 @@ extern "C" int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_sm
     cudaStream_t st = (cudaStream_t)stream;
     DevBuf bsm, bhits;
     const void *dsm = nullptr;
+    MB_TRY(mb_check_span(smem, n_smem * sizeof(mb_smem), "mb_locate: smem"));
     MB_TRY(mb_stage_in(smem, n_smem * sizeof(mb_smem), st, bsm, &dsm));
     mb_smem last;
     MB_CK(cudaMemcpyAsync(&last, (const mb_smem *)dsm + n_smem - 1, sizeof last, cudaMemcpyDeviceToHost, st));
@@ -1276,6 +1536,7 @@ extern "C" int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_sm
     if (total > cap) return MB_ERR_CAPACITY;
     if (total == 0) return MB_OK;
     if (!hits) return MB_ERR_ARG;
+    MB_TRY(mb_check_span(hits, total * 4, "mb_locate: hits"));
     u32 *dh = hits;
     const bool hdev = mb_is_device_ptr(hits);
     if (!hdev) {
@@ -1287,12 +1548,20 @@ extern "C" int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_sm
     DevBuf bw;
     ShareBufs b;
     MB_TRY(share_alloc(bw, n_smem, total, st, b));
+    b.checked = opts && (opts->flags & MB_CHECKED);
     u64 *wc = count ? mb_work_counter_buf(st) : nullptr;
     KTimer kt("locate", st);
     MB_TRY(locate_shared(I, (const mb_smem *)dsm, n_smem, nullptr, nullptr, dh, total, b, wc, count,
                          opts ? opts->prefetch_depth : 0, &kt, st));
+    u32 err = 0;
+    MB_CK(cudaMemcpyAsync(&err, b.err, 4, cudaMemcpyDeviceToHost, st));
     if (!hdev) MB_CK(cudaMemcpyAsync(hits, dh, total * 4, cudaMemcpyDeviceToHost, st));
     MB_CK(cudaStreamSynchronize(st));
+    if (err) {
+        mb_set_error("mb_locate: device check failed (0x%x): %s", err,
+                     (err & DEVCHK_RECORD) ? "a record's rows [k, k+s) leave the text" : "a row outside the text");
+        return MB_ERR_DEVICE_CHECK;
+    }
     return MB_OK;
 }
 
@@ -1398,6 +1667,7 @@ extern "C" int mb_seed_batch_noalloc(const mb_index *idx, const uint8_t *seq, co
     const u32 bs = (flags & MB_BS3) ? 1u : 0u;
     cudaStream_t st = (cudaStream_t)stream;
     u64 o0 = 0, o1 = 0;
+    MB_TRY(mb_check_span(off, (size_t)(n_reads + 1) * 8, "mb_seed_batch_noalloc: off"));
     MB_CK(cudaMemcpyAsync(&o0, off, 8, cudaMemcpyDeviceToHost, st));
     MB_CK(cudaMemcpyAsync(&o1, off + n_reads, 8, cudaMemcpyDeviceToHost, st));
     MB_CK(cudaStreamSynchronize(st));
@@ -1405,6 +1675,8 @@ extern "C" int mb_seed_batch_noalloc(const mb_index *idx, const uint8_t *seq, co
         mb_set_error("mb_seed_batch_noalloc: offsets decrease");
         return MB_ERR_ARG;
     }
+    MB_TRY(mb_check_span(seq + o0, o1 - o0, "mb_seed_batch_noalloc: seq[off[0], off[n_reads])"));
+    if (mate) MB_TRY(mb_check_span(mate, n_reads, "mb_seed_batch_noalloc: mate"));
     // scratch layout: [totals][counts][soff][overflow list][scan tmp][slots][hit counts][scan tmp]
     const size_t nr = n_reads;
     const size_t nslots = slots_total(o1 - o0, nr);
@@ -1420,7 +1692,7 @@ extern "C" int mb_seed_batch_noalloc(const mb_index *idx, const uint8_t *seq, co
     unsigned char *S = nullptr;
     MB_TRY(noalloc_scratch(&S));
     u64 *dtotal = (u64 *)S, *dhtotal = (u64 *)S + 1;
-    u32 *dovf_n = (u32 *)((u64 *)S + 2);
+    u32 *dovf_n = (u32 *)((u64 *)S + 2), *derr = (u32 *)((u64 *)S + 3);
     u64 *counts = (u64 *)(S + o_cnt), *soff = (u64 *)(S + o_soff);
     u32 *ovf = (u32 *)(S + o_ovf);
     SlotRec *slots = (SlotRec *)(S + o_slots);
@@ -1432,12 +1704,22 @@ extern "C" int mb_seed_batch_noalloc(const mb_index *idx, const uint8_t *seq, co
     {
         SmemArgs sa{I, seq, off, n_reads, mate, bs, l, c, kmer, slots, nslots, counts, ovf, dovf_n, nullptr, nullptr,
                     nullptr, nullptr, I.text2 && !(flags & MB_STEP_ONLY)};
+        smem_tuning(opts, sa);
+        sa.err = derr;
+        sa.chk = (flags & MB_CHECKED) ? derr : nullptr;
         MB_TRY(launch_smem(sa, false, false, 256, st));
     }
     MB_TRY(scan_exclusive_u64(counts, soff, nr, dtotal, S + o_tmp, st));
     u64 total = 0;
+    u32 err = 0;
     MB_CK(cudaMemcpyAsync(&total, dtotal, 8, cudaMemcpyDeviceToHost, st));
+    MB_CK(cudaMemcpyAsync(&err, derr, 4, cudaMemcpyDeviceToHost, st));
     MB_CK(cudaStreamSynchronize(st));
+    if (err) {
+        mb_set_error("mb_seed_batch_noalloc: device check failed (0x%x)", err);
+        return MB_ERR_DEVICE_CHECK;
+    }
+    MB_TRY(mb_check_span(out, total * sizeof(mb_smem), "mb_seed_batch_noalloc: out"));
     *n_out = total;
     if (total > cap) return MB_ERR_CAPACITY;
     if (total == 0) return MB_OK;
@@ -1485,6 +1767,8 @@ struct mb_plan {
     bool kmer = true, queue = false;
     int block = 256;
     u32 depth = 1;   // walks per lane in locate
+    bool split = true;   // SMEM kernel form and tuning
+    SmemTuning tune = {SMEM_BURST, SMEM_WAIT};
     u32 max_reads = 0;
     u64 max_bases = 0, max_smem = 0, max_hits = 0, nslots = 0;
     void *mem = nullptr;
@@ -1504,8 +1788,11 @@ struct mb_plan {
 };
 
 size_t mb_plan_bytes(const mb_plan *p) { return p ? p->bytes : 0; }
+// The plan's device error word: the upper half of misc[2] (its lower half counts the reads that
+// overflow their slots), so that misc[0..2] carry both counts and the error word in one copy.
+static u32 *plan_err(const mb_plan *p) { return (u32 *)(p->misc + 2) + 1; }
 int mb_plan_counts_async(mb_plan *p, u64 *host_counts, cudaStream_t st) {
-    MB_CK(cudaMemcpyAsync(host_counts, p->misc, 16, cudaMemcpyDeviceToHost, st));
+    MB_CK(cudaMemcpyAsync(host_counts, p->misc, 24, cudaMemcpyDeviceToHost, st));
     return MB_OK;
 }
 void mb_plan_arrays(const mb_plan *p, const mb_smem **smem, const u32 **hits, u64 *max_smem, u64 *max_hits) {
@@ -1513,6 +1800,30 @@ void mb_plan_arrays(const mb_plan *p, const mb_smem **smem, const u32 **hits, u6
     *hits = p->hits;
     *max_smem = p->max_smem;
     *max_hits = p->max_hits;
+}
+
+// Device workspace of a plan, one entry per array (in the order mb_plan_create lays them out).
+constexpr int PLAN_ARRAYS = 23;
+static void plan_sizes(const mb_opts *opts, u32 max_reads, u64 max_bases, u64 max_smem, u64 max_hits,
+                       size_t sizes[PLAN_ARRAYS]) {
+    const bool queue = opts && (opts->flags & MB_BATCHED);
+    const size_t nr = max_reads, ms = max_smem ? max_smem : 1, mh = max_hits ? max_hits : 1;
+    size_t tb = scan_tmp_bytes(nr > ms ? nr : ms);
+    const size_t rb = radix_tmp_bytes(nr), sb = share_tmp_bytes(ms);
+    if (rb > tb) tb = rb;
+    if (sb > tb) tb = sb;
+    const size_t z[PLAN_ARRAYS] = {slots_total(max_bases, max_reads) * sizeof(SlotRec), nr * 8, nr * 8, 256, ms * 8,
+                                   nr * 4, mh * 4, mh * 4, ms * sizeof(mb_smem), queue ? nr * 8 : 0,
+                                   queue ? nr * 8 : 0, queue ? nr * 4 : 0, queue ? nr * 4 : 0, tb, ms * 4,
+                                   ms * 8, ms * 8, ms * 8, ms * 4, ms * 4, ms * 4, ms * 4, mh * 4};
+    for (int i = 0; i < PLAN_ARRAYS; ++i) sizes[i] = z[i];
+}
+
+size_t mb_plan_workspace_bytes(const mb_opts *opts, u32 max_reads, u64 max_bases, u64 max_smem, u64 max_hits) {
+    size_t sizes[PLAN_ARRAYS], total = 0;
+    plan_sizes(opts, max_reads, max_bases, max_smem, max_hits, sizes);
+    for (size_t z : sizes) total += align_up(z);
+    return total;
 }
 
 extern "C" int mb_plan_create(const mb_index *idx, const mb_opts *opts, uint32_t max_reads, uint64_t max_bases,
@@ -1527,21 +1838,19 @@ extern "C" int mb_plan_create(const mb_index *idx, const mb_opts *opts, uint32_t
     P->block = opts && (opts->block_size == 128 || opts->block_size == 512) ? (int)opts->block_size : 256;
     const u32 dq = opts ? opts->prefetch_depth : 0;
     P->depth = dq >= 16 ? 16u : (dq >= 8 ? 8u : (dq >= 4 ? 4u : (dq >= 2 ? 2u : 1u)));
+    {
+        SmemArgs t{};
+        smem_tuning(opts, t);
+        P->split = t.split;
+        P->tune = t.tune;
+    }
     P->max_reads = max_reads;
     P->max_bases = max_bases;
     P->max_smem = max_smem ? max_smem : 1;
     P->max_hits = max_hits ? max_hits : 1;
     P->nslots = slots_total(max_bases, max_reads);
-    const size_t nr = max_reads;
-    size_t tb = scan_tmp_bytes(nr > P->max_smem ? nr : P->max_smem);
-    const size_t rb = radix_tmp_bytes(nr), sb = share_tmp_bytes(P->max_smem);
-    if (rb > tb) tb = rb;
-    if (sb > tb) tb = sb;
-    const size_t ms = P->max_smem;
-    size_t sizes[] = {P->nslots * sizeof(SlotRec), nr * 8, nr * 8, 256, ms * 8, nr * 4, P->max_hits * 4,
-                      P->max_hits * 4, ms * sizeof(mb_smem), P->queue ? nr * 8 : 0, P->queue ? nr * 8 : 0,
-                      P->queue ? nr * 4 : 0, P->queue ? nr * 4 : 0, tb, ms * 4,
-                      ms * 8, ms * 8, ms * 8, ms * 4, ms * 4, ms * 4, ms * 4, P->max_hits * 4};
+    size_t sizes[PLAN_ARRAYS];
+    plan_sizes(opts, max_reads, max_bases, max_smem, max_hits, sizes);
     size_t total = 0;
     for (size_t z : sizes) total += align_up(z);
     if (cudaMalloc(&P->mem, total) != cudaSuccess) {
@@ -1552,13 +1861,14 @@ extern "C" int mb_plan_create(const mb_index *idx, const mb_opts *opts, uint32_t
     }
     P->bytes = total;
     char *m = (char *)P->mem;
-    void **ptrs[] = {(void **)&P->slots, (void **)&P->counts, (void **)&P->soff, (void **)&P->misc, (void **)&P->hitc,
-                     (void **)&P->ovf, (void **)&P->rows, (void **)&P->hits, (void **)&P->out, (void **)&P->skeys,
-                     (void **)&P->skeys_alt, (void **)&P->perm, (void **)&P->perm_alt, (void **)&P->tmp,
-                     (void **)&P->known, (void **)&P->share.keys, (void **)&P->share.keys_alt,
-                     (void **)&P->share.roff, (void **)&P->share.vals, (void **)&P->share.vals_alt,
-                     (void **)&P->share.pmax, (void **)&P->share.last, (void **)&P->share.rpos};
-    for (size_t i = 0; i < sizeof(sizes) / sizeof(sizes[0]); ++i) {
+    void **ptrs[PLAN_ARRAYS] = {(void **)&P->slots, (void **)&P->counts, (void **)&P->soff, (void **)&P->misc,
+                                (void **)&P->hitc, (void **)&P->ovf, (void **)&P->rows, (void **)&P->hits,
+                                (void **)&P->out, (void **)&P->skeys, (void **)&P->skeys_alt, (void **)&P->perm,
+                                (void **)&P->perm_alt, (void **)&P->tmp, (void **)&P->known, (void **)&P->share.keys,
+                                (void **)&P->share.keys_alt, (void **)&P->share.roff, (void **)&P->share.vals,
+                                (void **)&P->share.vals_alt, (void **)&P->share.pmax, (void **)&P->share.last,
+                                (void **)&P->share.rpos};
+    for (int i = 0; i < PLAN_ARRAYS; ++i) {
         *ptrs[i] = sizes[i] ? (void *)m : nullptr;
         m += align_up(sizes[i]);
     }
@@ -1566,6 +1876,8 @@ extern "C" int mb_plan_create(const mb_index *idx, const mb_opts *opts, uint32_t
     P->share.nrows = P->misc + 4;
     P->share.nwalk = P->misc + 5;
     P->share.tmp = P->tmp;
+    P->share.err = plan_err(P);
+    P->share.checked = (P->flags & MB_CHECKED) != 0;
     *out = P;
     return MB_OK;
 }
@@ -1591,7 +1903,7 @@ static int plan_seed(mb_plan *P, const uint8_t *seq, const uint64_t *off, uint32
     const DevIndex I = mb_dev_index(P->idx);
     const u32 bs = (P->flags & MB_BS3) ? 1u : 0u;
     u64 *n_smem = P->misc, *n_hits = P->misc + 1;
-    u32 *ovf_n = (u32 *)(P->misc + 2), *qhead = (u32 *)(P->misc + 3);
+    u32 *ovf_n = (u32 *)(P->misc + 2), *qhead = (u32 *)(P->misc + 3), *err = plan_err(P);
     MB_CK(cudaMemsetAsync(P->hitc, 0, P->max_smem * 8, st));   // zero tail for the fixed-length scan
     const u32 *perm = nullptr;
     if (P->queue) {   // work queue in order of decreasing read length
@@ -1603,6 +1915,10 @@ static int plan_seed(mb_plan *P, const uint8_t *seq, const uint64_t *off, uint32
     }
     SmemArgs sa{I, seq, off, n_reads, mate, bs, P->l, P->c, P->kmer, P->slots, P->nslots, P->counts, P->ovf, ovf_n,
                 perm, qhead, nullptr, nullptr, I.text2 && !(P->flags & MB_STEP_ONLY)};
+    sa.split = P->split;
+    sa.tune = P->tune;
+    sa.err = err;
+    sa.chk = (P->flags & MB_CHECKED) ? err : nullptr;
     MB_TRY(launch_smem(sa, false, P->queue, P->block, st));
     MB_TRY(scan_exclusive_u64(P->counts, P->soff, n_reads, n_smem, P->tmp, st));
     const unsigned G = (unsigned)((n_reads + 255) / 256);
@@ -1639,9 +1955,13 @@ extern "C" int mb_plan_result(mb_plan *P, void *stream, const mb_smem **smem, ui
                               uint64_t *n_hits) {
     if (!P) return MB_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    u64 v[2] = {0, 0};
-    MB_CK(cudaMemcpyAsync(v, P->misc, 16, cudaMemcpyDeviceToHost, st));
+    u64 v[3] = {0, 0, 0};
+    MB_CK(cudaMemcpyAsync(v, P->misc, 24, cudaMemcpyDeviceToHost, st));
     MB_CK(cudaStreamSynchronize(st));
+    if (v[2] >> 32) {
+        mb_set_error("mb_plan_result: device check failed (0x%x)", (unsigned)(v[2] >> 32));
+        return MB_ERR_DEVICE_CHECK;
+    }
     if (n_smem) *n_smem = v[0];
     if (n_hits) *n_hits = v[1];
     if (smem) *smem = P->out;

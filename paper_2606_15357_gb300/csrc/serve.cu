@@ -1,20 +1,30 @@
 // Served form: continuous batching of seeding requests (the whole stage of Section 2.5 and
 // Algorithm 2 per request) on one GPU.
 //
-// A worker thread owns a set of execution slots (a stream, a seeding plan and pinned staging
-// buffers each, as many as fit the HBM budget).  Whenever a slot is free it merges every waiting
-// request that still fits the slot's limits into one launch group, copies the group in, runs the
-// plan and records an event; completion is handled in two asynchronous phases (the two result
-// counts, then the results themselves), so the worker never blocks on the GPU and groups on
-// different slots overlap on the device.  Each request gets back exactly what mb_seed_batch +
-// mb_locate give for it alone: read numbers and hit offsets are made relative to the request.
+// Submitting copies a request's bases into a pinned staging ring (on the caller's thread) and
+// queues it.  A worker thread owns the execution slots (a stream, a seeding plan and the device
+// copies of one launch group each).  Whenever a slot is free it merges every waiting request that
+// still fits the slot's limits into one group, copies the group in straight from the ring, runs
+// the plan and records an event; completion is handled in two asynchronous phases (the two result
+// counts, then the results), so the worker never blocks on the GPU and groups on different slots
+// overlap on the device.  Each request gets back exactly what mb_seed_batch + mb_locate give for
+// it alone: read numbers and hit offsets are made relative to the request.
+//
+// Admission by free device memory: slots are created only when work is waiting and no slot is
+// free, and only while the free device memory (cudaMemGetInfo) minus a reserve left to other
+// users holds one more slot and the slots stay within the caller's budget; otherwise requests wait
+// for a slot to free.  When free memory falls below the reserve, idle slots are released.  A group
+// that yields more records or hits than its plan holds is handed to a second thread, which seeds
+// its requests one by one with the allocating entry points, so the worker keeps serving.
 #include <chrono>
 #include <condition_variable>
 #include <deque>
 #include <memory>
 #include <mutex>
+#include <string.h>
 #include <thread>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 #include "common.cuh"
 
@@ -25,16 +35,57 @@ constexpr u64 SLOT_BASES = 64ull << 20;
 constexpr u64 SLOT_SMEM = 2ull << 20;
 constexpr u64 SLOT_HITS = 32ull << 20;
 constexpr int MAX_SLOTS = 16;
+constexpr u64 RING_BYTES = 1ull << 30;         // pinned staging of submitted bases
+constexpr u64 RESERVE_MIN = 1ull << 30;        // free device memory left to other users (at least)
+constexpr double MEM_POLL_MS = 1.0;            // how often the worker may query free memory
 
 double now_ms() {
     using namespace std::chrono;
     return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
 }
 
+// Pinned ring of request bases.  Positions grow monotonically (physical = pos % size); a request
+// never wraps (it starts again at the beginning when it does not fit before the end).  Space is
+// given back when the oldest live request is released, so requests that finish out of order wait
+// for the ones before them.
+struct Ring {
+    u8 *base = nullptr;
+    u64 size = 0, head = 0;
+    std::deque<u64> beg, end;      // live allocations in order
+    std::deque<bool> released;
+    u64 tail() const { return beg.empty() ? head : beg.front(); }
+    bool alloc(u64 bytes, u64 &pos) {
+        u64 p = head;
+        const u64 phys = p % size;
+        if (phys + bytes > size) p += size - phys;
+        if (p + bytes - tail() > size) return false;
+        pos = p;
+        head = p + bytes;
+        beg.push_back(p);
+        end.push_back(head);
+        released.push_back(false);
+        return true;
+    }
+    void release(u64 pos) {
+        for (size_t i = 0; i < beg.size(); ++i)
+            if (beg[i] == pos && !released[i]) {
+                released[i] = true;
+                break;
+            }
+        while (!beg.empty() && released.front()) {
+            beg.pop_front();
+            end.pop_front();
+            released.pop_front();
+        }
+    }
+    u8 *at(u64 pos) const { return base + pos % size; }
+};
+
 struct Request {
     u64 ticket = 0;
-    std::vector<u8> seq;
-    std::vector<u64> off;   // n_reads + 1, from 0
+    u64 ring_pos = 0;        // its bases in the ring
+    const u8 *seq = nullptr; // = ring.at(ring_pos)
+    std::vector<u64> off;    // n_reads + 1, from 0
     u32 n_reads = 0;
     double t_submit = 0, latency_ms = 0;
     bool done = false;
@@ -51,9 +102,8 @@ struct Slot {
     mb_plan *plan = nullptr;
     u8 *dseq = nullptr;
     u64 *doff = nullptr;
-    u8 *hseq = nullptr;       // pinned
     u64 *hoff = nullptr;      // pinned
-    u64 *hcnt = nullptr;      // pinned: n_smem, n_hits
+    u64 *hcnt = nullptr;      // pinned: n_smem, n_hits, the device error word
     mb_smem *hsmem = nullptr; // pinned
     u32 *hhits = nullptr;     // pinned
     cudaEvent_t ev = nullptr;
@@ -61,32 +111,52 @@ struct Slot {
     std::vector<ReqP> group;
     std::vector<u32> first_read;   // first group read of each request
     u32 n_reads = 0;
+    size_t dev_bytes = 0;
+    double idle_since = 0;
 };
+
+// live servers: calls on a destroyed server are refused instead of touching freed memory
+std::mutex g_live_mu;
+std::unordered_set<const mb_server *> g_live;
+bool alive(const mb_server *S) {
+    std::lock_guard<std::mutex> g(g_live_mu);
+    return S && g_live.count(S) != 0;
+}
 
 }  // namespace
 
 struct mb_server {
     const mb_index *idx = nullptr;
     mb_opts opts{};
-    std::vector<Slot> slots;
+    int device = 0;
+    u64 budget = 0;            // device bytes the slots may hold in all (0 = no cap but free memory)
+    u64 reserve = RESERVE_MIN;
+    size_t slot_bytes = 0;     // device bytes of one slot
+    std::vector<std::unique_ptr<Slot>> slots;
+    Ring ring;
     std::mutex mu;
     std::condition_variable cv;
     std::deque<ReqP> pending;
     std::unordered_map<u64, ReqP> reqs;
-    std::thread worker;
-    bool stop = false;
+    std::thread worker, helper;
+    std::deque<std::vector<ReqP>> outgrown;   // groups for the helper thread
+    bool stop = false, helper_stop = false;
     u64 next_ticket = 1;
-    u64 groups = 0, merged = 0;
-    int device = 0;
+    // counters (mb_serve_counters)
+    u64 groups = 0, merged = 0, created = 0, retired = 0, alloc_failures = 0, fallback_groups = 0, busy = 0;
+    double mem_wait_ms = 0;
+    // fault injection for tests (mb_serve_inject)
+    int64_t fake_free = -1;    // free device bytes reported to admission instead of cudaMemGetInfo's
+    u32 fail_next = 0;         // slot creations to fail
 };
 
 namespace {
 
 void free_slot(Slot &s) {
+    if (s.st) cudaStreamSynchronize(s.st);
     if (s.plan) mb_plan_free(s.plan);
     if (s.dseq) cudaFree(s.dseq);
     if (s.doff) cudaFree(s.doff);
-    if (s.hseq) cudaFreeHost(s.hseq);
     if (s.hoff) cudaFreeHost(s.hoff);
     if (s.hcnt) cudaFreeHost(s.hcnt);
     if (s.hsmem) cudaFreeHost(s.hsmem);
@@ -96,22 +166,86 @@ void free_slot(Slot &s) {
     s = Slot{};
 }
 
+size_t slot_device_bytes(const mb_opts *o) {
+    return mb_plan_workspace_bytes(o, SLOT_READS, SLOT_BASES, SLOT_SMEM, SLOT_HITS) + SLOT_BASES + 16 +
+           (SLOT_READS + 1) * 8;
+}
+
 int make_slot(mb_server *S, Slot &s) {
     if (cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
         return MB_ERR_CUDA;
+    }
     MB_TRY(mb_plan_create(S->idx, &S->opts, SLOT_READS, SLOT_BASES, SLOT_SMEM, SLOT_HITS, &s.plan));
-    if (cudaMalloc(&s.dseq, SLOT_BASES) != cudaSuccess || cudaMalloc(&s.doff, (SLOT_READS + 1) * 8) != cudaSuccess ||
-        cudaMallocHost(&s.hseq, SLOT_BASES) != cudaSuccess || cudaMallocHost(&s.hoff, (SLOT_READS + 1) * 8) != cudaSuccess ||
-        cudaMallocHost(&s.hcnt, 16) != cudaSuccess || cudaMallocHost(&s.hsmem, SLOT_SMEM * sizeof(mb_smem)) != cudaSuccess ||
+    if (cudaMalloc(&s.dseq, SLOT_BASES + 16) != cudaSuccess || cudaMalloc(&s.doff, (SLOT_READS + 1) * 8) != cudaSuccess ||
+        cudaMallocHost(&s.hoff, (SLOT_READS + 1) * 8) != cudaSuccess || cudaMallocHost(&s.hcnt, 32) != cudaSuccess ||
+        cudaMallocHost(&s.hsmem, SLOT_SMEM * sizeof(mb_smem)) != cudaSuccess ||
         cudaMallocHost(&s.hhits, SLOT_HITS * 4) != cudaSuccess) {
         cudaGetLastError();
         return MB_ERR_NOMEM;
     }
+    s.dev_bytes = mb_plan_bytes(s.plan) + SLOT_BASES + 16 + (SLOT_READS + 1) * 8;
     return MB_OK;
 }
 
-size_t slot_device_bytes(const Slot &s) { return mb_plan_bytes(s.plan) + SLOT_BASES + (SLOT_READS + 1) * 8; }
+// Free device memory as admission sees it.
+u64 free_device_bytes(mb_server *S) {
+    if (S->fake_free >= 0) return (u64)S->fake_free;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return fr;
+}
+
+u64 slots_bytes(const mb_server *S) {
+    u64 b = 0;
+    for (const auto &s : S->slots) b += s->dev_bytes;
+    return b;
+}
+
+// One more slot if the free device memory and the budget allow it (worker thread, lock not held).
+// Returns true if a slot was added.
+bool grow(mb_server *S) {
+    if ((int)S->slots.size() >= MAX_SLOTS) return false;
+    if (S->budget && slots_bytes(S) + S->slot_bytes > S->budget && !S->slots.empty()) return false;
+    if (free_device_bytes(S) < S->reserve + S->slot_bytes) return false;
+    std::unique_ptr<Slot> s(new Slot);
+    int rc = MB_OK;
+    {
+        std::lock_guard<std::mutex> g(S->mu);   // an allocation failure injected by mb_serve_inject
+        rc = S->fail_next ? (--S->fail_next, MB_ERR_NOMEM) : MB_OK;
+    }
+    if (rc == MB_OK) rc = make_slot(S, *s);
+    if (rc != MB_OK) {
+        free_slot(*s);
+        std::lock_guard<std::mutex> g(S->mu);
+        ++S->alloc_failures;
+        return false;
+    }
+    std::lock_guard<std::mutex> g(S->mu);
+    S->slots.push_back(std::move(s));
+    ++S->created;
+    return true;
+}
+
+// Idle slots are released while free device memory is below the reserve (worker thread).
+void retire(mb_server *S) {
+    if (free_device_bytes(S) >= S->reserve) return;
+    for (size_t i = 0; i < S->slots.size();) {
+        if (S->slots[i]->phase == IDLE) {
+            free_slot(*S->slots[i]);
+            std::lock_guard<std::mutex> g(S->mu);
+            S->slots.erase(S->slots.begin() + i);
+            ++S->retired;
+            if (free_device_bytes(S) >= S->reserve) return;
+        } else {
+            ++i;
+        }
+    }
+}
 
 // Merge waiting requests into the free slot s (called with the lock held).  Returns false if
 // nothing is waiting.
@@ -135,18 +269,29 @@ bool admit(mb_server *S, Slot &s) {
     return true;
 }
 
-// Copy the group in and run it (lock not held).
+// Copy the group in from the ring and run it (lock not held).
 int launch(mb_server *S, Slot &s) {
     u64 nb = 0;
     u32 nr = 0;
     s.hoff[0] = 0;
+    // consecutive requests are usually contiguous in the ring: one copy per contiguous run
+    const u8 *run = nullptr;
+    u64 run_len = 0, run_dst = 0;
     for (const ReqP &r : s.group) {
-        memcpy(s.hseq + nb, r->seq.data(), r->seq.size());
+        const u64 b = r->off[r->n_reads];
         for (u32 i = 0; i < r->n_reads; ++i) s.hoff[nr + i + 1] = nb + r->off[i + 1];
-        nb += r->seq.size();
+        if (run && run + run_len == r->seq) {
+            run_len += b;
+        } else {
+            if (run_len) MB_CK(cudaMemcpyAsync(s.dseq + run_dst, run, run_len, cudaMemcpyHostToDevice, s.st));
+            run = r->seq;
+            run_len = b;
+            run_dst = nb;
+        }
+        nb += b;
         nr += r->n_reads;
     }
-    MB_CK(cudaMemcpyAsync(s.dseq, s.hseq, nb ? nb : 1, cudaMemcpyHostToDevice, s.st));
+    if (run_len) MB_CK(cudaMemcpyAsync(s.dseq + run_dst, run, run_len, cudaMemcpyHostToDevice, s.st));
     MB_CK(cudaMemcpyAsync(s.doff, s.hoff, (size_t)(nr + 1) * 8, cudaMemcpyHostToDevice, s.st));
     MB_TRY(mb_plan_run(s.plan, s.dseq, s.doff, nr, nullptr, s.st));
     MB_TRY(mb_plan_counts_async(s.plan, s.hcnt, s.st));
@@ -155,31 +300,23 @@ int launch(mb_server *S, Slot &s) {
     return MB_OK;
 }
 
-// The group's counts are on the host: copy the results back (or fall back when a limit was hit).
+// The group's counts are on the host: copy the results back.  Returns 1 when the group outgrew
+// the plan (handed to the helper thread).
 int fetch(mb_server *S, Slot &s) {
     const u64 ns = s.hcnt[0], nh = s.hcnt[1];
+    if (s.hcnt[2] >> 32) return MB_ERR_DEVICE_CHECK;   // (the server builds the offsets itself)
     const mb_smem *dsm;
     const u32 *dh;
     u64 ms, mh;
     mb_plan_arrays(s.plan, &dsm, &dh, &ms, &mh);
     if (ns > ms || nh > mh) {
-        // the merged group outgrew the plan: seed its requests one by one with the allocating path
-        for (const ReqP &r : s.group) {
-            u64 m = 0, h = 0;
-            int rc = mb_seed_batch(S->idx, r->seq.data(), r->off.data(), r->n_reads, nullptr, &S->opts, s.st, nullptr,
-                                   0, &m, &h);
-            if (rc != MB_OK && rc != MB_ERR_CAPACITY) { r->status = rc; continue; }
-            r->smem.resize(m);
-            rc = mb_seed_batch(S->idx, r->seq.data(), r->off.data(), r->n_reads, nullptr, &S->opts, s.st,
-                               r->smem.data(), m, &m, &h);
-            if (rc == MB_OK) {
-                r->hits.resize(h);
-                rc = mb_locate(S->idx, r->smem.data(), m, &S->opts, s.st, r->hits.data(), h, &h);
-            }
-            r->status = rc;
-        }
+        std::lock_guard<std::mutex> g(S->mu);
+        S->outgrown.push_back(s.group);
+        ++S->fallback_groups;
+        S->cv.notify_all();
+        s.group.clear();
         s.phase = IDLE;
-        return 1;   // results are final
+        return 1;
     }
     if (ns) MB_CK(cudaMemcpyAsync(s.hsmem, dsm, ns * sizeof(mb_smem), cudaMemcpyDeviceToHost, s.st));
     if (nh) MB_CK(cudaMemcpyAsync(s.hhits, dh, nh * 4, cudaMemcpyDeviceToHost, s.st));
@@ -209,35 +346,49 @@ void split(Slot &s) {
     }
 }
 
-void finish(mb_server *S, Slot &s) {
+// Requests done: latency, ring space back, waiters woken (lock taken here).
+void complete(mb_server *S, const std::vector<ReqP> &group) {
     const double t = now_ms();
     std::lock_guard<std::mutex> g(S->mu);
-    for (const ReqP &r : s.group) {
+    for (const ReqP &r : group) {
         r->latency_ms = t - r->t_submit;
         r->done = true;
+        S->ring.release(r->ring_pos);
     }
     S->groups += 1;
-    if (s.group.size() > 1) S->merged += s.group.size();
+    if (group.size() > 1) S->merged += group.size();
+    S->cv.notify_all();
+}
+
+void finish(mb_server *S, Slot &s) {
+    complete(S, s.group);
     s.group.clear();
     s.phase = IDLE;
-    S->cv.notify_all();
+    s.idle_since = now_ms();
 }
 
 void worker_loop(mb_server *S) {
     cudaSetDevice(S->device);
+    double last_mem = -1e30, waiting_since = -1;
     for (;;) {
-        bool any_busy = false;
+        bool any_busy = false, waiting = false;
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            for (Slot &s : S->slots) any_busy |= s.phase != IDLE;
+            for (const auto &s : S->slots) any_busy |= s->phase != IDLE;
             if (S->stop && S->pending.empty() && !any_busy) return;
             if (S->pending.empty() && !any_busy) {
-                S->cv.wait(lk, [&] { return S->stop || !S->pending.empty(); });
+                S->cv.wait_for(lk, std::chrono::milliseconds(50), [&] { return S->stop || !S->pending.empty(); });
+                if (S->pending.empty()) {
+                    lk.unlock();
+                    retire(S);   // nothing to do: give memory back if others need it
+                }
                 continue;
             }
+            waiting = !S->pending.empty();
         }
-        bool progressed = false;
-        for (Slot &s : S->slots) {
+        bool progressed = false, idle_slot = false;
+        for (auto &sp : S->slots) {
+            Slot &s = *sp;
             if (s.phase == IDLE) {
                 bool got;
                 {
@@ -250,12 +401,13 @@ void worker_loop(mb_server *S) {
                         finish(S, s);
                     }
                     progressed = true;
+                } else {
+                    idle_slot = true;
                 }
             } else if (cudaEventQuery(s.ev) == cudaSuccess) {
                 if (s.phase == RUNNING) {
-                    int rc = fetch(S, s);
-                    if (rc == 1) finish(S, s);
-                    else if (rc != MB_OK) {
+                    const int rc = fetch(S, s);
+                    if (rc != MB_OK && rc != 1) {
                         for (const ReqP &r : s.group) r->status = rc;
                         finish(S, s);
                     }
@@ -266,8 +418,60 @@ void worker_loop(mb_server *S) {
                 progressed = true;
             }
         }
+        // work waits and every slot is busy: admission by free device memory may add a slot
+        const double t = now_ms();
+        if (waiting && !idle_slot && !progressed && t - last_mem >= MEM_POLL_MS) {
+            last_mem = t;
+            if (grow(S)) {
+                progressed = true;
+                waiting_since = -1;
+            } else if (waiting_since < 0) {
+                waiting_since = t;
+            }
+        }
+        if (progressed && waiting_since >= 0) {
+            std::lock_guard<std::mutex> g(S->mu);
+            S->mem_wait_ms += t - waiting_since;
+            waiting_since = -1;
+        }
         if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
+}
+
+// Groups that outgrew their plan: each request alone through the allocating entry points, on the
+// helper thread's own stream (the worker is not held up).
+void helper_loop(mb_server *S) {
+    cudaSetDevice(S->device);
+    cudaStream_t st = nullptr;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    for (;;) {
+        std::vector<ReqP> group;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv.wait(lk, [&] { return S->helper_stop || !S->outgrown.empty(); });
+            if (S->outgrown.empty()) break;
+            group = std::move(S->outgrown.front());
+            S->outgrown.pop_front();
+        }
+        for (const ReqP &r : group) {
+            u64 m = 0, h = 0;
+            int rc = mb_seed_batch(S->idx, r->seq, r->off.data(), r->n_reads, nullptr, &S->opts, st, nullptr, 0, &m, &h);
+            if (rc != MB_OK && rc != MB_ERR_CAPACITY) {
+                r->status = rc;
+                continue;
+            }
+            r->smem.resize(m);
+            rc = mb_seed_batch(S->idx, r->seq, r->off.data(), r->n_reads, nullptr, &S->opts, st, r->smem.data(), m,
+                               &m, &h);
+            if (rc == MB_OK) {
+                r->hits.resize(h);
+                rc = mb_locate(S->idx, r->smem.data(), m, &S->opts, st, r->hits.data(), h, &h);
+            }
+            r->status = rc;
+        }
+        complete(S, group);
+    }
+    if (st) cudaStreamDestroy(st);
 }
 
 }  // namespace
@@ -275,43 +479,41 @@ void worker_loop(mb_server *S) {
 extern "C" int mb_serve_create(const mb_index *idx, const mb_opts *opts, uint64_t hbm_budget, mb_server **out) {
     if (!idx || !out) return MB_ERR_ARG;
     *out = nullptr;
-    mb_server *S = new mb_server;
+    std::unique_ptr<mb_server> S(new mb_server);
     S->idx = idx;
     if (opts) S->opts = *opts;
     S->opts.flags |= MB_BATCHED;
     S->opts.flags &= ~(u32)MB_COUNT;
-    cudaGetDevice(&S->device);
-    u64 used = 0;
-    for (int i = 0; i < MAX_SLOTS; ++i) {
-        size_t fr = 0, tot = 0;
-        cudaMemGetInfo(&fr, &tot);
-        Slot s;
-        int rc = make_slot(S, s);
-        if (rc != MB_OK) {
-            free_slot(s);
-            if (i == 0) {
-                delete S;
-                mb_set_error("mb_serve_create: cannot create one execution slot");
-                return rc;
-            }
-            break;
-        }
-        const u64 b = slot_device_bytes(s);
-        if (i > 0 && used + b > hbm_budget) {
-            free_slot(s);
-            break;
-        }
-        used += b;
-        S->slots.push_back(s);
+    MB_CK(cudaGetDevice(&S->device));
+    S->budget = hbm_budget;
+    size_t fr = 0, tot = 0;
+    MB_CK(cudaMemGetInfo(&fr, &tot));
+    S->reserve = tot / 50 > RESERVE_MIN ? tot / 50 : RESERVE_MIN;
+    S->slot_bytes = slot_device_bytes(&S->opts);
+    S->ring.size = RING_BYTES;
+    if (cudaMallocHost(&S->ring.base, RING_BYTES) != cudaSuccess) {
+        cudaGetLastError();
+        mb_set_error("mb_serve_create: cannot allocate %llu bytes of pinned staging", (unsigned long long)RING_BYTES);
+        return MB_ERR_NOMEM;
     }
-    S->worker = std::thread(worker_loop, S);
-    *out = S;
+    mb_server *p = S.release();
+    {
+        std::lock_guard<std::mutex> g(g_live_mu);
+        g_live.insert(p);
+    }
+    p->worker = std::thread(worker_loop, p);
+    p->helper = std::thread(helper_loop, p);
+    *out = p;
     return MB_OK;
 }
 
 extern "C" int mb_serve_submit(mb_server *S, const uint8_t *seq, const uint64_t *off, uint32_t n_reads,
                                uint64_t *ticket) {
-    if (!S || !ticket || !off || (n_reads && !seq)) return MB_ERR_ARG;
+    if (!alive(S)) {
+        mb_set_error("mb_serve_submit: not a live server (destroyed?)");
+        return MB_ERR_ARG;
+    }
+    if (!ticket || !off || (n_reads && !seq)) return MB_ERR_ARG;
     auto r = std::make_shared<Request>();
     r->n_reads = n_reads;
     r->off.resize((size_t)n_reads + 1);
@@ -322,10 +524,20 @@ extern "C" int mb_serve_submit(mb_server *S, const uint8_t *seq, const uint64_t 
                      (unsigned long long)nb, SLOT_READS, (unsigned long long)SLOT_BASES);
         return MB_ERR_ARG;
     }
-    r->seq.assign(seq + off[0], seq + off[0] + nb);
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        if (S->stop) return MB_ERR_ARG;
+        if (!S->ring.alloc(nb ? nb : 1, r->ring_pos)) {
+            ++S->busy;
+            mb_set_error("mb_serve_submit: the staging ring is full (%llu bytes of requests outstanding)",
+                         (unsigned long long)(S->ring.head - S->ring.tail()));
+            return MB_ERR_BUSY;
+        }
+        r->seq = S->ring.at(r->ring_pos);
+    }
+    memcpy((void *)r->seq, seq + off[0], nb);   // the caller's thread stages the bases (pinned)
     r->t_submit = now_ms();
     std::lock_guard<std::mutex> g(S->mu);
-    if (S->stop) return MB_ERR_ARG;
     r->ticket = S->next_ticket++;
     S->reqs[r->ticket] = r;
     S->pending.push_back(r);
@@ -335,7 +547,7 @@ extern "C" int mb_serve_submit(mb_server *S, const uint8_t *seq, const uint64_t 
 }
 
 extern "C" int mb_serve_poll(mb_server *S, uint64_t ticket, int *done) {
-    if (!S || !done) return MB_ERR_ARG;
+    if (!alive(S) || !done) return MB_ERR_ARG;
     std::lock_guard<std::mutex> g(S->mu);
     auto it = S->reqs.find(ticket);
     if (it == S->reqs.end()) return MB_ERR_ARG;
@@ -345,7 +557,7 @@ extern "C" int mb_serve_poll(mb_server *S, uint64_t ticket, int *done) {
 
 extern "C" int mb_serve_wait(mb_server *S, uint64_t ticket, uint32_t timeout_ms, const mb_smem **smem,
                              uint64_t *n_smem, const uint32_t **hits, uint64_t *n_hits, double *latency_ms) {
-    if (!S) return MB_ERR_ARG;
+    if (!alive(S)) return MB_ERR_ARG;
     std::unique_lock<std::mutex> lk(S->mu);
     auto it = S->reqs.find(ticket);
     if (it == S->reqs.end()) return MB_ERR_ARG;
@@ -363,7 +575,7 @@ extern "C" int mb_serve_wait(mb_server *S, uint64_t ticket, uint32_t timeout_ms,
 }
 
 extern "C" int mb_serve_release(mb_server *S, uint64_t ticket) {
-    if (!S) return MB_ERR_ARG;
+    if (!alive(S)) return MB_ERR_ARG;
     std::lock_guard<std::mutex> g(S->mu);
     auto it = S->reqs.find(ticket);
     if (it == S->reqs.end() || !it->second->done) return MB_ERR_ARG;
@@ -372,7 +584,7 @@ extern "C" int mb_serve_release(mb_server *S, uint64_t ticket) {
 }
 
 extern "C" int mb_serve_stats(mb_server *S, uint32_t *slots, uint64_t *groups, uint64_t *merged) {
-    if (!S) return MB_ERR_ARG;
+    if (!alive(S)) return MB_ERR_ARG;
     std::lock_guard<std::mutex> g(S->mu);
     if (slots) *slots = (uint32_t)S->slots.size();
     if (groups) *groups = S->groups;
@@ -380,18 +592,44 @@ extern "C" int mb_serve_stats(mb_server *S, uint32_t *slots, uint64_t *groups, u
     return MB_OK;
 }
 
+extern "C" int mb_serve_counters(mb_server *S, uint64_t *out, uint32_t count) {
+    if (!alive(S) || (count && !out)) return MB_ERR_ARG;
+    std::lock_guard<std::mutex> g(S->mu);
+    const u64 v[] = {S->slots.size(), S->groups, S->merged, S->created, S->retired, S->alloc_failures,
+                     S->fallback_groups, S->busy, (u64)S->mem_wait_ms, S->slot_bytes, S->reserve};
+    for (u32 i = 0; i < count && i < sizeof(v) / sizeof(v[0]); ++i) out[i] = v[i];
+    return MB_OK;
+}
+
+extern "C" int mb_serve_inject(mb_server *S, int64_t free_bytes, uint32_t fail_slots) {
+    if (!alive(S)) return MB_ERR_ARG;
+    std::lock_guard<std::mutex> g(S->mu);
+    S->fake_free = free_bytes;
+    S->fail_next = fail_slots;
+    S->cv.notify_all();
+    return MB_OK;
+}
+
 extern "C" int mb_serve_destroy(mb_server *S) {
-    if (!S) return MB_ERR_ARG;
+    {
+        std::lock_guard<std::mutex> g(g_live_mu);
+        if (!S || !g_live.count(S)) return MB_ERR_ARG;
+        g_live.erase(S);
+    }
     {
         std::lock_guard<std::mutex> g(S->mu);
         S->stop = true;
         S->cv.notify_all();
     }
     if (S->worker.joinable()) S->worker.join();
-    for (Slot &s : S->slots) {
-        cudaStreamSynchronize(s.st);
-        free_slot(s);
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        S->helper_stop = true;
+        S->cv.notify_all();
     }
+    if (S->helper.joinable()) S->helper.join();
+    for (auto &s : S->slots) free_slot(*s);
+    if (S->ring.base) cudaFreeHost(S->ring.base);
     delete S;
     return MB_OK;
 }

@@ -170,3 +170,85 @@ def test_served_mix_on_100mbp_index_against_oracle(mb):
         assert sm.tobytes() == want_sm.tobytes(), q
         assert np.array_equal(hits, want_hits), q
         same_as_oracle(X, r, sm, hits, frac=0.05, seed=q)
+
+
+def test_admission_waits_for_free_device_memory(mb, served):
+    """Admission by free device memory: with the free memory admission sees held at 0 no slot can
+    be made and a submitted request waits; once the real value is back it is served, with the
+    same results as alone."""
+    ref, G, X = served
+    srv = mb.Server(G, hbm_budget=1 << 30)
+    srv.inject(free_bytes=0)
+    r = requests(ref, 1, 11)[0]
+    t = srv.submit(r.seq, r.off)
+    import time
+    time.sleep(0.3)
+    assert not srv.poll(t)
+    c = srv.counters()
+    assert c["slots"] == 0 and c["slots_created"] == 0
+    srv.inject(free_bytes=-1)
+    sm, hits, lat = srv.wait(t)
+    assert lat >= 300
+    want_sm, want_hits = mb.seed(G, r.seq, r.off)
+    assert sm.tobytes() == want_sm.tobytes() and np.array_equal(hits, want_hits)
+    c = srv.counters()
+    assert c["slots_created"] >= 1 and c["memory_wait_ms"] >= 250
+    srv.close()
+
+
+def test_slot_allocation_failure_is_retried(mb, served):
+    """Two slot creations fail (injected as allocation failures): admission retries, the third
+    succeeds and the request is served correctly."""
+    ref, G, X = served
+    srv = mb.Server(G, hbm_budget=1 << 30)
+    srv.inject(free_bytes=-1, fail_slots=2)
+    r = requests(ref, 1, 12)[0]
+    sm, hits, _ = srv.wait(srv.submit(r.seq, r.off))
+    c = srv.counters()
+    assert c["alloc_failures"] == 2 and c["slots_created"] >= 1
+    want_sm, want_hits = mb.seed(G, r.seq, r.off)
+    assert sm.tobytes() == want_sm.tobytes() and np.array_equal(hits, want_hits)
+    srv.close()
+
+
+def test_calls_after_destroy_are_refused(mb, served):
+    """Submit, poll, stats and destroy on a destroyed server return MB_ERR_ARG (no use after free)."""
+    import ctypes
+    ref, G, X = served
+    srv = mb.Server(G, hbm_budget=1 << 30)
+    h = srv._h
+    srv.close()
+    L = mb.lib()
+    r = requests(ref, 1, 13)[0]
+    t = ctypes.c_uint64()
+    seq = np.ascontiguousarray(r.seq)
+    off = np.ascontiguousarray(r.off, dtype=np.uint64)
+    assert L.mb_serve_submit(h, ctypes.c_void_p(seq.ctypes.data), ctypes.c_void_p(off.ctypes.data), r.n,
+                             ctypes.byref(t)) == -1
+    d = ctypes.c_int()
+    assert L.mb_serve_poll(h, 1, ctypes.byref(d)) == -1
+    assert L.mb_serve_destroy(h) == -1
+
+
+def test_group_outgrowing_its_plan_goes_to_the_helper(mb):
+    """Requests of 60,000 random reads seeded with min_len 5 against a 200 kbp reference: each read
+    has dozens of SMEMs, so a request yields more records than a slot's 2M; its group is seeded
+    again on the helper thread and every request still equals the plain entry points."""
+    ref = synth.reference(200_000, 81)
+    G = mb.mb_index_build(ref)
+    o = dict(min_len=5, max_occ=500)
+    srv = mb.Server(G, hbm_budget=2 << 30, opts=o)
+    reqs = []
+    for q in range(2):
+        reads = synth.reference(150 * 60_000, 8300 + q)
+        off = np.arange(60_001, dtype=np.uint64) * 150
+        reqs.append((reads, off))
+    tickets = [srv.submit(s_, o_) for s_, o_ in reqs]
+    got = [srv.wait(t) for t in tickets]
+    c = srv.counters()
+    srv.close()
+    assert c["outgrown_groups"] >= 1
+    for (s_, o_), (sm, hits, _) in zip(reqs, got):
+        want_sm, want_hits = mb.seed(G, s_, o_, opts=o)
+        assert sm.tobytes() == want_sm.tobytes()
+        assert np.array_equal(hits, want_hits)
