@@ -311,8 +311,10 @@ def run_reference(args):
 # --------------------------------------------------------------------------------- batched / served
 def bench_batched(mb, torch, dev, reps: int = 3):
     """Mixed-length workload (100 Mbp repeat-rich reference, 200,000 reads of 100 bp-10 kb):
-    one plain mb_seed_batch + mb_locate launch per length bucket, against the batched form
-    (autotuned plan, device work queue, replayed CUDA graph).  Output compared for identity."""
+    one plain launch per length bucket (a preallocated plan per bucket in the default launch
+    shape, run one after another), against the batched form (one autotuned plan over the whole
+    batch, device work queue, replayed CUDA graph).  Output compared for identity; the autotuner's
+    whole grid is reported."""
     ref, rd, params = synth.workload(4)
     G = mb.mb_index_build(torch.from_numpy(ref).to(dev))
     G.drop_sa()
@@ -323,63 +325,64 @@ def bench_batched(mb, torch, dev, reps: int = 3):
         ids = np.nonzero((lens >= lo) & (lens < hi))[0]
         if len(ids):
             sub = rd.subset(ids)
-            buckets.append((ids, torch.from_numpy(sub.seq).to(dev),
-                            torch.from_numpy(sub.off.view(np.int64)).to(dev)))
-    outs = []
-    for ids, s, o in buckets:   # sizes
-        _, m, nh = mb.mb_seed_batch(G, s, o, out=torch.empty(8 * len(ids) * 64 * 48, dtype=torch.uint8, device=dev),
-                                    cap=8 * len(ids) * 64)
-        outs.append((torch.empty(max(m, 1) * 48, dtype=torch.uint8, device=dev), m,
-                     torch.empty(max(nh, 1), dtype=torch.int32, device=dev), nh))
+            s_, o_ = torch.from_numpy(sub.seq).to(dev), torch.from_numpy(sub.off.view(np.int64)).to(dev)
+            _, m, nh = mb.mb_seed_batch(G, s_, o_, cap=64 * len(ids))
+            P = mb.Plan(G, len(ids), len(sub.seq), m + 64, nh + 64)
+            buckets.append((ids, s_, o_, P, m, nh))
 
     def plain():
-        for (ids, s, o), (ob, m, hb, nh) in zip(buckets, outs):
-            _, m2, nh2 = mb.mb_seed_batch(G, s, o, out=ob, cap=m)
-            mb.mb_locate(G, ob, m2, hits=hb, cap=nh2)
+        for ids, s_, o_, P, m, nh in buckets:
+            P.run(s_, o_)
 
     plain()
-    torch.cuda.synchronize()
-    t = time.time()
-    for _ in range(reps):
-        plain()
-    torch.cuda.synchronize()
-    plain_s = (time.time() - t) / reps
-    seq, off = torch.from_numpy(rd.seq).to(dev), torch.from_numpy(rd.off.view(np.int64)).to(dev)
-    best, tune_ms = mb.autotune(G, seq, off)
-    n_smem = sum(x[1] for x in outs)
-    n_hits = sum(x[3] for x in outs)
-    P = mb.Plan(G, rd.n, len(rd.seq), n_smem + 64, n_hits + 64, opts=best)
-    P.capture(seq, off)
-    P.replay()
     torch.cuda.synchronize()
     st = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
     for _ in range(reps):
-        P.replay()
+        plain()
+    e1.record(st)
+    torch.cuda.synchronize()
+    plain_s = e0.elapsed_time(e1) / 1000 / reps
+    seq, off = torch.from_numpy(rd.seq).to(dev), torch.from_numpy(rd.off.view(np.int64)).to(dev)
+    best, tune_ms, grid = mb.autotune(G, seq, off, points=True)
+    n_smem = sum(b[4] for b in buckets)
+    n_hits = sum(b[5] for b in buckets)
+    BP = mb.Plan(G, rd.n, len(rd.seq), n_smem + 64, n_hits + 64, opts=best)
+    BP.capture(seq, off)
+    BP.replay()
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(reps):
+        BP.replay()
     e1.record(st)
     torch.cuda.synchronize()
     batched_s = e0.elapsed_time(e1) / 1000 / reps
-    bsm, bhits = P.result()
+    bsm, bhits = BP.result()
+    BP.free()
     # identity with the per-bucket launches, put back in read order
     rec, hl = [], []
-    for (ids, s, o), (ob, m, hb, nh) in zip(buckets, outs):
-        x = ob[:m * 48].cpu().numpy().view(mb.SMEM_DTYPE)
-        h = hb[:nh].cpu().numpy().view(np.uint32)
+    for ids, s_, o_, P, m, nh in buckets:
+        x, h = P.result()
         for r in x:
             c = 0 if r["flags"] & 1 else int(r["s"])
             rec.append((int(ids[r["read"]]), int(r["qbeg"]), int(r["qend"]), int(r["k"]), int(r["kr"]), int(r["s"])))
             hl.append(h[int(r["hit_off"]):int(r["hit_off"]) + c])
+        P.free()
     order = sorted(range(len(rec)), key=lambda i: (rec[i][0], rec[i][1]))
     same = [rec[i] for i in order] == [tuple(int(v) for v in (r["read"], r["qbeg"], r["qend"], r["k"], r["kr"],
                                                                  r["s"])) for r in bsm]
     same = same and np.array_equal(np.concatenate([hl[i] for i in order]), bhits)
+    if not same:
+        raise SystemExit("bench: batched form disagrees with the per-bucket launches")
     return {"workload": "100 Mbp repeat-rich reference, 200,000 SE reads log-uniform 100 bp-10 kb",
             "reads": rd.n, "bases": int(len(rd.seq)), "smems": n_smem, "hits": n_hits,
+            "plain_per_bucket": "one preallocated plan per length bucket (default shape), run in turn",
             "plain_per_bucket_reads_per_s": rd.n / plain_s, "batched_graph_reads_per_s": rd.n / batched_s,
+            "plain_per_bucket_bases_per_s": len(rd.seq) / plain_s, "batched_graph_bases_per_s": len(rd.seq) / batched_s,
             "speedup": plain_s / batched_s, "identical_output": bool(same),
-            "autotuned": {"block_size": best.block_size, "work_queue": bool(best.flags & mb.MB_BATCHED),
-                          "locate_walks_per_lane": best.prefetch_depth},
+            "autotuned": mb.shape_of(best), "autotuned_ms": tune_ms,
+            "autotune_grid": [dict(mb.shape_of(o), ms=round(ms, 3)) for o, ms in grid],
             "plain_ms": plain_s * 1000, "batched_ms": batched_s * 1000}
 
 
@@ -638,14 +641,16 @@ def run_gpu(args):
     ns = min(n_reads, 1_000_000)
     if args.autotune:
         best, tune_ms = mb.autotune(idx, seq[:int(rd.off[ns])], off[:ns + 1], opts=opts)
-        log(f"autotuned on {ns} reads: block {best.block_size}, work queue {bool(best.flags & mb.MB_BATCHED)}, "
-            f"locate walks per lane {best.prefetch_depth}")
+        log(f"autotuned on {ns} reads: {mb.shape_of(best)}")
     else:
         best = mb.Opts(block_size=args.block, prefetch_depth=args.locate_walks,
-                       flags=mb.MB_BATCHED if args.queue else 0)
+                       flags=(mb.MB_BATCHED if args.queue else 0) | (mb.MB_SMEM_ONE_LOOP if args.one_loop else 0),
+                       smem_burst=args.smem_burst, smem_wait=args.smem_wait)
     opts["block_size"] = best.block_size
     opts["prefetch_depth"] = best.prefetch_depth
     opts["flags"] = best.flags
+    opts["smem_burst"] = best.smem_burst
+    opts["smem_wait"] = best.smem_wait
 
     for _ in range(args.warmup):
         step()
@@ -710,9 +715,7 @@ def run_gpu(args):
              "graph_plan": {"reads_per_s": ws * args.steps * n_reads / (graph_ms / 1000.0),
                             "bases_per_s": ws * args.steps * n_bases / (graph_ms / 1000.0),
                             "ms_per_step": graph_ms / args.steps, "identical_output": bool(same),
-                            "gpu_launches": graph_launches,
-                            "block_size": best.block_size, "work_queue": bool(best.flags & mb.MB_BATCHED),
-                            "locate_walks_per_lane": best.prefetch_depth},
+                            "gpu_launches": graph_launches, "shape": mb.shape_of(best)},
              "reported": "graph_plan" if use_graph else "plain_launch"}
 
     # roofline of the dominant kernel: algorithmic bytes / its event-timed duration
@@ -838,6 +841,24 @@ def run_gpu(args):
                          f"({obuild_s:.0f}s) untimed", "seconds": dt,
                "single_core": {"value": one.n / dt1, "unit": "reads/s", "cores": 1,
                                "sample": f"the first {one.n} reads of that sample", "seconds": dt1}}
+        # the survey's definition of the SMEM kernel's algorithmic bytes, from the oracle's own count
+        # of Algorithm 3 with the 10-mer cache (Section 2.5) on this sample: 64 B per distinct
+        # 128-row block an extension step reads, 12 B per cache lookup; scaled per read to the step
+        t = time.time()
+        st_, bl_, lk_ = X.count_alg3(sample.seq, sample.off, params["min_len"], params["min_occ"], block_rows=128,
+                                     kmer_k=10)
+        per_read = (64 * bl_ + 12 * lk_) / sample.n
+        survey_bytes = per_read * n_reads
+        sm_ms = roofline["kernels"]["smem"]["ms_per_launch"]
+        ach = survey_bytes / (sm_ms / 1000.0) / 1e9
+        roofline["survey_definition"] = {
+            "kernel": "smem", "definition": "64 B x distinct 128-row blocks per Algorithm 3 extension step with the "
+                                            "10-mer cache + 12 B per cache lookup (oracle's count on the CPU sample, "
+                                            "scaled per read)",
+            "bytes_per_read": per_read, "steps_per_read": st_ / sample.n, "lookups_per_read": lk_ / sample.n,
+            "bytes_per_launch": survey_bytes, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "sample_reads": sample.n, "count_s": time.time() - t}
+        log(f"survey-definition roofline: {roofline['survey_definition']}")
         del X
         cpu["batched_prefetch"] = cpu_batched_rate(cpu_index_src, sample, params, threads)
         cpu_index_src = None
@@ -907,6 +928,9 @@ def main():
     ap.add_argument("--no-queue", dest="queue", action="store_false",
                     help="SMEM kernel walks fixed read ranges per warp instead of a device work queue")
     ap.add_argument("--locate-walks", type=int, default=16, choices=[1, 2, 4, 8, 16])
+    ap.add_argument("--one-loop", action="store_true", help="SMEM kernel in its one-loop form")
+    ap.add_argument("--smem-burst", type=int, default=0, help="SMEM kernel block steps between service passes")
+    ap.add_argument("--smem-wait", type=int, default=0, help="SMEM kernel lanes out of the loop that call a pass")
     ap.add_argument("--reads", type=int, default=0,
                     help="seed only the first N reads of the batch (for ncu captures of the full index)")
     args = ap.parse_args()

@@ -262,9 +262,13 @@ int mb_seed_locate(const mb_index *idx, const uint8_t *seq, const uint64_t *off,
  * run (valid until the next run): records as mb_seed_batch writes them, and hits as mb_locate
  * writes them.  MB_ERR_CAPACITY (with the needed counts in *n_smem / *n_hits) if a limit was
  * exceeded; nothing beyond the limits was written.
- * mb_autotune times mb_plan_run on the given batch for every launch shape it supports
- * (block size 128/256/512 x work queue on/off x locate walks per lane 1/2/4/8/16) and writes the
- * fastest into *best (same output for all).
+ * mb_autotune times mb_plan_run on the given batch over the launch shapes in two stages and
+ * writes the fastest into *best (same output for all): first the SMEM kernel's shape, threads per
+ * block 128/256/512 x work queue off/on x kernel form (the one-loop form MB_SMEM_ONE_LOOP, or the
+ * split form with smem_burst 2/4/8/16 x smem_wait 4/8/16), with 16 locate walks per lane; then
+ * locate walks per lane 1/2/4/8 with the best SMEM shape (82 points).  mb_autotune_points does
+ * the same and also returns every point tried with its time in ms (up to cap points; *n_points
+ * receives the number tried).
  */
 typedef struct mb_plan mb_plan;
 int mb_plan_create(const mb_index *idx, const mb_opts *opts, uint32_t max_reads, uint64_t max_bases,
@@ -284,6 +288,9 @@ int mb_plan_capture(mb_plan *plan, const uint8_t *seq, const uint64_t *off, uint
 int mb_plan_replay(mb_plan *plan, void *stream);
 int mb_autotune(const mb_index *idx, const uint8_t *seq, const uint64_t *off, uint32_t n_reads,
                 const mb_opts *opts, void *stream, mb_opts *best, double *best_ms);
+int mb_autotune_points(const mb_index *idx, const uint8_t *seq, const uint64_t *off, uint32_t n_reads,
+                       const mb_opts *opts, void *stream, mb_opts *best, double *best_ms, mb_opts *points,
+                       double *points_ms, uint32_t cap, uint32_t *n_points);
 
 /* ---------------------------------------------------------------------------------------
  * Served form: continuous batching of seeding requests on one GPU.

@@ -82,7 +82,7 @@ def lib():
                 "orc_locate_sa": ([P, P, U64, P, I], None),
                 "orc_locate_slow": ([P, P, U64, P, I], None),
                 "orc_batch_locate": ([P, P, U64, P], None),
-                "orc_count_alg3": ([P, P, P, U32, U32, U32, U64, P], None),
+                "orc_count_alg3": ([P, P, P, U32, U32, U32, U64, U32, P], None),
                 "orc_count_locate": ([P, P, U64, P, I], None),
             }
             for name, (args, res) in sig.items():
@@ -194,7 +194,7 @@ class Index:
              threads: int = 0) -> np.ndarray:
         seq, off = _u8(seq), _u64(off)
         h = lib().orc_smem(self._h, _p(seq), _p(off), len(off) - 1, min_len, min_occ,
-                           {"def": 0, "alg3": 1}[method], threads)
+                           {"def": 0, "alg3": 1, "alg3_cache": 2}[method], threads)
         return _take_smem(h)
 
     def locate(self, rows, threads: int = 0) -> np.ndarray:
@@ -218,12 +218,18 @@ class Index:
             lib().orc_batch_locate(self._h, _p(rows), len(rows), _p(out))
         return out
 
-    def count_alg3(self, seq, off, min_len: int = 19, min_occ: int = 1, block_rows: int = 64) -> tuple:
+    def count_alg3(self, seq, off, min_len: int = 19, min_occ: int = 1, block_rows: int = 64,
+                   kmer_k: int = 0):
         """Work of Algorithm 3 over the reads: (extension steps with a base, blocks of
-        `block_rows` rows those steps read: 1 if rows p and p+s share a block, else 2)."""
+        `block_rows` rows those steps read: 1 if rows p and p+s share a block, else 2).  With
+        kmer_k > 0 the steps are those Algorithm 3 takes with the ds-interval cache of all
+        kmer_k-mers (Section 2.5), and a third value counts the cache lookups."""
         seq, off = _u8(seq), _u64(off)
-        out = np.zeros(2, dtype=np.uint64)
-        lib().orc_count_alg3(self._h, _p(seq), _p(off), len(off) - 1, min_len, min_occ, block_rows, _p(out))
+        out = np.zeros(3, dtype=np.uint64)
+        lib().orc_count_alg3(self._h, _p(seq), _p(off), len(off) - 1, min_len, min_occ, block_rows, kmer_k,
+                             _p(out))
+        if kmer_k:
+            return int(out[0]), int(out[1]), int(out[2])
         return int(out[0]), int(out[1])
 
     def count_locate(self, rows, threads: int = 0) -> tuple:

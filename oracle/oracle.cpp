@@ -266,7 +266,7 @@ void smem_def_read(const Index &X, const u8 *P, u32 m, u32 rid, u32 l, u32 c, st
  * base (an N reads nothing); the occurrence values a call needs sit at rows p and p+s of the
  * strand it extends (p = k backwards, k' forwards), i.e. in one block of `block_rows` rows when
  * both rows fall in it, else in two. */
-struct Work { u64 steps = 0, blocks = 0; u64 block_rows = 64; };
+struct Work { u64 steps = 0, blocks = 0, lookups = 0; u64 block_rows = 64; };
 void count_ext(Work *w, u64 p, u64 s, u8 a) {
     if (!w || a > 4) return;
     w->steps += 1;
@@ -290,9 +290,28 @@ void count_ext(Work *w, u64 p, u64 s, u8 a) {
  *     t + 1.
  * The extensions are BackwardExt / ForwardExt of Algorithm 1, in the order Algorithm 3 makes
  * them for this read, so the work counts are Algorithm 3's.
+ *
+ * With K > 0, the ds-interval cache of Section 2.5 (the intervals of all K-mers) stands in for the
+ * first K backward extensions from the whole interval, read as follows: the cached value of the
+ * K-mer P[t-K+1, t] is its ds-interval by definition (what K BackwardExt steps from the whole
+ * interval give).  In the window check it is used when the K-mer lies inside the window and holds
+ * no N; if the K-mer occurs fewer than c times, no window starting at or before its first base x
+ * can match and the scan moves on to x + 1.  Looking for the next start it is used once, when the
+ * K-mer lies above i and holds no N; if it fails there the extensions go one base at a time (the
+ * exact failing base is needed).  The SMEMs are the same with or without it.
  */
+static bool has_n(const u8 *P, int64_t a, int64_t b) {
+    for (int64_t q = a; q < b; ++q)
+        if (P[q] > 4) return true;
+    return false;
+}
+static DS kmer_ds(const Index &X, const u8 *P, int64_t a, u32 K) {   /* P in oracle codes 1..4 */
+    std::vector<u8> r(K);
+    for (u32 q = 0; q < K; ++q) r[q] = (u8)(P[a + q] - 1);
+    return ds_def(X, r.data(), K);
+}
 void smem_alg3_read(const Index &X, const u8 *P, int64_t m, u32 rid, u32 l, u32 c, std::vector<Smem> &out,
-                    Work *work) {
+                    Work *work, u32 K = 0) {
     const DS whole{0, 0, X.n};
     const int64_t L = (int64_t)l;
     if (L - 1 >= m) return;                       // the read is shorter than l
@@ -301,6 +320,17 @@ void smem_alg3_read(const Index &X, const u8 *P, int64_t m, u32 rid, u32 l, u32 
         /* window check of P[i, i+l) */
         DS v = whole;
         int64_t t = i + L - 1;
+        if (K && L >= (int64_t)K && !has_n(P, t - K + 1, t + 1)) {
+            if (work) work->lookups += 1;
+            const DS w = kmer_ds(X, P, t - K + 1, K);
+            if (w.s < c) {                        // no window starting at or before x = t-K+1
+                const int64_t x = t - K + 1;
+                if (x + L < m) { i = x + 1; continue; }
+                return;
+            }
+            v = w;
+            t -= K;
+        }
         for (; t >= i; --t) {
             count_ext(work, v.k, v.s, P[t]);
             const DS w = backward_ext(X, v, P[t]);
@@ -324,7 +354,16 @@ void smem_alg3_read(const Index &X, const u8 *P, int64_t m, u32 rid, u32 l, u32 
         if (e == m) return;
         /* the next start: backwards from the failing base e, not below i + 1 */
         v = whole;
-        for (t = e; t > i; --t) {
+        t = e;
+        if (K && t - (int64_t)K + 1 > i && !has_n(P, t - K + 1, t + 1)) {
+            if (work) work->lookups += 1;
+            const DS w = kmer_ds(X, P, t - K + 1, K);
+            if (w.s >= c) {
+                v = w;
+                t -= K;
+            }
+        }
+        for (; t > i; --t) {
             count_ext(work, v.k, v.s, P[t]);
             const DS w = backward_ext(X, v, P[t]);
             if (w.s < c) break;
@@ -337,24 +376,26 @@ void smem_alg3_read(const Index &X, const u8 *P, int64_t m, u32 rid, u32 l, u32 
 
 /* Algorithm 3 over a batch: every read on its own (see smem_alg3_read), reads in parallel. */
 void smem_alg3(const Index &X, const u8 *seq, const u64 *off, u32 nr, u32 l, u32 c,
-               std::vector<std::vector<Smem>> &out, Work *work = nullptr, int threads = 0) {
-    u64 steps = 0, blocks = 0;
+               std::vector<std::vector<Smem>> &out, Work *work = nullptr, int threads = 0, u32 K = 0) {
+    u64 steps = 0, blocks = 0, lookups = 0;
     const u64 br = work ? work->block_rows : 64;
 #pragma omp parallel for num_threads(threads > 0 ? threads : omp_get_max_threads()) schedule(dynamic, 16) \
-    reduction(+ : steps, blocks)
+    reduction(+ : steps, blocks, lookups)
     for (u32 rd = 0; rd < nr; ++rd) {
         const int64_t m = (int64_t)(off[rd + 1] - off[rd]);
         std::vector<u8> P(m);
         for (int64_t q = 0; q < m; ++q) P[q] = seq[off[rd] + q] < 4 ? (u8)(seq[off[rd] + q] + 1) : 5;
         Work w;
         w.block_rows = br;
-        smem_alg3_read(X, P.data(), m, rd, l, c, out[rd], work ? &w : nullptr);
+        smem_alg3_read(X, P.data(), m, rd, l, c, out[rd], work ? &w : nullptr, K);
         steps += w.steps;
         blocks += w.blocks;
+        lookups += w.lookups;
     }
     if (work) {
         work->steps += steps;
         work->blocks += blocks;
+        work->lookups += lookups;
     }
 }
 
@@ -488,8 +529,9 @@ void *orc_smem(void *x, const u8 *seq, const u64 *off, u32 nr, u32 l, u32 c, int
     const Index &X = *(Index *)x;
     Result *res = new Result;
     std::vector<std::vector<Smem>> per(nr);
-    if (method == 1) {
-        smem_alg3(X, seq, off, nr, l, c, per);
+    if (method == 1 || method == 2) {   /* 2: with the 10-mer cache of Section 2.5 */
+        Work w;
+        smem_alg3(X, seq, off, nr, l, c, per, method == 2 ? &w : nullptr, threads, method == 2 ? 10u : 0u);
         for (auto &v : per) std::sort(v.begin(), v.end(), [](const Smem &a, const Smem &b) { return a.qbeg < b.qbeg; });
     } else {
 #pragma omp parallel for num_threads(threads > 0 ? threads : omp_get_max_threads()) schedule(dynamic, 16)
@@ -539,15 +581,18 @@ void orc_locate_slow(void *x, const u64 *rows, u64 m, u64 *pos, int threads) {
 /* Algorithm 2, BatchLocate (single thread, one set E) */
 void orc_batch_locate(void *x, const u64 *rows, u64 m, u64 *pos) { batch_locate(*(Index *)x, rows, m, pos); }
 
-/* Work counts for the algorithmic bytes: Algorithm 3 over the reads (out: extension steps,
- * blocks of `block_rows` rows read), and Algorithm 2 over the rows (out: LF steps, S reads). */
-void orc_count_alg3(void *x, const u8 *seq, const u64 *off, u32 nr, u32 l, u32 c, u64 block_rows, u64 *out) {
+/* Work counts for the algorithmic bytes: Algorithm 3 over the reads, with the K-mer cache when
+ * K > 0 (out: extension steps, blocks of `block_rows` rows read, cache lookups), and Algorithm 2
+ * over the rows (out: LF steps, S reads). */
+void orc_count_alg3(void *x, const u8 *seq, const u64 *off, u32 nr, u32 l, u32 c, u64 block_rows, u32 K,
+                    u64 *out) {
     std::vector<std::vector<Smem>> per(nr);
     Work w;
     w.block_rows = block_rows;
-    smem_alg3(*(Index *)x, seq, off, nr, l, c, per, &w);
+    smem_alg3(*(Index *)x, seq, off, nr, l, c, per, &w, 0, K);
     out[0] = w.steps;
     out[1] = w.blocks;
+    out[2] = w.lookups;
 }
 void orc_count_locate(void *x, const u64 *rows, u64 m, u64 *out, int threads) {
     const Index &X = *(Index *)x;

@@ -92,6 +92,8 @@ def lib():
                 "mb_plan_capture": ([P, P, P, U32, P], I),
                 "mb_plan_replay": ([P, P], I),
                 "mb_autotune": ([P, P, P, U32, OP, P, OP, ctypes.POINTER(ctypes.c_double)], I),
+                "mb_autotune_points": ([P, P, P, U32, OP, P, OP, ctypes.POINTER(ctypes.c_double), OP,
+                                        ctypes.POINTER(ctypes.c_double), U32, ctypes.POINTER(U32)], I),
                 "mb_serve_create": ([P, OP, U64, PP], I),
                 "mb_serve_submit": ([P, P, P, U32, PU64], I),
                 "mb_serve_poll": ([P, U64, ctypes.POINTER(I)], I),
@@ -465,15 +467,35 @@ class Plan:
             pass
 
 
-def autotune(index: Index, seq, off, opts=None, stream=None):
-    """Fastest launch shape on this batch: (Opts, ms)."""
+def autotune(index: Index, seq, off, opts=None, stream=None, points: bool = False):
+    """Fastest launch shape on this batch: (Opts, ms), and with points=True also the list of every
+    shape tried as (Opts, ms)."""
     o = _opts(opts)
     best = Opts()
     ms = ctypes.c_double()
     n = (off.numel() if hasattr(off, "numel") else len(off)) - 1
-    _check(lib().mb_autotune(index.handle, _ptr(seq), _ptr(off), n, ctypes.byref(o), _stream(stream),
-                             ctypes.byref(best), ctypes.byref(ms)), "mb_autotune")
-    return best, ms.value
+    if not points:
+        _check(lib().mb_autotune(index.handle, _ptr(seq), _ptr(off), n, ctypes.byref(o), _stream(stream),
+                                 ctypes.byref(best), ctypes.byref(ms)), "mb_autotune")
+        return best, ms.value
+    cap = 256
+    pts = (Opts * cap)()
+    pms = (ctypes.c_double * cap)()
+    npts = ctypes.c_uint32()
+    _check(lib().mb_autotune_points(index.handle, _ptr(seq), _ptr(off), n, ctypes.byref(o), _stream(stream),
+                                    ctypes.byref(best), ctypes.byref(ms), pts, pms, cap, ctypes.byref(npts)),
+           "mb_autotune_points")
+    return best, ms.value, [(pts[i], pms[i]) for i in range(min(npts.value, cap))]
+
+
+def shape_of(o: Opts) -> dict:
+    """The launch-shape fields of an Opts as a plain dict (for reports)."""
+    split = not (o.flags & MB_SMEM_ONE_LOOP)
+    return {"block_size": o.block_size or 256, "work_queue": bool(o.flags & MB_BATCHED),
+            "smem_form": "split" if split else "one_loop",
+            "smem_burst": (o.smem_burst or 4) if split else None,
+            "smem_wait": (o.smem_wait or 8) if split else None,
+            "locate_walks_per_lane": o.prefetch_depth or 1}
 
 
 # ---------------------------------------------------------------------------- served form

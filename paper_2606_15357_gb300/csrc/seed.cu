@@ -2031,65 +2031,109 @@ extern "C" int mb_plan_replay(mb_plan *P, void *stream) {
     return MB_OK;
 }
 
-// Times every launch shape on this batch; all give the same output (tests check that).
-extern "C" int mb_autotune(const mb_index *idx, const uint8_t *seq, const uint64_t *off, uint32_t n_reads,
-                           const mb_opts *opts, void *stream, mb_opts *best, double *best_ms) {
+// Times launch shapes on this batch (all give the same output; tests check that), in two stages:
+// (1) the SMEM kernel's shape, over threads per block {128, 256, 512} x work queue off/on x the
+// kernel form (the one-loop form, and the split form with block steps between service passes
+// {2, 4, 8, 16} x lanes out of the loop that call a pass early {4, 8, 16}), with 16 locate walks
+// per lane; (2) locate walks per lane {1, 2, 4, 8} with the best SMEM shape.  Each point is the
+// best of two timed runs of mb_plan_run after one untimed run.  Every point tried is written to
+// points / points_ms when given (up to cap; *n_points receives the number tried).
+static int autotune_impl(const mb_index *idx, const uint8_t *seq, const uint64_t *off, uint32_t n_reads,
+                         const mb_opts *opts, cudaStream_t st, mb_opts *best, double *best_ms, mb_opts *points,
+                         double *points_ms, uint32_t cap, uint32_t *n_points) {
     if (!idx || !best || !seq || !off || n_reads == 0) return MB_ERR_ARG;
-    cudaStream_t st = (cudaStream_t)stream;
     // sizes from one run of the allocating path
     u64 n_smem = 0, n_hits = 0;
     {
         mb_opts o = opts ? *opts : mb_opts{};
         DevBuf tmp;
-        int rc = mb_seed_batch(idx, seq, off, n_reads, nullptr, &o, stream, nullptr, 0, &n_smem, &n_hits);
+        int rc = mb_seed_batch(idx, seq, off, n_reads, nullptr, &o, st, nullptr, 0, &n_smem, &n_hits);
         if (rc != MB_OK && rc != MB_ERR_CAPACITY) return rc;
         MB_TRY(tmp.alloc(n_smem * sizeof(mb_smem) + 64, st));
-        MB_TRY(mb_seed_batch(idx, seq, off, n_reads, nullptr, &o, stream, tmp.as<mb_smem>(), n_smem, &n_smem,
-                             &n_hits));
+        MB_TRY(mb_seed_batch(idx, seq, off, n_reads, nullptr, &o, st, tmp.as<mb_smem>(), n_smem, &n_smem, &n_hits));
     }
     u64 o0 = 0, o1 = 0;
     MB_CK(cudaMemcpyAsync(&o0, off, 8, cudaMemcpyDefault, st));
     MB_CK(cudaMemcpyAsync(&o1, off + n_reads, 8, cudaMemcpyDefault, st));
     MB_CK(cudaStreamSynchronize(st));
-    const int blocks[3] = {128, 256, 512};
-    double bms = 1e30;
-    mb_opts bo = opts ? *opts : mb_opts{};
     cudaEvent_t a, b;
     MB_CK(cudaEventCreate(&a));
     MB_CK(cudaEventCreate(&b));
+    u32 np = 0;
+    double bms = 1e30;
+    mb_opts bo = opts ? *opts : mb_opts{};
+    auto time_point = [&](const mb_opts &o) -> int {
+        mb_plan *P = nullptr;
+        int rc = mb_plan_create(idx, &o, n_reads, o1 - o0, n_smem, n_hits, &P);
+        if (rc != MB_OK) return rc;
+        double t_best = 1e30;
+        for (int rep = 0; rep < 3 && rc == MB_OK; ++rep) {
+            cudaEventRecord(a, st);
+            rc = mb_plan_run(P, seq, off, n_reads, nullptr, st);
+            cudaEventRecord(b, st);
+            if (cudaEventSynchronize(b) != cudaSuccess) rc = MB_ERR_CUDA;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, a, b);
+            if (rep > 0 && ms < t_best) t_best = ms;   // the first run warms up
+        }
+        mb_plan_free(P);
+        if (rc != MB_OK) return rc;
+        if (points && np < cap) {
+            points[np] = o;
+            if (points_ms) points_ms[np] = t_best;
+        }
+        ++np;
+        if (t_best < bms) {
+            bms = t_best;
+            bo = o;
+        }
+        return MB_OK;
+    };
     int rc = MB_OK;
+    const int blocks[3] = {128, 256, 512};
+    const u32 bursts[4] = {2, 4, 8, 16}, waits[3] = {4, 8, 16};
     for (int q = 0; q < 2 && rc == MB_OK; ++q)
         for (int bi = 0; bi < 3 && rc == MB_OK; ++bi)
-        for (int dep = 1; dep <= 16 && rc == MB_OK; dep *= 2) {
-            mb_opts o = opts ? *opts : mb_opts{};
-            o.flags = (o.flags & ~MB_BATCHED) | (q ? MB_BATCHED : 0u);
-            o.block_size = (u32)blocks[bi];
-            o.prefetch_depth = (u32)dep;
-            mb_plan *P = nullptr;
-            rc = mb_plan_create(idx, &o, n_reads, o1 - o0, n_smem, n_hits, &P);
-            if (rc != MB_OK) break;
-            double t_best = 1e30;
-            for (int rep = 0; rep < 3 && rc == MB_OK; ++rep) {
-                cudaEventRecord(a, st);
-                rc = mb_plan_run(P, seq, off, n_reads, nullptr, st);
-                cudaEventRecord(b, st);
-                if (cudaEventSynchronize(b) != cudaSuccess) rc = MB_ERR_CUDA;
-                float ms = 0;
-                cudaEventElapsedTime(&ms, a, b);
-                if (rep > 0 && ms < t_best) t_best = ms;   // first run warms up
+            for (int f = -1; f < 12 && rc == MB_OK; ++f) {
+                mb_opts o = opts ? *opts : mb_opts{};
+                o.flags = (o.flags & ~(MB_BATCHED | MB_SMEM_ONE_LOOP)) | (q ? MB_BATCHED : 0u);
+                o.block_size = (u32)blocks[bi];
+                o.prefetch_depth = 16;
+                if (f < 0) {
+                    o.flags |= MB_SMEM_ONE_LOOP;
+                    o.smem_burst = o.smem_wait = 0;
+                } else {
+                    o.smem_burst = bursts[f / 3];
+                    o.smem_wait = waits[f % 3];
+                }
+                rc = time_point(o);
             }
-            mb_plan_free(P);
-            if (rc == MB_OK && t_best < bms) {
-                bms = t_best;
-                bo = o;
-            }
-        }
+    const mb_opts smem_best = bo;
+    for (u32 dep = 1; dep <= 8 && rc == MB_OK; dep *= 2) {
+        mb_opts o = smem_best;
+        o.prefetch_depth = dep;
+        rc = time_point(o);
+    }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (rc != MB_OK) return rc;
     *best = bo;
     if (best_ms) *best_ms = bms;
+    if (n_points) *n_points = np;
     return MB_OK;
+}
+
+extern "C" int mb_autotune(const mb_index *idx, const uint8_t *seq, const uint64_t *off, uint32_t n_reads,
+                           const mb_opts *opts, void *stream, mb_opts *best, double *best_ms) {
+    return autotune_impl(idx, seq, off, n_reads, opts, (cudaStream_t)stream, best, best_ms, nullptr, nullptr, 0,
+                         nullptr);
+}
+
+extern "C" int mb_autotune_points(const mb_index *idx, const uint8_t *seq, const uint64_t *off, uint32_t n_reads,
+                                  const mb_opts *opts, void *stream, mb_opts *best, double *best_ms, mb_opts *points,
+                                  double *points_ms, uint32_t cap, uint32_t *n_points) {
+    return autotune_impl(idx, seq, off, n_reads, opts, (cudaStream_t)stream, best, best_ms, points, points_ms, cap,
+                         n_points);
 }
 
 // ============================================================================ second seeding round

@@ -56,6 +56,21 @@ def test_plan_every_launch_shape(mb, mixed, queue, block, depth):
     assert np.array_equal(phits, hits)
 
 
+@pytest.mark.parametrize("form", [dict(flags=0x80), dict(smem_burst=1, smem_wait=1), dict(smem_burst=2, smem_wait=32),
+                                  dict(smem_burst=16, smem_wait=4), dict(smem_burst=64, smem_wait=16)])
+@pytest.mark.parametrize("queue", [False, True])
+def test_plan_every_smem_form(mb, mixed, queue, form):
+    """The SMEM kernel's one-loop form and its split form at several service schedules give the
+    same records and hits."""
+    ref, rd, G, sm, hits = mixed
+    o = dict(form, flags=form.get("flags", 0) | (mb.MB_BATCHED if queue else 0), block_size=512, prefetch_depth=8)
+    P = mb.Plan(G, rd.n, len(rd.seq), len(sm) + 10, len(hits) + 10, opts=o)
+    P.run(dev(rd.seq), dev(rd.off))
+    psm, phits = P.result()
+    assert psm.tobytes() == sm.tobytes()
+    assert np.array_equal(phits, hits)
+
+
 def test_graph_replay_on_new_batches(mb, mixed):
     ref, rd, G, sm, hits = mixed
     seq, off = dev(rd.seq), dev(rd.off)
@@ -119,9 +134,12 @@ def test_batched_equals_plain_per_length_bucket(mb, mixed):
 
 def test_autotune_picks_a_supported_shape(mb, mixed):
     ref, rd, G, sm, hits = mixed
-    best, ms = mb.autotune(G, dev(rd.seq), dev(rd.off))
+    best, ms, grid = mb.autotune(G, dev(rd.seq), dev(rd.off), points=True)
     assert best.block_size in (128, 256, 512)
     assert ms > 0
+    assert len(grid) == 82 and min(t for _, t in grid) == ms
+    shapes = {tuple(sorted(mb.shape_of(o).items())) for o, _ in grid}
+    assert len(shapes) == 82                     # every point a distinct launch shape
     P = mb.Plan(G, rd.n, len(rd.seq), len(sm) + 1, len(hits) + 1, opts=best)
     P.run(dev(rd.seq), dev(rd.off))
     psm, phits = P.result()

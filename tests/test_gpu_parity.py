@@ -207,6 +207,13 @@ def test_work_counters_match_oracle(mb):
                            for k, s in zip(sm["k"][keep], sm["s"][keep])])
     assert len(np.unique(rows)) < len(rows)   # the repeat-rich reads repeat rows
     assert (wc["lf_steps"], wc["sa_reads"]) == X.count_locate(np.unique(rows))
+    # with the index's 10-mer table (Section 2.5): the same steps, blocks and lookups as the
+    # oracle's Algorithm 3 with the cache
+    mb.profile_reset()
+    o = dict(flags=mb.MB_COUNT | mb.MB_STEP_ONLY)
+    mb.mb_seed_batch(G, rd.seq, rd.off, opts=o)
+    wc = mb.work_counters()
+    assert (wc["ext_steps"], wc["ext_blocks"], wc["kmer_lookups"]) == X.count_alg3(rd.seq, rd.off, kmer_k=10)
 
 
 def test_auxiliary_arrays_and_text_extension(mb):

@@ -409,6 +409,39 @@ def test_alg3_work_counts_exact_unique_read():
         assert X.count_alg3(P, off, l, 1, 128)[0] == L
 
 
+@pytest.mark.parametrize("l,c", [(19, 1), (19, 2), (12, 3), (10, 1), (25, 1)])
+def test_alg3_with_kmer_cache_gives_the_definition(l, c):
+    """Section 2.5's 10-mer cache changes only the work: Algorithm 3 with it gives exactly the
+    SMEMs of the definition (repeat-rich reads with N)."""
+    ref, rd, p = synth.workload(2, scale=0.003)
+    X = oracle.Index(ref)
+    sub = rd.subset(np.arange(min(rd.n, 1500)))
+    d = X.smem(sub.seq, sub.off, l, c, "def")
+    a = X.smem(sub.seq, sub.off, l, c, "alg3_cache")
+    assert len(d) > 0 and d.tobytes() == a.tobytes()
+
+
+def test_alg3_kmer_cache_work_counts_exact_unique_read():
+    """An error-free read that occurs in T, with the 10-mer cache: one lookup covers the last 10
+    bases of the first window, then l - 10 backward steps and |P| - l forward steps, |P| - 10 in
+    all; the blocks follow from the definition's intervals as without the cache."""
+    ref = synth.reference(100_000, 41)
+    X = oracle.Index(ref)
+    l, L, K = 19, 120, 10
+    for start in (1000, 55_555, 99_000):
+        P = ref[start:start + L].astype(np.uint8)
+        off = np.array([0, L], np.uint64)
+        for br in (64, 128):
+            blocks = 0
+            for j in range(l - K - 1, -1, -1):
+                k, kr, s = X.ds_interval(P[j + 1:l])
+                blocks += 1 if k // br == (k + s) // br else 2
+            for j in range(l, L):
+                k, kr, s = X.ds_interval(P[0:j])
+                blocks += 1 if kr // br == (kr + s) // br else 2
+            assert X.count_alg3(P, off, l, 1, br, kmer_k=K) == (L - K, blocks, 1)
+
+
 def _bs_seed_and_split(ref, seq, off, mate):
     X = oracle.Index(ref, bs3=True)
     conv = oracle.bs_convert_reads(seq, off, mate)

@@ -67,15 +67,16 @@ def test_noalloc_matches_allocating_entry_point_on_two_calls(mb):
 def test_noalloc_reads_with_more_smems_than_slots(mb):
     """Short minimum lengths give reads more SMEMs than their scratch slots, so those reads are
     recomputed by the overflow pass; the output still equals mb_seed_batch's."""
-    ref, rd, p = synth.workload(2, scale=0.002)
+    ref = synth.reference(200_000, 81)
     idx = mb.mb_index_build(_dev(ref))
-    sub = rd.subset(np.arange(min(rd.n, 400)))
-    seq, off = _dev(sub.seq), _dev(sub.off)
-    for opts in (dict(min_len=1, max_occ=500), dict(min_len=5, max_occ=3)):
+    n = 400
+    seq = _dev(synth.reference(150 * n, 8200))              # random reads: they match only in pieces
+    off = _dev(np.arange(n + 1, dtype=np.uint64) * 150)
+    for opts in (dict(min_len=5, max_occ=50), dict(min_len=7, max_occ=3)):
         want, m, nh = mb.mb_seed_batch(idx, seq, off, opts=opts)
-        assert m > 8 * sub.n                              # many records per read: some overflow
+        assert m > 20 * n                                 # more records per read than its 17 slots
         for _ in range(2):
-            got, m2, nh2, rc = noalloc(mb, idx, seq, off, sub.n, cap=m, opts=opts)
+            got, m2, nh2, rc = noalloc(mb, idx, seq, off, n, cap=m, opts=opts)
             assert rc == 0 and (m2, nh2) == (m, nh)
             assert got.tobytes() == want.tobytes()
 
