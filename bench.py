@@ -574,6 +574,77 @@ def bench_served(mb, G, ref, n_requests: int, pool: int = 2000, load: float = 0.
             "server_counters_after_capacity_run": cap_counters, "server_counters": stats}
 
 
+def bench_bisulfite(mb, torch, dev, ref, opts, reps: int = 3):
+    """Directional bisulfite set of the 1 Gbp workload (Section 2.9): the 3-base index over
+    CT(R).GA(R) (n = 4|R| + 1), 1M pairs of converted reads seeded (read 1 C->T, read 2 G->A),
+    located, filtered by strand and split at T-to-C mismatches; device buffers, each step timed
+    with CUDA events on the stream (the split's host copy of its pieces included)."""
+    rd = synth.bisulfite_reads(ref)
+    o = dict(opts, flags=(opts.get("flags", 0) | mb.MB_BS3))
+    torch.cuda.synchronize()
+    t = time.time()
+    G = mb.mb_index_build(torch.from_numpy(ref).to(dev), opts=o)
+    torch.cuda.synchronize()
+    build_s = time.time() - t
+    G.drop_sa()
+    seq, off, mate = (torch.from_numpy(rd.seq).to(dev), torch.from_numpy(rd.off.view(np.int64)).to(dev),
+                      torch.from_numpy(rd.mate).to(dev))
+    ref_d = torch.from_numpy(ref).to(dev)
+    cap = 8 * rd.n
+    out = torch.empty(cap * 48, dtype=torch.uint8, device=dev)
+    _, m, nh = mb.mb_seed_batch(G, seq, off, mate=mate, opts=o, out=out, cap=cap)
+    hits = torch.empty(max(nh, 1), dtype=torch.int32, device=dev)
+    keep = torch.empty(max(nh, 1), dtype=torch.uint8, device=dev)
+    mb.mb_locate(G, out, m, opts=o, hits=hits, cap=nh)
+    mb.mb_bs_filter(G, out, m, mate, hits, nh, keep=keep)
+    import ctypes
+    oo = mb.Opts(**o)
+
+    def split_into(buf):
+        """mb_bs_split into a device buffer of pieces (24 B each); returns the count."""
+        n = ctypes.c_uint64()
+        cap_p = buf.numel() // 24
+        rc = mb.lib().mb_bs_split(G.handle, mb._ptr(ref_d), mb._ptr(seq), mb._ptr(off), rd.n, mb._ptr(mate),
+                                  mb._ptr(out), m, mb._ptr(hits), mb._ptr(keep), nh, ctypes.byref(oo), None,
+                                  mb._ptr(buf), cap_p, ctypes.byref(n))
+        if rc not in (0, mb.MB_ERR_CAPACITY):
+            raise mb.MbError(rc, "mb_bs_split")
+        return n.value
+
+    need = split_into(torch.empty(24, dtype=torch.uint8, device=dev))
+    pieces = torch.empty(max(need, 1) * 24, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    times = {"seed": [], "locate": [], "filter": [], "split": []}
+    npieces = 0
+    for it in range(reps + 1):
+        ev[0].record(st)
+        mb.mb_seed_batch(G, seq, off, mate=mate, opts=o, out=out, cap=cap)
+        ev[1].record(st)
+        mb.mb_locate(G, out, m, opts=o, hits=hits, cap=nh)
+        ev[2].record(st)
+        mb.mb_bs_filter(G, out, m, mate, hits, nh, keep=keep)
+        ev[3].record(st)
+        npieces = split_into(pieces)
+        ev[4].record(st)
+        torch.cuda.synchronize()
+        if it:
+            for k, (a, b) in zip(times, zip(ev[:-1], ev[1:])):
+                times[k].append(a.elapsed_time(b))
+    ms = {k: float(np.min(v)) for k, v in times.items()}
+    total = sum(ms.values())
+    res = {"workload": "directional bisulfite set: 1M pairs 2x150 (read 1 C->T, read 2 G->A; 98% non-CpG, "
+                       "30% CpG conversion) on the 3-base index of the 1 Gbp reference",
+           "n": int(G.n), "index_build_s": build_s, "reads": rd.n, "smems": m, "hits": nh,
+           "kept_hits": int(keep[:nh].sum().item()), "pieces": npieces, "ms": ms,
+           "seed_locate_reads_per_s": rd.n / ((ms["seed"] + ms["locate"]) / 1000.0),
+           "whole_bs_path_reads_per_s": rd.n / (total / 1000.0)}
+    del out, hits, keep, seq, off, mate, ref_d, pieces
+    G.free()
+    torch.cuda.empty_cache()
+    return res
+
+
 # --------------------------------------------------------------------------------- GPU side
 def run_gpu(args):
     import torch
@@ -823,6 +894,11 @@ def run_gpu(args):
         batched = bench_batched(mb, torch, dev)
         log(f"batched: {batched}")
 
+    bisulfite = None
+    if rank == 0 and not args.no_bisulfite and args.workload == 3:
+        bisulfite = bench_bisulfite(mb, torch, dev, ref, dict(opts, flags=best.flags))
+        log(f"bisulfite: {bisulfite}")
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
@@ -887,6 +963,7 @@ def run_gpu(args):
         "batched": batched,
         "rescue_prefilter": rescue,
         "served": served,
+        "bisulfite": bisulfite,
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
@@ -911,6 +988,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the mixed-length batched comparison")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-form measurement")
     ap.add_argument("--no-rescue", action="store_true", help="skip the mate-rescue prefilter measurement")
+    ap.add_argument("--no-bisulfite", action="store_true", help="skip the bisulfite (3-base index) measurement")
     ap.add_argument("--rescue-pairs", type=int, default=1_000_000)
     ap.add_argument("--serve-requests", type=int, default=50_000,
                     help="requests in the served stream (Poisson arrivals)")

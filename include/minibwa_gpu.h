@@ -417,6 +417,14 @@ int mb_set_l2_fetch_granularity(int bytes, int *now);
  * MB_ERR_CUDA when the driver cannot tell (then those checks are skipped).  No counterpart in the
  * paper. */
 int mb_device_extent(const void *p, uint64_t *base, uint64_t *size);
+/* L2 persistence for the k-mer ds-interval table (Section 2.5 keeps it in a CPU cache): sets an
+ * access-policy window on `stream` over the first min(max_bytes, table bytes, the device's window
+ * and persisting-L2 limits) bytes of the table, hits persisting, and sets this context's
+ * persisting-L2 limit to that size (*window receives it).  Kernels later launched on `stream`
+ * keep those table lines in L2.  max_bytes = 0 removes the window and resets persisting lines.
+ * Like mb_set_l2_fetch_granularity this changes only the calling process's context.  No
+ * counterpart in the paper. */
+int mb_index_l2_persist(const mb_index *idx, void *stream, uint64_t max_bytes, uint64_t *window);
 /* Detail of the last error of this library (host-side message), for diagnostics. */
 const char *mb_last_error(void);
 

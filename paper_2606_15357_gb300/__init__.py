@@ -82,6 +82,7 @@ def lib():
                 "mb_strerror": ([I], ctypes.c_char_p),
                 "mb_last_error": ([], ctypes.c_char_p),
                 "mb_device_extent": ([P, PU64, PU64], I),
+                "mb_index_l2_persist": ([P, P, U64, PU64], I),
                 "mb_seed_batch_noalloc": ([P, P, P, U32, P, OP, P, P, U64, PU64, PU64], I),
                 "mb_reseed": ([P, P, P, U32, P, P, U64, OP, P, P, U64, PU64, PU64], I),
                 "mb_plan_create": ([P, OP, U32, U64, U64, U64, PP], I),
@@ -216,6 +217,14 @@ class Index:
         ix = np.empty((n + AUX_RATE - 1) // AUX_RATE, np.uint32)
         _check(lib().mb_index_export_aux(self._h, _ptr(t2), _ptr(sx), _ptr(ix)), "mb_index_export_aux")
         return t2, sx, ix
+
+    def l2_persist(self, max_bytes: int, stream=None) -> int:
+        """Access-policy window over the k-mer table on `stream` (mb_index_l2_persist); returns the
+        window's bytes (0 removes it)."""
+        w = ctypes.c_uint64()
+        _check(lib().mb_index_l2_persist(self._h, _stream(stream), max_bytes, ctypes.byref(w)),
+               "mb_index_l2_persist")
+        return w.value
 
     def hit_to_ref(self, pos: int, length: int):
         strand, rpos = ctypes.c_int(), ctypes.c_uint64()

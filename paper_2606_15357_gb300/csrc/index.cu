@@ -881,6 +881,37 @@ extern "C" int mb_set_l2_fetch_granularity(int bytes, int *now) {
     return MB_OK;
 }
 
+extern "C" int mb_index_l2_persist(const mb_index *idx, void *stream, uint64_t max_bytes, uint64_t *window) {
+    if (!idx || !idx->kmer) return MB_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0;
+    MB_CK(cudaGetDevice(&dev));
+    cudaStreamAttrValue v;
+    memset(&v, 0, sizeof v);
+    u64 w = 0;
+    if (max_bytes) {
+        int max_win = 0, max_persist = 0;
+        MB_CK(cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, dev));
+        MB_CK(cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev));
+        w = (1ULL << (2 * idx->kmer_k)) * 12;
+        if (w > max_bytes) w = max_bytes;
+        if (w > (u64)max_win) w = (u64)max_win;
+        if (w > (u64)max_persist) w = (u64)max_persist;
+        MB_CK(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)w));
+        v.accessPolicyWindow.base_ptr = idx->kmer;
+        v.accessPolicyWindow.num_bytes = (size_t)w;
+        v.accessPolicyWindow.hitRatio = 1.0f;
+        v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    } else {
+        v.accessPolicyWindow.num_bytes = 0;   // window off
+        MB_CK(cudaCtxResetPersistingL2Cache());
+    }
+    MB_CK(cudaStreamSetAttribute(st, cudaStreamAttributeAccessPolicyWindow, &v));
+    if (window) *window = w;
+    return MB_OK;
+}
+
 extern "C" const char *mb_strerror(int code) {
     switch (code) {
     case MB_OK: return "ok";

@@ -941,7 +941,12 @@ __device__ __forceinline__ u64 owner_of(const mb_smem *__restrict__ sm, u64 nsm,
 // any intervals (the public mb_locate takes records from the caller); nested ones share every
 // repeated row.
 constexpr int SHARE_S_BITS = 9;                                   // s in the low bits of the sort key
-constexpr int SHARE_KEY_BITS = 32 + SHARE_S_BITS;
+// key bits to sort: those of the largest row k < n, then s (k's unused high bits are all zero)
+inline int share_key_bits(u64 n) {
+    int b = 1;
+    while (b < 32 && (n - 1) >> b) ++b;
+    return b + SHARE_S_BITS;
+}
 
 __device__ __forceinline__ u64 count_of(u64 cap, const u64 *n_dev) { return n_dev && *n_dev < cap ? *n_dev : cap; }
 __device__ __forceinline__ u64 hits_of(const mb_smem *__restrict__ sm, u64 m) {
@@ -1310,7 +1315,7 @@ int locate_shared(const DevIndex &I, const mb_smem *sm, u64 cap, const u64 *nsm_
     MB_TRY(scan_exclusive_u64(b.roff, b.roff, cap, b.nwalk, b.tmp, st));
     k_share_compact<<<G, 256, 0, st>>>(sm, cap, nsm_dev, known, b.roff, b.keys, b.vals, I.n);
     MB_KCHECK();
-    const BitRange r[1] = {{0, SHARE_KEY_BITS}};
+    const BitRange r[1] = {{0, share_key_bits(I.n)}};
     MB_TRY(radix_sort_pairs(b.keys, b.vals, b.keys_alt, b.vals_alt, cap, r, 1, b.tmp, st, b.nwalk));
     u32 *ss = b.vals_alt;   // the sort's scratch, free again
     u64 *sho = b.keys_alt;

@@ -422,12 +422,8 @@ void worker_loop(mb_server *S) {
         const double t = now_ms();
         if (waiting && !idle_slot && !progressed && t - last_mem >= MEM_POLL_MS) {
             last_mem = t;
-            if (grow(S)) {
-                progressed = true;
-                waiting_since = -1;
-            } else if (waiting_since < 0) {
-                waiting_since = t;
-            }
+            if (grow(S)) progressed = true;
+            else if (waiting_since < 0) waiting_since = t;
         }
         if (progressed && waiting_since >= 0) {
             std::lock_guard<std::mutex> g(S->mu);

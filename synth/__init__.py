@@ -170,9 +170,7 @@ def workload(cfg: int, scale: float = 1.0, bisulfite: bool = False):
     elif cfg == 3:
         ref = repeat_rich_reference(max(int(1_000_000_000 * scale), 20000), SEED[3], 0.45)
         if bisulfite:
-            n = max(int(1_000_000 * scale), 8) * 2
-            rd = reads(ref, n, SEED[3] + 200, mode=1, read_len=150, sub_lo=0.001, sub_hi=0.01,
-                       indel=0.0001, bisulfite=True)
+            rd = bisulfite_reads(ref, scale)
         else:
             n = max(int(10_000_000 * scale), 8) * 2
             rd = reads(ref, n, SEED[3] + 100, mode=1, read_len=150, sub_lo=0.001, sub_hi=0.01,
@@ -180,6 +178,15 @@ def workload(cfg: int, scale: float = 1.0, bisulfite: bool = False):
     else:
         raise ValueError(cfg)
     return ref, rd, params
+
+
+def bisulfite_reads(ref: np.ndarray, scale: float = 1.0) -> Reads:
+    """The directional bisulfite read set of workload 3 on `ref`: 1M pairs (x scale) of 2x150 bp,
+    read 1 C->T and read 2 G->A at 98% of non-CpG and 30% of CpG C, substitutions and indels as in
+    workload 3."""
+    n = max(int(1_000_000 * scale), 8) * 2
+    return reads(ref, n, SEED[3] + 200, mode=1, read_len=150, sub_lo=0.001, sub_hi=0.01, indel=0.0001,
+                 bisulfite=True)
 
 
 def rescue_pairs(ref: np.ndarray, n_pairs: int, seed: int, read_len: int = 150, win_len: int = 600,
