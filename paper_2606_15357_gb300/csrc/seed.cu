@@ -1724,10 +1724,10 @@ extern "C" int mb_seed_batch_noalloc(const mb_index *idx, const uint8_t *seq, co
         mb_set_error("mb_seed_batch_noalloc: device check failed (0x%x)", err);
         return MB_ERR_DEVICE_CHECK;
     }
-    MB_TRY(mb_check_span(out, total * sizeof(mb_smem), "mb_seed_batch_noalloc: out"));
     *n_out = total;
     if (total > cap) return MB_ERR_CAPACITY;
     if (total == 0) return MB_OK;
+    MB_TRY(mb_check_span(out, total * sizeof(mb_smem), "mb_seed_batch_noalloc: out"));
     const size_t o_hitc = fixed, o_htmp = o_hitc + al256(total * 8);
     const size_t need = o_htmp + al256(scan_tmp_bytes(total));
     if (need > MB_NOALLOC_SCRATCH_BYTES) {
