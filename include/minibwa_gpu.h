@@ -87,9 +87,12 @@ typedef struct {
     uint32_t prefetch_depth;  /* tuning: LF-walks in flight per lane in locate, 1/2/4/8/16 (0 = 1) */
     uint32_t block_size;      /* tuning: threads per block (0 = default) */
     uint32_t smem_burst;      /* tuning: SMEM kernel, block steps (extensions, walk steps) a warp runs
-                                 between two service passes of its other actions (0 = default 4) */
+                                 between two service passes of its other actions (0 = default) */
     uint32_t smem_wait;       /* tuning: SMEM kernel, lanes out of the block steps that call a service
-                                 pass early, 1..32 (0 = default 8) */
+                                 pass early, 1..32 (0 = default) */
+    uint32_t smem_warps;      /* tuning: SMEM kernel (split form), resident warps per SM its register
+                                 budget aims at: 40 (256 threads per block) or 48 (256 or 512); 0 =
+                                 24 at 128 threads per block, else 32 */
 } mb_opts;
 
 /* One SMEM (48 bytes).  (k, kr, s) is its ds-interval (lo(P), lo(revcomp P), occ(P)),

@@ -37,7 +37,7 @@ class Opts(ctypes.Structure):
                 ("kmer_k", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                 ("chunk_reads", ctypes.c_uint32), ("prefetch_depth", ctypes.c_uint32),
                 ("block_size", ctypes.c_uint32), ("smem_burst", ctypes.c_uint32),
-                ("smem_wait", ctypes.c_uint32)]
+                ("smem_wait", ctypes.c_uint32), ("smem_warps", ctypes.c_uint32)]
 
 
 class MbError(RuntimeError):

@@ -222,7 +222,7 @@ constexpr int U_MIN = 16;
 struct SmemTuning {
     u32 burst, wait;
 };
-constexpr u32 SMEM_BURST = 4, SMEM_WAIT = 8;
+constexpr u32 SMEM_BURST = 8, SMEM_WAIT = 16;
 
 // Moves through the steps of Algorithm 3 that need no memory and picks the next memory action:
 // ACT_EXT, an extension of P[j] (backward in stages 1 and 3, forward in stage 2); ACT_KMER, a
@@ -486,6 +486,7 @@ struct SmemArgs {
     u32 *err = nullptr;                // device error word (always given)
     u32 *chk = nullptr;                // with MB_CHECKED: the error word, for the per-step bounds checks
     bool split = true;                 // k_smem_split (else k_smem, one loop for every stage)
+    u32 warps = 0;                     // k_smem_split: resident warps per SM aimed at (0: by block size)
     SmemTuning tune = {SMEM_BURST, SMEM_WAIT};
 };
 
@@ -660,8 +661,9 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 128 ? 6 : 1024 / BLOCK) k_smem
 //    text comparison); finished lanes take new reads.
 // So the branches of the seven stages are executed together once per service pass instead of in
 // every iteration.
-template <bool QUEUE, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, BLOCK == 128 ? 6 : 1024 / BLOCK)
+// WARPS: resident warps per SM the launch bounds aim at (their register cap: 65,536 / (WARPS x 32)).
+template <bool QUEUE, int BLOCK, int WARPS>
+__global__ void __launch_bounds__(BLOCK, WARPS * 32 / BLOCK)
     k_smem_split(DevIndex I, const u8 *__restrict__ seq, const u64 *__restrict__ off, u32 nr,
                  const u8 *__restrict__ mate, u32 bs, u32 l, u32 c, bool kmer, SlotRec *__restrict__ slots,
                  u64 slot_total, u64 *__restrict__ counts, u32 *__restrict__ ovf_list, u32 *__restrict__ ovf_n,
@@ -1232,15 +1234,28 @@ unsigned resident_grid(const void *kernel, int block, u64 work_items) {
     return (unsigned)(g ? g : 1);
 }
 
+template <bool QUEUE, int BLOCK, int WARPS>
+int launch_split_t(const SmemArgs &a, cudaStream_t st) {
+    const unsigned g = resident_grid((const void *)k_smem_split<QUEUE, BLOCK, WARPS>, BLOCK, a.nr);
+    k_smem_split<QUEUE, BLOCK, WARPS><<<g, BLOCK, 0, st>>>(a.I, a.seq, a.off, a.nr, a.mate, a.bs, a.l, a.c, a.kmer,
+                                                           a.slots, a.slot_total, a.counts, a.ovf_list, a.ovf_n,
+                                                           a.perm, a.qhead, a.lc, a.uext, a.tune, a.err, a.chk);
+    MB_KCHECK();
+    return MB_OK;
+}
+
 template <bool COUNT, bool QUEUE, int BLOCK>
 int launch_smem_t(const SmemArgs &a, cudaStream_t st) {
-    if (!COUNT && a.split) {
-        const unsigned g = resident_grid((const void *)k_smem_split<QUEUE, BLOCK>, BLOCK, a.nr);
-        k_smem_split<QUEUE, BLOCK><<<g, BLOCK, 0, st>>>(a.I, a.seq, a.off, a.nr, a.mate, a.bs, a.l, a.c, a.kmer,
-                                                        a.slots, a.slot_total, a.counts, a.ovf_list, a.ovf_n, a.perm,
-                                                        a.qhead, a.lc, a.uext, a.tune, a.err, a.chk);
-        MB_KCHECK();
-        return MB_OK;
+    if constexpr (!COUNT) {
+        if (a.split) {
+            if constexpr (BLOCK != 128) {
+                if (a.warps >= 48) return launch_split_t<QUEUE, BLOCK, 48>(a, st);
+            }
+            if constexpr (BLOCK == 256) {
+                if (a.warps >= 40) return launch_split_t<QUEUE, BLOCK, 40>(a, st);
+            }
+            return launch_split_t<QUEUE, BLOCK, BLOCK == 128 ? 24 : 32>(a, st);
+        }
     }
     const unsigned g = resident_grid((const void *)k_smem<COUNT, QUEUE, BLOCK>, BLOCK, a.nr);
     k_smem<COUNT, QUEUE, BLOCK><<<g, BLOCK, 0, st>>>(a.I, a.seq, a.off, a.nr, a.mate, a.bs, a.l, a.c, a.kmer, a.slots,
@@ -1255,6 +1270,7 @@ void smem_tuning(const mb_opts *o, SmemArgs &a) {
     a.split = !(o && (o->flags & MB_SMEM_ONE_LOOP));
     a.tune.burst = o && o->smem_burst ? o->smem_burst : SMEM_BURST;
     a.tune.wait = o && o->smem_wait ? (o->smem_wait > 32 ? 32u : o->smem_wait) : SMEM_WAIT;
+    a.warps = o ? o->smem_warps : 0;
 }
 
 template <bool COUNT, bool POW2, int D>
@@ -1774,6 +1790,7 @@ struct mb_plan {
     u32 depth = 1;   // walks per lane in locate
     bool split = true;   // SMEM kernel form and tuning
     SmemTuning tune = {SMEM_BURST, SMEM_WAIT};
+    u32 warps = 0;
     u32 max_reads = 0;
     u64 max_bases = 0, max_smem = 0, max_hits = 0, nslots = 0;
     void *mem = nullptr;
@@ -1848,6 +1865,7 @@ extern "C" int mb_plan_create(const mb_index *idx, const mb_opts *opts, uint32_t
         smem_tuning(opts, t);
         P->split = t.split;
         P->tune = t.tune;
+        P->warps = t.warps;
     }
     P->max_reads = max_reads;
     P->max_bases = max_bases;
@@ -1922,6 +1940,7 @@ static int plan_seed(mb_plan *P, const uint8_t *seq, const uint64_t *off, uint32
                 perm, qhead, nullptr, nullptr, I.text2 && !(P->flags & MB_STEP_ONLY)};
     sa.split = P->split;
     sa.tune = P->tune;
+    sa.warps = P->warps;
     sa.err = err;
     sa.chk = (P->flags & MB_CHECKED) ? err : nullptr;
     MB_TRY(launch_smem(sa, false, P->queue, P->block, st));
