@@ -793,7 +793,9 @@ def run_gpu(args):
     peak, peak_kind = measured_peaks()
     smem_bytes = (BLOCK_BYTES * (wc["ext_blocks"] + wc["u_walk_steps"]) + 12 * wc["kmer_lookups"] +
                   4 * wc["u_samples"] + 8 * wc["u_text_loads"])
-    loc_bytes = BLOCK_BYTES * wc["lf_steps"] + 4 * wc["sa_reads"]
+    # locate with walks that join: 32 B per LF step, 4 B per sampled-S read, 8 B per mark-word read,
+    # 4 B per rank read of a join
+    loc_bytes = BLOCK_BYTES * wc["lf_steps"] + 4 * wc["sa_reads"] + 8 * wc["mark_reads"] + 4 * wc["joins"]
     if loc_ms / max(loc_n, 1) >= smem_ms / max(smem_n, 1):
         kname, kbytes, kms = "locate", loc_bytes, loc_ms / max(loc_n, 1)
     else:

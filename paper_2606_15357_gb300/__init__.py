@@ -20,7 +20,7 @@ __all__ = ["SMEM_DTYPE", "Opts", "MbError", "lib", "build", "Index", "mb_index_b
            "mb_index_load", "mb_seed_batch", "mb_locate", "mb_bs_filter", "seed"]
 
 MB_BS3, MB_BATCHED, MB_CHECKED, MB_NO_KMER, MB_COUNT = 0x1, 0x2, 0x4, 0x8, 0x10
-MB_NO_AUX, MB_STEP_ONLY, MB_SMEM_ONE_LOOP = 0x20, 0x40, 0x80
+MB_NO_AUX, MB_STEP_ONLY, MB_SMEM_ONE_LOOP, MB_LOCATE_NO_JOIN = 0x20, 0x40, 0x80, 0x100
 AUX_RATE = 4   # sample rate of the auxiliary SA / ISA samples (mb_index_export_aux)
 MB_SMEM_OVER_MAX_OCC, MB_SMEM_ROUND2 = 0x1, 0x2
 MB_ERR_CAPACITY = -3
@@ -415,10 +415,10 @@ def launch_count() -> int:
 
 
 def work_counters() -> dict:
-    v = np.zeros(8, dtype=np.uint64)
-    lib().mb_work_counters_all(_ptr(v), 8)
+    v = np.zeros(10, dtype=np.uint64)
+    lib().mb_work_counters_all(_ptr(v), 10)
     return dict(zip(("ext_steps", "ext_blocks", "kmer_lookups", "lf_steps", "sa_reads", "u_walk_steps",
-                     "u_samples", "u_text_loads"), (int(x) for x in v)))
+                     "u_samples", "u_text_loads", "mark_reads", "joins"), (int(x) for x in v)))
 
 
 # ---------------------------------------------------------------------------- batched form

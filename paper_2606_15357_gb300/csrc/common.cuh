@@ -91,7 +91,9 @@ struct KTimer {
 // device-side work counters (index into the array handed to kernels in counting mode)
 enum {
     WC_EXT_STEPS = 0, WC_EXT_BLOCKS = 1, WC_KMER = 2, WC_LF_STEPS = 3, WC_SA_READS = 4,
-    WC_U_WALK = 5, WC_U_SAMPLE = 6, WC_U_TEXT = 7, WC_N = 8   // U_*: extension of unique matches by text
+    WC_U_WALK = 5, WC_U_SAMPLE = 6, WC_U_TEXT = 7,   // U_*: extension of unique matches by text
+    WC_MARKS = 8, WC_LINKS = 9,                       // locate: mark-word loads, walks ended at another hit row
+    WC_N = 10
 };
 u64 *mb_work_counter_buf(cudaStream_t st);   // device array of WC_N u64 (zeroed on first use)
 
@@ -267,7 +269,8 @@ int radix_sort_pairs(u64 *keys, u32 *vals, u64 *keys_alt, u32 *vals_alt, size_t 
 // the third), and its device result arrays
 size_t mb_plan_bytes(const mb_plan *p);
 // device bytes mb_plan_create would allocate for these limits (no allocation)
-size_t mb_plan_workspace_bytes(const mb_opts *opts, u32 max_reads, u64 max_bases, u64 max_smem, u64 max_hits);
+size_t mb_plan_workspace_bytes(const mb_opts *opts, u64 n, u32 max_reads, u64 max_bases, u64 max_smem,
+                               u64 max_hits);
 int mb_plan_counts_async(mb_plan *p, u64 *host_counts, cudaStream_t st);
 void mb_plan_arrays(const mb_plan *p, const mb_smem **smem, const u32 **hits, u64 *max_smem, u64 *max_hits);
 // seeding of a plan's batch without the locate (records with hit offsets), the plan's per-record

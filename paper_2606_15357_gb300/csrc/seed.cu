@@ -44,7 +44,7 @@ __device__ __forceinline__ u64 slot_base(const u64 *off, u64 r) { return slots_b
 // Work counters of the measurement mode (MB_COUNT); compiled out otherwise.
 template <bool ON>
 struct Work {
-    u64 steps = 0, blocks = 0, kmer = 0, lf = 0, sa = 0, uwalk = 0, usample = 0, utext = 0;
+    u64 steps = 0, blocks = 0, kmer = 0, lf = 0, sa = 0, uwalk = 0, usample = 0, utext = 0, marks = 0, links = 0;
     __device__ __forceinline__ void ext(u64 p, u64 s) {
         if (ON) {
             ++steps;
@@ -61,6 +61,8 @@ struct Work {
             if (uwalk) atomicAdd((unsigned long long *)&wc[WC_U_WALK], (unsigned long long)uwalk);
             if (usample) atomicAdd((unsigned long long *)&wc[WC_U_SAMPLE], (unsigned long long)usample);
             if (utext) atomicAdd((unsigned long long *)&wc[WC_U_TEXT], (unsigned long long)utext);
+            if (marks) atomicAdd((unsigned long long *)&wc[WC_MARKS], (unsigned long long)marks);
+            if (links) atomicAdd((unsigned long long *)&wc[WC_LINKS], (unsigned long long)links);
         }
     }
 };
@@ -1197,6 +1199,197 @@ __global__ void __launch_bounds__(256, D == 8 ? 2 : 1) k_locate(DevIndex I, cons
     work.flush(wc);
 }
 
+// ---------------------------------------------------------------------------- walks that join
+// Reads that cover the same place give hits a few text positions apart (SMEMs of one read overlap):
+// on the workloads here about 78% of the distinct hit positions have another hit within 8
+// positions to their left.  An LF-walk (Algorithm 2) from the row of position p visits the rows of
+// p - 1, p - 2, ... in turn, so when it reaches the row of another hit q after d = p - q steps,
+// S(row of p) = S(row of q) + d: the walk can stop there.  Each walked row is marked in a bitmap
+// with per-word ranks (mark words of 64 rows: the bits and the number of marked rows before the
+// word), so a walk recognises a marked row from the word of its current row and finds that row's
+// place in the sorted row list by its rank.  A walk stops at the first sampled row, the $ row or
+// marked row it reaches, in that order of checks; a walk that stops at a marked row records the
+// distance and becomes that row's successor.  Every row has at most one successor (a walk meeting
+// the row of q passes the rows of every position between, so only the nearest hit to q's right
+// can stop at q), links point strictly to smaller positions, and a chain ends at a walk that
+// reached a sampled or $ row; one thread per chain head then adds the distances along its chain.
+// The positions are exactly those of the plain walks.  This needs the walked rows sorted and
+// distinct (true for the records of one seeding call, whose intervals are nested or disjoint);
+// otherwise a device flag turns the marks off and every walk runs to its sampled row.
+constexpr u32 LINKED = 0xFFFFFFFEu;   // rpos of a walk that stopped at another walked row
+
+__device__ __forceinline__ uint2 load_mark_bits(const uint4 *__restrict__ marks, u32 w) {
+    uint2 v;
+    asm("ld.global.nc.v2.u32 {%0,%1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(marks + w));
+    return v;
+}
+
+// Bits of the walked rows (warp-aggregated atomics over the sorted rows) and the not-sorted flag.
+__global__ void k_join_mark(const u32 *__restrict__ rows, const u64 *__restrict__ nrows_dev, u64 cap,
+                            uint4 *__restrict__ marks, u32 *__restrict__ nojoin) {
+    const u64 nr = count_of(cap, nrows_dev);
+    const u32 lane = threadIdx.x & 31;
+    for (u64 base = (blockIdx.x * (u64)blockDim.x + threadIdx.x) & ~31ull; base < nr;
+         base += (u64)gridDim.x * blockDim.x) {
+        const u64 i = base + lane;
+        const bool on = i < nr;
+        const u32 y = on ? rows[i] : 0u;
+        if (on && i + 1 < nr && rows[i + 1] <= y) atomicOr(nojoin, 1u);
+        const u32 w = y >> BLK_SHIFT;
+        const u32 act = __ballot_sync(0xffffffffu, on);
+        if (!on) continue;
+        const u32 grp = __match_any_sync(act, w);
+        const u64 bit = 1ull << (y & BLK_MASK);
+        const u32 lo = __reduce_or_sync(grp, (u32)bit), hi = __reduce_or_sync(grp, (u32)(bit >> 32));
+        if (lane == (u32)(__ffs(grp) - 1)) {
+            if (lo) atomicOr(&marks[w].x, lo);
+            if (hi) atomicOr(&marks[w].y, hi);
+        }
+    }
+}
+__global__ void k_join_popc(const uint4 *__restrict__ marks, u64 nw, u32 *__restrict__ cnt) {
+    for (u64 w = blockIdx.x * (u64)blockDim.x + threadIdx.x; w < nw; w += (u64)gridDim.x * blockDim.x)
+        cnt[w] = __popc(marks[w].x) + __popc(marks[w].y);
+}
+__global__ void k_join_before(uint4 *__restrict__ marks, u64 nw, const u32 *__restrict__ cnt) {
+    for (u64 w = blockIdx.x * (u64)blockDim.x + threadIdx.x; w < nw; w += (u64)gridDim.x * blockDim.x)
+        marks[w].z = cnt[w];
+}
+
+// Algorithm 2 over the sorted rows with joins: k_locate's walk loop (D walks per lane, one warp-wide
+// hand-out per iteration) plus, for a walk past its first row, the mark word of its current row,
+// loaded with the block.  A marked row ends the walk at the next iteration: its rank replaces the
+// row, and the hand-out writes LINKED, the distance, and the successor entry.
+template <bool COUNT, bool POW2, int D>
+__global__ void __launch_bounds__(256, D <= 8 ? 2 : 1)
+    k_locate_join(DevIndex I, const u32 *__restrict__ rows, u64 nhits, const u64 *__restrict__ nhits_dev,
+                  u32 *__restrict__ hits, const uint4 *__restrict__ marks, const u32 *__restrict__ nojoin,
+                  u32 *__restrict__ succ, u32 *__restrict__ dist, u64 *wc, u32 *chk) {
+    const u32 lane = threadIdx.x & 31;
+    if (nhits_dev && *nhits_dev < nhits) nhits = *nhits_dev;
+    const bool join = *nojoin == 0;
+    Work<COUNT> work;
+    const u32 r = I.r, rmask = I.r - 1, rshift = __ffs(I.r) - 1, prim = (u32)I.primary, n = (u32)I.n;
+    const u32 C0 = (u32)I.C[0], C1 = (u32)I.C[1], C2 = (u32)I.C[2], C3 = (u32)I.C[3];
+    WarpRange wr;
+    wr.init(nhits);
+    const u64 wbase = wr.next;
+    const u32 wlen = (u32)(wr.end - wr.next);
+    const u32 *__restrict__ wrows = rows + wbase;
+    u32 *__restrict__ whits = hits + wbase;
+    u32 h[D], row[D], steps[D];
+    u32 live = 0, lnk = 0;   // bit d: slot d holds a walk; the walk of slot d met a marked row
+    u32 next = 0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const u32 o = next + lane;
+        h[d] = o;
+        steps[d] = 0;
+        row[d] = 0;
+        if (o < wlen) {
+            live |= 1u << d;
+            row[d] = __ldg(&wrows[o]);
+        }
+        next += 32;
+    }
+    for (;;) {
+        if (__all_sync(0xffffffffu, live == 0)) break;
+        if (next + 128 + lane < wlen) asm volatile("prefetch.global.L1 [%0];" ::"l"(wrows + next + 128 + lane));
+        u32 stop = 0, smp = 0, skp = 0, ld = 0;
+        u32 sv[D];
+        Blk b[D];
+        uint2 mk[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const bool on = (live >> d) & 1u;
+            const bool linked = (lnk >> d) & 1u;
+            const bool skip = !linked && row[d] == NOPOS;
+            const bool bad = chk && on && !linked && !skip && row[d] >= n;
+            if (bad) atomicOr(chk, (u32)DEVCHK_BOUNDS);
+            const bool sampled = !linked && !skip && !bad && (POW2 ? (row[d] & rmask) == 0 : row[d] % r == 0);
+            const bool st = on && (linked || skip || bad || sampled || row[d] == prim || steps[d] > n);
+            sv[d] = 0;
+            mk[d] = make_uint2(0u, 0u);
+            if (st) {
+                stop |= 1u << d;
+                if (skip) skp |= 1u << d;
+                if (sampled) {
+                    smp |= 1u << d;
+                    sv[d] = __ldg(&I.ssa[POW2 ? (row[d] >> rshift) : row[d] / r]);
+                }
+            } else if (on) {
+                b[d] = load_blk(I.occ + (row[d] >> BLK_SHIFT));
+                if (join && steps[d] > 0) {
+                    mk[d] = load_mark_bits(marks, row[d] >> BLK_SHIFT);
+                    ld |= 1u << d;
+                }
+            }
+        }
+        const u32 cnt = __popc(stop);
+        u32 incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const u32 v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (u32)o) incl += v;
+        }
+        u32 give = next + incl - cnt;
+        next += __shfl_sync(0xffffffffu, incl, 31);
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            if ((stop >> d) & 1u) {
+                if ((lnk >> d) & 1u) {   // row[d] holds the rank of the marked row met
+                    whits[h[d]] = LINKED;
+                    dist[wbase + h[d]] = steps[d];
+                    succ[row[d]] = (u32)(wbase + h[d]);
+                    work.links += 1;
+                } else if (!((skp >> d) & 1u)) {
+                    whits[h[d]] = (steps[d] > n || row[d] >= n) ? 0xFFFFFFFFu
+                                                                : (((smp >> d) & 1u) ? sv[d] + steps[d] : steps[d]);
+                }
+                work.lf += steps[d];
+                work.sa += (smp >> d) & 1u;
+                lnk &= ~(1u << d);
+                h[d] = give;
+                steps[d] = 0;
+                if (give < wlen) row[d] = __ldg(&wrows[give]);
+                else live &= ~(1u << d);
+                ++give;
+            } else if ((live >> d) & 1u) {
+                const u32 m = row[d] & BLK_MASK;
+                const u64 bits = ((u64)mk[d].y << 32) | mk[d].x;
+                if ((ld >> d) & 1u) work.marks += 1;
+                if ((bits >> m) & 1ull) {   // a walked row: its rank in the sorted rows
+                    row[d] = __ldg(&marks[row[d] >> BLK_SHIFT].z) + (u32)__popcll(bits & rows_before(m));
+                    lnk |= 1u << d;
+                } else {
+                    row[d] = lf_blk(b[d], row[d], prim, C0, C1, C2, C3);
+                    ++steps[d];
+                }
+            }
+        }
+    }
+    work.flush(wc);
+}
+
+// Positions of the linked walks: one thread per chain head (a walk that reached a sampled or $
+// row) adds the distances along its successors.
+__global__ void k_join_resolve(u32 *__restrict__ rpos, const u32 *__restrict__ succ, const u32 *__restrict__ dist,
+                               const u64 *__restrict__ nrows_dev, u64 cap) {
+    const u64 nr = count_of(cap, nrows_dev);
+    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < nr; i += (u64)gridDim.x * blockDim.x) {
+        u32 p = rpos[i];
+        if (p >= LINKED) continue;
+        u32 cur = (u32)i;
+        for (u64 guard = 0; guard < nr; ++guard) {   // a chain visits each row once
+            const u32 s = succ[cur];
+            if (s == NOPOS || s >= nr) break;
+            p += dist[s];
+            rpos[s] = p;
+            cur = s;
+        }
+    }
+}
+
 __global__ void k_bs_filter(const mb_smem *__restrict__ sm, u64 nsm, const u8 *__restrict__ mate,
                             const u32 *__restrict__ hits, u64 nhits, u64 M, u8 *__restrict__ keep) {
     for (u64 h = blockIdx.x * (u64)blockDim.x + threadIdx.x; h < nhits; h += (u64)gridDim.x * blockDim.x) {
@@ -1311,10 +1504,59 @@ struct ShareBufs {
     void *tmp = nullptr;
     u32 *err = nullptr;   // the device error word (records with rows outside the text; MB_CHECKED bounds)
     bool checked = false; // MB_CHECKED: the locate kernel checks every row it walks
+    // walks that join (k_locate_join): mark words of the walked rows, their popcounts, the
+    // not-sorted flag, per walked row its successor and its distance
+    bool join = true;
+    uint4 *marks = nullptr;
+    u32 *mcnt = nullptr, *nojoin = nullptr, *succ = nullptr, *dist = nullptr;
 };
-size_t share_tmp_bytes(u64 cap) {
-    const size_t a = radix_tmp_bytes(cap), b = scan_tmp_bytes(cap);
-    return a > b ? a : b;
+// mark words of an index of n rows
+inline u64 join_words(u64 n) { return n / BLK_ROWS + 1; }
+
+template <bool COUNT, bool POW2, int D>
+int launch_join_t(const DevIndex &I, const u32 *rows, u64 nhits, const u64 *nhits_dev, u32 *rpos, const uint4 *marks,
+                  const u32 *nojoin, u32 *succ, u32 *dist, u64 *wc, u32 *chk, cudaStream_t st) {
+    const unsigned g =
+        resident_grid((const void *)k_locate_join<COUNT, POW2, D>, 256, (nhits + 63) / 64 * 32);
+    const u64 warps = (u64)g * 8;
+    if ((nhits + warps - 1) / warps >= (1ull << 32) - 4096) {
+        mb_set_error("locate: %llu hits over %llu warps", (unsigned long long)nhits, (unsigned long long)warps);
+        return MB_ERR_ARG;
+    }
+    k_locate_join<COUNT, POW2, D><<<g, 256, 0, st>>>(I, rows, nhits, nhits_dev, rpos, marks, nojoin, succ, dist, wc,
+                                                     chk);
+    MB_KCHECK();
+    return MB_OK;
+}
+int launch_join(const DevIndex &I, const u32 *rows, u64 nhits, const u64 *nhits_dev, u32 *rpos, const ShareBufs &b,
+                u64 *wc, bool count, u32 depth, u32 *chk, cudaStream_t st) {
+    const bool pow2 = (I.r & (I.r - 1)) == 0;
+    if (count || !pow2)
+        return count ? (pow2 ? launch_join_t<true, true, 1>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin, b.succ,
+                                                             b.dist, wc, chk, st)
+                             : launch_join_t<true, false, 1>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin,
+                                                              b.succ, b.dist, wc, chk, st))
+                     : launch_join_t<false, false, 1>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin, b.succ,
+                                                       b.dist, wc, chk, st);
+    if (depth >= 16)
+        return launch_join_t<false, true, 16>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin, b.succ, b.dist, wc,
+                                              chk, st);
+    if (depth >= 8)
+        return launch_join_t<false, true, 8>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin, b.succ, b.dist, wc,
+                                             chk, st);
+    if (depth >= 4)
+        return launch_join_t<false, true, 4>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin, b.succ, b.dist, wc,
+                                             chk, st);
+    if (depth >= 2)
+        return launch_join_t<false, true, 2>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin, b.succ, b.dist, wc,
+                                             chk, st);
+    return launch_join_t<false, true, 1>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin, b.succ, b.dist, wc, chk,
+                                         st);
+}
+
+size_t share_tmp_bytes(u64 cap, u64 n) {
+    const size_t a = radix_tmp_bytes(cap), b = scan_tmp_bytes(cap), c = scan_tmp_bytes(join_words(n));
+    return a > b ? (a > c ? a : c) : (b > c ? b : c);
 }
 // bytes of the per-record arrays (keys, keys_alt, roff: u64; vals, vals_alt, pmax, last: u32)
 constexpr size_t SHARE_BYTES_PER_RECORD = 3 * 8 + 4 * 4;
@@ -1344,9 +1586,31 @@ int locate_shared(const DevIndex &I, const mb_smem *sm, u64 cap, const u64 *nsm_
     MB_TRY(scan_inclusive_max_u32(b.last, b.last, cap, b.tmp, st));
     k_share_rows<<<G, 256, 0, st>>>(b.keys, ss, b.last, b.roff, cap, b.nwalk, b.rows, hits_cap);
     MB_KCHECK();
-    if (kt) kt->start();
-    MB_TRY(launch_locate(I, b.rows, hits_cap, b.nrows, b.rpos, wc, count, depth, b.checked ? b.err : nullptr, st));
-    if (kt) kt->stop();
+    u32 *chk = b.checked ? b.err : nullptr;
+    if (b.join && b.marks) {
+        // marks of the walked rows and their ranks, then the walks with joins, then the chains
+        const u64 nw = join_words(I.n);
+        MB_CK(cudaMemsetAsync(b.marks, 0, nw * sizeof(uint4), st));
+        MB_CK(cudaMemsetAsync(b.nojoin, 0, 4, st));
+        MB_CK(cudaMemsetAsync(b.succ, 0xFF, hits_cap * 4, st));
+        const unsigned GR = grid_for(hits_cap, 256);
+        k_join_mark<<<GR, 256, 0, st>>>(b.rows, b.nrows, hits_cap, b.marks, b.nojoin);
+        MB_KCHECK();
+        k_join_popc<<<grid_for(nw, 256), 256, 0, st>>>(b.marks, nw, b.mcnt);
+        MB_KCHECK();
+        MB_TRY(scan_exclusive_u32(b.mcnt, b.mcnt, nw, nullptr, b.tmp, st));
+        k_join_before<<<grid_for(nw, 256), 256, 0, st>>>(b.marks, nw, b.mcnt);
+        MB_KCHECK();
+        if (kt) kt->start();
+        MB_TRY(launch_join(I, b.rows, hits_cap, b.nrows, b.rpos, b, wc, count, depth, chk, st));
+        if (kt) kt->stop();
+        k_join_resolve<<<GR, 256, 0, st>>>(b.rpos, b.succ, b.dist, b.nrows, hits_cap);
+        MB_KCHECK();
+    } else {
+        if (kt) kt->start();
+        MB_TRY(launch_locate(I, b.rows, hits_cap, b.nrows, b.rpos, wc, count, depth, chk, st));
+        if (kt) kt->stop();
+    }
     k_share_copy<<<G, 256, 0, st>>>(b.keys, ss, sho, b.last, b.roff, cap, b.nwalk, b.rpos, hits_cap, hits, hits_cap);
     MB_KCHECK();
     return MB_OK;
@@ -1502,11 +1766,12 @@ extern "C" int mb_seed_batch(const mb_index *idx, const uint8_t *seq, const uint
                        st, out, cap, n_out, n_hits);
 }
 
-// The shared-walk workspace for n_smem records and total hits, carved from one stream-ordered
-// allocation.
-static int share_alloc(DevBuf &bw, u64 n_smem, u64 total, cudaStream_t st, ShareBufs &b) {
+// The shared-walk workspace for n_smem records and total hits on an index of n rows (with the
+// arrays of the walks that join unless `join` is false), carved from one stream-ordered allocation.
+static int share_alloc(DevBuf &bw, u64 n_smem, u64 total, u64 n, bool join, cudaStream_t st, ShareBufs &b) {
     const size_t rec_bytes = (size_t)n_smem * SHARE_BYTES_PER_RECORD, row_bytes = (size_t)total * 8;
-    MB_TRY(bw.alloc(rec_bytes + row_bytes + 16 + share_tmp_bytes(n_smem) + 14 * 256, st));
+    const size_t nw = join ? join_words(n) : 0, join_bytes = join ? nw * 20 + (size_t)total * 8 + 4 * 256 : 0;
+    MB_TRY(bw.alloc(rec_bytes + row_bytes + 16 + share_tmp_bytes(n_smem, n) + join_bytes + 14 * 256, st));
     char *m = (char *)bw.p;
     auto take = [&](size_t bytes) { void *p = m; m += (bytes + 255) & ~(size_t)255; return p; };
     b.keys = (u64 *)take(n_smem * 8);
@@ -1521,7 +1786,15 @@ static int share_alloc(DevBuf &bw, u64 n_smem, u64 total, cudaStream_t st, Share
     b.nrows = (u64 *)take(8);
     b.nwalk = (u64 *)take(8);
     b.err = (u32 *)take(8);
-    b.tmp = take(share_tmp_bytes(n_smem));
+    b.tmp = take(share_tmp_bytes(n_smem, n));
+    b.join = join;
+    if (join) {
+        b.marks = (uint4 *)take(nw * sizeof(uint4));
+        b.mcnt = (u32 *)take(nw * 4);
+        b.nojoin = (u32 *)take(8);
+        b.succ = (u32 *)take(total * 4);
+        b.dist = (u32 *)take(total * 4);
+    }
     MB_CK(cudaMemsetAsync(b.err, 0, 8, st));
     return MB_OK;
 }
@@ -1531,9 +1804,9 @@ int mb_locate_records(const mb_index *idx, const mb_smem *sm, u64 n_smem, const 
     if (n_smem == 0 || n_hits == 0) return MB_OK;
     DevBuf bw;
     ShareBufs b;
-    MB_TRY(share_alloc(bw, n_smem, n_hits, st, b));
-    return locate_shared(mb_dev_index(idx), sm, n_smem, nullptr, known, hits, n_hits, b, nullptr, false, depth,
-                         nullptr, st);
+    const DevIndex I = mb_dev_index(idx);
+    MB_TRY(share_alloc(bw, n_smem, n_hits, I.n, true, st, b));
+    return locate_shared(I, sm, n_smem, nullptr, known, hits, n_hits, b, nullptr, false, depth, nullptr, st);
 }
 
 extern "C" int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_smem, const mb_opts *opts,
@@ -1568,7 +1841,7 @@ extern "C" int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_sm
     const bool count = opts && (opts->flags & MB_COUNT);
     DevBuf bw;
     ShareBufs b;
-    MB_TRY(share_alloc(bw, n_smem, total, st, b));
+    MB_TRY(share_alloc(bw, n_smem, total, I.n, !(opts && (opts->flags & MB_LOCATE_NO_JOIN)), st, b));
     b.checked = opts && (opts->flags & MB_CHECKED);
     u64 *wc = count ? mb_work_counter_buf(st) : nullptr;
     KTimer kt("locate", st);
@@ -1825,25 +2098,34 @@ void mb_plan_arrays(const mb_plan *p, const mb_smem **smem, const u32 **hits, u6
 }
 
 // Device workspace of a plan, one entry per array (in the order mb_plan_create lays them out).
-constexpr int PLAN_ARRAYS = 23;
-static void plan_sizes(const mb_opts *opts, u32 max_reads, u64 max_bases, u64 max_smem, u64 max_hits,
+constexpr int PLAN_ARRAYS = 28;
+// A plan locates with walks that join (their arrays sized by the index's n rows) unless the options
+// say MB_LOCATE_NO_JOIN or the plan holds no hits to locate (a seeding-only plan).
+static bool plan_joins(const mb_opts *opts, u64 max_hits) {
+    return !(opts && (opts->flags & MB_LOCATE_NO_JOIN)) && max_hits > 1;
+}
+static void plan_sizes(const mb_opts *opts, u64 n, u32 max_reads, u64 max_bases, u64 max_smem, u64 max_hits,
                        size_t sizes[PLAN_ARRAYS]) {
     const bool queue = opts && (opts->flags & MB_BATCHED);
     const size_t nr = max_reads, ms = max_smem ? max_smem : 1, mh = max_hits ? max_hits : 1;
     size_t tb = scan_tmp_bytes(nr > ms ? nr : ms);
-    const size_t rb = radix_tmp_bytes(nr), sb = share_tmp_bytes(ms);
+    const size_t rb = radix_tmp_bytes(nr), sb = share_tmp_bytes(ms, n);
     if (rb > tb) tb = rb;
     if (sb > tb) tb = sb;
+    const bool join = plan_joins(opts, max_hits);
+    const size_t nw = join ? join_words(n) : 0;
     const size_t z[PLAN_ARRAYS] = {slots_total(max_bases, max_reads) * sizeof(SlotRec), nr * 8, nr * 8, 256, ms * 8,
                                    nr * 4, mh * 4, mh * 4, ms * sizeof(mb_smem), queue ? nr * 8 : 0,
                                    queue ? nr * 8 : 0, queue ? nr * 4 : 0, queue ? nr * 4 : 0, tb, ms * 4,
-                                   ms * 8, ms * 8, ms * 8, ms * 4, ms * 4, ms * 4, ms * 4, mh * 4};
+                                   ms * 8, ms * 8, ms * 8, ms * 4, ms * 4, ms * 4, ms * 4, mh * 4,
+                                   nw * sizeof(uint4), nw * 4, join ? 8u : 0u, join ? mh * 4 : 0, join ? mh * 4 : 0};
     for (int i = 0; i < PLAN_ARRAYS; ++i) sizes[i] = z[i];
 }
 
-size_t mb_plan_workspace_bytes(const mb_opts *opts, u32 max_reads, u64 max_bases, u64 max_smem, u64 max_hits) {
+size_t mb_plan_workspace_bytes(const mb_opts *opts, u64 n, u32 max_reads, u64 max_bases, u64 max_smem,
+                               u64 max_hits) {
     size_t sizes[PLAN_ARRAYS], total = 0;
-    plan_sizes(opts, max_reads, max_bases, max_smem, max_hits, sizes);
+    plan_sizes(opts, n, max_reads, max_bases, max_smem, max_hits, sizes);
     for (size_t z : sizes) total += align_up(z);
     return total;
 }
@@ -1873,7 +2155,8 @@ extern "C" int mb_plan_create(const mb_index *idx, const mb_opts *opts, uint32_t
     P->max_hits = max_hits ? max_hits : 1;
     P->nslots = slots_total(max_bases, max_reads);
     size_t sizes[PLAN_ARRAYS];
-    plan_sizes(opts, max_reads, max_bases, max_smem, max_hits, sizes);
+    const u64 n_rows = mb_dev_index(idx).n;
+    plan_sizes(opts, n_rows, max_reads, max_bases, max_smem, max_hits, sizes);
     size_t total = 0;
     for (size_t z : sizes) total += align_up(z);
     if (cudaMalloc(&P->mem, total) != cudaSuccess) {
@@ -1890,7 +2173,8 @@ extern "C" int mb_plan_create(const mb_index *idx, const mb_opts *opts, uint32_t
                                 (void **)&P->perm_alt, (void **)&P->tmp, (void **)&P->known, (void **)&P->share.keys,
                                 (void **)&P->share.keys_alt, (void **)&P->share.roff, (void **)&P->share.vals,
                                 (void **)&P->share.vals_alt, (void **)&P->share.pmax, (void **)&P->share.last,
-                                (void **)&P->share.rpos};
+                                (void **)&P->share.rpos, (void **)&P->share.marks, (void **)&P->share.mcnt,
+                                (void **)&P->share.nojoin, (void **)&P->share.succ, (void **)&P->share.dist};
     for (int i = 0; i < PLAN_ARRAYS; ++i) {
         *ptrs[i] = sizes[i] ? (void *)m : nullptr;
         m += align_up(sizes[i]);
@@ -1901,6 +2185,7 @@ extern "C" int mb_plan_create(const mb_index *idx, const mb_opts *opts, uint32_t
     P->share.tmp = P->tmp;
     P->share.err = plan_err(P);
     P->share.checked = (P->flags & MB_CHECKED) != 0;
+    P->share.join = plan_joins(opts, max_hits);
     *out = P;
     return MB_OK;
 }

@@ -166,8 +166,10 @@ void free_slot(Slot &s) {
     s = Slot{};
 }
 
-size_t slot_device_bytes(const mb_opts *o) {
-    return mb_plan_workspace_bytes(o, SLOT_READS, SLOT_BASES, SLOT_SMEM, SLOT_HITS) + SLOT_BASES + 16 +
+size_t slot_device_bytes(const mb_index *idx, const mb_opts *o) {
+    u64 n = 0, prim = 0, rl = 0;
+    mb_index_info(idx, &n, &prim, &rl);
+    return mb_plan_workspace_bytes(o, n, SLOT_READS, SLOT_BASES, SLOT_SMEM, SLOT_HITS) + SLOT_BASES + 16 +
            (SLOT_READS + 1) * 8;
 }
 
@@ -478,14 +480,14 @@ extern "C" int mb_serve_create(const mb_index *idx, const mb_opts *opts, uint64_
     std::unique_ptr<mb_server> S(new mb_server);
     S->idx = idx;
     if (opts) S->opts = *opts;
-    S->opts.flags |= MB_BATCHED;
+    S->opts.flags |= MB_BATCHED | MB_LOCATE_NO_JOIN;   // slots stay small: no mark words per slot
     S->opts.flags &= ~(u32)MB_COUNT;
     MB_CK(cudaGetDevice(&S->device));
     S->budget = hbm_budget;
     size_t fr = 0, tot = 0;
     MB_CK(cudaMemGetInfo(&fr, &tot));
     S->reserve = tot / 50 > RESERVE_MIN ? tot / 50 : RESERVE_MIN;
-    S->slot_bytes = slot_device_bytes(&S->opts);
+    S->slot_bytes = slot_device_bytes(idx, &S->opts);
     S->ring.size = RING_BYTES;
     if (cudaMallocHost(&S->ring.base, RING_BYTES) != cudaSuccess) {
         cudaGetLastError();

@@ -196,7 +196,7 @@ def test_work_counters_match_oracle(mb):
     G = mb.mb_index_build(ref)
     X = oracle.Index(ref)
     mb.profile_reset()
-    o = dict(flags=mb.MB_COUNT | mb.MB_NO_KMER | mb.MB_STEP_ONLY)
+    o = dict(flags=mb.MB_COUNT | mb.MB_NO_KMER | mb.MB_STEP_ONLY | mb.MB_LOCATE_NO_JOIN)
     sm, m, nh = mb.mb_seed_batch(G, rd.seq, rd.off, opts=o)
     mb.mb_locate(G, sm, m, opts=o, cap=nh)
     wc = mb.work_counters()
@@ -207,6 +207,11 @@ def test_work_counters_match_oracle(mb):
                            for k, s in zip(sm["k"][keep], sm["s"][keep])])
     assert len(np.unique(rows)) < len(rows)   # the repeat-rich reads repeat rows
     assert (wc["lf_steps"], wc["sa_reads"]) == X.count_locate(np.unique(rows))
+    # walks that join (the default): LF steps, S reads, joins and mark reads as the oracle counts
+    mb.profile_reset()
+    mb.mb_locate(G, sm, m, opts=dict(flags=mb.MB_COUNT), cap=nh)
+    wc = mb.work_counters()
+    assert (wc["lf_steps"], wc["sa_reads"], wc["joins"], wc["mark_reads"]) == X.count_locate_join(np.unique(rows))
     # with the index's 10-mer table (Section 2.5): the same steps, blocks and lookups as the
     # oracle's Algorithm 3 with the cache
     mb.profile_reset()

@@ -442,6 +442,44 @@ def test_alg3_kmer_cache_work_counts_exact_unique_read():
             assert X.count_alg3(P, off, l, 1, br, kmer_k=K) == (L - K, blocks, 1)
 
 
+def test_locate_join_work_counts_by_suffix_array():
+    """Walks that join, from the suffix array alone: the walk from the row of text position p
+    visits the rows of p-1, p-2, ...; it stops at the first position q <= p whose row is sampled
+    or is the $ row (q = 0), or, for q < p, whose row is another of the walked rows.  Its LF steps
+    are p - q; the oracle's counts (steps, S reads, joins, mark reads) must match this scan."""
+    ref, rd, p = synth.workload(2, scale=0.002)
+    X = oracle.Index(ref)
+    sm, over, hoff, hits = X.seed(rd.seq, rd.off)
+    rows = np.unique(np.concatenate([np.arange(int(k), int(k) + int(s_), dtype=np.uint64)
+                                     for k, s_, o in zip(sm["k"], sm["s"], over) if not o]))
+    SA = X.sa().astype(np.int64)
+    n = len(SA)
+    ISA = np.empty(n, np.int64)
+    ISA[SA] = np.arange(n)
+    walked = np.zeros(n, bool)
+    walked[rows.astype(np.int64)] = True
+    steps = sa = links = marks = 0
+    for row in rows.astype(np.int64):
+        pos, t = int(SA[row]), 0
+        while True:
+            rr = ISA[pos - t]
+            if rr % 32 == 0:
+                sa += 1
+                break
+            if pos - t == 0:          # the row of position 0 is the $ row
+                break
+            if t > 0:
+                marks += 1
+                if walked[rr]:
+                    links += 1
+                    break
+            t += 1
+        steps += t
+    assert X.count_locate_join(rows) == (steps, sa, links, marks)
+    assert links > len(rows) // 4          # repeat-rich reads: many walks join
+    assert steps < X.count_locate(rows)[0] // 2
+
+
 def _bs_seed_and_split(ref, seq, off, mate):
     X = oracle.Index(ref, bs3=True)
     conv = oracle.bs_convert_reads(seq, off, mate)
