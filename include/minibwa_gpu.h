@@ -446,8 +446,8 @@ const char *mb_last_error(void);
  * lookups, LF steps of Algorithm 2 and sampled-SA reads.
  * mb_work_counters_all: the same five followed by the work of extending unique matches by text
  * comparison (LF steps of its walks, SA / ISA sample reads, text loads of 8 bytes), then of the
- * locate walks that join (mark-word reads, walks that stopped at another walked row), `count`
- * values at most (10 exist).  The LF steps and sampled-S reads are those of the walks run: with
+ * locate walks that join (mark-word reads, walks that stopped at another walked row, the longest
+ * chain of such walks: a maximum, not a sum), `count` values at most (11 exist).  The LF steps and sampled-S reads are those of the walks run: with
  * joins (the default) fewer than Algorithm 2's, with MB_LOCATE_NO_JOIN exactly Algorithm 2's over
  * the distinct rows.
  */

@@ -415,10 +415,10 @@ def launch_count() -> int:
 
 
 def work_counters() -> dict:
-    v = np.zeros(10, dtype=np.uint64)
-    lib().mb_work_counters_all(_ptr(v), 10)
+    v = np.zeros(11, dtype=np.uint64)
+    lib().mb_work_counters_all(_ptr(v), 11)
     return dict(zip(("ext_steps", "ext_blocks", "kmer_lookups", "lf_steps", "sa_reads", "u_walk_steps",
-                     "u_samples", "u_text_loads", "mark_reads", "joins"), (int(x) for x in v)))
+                     "u_samples", "u_text_loads", "mark_reads", "joins", "longest_chain"), (int(x) for x in v)))
 
 
 # ---------------------------------------------------------------------------- batched form

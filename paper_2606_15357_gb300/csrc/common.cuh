@@ -93,7 +93,8 @@ enum {
     WC_EXT_STEPS = 0, WC_EXT_BLOCKS = 1, WC_KMER = 2, WC_LF_STEPS = 3, WC_SA_READS = 4,
     WC_U_WALK = 5, WC_U_SAMPLE = 6, WC_U_TEXT = 7,   // U_*: extension of unique matches by text
     WC_MARKS = 8, WC_LINKS = 9,                       // locate: mark-word loads, walks ended at another hit row
-    WC_N = 10
+    WC_CHAIN_MAX = 10,                                // locate: the longest chain of joined walks
+    WC_N = 11
 };
 u64 *mb_work_counter_buf(cudaStream_t st);   // device array of WC_N u64 (zeroed on first use)
 

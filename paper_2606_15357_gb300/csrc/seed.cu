@@ -1264,7 +1264,7 @@ template <bool COUNT, bool POW2, int D>
 __global__ void __launch_bounds__(256, D <= 8 ? 2 : 1)
     k_locate_join(DevIndex I, const u32 *__restrict__ rows, u64 nhits, const u64 *__restrict__ nhits_dev,
                   u32 *__restrict__ hits, const uint4 *__restrict__ marks, const u32 *__restrict__ nojoin,
-                  u32 *__restrict__ succ, u32 *__restrict__ dist, u64 *wc, u32 *chk) {
+                  u32 *__restrict__ succ, u64 *wc, u32 *chk) {
     const u32 lane = threadIdx.x & 31;
     if (nhits_dev && *nhits_dev < nhits) nhits = *nhits_dev;
     const bool join = *nojoin == 0;
@@ -1339,8 +1339,7 @@ __global__ void __launch_bounds__(256, D <= 8 ? 2 : 1)
             if ((stop >> d) & 1u) {
                 if ((lnk >> d) & 1u) {   // row[d] holds the rank of the marked row met
                     whits[h[d]] = LINKED;
-                    dist[wbase + h[d]] = steps[d];
-                    succ[row[d]] = (u32)(wbase + h[d]);
+                    reinterpret_cast<uint2 *>(succ)[row[d]] = make_uint2((u32)(wbase + h[d]), steps[d]);
                     work.links += 1;
                 } else if (!((skp >> d) & 1u)) {
                     whits[h[d]] = (steps[d] > n || row[d] >= n) ? 0xFFFFFFFFu
@@ -1372,22 +1371,27 @@ __global__ void __launch_bounds__(256, D <= 8 ? 2 : 1)
 }
 
 // Positions of the linked walks: one thread per chain head (a walk that reached a sampled or $
-// row) adds the distances along its successors.
-__global__ void k_join_resolve(u32 *__restrict__ rpos, const u32 *__restrict__ succ, const u32 *__restrict__ dist,
-                               const u64 *__restrict__ nrows_dev, u64 cap) {
+// row) adds the distances along its successors; link[j] = {the walk that stopped at row j, its
+// distance}, one load per link.
+__global__ void k_join_resolve(u32 *__restrict__ rpos, const uint2 *__restrict__ link,
+                               const u64 *__restrict__ nrows_dev, u64 cap, u64 *wc) {
     const u64 nr = count_of(cap, nrows_dev);
+    u64 longest = 0;
     for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < nr; i += (u64)gridDim.x * blockDim.x) {
         u32 p = rpos[i];
         if (p >= LINKED) continue;
         u32 cur = (u32)i;
-        for (u64 guard = 0; guard < nr; ++guard) {   // a chain visits each row once
-            const u32 s = succ[cur];
-            if (s == NOPOS || s >= nr) break;
-            p += dist[s];
-            rpos[s] = p;
-            cur = s;
+        u64 len = 0;
+        for (; len < nr; ++len) {   // a chain visits each row once
+            const uint2 l = link[cur];
+            if (l.x >= nr) break;
+            p += l.y;
+            rpos[l.x] = p;
+            cur = l.x;
         }
+        longest = len > longest ? len : longest;
     }
+    if (wc && longest) atomicMax((unsigned long long *)&wc[WC_CHAIN_MAX], (unsigned long long)longest);
 }
 
 __global__ void k_bs_filter(const mb_smem *__restrict__ sm, u64 nsm, const u8 *__restrict__ mate,
@@ -1508,14 +1512,15 @@ struct ShareBufs {
     // not-sorted flag, per walked row its successor and its distance
     bool join = true;
     uint4 *marks = nullptr;
-    u32 *mcnt = nullptr, *nojoin = nullptr, *succ = nullptr, *dist = nullptr;
+    u32 *mcnt = nullptr, *nojoin = nullptr;
+    u32 *succ = nullptr;   // uint2 per walked row: the walk that stopped at it and that walk's distance
 };
 // mark words of an index of n rows
 inline u64 join_words(u64 n) { return n / BLK_ROWS + 1; }
 
 template <bool COUNT, bool POW2, int D>
 int launch_join_t(const DevIndex &I, const u32 *rows, u64 nhits, const u64 *nhits_dev, u32 *rpos, const uint4 *marks,
-                  const u32 *nojoin, u32 *succ, u32 *dist, u64 *wc, u32 *chk, cudaStream_t st) {
+                  const u32 *nojoin, u32 *succ, u64 *wc, u32 *chk, cudaStream_t st) {
     const unsigned g =
         resident_grid((const void *)k_locate_join<COUNT, POW2, D>, 256, (nhits + 63) / 64 * 32);
     const u64 warps = (u64)g * 8;
@@ -1523,8 +1528,7 @@ int launch_join_t(const DevIndex &I, const u32 *rows, u64 nhits, const u64 *nhit
         mb_set_error("locate: %llu hits over %llu warps", (unsigned long long)nhits, (unsigned long long)warps);
         return MB_ERR_ARG;
     }
-    k_locate_join<COUNT, POW2, D><<<g, 256, 0, st>>>(I, rows, nhits, nhits_dev, rpos, marks, nojoin, succ, dist, wc,
-                                                     chk);
+    k_locate_join<COUNT, POW2, D><<<g, 256, 0, st>>>(I, rows, nhits, nhits_dev, rpos, marks, nojoin, succ, wc, chk);
     MB_KCHECK();
     return MB_OK;
 }
@@ -1532,25 +1536,24 @@ int launch_join(const DevIndex &I, const u32 *rows, u64 nhits, const u64 *nhits_
                 u64 *wc, bool count, u32 depth, u32 *chk, cudaStream_t st) {
     const bool pow2 = (I.r & (I.r - 1)) == 0;
     if (count || !pow2)
-        return count ? (pow2 ? launch_join_t<true, true, 1>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin, b.succ,
-                                                             b.dist, wc, chk, st)
+        return count ? (pow2 ? launch_join_t<true, true, 1>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin, b.succ, wc, chk, st)
                              : launch_join_t<true, false, 1>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin,
-                                                              b.succ, b.dist, wc, chk, st))
+                                                              b.succ, wc, chk, st))
                      : launch_join_t<false, false, 1>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin, b.succ,
-                                                       b.dist, wc, chk, st);
+                                                       wc, chk, st);
     if (depth >= 16)
-        return launch_join_t<false, true, 16>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin, b.succ, b.dist, wc,
+        return launch_join_t<false, true, 16>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin, b.succ, wc,
                                               chk, st);
     if (depth >= 8)
-        return launch_join_t<false, true, 8>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin, b.succ, b.dist, wc,
+        return launch_join_t<false, true, 8>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin, b.succ, wc,
                                              chk, st);
     if (depth >= 4)
-        return launch_join_t<false, true, 4>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin, b.succ, b.dist, wc,
+        return launch_join_t<false, true, 4>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin, b.succ, wc,
                                              chk, st);
     if (depth >= 2)
-        return launch_join_t<false, true, 2>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin, b.succ, b.dist, wc,
+        return launch_join_t<false, true, 2>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin, b.succ, wc,
                                              chk, st);
-    return launch_join_t<false, true, 1>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin, b.succ, b.dist, wc, chk,
+    return launch_join_t<false, true, 1>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin, b.succ, wc, chk,
                                          st);
 }
 
@@ -1592,7 +1595,7 @@ int locate_shared(const DevIndex &I, const mb_smem *sm, u64 cap, const u64 *nsm_
         const u64 nw = join_words(I.n);
         MB_CK(cudaMemsetAsync(b.marks, 0, nw * sizeof(uint4), st));
         MB_CK(cudaMemsetAsync(b.nojoin, 0, 4, st));
-        MB_CK(cudaMemsetAsync(b.succ, 0xFF, hits_cap * 4, st));
+        MB_CK(cudaMemsetAsync(b.succ, 0xFF, hits_cap * 8, st));
         const unsigned GR = grid_for(hits_cap, 256);
         k_join_mark<<<GR, 256, 0, st>>>(b.rows, b.nrows, hits_cap, b.marks, b.nojoin);
         MB_KCHECK();
@@ -1604,7 +1607,7 @@ int locate_shared(const DevIndex &I, const mb_smem *sm, u64 cap, const u64 *nsm_
         if (kt) kt->start();
         MB_TRY(launch_join(I, b.rows, hits_cap, b.nrows, b.rpos, b, wc, count, depth, chk, st));
         if (kt) kt->stop();
-        k_join_resolve<<<GR, 256, 0, st>>>(b.rpos, b.succ, b.dist, b.nrows, hits_cap);
+        k_join_resolve<<<GR, 256, 0, st>>>(b.rpos, reinterpret_cast<const uint2 *>(b.succ), b.nrows, hits_cap, wc);
         MB_KCHECK();
     } else {
         if (kt) kt->start();
@@ -1792,8 +1795,7 @@ static int share_alloc(DevBuf &bw, u64 n_smem, u64 total, u64 n, bool join, cuda
         b.marks = (uint4 *)take(nw * sizeof(uint4));
         b.mcnt = (u32 *)take(nw * 4);
         b.nojoin = (u32 *)take(8);
-        b.succ = (u32 *)take(total * 4);
-        b.dist = (u32 *)take(total * 4);
+        b.succ = (u32 *)take(total * 8);
     }
     MB_CK(cudaMemsetAsync(b.err, 0, 8, st));
     return MB_OK;
@@ -2098,7 +2100,7 @@ void mb_plan_arrays(const mb_plan *p, const mb_smem **smem, const u32 **hits, u6
 }
 
 // Device workspace of a plan, one entry per array (in the order mb_plan_create lays them out).
-constexpr int PLAN_ARRAYS = 28;
+constexpr int PLAN_ARRAYS = 27;
 // A plan locates with walks that join (their arrays sized by the index's n rows) unless the options
 // say MB_LOCATE_NO_JOIN or the plan holds no hits to locate (a seeding-only plan).
 static bool plan_joins(const mb_opts *opts, u64 max_hits) {
@@ -2118,7 +2120,7 @@ static void plan_sizes(const mb_opts *opts, u64 n, u32 max_reads, u64 max_bases,
                                    nr * 4, mh * 4, mh * 4, ms * sizeof(mb_smem), queue ? nr * 8 : 0,
                                    queue ? nr * 8 : 0, queue ? nr * 4 : 0, queue ? nr * 4 : 0, tb, ms * 4,
                                    ms * 8, ms * 8, ms * 8, ms * 4, ms * 4, ms * 4, ms * 4, mh * 4,
-                                   nw * sizeof(uint4), nw * 4, join ? 8u : 0u, join ? mh * 4 : 0, join ? mh * 4 : 0};
+                                   nw * sizeof(uint4), nw * 4, join ? 8u : 0u, join ? mh * 8 : 0};
     for (int i = 0; i < PLAN_ARRAYS; ++i) sizes[i] = z[i];
 }
 
@@ -2174,7 +2176,7 @@ extern "C" int mb_plan_create(const mb_index *idx, const mb_opts *opts, uint32_t
                                 (void **)&P->share.keys_alt, (void **)&P->share.roff, (void **)&P->share.vals,
                                 (void **)&P->share.vals_alt, (void **)&P->share.pmax, (void **)&P->share.last,
                                 (void **)&P->share.rpos, (void **)&P->share.marks, (void **)&P->share.mcnt,
-                                (void **)&P->share.nojoin, (void **)&P->share.succ, (void **)&P->share.dist};
+                                (void **)&P->share.nojoin, (void **)&P->share.succ};
     for (int i = 0; i < PLAN_ARRAYS; ++i) {
         *ptrs[i] = sizes[i] ? (void *)m : nullptr;
         m += align_up(sizes[i]);
