@@ -63,10 +63,11 @@ enum {
                               by comparing text */
 #define MB_STEP_ONLY 0x40u /* seeding: extend every match step by step (Algorithm 1), even where
                               the auxiliary arrays allow comparing text */
-#define MB_LOCATE_NO_JOIN 0x100u /* locate: every LF-walk runs to its sampled row; by default a walk
-                              stops where it meets the row of another hit of the call and takes that
-                              hit's position plus its distance (same positions, fewer LF steps; it
-                              needs about 20 bytes per 64 text positions of device workspace) */
+#define MB_LOCATE_JOIN 0x100u /* locate: a walk stops where it meets the row of another hit of the
+                              call and takes that hit's position plus its distance, chains of such
+                              walks resolved from their heads (same positions, about 6x fewer LF
+                              steps; about 20 bytes per 64 text positions of device workspace); by
+                              default every LF-walk runs to its sampled row */
 #define MB_SMEM_ONE_LOOP 0x80u /* tuning: the SMEM kernel in its one-loop form (every iteration runs
                               every stage's code) instead of the split form (uniform block steps,
                               the other actions in service passes); same output */
@@ -447,9 +448,8 @@ const char *mb_last_error(void);
  * mb_work_counters_all: the same five followed by the work of extending unique matches by text
  * comparison (LF steps of its walks, SA / ISA sample reads, text loads of 8 bytes), then of the
  * locate walks that join (mark-word reads, walks that stopped at another walked row, the longest
- * chain of such walks: a maximum, not a sum), `count` values at most (11 exist).  The LF steps and sampled-S reads are those of the walks run: with
- * joins (the default) fewer than Algorithm 2's, with MB_LOCATE_NO_JOIN exactly Algorithm 2's over
- * the distinct rows.
+ * chain of such walks: a maximum, not a sum), `count` values at most (11 exist).  The LF steps and sampled-S reads are those of the walks run: exactly
+ * Algorithm 2's over the distinct rows, or fewer with MB_LOCATE_JOIN.
  */
 void mb_profile_enable(int on);
 int mb_profile_get(const char *kernel, double *ms, uint64_t *launches);

@@ -20,7 +20,7 @@ __all__ = ["SMEM_DTYPE", "Opts", "MbError", "lib", "build", "Index", "mb_index_b
            "mb_index_load", "mb_seed_batch", "mb_locate", "mb_bs_filter", "seed"]
 
 MB_BS3, MB_BATCHED, MB_CHECKED, MB_NO_KMER, MB_COUNT = 0x1, 0x2, 0x4, 0x8, 0x10
-MB_NO_AUX, MB_STEP_ONLY, MB_SMEM_ONE_LOOP, MB_LOCATE_NO_JOIN = 0x20, 0x40, 0x80, 0x100
+MB_NO_AUX, MB_STEP_ONLY, MB_SMEM_ONE_LOOP, MB_LOCATE_JOIN = 0x20, 0x40, 0x80, 0x100
 AUX_RATE = 4   # sample rate of the auxiliary SA / ISA samples (mb_index_export_aux)
 MB_SMEM_OVER_MAX_OCC, MB_SMEM_ROUND2 = 0x1, 0x2
 MB_ERR_CAPACITY = -3

@@ -1807,7 +1807,7 @@ int mb_locate_records(const mb_index *idx, const mb_smem *sm, u64 n_smem, const 
     DevBuf bw;
     ShareBufs b;
     const DevIndex I = mb_dev_index(idx);
-    MB_TRY(share_alloc(bw, n_smem, n_hits, I.n, true, st, b));
+    MB_TRY(share_alloc(bw, n_smem, n_hits, I.n, false, st, b));
     return locate_shared(I, sm, n_smem, nullptr, known, hits, n_hits, b, nullptr, false, depth, nullptr, st);
 }
 
@@ -1843,7 +1843,7 @@ extern "C" int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_sm
     const bool count = opts && (opts->flags & MB_COUNT);
     DevBuf bw;
     ShareBufs b;
-    MB_TRY(share_alloc(bw, n_smem, total, I.n, !(opts && (opts->flags & MB_LOCATE_NO_JOIN)), st, b));
+    MB_TRY(share_alloc(bw, n_smem, total, I.n, opts && (opts->flags & MB_LOCATE_JOIN), st, b));
     b.checked = opts && (opts->flags & MB_CHECKED);
     u64 *wc = count ? mb_work_counter_buf(st) : nullptr;
     KTimer kt("locate", st);
@@ -2101,10 +2101,10 @@ void mb_plan_arrays(const mb_plan *p, const mb_smem **smem, const u32 **hits, u6
 
 // Device workspace of a plan, one entry per array (in the order mb_plan_create lays them out).
 constexpr int PLAN_ARRAYS = 27;
-// A plan locates with walks that join (their arrays sized by the index's n rows) unless the options
-// say MB_LOCATE_NO_JOIN or the plan holds no hits to locate (a seeding-only plan).
+// A plan locates with walks that join (their arrays sized by the index's n rows) when the options
+// say MB_LOCATE_JOIN and the plan holds hits to locate (not a seeding-only plan).
 static bool plan_joins(const mb_opts *opts, u64 max_hits) {
-    return !(opts && (opts->flags & MB_LOCATE_NO_JOIN)) && max_hits > 1;
+    return opts && (opts->flags & MB_LOCATE_JOIN) && max_hits > 1;
 }
 static void plan_sizes(const mb_opts *opts, u64 n, u32 max_reads, u64 max_bases, u64 max_smem, u64 max_hits,
                        size_t sizes[PLAN_ARRAYS]) {

@@ -480,7 +480,8 @@ extern "C" int mb_serve_create(const mb_index *idx, const mb_opts *opts, uint64_
     std::unique_ptr<mb_server> S(new mb_server);
     S->idx = idx;
     if (opts) S->opts = *opts;
-    S->opts.flags |= MB_BATCHED | MB_LOCATE_NO_JOIN;   // slots stay small: no mark words per slot
+    S->opts.flags |= MB_BATCHED;
+    S->opts.flags &= ~(u32)MB_LOCATE_JOIN;   // slots stay small: no mark words per slot
     S->opts.flags &= ~(u32)MB_COUNT;
     MB_CK(cudaGetDevice(&S->device));
     S->budget = hbm_budget;

@@ -106,15 +106,23 @@ def test_workload1_full(mb):
     compare_seed(sm, hits, X, rd.seq, rd.off)
 
 
+@pytest.mark.parametrize("join", [False, True])
 @pytest.mark.parametrize("depth", [1, 2, 4, 8, 16])
-def test_locate_walks_per_lane(mb, depth):
-    """Locate with 1, 2, 4, 8 or 16 LF-walks in flight per lane gives the same hits."""
+def test_locate_walks_per_lane(mb, depth, join):
+    """Locate with 1, 2, 4, 8 or 16 LF-walks in flight per lane, with and without walks that join
+    (MB_LOCATE_JOIN), gives the same hits."""
     ref, rd, p = synth.workload(2, scale=0.01)
     G = mb.mb_index_build(ref)
     X = oracle.Index(ref)
     sm, m, nh = mb.mb_seed_batch(G, rd.seq, rd.off)
-    hits, _ = mb.mb_locate(G, sm, m, opts=dict(prefetch_depth=depth), cap=nh)
+    o = dict(prefetch_depth=depth, flags=mb.MB_LOCATE_JOIN if join else 0)
+    hits, _ = mb.mb_locate(G, sm, m, opts=o, cap=nh)
     compare_seed(sm, hits, X, rd.seq, rd.off)
+    if join:   # the same through a plan (its own mark words and successor entries)
+        P = mb.Plan(G, rd.n, len(rd.seq), m + 8, nh + 8, opts=o)
+        P.run(torch.from_numpy(rd.seq).cuda(), torch.from_numpy(rd.off.view(np.int64)).cuda())
+        psm, phits = P.result()
+        assert psm.tobytes() == sm.tobytes() and np.array_equal(phits, hits)
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
@@ -160,9 +168,11 @@ def test_locate_shared_rows_any_intervals(mb, seed):
     rows = np.concatenate([np.arange(int(k), int(k) + int(c), dtype=np.int64) for k, c in zip(sm["k"], cnt)])
     assert len(np.unique(rows)) < len(rows)
     for depth in (1, 16):
-        hits, nh = mb.mb_locate(G, sm, len(sm), opts=dict(prefetch_depth=depth), cap=int(cnt.sum()))
-        assert nh == len(rows)
-        assert np.array_equal(hits.astype(np.int64), S[rows].astype(np.int64))
+        for flags in (0, mb.MB_LOCATE_JOIN):   # with joins the rows are not sorted: the walks run plain
+            hits, nh = mb.mb_locate(G, sm, len(sm), opts=dict(prefetch_depth=depth, flags=flags),
+                                    cap=int(cnt.sum()))
+            assert nh == len(rows)
+            assert np.array_equal(hits.astype(np.int64), S[rows].astype(np.int64))
     dsm = torch.from_numpy(sm.view(np.uint8)).cuda()
     out = torch.empty(len(rows), dtype=torch.int32, device="cuda")
     mb.mb_locate(G, dsm, len(sm), hits=out, cap=len(rows))
@@ -196,7 +206,7 @@ def test_work_counters_match_oracle(mb):
     G = mb.mb_index_build(ref)
     X = oracle.Index(ref)
     mb.profile_reset()
-    o = dict(flags=mb.MB_COUNT | mb.MB_NO_KMER | mb.MB_STEP_ONLY | mb.MB_LOCATE_NO_JOIN)
+    o = dict(flags=mb.MB_COUNT | mb.MB_NO_KMER | mb.MB_STEP_ONLY)
     sm, m, nh = mb.mb_seed_batch(G, rd.seq, rd.off, opts=o)
     mb.mb_locate(G, sm, m, opts=o, cap=nh)
     wc = mb.work_counters()
@@ -207,9 +217,9 @@ def test_work_counters_match_oracle(mb):
                            for k, s in zip(sm["k"][keep], sm["s"][keep])])
     assert len(np.unique(rows)) < len(rows)   # the repeat-rich reads repeat rows
     assert (wc["lf_steps"], wc["sa_reads"]) == X.count_locate(np.unique(rows))
-    # walks that join (the default): LF steps, S reads, joins and mark reads as the oracle counts
+    # walks that join (MB_LOCATE_JOIN): LF steps, S reads, joins and mark reads as the oracle counts
     mb.profile_reset()
-    mb.mb_locate(G, sm, m, opts=dict(flags=mb.MB_COUNT), cap=nh)
+    mb.mb_locate(G, sm, m, opts=dict(flags=mb.MB_COUNT | mb.MB_LOCATE_JOIN), cap=nh)
     wc = mb.work_counters()
     assert (wc["lf_steps"], wc["sa_reads"], wc["joins"], wc["mark_reads"]) == X.count_locate_join(np.unique(rows))
     # with the index's 10-mer table (Section 2.5): the same steps, blocks and lookups as the
