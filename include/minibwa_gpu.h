@@ -51,9 +51,9 @@ enum {
 #define MB_BATCHED  0x2u   /* seeding: lanes take reads from a device work queue (a plan orders it
                               by decreasing read length; mb_seed_batch keeps read order) */
 #define MB_CHECKED  0x4u   /* seeding / locate: the kernels also check every occurrence row they
-                              read against the text length (only a damaged index can fail it); a
-                              failed check ends that read or walk and the call returns
-                              MB_ERR_DEVICE_CHECK.  Without the flag the kernels still check every
+                              read against the text length (only a damaged index can fail it; the
+                              checked locate runs one walk per lane); a failed check ends that read
+                              or walk and the call returns MB_ERR_DEVICE_CHECK.  Without the flag the kernels still check every
                               read's offsets and every record's rows (MB_ERR_DEVICE_CHECK), and the
                               host checks every device buffer against its allocation (MB_ERR_ARG) */
 #define MB_NO_KMER  0x8u   /* seeding: do not use the k-mer ds-interval table */

@@ -1111,7 +1111,8 @@ __global__ void k_share_copy(const u64 *__restrict__ keys, const u32 *__restrict
 // 0xFFFFFFFF).  Offsets within a warp's range are u32 (the host keeps ranges below 2^32 - 2^12).
 // Launch bounds: 16 walks per lane fit one block of 8 warps per SM, 8 walks two blocks, fewer
 // walks three.
-template <bool COUNT, bool POW2, int D>
+// CHK (MB_CHECKED): every row walked is checked against the text length, failures recorded in *chk.
+template <bool COUNT, bool POW2, int D, bool CHK = false>
 __global__ void __launch_bounds__(256, D == 8 ? 2 : 1) k_locate(DevIndex I, const u32 *__restrict__ rows, u64 nhits,
                                                 const u64 *__restrict__ nhits_dev, u32 *__restrict__ hits, u64 *wc,
                                                 u32 *chk) {
@@ -1151,8 +1152,8 @@ __global__ void __launch_bounds__(256, D == 8 ? 2 : 1) k_locate(DevIndex I, cons
         for (int d = 0; d < D; ++d) {
             const bool on = (live >> d) & 1u;
             const bool skip = row[d] == NOPOS;   // a row to skip (its hit is written elsewhere)
-            const bool bad = chk && on && !skip && row[d] >= n;   // MB_CHECKED: a row outside the text
-            if (bad) atomicOr(chk, (u32)DEVCHK_BOUNDS);
+            const bool bad = CHK && on && !skip && row[d] >= n;   // MB_CHECKED: a row outside the text
+            if (CHK && bad) atomicOr(chk, (u32)DEVCHK_BOUNDS);
             const bool sampled = !skip && !bad && (POW2 ? (row[d] & rmask) == 0 : row[d] % r == 0);
             const bool st = on && (skip || bad || sampled || row[d] == prim || steps[d] > n);
             sv[d] = 0;
@@ -1181,8 +1182,9 @@ __global__ void __launch_bounds__(256, D == 8 ? 2 : 1) k_locate(DevIndex I, cons
         for (int d = 0; d < D; ++d) {
             if ((stop >> d) & 1u) {
                 if (!((skp >> d) & 1u))
-                    whits[h[d]] = (steps[d] > n || row[d] >= n) ? 0xFFFFFFFFu
-                                                                : (((smp >> d) & 1u) ? sv[d] + steps[d] : steps[d]);
+                    whits[h[d]] = (steps[d] > n || (CHK && row[d] >= n))
+                                      ? 0xFFFFFFFFu
+                                      : (((smp >> d) & 1u) ? sv[d] + steps[d] : steps[d]);
                 work.lf += steps[d];
                 work.sa += (smp >> d) & 1u;
                 h[d] = give;
@@ -1470,16 +1472,16 @@ void smem_tuning(const mb_opts *o, SmemArgs &a) {
     a.warps = o ? o->smem_warps : 0;
 }
 
-template <bool COUNT, bool POW2, int D>
+template <bool COUNT, bool POW2, int D, bool CHK = false>
 int launch_locate_t(const DevIndex &I, const u32 *rows, u64 nhits, const u64 *nhits_dev, u32 *hits, u64 *wc,
                     u32 *chk, cudaStream_t st) {
-    const unsigned g = resident_grid((const void *)k_locate<COUNT, POW2, D>, 256, (nhits + 63) / 64 * 32);
+    const unsigned g = resident_grid((const void *)k_locate<COUNT, POW2, D, CHK>, 256, (nhits + 63) / 64 * 32);
     const u64 warps = (u64)g * 8;
     if ((nhits + warps - 1) / warps >= (1ull << 32) - 4096) {   // offsets within a warp's range are u32
         mb_set_error("locate: %llu hits over %llu warps", (unsigned long long)nhits, (unsigned long long)warps);
         return MB_ERR_ARG;
     }
-    k_locate<COUNT, POW2, D><<<g, 256, 0, st>>>(I, rows, nhits, nhits_dev, hits, wc, chk);
+    k_locate<COUNT, POW2, D, CHK><<<g, 256, 0, st>>>(I, rows, nhits, nhits_dev, hits, wc, chk);
     MB_KCHECK();
     return MB_OK;
 }
@@ -1488,6 +1490,9 @@ int launch_locate_t(const DevIndex &I, const u32 *rows, u64 nhits, const u64 *nh
 int launch_locate(const DevIndex &I, const u32 *rows, u64 nhits, const u64 *nhits_dev, u32 *hits, u64 *wc,
                   bool count, u32 depth, u32 *chk, cudaStream_t st) {
     const bool pow2 = (I.r & (I.r - 1)) == 0;
+    if (chk)   // MB_CHECKED: one walk per lane, every row checked
+        return pow2 ? launch_locate_t<false, true, 1, true>(I, rows, nhits, nhits_dev, hits, wc, chk, st)
+                    : launch_locate_t<false, false, 1, true>(I, rows, nhits, nhits_dev, hits, wc, chk, st);
     if (count) return pow2 ? launch_locate_t<true, true, 1>(I, rows, nhits, nhits_dev, hits, wc, chk, st)
                            : launch_locate_t<true, false, 1>(I, rows, nhits, nhits_dev, hits, wc, chk, st);
     if (!pow2) return launch_locate_t<false, false, 1>(I, rows, nhits, nhits_dev, hits, wc, chk, st);
