@@ -701,7 +701,7 @@ def run_gpu(args):
 
     # work counters (untimed pass with counting kernels)
     mb.profile_reset()
-    copts = dict(opts, flags=mb.MB_COUNT)
+    copts = dict(opts, flags=mb.MB_COUNT | (mb.MB_LOCATE_JOIN if args.locate_join else 0))
     _, m, nh = mb.mb_seed_batch(idx, seq, off, opts=copts, out=out, cap=cap)
     mb.mb_locate(idx, out, m, opts=copts, hits=hits, cap=nh)
     wc = mb.work_counters()
@@ -715,7 +715,8 @@ def run_gpu(args):
         log(f"autotuned on {ns} reads: {mb.shape_of(best)}")
     else:
         best = mb.Opts(block_size=args.block, prefetch_depth=args.locate_walks,
-                       flags=(mb.MB_BATCHED if args.queue else 0) | (mb.MB_SMEM_ONE_LOOP if args.one_loop else 0),
+                       flags=(mb.MB_BATCHED if args.queue else 0) | (mb.MB_SMEM_ONE_LOOP if args.one_loop else 0) |
+                       (mb.MB_LOCATE_JOIN if args.locate_join else 0),
                        smem_burst=args.smem_burst, smem_wait=args.smem_wait)
     opts["block_size"] = best.block_size
     opts["prefetch_depth"] = best.prefetch_depth
@@ -1009,6 +1010,7 @@ def main():
                     help="SMEM kernel walks fixed read ranges per warp instead of a device work queue")
     ap.add_argument("--locate-walks", type=int, default=16, choices=[1, 2, 4, 8, 16])
     ap.add_argument("--one-loop", action="store_true", help="SMEM kernel in its one-loop form")
+    ap.add_argument("--locate-join", action="store_true", help="locate with walks that join (MB_LOCATE_JOIN)")
     ap.add_argument("--smem-burst", type=int, default=0, help="SMEM kernel block steps between service passes")
     ap.add_argument("--smem-wait", type=int, default=0, help="SMEM kernel lanes out of the loop that call a pass")
     ap.add_argument("--reads", type=int, default=0,
