@@ -699,14 +699,6 @@ def run_gpu(args):
         mb.mb_locate(idx, out, m_, opts=opts, hits=hits, cap=nh_)
         return m_, nh_
 
-    # work counters (untimed pass with counting kernels)
-    mb.profile_reset()
-    copts = dict(opts, flags=mb.MB_COUNT | (mb.MB_LOCATE_JOIN if args.locate_join else 0))
-    _, m, nh = mb.mb_seed_batch(idx, seq, off, opts=copts, out=out, cap=cap)
-    mb.mb_locate(idx, out, m, opts=copts, hits=hits, cap=nh)
-    wc = mb.work_counters()
-    log(f"work: {m} SMEMs, {nh} hits, {wc}")
-
     # launch shape: fixed (--block / --locate-walks, the autotuner's choice on this workload), or
     # autotuned on a sample of the batch with --autotune; used for both forms
     ns = min(n_reads, 1_000_000)
@@ -723,6 +715,14 @@ def run_gpu(args):
     opts["flags"] = best.flags
     opts["smem_burst"] = best.smem_burst
     opts["smem_wait"] = best.smem_wait
+
+    # work counters of the chosen form (untimed pass with counting kernels)
+    mb.profile_reset()
+    copts = dict(opts, flags=mb.MB_COUNT | (best.flags & mb.MB_LOCATE_JOIN))
+    _, m, nh = mb.mb_seed_batch(idx, seq, off, opts=copts, out=out, cap=cap)
+    mb.mb_locate(idx, out, m, opts=copts, hits=hits, cap=nh)
+    wc = mb.work_counters()
+    log(f"work: {m} SMEMs, {nh} hits, {wc}")
 
     for _ in range(args.warmup):
         step()
@@ -794,9 +794,9 @@ def run_gpu(args):
     peak, peak_kind = measured_peaks()
     smem_bytes = (BLOCK_BYTES * (wc["ext_blocks"] + wc["u_walk_steps"]) + 12 * wc["kmer_lookups"] +
                   4 * wc["u_samples"] + 8 * wc["u_text_loads"])
-    # locate with walks that join: 32 B per LF step, 4 B per sampled-S read, 8 B per mark-word read,
-    # 4 B per rank read of a join
-    loc_bytes = BLOCK_BYTES * wc["lf_steps"] + 4 * wc["sa_reads"] + 8 * wc["mark_reads"] + 4 * wc["joins"]
+    # locate: 32 B per LF step (an occurrence block or a walk block), 4 B per sampled-S read, and
+    # for walks that join 8 B per join (the rank word and the joined row's position)
+    loc_bytes = BLOCK_BYTES * wc["lf_steps"] + 4 * wc["sa_reads"] + 8 * wc["joins"]
     if loc_ms / max(loc_n, 1) >= smem_ms / max(smem_n, 1):
         kname, kbytes, kms = "locate", loc_bytes, loc_ms / max(loc_n, 1)
     else:
@@ -1008,9 +1008,12 @@ def main():
     ap.add_argument("--block", type=int, default=512, choices=[128, 256, 512])
     ap.add_argument("--no-queue", dest="queue", action="store_false",
                     help="SMEM kernel walks fixed read ranges per warp instead of a device work queue")
-    ap.add_argument("--locate-walks", type=int, default=16, choices=[1, 2, 4, 8, 16])
+    ap.add_argument("--locate-walks", type=int, default=4, choices=[1, 2, 4, 8, 16])
     ap.add_argument("--one-loop", action="store_true", help="SMEM kernel in its one-loop form")
-    ap.add_argument("--locate-join", action="store_true", help="locate with walks that join (MB_LOCATE_JOIN)")
+    ap.add_argument("--locate-join", dest="locate_join", action="store_true", default=True,
+                    help="(default) locate with walks that join (MB_LOCATE_JOIN)")
+    ap.add_argument("--no-locate-join", dest="locate_join", action="store_false",
+                    help="plain locate walks: every walk runs to its sampled row")
     ap.add_argument("--smem-burst", type=int, default=0, help="SMEM kernel block steps between service passes")
     ap.add_argument("--smem-wait", type=int, default=0, help="SMEM kernel lanes out of the loop that call a pass")
     ap.add_argument("--reads", type=int, default=0,

@@ -63,11 +63,12 @@ enum {
                               by comparing text */
 #define MB_STEP_ONLY 0x40u /* seeding: extend every match step by step (Algorithm 1), even where
                               the auxiliary arrays allow comparing text */
-#define MB_LOCATE_JOIN 0x100u /* locate: a walk stops where it meets the row of another hit of the
-                              call and takes that hit's position plus its distance, chains of such
-                              walks resolved from their heads (same positions, about 6x fewer LF
-                              steps; about 20 bytes per 64 text positions of device workspace); by
-                              default every LF-walk runs to its sampled row */
+#define MB_LOCATE_JOIN 0x100u /* locate: the walked rows go in 8 passes (by a hash of the row); a walk
+                              stops where it meets a walked row of an earlier pass and takes that
+                              row's position plus its distance (same positions, fewer LF steps; 36
+                              bytes per 64 index rows plus 4 bytes per walked row of device
+                              workspace).  Off under MB_CHECKED.  By default every LF-walk runs to
+                              its sampled row */
 #define MB_SMEM_ONE_LOOP 0x80u /* tuning: the SMEM kernel in its one-loop form (every iteration runs
                               every stage's code) instead of the split form (uniform block steps,
                               the other actions in service passes); same output */
@@ -273,8 +274,9 @@ int mb_seed_locate(const mb_index *idx, const uint8_t *seq, const uint64_t *off,
  * mb_autotune times mb_plan_run on the given batch over the launch shapes in two stages and
  * writes the fastest into *best (same output for all): first the SMEM kernel's shape, threads per
  * block 128/256/512 x work queue off/on x kernel form (the one-loop form MB_SMEM_ONE_LOOP, or the
- * split form with smem_burst 2/4/8/16 x smem_wait 4/8/16), with 16 locate walks per lane; then
- * locate walks per lane 1/2/4/8 with the best SMEM shape (82 points).  mb_autotune_points does
+ * split form with smem_burst 2/4/8/16 x smem_wait 4/8/16), with 16 plain locate walks per lane;
+ * then, with the best SMEM shape, locate walks per lane 1/2/4/8 plain and 1/2/4/8/16 with walks
+ * that join (MB_LOCATE_JOIN) (87 points).  mb_autotune_points does
  * the same and also returns every point tried with its time in ms (up to cap points; *n_points
  * receives the number tried).
  */
@@ -447,9 +449,10 @@ const char *mb_last_error(void);
  * lookups, LF steps of Algorithm 2 and sampled-SA reads.
  * mb_work_counters_all: the same five followed by the work of extending unique matches by text
  * comparison (LF steps of its walks, SA / ISA sample reads, text loads of 8 bytes), then of the
- * locate walks that join (mark-word reads, walks that stopped at another walked row, the longest
- * chain of such walks: a maximum, not a sum), `count` values at most (11 exist).  The LF steps and sampled-S reads are those of the walks run: exactly
- * Algorithm 2's over the distinct rows, or fewer with MB_LOCATE_JOIN.
+ * locate walks that join (walks that stopped at a walked row of an earlier pass, each reading that
+ * row's rank and position; calls whose walked rows were not sorted and distinct, so that no walk
+ * joined), `count` values at most (10 exist).  The LF steps and sampled-S reads are those of the
+ * walks run: exactly Algorithm 2's over the distinct rows, or fewer with MB_LOCATE_JOIN.
  */
 void mb_profile_enable(int on);
 int mb_profile_get(const char *kernel, double *ms, uint64_t *launches);

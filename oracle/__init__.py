@@ -83,7 +83,7 @@ def lib():
                 "orc_locate_slow": ([P, P, U64, P, I], None),
                 "orc_batch_locate": ([P, P, U64, P], None),
                 "orc_count_alg3": ([P, P, P, U32, U32, U32, U64, U32, P], None),
-                "orc_count_locate_join": ([P, P, U64, P, I], None),
+                "orc_count_locate_join": ([P, P, U64, U32, P, I], None),
                 "orc_count_locate": ([P, P, U64, P, I], None),
             }
             for name, (args, res) in sig.items():
@@ -242,13 +242,13 @@ class Index:
             lib().orc_count_locate(self._h, _p(rows), len(rows), _p(out), threads)
         return int(out[0]), int(out[1])
 
-    def count_locate_join(self, rows, threads: int = 0) -> tuple:
-        """Work of locate with walks that join over the distinct rows: (LF steps, sampled-S reads,
-        walks stopped at another of the rows, mark-word reads)."""
+    def count_locate_join(self, rows, pass_bits: int = 3, threads: int = 0) -> tuple:
+        """Work of locate with walks that join over the distinct rows in 2**pass_bits passes:
+        (LF steps, sampled-S reads, walks stopped at a row of an earlier pass)."""
         rows = _u64(rows)
-        out = np.zeros(4, dtype=np.uint64)
+        out = np.zeros(3, dtype=np.uint64)
         if len(rows):
-            lib().orc_count_locate_join(self._h, _p(rows), len(rows), _p(out), threads)
+            lib().orc_count_locate_join(self._h, _p(rows), len(rows), pass_bits, _p(out), threads)
         return tuple(int(v) for v in out)
 
     def seed(self, seq, off, min_len: int = 19, min_occ: int = 1, max_occ: int = 500,

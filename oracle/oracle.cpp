@@ -604,26 +604,28 @@ void orc_count_locate(void *x, const u64 *rows, u64 m, u64 *out, int threads) {
     out[1] = sa;
 }
 
-/* Work of locate with walks that join, over the sorted distinct rows R: from each row, LF steps
- * until a sampled row or the $ row (an S read for a sampled row), or, after at least one step, a
- * row of R (the walk takes that row's position plus its distance).  out: LF steps, S reads, walks
- * that stopped at a row of R, and mark-word reads (one per check of a row past the first). */
-void orc_count_locate_join(void *x, const u64 *rows, u64 m, u64 *out, int threads) {
+/* Work of locate with walks that join, over the sorted distinct rows R, in 2^bits passes: row y
+ * belongs to pass (y * 2654435761 mod 2^32) >> (32 - bits) (Knuth's multiplicative hash).  From
+ * each row, LF steps until a sampled row or the $ row (an S read for a sampled row), or, after at
+ * least one step, a row of R of an earlier pass than the walk's own (the walk takes that row's
+ * position plus its distance).  out: LF steps, S reads, walks that stopped at a row of R. */
+void orc_count_locate_join(void *x, const u64 *rows, u64 m, u32 bits, u64 *out, int threads) {
     const Index &X = *(Index *)x;
     std::vector<u64> R(rows, rows + m);
     std::sort(R.begin(), R.end());
-    u64 steps = 0, sa = 0, links = 0, marks = 0;
+    auto pass = [bits](u64 y) -> u32 {
+        return bits == 0 ? 0u : (u32)(((u32)y * 2654435761u) >> (32 - bits));
+    };
+    u64 steps = 0, sa = 0, links = 0;
 #pragma omp parallel for num_threads(threads > 0 ? threads : omp_get_max_threads()) schedule(dynamic, 64) \
-    reduction(+ : steps, sa, links, marks)
+    reduction(+ : steps, sa, links)
     for (u64 q = 0; q < m; ++q) {
         u64 k = rows[q], t = 0;
+        const u32 own = pass(rows[q]);
         for (;;) {
             if (k % X.r == 0) { ++sa; break; }
             if (k == X.primary) break;
-            if (t > 0) {
-                ++marks;
-                if (std::binary_search(R.begin(), R.end(), k)) { ++links; break; }
-            }
+            if (t > 0 && pass(k) < own && std::binary_search(R.begin(), R.end(), k)) { ++links; break; }
             k = pi(X, X.B[k], k);
             ++t;
         }
@@ -632,7 +634,6 @@ void orc_count_locate_join(void *x, const u64 *rows, u64 m, u64 *out, int thread
     out[0] = steps;
     out[1] = sa;
     out[2] = links;
-    out[3] = marks;
 }
 
 }  // extern "C"

@@ -415,10 +415,10 @@ def launch_count() -> int:
 
 
 def work_counters() -> dict:
-    v = np.zeros(11, dtype=np.uint64)
-    lib().mb_work_counters_all(_ptr(v), 11)
+    v = np.zeros(10, dtype=np.uint64)
+    lib().mb_work_counters_all(_ptr(v), 10)
     return dict(zip(("ext_steps", "ext_blocks", "kmer_lookups", "lf_steps", "sa_reads", "u_walk_steps",
-                     "u_samples", "u_text_loads", "mark_reads", "joins", "longest_chain"), (int(x) for x in v)))
+                     "u_samples", "u_text_loads", "joins", "joins_off"), (int(x) for x in v)))
 
 
 # ---------------------------------------------------------------------------- batched form
@@ -505,7 +505,7 @@ def shape_of(o: Opts) -> dict:
             "smem_burst": (o.smem_burst or 8) if split else None,
             "smem_wait": (o.smem_wait or 16) if split else None,
             "smem_warps": (o.smem_warps or None) if split else None,
-            "locate_walks_per_lane": o.prefetch_depth or 1}
+            "locate_walks_per_lane": o.prefetch_depth or 1, "locate_join": bool(o.flags & MB_LOCATE_JOIN)}
 
 
 # ---------------------------------------------------------------------------- served form

@@ -92,9 +92,9 @@ struct KTimer {
 enum {
     WC_EXT_STEPS = 0, WC_EXT_BLOCKS = 1, WC_KMER = 2, WC_LF_STEPS = 3, WC_SA_READS = 4,
     WC_U_WALK = 5, WC_U_SAMPLE = 6, WC_U_TEXT = 7,   // U_*: extension of unique matches by text
-    WC_MARKS = 8, WC_LINKS = 9,                       // locate: mark-word loads, walks ended at another hit row
-    WC_CHAIN_MAX = 10,                                // locate: the longest chain of joined walks
-    WC_N = 11
+    WC_JOINS = 8,                                     // locate: walks that stopped at a row of an earlier pass
+    WC_JOIN_OFF = 9,                                  // locate: calls whose walked rows allowed no joins
+    WC_N = 10
 };
 u64 *mb_work_counter_buf(cudaStream_t st);   // device array of WC_N u64 (zeroed on first use)
 

@@ -44,7 +44,7 @@ __device__ __forceinline__ u64 slot_base(const u64 *off, u64 r) { return slots_b
 // Work counters of the measurement mode (MB_COUNT); compiled out otherwise.
 template <bool ON>
 struct Work {
-    u64 steps = 0, blocks = 0, kmer = 0, lf = 0, sa = 0, uwalk = 0, usample = 0, utext = 0, marks = 0, links = 0;
+    u64 steps = 0, blocks = 0, kmer = 0, lf = 0, sa = 0, uwalk = 0, usample = 0, utext = 0, joins = 0;
     __device__ __forceinline__ void ext(u64 p, u64 s) {
         if (ON) {
             ++steps;
@@ -61,8 +61,7 @@ struct Work {
             if (uwalk) atomicAdd((unsigned long long *)&wc[WC_U_WALK], (unsigned long long)uwalk);
             if (usample) atomicAdd((unsigned long long *)&wc[WC_U_SAMPLE], (unsigned long long)usample);
             if (utext) atomicAdd((unsigned long long *)&wc[WC_U_TEXT], (unsigned long long)utext);
-            if (marks) atomicAdd((unsigned long long *)&wc[WC_MARKS], (unsigned long long)marks);
-            if (links) atomicAdd((unsigned long long *)&wc[WC_LINKS], (unsigned long long)links);
+            if (joins) atomicAdd((unsigned long long *)&wc[WC_JOINS], (unsigned long long)joins);
         }
     }
 };
@@ -1205,30 +1204,61 @@ __global__ void __launch_bounds__(256, D == 8 ? 2 : 1) k_locate(DevIndex I, cons
 // Reads that cover the same place give hits a few text positions apart (SMEMs of one read overlap):
 // on the workloads here about 78% of the distinct hit positions have another hit within 8
 // positions to their left.  An LF-walk (Algorithm 2) from the row of position p visits the rows of
-// p - 1, p - 2, ... in turn, so when it reaches the row of another hit q after d = p - q steps,
-// S(row of p) = S(row of q) + d: the walk can stop there.  Each walked row is marked in a bitmap
-// with per-word ranks (mark words of 64 rows: the bits and the number of marked rows before the
-// word), so a walk recognises a marked row from the word of its current row and finds that row's
-// place in the sorted row list by its rank.  A walk stops at the first sampled row, the $ row or
-// marked row it reaches, in that order of checks; a walk that stops at a marked row records the
-// distance and becomes that row's successor.  Every row has at most one successor (a walk meeting
-// the row of q passes the rows of every position between, so only the nearest hit to q's right
-// can stop at q), links point strictly to smaller positions, and a chain ends at a walk that
-// reached a sampled or $ row; one thread per chain head then adds the distances along its chain.
-// The positions are exactly those of the plain walks.  This needs the walked rows sorted and
-// distinct (true for the records of one seeding call, whose intervals are nested or disjoint);
-// otherwise a device flag turns the marks off and every walk runs to its sampled row.
-constexpr u32 LINKED = 0xFFFFFFFEu;   // rpos of a walk that stopped at another walked row
+// p - 1, p - 2, ... in turn, so when it reaches the row of another hit q whose position is already
+// known, after d = p - q steps, S(row of p) = S(row of q) + d and the walk can stop.
+//
+// The walked rows go in JOIN_PASSES passes by a hash of the row; a walk of pass k may stop at a
+// walked row of an earlier pass (its position is final by then), so no walk waits on another.
+// Membership must cost no extra random read per step, so each call makes its own copy of the
+// occurrence blocks ("walk blocks", 32 bytes per 64 rows like the blocks): the counts of A, C and
+// G as 21-bit offsets from coarse counts kept per 2^21 rows (T follows from the row count), the
+// two bit planes, and 64 mark bits of the walked rows.  The coarse counts (at most 2,049 of them,
+// 16 bytes each) sit in shared memory.  The rank of a marked row (its place in the sorted row
+// list, where its position is written) is the block's count of marked rows before it plus a
+// popcount.  The positions are exactly those of the plain walks.  This needs the walked rows
+// sorted and distinct (true for the records of one seeding call, whose intervals are nested or
+// disjoint); otherwise a device flag turns the joins off and every walk runs to its sampled row.
+constexpr int JOIN_PASSES = 8, JOIN_PASS_BITS = 3;
+constexpr u32 COARSE_SHIFT = 21;        // coarse counts per 2^21 rows
+constexpr u32 FINE_BITS = 21, FINE_MASK = (1u << FINE_BITS) - 1;
+constexpr u64 JOIN_TILE = 4096;         // rows per warp tile of the pass partition
 
-__device__ __forceinline__ uint2 load_mark_bits(const uint4 *__restrict__ marks, u32 w) {
-    uint2 v;
-    asm("ld.global.nc.v2.u32 {%0,%1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(marks + w));
-    return v;
+struct __align__(32) WalkBlk {
+    u64 fc;          // counts of A, C, G before the block minus the coarse counts, 21 bits each
+    u64 lo, hi;      // the bit planes, as in the occurrence block
+    u64 marks;       // bit q: row q of the block is a walked row
+};
+__device__ __forceinline__ u32 join_pass(u32 row) { return (row * 0x9E3779B1u) >> (32 - JOIN_PASS_BITS); }
+__device__ __forceinline__ void load_walk_blk(const WalkBlk *__restrict__ w, u64 &fc, u64 &lo, u64 &hi, u64 &mk) {
+    asm("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];" : "=l"(fc), "=l"(lo), "=l"(hi), "=l"(mk) : "l"(w));
 }
 
-// Bits of the walked rows (warp-aggregated atomics over the sorted rows) and the not-sorted flag.
+// Coarse counts (C[a] plus the block counts at every 2^15-th block) and the walk blocks with no
+// marks.
+__global__ void k_walk_blocks(DevIndex I, u64 nb, uint4 *__restrict__ coarse, WalkBlk *__restrict__ wb) {
+    constexpr u32 GB = COARSE_SHIFT - BLK_SHIFT;
+    for (u64 b = blockIdx.x * (u64)blockDim.x + threadIdx.x; b < nb; b += (u64)gridDim.x * blockDim.x) {
+        const OccBlock o = I.occ[b];
+        const u64 cb = (b >> GB) << GB;
+        const OccBlock c = I.occ[cb];
+        if (b == cb)
+            coarse[b >> GB] = make_uint4((u32)I.C[0] + o.cnt[0], (u32)I.C[1] + o.cnt[1], (u32)I.C[2] + o.cnt[2],
+                                         (u32)I.C[3] + o.cnt[3]);
+        WalkBlk w;
+        w.fc = (u64)(o.cnt[0] - c.cnt[0]) | ((u64)(o.cnt[1] - c.cnt[1]) << FINE_BITS) |
+               ((u64)(o.cnt[2] - c.cnt[2]) << (2 * FINE_BITS));
+        w.lo = o.lo;
+        w.hi = o.hi;
+        w.marks = 0;
+        wb[b] = w;
+    }
+}
+
+// Mark bits of the walked rows (warp-aggregated atomics over the sorted rows), the not-sorted
+// flag, and for every block holding walked rows the number of walked rows before it (written by
+// the block's first row; only marked blocks are ever read).
 __global__ void k_join_mark(const u32 *__restrict__ rows, const u64 *__restrict__ nrows_dev, u64 cap,
-                            uint4 *__restrict__ marks, u32 *__restrict__ nojoin) {
+                            WalkBlk *__restrict__ wb, u32 *__restrict__ before, u32 *__restrict__ nojoin) {
     const u64 nr = count_of(cap, nrows_dev);
     const u32 lane = threadIdx.x & 31;
     for (u64 base = (blockIdx.x * (u64)blockDim.x + threadIdx.x) & ~31ull; base < nr;
@@ -1238,93 +1268,118 @@ __global__ void k_join_mark(const u32 *__restrict__ rows, const u64 *__restrict_
         const u32 y = on ? rows[i] : 0u;
         if (on && i + 1 < nr && rows[i + 1] <= y) atomicOr(nojoin, 1u);
         const u32 w = y >> BLK_SHIFT;
+        if (on && (i == 0 || (rows[i - 1] >> BLK_SHIFT) != w)) before[w] = (u32)i;
         const u32 act = __ballot_sync(0xffffffffu, on);
         if (!on) continue;
         const u32 grp = __match_any_sync(act, w);
         const u64 bit = 1ull << (y & BLK_MASK);
         const u32 lo = __reduce_or_sync(grp, (u32)bit), hi = __reduce_or_sync(grp, (u32)(bit >> 32));
-        if (lane == (u32)(__ffs(grp) - 1)) {
-            if (lo) atomicOr(&marks[w].x, lo);
-            if (hi) atomicOr(&marks[w].y, hi);
-        }
+        if (lane == (u32)(__ffs(grp) - 1))
+            atomicOr((unsigned long long *)&wb[w].marks, ((unsigned long long)hi << 32) | lo);
     }
 }
-__global__ void k_join_popc(const uint4 *__restrict__ marks, u64 nw, u32 *__restrict__ cnt) {
-    for (u64 w = blockIdx.x * (u64)blockDim.x + threadIdx.x; w < nw; w += (u64)gridDim.x * blockDim.x)
-        cnt[w] = __popc(marks[w].x) + __popc(marks[w].y);
-}
-__global__ void k_join_before(uint4 *__restrict__ marks, u64 nw, const u32 *__restrict__ cnt) {
-    for (u64 w = blockIdx.x * (u64)blockDim.x + threadIdx.x; w < nw; w += (u64)gridDim.x * blockDim.x)
-        marks[w].z = cnt[w];
+
+// Counting mode: the calls whose walked rows were not sorted and distinct (no joins).
+__global__ void k_join_flag_count(const u32 *__restrict__ nojoin, u64 *wc) {
+    if (threadIdx.x == 0 && *nojoin) atomicAdd((unsigned long long *)&wc[WC_JOIN_OFF], 1ull);
 }
 
-// Algorithm 2 over the sorted rows with joins: k_locate's walk loop (D walks per lane, one warp-wide
-// hand-out per iteration) plus, for a walk past its first row, the mark word of its current row,
-// loaded with the block.  A marked row ends the walk at the next iteration: its rank replaces the
-// row, and the hand-out writes LINKED, the distance, and the successor entry.
+// Stable partition of the sorted rows by pass: per warp tile of JOIN_TILE rows, the count of each
+// pass (tcnt[p * ntiles + tile]); after an exclusive scan of those counts (pass-major), the row
+// numbers of each pass in order (idx) and the pass boundaries (range[p], range[JOIN_PASSES]).
+template <bool SCATTER>
+__global__ void k_pass_split(const u32 *__restrict__ rows, const u64 *__restrict__ nrows_dev, u64 cap, u64 ntiles,
+                             u32 *__restrict__ tcnt, u32 *__restrict__ idx, u64 *__restrict__ range) {
+    const u64 nr = count_of(cap, nrows_dev);
+    const u32 lane = threadIdx.x & 31;
+    const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
+    for (u64 t = (blockIdx.x * (u64)blockDim.x + threadIdx.x) >> 5; t < ntiles; t += nwarps) {
+        u32 run[JOIN_PASSES];
+#pragma unroll
+        for (int p = 0; p < JOIN_PASSES; ++p) run[p] = SCATTER ? tcnt[(u64)p * ntiles + t] : 0u;
+        const u64 e = (t + 1) * JOIN_TILE < nr ? (t + 1) * JOIN_TILE : nr;
+        for (u64 c = t * JOIN_TILE; c < e; c += 32) {
+            const u64 i = c + lane;
+            const u32 ps = i < e ? join_pass(rows[i]) : JOIN_PASSES;
+#pragma unroll
+            for (int p = 0; p < JOIN_PASSES; ++p) {
+                const u32 m = __ballot_sync(0xffffffffu, ps == (u32)p);
+                if (SCATTER && ps == (u32)p) idx[run[p] + __popc(m & ((1u << lane) - 1u))] = (u32)i;
+                run[p] += __popc(m);
+            }
+        }
+        if (!SCATTER && lane == 0)
+            for (int p = 0; p < JOIN_PASSES; ++p) tcnt[(u64)p * ntiles + t] = run[p];
+    }
+    if (SCATTER && blockIdx.x == 0 && threadIdx.x <= JOIN_PASSES)
+        range[threadIdx.x] = threadIdx.x < JOIN_PASSES ? (ntiles ? tcnt[(u64)threadIdx.x * ntiles] : 0) : nr;
+}
+
+// Algorithm 2 over the rows of one pass: k_locate's walk loop (D walks per lane, one warp-wide
+// hand-out per iteration) on the walk blocks.  A walk past its first row that stands on a marked
+// row of an earlier pass stops: the next iteration reads the block's count of marked rows before
+// it (the rank), the one after reads that row's position.  The hand-out takes the rows of the
+// pass through idx and keeps each walk's row number (where its position goes) in h[].
 template <bool COUNT, bool POW2, int D>
 __global__ void __launch_bounds__(256, D <= 8 ? 2 : 1)
-    k_locate_join(DevIndex I, const u32 *__restrict__ rows, u64 nhits, const u64 *__restrict__ nhits_dev,
-                  u32 *__restrict__ hits, const uint4 *__restrict__ marks, const u32 *__restrict__ nojoin,
-                  u32 *__restrict__ succ, u64 *wc, u32 *chk) {
+    k_locate_pass(DevIndex I, const u32 *__restrict__ rows, const u32 *__restrict__ idx, const u64 *__restrict__ range,
+                  u32 pass, const WalkBlk *__restrict__ wb, const uint4 *__restrict__ coarse, u32 ncoarse,
+                  const u32 *__restrict__ before, const u32 *__restrict__ nojoin, u32 *__restrict__ rpos, u64 *wc) {
+    extern __shared__ uint4 cs[];   // the coarse counts
+    for (u32 g = threadIdx.x; g < ncoarse; g += blockDim.x) cs[g] = coarse[g];
+    __syncthreads();
     const u32 lane = threadIdx.x & 31;
-    if (nhits_dev && *nhits_dev < nhits) nhits = *nhits_dev;
-    const bool join = *nojoin == 0;
+    const u64 lo_r = range[pass], hi_r = range[pass + 1];
+    const u64 nitems = hi_r > lo_r ? hi_r - lo_r : 0;
+    const bool join = *nojoin == 0 && pass > 0;
     Work<COUNT> work;
     const u32 r = I.r, rmask = I.r - 1, rshift = __ffs(I.r) - 1, prim = (u32)I.primary, n = (u32)I.n;
-    const u32 C0 = (u32)I.C[0], C1 = (u32)I.C[1], C2 = (u32)I.C[2], C3 = (u32)I.C[3];
     WarpRange wr;
-    wr.init(nhits);
-    const u64 wbase = wr.next;
+    wr.init(nitems);
+    const u32 *__restrict__ widx = idx + lo_r + wr.next;
     const u32 wlen = (u32)(wr.end - wr.next);
-    const u32 *__restrict__ wrows = rows + wbase;
-    u32 *__restrict__ whits = hits + wbase;
     u32 h[D], row[D], steps[D];
-    u32 live = 0, lnk = 0;   // bit d: slot d holds a walk; the walk of slot d met a marked row
+    u32 live = 0, rk1 = 0, rk2 = 0;   // walks: present; met a marked row (row[] = block | pc << 26); rank known
     u32 next = 0;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
         const u32 o = next + lane;
-        h[d] = o;
         steps[d] = 0;
         row[d] = 0;
+        h[d] = 0;
         if (o < wlen) {
             live |= 1u << d;
-            row[d] = __ldg(&wrows[o]);
+            h[d] = __ldg(&widx[o]);
+            row[d] = __ldg(&rows[h[d]]);
         }
         next += 32;
     }
     for (;;) {
         if (__all_sync(0xffffffffu, live == 0)) break;
-        if (next + 128 + lane < wlen) asm volatile("prefetch.global.L1 [%0];" ::"l"(wrows + next + 128 + lane));
-        u32 stop = 0, smp = 0, skp = 0, ld = 0;
+        u32 stop = 0, smp = 0, ld = 0;
         u32 sv[D];
-        Blk b[D];
-        uint2 mk[D];
+        u64 fc[D], bl[D], bh[D], mk[D];
 #pragma unroll
         for (int d = 0; d < D; ++d) {
             const bool on = (live >> d) & 1u;
-            const bool linked = (lnk >> d) & 1u;
-            const bool skip = !linked && row[d] == NOPOS;
-            const bool bad = chk && on && !linked && !skip && row[d] >= n;
-            if (bad) atomicOr(chk, (u32)DEVCHK_BOUNDS);
-            const bool sampled = !linked && !skip && !bad && (POW2 ? (row[d] & rmask) == 0 : row[d] % r == 0);
-            const bool st = on && (linked || skip || bad || sampled || row[d] == prim || steps[d] > n);
+            const bool r1 = (rk1 >> d) & 1u, r2 = (rk2 >> d) & 1u;
+            const bool sampled = !r1 && !r2 && (POW2 ? (row[d] & rmask) == 0 : row[d] % r == 0);
+            const bool st = on && (r2 || sampled || (!r1 && row[d] == prim) || steps[d] > n);
             sv[d] = 0;
-            mk[d] = make_uint2(0u, 0u);
             if (st) {
                 stop |= 1u << d;
-                if (skip) skp |= 1u << d;
-                if (sampled) {
+                if (r2) {
+                    sv[d] = __ldg(&rpos[row[d]]);   // the joined row's position, final since its pass
+                    smp |= 1u << d;
+                } else if (sampled) {
                     smp |= 1u << d;
                     sv[d] = __ldg(&I.ssa[POW2 ? (row[d] >> rshift) : row[d] / r]);
                 }
+            } else if (on && r1) {
+                sv[d] = __ldg(&before[row[d] & 0x3FFFFFFu]);
             } else if (on) {
-                b[d] = load_blk(I.occ + (row[d] >> BLK_SHIFT));
-                if (join && steps[d] > 0) {
-                    mk[d] = load_mark_bits(marks, row[d] >> BLK_SHIFT);
-                    ld |= 1u << d;
-                }
+                load_walk_blk(wb + (row[d] >> BLK_SHIFT), fc[d], bl[d], bh[d], mk[d]);
+                ld |= 1u << d;
             }
         }
         const u32 cnt = __popc(stop);
@@ -1339,61 +1394,47 @@ __global__ void __launch_bounds__(256, D <= 8 ? 2 : 1)
 #pragma unroll
         for (int d = 0; d < D; ++d) {
             if ((stop >> d) & 1u) {
-                if ((lnk >> d) & 1u) {   // row[d] holds the rank of the marked row met
-                    whits[h[d]] = LINKED;
-                    reinterpret_cast<uint2 *>(succ)[row[d]] = make_uint2((u32)(wbase + h[d]), steps[d]);
-                    work.links += 1;
-                } else if (!((skp >> d) & 1u)) {
-                    whits[h[d]] = (steps[d] > n || row[d] >= n) ? 0xFFFFFFFFu
-                                                                : (((smp >> d) & 1u) ? sv[d] + steps[d] : steps[d]);
-                }
+                rpos[h[d]] = steps[d] > n ? 0xFFFFFFFFu : (((smp >> d) & 1u) ? sv[d] + steps[d] : steps[d]);
                 work.lf += steps[d];
-                work.sa += (smp >> d) & 1u;
-                lnk &= ~(1u << d);
-                h[d] = give;
+                work.sa += ((smp >> d) & 1u) && !((rk2 >> d) & 1u);
+                work.joins += (rk2 >> d) & 1u;
+                rk1 &= ~(1u << d);
+                rk2 &= ~(1u << d);
                 steps[d] = 0;
-                if (give < wlen) row[d] = __ldg(&wrows[give]);
-                else live &= ~(1u << d);
-                ++give;
-            } else if ((live >> d) & 1u) {
-                const u32 m = row[d] & BLK_MASK;
-                const u64 bits = ((u64)mk[d].y << 32) | mk[d].x;
-                if ((ld >> d) & 1u) work.marks += 1;
-                if ((bits >> m) & 1ull) {   // a walked row: its rank in the sorted rows
-                    row[d] = __ldg(&marks[row[d] >> BLK_SHIFT].z) + (u32)__popcll(bits & rows_before(m));
-                    lnk |= 1u << d;
+                if (give < wlen) {
+                    h[d] = __ldg(&widx[give]);
+                    row[d] = __ldg(&rows[h[d]]);
                 } else {
-                    row[d] = lf_blk(b[d], row[d], prim, C0, C1, C2, C3);
+                    live &= ~(1u << d);
+                }
+                ++give;
+            } else if ((rk1 >> d) & 1u) {   // the rank: marked rows before the block, then in it
+                row[d] = sv[d] + (row[d] >> 26);
+                rk1 &= ~(1u << d);
+                rk2 |= 1u << d;
+            } else if ((ld >> d) & 1u) {
+                const u32 x = row[d], m = x & BLK_MASK;
+                if (join && steps[d] > 0 && ((mk[d] >> m) & 1ull) && join_pass(x) < pass) {
+                    row[d] = (x >> BLK_SHIFT) | ((u32)__popcll(mk[d] & rows_before(m)) << 26);
+                    rk1 |= 1u << d;
+                } else {
+                    const u32 a = (u32)((bl[d] >> m) & 1) | ((u32)((bh[d] >> m) & 1) << 1);
+                    const u64 eq = (bl[d] ^ ((u64)(a & 1) - 1)) & (bh[d] ^ ((u64)(a >> 1) - 1));
+                    u32 c = (u32)__popcll(eq & rows_before(m));
+                    if (a == 0) c -= dollar_before(x, prim);
+                    const u32 fa = (u32)fc[d] & FINE_MASK, fcc = (u32)(fc[d] >> FINE_BITS) & FINE_MASK,
+                              fg = (u32)(fc[d] >> (2 * FINE_BITS)) & FINE_MASK;
+                    // T: the rows of the group before the block, less A, C, G and the $ row
+                    const u32 gs = x & ~((1u << COARSE_SHIFT) - 1), bs = x & ~BLK_MASK;
+                    const u32 ft = (bs - gs) - fa - fcc - fg - (prim >= gs && prim < bs ? 1u : 0u);
+                    const uint4 g = cs[x >> COARSE_SHIFT];
+                    row[d] = sel4(a, g.x + fa, g.y + fcc, g.z + fg, g.w + ft) + c;
                     ++steps[d];
                 }
             }
         }
     }
     work.flush(wc);
-}
-
-// Positions of the linked walks: one thread per chain head (a walk that reached a sampled or $
-// row) adds the distances along its successors; link[j] = {the walk that stopped at row j, its
-// distance}, one load per link.
-__global__ void k_join_resolve(u32 *__restrict__ rpos, const uint2 *__restrict__ link,
-                               const u64 *__restrict__ nrows_dev, u64 cap, u64 *wc) {
-    const u64 nr = count_of(cap, nrows_dev);
-    u64 longest = 0;
-    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < nr; i += (u64)gridDim.x * blockDim.x) {
-        u32 p = rpos[i];
-        if (p >= LINKED) continue;
-        u32 cur = (u32)i;
-        u64 len = 0;
-        for (; len < nr; ++len) {   // a chain visits each row once
-            const uint2 l = link[cur];
-            if (l.x >= nr) break;
-            p += l.y;
-            rpos[l.x] = p;
-            cur = l.x;
-        }
-        longest = len > longest ? len : longest;
-    }
-    if (wc && longest) atomicMax((unsigned long long *)&wc[WC_CHAIN_MAX], (unsigned long long)longest);
 }
 
 __global__ void k_bs_filter(const mb_smem *__restrict__ sm, u64 nsm, const u8 *__restrict__ mate,
@@ -1513,58 +1554,62 @@ struct ShareBufs {
     void *tmp = nullptr;
     u32 *err = nullptr;   // the device error word (records with rows outside the text; MB_CHECKED bounds)
     bool checked = false; // MB_CHECKED: the locate kernel checks every row it walks
-    // walks that join (k_locate_join): mark words of the walked rows, their popcounts, the
-    // not-sorted flag, per walked row its successor and its distance
+    // walks that join (k_locate_pass, MB_LOCATE_JOIN): the walk blocks and coarse counts, per
+    // block the walked rows before it, the not-sorted flag, and the partition of the rows by pass
+    // (per-tile pass counts, the row numbers by pass, the pass boundaries)
     bool join = true;
-    uint4 *marks = nullptr;
-    u32 *mcnt = nullptr, *nojoin = nullptr;
-    u32 *succ = nullptr;   // uint2 per walked row: the walk that stopped at it and that walk's distance
+    WalkBlk *wb = nullptr;
+    uint4 *coarse = nullptr;
+    u32 *before = nullptr, *nojoin = nullptr, *tcnt = nullptr, *idx = nullptr;
+    u64 *range = nullptr;
 };
-// mark words of an index of n rows
+// sizes of carved workspace arrays are rounded up to 256 bytes
+inline size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+// walk blocks of an index of n rows (one per occurrence block), coarse counts, partition tiles
 inline u64 join_words(u64 n) { return n / BLK_ROWS + 1; }
+inline u64 join_coarse(u64 n) { return (join_words(n) >> (COARSE_SHIFT - BLK_SHIFT)) + 1; }
+inline u64 join_tiles(u64 rows_cap) { return (rows_cap + JOIN_TILE - 1) / JOIN_TILE; }
+// device bytes of the join arrays for an index of n rows and rows_cap walked rows
+inline size_t join_bytes(u64 n, u64 rows_cap) {
+    return align_up(join_words(n) * sizeof(WalkBlk)) + align_up(join_coarse(n) * 16) + align_up(join_words(n) * 4) +
+           align_up(8) + align_up(JOIN_PASSES * join_tiles(rows_cap) * 4 + 4) + align_up(rows_cap * 4) +
+           align_up((JOIN_PASSES + 1) * 8);
+}
 
 template <bool COUNT, bool POW2, int D>
-int launch_join_t(const DevIndex &I, const u32 *rows, u64 nhits, const u64 *nhits_dev, u32 *rpos, const uint4 *marks,
-                  const u32 *nojoin, u32 *succ, u64 *wc, u32 *chk, cudaStream_t st) {
+int launch_pass_t(const DevIndex &I, const u32 *rows, u64 nhits, u32 pass, u32 *rpos, const ShareBufs &b, u64 *wc,
+                  cudaStream_t st) {
     const unsigned g =
-        resident_grid((const void *)k_locate_join<COUNT, POW2, D>, 256, (nhits + 63) / 64 * 32);
+        resident_grid((const void *)k_locate_pass<COUNT, POW2, D>, 256, (nhits / JOIN_PASSES + 63) / 64 * 32 + 32);
     const u64 warps = (u64)g * 8;
     if ((nhits + warps - 1) / warps >= (1ull << 32) - 4096) {
         mb_set_error("locate: %llu hits over %llu warps", (unsigned long long)nhits, (unsigned long long)warps);
         return MB_ERR_ARG;
     }
-    k_locate_join<COUNT, POW2, D><<<g, 256, 0, st>>>(I, rows, nhits, nhits_dev, rpos, marks, nojoin, succ, wc, chk);
+    const u32 nc = (u32)join_coarse(I.n);
+    k_locate_pass<COUNT, POW2, D><<<g, 256, nc * sizeof(uint4), st>>>(I, rows, b.idx, b.range, pass, b.wb, b.coarse,
+                                                                      nc, b.before, b.nojoin, rpos, wc);
     MB_KCHECK();
     return MB_OK;
 }
-int launch_join(const DevIndex &I, const u32 *rows, u64 nhits, const u64 *nhits_dev, u32 *rpos, const ShareBufs &b,
-                u64 *wc, bool count, u32 depth, u32 *chk, cudaStream_t st) {
+int launch_pass(const DevIndex &I, const u32 *rows, u64 nhits, u32 pass, u32 *rpos, const ShareBufs &b, u64 *wc,
+                bool count, u32 depth, cudaStream_t st) {
     const bool pow2 = (I.r & (I.r - 1)) == 0;
-    if (count || !pow2)
-        return count ? (pow2 ? launch_join_t<true, true, 1>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin, b.succ, wc, chk, st)
-                             : launch_join_t<true, false, 1>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin,
-                                                              b.succ, wc, chk, st))
-                     : launch_join_t<false, false, 1>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin, b.succ,
-                                                       wc, chk, st);
-    if (depth >= 16)
-        return launch_join_t<false, true, 16>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin, b.succ, wc,
-                                              chk, st);
-    if (depth >= 8)
-        return launch_join_t<false, true, 8>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin, b.succ, wc,
-                                             chk, st);
-    if (depth >= 4)
-        return launch_join_t<false, true, 4>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin, b.succ, wc,
-                                             chk, st);
-    if (depth >= 2)
-        return launch_join_t<false, true, 2>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin, b.succ, wc,
-                                             chk, st);
-    return launch_join_t<false, true, 1>(I, rows, nhits, nhits_dev, rpos, b.marks, b.nojoin, b.succ, wc, chk,
-                                         st);
+    if (count) return pow2 ? launch_pass_t<true, true, 1>(I, rows, nhits, pass, rpos, b, wc, st)
+                           : launch_pass_t<true, false, 1>(I, rows, nhits, pass, rpos, b, wc, st);
+    if (!pow2) return launch_pass_t<false, false, 1>(I, rows, nhits, pass, rpos, b, wc, st);
+    if (depth >= 16) return launch_pass_t<false, true, 16>(I, rows, nhits, pass, rpos, b, wc, st);
+    if (depth >= 8) return launch_pass_t<false, true, 8>(I, rows, nhits, pass, rpos, b, wc, st);
+    if (depth >= 4) return launch_pass_t<false, true, 4>(I, rows, nhits, pass, rpos, b, wc, st);
+    if (depth >= 2) return launch_pass_t<false, true, 2>(I, rows, nhits, pass, rpos, b, wc, st);
+    return launch_pass_t<false, true, 1>(I, rows, nhits, pass, rpos, b, wc, st);
 }
 
-size_t share_tmp_bytes(u64 cap, u64 n) {
-    const size_t a = radix_tmp_bytes(cap), b = scan_tmp_bytes(cap), c = scan_tmp_bytes(join_words(n));
-    return a > b ? (a > c ? a : c) : (b > c ? b : c);
+size_t share_tmp_bytes(u64 cap, u64 rows_cap) {
+    size_t t = radix_tmp_bytes(cap);
+    const size_t z[2] = {scan_tmp_bytes(cap), scan_tmp_bytes(JOIN_PASSES * join_tiles(rows_cap) + 1)};
+    for (size_t v : z) t = v > t ? v : t;
+    return t;
 }
 // bytes of the per-record arrays (keys, keys_alt, roff: u64; vals, vals_alt, pmax, last: u32)
 constexpr size_t SHARE_BYTES_PER_RECORD = 3 * 8 + 4 * 4;
@@ -1595,25 +1640,26 @@ int locate_shared(const DevIndex &I, const mb_smem *sm, u64 cap, const u64 *nsm_
     k_share_rows<<<G, 256, 0, st>>>(b.keys, ss, b.last, b.roff, cap, b.nwalk, b.rows, hits_cap);
     MB_KCHECK();
     u32 *chk = b.checked ? b.err : nullptr;
-    if (b.join && b.marks) {
-        // marks of the walked rows and their ranks, then the walks with joins, then the chains
-        const u64 nw = join_words(I.n);
-        MB_CK(cudaMemsetAsync(b.marks, 0, nw * sizeof(uint4), st));
+    if (b.join && b.wb && !chk) {
+        // walk blocks with the marks of the walked rows and their ranks, the rows by pass, then
+        // one walk launch per pass (a pass joins only into rows of the passes before it)
+        const u64 nw = join_words(I.n), nt = join_tiles(hits_cap);   // blocks, partition tiles
         MB_CK(cudaMemsetAsync(b.nojoin, 0, 4, st));
-        MB_CK(cudaMemsetAsync(b.succ, 0xFF, hits_cap * 8, st));
+        k_walk_blocks<<<grid_for(nw, 256), 256, 0, st>>>(I, nw, b.coarse, b.wb);
+        MB_KCHECK();
         const unsigned GR = grid_for(hits_cap, 256);
-        k_join_mark<<<GR, 256, 0, st>>>(b.rows, b.nrows, hits_cap, b.marks, b.nojoin);
+        k_join_mark<<<GR, 256, 0, st>>>(b.rows, b.nrows, hits_cap, b.wb, b.before, b.nojoin);
         MB_KCHECK();
-        k_join_popc<<<grid_for(nw, 256), 256, 0, st>>>(b.marks, nw, b.mcnt);
+        const unsigned GT = grid_for(nt * 32, 256);
+        k_pass_split<false><<<GT, 256, 0, st>>>(b.rows, b.nrows, hits_cap, nt, b.tcnt, b.idx, b.range);
         MB_KCHECK();
-        MB_TRY(scan_exclusive_u32(b.mcnt, b.mcnt, nw, nullptr, b.tmp, st));
-        k_join_before<<<grid_for(nw, 256), 256, 0, st>>>(b.marks, nw, b.mcnt);
+        MB_TRY(scan_exclusive_u32(b.tcnt, b.tcnt, JOIN_PASSES * nt, nullptr, b.tmp, st));
+        k_pass_split<true><<<GT, 256, 0, st>>>(b.rows, b.nrows, hits_cap, nt, b.tcnt, b.idx, b.range);
         MB_KCHECK();
+        if (count) k_join_flag_count<<<1, 32, 0, st>>>(b.nojoin, wc);
         if (kt) kt->start();
-        MB_TRY(launch_join(I, b.rows, hits_cap, b.nrows, b.rpos, b, wc, count, depth, chk, st));
+        for (u32 p = 0; p < (u32)JOIN_PASSES; ++p) MB_TRY(launch_pass(I, b.rows, hits_cap, p, b.rpos, b, wc, count, depth, st));
         if (kt) kt->stop();
-        k_join_resolve<<<GR, 256, 0, st>>>(b.rpos, reinterpret_cast<const uint2 *>(b.succ), b.nrows, hits_cap, wc);
-        MB_KCHECK();
     } else {
         if (kt) kt->start();
         MB_TRY(launch_locate(I, b.rows, hits_cap, b.nrows, b.rpos, wc, count, depth, chk, st));
@@ -1778,8 +1824,8 @@ extern "C" int mb_seed_batch(const mb_index *idx, const uint8_t *seq, const uint
 // arrays of the walks that join unless `join` is false), carved from one stream-ordered allocation.
 static int share_alloc(DevBuf &bw, u64 n_smem, u64 total, u64 n, bool join, cudaStream_t st, ShareBufs &b) {
     const size_t rec_bytes = (size_t)n_smem * SHARE_BYTES_PER_RECORD, row_bytes = (size_t)total * 8;
-    const size_t nw = join ? join_words(n) : 0, join_bytes = join ? nw * 20 + (size_t)total * 8 + 4 * 256 : 0;
-    MB_TRY(bw.alloc(rec_bytes + row_bytes + 16 + share_tmp_bytes(n_smem, n) + join_bytes + 14 * 256, st));
+    const size_t tmp = share_tmp_bytes(n_smem, total), jb = join ? join_bytes(n, total) : 0;
+    MB_TRY(bw.alloc(rec_bytes + row_bytes + 16 + tmp + jb + 14 * 256, st));
     char *m = (char *)bw.p;
     auto take = [&](size_t bytes) { void *p = m; m += (bytes + 255) & ~(size_t)255; return p; };
     b.keys = (u64 *)take(n_smem * 8);
@@ -1794,13 +1840,16 @@ static int share_alloc(DevBuf &bw, u64 n_smem, u64 total, u64 n, bool join, cuda
     b.nrows = (u64 *)take(8);
     b.nwalk = (u64 *)take(8);
     b.err = (u32 *)take(8);
-    b.tmp = take(share_tmp_bytes(n_smem, n));
+    b.tmp = take(tmp);
     b.join = join;
-    if (join) {
-        b.marks = (uint4 *)take(nw * sizeof(uint4));
-        b.mcnt = (u32 *)take(nw * 4);
+    if (join) {   // the order and sizes of join_bytes
+        b.wb = (WalkBlk *)take(join_words(n) * sizeof(WalkBlk));
+        b.coarse = (uint4 *)take(join_coarse(n) * 16);
+        b.before = (u32 *)take(join_words(n) * 4);
         b.nojoin = (u32 *)take(8);
-        b.succ = (u32 *)take(total * 8);
+        b.tcnt = (u32 *)take(JOIN_PASSES * join_tiles(total) * 4 + 4);
+        b.idx = (u32 *)take(total * 4);
+        b.range = (u64 *)take((JOIN_PASSES + 1) * 8);
     }
     MB_CK(cudaMemsetAsync(b.err, 0, 8, st));
     return MB_OK;
@@ -1848,7 +1897,8 @@ extern "C" int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_sm
     const bool count = opts && (opts->flags & MB_COUNT);
     DevBuf bw;
     ShareBufs b;
-    MB_TRY(share_alloc(bw, n_smem, total, I.n, opts && (opts->flags & MB_LOCATE_JOIN), st, b));
+    MB_TRY(share_alloc(bw, n_smem, total, I.n, opts && (opts->flags & MB_LOCATE_JOIN) && !(opts->flags & MB_CHECKED),
+                       st, b));
     b.checked = opts && (opts->flags & MB_CHECKED);
     u64 *wc = count ? mb_work_counter_buf(st) : nullptr;
     KTimer kt("locate", st);
@@ -2059,7 +2109,6 @@ __global__ void k_len_keys(const u64 *__restrict__ off, u32 nr, u64 *__restrict_
         ids[r] = (u32)r;
     }
 }
-size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 }  // namespace
 
 struct mb_plan {
@@ -2105,27 +2154,29 @@ void mb_plan_arrays(const mb_plan *p, const mb_smem **smem, const u32 **hits, u6
 }
 
 // Device workspace of a plan, one entry per array (in the order mb_plan_create lays them out).
-constexpr int PLAN_ARRAYS = 27;
+constexpr int PLAN_ARRAYS = 30;
 // A plan locates with walks that join (their arrays sized by the index's n rows) when the options
-// say MB_LOCATE_JOIN and the plan holds hits to locate (not a seeding-only plan).
+// say MB_LOCATE_JOIN without MB_CHECKED and the plan holds hits to locate (not a seeding-only plan).
 static bool plan_joins(const mb_opts *opts, u64 max_hits) {
-    return opts && (opts->flags & MB_LOCATE_JOIN) && max_hits > 1;
+    return opts && (opts->flags & MB_LOCATE_JOIN) && !(opts->flags & MB_CHECKED) && max_hits > 1;
 }
 static void plan_sizes(const mb_opts *opts, u64 n, u32 max_reads, u64 max_bases, u64 max_smem, u64 max_hits,
                        size_t sizes[PLAN_ARRAYS]) {
     const bool queue = opts && (opts->flags & MB_BATCHED);
     const size_t nr = max_reads, ms = max_smem ? max_smem : 1, mh = max_hits ? max_hits : 1;
     size_t tb = scan_tmp_bytes(nr > ms ? nr : ms);
-    const size_t rb = radix_tmp_bytes(nr), sb = share_tmp_bytes(ms, n);
+    const size_t rb = radix_tmp_bytes(nr), sb = share_tmp_bytes(ms, mh);
     if (rb > tb) tb = rb;
     if (sb > tb) tb = sb;
     const bool join = plan_joins(opts, max_hits);
-    const size_t nw = join ? join_words(n) : 0;
+    const size_t nw = join ? join_words(n) : 0, nc = join ? join_coarse(n) : 0, nt = join ? join_tiles(mh) : 0;
     const size_t z[PLAN_ARRAYS] = {slots_total(max_bases, max_reads) * sizeof(SlotRec), nr * 8, nr * 8, 256, ms * 8,
                                    nr * 4, mh * 4, mh * 4, ms * sizeof(mb_smem), queue ? nr * 8 : 0,
                                    queue ? nr * 8 : 0, queue ? nr * 4 : 0, queue ? nr * 4 : 0, tb, ms * 4,
                                    ms * 8, ms * 8, ms * 8, ms * 4, ms * 4, ms * 4, ms * 4, mh * 4,
-                                   nw * sizeof(uint4), nw * 4, join ? 8u : 0u, join ? mh * 8 : 0};
+                                   nw * sizeof(WalkBlk), nc * 16, nw * 4, join ? 8u : 0u,
+                                   join ? JOIN_PASSES * nt * 4 + 4 : 0, join ? mh * 4 : 0,
+                                   join ? (JOIN_PASSES + 1) * 8 : 0};
     for (int i = 0; i < PLAN_ARRAYS; ++i) sizes[i] = z[i];
 }
 
@@ -2180,8 +2231,9 @@ extern "C" int mb_plan_create(const mb_index *idx, const mb_opts *opts, uint32_t
                                 (void **)&P->perm_alt, (void **)&P->tmp, (void **)&P->known, (void **)&P->share.keys,
                                 (void **)&P->share.keys_alt, (void **)&P->share.roff, (void **)&P->share.vals,
                                 (void **)&P->share.vals_alt, (void **)&P->share.pmax, (void **)&P->share.last,
-                                (void **)&P->share.rpos, (void **)&P->share.marks, (void **)&P->share.mcnt,
-                                (void **)&P->share.nojoin, (void **)&P->share.succ};
+                                (void **)&P->share.rpos, (void **)&P->share.wb, (void **)&P->share.coarse,
+                                (void **)&P->share.before, (void **)&P->share.nojoin, (void **)&P->share.tcnt,
+                                (void **)&P->share.idx, (void **)&P->share.range};
     for (int i = 0; i < PLAN_ARRAYS; ++i) {
         *ptrs[i] = sizes[i] ? (void *)m : nullptr;
         m += align_up(sizes[i]);
@@ -2412,7 +2464,7 @@ static int autotune_impl(const mb_index *idx, const uint8_t *seq, const uint64_t
         for (int bi = 0; bi < 3 && rc == MB_OK; ++bi)
             for (int f = -1; f < 12 && rc == MB_OK; ++f) {
                 mb_opts o = opts ? *opts : mb_opts{};
-                o.flags = (o.flags & ~(MB_BATCHED | MB_SMEM_ONE_LOOP)) | (q ? MB_BATCHED : 0u);
+                o.flags = (o.flags & ~(MB_BATCHED | MB_SMEM_ONE_LOOP | MB_LOCATE_JOIN)) | (q ? MB_BATCHED : 0u);
                 o.block_size = (u32)blocks[bi];
                 o.prefetch_depth = 16;
                 if (f < 0) {
@@ -2425,11 +2477,13 @@ static int autotune_impl(const mb_index *idx, const uint8_t *seq, const uint64_t
                 rc = time_point(o);
             }
     const mb_opts smem_best = bo;
-    for (u32 dep = 1; dep <= 8 && rc == MB_OK; dep *= 2) {
-        mb_opts o = smem_best;
-        o.prefetch_depth = dep;
-        rc = time_point(o);
-    }
+    for (int join = 0; join < 2; ++join)
+        for (u32 dep = 1; dep <= (join ? 16u : 8u) && rc == MB_OK; dep *= 2) {
+            mb_opts o = smem_best;
+            o.prefetch_depth = dep;
+            if (join) o.flags |= MB_LOCATE_JOIN;
+            rc = time_point(o);
+        }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (rc != MB_OK) return rc;

@@ -137,9 +137,9 @@ def test_autotune_picks_a_supported_shape(mb, mixed):
     best, ms, grid = mb.autotune(G, dev(rd.seq), dev(rd.off), points=True)
     assert best.block_size in (128, 256, 512)
     assert ms > 0
-    assert len(grid) == 82 and min(t for _, t in grid) == ms
+    assert len(grid) == 87 and min(t for _, t in grid) == ms
     shapes = {tuple(sorted(mb.shape_of(o).items())) for o, _ in grid}
-    assert len(shapes) == 82                     # every point a distinct launch shape
+    assert len(shapes) == 87                     # every point a distinct launch shape
     P = mb.Plan(G, rd.n, len(rd.seq), len(sm) + 1, len(hits) + 1, opts=best)
     P.run(dev(rd.seq), dev(rd.off))
     psm, phits = P.result()

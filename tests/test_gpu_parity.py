@@ -118,7 +118,7 @@ def test_locate_walks_per_lane(mb, depth, join):
     o = dict(prefetch_depth=depth, flags=mb.MB_LOCATE_JOIN if join else 0)
     hits, _ = mb.mb_locate(G, sm, m, opts=o, cap=nh)
     compare_seed(sm, hits, X, rd.seq, rd.off)
-    if join:   # the same through a plan (its own mark words and successor entries)
+    if join:   # the same through a plan (its own walk blocks and pass partition)
         P = mb.Plan(G, rd.n, len(rd.seq), m + 8, nh + 8, opts=o)
         P.run(torch.from_numpy(rd.seq).cuda(), torch.from_numpy(rd.off.view(np.int64)).cuda())
         psm, phits = P.result()
@@ -168,7 +168,7 @@ def test_locate_shared_rows_any_intervals(mb, seed):
     rows = np.concatenate([np.arange(int(k), int(k) + int(c), dtype=np.int64) for k, c in zip(sm["k"], cnt)])
     assert len(np.unique(rows)) < len(rows)
     for depth in (1, 16):
-        for flags in (0, mb.MB_LOCATE_JOIN):   # with joins the rows are not sorted: the walks run plain
+        for flags in (0, mb.MB_LOCATE_JOIN):
             hits, nh = mb.mb_locate(G, sm, len(sm), opts=dict(prefetch_depth=depth, flags=flags),
                                     cap=int(cnt.sum()))
             assert nh == len(rows)
@@ -217,11 +217,12 @@ def test_work_counters_match_oracle(mb):
                            for k, s in zip(sm["k"][keep], sm["s"][keep])])
     assert len(np.unique(rows)) < len(rows)   # the repeat-rich reads repeat rows
     assert (wc["lf_steps"], wc["sa_reads"]) == X.count_locate(np.unique(rows))
-    # walks that join (MB_LOCATE_JOIN): LF steps, S reads, joins and mark reads as the oracle counts
+    # walks that join in 8 passes (MB_LOCATE_JOIN): LF steps, S reads and joins as the oracle counts
     mb.profile_reset()
     mb.mb_locate(G, sm, m, opts=dict(flags=mb.MB_COUNT | mb.MB_LOCATE_JOIN), cap=nh)
     wc = mb.work_counters()
-    assert (wc["lf_steps"], wc["sa_reads"], wc["joins"], wc["mark_reads"]) == X.count_locate_join(np.unique(rows))
+    assert (wc["lf_steps"], wc["sa_reads"], wc["joins"]) == X.count_locate_join(np.unique(rows), pass_bits=3)
+    assert wc["joins"] > 0 and wc["joins_off"] == 0
     # with the index's 10-mer table (Section 2.5): the same steps, blocks and lookups as the
     # oracle's Algorithm 3 with the cache
     mb.profile_reset()

@@ -445,8 +445,9 @@ def test_alg3_kmer_cache_work_counts_exact_unique_read():
 def test_locate_join_work_counts_by_suffix_array():
     """Walks that join, from the suffix array alone: the walk from the row of text position p
     visits the rows of p-1, p-2, ...; it stops at the first position q <= p whose row is sampled
-    or is the $ row (q = 0), or, for q < p, whose row is another of the walked rows.  Its LF steps
-    are p - q; the oracle's counts (steps, S reads, joins, mark reads) must match this scan."""
+    or is the $ row (q = 0), or, for q < p, whose row is another of the walked rows and lies in
+    an earlier pass (pass of row y: the top bits of the 32-bit product y * 2654435761).  Its LF
+    steps are p - q; the oracle's counts (steps, S reads, joins) must match this scan."""
     ref, rd, p = synth.workload(2, scale=0.002)
     X = oracle.Index(ref)
     sm, over, hoff, hits = X.seed(rd.seq, rd.off)
@@ -458,26 +459,35 @@ def test_locate_join_work_counts_by_suffix_array():
     ISA[SA] = np.arange(n)
     walked = np.zeros(n, bool)
     walked[rows.astype(np.int64)] = True
-    steps = sa = links = marks = 0
-    for row in rows.astype(np.int64):
-        pos, t = int(SA[row]), 0
-        while True:
-            rr = ISA[pos - t]
-            if rr % 32 == 0:
-                sa += 1
-                break
-            if pos - t == 0:          # the row of position 0 is the $ row
-                break
-            if t > 0:
-                marks += 1
-                if walked[rr]:
+    plain = X.count_locate(rows)
+
+    def scan(bits):
+        def pass_of(y):
+            return ((int(y) * 2654435761) & 0xFFFFFFFF) >> (32 - bits) if bits else 0
+        steps = sa = links = 0
+        for row in rows.astype(np.int64):
+            pos, t, own = int(SA[row]), 0, pass_of(row)
+            while True:
+                rr = ISA[pos - t]
+                if rr % 32 == 0:
+                    sa += 1
+                    break
+                if pos - t == 0:          # the row of position 0 is the $ row
+                    break
+                if t > 0 and walked[rr] and pass_of(rr) < own:
                     links += 1
                     break
-            t += 1
-        steps += t
-    assert X.count_locate_join(rows) == (steps, sa, links, marks)
+                t += 1
+            steps += t
+        return steps, sa, links
+
+    for bits in (0, 1, 3):
+        got = X.count_locate_join(rows, pass_bits=bits)
+        assert got == scan(bits), bits
+    assert X.count_locate_join(rows, pass_bits=0) == plain + (0,)   # one pass: the plain walks
+    steps, sa, links = X.count_locate_join(rows, pass_bits=3)
     assert links > len(rows) // 4          # repeat-rich reads: many walks join
-    assert steps < X.count_locate(rows)[0] // 2
+    assert steps < plain[0] // 2
 
 
 def _bs_seed_and_split(ref, seq, off, mate):
