@@ -1000,8 +1000,9 @@ def main():
     ap.add_argument("--probe-gib", type=float, default=1, help="buffer of the random-gather probe (GiB)")
     ap.add_argument("--probe-sweep", action="store_true",
                     help="only the random-read probe over buffer sizes 1/32 .. 8 GiB (one JSON line each)")
-    ap.add_argument("--kmer-k", type=int, default=14, choices=range(1, 15),
-                    help="k of the k-mer ds-interval table (Section 2.5 uses 10; same SMEMs for any k)")
+    ap.add_argument("--kmer-k", type=int, default=14, choices=range(1, 17),
+                    help="k of the k-mer ds-interval table (Section 2.5 uses 10; same SMEMs for any k; "
+                         "12 * 4^k bytes, 51.5 GB at 16)")
     ap.add_argument("--autotune", action="store_true",
                     help="autotune the launch shape on 1M reads instead of --block / --locate-walks")
     ap.add_argument("--no-autotune", action="store_true", help="(default) fixed launch shape")

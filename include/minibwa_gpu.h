@@ -86,8 +86,9 @@ typedef struct {
     uint32_t min_occ;         /* c, minimum occurrence (default 1) */
     uint32_t max_occ;         /* SMEMs with s > max_occ are flagged and not located (default 500) */
     uint32_t sa_rate;         /* r, suffix array sample rate (default 32, Section 2.4) */
-    uint32_t kmer_k;          /* k of the k-mer ds-interval table (default 10, Section 2.5), <= 14;
-                                 the table takes 12 * 4^k bytes (3.2 GB at k = 14) */
+    uint32_t kmer_k;          /* k of the k-mer ds-interval table (default 10, Section 2.5), <= 16;
+                                 the table takes 12 * 4^k bytes (3.2 GB at k = 14, 51.5 GB at
+                                 k = 16) */
     uint32_t flags;           /* MB_* flags above */
     uint32_t chunk_reads;     /* mb_seed_locate: reads per pipelined chunk (0 = 2^22) */
     uint32_t prefetch_depth;  /* tuning: LF-walks in flight per lane in locate, 1/2/4/8/16 (0 = 1) */
@@ -150,6 +151,11 @@ int mb_index_export(const mb_index *idx, uint32_t *sa, uint8_t *bwt, uint32_t *s
  * row of the suffix at text position 4p).  No counterpart in the paper: they let seeding extend
  * a match that occurs once by comparing the read with the text (same SMEMs). */
 int mb_index_export_aux(const mb_index *idx, uint32_t *text2, uint32_t *sa_aux, uint32_t *isa_aux);
+/* Entries of the k-mer table (Section 2.5) for `n` k-mer codes (host array `codes`, each below
+ * 4^k, base t of the k-mer in bits 2t..2t+1): out (host, 3n u32) receives (k, kr, s) per code, the
+ * ds-interval of the k-mer.  Reads n x 12 bytes of the table instead of copying all of it (51.5 GB
+ * at k = 16).  MB_ERR_ARG for a null pointer or a code of 4^k or more (nothing written). */
+int mb_index_kmer_get(const mb_index *idx, const uint64_t *codes, uint64_t n, uint32_t *out);
 /* Free the full suffix array kept after the build (it is only needed for mb_index_export). */
 int mb_index_drop_sa(mb_index *idx);
 

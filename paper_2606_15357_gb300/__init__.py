@@ -72,6 +72,7 @@ def lib():
                 "mb_index_export": ([P, P, P, P, P, P, P], I),
                 "mb_index_drop_sa": ([P], I),
                 "mb_index_export_aux": ([P, P, P, P], I),
+                "mb_index_kmer_get": ([P, P, U64, P], I),
                 "mb_seed_batch": ([P, P, P, U32, P, OP, P, P, U64, PU64, PU64], I),
                 "mb_locate": ([P, P, U64, OP, P, P, U64, PU64], I),
                 "mb_seed_locate": ([P, P, P, U32, P, OP, P, P, U64, P, U64, PU64, PU64], I),
@@ -217,6 +218,13 @@ class Index:
         ix = np.empty((n + AUX_RATE - 1) // AUX_RATE, np.uint32)
         _check(lib().mb_index_export_aux(self._h, _ptr(t2), _ptr(sx), _ptr(ix)), "mb_index_export_aux")
         return t2, sx, ix
+
+    def kmer_get(self, codes) -> np.ndarray:
+        """(k, kr, s) of the k-mer table for each k-mer code, as an (n, 3) array (mb_index_kmer_get)."""
+        codes = np.ascontiguousarray(codes, dtype=np.uint64)
+        out = np.empty((len(codes), 3), np.uint32)
+        _check(lib().mb_index_kmer_get(self._h, _ptr(codes), len(codes), _ptr(out)), "mb_index_kmer_get")
+        return out
 
     def l2_persist(self, max_bytes: int, stream=None) -> int:
         """Access-policy window over the k-mer table on `stream` (mb_index_l2_persist); returns the

@@ -548,8 +548,8 @@ extern "C" int mb_index_build(const uint8_t *ref, uint64_t len, const mb_opts *o
     u32 flags = opts ? opts->flags : 0;
     u32 r = opts && opts->sa_rate ? opts->sa_rate : 32;
     u32 kk = opts && opts->kmer_k ? opts->kmer_k : 10;
-    if (kk > 14 || r == 0) {
-        mb_set_error("mb_index_build: kmer_k must be <= 14 and sa_rate > 0");
+    if (kk > 16 || r == 0) {
+        mb_set_error("mb_index_build: kmer_k must be <= 16 and sa_rate > 0");
         return MB_ERR_ARG;
     }
     int bs3 = (flags & MB_BS3) ? 1 : 0;
@@ -667,6 +667,39 @@ extern "C" int mb_index_drop_sa(mb_index *idx) {
 static int copy_out(void *dst, const void *src, size_t bytes) {
     if (!dst || bytes == 0) return MB_OK;
     MB_CK(cudaMemcpy(dst, src, bytes, cudaMemcpyDefault));
+    return MB_OK;
+}
+
+namespace {
+__global__ void k_kmer_get(const u32 *__restrict__ kmer, const u64 *__restrict__ codes, u64 n, u32 *__restrict__ out) {
+    for (u64 i = blockIdx.x * (u64)blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x) {
+        const u64 w = codes[i];
+        out[3 * i + 0] = kmer[3 * w + 0];
+        out[3 * i + 1] = kmer[3 * w + 1];
+        out[3 * i + 2] = kmer[3 * w + 2];
+    }
+}
+}  // namespace
+
+extern "C" int mb_index_kmer_get(const mb_index *idx, const uint64_t *codes, uint64_t n, uint32_t *out) {
+    if (!idx || !idx->kmer || (n && (!codes || !out))) {
+        mb_set_error("mb_index_kmer_get: null argument");
+        return MB_ERR_ARG;
+    }
+    const u64 nk = 1ULL << (2 * idx->kmer_k);
+    for (u64 i = 0; i < n; ++i)
+        if (codes[i] >= nk) {
+            mb_set_error("mb_index_kmer_get: code %llu is not below 4^%u", (unsigned long long)codes[i], idx->kmer_k);
+            return MB_ERR_ARG;
+        }
+    if (n == 0) return MB_OK;
+    DevBuf dc, dout;
+    MB_TRY(dc.alloc(n * 8, 0));
+    MB_TRY(dout.alloc(n * 12, 0));
+    MB_CK(cudaMemcpy(dc.p, codes, n * 8, cudaMemcpyHostToDevice));
+    k_kmer_get<<<grid_for(n, 256), 256>>>(idx->kmer, dc.as<u64>(), n, dout.as<u32>());
+    MB_KCHECK();
+    MB_CK(cudaMemcpy(out, dout.p, n * 12, cudaMemcpyDeviceToHost));
     return MB_OK;
 }
 
@@ -794,7 +827,7 @@ extern "C" int mb_index_load(const char *path, void *stream, mb_index **out) {
         mb_set_error("mb_index_load: short header");
         return MB_ERR_CORRUPT;
     }
-    if (h.magic != MAGIC || h.version != 4 || h.sa_rate == 0 || h.kmer_k > 14 || h.n >= (1ULL << 32) ||
+    if (h.magic != MAGIC || h.version != 4 || h.sa_rate == 0 || h.kmer_k > 16 || h.n >= (1ULL << 32) ||
         h.n < 2 || h.nblocks != h.n / BLK_ROWS + 1) {
         fclose(f);
         mb_set_error("mb_index_load: bad header");

@@ -134,7 +134,7 @@ __device__ __forceinline__ u64 convert8(u64 x, u32 conv) {
     return x;
 }
 
-// k-mer code of P[j-K+1 .. j] (K <= 14), first base in the lowest bits; false if it holds an N.
+// k-mer code of P[j-K+1 .. j] (K <= 16), first base in the lowest bits; false if it holds an N.
 // The K bytes lie in two aligned 16-byte chunks: both are loaded, the K bytes shifted out, and
 // tested, converted and packed eight at a time.  Next to the end of the batch it goes byte by
 // byte.
@@ -151,7 +151,7 @@ __device__ __forceinline__ bool kmer_code(SmemState &S, int j, u32 K, u32 &code)
         u64 lo = sh ? (w0 >> sh) | (w1 << (64 - sh)) : w0;
         u64 hi = sh ? (w1 >> sh) | (w2 << (64 - sh)) : w1;
         lo &= K >= 8 ? ~0ULL : ((1ULL << (8 * K)) - 1);
-        hi &= K > 8 ? ((1ULL << (8 * (K - 8))) - 1) : 0ULL;
+        hi &= K >= 16 ? ~0ULL : (K > 8 ? ((1ULL << (8 * (K - 8))) - 1) : 0ULL);
         if (((lo | hi) & 0xFCFCFCFCFCFCFCFCULL) != 0) return false;   // an N (any code > 3)
         code = pack8(convert8(lo, S.conv)) | (pack8(convert8(hi, S.conv)) << 16);
         return true;
@@ -1856,12 +1856,12 @@ static int share_alloc(DevBuf &bw, u64 n_smem, u64 total, u64 n, bool join, cuda
 }
 
 int mb_locate_records(const mb_index *idx, const mb_smem *sm, u64 n_smem, const u32 *known, u32 *hits, u64 n_hits,
-                      u32 depth, cudaStream_t st) {
+                      u32 depth, bool join, cudaStream_t st) {
     if (n_smem == 0 || n_hits == 0) return MB_OK;
     DevBuf bw;
     ShareBufs b;
     const DevIndex I = mb_dev_index(idx);
-    MB_TRY(share_alloc(bw, n_smem, n_hits, I.n, false, st, b));
+    MB_TRY(share_alloc(bw, n_smem, n_hits, I.n, join && n_hits > 1, st, b));
     return locate_shared(I, sm, n_smem, nullptr, known, hits, n_hits, b, nullptr, false, depth, nullptr, st);
 }
 

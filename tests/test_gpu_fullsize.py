@@ -129,22 +129,20 @@ def test_workload3_1gbp_full_index_and_sampled_reads(mb, w3):
 
 # the launch configuration bench.py times on the 1 Gbp workload
 BENCH_KMER_K = 14
-BENCH_OPTS = dict(block_size=512, prefetch_depth=16)
+BENCH_OPTS = dict(block_size=512, prefetch_depth=4)
 
 
 def test_workload3_1gbp_in_the_bench_configuration(mb, w3):
-    """The bench's exact configuration: 14-mer table, work queue, block 512, 16 walks per lane;
-    plain calls == captured plan graph == mb_seed_locate on pinned host buffers, and 1% of the
-    reads against the oracle."""
+    """The bench's exact configuration: 14-mer table, work queue, block 512, 4 walks per lane
+    that join; plain calls == captured plan graph == mb_seed_locate on pinned host buffers, and
+    1% of the reads against the oracle."""
     ref, rd, params, X = w3
     G = mb.mb_index_build(dev(ref), opts=dict(kmer_k=BENCH_KMER_K))
-    e = G.export(kmer=True, kmer_k=BENCH_KMER_K)
     words = np.sort(np.random.default_rng(0x6D67).choice(4 ** BENCH_KMER_K, 50_000, replace=False))
     pats = np.stack([(words >> (2 * t)) & 3 for t in range(BENCH_KMER_K)], axis=1).astype(np.uint8)
-    assert np.array_equal(e["kmer"].reshape(-1, 3)[words], X.ds_intervals(pats).astype(np.uint32))
-    del e
+    assert np.array_equal(G.kmer_get(words), X.ds_intervals(pats).astype(np.uint32))
     G.drop_sa()
-    opts = dict(BENCH_OPTS, flags=mb.MB_BATCHED)
+    opts = dict(BENCH_OPTS, flags=mb.MB_BATCHED | mb.MB_LOCATE_JOIN)
     seq, off = dev(rd.seq), dev(rd.off)
     # plain calls in the bench's launch shape
     cap = 4 * rd.n

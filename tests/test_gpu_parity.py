@@ -179,22 +179,31 @@ def test_locate_shared_rows_any_intervals(mb, seed):
     assert np.array_equal(out.cpu().numpy().view(np.uint32).astype(np.int64), S[rows].astype(np.int64))
 
 
-@pytest.mark.parametrize("k", [12, 14])
+@pytest.mark.parametrize("k", [12, 14, 16])
 def test_larger_kmer_tables(mb, k):
-    """k-mer tables above the paper's k = 10 (12 * 4^k bytes, 3.2 GB at k = 14): sampled entries
-    against the oracle's ds-intervals, and the same SMEMs and hits as without a table."""
+    """k-mer tables above the paper's k = 10 (12 * 4^k bytes: 3.2 GB at k = 14, 51.5 GB at
+    k = 16): sampled entries against the oracle's ds-intervals, and the same SMEMs and hits as
+    without a table."""
     ref, rd, p = synth.workload(2, scale=0.005)
     G = mb.mb_index_build(ref, opts=dict(kmer_k=k))
     X = oracle.Index(ref)
-    e = G.export(kmer=True, kmer_k=k)
     words = np.sort(np.random.default_rng(k).choice(4 ** k, 50_000, replace=False)).astype(np.int64)
-    pats = np.stack([(words >> (2 * t)) & 3 for t in range(k)], axis=1).astype(np.uint8)
-    assert np.array_equal(e["kmer"].reshape(-1, 3)[words], X.ds_intervals(pats).astype(np.uint32))
-    del e
+    present = X.ds_intervals(np.stack([(words >> (2 * t)) & 3 for t in range(k)], axis=1).astype(np.uint8))
+    # k-mers of the reference itself, so that most sampled entries are not empty
+    starts = np.random.default_rng(k + 1).integers(0, len(ref) - k, 20_000)
+    win = ref[starts[:, None] + np.arange(k)].astype(np.int64)
+    ok = (win < 4).all(axis=1)
+    rw = (win[ok] << (2 * np.arange(k))).sum(axis=1)
+    allw = np.concatenate([words, rw])
+    want = np.concatenate([present, X.ds_intervals(win[ok].astype(np.uint8))]).astype(np.uint32)
+    assert np.array_equal(G.kmer_get(allw), want)
+    assert (want[:, 2] > 0).sum() >= len(rw)
     sm, hits = mb.seed(G, rd.seq, rd.off)
     compare_seed(sm, hits, X, rd.seq, rd.off)
     nsm, nhits = mb.seed(G, rd.seq, rd.off, opts=dict(flags=mb.MB_NO_KMER))
     assert sm.tobytes() == nsm.tobytes() and np.array_equal(hits, nhits)
+    with pytest.raises(mb.MbError):
+        G.kmer_get([4 ** k])
 
 
 def test_work_counters_match_oracle(mb):

@@ -47,10 +47,13 @@ def repeat_rich(mb):
     return ref, rd, G
 
 
+@pytest.mark.parametrize("join", [False, True])
 @pytest.mark.parametrize("chunk", [997, 4096, 0])
-def test_host_buffers_against_oracle_and_plain(mb, repeat_rich, chunk):
+def test_host_buffers_against_oracle_and_plain(mb, repeat_rich, chunk, join):
+    """mb_seed_locate on host buffers, plain walks or walks that join (MB_LOCATE_JOIN)."""
     ref, rd, G = repeat_rich
-    sm, hits = mb.seed_locate(G, rd.seq, rd.off, opts=dict(chunk_reads=chunk))
+    o = dict(chunk_reads=chunk, prefetch_depth=4, flags=mb.MB_LOCATE_JOIN if join else 0)
+    sm, hits = mb.seed_locate(G, rd.seq, rd.off, opts=o)
     check_oracle(sm, hits, oracle.Index(ref), rd.seq, rd.off)
     psm, phits = mb.seed(G, rd.seq, rd.off)
     assert sm.tobytes() == psm.tobytes()
@@ -64,7 +67,8 @@ def test_several_slices(mb, repeat_rich, monkeypatch):
     monkeypatch.setenv("MB_SLICE_READS", "3000")
     psm, phits = mb.seed(G, rd.seq, rd.off)
     for chunk in (1000, 2999, 0):
-        sm, hits = mb.seed_locate(G, rd.seq, rd.off, opts=dict(chunk_reads=chunk))
+        o = dict(chunk_reads=chunk, flags=mb.MB_LOCATE_JOIN if chunk == 2999 else 0)
+        sm, hits = mb.seed_locate(G, rd.seq, rd.off, opts=o)
         assert sm.tobytes() == psm.tobytes()
         assert np.array_equal(hits, phits)
     out = torch.empty(len(psm) * 48, dtype=torch.uint8, device="cuda")
