@@ -218,6 +218,66 @@ enum { ACT_NONE = 0, ACT_EXT = 1, ACT_KMER = 2, ACT_WALK = 3, ACT_SAMPLE = 4, AC
 // steps they replace.
 constexpr int U_MIN = 16;
 
+// The memory actions of the uniform step of k_smem_split: block reads (an extension or an LF step
+// of a walk), a text comparison, an SA / ISA sample, a k-mer table entry.
+enum { R_BLOCK = 0, R_TEXT = 1, R_SAMPLE = 2, R_KMER = 3 };
+
+// Stages 4-7 up to their next memory action: R_BLOCK (a walk step), R_SAMPLE (sa_aux in stage 4,
+// isa_aux in stage 6, index in acode) or R_TEXT.  Returns false only in stage 7 with the walk
+// done (s = 0), where the match is emitted.
+__device__ __forceinline__ bool uniq_next(SmemState &S, u32 n, u32 prim, int &ract, u32 &acode) {
+    for (;;) {
+        if (S.u == 4) {
+            if (S.kr == prim) {                     // the $ row: S = 0
+                S.pos = S.s;
+                S.u = 5;
+                continue;
+            }
+            if ((S.kr & (AUX_RATE - 1)) == 0) {
+                acode = S.kr / AUX_RATE;
+                ract = R_SAMPLE;
+                return true;
+            }
+            if (S.s > n) {                          // only on a corrupted index: compare nothing
+                S.pos = n;
+                S.u = 5;
+                continue;
+            }
+            ract = R_BLOCK;
+            return true;
+        }
+        if (S.u == 5) {
+            if (S.j >= S.L || (u64)S.pos + (u32)(S.j - S.i) >= (u64)n - 1) {
+                S.u = 6;
+                continue;
+            }
+            ract = R_TEXT;
+            return true;
+        }
+        if (S.u == 6) {
+            const u64 end = (u64)S.pos + (u32)(S.j - S.i);
+            const u64 y = end < (u64)n - 1 ? (u64)n - 1 - end : 0;
+            u64 q = (y + AUX_RATE - 1) / AUX_RATE * AUX_RATE;
+            if (q >= (u64)n - 1) {                  // the $ suffix, row 0
+                q = (u64)n - 1;
+                S.kr = 0;
+                S.s = (u32)(q - y);
+                S.u = 7;
+                continue;
+            }
+            S.s = (u32)(q - y);
+            acode = (u32)(q / AUX_RATE);
+            ract = R_SAMPLE;
+            return true;
+        }
+        if (S.u == 7 && S.s != 0) {
+            ract = R_BLOCK;
+            return true;
+        }
+        return false;
+    }
+}
+
 // Tuning of k_smem_split: block steps between two service passes, and lanes out of the block loop
 // that call a service pass early (defaults; mb_opts.smem_burst / smem_wait override them).
 struct SmemTuning {
@@ -254,58 +314,19 @@ __device__ __forceinline__ int smem_next(SmemState &S, const DevIndex &I, u32 l,
             }
             return ACT_EXT;
         }
-        if (S.u == 4) {
-            if (S.kr == (u32)I.primary) {           // the $ row: S = 0
-                S.pos = S.s;
-                S.u = 5;
-                continue;
+        if (S.u >= 4) {                             // stages 4-7
+            int ract = R_BLOCK;
+            if (uniq_next(S, n, (u32)I.primary, ract, code))
+                return ract == R_TEXT ? ACT_TEXT : (ract == R_SAMPLE ? ACT_SAMPLE : ACT_WALK);
+            emit(S.i, S.j, S.k, S.kr, 1u, S.pos);   // stage 7 done: P[i, j) occurs once
+            if (S.j == S.L) {
+                S.u = 0;
+                return ACT_NONE;
             }
-            if ((S.kr & (AUX_RATE - 1)) == 0) {
-                code = S.kr / AUX_RATE;
-                return ACT_SAMPLE;
-            }
-            if (S.s > n) {                          // only on a corrupted index: compare nothing
-                S.pos = n;
-                S.u = 5;
-                continue;
-            }
-            return ACT_WALK;
-        }
-        if (S.u == 5) {
-            if (S.j >= S.L || (u64)S.pos + (u32)(S.j - S.i) >= (u64)n - 1) {
-                S.u = 6;
-                continue;
-            }
-            return ACT_TEXT;
-        }
-        if (S.u == 6) {
-            const u64 end = (u64)S.pos + (u32)(S.j - S.i);
-            const u64 y = end < (u64)n - 1 ? (u64)n - 1 - end : 0;
-            u64 q = (y + AUX_RATE - 1) / AUX_RATE * AUX_RATE;
-            if (q >= (u64)n - 1) {                  // the $ suffix, row 0
-                q = (u64)n - 1;
-                S.kr = 0;
-                S.s = (u32)(q - y);
-                S.u = 7;
-                continue;
-            }
-            S.s = (u32)(q - y);
-            code = (u32)(q / AUX_RATE);
-            return ACT_SAMPLE;
-        }
-        if (S.u == 7) {
-            if (S.s == 0) {
-                emit(S.i, S.j, S.k, S.kr, 1u, S.pos);
-                if (S.j == S.L) {
-                    S.u = 0;
-                    return ACT_NONE;
-                }
-                S.u = 3;                            // as after a failed ForwardExt
-                S.k = 0; S.kr = 0; S.s = n;
-                S.tried = false;
-                continue;
-            }
-            return ACT_WALK;
+            S.u = 3;                                // as after a failed ForwardExt
+            S.k = 0; S.kr = 0; S.s = n;
+            S.tried = false;
+            continue;
         }
         if (S.u == 1) {
             if (S.j < S.i) {                        // P[i, i+l) is a match: stage 2
@@ -648,20 +669,36 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 128 ? 6 : 1024 / BLOCK) k_smem
     work.flush(wc);
 }
 
-// The SMEM kernel with the block actions split from the rest.  Its lanes go through Algorithm 3
+// Text comparison of stage 5 with the text words t0, t1 at T[x & ~15, ...), x = pos + j - i: the
+// matching prefix of up to 16 read bases; a mismatch or an N ends the match (stage 6).
+__device__ __forceinline__ void text_apply(SmemState &S, u32 t0, u32 t1, u32 n) {
+    const u32 x = S.pos + (u32)(S.j - S.i);
+    u32 rc = 0, rn = 0;
+    const u32 rcnt = read_codes16(S, S.j, rc, rn);
+    const u32 tc = (u32)((((u64)t1 << 32) | t0) >> (2 * (x & 15)));
+    const u32 lim = min(min(rcnt, (u32)(S.L - S.j)), n - 1 - x);
+    const u32 d = rc ^ tc, m2 = ((d | (d >> 1)) & 0x55555555u) | rn;
+    const u32 first = m2 ? (u32)(__ffs(m2) - 1) >> 1 : 16u;
+    S.j += (int)min(first, lim);
+    if (first < lim) S.u = 6;
+}
+
+// The SMEM kernel with the memory actions split from the rest.  Its lanes go through Algorithm 3
 // exactly as k_smem's do (same reads, same steps in the same order, same records), but a warp
 // runs two kinds of iteration:
-//  - a block step, uniform code for every lane whose next action reads occurrence blocks: an
-//    extension by P[j] (stages 1-3; Algorithm 1) or one LF step of a walk (stages 4 and 7).  A
-//    lane whose extension succeeds and whose next action is again a block action stays in this
-//    loop; most steps of Algorithm 3 are such extensions;
-//  - a service pass, run when at least `wait` lanes are out of the block loop, when `burst` block
-//    steps ran since the last pass, or when no lane can take a block step: every lane out of the
-//    loop applies a failed extension (a record, a restart), moves through the stage changes that
-//    need no memory, and takes at most one other memory action (k-mer table, SA / ISA sample,
-//    text comparison); finished lanes take new reads.
-// So the branches of the seven stages are executed together once per service pass instead of in
-// every iteration.
+//  - a memory step, uniform for every lane that holds a memory action: an extension by P[j]
+//    (stages 1-3; Algorithm 1) or an LF step of a walk (stages 4 and 7), both reading
+//    occurrence blocks; a text comparison (stage 5); an SA or ISA sample (stages 4 and 6); a
+//    k-mer table entry (Section 2.5).  The loads of all lanes are issued before any result is
+//    used, so they are in flight together.  A lane whose next action follows without a record or
+//    a stage change of Algorithm 3 (another extension of the same stage, the next walk step, the
+//    next text comparison, the sample at the end of a walk, ...) stays in this loop;
+//  - a service pass, run when at least `wait` lanes are out of the loop, when `burst` memory
+//    steps ran since the last pass, or when no lane holds a memory action: every lane out of the
+//    loop applies a failed extension (a record, a restart) and moves through the stage changes
+//    up to its next memory action; finished lanes take new reads.  A pass reads no index array.
+// So the branches of the stages are executed together once per service pass instead of in every
+// iteration.
 // WARPS: resident warps per SM the launch bounds aim at (their register cap: 65,536 / (WARPS x 32)).
 template <bool QUEUE, int BLOCK, int WARPS>
 __global__ void __launch_bounds__(BLOCK, WARPS * 32 / BLOCK)
@@ -672,11 +709,10 @@ __global__ void __launch_bounds__(BLOCK, WARPS * 32 / BLOCK)
                  u32 *err, u32 *chk) {
     const u32 FULL = 0xffffffffu;
     const u32 lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
-    const u32 n = (u32)I.n, prim = (u32)I.primary;
+    const u32 n = (u32)I.n, prim = (u32)I.primary, K = I.kmer_k;
     const u64 o0 = off[0];
     const u64 o1 = off[nr];
     const u8 *const end = seq + o1;
-    Work<false> work;
     SmemState S;
     SlotEmit em;
     WarpRange wr;
@@ -714,47 +750,24 @@ __global__ void __launch_bounds__(BLOCK, WARPS * 32 / BLOCK)
             wr.next += k;
         }
     };
-    // one service of a lane out of the block loop: its pending failure, the stage changes, and at
-    // most one memory action that is not a block action.  Returns true when the read is finished.
+    // lane state: rdy = holds the memory action ract (acode: its sample index or k-mer code);
+    // pend = an extension failed and is applied at the next pass
     bool rdy = false, pend = false;
+    int ract = R_BLOCK;
+    u32 acode = 0;
+    // one service of a lane out of the loop: its pending failure and the stage changes up to its
+    // next memory action.  Returns true when the read is finished.
     auto service = [&]() -> bool {
         if (pend) {
             pend = false;
             if (!smem_apply(S, 0, 0, 0, lr, cr, n, em)) return true;
         }
         u32 code = 0;
-        const int act = smem_next(S, I, lr, kmer && lr >= I.kmer_k, em, code, uext);
+        const int act = smem_next(S, I, lr, kmer && lr >= K, em, code, uext);
         if (act == ACT_NONE) return true;
-        if (act == ACT_EXT || act == ACT_WALK) {
-            rdy = true;
-            return false;
-        }
-        if (act == ACT_KMER) {
-            const u32 *t = I.kmer + 3 * (u64)code;
-            return !smem_apply_kmer(S, __ldg(t), __ldg(t + 1), __ldg(t + 2), lr, cr, I.kmer_k);
-        }
-        if (act == ACT_SAMPLE) {
-            const u32 smp = __ldg((S.u == 4 ? I.sa_aux : I.isa_aux) + code);
-            if (S.u == 4) {
-                S.pos = smp + S.s;
-                S.u = 5;
-            } else {
-                S.kr = smp;
-                S.u = 7;
-            }
-            return false;
-        }
-        // ACT_TEXT: the matching prefix of read and text, up to 16 bases
-        const u32 x = S.pos + (u32)(S.j - S.i);
-        const u32 t0 = __ldg(I.text2 + (x >> 4)), t1 = __ldg(I.text2 + (x >> 4) + 1);
-        u32 rc = 0, rn = 0;
-        const u32 rcnt = read_codes16(S, S.j, rc, rn);
-        const u32 tc = (u32)((((u64)t1 << 32) | t0) >> (2 * (x & 15)));
-        const u32 lim = min(min(rcnt, (u32)(S.L - S.j)), n - 1 - x);
-        const u32 d = rc ^ tc, m2 = ((d | (d >> 1)) & 0x55555555u) | rn;
-        const u32 first = m2 ? (u32)(__ffs(m2) - 1) >> 1 : 16u;
-        S.j += (int)min(first, lim);
-        if (first < lim) S.u = 6;
+        ract = act == ACT_TEXT ? R_TEXT : (act == ACT_SAMPLE ? R_SAMPLE : (act == ACT_KMER ? R_KMER : R_BLOCK));
+        acode = code;
+        rdy = true;
         return false;
     };
     u64 item, r = 0;
@@ -771,10 +784,10 @@ __global__ void __launch_bounds__(BLOCK, WARPS * 32 / BLOCK)
         const u32 in_mask = __ballot_sync(FULL, rdy);
         if (out_mask && (in_mask == 0 || since >= tune.burst || (u32)__popc(out_mask) >= tune.wait)) {
             since = 0;
-            // ---- service pass (divergent)
+            // ---- service pass (divergent, no index reads)
             bool fin = live && !rdy && service();
-            // finished lanes hand in their counts and take new reads, which take their first
-            // action at once (a read shorter than l finishes there and takes the next one)
+            // finished lanes hand in their counts and take new reads, which go to their first
+            // memory action at once (a read shorter than l finishes there and takes the next one)
             for (;;) {
                 if (fin) {
                     counts[r] = em.cnt;
@@ -800,8 +813,8 @@ __global__ void __launch_bounds__(BLOCK, WARPS * 32 / BLOCK)
             }
         }
         ++since;
-        // ---- block step (uniform): an extension or an LF step of a walk for every ready lane
-        if (rdy && chk) {   // MB_CHECKED: both rows inside the text (always so on a sound index)
+        // ---- memory step (uniform): every lane's memory action, loads first
+        if (rdy && ract == R_BLOCK && chk) {   // MB_CHECKED: both rows inside the text (always so on a sound index)
             const bool walk = S.u >= 4, fwd = S.u == 2;
             const u64 p = (fwd || walk) ? S.kr : S.k;
             if (p + (walk ? 0u : S.s) > n) {
@@ -810,38 +823,80 @@ __global__ void __launch_bounds__(BLOCK, WARPS * 32 / BLOCK)
                 S.u = 0;   // the read ends here; the next service pass finishes it
             }
         }
-        if (rdy) {
-            const bool walk = S.u >= 4, fwd = S.u == 2;
-            const u32 p = (fwd || walk) ? S.kr : S.k, q = fwd ? S.k : S.kr, sz = walk ? 0u : S.s, e = p + sz;
-            const Blk b0 = load_blk(I.occ + (p >> BLK_SHIFT));
-            Blk b1 = b0;
-            if ((e >> BLK_SHIFT) != (p >> BLK_SHIFT)) b1 = load_blk(I.occ + (e >> BLK_SHIFT));
+        if (!rdy) continue;
+        const bool walk = S.u >= 4, fwd = S.u == 2;
+        const u32 p = (fwd || walk) ? S.kr : S.k, sz = walk ? 0u : S.s;
+        Blk b0, b1;
+        u32 w0 = 0, w1 = 0, w2 = 0;
+        if (ract == R_BLOCK) {
+            b0 = load_blk(I.occ + (p >> BLK_SHIFT));
+            b1 = b0;
+            if (((p + sz) >> BLK_SHIFT) != (p >> BLK_SHIFT)) b1 = load_blk(I.occ + ((p + sz) >> BLK_SHIFT));
+        } else if (ract == R_TEXT) {
+            const u32 x = S.pos + (u32)(S.j - S.i);
+            w0 = __ldg(I.text2 + (x >> 4));
+            w1 = __ldg(I.text2 + (x >> 4) + 1);
+        } else if (ract == R_SAMPLE) {
+            w0 = __ldg((S.u == 4 ? I.sa_aux : I.isa_aux) + acode);
+        } else {
+            const u32 *t = I.kmer + 3 * (u64)acode;
+            w0 = __ldg(t);
+            w1 = __ldg(t + 1);
+            w2 = __ldg(t + 2);
+        }
+        if (ract == R_BLOCK) {
+            const u32 q = fwd ? S.k : S.kr;
             const u32 a = walk ? 0u : cached_base(S, S.j);
             const u32 sym = walk ? sym_at(b0, p & BLK_MASK) : ((fwd ? 3u - a : a) & 3u);
             const Ext x = extend_blocks(I, b0, b1, p, q, sz, sym);
             if (walk) {
                 S.kr = x.p;
-                if (S.u == 4) {
+                if (S.u == 4)
                     ++S.s;
-                    rdy = S.kr != prim && (S.kr & (AUX_RATE - 1)) != 0 && S.s <= n;
-                } else {
+                else
                     --S.s;
-                    rdy = S.s != 0;
-                }
+                rdy = uniq_next(S, n, prim, ract, acode);
             } else if (a < 4 && x.s >= cr) {
                 S.k = fwd ? x.q : x.p;
                 S.kr = fwd ? x.p : x.q;
                 S.s = x.s;
                 S.j += fwd ? 1 : -1;
-                rdy = S.u == 1 ? S.j >= S.i
-                               : (S.u == 2 ? (S.j != S.L && !(uext && S.s == 1 && S.L - S.j >= U_MIN)) : S.j > S.i);
+                if (S.u == 1) {
+                    rdy = S.j >= S.i;
+                } else if (S.u == 3) {
+                    rdy = S.j > S.i;
+                } else if (S.j == S.L) {
+                    rdy = false;
+                } else if (uext && S.s == 1 && S.L - S.j >= U_MIN) {   // one occurrence: compare text
+                    S.u = 4;
+                    S.kr = S.k;
+                    S.s = 0;
+                    rdy = uniq_next(S, n, prim, ract, acode);
+                }
             } else {   // the extension fails: applied at the next service pass
                 rdy = false;
                 pend = true;
             }
+        } else if (ract == R_TEXT) {
+            text_apply(S, w0, w1, n);
+            rdy = uniq_next(S, n, prim, ract, acode);
+        } else if (ract == R_SAMPLE) {
+            if (S.u == 4) {
+                S.pos = w0 + S.s;
+                S.u = 5;
+            } else {
+                S.kr = w0;
+                S.u = 7;
+            }
+            rdy = uniq_next(S, n, prim, ract, acode);
+        } else {
+            // a k-mer entry; the next action is an extension of the same stage when the match
+            // goes on (else the pass decides; a finished read has u = 0)
+            rdy = smem_apply_kmer(S, w0, w1, w2, lr, cr, K) &&
+                  ((S.u == 1 && S.j >= S.i && S.s != n) || (S.u == 3 && S.j > S.i));
+            ract = R_BLOCK;
         }
     }
-    (void)work;
 }
 
 __device__ __forceinline__ void write_rec(mb_smem *out, u64 *hitc, u64 m, u32 r, u32 qbeg, u32 qend, u64 k, u64 kr,
