@@ -595,7 +595,22 @@ def bench_bisulfite(mb, torch, dev, ref, opts, reps: int = 3):
     _, m, nh = mb.mb_seed_batch(G, seq, off, mate=mate, opts=o, out=out, cap=cap)
     hits = torch.empty(max(nh, 1), dtype=torch.int32, device=dev)
     keep = torch.empty(max(nh, 1), dtype=torch.uint8, device=dev)
-    mb.mb_locate(G, out, m, opts=o, hits=hits, cap=nh)
+    # locate form for this batch: plain walks (16 per lane) or walks that join (4 per lane), the
+    # faster of the two on one timed call each (the join's per-call setup scales with the index)
+    forms = {"plain": dict(o, flags=o["flags"] & ~mb.MB_LOCATE_JOIN, prefetch_depth=16),
+             "join": dict(o, flags=o["flags"] | mb.MB_LOCATE_JOIN, prefetch_depth=4)}
+    st = torch.cuda.current_stream()
+    form_ms = {}
+    for name, fo in forms.items():
+        mb.mb_locate(G, out, m, opts=fo, hits=hits, cap=nh)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        mb.mb_locate(G, out, m, opts=fo, hits=hits, cap=nh)
+        e1.record(st)
+        torch.cuda.synchronize()
+        form_ms[name] = e0.elapsed_time(e1)
+    loc_form = min(form_ms, key=form_ms.get)
+    lo = forms[loc_form]
     mb.mb_bs_filter(G, out, m, mate, hits, nh, keep=keep)
     import ctypes
     oo = mb.Opts(**o)
@@ -613,7 +628,6 @@ def bench_bisulfite(mb, torch, dev, ref, opts, reps: int = 3):
 
     need = split_into(torch.empty(24, dtype=torch.uint8, device=dev))
     pieces = torch.empty(max(need, 1) * 24, dtype=torch.uint8, device=dev)
-    st = torch.cuda.current_stream()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
     times = {"seed": [], "locate": [], "filter": [], "split": []}
     npieces = 0
@@ -621,7 +635,7 @@ def bench_bisulfite(mb, torch, dev, ref, opts, reps: int = 3):
         ev[0].record(st)
         mb.mb_seed_batch(G, seq, off, mate=mate, opts=o, out=out, cap=cap)
         ev[1].record(st)
-        mb.mb_locate(G, out, m, opts=o, hits=hits, cap=nh)
+        mb.mb_locate(G, out, m, opts=lo, hits=hits, cap=nh)
         ev[2].record(st)
         mb.mb_bs_filter(G, out, m, mate, hits, nh, keep=keep)
         ev[3].record(st)
@@ -637,6 +651,7 @@ def bench_bisulfite(mb, torch, dev, ref, opts, reps: int = 3):
                        "30% CpG conversion) on the 3-base index of the 1 Gbp reference",
            "n": int(G.n), "index_build_s": build_s, "reads": rd.n, "smems": m, "hits": nh,
            "kept_hits": int(keep[:nh].sum().item()), "pieces": npieces, "ms": ms,
+           "locate_form": loc_form, "locate_form_ms": form_ms,
            "seed_locate_reads_per_s": rd.n / ((ms["seed"] + ms["locate"]) / 1000.0),
            "whole_bs_path_reads_per_s": rd.n / (total / 1000.0)}
     del out, hits, keep, seq, off, mate, ref_d, pieces
