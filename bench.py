@@ -724,12 +724,13 @@ def run_gpu(args):
         best = mb.Opts(block_size=args.block, prefetch_depth=args.locate_walks,
                        flags=(mb.MB_BATCHED if args.queue else 0) | (mb.MB_SMEM_ONE_LOOP if args.one_loop else 0) |
                        (mb.MB_LOCATE_JOIN if args.locate_join else 0),
-                       smem_burst=args.smem_burst, smem_wait=args.smem_wait)
+                       smem_burst=args.smem_burst, smem_wait=args.smem_wait, smem_warps=args.smem_warps)
     opts["block_size"] = best.block_size
     opts["prefetch_depth"] = best.prefetch_depth
     opts["flags"] = best.flags
     opts["smem_burst"] = best.smem_burst
     opts["smem_wait"] = best.smem_wait
+    opts["smem_warps"] = best.smem_warps
 
     # work counters of the chosen form (untimed pass with counting kernels)
     mb.profile_reset()
@@ -1032,6 +1033,8 @@ def main():
                     help="plain locate walks: every walk runs to its sampled row")
     ap.add_argument("--smem-burst", type=int, default=0, help="SMEM kernel block steps between service passes")
     ap.add_argument("--smem-wait", type=int, default=0, help="SMEM kernel lanes out of the loop that call a pass")
+    ap.add_argument("--smem-warps", type=int, default=0,
+                    help="SMEM kernel register budget: resident warps per SM aimed at (40: block 256 only; 48)")
     ap.add_argument("--reads", type=int, default=0,
                     help="seed only the first N reads of the batch (for ncu captures of the full index)")
     args = ap.parse_args()

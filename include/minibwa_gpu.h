@@ -93,10 +93,11 @@ typedef struct {
     uint32_t chunk_reads;     /* mb_seed_locate: reads per pipelined chunk (0 = 2^22) */
     uint32_t prefetch_depth;  /* tuning: LF-walks in flight per lane in locate, 1/2/4/8/16 (0 = 1) */
     uint32_t block_size;      /* tuning: threads per block (0 = default) */
-    uint32_t smem_burst;      /* tuning: SMEM kernel, block steps (extensions, walk steps) a warp runs
-                                 between two service passes of its other actions (0 = default) */
-    uint32_t smem_wait;       /* tuning: SMEM kernel, lanes out of the block steps that call a service
-                                 pass early, 1..32 (0 = default) */
+    uint32_t smem_burst;      /* tuning: SMEM kernel (split form), memory steps (extensions, walk
+                                 steps, text comparisons, samples, k-mer entries) a warp runs between
+                                 two service passes of its stage changes (0 = default, 8) */
+    uint32_t smem_wait;       /* tuning: SMEM kernel (split form), lanes out of the memory steps that
+                                 call a service pass early, 1..32 (0 = default, 8) */
     uint32_t smem_warps;      /* tuning: SMEM kernel (split form), resident warps per SM its register
                                  budget aims at: 40 (256 threads per block) or 48 (256 or 512); 0 =
                                  24 at 128 threads per block, else 32 */

@@ -511,7 +511,7 @@ def shape_of(o: Opts) -> dict:
     return {"block_size": o.block_size or 256, "work_queue": bool(o.flags & MB_BATCHED),
             "smem_form": "split" if split else "one_loop",
             "smem_burst": (o.smem_burst or 8) if split else None,
-            "smem_wait": (o.smem_wait or 16) if split else None,
+            "smem_wait": (o.smem_wait or 8) if split else None,
             "smem_warps": (o.smem_warps or None) if split else None,
             "locate_walks_per_lane": o.prefetch_depth or 1, "locate_join": bool(o.flags & MB_LOCATE_JOIN)}
 

@@ -278,12 +278,12 @@ __device__ __forceinline__ bool uniq_next(SmemState &S, u32 n, u32 prim, int &ra
     }
 }
 
-// Tuning of k_smem_split: block steps between two service passes, and lanes out of the block loop
-// that call a service pass early (defaults; mb_opts.smem_burst / smem_wait override them).
+// Tuning of k_smem_split: memory steps between two service passes, and lanes out of the loop that
+// call a service pass early (defaults; mb_opts.smem_burst / smem_wait override them).
 struct SmemTuning {
     u32 burst, wait;
 };
-constexpr u32 SMEM_BURST = 8, SMEM_WAIT = 16;
+constexpr u32 SMEM_BURST = 8, SMEM_WAIT = 8;
 
 // Moves through the steps of Algorithm 3 that need no memory and picks the next memory action:
 // ACT_EXT, an extension of P[j] (backward in stages 1 and 3, forward in stage 2); ACT_KMER, a
@@ -691,8 +691,9 @@ __device__ __forceinline__ void text_apply(SmemState &S, u32 t0, u32 t1, u32 n) 
 //    occurrence blocks; a text comparison (stage 5); an SA or ISA sample (stages 4 and 6); a
 //    k-mer table entry (Section 2.5).  The loads of all lanes are issued before any result is
 //    used, so they are in flight together.  A lane whose next action follows without a record or
-//    a stage change of Algorithm 3 (another extension of the same stage, the next walk step, the
-//    next text comparison, the sample at the end of a walk, ...) stays in this loop;
+//    a restart (another extension of the same stage, stage 1's match going on to stage 2, the
+//    next walk step, the next text comparison, the sample at the end of a walk, ...) stays in
+//    this loop;
 //  - a service pass, run when at least `wait` lanes are out of the loop, when `burst` memory
 //    steps ran since the last pass, or when no lane holds a memory action: every lane out of the
 //    loop applies a failed extension (a record, a restart) and moves through the stage changes
@@ -861,8 +862,12 @@ __global__ void __launch_bounds__(BLOCK, WARPS * 32 / BLOCK)
                 S.kr = fwd ? x.p : x.q;
                 S.s = x.s;
                 S.j += fwd ? 1 : -1;
+                if (S.u == 1 && S.j < S.i) {   // P[i, i+l) is a match: stage 2 (as smem_next)
+                    S.u = 2;
+                    S.j = S.i + (int)lr;
+                }
                 if (S.u == 1) {
-                    rdy = S.j >= S.i;
+                    rdy = true;
                 } else if (S.u == 3) {
                     rdy = S.j > S.i;
                 } else if (S.j == S.L) {
