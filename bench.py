@@ -360,6 +360,24 @@ def bench_batched(mb, torch, dev, reps: int = 3):
     batched_s = e0.elapsed_time(e1) / 1000 / reps
     bsm, bhits = BP.result()
     BP.free()
+    # the fastest shape with the device work queue (reads handed out longest first), as its own
+    # replayed graph: reported beside the autotuner's choice, output compared
+    qo, _ = min(((o, t) for o, t in grid if o.flags & mb.MB_BATCHED), key=lambda p: p[1])
+    QP = mb.Plan(G, rd.n, len(rd.seq), n_smem + 64, n_hits + 64, opts=qo)
+    QP.capture(seq, off)
+    QP.replay()
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(reps):
+        QP.replay()
+    e1.record(st)
+    torch.cuda.synchronize()
+    queue_s = e0.elapsed_time(e1) / 1000 / reps
+    qsm, qhits = QP.result()
+    QP.free()
+    queue_same = qsm.tobytes() == bsm.tobytes() and np.array_equal(qhits, bhits)
+    if not queue_same:
+        raise SystemExit("bench: the work-queue form disagrees with the autotuned form")
     # identity with the per-bucket launches, put back in read order
     rec, hl = [], []
     for ids, s_, o_, P, m, nh in buckets:
@@ -383,7 +401,9 @@ def bench_batched(mb, torch, dev, reps: int = 3):
             "speedup": plain_s / batched_s, "identical_output": bool(same),
             "autotuned": mb.shape_of(best), "autotuned_ms": tune_ms,
             "autotune_grid": [dict(mb.shape_of(o), ms=round(ms, 3)) for o, ms in grid],
-            "plain_ms": plain_s * 1000, "batched_ms": batched_s * 1000}
+            "plain_ms": plain_s * 1000, "batched_ms": batched_s * 1000,
+            "work_queue_best": dict(mb.shape_of(qo), graph_reads_per_s=rd.n / queue_s, ms=queue_s * 1000,
+                                    identical_output=bool(queue_same))}
 
 
 def serve_requests(ref, n, seed):

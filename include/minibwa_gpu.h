@@ -101,6 +101,9 @@ typedef struct {
     uint32_t smem_warps;      /* tuning: SMEM kernel (split form), resident warps per SM its register
                                  budget aims at: 40 (256 threads per block) or 48 (256 or 512); 0 =
                                  24 at 128 threads per block, else 32 */
+    uint32_t smem_reads_per_warp; /* tuning: SMEM kernel (split form), reads a warp holds at once,
+                                 one per lane, 1..32 (0 = 32); with fewer the other lanes stay idle
+                                 (a read's steps depend on each other, so lanes cannot share one) */
 } mb_opts;
 
 /* One SMEM (48 bytes).  (k, kr, s) is its ds-interval (lo(P), lo(revcomp P), occ(P)),
@@ -282,8 +285,9 @@ int mb_seed_locate(const mb_index *idx, const uint8_t *seq, const uint64_t *off,
  * writes the fastest into *best (same output for all): first the SMEM kernel's shape, threads per
  * block 128/256/512 x work queue off/on x kernel form (the one-loop form MB_SMEM_ONE_LOOP, or the
  * split form with smem_burst 2/4/8/16 x smem_wait 4/8/16), with 16 plain locate walks per lane;
- * then, with the best SMEM shape, locate walks per lane 1/2/4/8 plain and 1/2/4/8/16 with walks
- * that join (MB_LOCATE_JOIN) (87 points).  mb_autotune_points does
+ * then, when the best is a split form, smem_reads_per_warp 1/2/4/8/16 (against its 32); then, with
+ * the best SMEM shape, locate walks per lane 1/2/4/8 plain and 1/2/4/8/16 with walks that join
+ * (MB_LOCATE_JOIN) (92 points, 87 when the one-loop form wins).  mb_autotune_points does
  * the same and also returns every point tried with its time in ms (up to cap points; *n_points
  * receives the number tried).
  */

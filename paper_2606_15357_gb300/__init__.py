@@ -37,7 +37,8 @@ class Opts(ctypes.Structure):
                 ("kmer_k", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                 ("chunk_reads", ctypes.c_uint32), ("prefetch_depth", ctypes.c_uint32),
                 ("block_size", ctypes.c_uint32), ("smem_burst", ctypes.c_uint32),
-                ("smem_wait", ctypes.c_uint32), ("smem_warps", ctypes.c_uint32)]
+                ("smem_wait", ctypes.c_uint32), ("smem_warps", ctypes.c_uint32),
+                ("smem_reads_per_warp", ctypes.c_uint32)]
 
 
 class MbError(RuntimeError):
@@ -513,6 +514,7 @@ def shape_of(o: Opts) -> dict:
             "smem_burst": (o.smem_burst or 8) if split else None,
             "smem_wait": (o.smem_wait or 8) if split else None,
             "smem_warps": (o.smem_warps or None) if split else None,
+            "smem_reads_per_warp": (o.smem_reads_per_warp or 32) if split else None,
             "locate_walks_per_lane": o.prefetch_depth or 1, "locate_join": bool(o.flags & MB_LOCATE_JOIN)}
 
 

@@ -94,7 +94,8 @@ struct Pipeline {
 bool same_plan_opts(const mb_opts &a, const mb_opts &b) {
     return a.min_len == b.min_len && a.min_occ == b.min_occ && a.max_occ == b.max_occ && a.flags == b.flags &&
            a.prefetch_depth == b.prefetch_depth && a.block_size == b.block_size && a.smem_burst == b.smem_burst &&
-           a.smem_wait == b.smem_wait && a.smem_warps == b.smem_warps;
+           a.smem_wait == b.smem_wait && a.smem_warps == b.smem_warps &&
+           a.smem_reads_per_warp == b.smem_reads_per_warp;
 }
 
 constexpr size_t KEEP = 2;

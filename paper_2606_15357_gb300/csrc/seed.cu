@@ -282,6 +282,7 @@ __device__ __forceinline__ bool uniq_next(SmemState &S, u32 n, u32 prim, int &ra
 // call a service pass early (defaults; mb_opts.smem_burst / smem_wait override them).
 struct SmemTuning {
     u32 burst, wait;
+    u32 rpw;   // reads a warp holds at once (lanes 0 .. rpw-1), 1..32
 };
 constexpr u32 SMEM_BURST = 8, SMEM_WAIT = 8;
 
@@ -509,7 +510,7 @@ struct SmemArgs {
     u32 *chk = nullptr;                // with MB_CHECKED: the error word, for the per-step bounds checks
     bool split = true;                 // k_smem_split (else k_smem, one loop for every stage)
     u32 warps = 0;                     // k_smem_split: resident warps per SM aimed at (0: by block size)
-    SmemTuning tune = {SMEM_BURST, SMEM_WAIT};
+    SmemTuning tune = {SMEM_BURST, SMEM_WAIT, 32};
 };
 
 // Launch bounds per shape: 128 threads allow 85 registers (6 blocks, 24 warps per SM); 256 and
@@ -773,7 +774,8 @@ __global__ void __launch_bounds__(BLOCK, WARPS * 32 / BLOCK)
     };
     u64 item, r = 0;
     bool live;
-    take(32, lane, item, live);
+    take(tune.rpw, lane < tune.rpw ? lane : 0u, item, live);   // lanes rpw.. hold no read
+    live = live && lane < tune.rpw;
     if (live) {
         r = QUEUE && perm ? perm[item] : item;
         start(r);
@@ -1571,6 +1573,7 @@ void smem_tuning(const mb_opts *o, SmemArgs &a) {
     a.tune.burst = o && o->smem_burst ? o->smem_burst : SMEM_BURST;
     a.tune.wait = o && o->smem_wait ? (o->smem_wait > 32 ? 32u : o->smem_wait) : SMEM_WAIT;
     a.warps = o ? o->smem_warps : 0;
+    a.tune.rpw = o && o->smem_reads_per_warp && o->smem_reads_per_warp < 32 ? o->smem_reads_per_warp : 32u;
 }
 
 template <bool COUNT, bool POW2, int D, bool CHK = false>
@@ -2178,7 +2181,7 @@ struct mb_plan {
     int block = 256;
     u32 depth = 1;   // walks per lane in locate
     bool split = true;   // SMEM kernel form and tuning
-    SmemTuning tune = {SMEM_BURST, SMEM_WAIT};
+    SmemTuning tune = {SMEM_BURST, SMEM_WAIT, 32};
     u32 warps = 0;
     u32 max_reads = 0;
     u64 max_bases = 0, max_smem = 0, max_hits = 0, nslots = 0;
@@ -2525,6 +2528,7 @@ static int autotune_impl(const mb_index *idx, const uint8_t *seq, const uint64_t
             for (int f = -1; f < 12 && rc == MB_OK; ++f) {
                 mb_opts o = opts ? *opts : mb_opts{};
                 o.flags = (o.flags & ~(MB_BATCHED | MB_SMEM_ONE_LOOP | MB_LOCATE_JOIN)) | (q ? MB_BATCHED : 0u);
+                o.smem_reads_per_warp = 0;
                 o.block_size = (u32)blocks[bi];
                 o.prefetch_depth = 16;
                 if (f < 0) {
@@ -2536,6 +2540,12 @@ static int autotune_impl(const mb_index *idx, const uint8_t *seq, const uint64_t
                 }
                 rc = time_point(o);
             }
+    // reads per warp below 32 (lanes left idle) with the best SMEM shape
+    for (u32 rpw = 1; rpw <= 16 && rc == MB_OK && !(bo.flags & MB_SMEM_ONE_LOOP); rpw *= 2) {
+        mb_opts o = bo;
+        o.smem_reads_per_warp = rpw;
+        rc = time_point(o);
+    }
     const mb_opts smem_best = bo;
     for (int join = 0; join < 2; ++join)
         for (u32 dep = 1; dep <= (join ? 16u : 8u) && rc == MB_OK; dep *= 2) {
