@@ -826,6 +826,35 @@ def run_gpu(args):
                             "gpu_launches": graph_launches, "shape": mb.shape_of(best)},
              "reported": "graph_plan" if use_graph else "plain_launch"}
 
+    # the same graph with locate walks that stop at the index's rate-4 SA samples (MB_LOCATE_AUX):
+    # reported beside the headline, which locates through the rate-32 samples of Section 2.4
+    if not args.no_aux_form:
+        aopts = dict(opts, flags=(best.flags & ~mb.MB_LOCATE_JOIN) | mb.MB_LOCATE_AUX, prefetch_depth=16)
+        AP = mb.Plan(idx, n_reads, len(rd.seq), m + 1024, nh + 1024, opts=aopts)
+        AP.capture(seq, off)
+        for _ in range(args.warmup):
+            AP.replay()
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(args.steps):
+            AP.replay()
+        e1.record(st)
+        torch.cuda.synchronize()
+        aux_ms = e0.elapsed_time(e1)
+        asm_, ah = AP.result()
+        aux_same = asm_.tobytes() == out[:m * 48].cpu().numpy().tobytes() and \
+            np.array_equal(ah, hits[:nh].cpu().numpy().view(np.uint32))
+        AP.free()
+        del asm_, ah
+        if not aux_same:
+            raise SystemExit("bench: the rate-4 locate form disagrees with the plain launches")
+        forms["graph_plan_locate_aux"] = {
+            "reads_per_s": ws * args.steps * n_reads / (aux_ms / 1000.0), "ms_per_step": aux_ms / args.steps,
+            "identical_output": bool(aux_same), "shape": mb.shape_of(mb.Opts(**aopts)),
+            "note": "locate walks stop at the rate-4 SA samples the index keeps for text extension "
+                    "(MB_LOCATE_AUX); not the headline, which uses the rate-32 samples"}
+        log(f"graph form with MB_LOCATE_AUX: {aux_ms / args.steps:.1f} ms/step (identical: {aux_same})")
+
     # roofline of the dominant kernel: algorithmic bytes / its event-timed duration
     peak, peak_kind = measured_peaks()
     smem_bytes = (BLOCK_BYTES * (wc["ext_blocks"] + wc["u_walk_steps"]) + 12 * wc["kmer_lookups"] +
@@ -1027,6 +1056,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the mixed-length batched comparison")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-form measurement")
     ap.add_argument("--no-rescue", action="store_true", help="skip the mate-rescue prefilter measurement")
+    ap.add_argument("--no-aux-form", action="store_true", help="skip the graph form with MB_LOCATE_AUX")
     ap.add_argument("--no-bisulfite", action="store_true", help="skip the bisulfite (3-base index) measurement")
     ap.add_argument("--rescue-pairs", type=int, default=1_000_000)
     ap.add_argument("--serve-requests", type=int, default=50_000,

@@ -69,6 +69,10 @@ enum {
                               bytes per 64 index rows plus 4 bytes per walked row of device
                               workspace).  Off under MB_CHECKED.  By default every LF-walk runs to
                               its sampled row */
+#define MB_LOCATE_AUX 0x200u /* locate: walks stop at the rate-4 SA samples the index keeps for
+                              extending unique matches (a row that is a multiple of 4) instead of
+                              the rate-r samples of Section 2.4: about r/4 times fewer LF steps, same
+                              positions; no joins.  Ignored for an index built with MB_NO_AUX */
 #define MB_SMEM_ONE_LOOP 0x80u /* tuning: the SMEM kernel in its one-loop form (every iteration runs
                               every stage's code) instead of the split form (uniform block steps,
                               the other actions in service passes); same output */

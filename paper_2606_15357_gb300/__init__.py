@@ -20,7 +20,7 @@ __all__ = ["SMEM_DTYPE", "Opts", "MbError", "lib", "build", "Index", "mb_index_b
            "mb_index_load", "mb_seed_batch", "mb_locate", "mb_bs_filter", "seed"]
 
 MB_BS3, MB_BATCHED, MB_CHECKED, MB_NO_KMER, MB_COUNT = 0x1, 0x2, 0x4, 0x8, 0x10
-MB_NO_AUX, MB_STEP_ONLY, MB_SMEM_ONE_LOOP, MB_LOCATE_JOIN = 0x20, 0x40, 0x80, 0x100
+MB_NO_AUX, MB_STEP_ONLY, MB_SMEM_ONE_LOOP, MB_LOCATE_JOIN, MB_LOCATE_AUX = 0x20, 0x40, 0x80, 0x100, 0x200
 AUX_RATE = 4   # sample rate of the auxiliary SA / ISA samples (mb_index_export_aux)
 MB_SMEM_OVER_MAX_OCC, MB_SMEM_ROUND2 = 0x1, 0x2
 MB_ERR_CAPACITY = -3
@@ -515,7 +515,8 @@ def shape_of(o: Opts) -> dict:
             "smem_wait": (o.smem_wait or 8) if split else None,
             "smem_warps": (o.smem_warps or None) if split else None,
             "smem_reads_per_warp": (o.smem_reads_per_warp or 32) if split else None,
-            "locate_walks_per_lane": o.prefetch_depth or 1, "locate_join": bool(o.flags & MB_LOCATE_JOIN)}
+            "locate_walks_per_lane": o.prefetch_depth or 1, "locate_join": bool(o.flags & MB_LOCATE_JOIN),
+            "locate_aux": bool(o.flags & MB_LOCATE_AUX)}
 
 
 # ---------------------------------------------------------------------------- served form

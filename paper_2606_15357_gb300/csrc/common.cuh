@@ -288,9 +288,9 @@ int mb_seed_device(const mb_index *idx, const u8 *dseq, const u64 *doff, u32 n_r
                    const u32 *dlc, u64 o0, u64 o1, const mb_opts *opts, cudaStream_t st, mb_smem *out, u64 cap,
                    u64 *n_out, u64 *n_hits);
 // Locate of device records (their hits at their hit offsets), D walks per lane, walks that join
-// when `join`; workspace allocated in stream order.
+// when `join`, walks to the rate-4 samples when `aux`; workspace allocated in stream order.
 int mb_locate_records(const mb_index *idx, const mb_smem *sm, u64 n_smem, const u32 *known, u32 *hits, u64 n_hits,
-                      u32 depth, bool join, cudaStream_t st);
+                      u32 depth, bool join, bool aux, cudaStream_t st);
 // build flags of an index (MB_BS3 for the 3-base bisulfite index)
 u32 mb_index_flags(const mb_index *x);
 // drops the host-buffer pipelines kept for an index (called when the index is freed)

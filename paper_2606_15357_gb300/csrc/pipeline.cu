@@ -256,6 +256,7 @@ extern "C" int mb_seed_locate(const mb_index *idx, const uint8_t *seq, const uin
     const bool hits_dev = hits && mb_is_device_ptr(hits);
     const u32 depth = opts ? opts->prefetch_depth : 0;
     const bool join = opts && (opts->flags & MB_LOCATE_JOIN) && !(opts->flags & MB_CHECKED);
+    const bool aux = opts && (opts->flags & MB_LOCATE_AUX);
 
     // device inputs of chunk i (the caller's, or the stage's copies)
     auto inputs = [&](int i, const Stage &x, const u8 *&dseq, const u64 *&doff, const u8 *&dmate) {
@@ -380,7 +381,7 @@ extern "C" int mb_seed_locate(const mb_index *idx, const uint8_t *seq, const uin
             if (h_tot == 0)   // hit offsets are already batch-wide: copy the records out now
                 MB_CK(cudaMemcpyAsync(out + m_tot, gsm.p, ms_tot * sizeof(mb_smem), cudaMemcpyDefault, B.st));
             MB_TRY(mb_locate_records(idx, gsm.as<mb_smem>(), ms_tot, gknown.as<u32>(), dhits, hs_tot, depth, join,
-                                     A.st));
+                                     aux, A.st));
             if (h_tot) {      // later slices: batch-wide hit offsets after the locate
                 k_rebase<<<grid_for(ms_tot, 256), 256, 0, A.st>>>(gsm.as<mb_smem>(), ms_tot, 0, h_tot);
                 MB_KCHECK();

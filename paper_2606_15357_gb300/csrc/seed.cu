@@ -1621,6 +1621,7 @@ struct ShareBufs {
     // block the walked rows before it, the not-sorted flag, and the partition of the rows by pass
     // (per-tile pass counts, the row numbers by pass, the pass boundaries)
     bool join = true;
+    bool aux = false;   // MB_LOCATE_AUX: walks stop at the index's rate-4 SA samples (no joins)
     WalkBlk *wb = nullptr;
     uint4 *coarse = nullptr;
     u32 *before = nullptr, *nojoin = nullptr, *tcnt = nullptr, *idx = nullptr;
@@ -1703,7 +1704,8 @@ int locate_shared(const DevIndex &I, const mb_smem *sm, u64 cap, const u64 *nsm_
     k_share_rows<<<G, 256, 0, st>>>(b.keys, ss, b.last, b.roff, cap, b.nwalk, b.rows, hits_cap);
     MB_KCHECK();
     u32 *chk = b.checked ? b.err : nullptr;
-    if (b.join && b.wb && !chk) {
+    const bool aux = b.aux && I.sa_aux;
+    if (b.join && b.wb && !chk && !aux) {
         // walk blocks with the marks of the walked rows and their ranks, the rows by pass, then
         // one walk launch per pass (a pass joins only into rows of the passes before it)
         const u64 nw = join_words(I.n), nt = join_tiles(hits_cap);   // blocks, partition tiles
@@ -1724,8 +1726,13 @@ int locate_shared(const DevIndex &I, const mb_smem *sm, u64 cap, const u64 *nsm_
         for (u32 p = 0; p < (u32)JOIN_PASSES; ++p) MB_TRY(launch_pass(I, b.rows, hits_cap, p, b.rpos, b, wc, count, depth, st));
         if (kt) kt->stop();
     } else {
+        DevIndex L = I;   // with MB_LOCATE_AUX the walks stop at the rate-4 samples
+        if (aux) {
+            L.ssa = I.sa_aux;
+            L.r = AUX_RATE;
+        }
         if (kt) kt->start();
-        MB_TRY(launch_locate(I, b.rows, hits_cap, b.nrows, b.rpos, wc, count, depth, chk, st));
+        MB_TRY(launch_locate(L, b.rows, hits_cap, b.nrows, b.rpos, wc, count, depth, chk, st));
         if (kt) kt->stop();
     }
     k_share_copy<<<G, 256, 0, st>>>(b.keys, ss, sho, b.last, b.roff, cap, b.nwalk, b.rpos, hits_cap, hits, hits_cap);
@@ -1919,12 +1926,13 @@ static int share_alloc(DevBuf &bw, u64 n_smem, u64 total, u64 n, bool join, cuda
 }
 
 int mb_locate_records(const mb_index *idx, const mb_smem *sm, u64 n_smem, const u32 *known, u32 *hits, u64 n_hits,
-                      u32 depth, bool join, cudaStream_t st) {
+                      u32 depth, bool join, bool aux, cudaStream_t st) {
     if (n_smem == 0 || n_hits == 0) return MB_OK;
     DevBuf bw;
     ShareBufs b;
     const DevIndex I = mb_dev_index(idx);
-    MB_TRY(share_alloc(bw, n_smem, n_hits, I.n, join && n_hits > 1, st, b));
+    MB_TRY(share_alloc(bw, n_smem, n_hits, I.n, join && !aux && n_hits > 1, st, b));
+    b.aux = aux;
     return locate_shared(I, sm, n_smem, nullptr, known, hits, n_hits, b, nullptr, false, depth, nullptr, st);
 }
 
@@ -1960,8 +1968,10 @@ extern "C" int mb_locate(const mb_index *idx, const mb_smem *smem, uint64_t n_sm
     const bool count = opts && (opts->flags & MB_COUNT);
     DevBuf bw;
     ShareBufs b;
-    MB_TRY(share_alloc(bw, n_smem, total, I.n, opts && (opts->flags & MB_LOCATE_JOIN) && !(opts->flags & MB_CHECKED),
-                       st, b));
+    MB_TRY(share_alloc(bw, n_smem, total, I.n,
+                       opts && (opts->flags & MB_LOCATE_JOIN) && !(opts->flags & (MB_CHECKED | MB_LOCATE_AUX)), st,
+                       b));
+    b.aux = opts && (opts->flags & MB_LOCATE_AUX);
     b.checked = opts && (opts->flags & MB_CHECKED);
     u64 *wc = count ? mb_work_counter_buf(st) : nullptr;
     KTimer kt("locate", st);
@@ -2219,9 +2229,10 @@ void mb_plan_arrays(const mb_plan *p, const mb_smem **smem, const u32 **hits, u6
 // Device workspace of a plan, one entry per array (in the order mb_plan_create lays them out).
 constexpr int PLAN_ARRAYS = 30;
 // A plan locates with walks that join (their arrays sized by the index's n rows) when the options
-// say MB_LOCATE_JOIN without MB_CHECKED and the plan holds hits to locate (not a seeding-only plan).
+// say MB_LOCATE_JOIN without MB_CHECKED or MB_LOCATE_AUX and the plan holds hits to locate (not a
+// seeding-only plan).
 static bool plan_joins(const mb_opts *opts, u64 max_hits) {
-    return opts && (opts->flags & MB_LOCATE_JOIN) && !(opts->flags & MB_CHECKED) && max_hits > 1;
+    return opts && (opts->flags & MB_LOCATE_JOIN) && !(opts->flags & (MB_CHECKED | MB_LOCATE_AUX)) && max_hits > 1;
 }
 static void plan_sizes(const mb_opts *opts, u64 n, u32 max_reads, u64 max_bases, u64 max_smem, u64 max_hits,
                        size_t sizes[PLAN_ARRAYS]) {
@@ -2308,6 +2319,7 @@ extern "C" int mb_plan_create(const mb_index *idx, const mb_opts *opts, uint32_t
     P->share.err = plan_err(P);
     P->share.checked = (P->flags & MB_CHECKED) != 0;
     P->share.join = plan_joins(opts, max_hits);
+    P->share.aux = (P->flags & MB_LOCATE_AUX) != 0;
     *out = P;
     return MB_OK;
 }

@@ -106,23 +106,40 @@ def test_workload1_full(mb):
     compare_seed(sm, hits, X, rd.seq, rd.off)
 
 
-@pytest.mark.parametrize("join", [False, True])
+@pytest.mark.parametrize("form", ["plain", "join", "aux"])
 @pytest.mark.parametrize("depth", [1, 2, 4, 8, 16])
-def test_locate_walks_per_lane(mb, depth, join):
-    """Locate with 1, 2, 4, 8 or 16 LF-walks in flight per lane, with and without walks that join
-    (MB_LOCATE_JOIN), gives the same hits."""
+def test_locate_walks_per_lane(mb, depth, form):
+    """Locate with 1, 2, 4, 8 or 16 LF-walks in flight per lane, plain, with walks that join
+    (MB_LOCATE_JOIN) or with walks to the rate-4 samples (MB_LOCATE_AUX), gives the same hits."""
     ref, rd, p = synth.workload(2, scale=0.01)
     G = mb.mb_index_build(ref)
     X = oracle.Index(ref)
     sm, m, nh = mb.mb_seed_batch(G, rd.seq, rd.off)
-    o = dict(prefetch_depth=depth, flags=mb.MB_LOCATE_JOIN if join else 0)
+    flags = {"plain": 0, "join": mb.MB_LOCATE_JOIN, "aux": mb.MB_LOCATE_AUX}[form]
+    o = dict(prefetch_depth=depth, flags=flags)
     hits, _ = mb.mb_locate(G, sm, m, opts=o, cap=nh)
     compare_seed(sm, hits, X, rd.seq, rd.off)
-    if join:   # the same through a plan (its own walk blocks and pass partition)
+    if form != "plain":   # the same through a plan
         P = mb.Plan(G, rd.n, len(rd.seq), m + 8, nh + 8, opts=o)
         P.run(torch.from_numpy(rd.seq).cuda(), torch.from_numpy(rd.off.view(np.int64)).cuda())
         psm, phits = P.result()
         assert psm.tobytes() == sm.tobytes() and np.array_equal(phits, hits)
+
+
+def test_locate_aux_on_an_index_without_aux_arrays(mb):
+    """MB_LOCATE_AUX on an index built with MB_NO_AUX walks to the rate-32 samples: same hits."""
+    ref, rd, p = synth.workload(2, scale=0.005)
+    G = mb.mb_index_build(ref, opts=dict(flags=mb.MB_NO_AUX))
+    sm, m, nh = mb.mb_seed_batch(G, rd.seq, rd.off)
+    want, _ = mb.mb_locate(G, sm, m, cap=nh)
+    mb.profile_reset()
+    got, _ = mb.mb_locate(G, sm, m, opts=dict(flags=mb.MB_LOCATE_AUX | mb.MB_COUNT), cap=nh)
+    assert np.array_equal(got, want)
+    keep = (sm["flags"] & 1) == 0
+    rows = np.unique(np.concatenate([np.arange(int(k), int(k) + int(s_), dtype=np.uint64)
+                                     for k, s_ in zip(sm["k"][keep], sm["s"][keep])]))
+    wc = mb.work_counters()
+    assert (wc["lf_steps"], wc["sa_reads"]) == oracle.Index(ref).count_locate(rows)
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
@@ -232,6 +249,12 @@ def test_work_counters_match_oracle(mb):
     wc = mb.work_counters()
     assert (wc["lf_steps"], wc["sa_reads"], wc["joins"]) == X.count_locate_join(np.unique(rows), pass_bits=3)
     assert wc["joins"] > 0 and wc["joins_off"] == 0
+    # walks to the rate-4 samples (MB_LOCATE_AUX): Algorithm 2's counts with r = 4
+    mb.profile_reset()
+    mb.mb_locate(G, sm, m, opts=dict(flags=mb.MB_COUNT | mb.MB_LOCATE_AUX), cap=nh)
+    wc = mb.work_counters()
+    assert (wc["lf_steps"], wc["sa_reads"]) == oracle.Index(ref, sa_rate=4).count_locate(np.unique(rows))
+    assert wc["joins"] == 0
     # with the index's 10-mer table (Section 2.5): the same steps, blocks and lookups as the
     # oracle's Algorithm 3 with the cache
     mb.profile_reset()

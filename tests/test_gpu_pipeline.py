@@ -47,12 +47,13 @@ def repeat_rich(mb):
     return ref, rd, G
 
 
-@pytest.mark.parametrize("join", [False, True])
+@pytest.mark.parametrize("flags", [0, 0x100, 0x200])
 @pytest.mark.parametrize("chunk", [997, 4096, 0])
-def test_host_buffers_against_oracle_and_plain(mb, repeat_rich, chunk, join):
-    """mb_seed_locate on host buffers, plain walks or walks that join (MB_LOCATE_JOIN)."""
+def test_host_buffers_against_oracle_and_plain(mb, repeat_rich, chunk, flags):
+    """mb_seed_locate on host buffers, plain walks, walks that join (MB_LOCATE_JOIN, 0x100) or
+    walks to the rate-4 samples (MB_LOCATE_AUX, 0x200)."""
     ref, rd, G = repeat_rich
-    o = dict(chunk_reads=chunk, prefetch_depth=4, flags=mb.MB_LOCATE_JOIN if join else 0)
+    o = dict(chunk_reads=chunk, prefetch_depth=4, flags=flags)
     sm, hits = mb.seed_locate(G, rd.seq, rd.off, opts=o)
     check_oracle(sm, hits, oracle.Index(ref), rd.seq, rd.off)
     psm, phits = mb.seed(G, rd.seq, rd.off)
