@@ -466,7 +466,8 @@ def bench_rescue(mb, torch, dev, ref, n_pairs: int, reps: int = 5):
 
 
 def bench_served(mb, G, ref, n_requests: int, pool: int = 2000, load: float = 0.7,
-                 sweep=(0.3, 0.5, 0.9, 0.95), window: int = 4096, seq_prefix: int = 2000):
+                 sweep=(0.3, 0.5, 0.9, 0.95), window: int = 4096, seq_prefix: int = 2000,
+                 budget_gib: float = 8, opts=None, clients: int = 8):
     """Served form on the resident index: capacity (the whole stream submitted with at most
     `window` requests outstanding), then Poisson arrivals at `load` x capacity; latency per request
     from submit to results on the host.  The stream's requests are drawn (seeded) from `pool`
@@ -474,7 +475,9 @@ def bench_served(mb, G, ref, n_requests: int, pool: int = 2000, load: float = 0.
     seeded in full.  The first `seq_prefix` arrivals are also served by sequential plain launches
     (one request at a time through one preallocated plan: copy in, run, copy the results out; no
     allocation per request) for comparison, and the served form's latencies at the other offered
-    loads of `sweep` are reported."""
+    loads of `sweep` are reported.  Requests are submitted by `clients` threads (a server takes
+    submissions from many callers at once; one Python thread alone cannot stage the bases fast
+    enough), each with an equal share of the stream and of the window."""
     import collections
     import threading as th
     import torch
@@ -484,7 +487,7 @@ def bench_served(mb, G, ref, n_requests: int, pool: int = 2000, load: float = 0.
     reqs = [base[i] for i in pick]
     total_reads = sum(r.n for r in reqs)
     total_bases = sum(int(r.off[-1] - r.off[0]) for r in reqs)
-    srv = mb.Server(G, hbm_budget=8 << 30)
+    srv = mb.Server(G, hbm_budget=int(budget_gib * (1 << 30)), opts=opts)
 
     def submit(r, before=None):
         """Submit; when the staging ring is full (MB_ERR_BUSY), make room first."""
@@ -500,20 +503,31 @@ def bench_served(mb, G, ref, n_requests: int, pool: int = 2000, load: float = 0.
                     time.sleep(0.0005)
 
     counts = {}
-    t = time.time()
-    out = collections.deque()
 
-    def collect_one():
-        q, tk = out.popleft()
-        sm, hits, _ = srv.wait(tk)
-        counts[int(pick[q])] = (len(sm), len(hits))
+    def client(ids, win):
+        """One client thread: submits its requests in order with at most `win` outstanding,
+        collecting the oldest when the window or the staging ring is full."""
+        out = collections.deque()
 
-    for q, r in enumerate(reqs):
-        if len(out) >= window:
+        def collect_one():
+            q, tk = out.popleft()
+            sm, hits, _ = srv.wait(tk)
+            counts[int(pick[q])] = (len(sm), len(hits))
+
+        for q in ids:
+            if len(out) >= win:
+                collect_one()
+            out.append((q, submit(reqs[q], collect_one if out else None)))
+        while out:
             collect_one()
-        out.append((q, submit(r, collect_one if out else None)))
-    while out:
-        collect_one()
+
+    t = time.time()
+    cl = [th.Thread(target=client, args=(range(c, n_requests, clients), max(1, window // clients)))
+          for c in range(clients)]
+    for c in cl:
+        c.start()
+    for c in cl:
+        c.join()
     cap_s = time.time() - t
     cap_rps = n_requests / cap_s
     cap_counters = srv.counters()
@@ -531,14 +545,21 @@ def bench_served(mb, G, ref, n_requests: int, pool: int = 2000, load: float = 0.
                     time.sleep(0.0002)
                 _, _, lat[i] = srv.wait(tk[i])
 
+        def submitter(ids):
+            for i in ids:
+                d = t0 + arrivals[i] - time.time()
+                if d > 0:
+                    time.sleep(d)
+                tk[i] = submit(reqs[i])
+
         col = th.Thread(target=collect)
         col.start()
         t0 = time.time()
-        for i, r in enumerate(reqs):
-            d = t0 + arrivals[i] - time.time()
-            if d > 0:
-                time.sleep(d)
-            tk[i] = submit(r)
+        subs = [th.Thread(target=submitter, args=(range(c, n_requests, clients),)) for c in range(clients)]
+        for x in subs:
+            x.start()
+        for x in subs:
+            x.join()
         col.join()
         return lat, time.time() - t0, arrivals
 
@@ -580,7 +601,7 @@ def bench_served(mb, G, ref, n_requests: int, pool: int = 2000, load: float = 0.
             "stream": f"{n_requests} requests drawn (seeded) from {len(base)} generated ones",
             "mix": "80% short (1-4,096 pairs of 2x150), 20% long (1-4,096 reads of 1-10 kb), log-uniform sizes",
             "capacity_requests_per_s": cap_rps, "capacity_reads_per_s": total_reads / cap_s,
-            "capacity_bases_per_s": total_bases / cap_s, "capacity_window": window,
+            "capacity_bases_per_s": total_bases / cap_s, "capacity_window": window, "clients": clients,
             "offered_load": load, "arrival_rate_per_s": rate,
             "served_reads_per_s": total_reads / wall, "served_bases_per_s": total_bases / wall,
             "served_p50_ms": pct(lat, 50), "served_p95_ms": pct(lat, 95), "served_p99_ms": pct(lat, 99),
@@ -953,7 +974,10 @@ def run_gpu(args):
 
     served = None
     if rank == 0 and not args.no_serve:
-        served = bench_served(mb, idx, ref, args.serve_requests, pool=args.serve_pool)
+        served = bench_served(mb, idx, ref, args.serve_requests, pool=args.serve_pool,
+                              budget_gib=args.serve_budget_gib, clients=args.serve_clients,
+                              opts=dict(min_len=opts["min_len"], min_occ=opts["min_occ"], max_occ=opts["max_occ"],
+                                        prefetch_depth=args.serve_walks))
         log(f"served: {served}")
     del out, hits
     torch.cuda.empty_cache()
@@ -1061,6 +1085,11 @@ def main():
     ap.add_argument("--rescue-pairs", type=int, default=1_000_000)
     ap.add_argument("--serve-requests", type=int, default=50_000,
                     help="requests in the served stream (Poisson arrivals)")
+    ap.add_argument("--serve-budget-gib", type=float, default=8,
+                    help="device memory budget of the served form's slots (GiB)")
+    ap.add_argument("--serve-clients", type=int, default=8, help="client threads submitting to the served form")
+    ap.add_argument("--serve-walks", type=int, default=16, choices=[1, 2, 4, 8, 16],
+                    help="locate walks per lane in the served form's slots")
     ap.add_argument("--serve-pool", type=int, default=2000,
                     help="distinct generated requests the stream draws from")
     ap.add_argument("--probe-gib", type=float, default=1, help="buffer of the random-gather probe (GiB)")

@@ -321,15 +321,20 @@ int mb_autotune_points(const mb_index *idx, const uint8_t *seq, const uint64_t *
  * Served form: continuous batching of seeding requests on one GPU.
  * mb_serve_create starts a worker thread and a helper thread and allocates a 1 GiB pinned host
  * ring in which submitted bases wait.  Device work runs in execution slots (a stream and a seeding
- * plan for up to 65,536 reads / 64M bases / 2M SMEMs / 32M hits each, about 0.75 GB of device
- * memory).  Slots are admitted by free device memory: a slot is created only when requests wait
+ * plan for up to 65,536 reads / 64M bases / 2M SMEMs / 32M hits each, about 0.8 GB of device
+ * memory; at most 32 slots).  Slots are admitted by free device memory: a slot is created only when requests wait
  * and every slot is busy, and only while cudaMemGetInfo's free bytes minus a reserve left to other
  * users (2% of the device, at least 1 GiB) hold one more slot and the slots stay within
  * hbm_budget bytes (0 = no budget; one slot is always allowed by the budget); otherwise requests
  * wait until a slot frees.  Idle slots are released while free memory is below the reserve.
- * Whenever a slot is free, every waiting request that still fits the slot's limits is merged into
- * one launch group, so requests arriving while others are on the GPU are admitted as soon as a
- * slot frees, and groups run concurrently on their own streams.  A group whose records or hits
+ * Whenever a slot is free, the oldest waiting request and the later ones of its kind that still
+ * fit the slot's limits are merged into one launch group, so requests arriving while others are
+ * on the GPU are admitted as soon as a slot frees, and groups run concurrently on their own
+ * streams.  The kinds: requests with a read of 1,000 bases or more, and the others; a group takes
+ * as long as its longest read, so requests of short reads are never grouped with long reads, and
+ * groups of long reads hold at most half of the slots at a time.  Each slot runs its plan as one
+ * CUDA graph captured for the slot's 65,536 reads (a smaller group pads its offsets with empty
+ * reads), so a group costs one graph launch on the worker thread.  A group whose records or hits
  * exceed its plan is seeded again request by request on the helper thread (allocating entry
  * points), so the worker keeps serving.  Each request's results are exactly those of
  * mb_seed_batch + mb_locate on that request alone (read numbers and hit offsets relative to it).

@@ -10,6 +10,11 @@
 // overlap on the device.  Each request gets back exactly what mb_seed_batch + mb_locate give for
 // it alone: read numbers and hit offsets are made relative to the request.
 //
+// Each slot runs its plan as one CUDA graph captured when the slot is made, for SLOT_READS reads:
+// a group of n reads fills the offsets past its last read with its end (empty reads, which yield
+// nothing), so one graph launch replaces the hundred-odd kernel launches of a plan run and the
+// worker's time per group no longer bounds the request rate.
+//
 // Admission by free device memory: slots are created only when work is waiting and no slot is
 // free, and only while the free device memory (cudaMemGetInfo) minus a reserve left to other
 // users holds one more slot and the slots stay within the caller's budget; otherwise requests wait
@@ -34,10 +39,15 @@ constexpr u32 SLOT_READS = 65536;
 constexpr u64 SLOT_BASES = 64ull << 20;
 constexpr u64 SLOT_SMEM = 2ull << 20;
 constexpr u64 SLOT_HITS = 32ull << 20;
-constexpr int MAX_SLOTS = 16;
+constexpr int MAX_SLOTS = 32;
 constexpr u64 RING_BYTES = 1ull << 30;         // pinned staging of submitted bases
 constexpr u64 RESERVE_MIN = 1ull << 30;        // free device memory left to other users (at least)
 constexpr double MEM_POLL_MS = 1.0;            // how often the worker may query free memory
+// A group takes as long as its longest read (Algorithm 3's steps on one read are sequential), so
+// requests with reads of at least LONG_READ bases are grouped apart from the others: a request of
+// short reads never waits for a long read of another request.
+constexpr u64 LONG_READ = 1000;
+constexpr double LONG_SLOT_SHARE = 0.5;
 
 double now_ms() {
     using namespace std::chrono;
@@ -87,6 +97,7 @@ struct Request {
     const u8 *seq = nullptr; // = ring.at(ring_pos)
     std::vector<u64> off;    // n_reads + 1, from 0
     u32 n_reads = 0;
+    bool long_reads = false;  // holds a read of LONG_READ bases or more (grouped apart)
     double t_submit = 0, latency_ms = 0;
     bool done = false;
     int status = MB_OK;
@@ -107,12 +118,14 @@ struct Slot {
     mb_smem *hsmem = nullptr; // pinned
     u32 *hhits = nullptr;     // pinned
     cudaEvent_t ev = nullptr;
+    cudaGraphExec_t exec = nullptr;   // the plan run over SLOT_READS reads (null: launched directly)
     Phase phase = IDLE;
     std::vector<ReqP> group;
     std::vector<u32> first_read;   // first group read of each request
     u32 n_reads = 0;
     size_t dev_bytes = 0;
     double idle_since = 0;
+    bool long_group = false;   // the group holds requests with long reads
 };
 
 // live servers: calls on a destroyed server are refused instead of touching freed memory
@@ -152,8 +165,20 @@ struct mb_server {
 
 namespace {
 
+// Offsets past a group's last read: off[i] = off[n] for n < i <= max_n, n = off[max_n + 1] (the
+// count the group's copy puts after the offsets), so a plan over max_n reads sees n reads and
+// max_n - n empty ones.
+__global__ void k_off_tail(u64 *off, u32 max_n) {
+    const u64 n = off[(u64)max_n + 1];
+    if (n > max_n) return;
+    const u64 end = off[n];
+    for (u64 i = n + 1 + blockIdx.x * (u64)blockDim.x + threadIdx.x; i <= max_n; i += (u64)gridDim.x * blockDim.x)
+        off[i] = end;
+}
+
 void free_slot(Slot &s) {
     if (s.st) cudaStreamSynchronize(s.st);
+    if (s.exec) cudaGraphExecDestroy(s.exec);
     if (s.plan) mb_plan_free(s.plan);
     if (s.dseq) cudaFree(s.dseq);
     if (s.doff) cudaFree(s.doff);
@@ -170,7 +195,7 @@ size_t slot_device_bytes(const mb_index *idx, const mb_opts *o) {
     u64 n = 0, prim = 0, rl = 0;
     mb_index_info(idx, &n, &prim, &rl);
     return mb_plan_workspace_bytes(o, n, SLOT_READS, SLOT_BASES, SLOT_SMEM, SLOT_HITS) + SLOT_BASES + 16 +
-           (SLOT_READS + 1) * 8;
+           (SLOT_READS + 2) * 8;
 }
 
 int make_slot(mb_server *S, Slot &s) {
@@ -180,14 +205,30 @@ int make_slot(mb_server *S, Slot &s) {
         return MB_ERR_CUDA;
     }
     MB_TRY(mb_plan_create(S->idx, &S->opts, SLOT_READS, SLOT_BASES, SLOT_SMEM, SLOT_HITS, &s.plan));
-    if (cudaMalloc(&s.dseq, SLOT_BASES + 16) != cudaSuccess || cudaMalloc(&s.doff, (SLOT_READS + 1) * 8) != cudaSuccess ||
-        cudaMallocHost(&s.hoff, (SLOT_READS + 1) * 8) != cudaSuccess || cudaMallocHost(&s.hcnt, 32) != cudaSuccess ||
+    if (cudaMalloc(&s.dseq, SLOT_BASES + 16) != cudaSuccess || cudaMalloc(&s.doff, (SLOT_READS + 2) * 8) != cudaSuccess ||
+        cudaMallocHost(&s.hoff, (SLOT_READS + 2) * 8) != cudaSuccess || cudaMallocHost(&s.hcnt, 32) != cudaSuccess ||
         cudaMallocHost(&s.hsmem, SLOT_SMEM * sizeof(mb_smem)) != cudaSuccess ||
         cudaMallocHost(&s.hhits, SLOT_HITS * 4) != cudaSuccess) {
         cudaGetLastError();
         return MB_ERR_NOMEM;
     }
-    s.dev_bytes = mb_plan_bytes(s.plan) + SLOT_BASES + 16 + (SLOT_READS + 1) * 8;
+    s.dev_bytes = mb_plan_bytes(s.plan) + SLOT_BASES + 16 + (SLOT_READS + 2) * 8;
+    // the plan run as one graph: the offsets' tail, the run over SLOT_READS reads, the counts out
+    // (left null when the capture fails: the worker then launches the run directly)
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(s.st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        k_off_tail<<<(SLOT_READS + 255) / 256, 256, 0, s.st>>>(s.doff, SLOT_READS);
+        mb_count_launch();
+        const int rc = mb_plan_run(s.plan, s.dseq, s.doff, SLOT_READS, nullptr, s.st) == MB_OK &&
+                               mb_plan_counts_async(s.plan, s.hcnt, s.st) == MB_OK
+                           ? MB_OK
+                           : MB_ERR_CUDA;
+        if (cudaStreamEndCapture(s.st, &g) != cudaSuccess || rc != MB_OK ||
+            cudaGraphInstantiate(&s.exec, g, 0) != cudaSuccess)
+            s.exec = nullptr;
+        if (g) cudaGraphDestroy(g);
+    }
+    cudaGetLastError();
     return MB_OK;
 }
 
@@ -249,23 +290,50 @@ void retire(mb_server *S) {
     }
 }
 
-// Merge waiting requests into the free slot s (called with the lock held).  Returns false if
-// nothing is waiting.
-bool admit(mb_server *S, Slot &s) {
+// Merge waiting requests into the free slot s (called with the lock held): the oldest waiting
+// request and, in arrival order, the later ones of its kind (long reads or not) while they fit
+// the slot.  With `no_long`, the oldest waiting request without long reads leads instead (none:
+// nothing is admitted).  Returns false if nothing was admitted.
+bool admit(mb_server *S, Slot &s, bool no_long) {
     if (S->pending.empty()) return false;
+    bool kind = S->pending.front()->long_reads;
+    if (kind && no_long) {
+        bool any_short = false;
+        for (const ReqP &r : S->pending)
+            if (!r->long_reads) {
+                any_short = true;
+                break;
+            }
+        if (!any_short) return false;
+        kind = false;
+    }
     s.group.clear();
     s.first_read.clear();
+    s.long_group = kind;
     u32 nr = 0;
     u64 nb = 0;
+    std::deque<ReqP> rest;
     while (!S->pending.empty()) {
-        const ReqP &r = S->pending.front();
+        ReqP r = S->pending.front();
+        S->pending.pop_front();
         const u64 b = r->off[r->n_reads];
-        if (!s.group.empty() && (nr + r->n_reads > SLOT_READS || nb + b > SLOT_BASES)) break;
+        if (r->long_reads != kind) {
+            rest.push_back(r);
+            if (rest.size() >= 256) break;   // bounded look-ahead past the other kind
+            continue;
+        }
+        if (!s.group.empty() && (nr + r->n_reads > SLOT_READS || nb + b > SLOT_BASES)) {
+            S->pending.push_front(r);
+            break;
+        }
         s.first_read.push_back(nr);
         s.group.push_back(r);
         nr += r->n_reads;
         nb += b;
-        S->pending.pop_front();
+    }
+    while (!rest.empty()) {   // the skipped requests go back in front, in their order
+        S->pending.push_front(rest.back());
+        rest.pop_back();
     }
     s.n_reads = nr;
     return true;
@@ -295,8 +363,14 @@ int launch(mb_server *S, Slot &s) {
     }
     if (run_len) MB_CK(cudaMemcpyAsync(s.dseq + run_dst, run, run_len, cudaMemcpyHostToDevice, s.st));
     MB_CK(cudaMemcpyAsync(s.doff, s.hoff, (size_t)(nr + 1) * 8, cudaMemcpyHostToDevice, s.st));
-    MB_TRY(mb_plan_run(s.plan, s.dseq, s.doff, nr, nullptr, s.st));
-    MB_TRY(mb_plan_counts_async(s.plan, s.hcnt, s.st));
+    if (s.exec) {   // the group's read count after the offsets, then the captured run
+        s.hoff[SLOT_READS + 1] = nr;
+        MB_CK(cudaMemcpyAsync(s.doff + SLOT_READS + 1, s.hoff + SLOT_READS + 1, 8, cudaMemcpyHostToDevice, s.st));
+        MB_CK(cudaGraphLaunch(s.exec, s.st));
+    } else {
+        MB_TRY(mb_plan_run(s.plan, s.dseq, s.doff, nr, nullptr, s.st));
+        MB_TRY(mb_plan_counts_async(s.plan, s.hcnt, s.st));
+    }
     MB_CK(cudaEventRecord(s.ev, s.st));
     s.phase = RUNNING;
     return MB_OK;
@@ -392,10 +466,15 @@ void worker_loop(mb_server *S) {
         for (auto &sp : S->slots) {
             Slot &s = *sp;
             if (s.phase == IDLE) {
+                // long-read groups take at most LONG_SLOT_SHARE of the slots, so requests of short
+                // reads always find one
+                int long_busy = 0;
+                for (const auto &o : S->slots) long_busy += o->phase != IDLE && o->long_group;
+                const bool no_long = long_busy >= (int)(LONG_SLOT_SHARE * (double)S->slots.size()) && long_busy > 0;
                 bool got;
                 {
                     std::lock_guard<std::mutex> g(S->mu);
-                    got = admit(S, s);
+                    got = admit(S, s, no_long);
                 }
                 if (got) {
                     if (launch(S, s) != MB_OK) {
@@ -517,6 +596,7 @@ extern "C" int mb_serve_submit(mb_server *S, const uint8_t *seq, const uint64_t 
     r->n_reads = n_reads;
     r->off.resize((size_t)n_reads + 1);
     for (u32 i = 0; i <= n_reads; ++i) r->off[i] = off[i] - off[0];
+    for (u32 i = 0; i < n_reads && !r->long_reads; ++i) r->long_reads = r->off[i + 1] - r->off[i] >= LONG_READ;
     const u64 nb = r->off[n_reads];
     if (n_reads > SLOT_READS || nb > SLOT_BASES) {
         mb_set_error("mb_serve_submit: %u reads / %llu bases exceed one slot (%u / %llu)", n_reads,
