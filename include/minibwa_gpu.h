@@ -364,7 +364,8 @@ int mb_serve_stats(mb_server *srv, uint32_t *slots, uint64_t *groups, uint64_t *
 /* Up to `count` counters, in this order: slots now, groups, merged, slots created, slots released,
  * slot allocations that failed, groups that outgrew their plan, submits refused with MB_ERR_BUSY,
  * ms that waiting requests spent with every slot busy and no memory for another, device bytes of
- * one slot, the free-memory reserve in bytes. */
+ * one slot, the free-memory reserve in bytes, groups of requests with long reads, ms the worker
+ * thread spent launching groups and handing out results (13 exist). */
 int mb_serve_counters(mb_server *srv, uint64_t *out, uint32_t count);
 /* Fault injection for tests of admission (no counterpart in the paper): from now on admission sees
  * free_bytes of free device memory instead of cudaMemGetInfo's value (free_bytes < 0 restores the

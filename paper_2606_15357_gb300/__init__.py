@@ -567,7 +567,8 @@ class Server:
         return dict(slots=sl.value, groups=g.value, merged=m.value)
 
     COUNTERS = ("slots", "groups", "merged", "slots_created", "slots_released", "alloc_failures",
-                "outgrown_groups", "busy", "memory_wait_ms", "slot_bytes", "reserve_bytes")
+                "outgrown_groups", "busy", "memory_wait_ms", "slot_bytes", "reserve_bytes", "long_groups",
+                "worker_busy_ms")
 
     def counters(self):
         v = np.zeros(len(self.COUNTERS), dtype=np.uint64)

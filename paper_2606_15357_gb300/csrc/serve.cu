@@ -21,6 +21,7 @@
 // for a slot to free.  When free memory falls below the reserve, idle slots are released.  A group
 // that yields more records or hits than its plan holds is handed to a second thread, which seeds
 // its requests one by one with the allocating entry points, so the worker keeps serving.
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -157,7 +158,9 @@ struct mb_server {
     u64 next_ticket = 1;
     // counters (mb_serve_counters)
     u64 groups = 0, merged = 0, created = 0, retired = 0, alloc_failures = 0, fallback_groups = 0, busy = 0;
+    u64 long_groups = 0;
     double mem_wait_ms = 0;
+    std::atomic<u64> worker_busy_us{0};   // worker thread time launching groups and handing out results
     // fault injection for tests (mb_serve_inject)
     int64_t fake_free = -1;    // free device bytes reported to admission instead of cudaMemGetInfo's
     u32 fail_next = 0;         // slot creations to fail
@@ -472,9 +475,11 @@ void worker_loop(mb_server *S) {
                 for (const auto &o : S->slots) long_busy += o->phase != IDLE && o->long_group;
                 const bool no_long = long_busy >= (int)(LONG_SLOT_SHARE * (double)S->slots.size()) && long_busy > 0;
                 bool got;
+                const double t0 = now_ms();
                 {
                     std::lock_guard<std::mutex> g(S->mu);
                     got = admit(S, s, no_long);
+                    S->long_groups += got && s.long_group;
                 }
                 if (got) {
                     if (launch(S, s) != MB_OK) {
@@ -482,10 +487,12 @@ void worker_loop(mb_server *S) {
                         finish(S, s);
                     }
                     progressed = true;
+                    S->worker_busy_us += (u64)((now_ms() - t0) * 1000.0);
                 } else {
                     idle_slot = true;
                 }
             } else if (cudaEventQuery(s.ev) == cudaSuccess) {
+                const double t0 = now_ms();
                 if (s.phase == RUNNING) {
                     const int rc = fetch(S, s);
                     if (rc != MB_OK && rc != 1) {
@@ -497,6 +504,7 @@ void worker_loop(mb_server *S) {
                     finish(S, s);
                 }
                 progressed = true;
+                S->worker_busy_us += (u64)((now_ms() - t0) * 1000.0);
             }
         }
         // work waits and every slot is busy: admission by free device memory may add a slot
@@ -675,7 +683,8 @@ extern "C" int mb_serve_counters(mb_server *S, uint64_t *out, uint32_t count) {
     if (!alive(S) || (count && !out)) return MB_ERR_ARG;
     std::lock_guard<std::mutex> g(S->mu);
     const u64 v[] = {S->slots.size(), S->groups, S->merged, S->created, S->retired, S->alloc_failures,
-                     S->fallback_groups, S->busy, (u64)S->mem_wait_ms, S->slot_bytes, S->reserve};
+                     S->fallback_groups, S->busy, (u64)S->mem_wait_ms, S->slot_bytes, S->reserve, S->long_groups,
+                     S->worker_busy_us.load() / 1000};
     for (u32 i = 0; i < count && i < sizeof(v) / sizeof(v[0]); ++i) out[i] = v[i];
     return MB_OK;
 }
