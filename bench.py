@@ -1104,7 +1104,7 @@ def main():
     ap.add_argument("--block", type=int, default=512, choices=[128, 256, 512])
     ap.add_argument("--no-queue", dest="queue", action="store_false",
                     help="SMEM kernel walks fixed read ranges per warp instead of a device work queue")
-    ap.add_argument("--locate-walks", type=int, default=4, choices=[1, 2, 4, 8, 16])
+    ap.add_argument("--locate-walks", type=int, default=2, choices=[1, 2, 4, 8, 16])
     ap.add_argument("--one-loop", action="store_true", help="SMEM kernel in its one-loop form")
     ap.add_argument("--locate-join", dest="locate_join", action="store_true", default=True,
                     help="(default) locate with walks that join (MB_LOCATE_JOIN)")

@@ -1377,47 +1377,58 @@ __global__ void k_pass_split(const u32 *__restrict__ rows, const u64 *__restrict
         range[threadIdx.x] = threadIdx.x < JOIN_PASSES ? (ntiles ? tcnt[(u64)threadIdx.x * ntiles] : 0) : nr;
 }
 
-// Algorithm 2 over the rows of one pass: k_locate's walk loop (D walks per lane, one warp-wide
-// hand-out per iteration) on the walk blocks.  A walk past its first row that stands on a marked
-// row of an earlier pass stops: the next iteration reads the block's count of marked rows before
-// it (the rank), the one after reads that row's position.  The hand-out takes the rows of the
-// pass through idx and keeps each walk's row number (where its position goes) in h[].
+__device__ __forceinline__ u32 ld_cg_u32(const u32 *p) {   // from L2 (written by an earlier launch)
+    u32 v;
+    asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+// Algorithm 2 over the rows of one pass with joins: k_locate's walk loop (D walks per lane) on
+// the walk blocks.  A walk past its first row that stands on a marked row of an earlier pass
+// stops: the next iteration reads the block's count of marked rows before it (the rank), the one
+// after reads that row's position (final: its pass ran in an earlier launch).  Warps take the
+// pass's rows (through idx, in row order) from a device queue in chunks of 256 per walk slot, so
+// warps whose walks happen to be short take more rows and the pass ends with the grid's last
+// walks rather than with its most loaded warp.
 template <bool COUNT, bool POW2, int D>
-__global__ void __launch_bounds__(256, D <= 8 ? 2 : 1)
-    k_locate_pass(DevIndex I, const u32 *__restrict__ rows, const u32 *__restrict__ idx, const u64 *__restrict__ range,
+__global__ void __launch_bounds__(256, D <= 2 ? 4 : (D <= 4 ? 3 : (D <= 8 ? 2 : 1)))
+    k_locate_join(DevIndex I, const u32 *__restrict__ rows, const u32 *__restrict__ idx, const u64 *__restrict__ range,
                   u32 pass, const WalkBlk *__restrict__ wb, const uint4 *__restrict__ coarse, u32 ncoarse,
-                  const u32 *__restrict__ before, const u32 *__restrict__ nojoin, u32 *__restrict__ rpos, u64 *wc) {
-    extern __shared__ uint4 cs[];   // the coarse counts
+                  const u32 *__restrict__ before, const u32 *__restrict__ nojoin, u32 *__restrict__ rpos,
+                  u32 *__restrict__ qhead, u64 *wc) {
+    constexpr u32 CHUNK = 256u * D;   // queue positions a warp takes at a time
+    extern __shared__ uint4 cs[];     // the coarse counts
     for (u32 g = threadIdx.x; g < ncoarse; g += blockDim.x) cs[g] = coarse[g];
     __syncthreads();
-    const u32 lane = threadIdx.x & 31;
+    const u32 FULL = 0xffffffffu, lane = threadIdx.x & 31;
     const u64 lo_r = range[pass], hi_r = range[pass + 1];
-    const u64 nitems = hi_r > lo_r ? hi_r - lo_r : 0;
+    const u32 nitems = hi_r > lo_r ? (u32)(hi_r - lo_r) : 0u;
+    const u32 *__restrict__ qidx = idx + lo_r;
+    u32 *const head = qhead + pass;
     const bool join = *nojoin == 0 && pass > 0;
     Work<COUNT> work;
     const u32 r = I.r, rmask = I.r - 1, rshift = __ffs(I.r) - 1, prim = (u32)I.primary, n = (u32)I.n;
-    WarpRange wr;
-    wr.init(nitems);
-    const u32 *__restrict__ widx = idx + lo_r + wr.next;
-    const u32 wlen = (u32)(wr.end - wr.next);
     u32 h[D], row[D], steps[D];
     u32 live = 0, rk1 = 0, rk2 = 0;   // walks: present; met a marked row (row[] = block | pc << 26); rank known
-    u32 next = 0;
+    u32 next = 0;                     // the warp's queue chunk: positions [next, cend)
+    if (lane == 0) next = atomicAdd(head, CHUNK);
+    next = __shfl_sync(FULL, next, 0);
+    u32 cend = next + CHUNK;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-        const u32 o = next + lane;
+        const u32 o = next + 32u * d + lane;
         steps[d] = 0;
         row[d] = 0;
         h[d] = 0;
-        if (o < wlen) {
+        if (o < nitems) {
             live |= 1u << d;
-            h[d] = __ldg(&widx[o]);
+            h[d] = __ldg(&qidx[o]);
             row[d] = __ldg(&rows[h[d]]);
         }
-        next += 32;
     }
+    next += 32u * D;
     for (;;) {
-        if (__all_sync(0xffffffffu, live == 0)) break;
+        if (__all_sync(FULL, live == 0)) break;
         u32 stop = 0, smp = 0, ld = 0;
         u32 sv[D];
         u64 fc[D], bl[D], bh[D], mk[D];
@@ -1431,7 +1442,7 @@ __global__ void __launch_bounds__(256, D <= 8 ? 2 : 1)
             if (st) {
                 stop |= 1u << d;
                 if (r2) {
-                    sv[d] = __ldg(&rpos[row[d]]);   // the joined row's position, final since its pass
+                    sv[d] = ld_cg_u32(&rpos[row[d]]);   // the joined row's position, final since its pass
                     smp |= 1u << d;
                 } else if (sampled) {
                     smp |= 1u << d;
@@ -1444,15 +1455,21 @@ __global__ void __launch_bounds__(256, D <= 8 ? 2 : 1)
                 ld |= 1u << d;
             }
         }
+        // queue positions for the walks that end: from the warp's chunk, then a new chunk
         const u32 cnt = __popc(stop);
         u32 incl = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const u32 v = __shfl_up_sync(0xffffffffu, incl, o);
+            const u32 v = __shfl_up_sync(FULL, incl, o);
             if (lane >= (u32)o) incl += v;
         }
-        u32 give = next + incl - cnt;
-        next += __shfl_sync(0xffffffffu, incl, 31);
+        const u32 total = __shfl_sync(FULL, incl, 31), avail = cend - next;
+        u32 nb = cend;   // past the end once the chunk reached it (a new chunk would too)
+        if (total > avail && cend < nitems) {
+            if (lane == 0) nb = atomicAdd(head, CHUNK);
+            nb = __shfl_sync(FULL, nb, 0);
+        }
+        u32 k = incl - cnt;   // this lane's first position among the warp's
 #pragma unroll
         for (int d = 0; d < D; ++d) {
             if ((stop >> d) & 1u) {
@@ -1463,13 +1480,14 @@ __global__ void __launch_bounds__(256, D <= 8 ? 2 : 1)
                 rk1 &= ~(1u << d);
                 rk2 &= ~(1u << d);
                 steps[d] = 0;
-                if (give < wlen) {
-                    h[d] = __ldg(&widx[give]);
+                const u32 pos = k < avail ? next + k : nb + (k - avail);
+                ++k;
+                if (pos < nitems) {
+                    h[d] = __ldg(&qidx[pos]);
                     row[d] = __ldg(&rows[h[d]]);
                 } else {
                     live &= ~(1u << d);
                 }
-                ++give;
             } else if ((rk1 >> d) & 1u) {   // the rank: marked rows before the block, then in it
                 row[d] = sv[d] + (row[d] >> 26);
                 rk1 &= ~(1u << d);
@@ -1494,6 +1512,12 @@ __global__ void __launch_bounds__(256, D <= 8 ? 2 : 1)
                     ++steps[d];
                 }
             }
+        }
+        if (total > avail) {
+            next = nb + (total - avail);
+            cend = nb + CHUNK;
+        } else {
+            next += total;
         }
     }
     work.flush(wc);
@@ -1617,7 +1641,7 @@ struct ShareBufs {
     void *tmp = nullptr;
     u32 *err = nullptr;   // the device error word (records with rows outside the text; MB_CHECKED bounds)
     bool checked = false; // MB_CHECKED: the locate kernel checks every row it walks
-    // walks that join (k_locate_pass, MB_LOCATE_JOIN): the walk blocks and coarse counts, per
+    // walks that join (k_locate_join, MB_LOCATE_JOIN): the walk blocks and coarse counts, per
     // block the walked rows before it, the not-sorted flag, and the partition of the rows by pass
     // (per-tile pass counts, the row numbers by pass, the pass boundaries)
     bool join = true;
@@ -1626,6 +1650,7 @@ struct ShareBufs {
     uint4 *coarse = nullptr;
     u32 *before = nullptr, *nojoin = nullptr, *tcnt = nullptr, *idx = nullptr;
     u64 *range = nullptr;
+    u32 *qhead = nullptr;  // per pass: the head of the queue its launch takes rows from
 };
 // sizes of carved workspace arrays are rounded up to 256 bytes
 inline size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -1637,36 +1662,35 @@ inline u64 join_tiles(u64 rows_cap) { return (rows_cap + JOIN_TILE - 1) / JOIN_T
 inline size_t join_bytes(u64 n, u64 rows_cap) {
     return align_up(join_words(n) * sizeof(WalkBlk)) + align_up(join_coarse(n) * 16) + align_up(join_words(n) * 4) +
            align_up(8) + align_up(JOIN_PASSES * join_tiles(rows_cap) * 4 + 4) + align_up(rows_cap * 4) +
-           align_up((JOIN_PASSES + 1) * 8);
+           align_up((JOIN_PASSES + 1) * 8) + align_up(JOIN_PASSES * 4);
 }
 
 template <bool COUNT, bool POW2, int D>
-int launch_pass_t(const DevIndex &I, const u32 *rows, u64 nhits, u32 pass, u32 *rpos, const ShareBufs &b, u64 *wc,
+int launch_join_t(const DevIndex &I, const u32 *rows, u64 nhits, u32 pass, u32 *rpos, const ShareBufs &b, u64 *wc,
                   cudaStream_t st) {
-    const unsigned g =
-        resident_grid((const void *)k_locate_pass<COUNT, POW2, D>, 256, (nhits / JOIN_PASSES + 63) / 64 * 32 + 32);
-    const u64 warps = (u64)g * 8;
-    if ((nhits + warps - 1) / warps >= (1ull << 32) - 4096) {
-        mb_set_error("locate: %llu hits over %llu warps", (unsigned long long)nhits, (unsigned long long)warps);
+    const unsigned g = resident_grid((const void *)k_locate_join<COUNT, POW2, D>, 256,
+                                     (nhits / JOIN_PASSES + 63) / 64 * 32 + 32);
+    if (nhits + (u64)g * 8 * 256 * D + 256 * D >= (1ull << 32)) {   // queue positions are u32
+        mb_set_error("locate: %llu hits exceed the walk queue", (unsigned long long)nhits);
         return MB_ERR_ARG;
     }
     const u32 nc = (u32)join_coarse(I.n);
-    k_locate_pass<COUNT, POW2, D><<<g, 256, nc * sizeof(uint4), st>>>(I, rows, b.idx, b.range, pass, b.wb, b.coarse,
-                                                                      nc, b.before, b.nojoin, rpos, wc);
+    k_locate_join<COUNT, POW2, D><<<g, 256, nc * sizeof(uint4), st>>>(I, rows, b.idx, b.range, pass, b.wb, b.coarse,
+                                                                      nc, b.before, b.nojoin, rpos, b.qhead, wc);
     MB_KCHECK();
     return MB_OK;
 }
-int launch_pass(const DevIndex &I, const u32 *rows, u64 nhits, u32 pass, u32 *rpos, const ShareBufs &b, u64 *wc,
+int launch_join(const DevIndex &I, const u32 *rows, u64 nhits, u32 pass, u32 *rpos, const ShareBufs &b, u64 *wc,
                 bool count, u32 depth, cudaStream_t st) {
     const bool pow2 = (I.r & (I.r - 1)) == 0;
-    if (count) return pow2 ? launch_pass_t<true, true, 1>(I, rows, nhits, pass, rpos, b, wc, st)
-                           : launch_pass_t<true, false, 1>(I, rows, nhits, pass, rpos, b, wc, st);
-    if (!pow2) return launch_pass_t<false, false, 1>(I, rows, nhits, pass, rpos, b, wc, st);
-    if (depth >= 16) return launch_pass_t<false, true, 16>(I, rows, nhits, pass, rpos, b, wc, st);
-    if (depth >= 8) return launch_pass_t<false, true, 8>(I, rows, nhits, pass, rpos, b, wc, st);
-    if (depth >= 4) return launch_pass_t<false, true, 4>(I, rows, nhits, pass, rpos, b, wc, st);
-    if (depth >= 2) return launch_pass_t<false, true, 2>(I, rows, nhits, pass, rpos, b, wc, st);
-    return launch_pass_t<false, true, 1>(I, rows, nhits, pass, rpos, b, wc, st);
+    if (count) return pow2 ? launch_join_t<true, true, 1>(I, rows, nhits, pass, rpos, b, wc, st)
+                           : launch_join_t<true, false, 1>(I, rows, nhits, pass, rpos, b, wc, st);
+    if (!pow2) return launch_join_t<false, false, 1>(I, rows, nhits, pass, rpos, b, wc, st);
+    if (depth >= 16) return launch_join_t<false, true, 16>(I, rows, nhits, pass, rpos, b, wc, st);
+    if (depth >= 8) return launch_join_t<false, true, 8>(I, rows, nhits, pass, rpos, b, wc, st);
+    if (depth >= 4) return launch_join_t<false, true, 4>(I, rows, nhits, pass, rpos, b, wc, st);
+    if (depth >= 2) return launch_join_t<false, true, 2>(I, rows, nhits, pass, rpos, b, wc, st);
+    return launch_join_t<false, true, 1>(I, rows, nhits, pass, rpos, b, wc, st);
 }
 
 size_t share_tmp_bytes(u64 cap, u64 rows_cap) {
@@ -1707,9 +1731,10 @@ int locate_shared(const DevIndex &I, const mb_smem *sm, u64 cap, const u64 *nsm_
     const bool aux = b.aux && I.sa_aux;
     if (b.join && b.wb && !chk && !aux) {
         // walk blocks with the marks of the walked rows and their ranks, the rows by pass, then
-        // one walk launch per pass (a pass joins only into rows of the passes before it)
+        // the walks (a walk joins only rows of complete passes)
         const u64 nw = join_words(I.n), nt = join_tiles(hits_cap);   // blocks, partition tiles
         MB_CK(cudaMemsetAsync(b.nojoin, 0, 4, st));
+        MB_CK(cudaMemsetAsync(b.qhead, 0, JOIN_PASSES * 4, st));
         k_walk_blocks<<<grid_for(nw, 256), 256, 0, st>>>(I, nw, b.coarse, b.wb);
         MB_KCHECK();
         const unsigned GR = grid_for(hits_cap, 256);
@@ -1723,7 +1748,7 @@ int locate_shared(const DevIndex &I, const mb_smem *sm, u64 cap, const u64 *nsm_
         MB_KCHECK();
         if (count) k_join_flag_count<<<1, 32, 0, st>>>(b.nojoin, wc);
         if (kt) kt->start();
-        for (u32 p = 0; p < (u32)JOIN_PASSES; ++p) MB_TRY(launch_pass(I, b.rows, hits_cap, p, b.rpos, b, wc, count, depth, st));
+        for (u32 p = 0; p < (u32)JOIN_PASSES; ++p) MB_TRY(launch_join(I, b.rows, hits_cap, p, b.rpos, b, wc, count, depth, st));
         if (kt) kt->stop();
     } else {
         DevIndex L = I;   // with MB_LOCATE_AUX the walks stop at the rate-4 samples
@@ -1920,6 +1945,7 @@ static int share_alloc(DevBuf &bw, u64 n_smem, u64 total, u64 n, bool join, cuda
         b.tcnt = (u32 *)take(JOIN_PASSES * join_tiles(total) * 4 + 4);
         b.idx = (u32 *)take(total * 4);
         b.range = (u64 *)take((JOIN_PASSES + 1) * 8);
+        b.qhead = (u32 *)take(JOIN_PASSES * 4);
     }
     MB_CK(cudaMemsetAsync(b.err, 0, 8, st));
     return MB_OK;
@@ -2227,7 +2253,7 @@ void mb_plan_arrays(const mb_plan *p, const mb_smem **smem, const u32 **hits, u6
 }
 
 // Device workspace of a plan, one entry per array (in the order mb_plan_create lays them out).
-constexpr int PLAN_ARRAYS = 30;
+constexpr int PLAN_ARRAYS = 31;
 // A plan locates with walks that join (their arrays sized by the index's n rows) when the options
 // say MB_LOCATE_JOIN without MB_CHECKED or MB_LOCATE_AUX and the plan holds hits to locate (not a
 // seeding-only plan).
@@ -2250,7 +2276,7 @@ static void plan_sizes(const mb_opts *opts, u64 n, u32 max_reads, u64 max_bases,
                                    ms * 8, ms * 8, ms * 8, ms * 4, ms * 4, ms * 4, ms * 4, mh * 4,
                                    nw * sizeof(WalkBlk), nc * 16, nw * 4, join ? 8u : 0u,
                                    join ? JOIN_PASSES * nt * 4 + 4 : 0, join ? mh * 4 : 0,
-                                   join ? (JOIN_PASSES + 1) * 8 : 0};
+                                   join ? (JOIN_PASSES + 1) * 8 : 0, join ? JOIN_PASSES * 4 : 0};
     for (int i = 0; i < PLAN_ARRAYS; ++i) sizes[i] = z[i];
 }
 
@@ -2307,7 +2333,7 @@ extern "C" int mb_plan_create(const mb_index *idx, const mb_opts *opts, uint32_t
                                 (void **)&P->share.vals_alt, (void **)&P->share.pmax, (void **)&P->share.last,
                                 (void **)&P->share.rpos, (void **)&P->share.wb, (void **)&P->share.coarse,
                                 (void **)&P->share.before, (void **)&P->share.nojoin, (void **)&P->share.tcnt,
-                                (void **)&P->share.idx, (void **)&P->share.range};
+                                (void **)&P->share.idx, (void **)&P->share.range, (void **)&P->share.qhead};
     for (int i = 0; i < PLAN_ARRAYS; ++i) {
         *ptrs[i] = sizes[i] ? (void *)m : nullptr;
         m += align_up(sizes[i]);

@@ -129,11 +129,11 @@ def test_workload3_1gbp_full_index_and_sampled_reads(mb, w3):
 
 # the launch configuration bench.py times on the 1 Gbp workload
 BENCH_KMER_K = 14
-BENCH_OPTS = dict(block_size=512, prefetch_depth=4)
+BENCH_OPTS = dict(block_size=512, prefetch_depth=2)
 
 
 def test_workload3_1gbp_in_the_bench_configuration(mb, w3):
-    """The bench's exact configuration: 14-mer table, work queue, block 512, 4 walks per lane
+    """The bench's exact configuration: 14-mer table, work queue, block 512, 2 walks per lane
     that join; plain calls == captured plan graph == mb_seed_locate on pinned host buffers, and
     1% of the reads against the oracle."""
     ref, rd, params, X = w3
