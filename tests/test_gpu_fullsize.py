@@ -7,7 +7,7 @@ and a seeded random sample of the reads (every SMEM record and every hit of each
 - The 1 Gbp workload runs twice: with the binding's defaults (10-mer table, fixed read ranges
   per warp, one locate walk per lane; one mb_seed_batch + one mb_locate call), and in exactly
   the launch configuration bench.py times (14-mer table, device work queue, 512 threads per
-  block, 16 locate walks per lane) through all three forms the bench runs: the plain calls, the
+  block, locate walks that join, 2 per lane) through all three forms the bench runs: the plain calls, the
   captured CUDA graph of a plan, and mb_seed_locate on pinned host buffers.  The three must be
   identical byte for byte, and 1% of the reads must match the oracle.
 - The mixed-length workload (100 Mbp, 200,000 reads of 100 bp - 10 kb) runs in the batched
