@@ -1163,49 +1163,50 @@ __global__ void k_share_copy(const u64 *__restrict__ keys, const u32 *__restrict
 
 // Locate (Algorithm 2).  Each lane LF-walks D rows at a time (D independent block reads in
 // flight per lane), one step of each per loop iteration.  The walks that end in an iteration are
-// replaced by the next rows of the warp's range in one hand-out: the lanes' counts of ended walks
-// are scanned across the warp, each ended walk takes the next offset in lane order, then slot
-// order, and loads its row directly (the range's rows are prefetched into L1 about 128 ahead).  A
+// replaced in one hand-out: the lanes' counts of ended walks are scanned across the warp and each
+// ended walk takes the next position of the warp's chunk of the row list (in lane order, then
+// slot order); warps take chunks of 256 positions per walk slot from a device queue, so a warp
+// whose walks happen to be short takes more rows and the launch ends with its last walks.  A
 // walk ends on a sampled row (position = steps + S(row)) or on the $ row (S = 0, position =
 // steps).  The sampled-SA reads and the block reads of one iteration are issued together.  A walk
 // needs fewer than n steps; the bound only guards against a corrupted index (it then writes
-// 0xFFFFFFFF).  Offsets within a warp's range are u32 (the host keeps ranges below 2^32 - 2^12).
-// Launch bounds: 16 walks per lane fit one block of 8 warps per SM, 8 walks two blocks, fewer
-// walks three.
+// 0xFFFFFFFF).  Queue positions are u32 (the host keeps them below 2^32).
+// Launch bounds: 16 walks per lane fit one block of 8 warps per SM, 8 walks two, 4 three, fewer
+// four.
 // CHK (MB_CHECKED): every row walked is checked against the text length, failures recorded in *chk.
 template <bool COUNT, bool POW2, int D, bool CHK = false>
-__global__ void __launch_bounds__(256, D == 8 ? 2 : 1) k_locate(DevIndex I, const u32 *__restrict__ rows, u64 nhits,
-                                                const u64 *__restrict__ nhits_dev, u32 *__restrict__ hits, u64 *wc,
-                                                u32 *chk) {
-    const u32 lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(256, D <= 2 ? 4 : (D <= 4 ? 3 : (D <= 8 ? 2 : 1)))
+    k_locate(DevIndex I, const u32 *__restrict__ rows, u64 nhits, const u64 *__restrict__ nhits_dev,
+             u32 *__restrict__ hits, u32 *__restrict__ qhead, u64 *wc, u32 *chk) {
+    constexpr u32 CHUNK = 256u * D;   // queue positions a warp takes at a time
+    const u32 FULL = 0xffffffffu, lane = threadIdx.x & 31;
     if (nhits_dev && *nhits_dev < nhits) nhits = *nhits_dev;
+    const u32 nitems = (u32)nhits;
     Work<COUNT> work;
     const u32 r = I.r, rmask = I.r - 1, rshift = __ffs(I.r) - 1, prim = (u32)I.primary, n = (u32)I.n;
     const u32 C0 = (u32)I.C[0], C1 = (u32)I.C[1], C2 = (u32)I.C[2], C3 = (u32)I.C[3];
-    WarpRange wr;
-    wr.init(nhits);
-    const u64 wbase = wr.next;
-    const u32 wlen = (u32)(wr.end - wr.next);
-    const u32 *__restrict__ wrows = rows + wbase;
-    u32 *__restrict__ whits = hits + wbase;
     u32 h[D], row[D], steps[D];
     u32 live = 0;   // bit d: slot d holds a walk
-    u32 next = 0;   // next offset of the range to hand out (warp-uniform)
+    u32 next = 0;   // the warp's queue chunk: positions [next, cend)
+    if (lane == 0) next = atomicAdd(qhead, CHUNK);
+    next = __shfl_sync(FULL, next, 0);
+    u32 cend = next + CHUNK;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-        const u32 o = next + lane;
+        const u32 o = next + 32u * d + lane;
         h[d] = o;
         steps[d] = 0;
         row[d] = 0;
-        if (o < wlen) {
+        if (o < nitems) {
             live |= 1u << d;
-            row[d] = __ldg(&wrows[o]);
+            row[d] = __ldg(&rows[o]);
         }
-        next += 32;
     }
+    next += 32u * D;
     for (;;) {
-        if (__all_sync(0xffffffffu, live == 0)) break;
-        if (next + 128 + lane < wlen) asm volatile("prefetch.global.L1 [%0];" ::"l"(wrows + next + 128 + lane));
+        if (__all_sync(FULL, live == 0)) break;
+        if (next + 128 + lane < cend && next + 128 + lane < nitems)
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(rows + next + 128 + lane));
         u32 stop = 0, smp = 0, skp = 0;
         u32 sv[D];
         Blk b[D];
@@ -1229,34 +1230,46 @@ __global__ void __launch_bounds__(256, D == 8 ? 2 : 1) k_locate(DevIndex I, cons
                 b[d] = load_blk(I.occ + (row[d] >> BLK_SHIFT));
             }
         }
-        // offsets for this iteration's ended walks: exclusive scan of the per-lane counts
+        // positions for this iteration's ended walks: from the warp's chunk, then a new chunk
         const u32 cnt = __popc(stop);
         u32 incl = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const u32 v = __shfl_up_sync(0xffffffffu, incl, o);
+            const u32 v = __shfl_up_sync(FULL, incl, o);
             if (lane >= (u32)o) incl += v;
         }
-        u32 give = next + incl - cnt;
-        next += __shfl_sync(0xffffffffu, incl, 31);
+        const u32 total = __shfl_sync(FULL, incl, 31), avail = cend - next;
+        u32 nb = cend;   // past the end once the chunk reached it (a new chunk would too)
+        if (total > avail && cend < nitems) {
+            if (lane == 0) nb = atomicAdd(qhead, CHUNK);
+            nb = __shfl_sync(FULL, nb, 0);
+        }
+        u32 k = incl - cnt;   // this lane's first position among the warp's
 #pragma unroll
         for (int d = 0; d < D; ++d) {
             if ((stop >> d) & 1u) {
                 if (!((skp >> d) & 1u))
-                    whits[h[d]] = (steps[d] > n || (CHK && row[d] >= n))
-                                      ? 0xFFFFFFFFu
-                                      : (((smp >> d) & 1u) ? sv[d] + steps[d] : steps[d]);
+                    hits[h[d]] = (steps[d] > n || (CHK && row[d] >= n))
+                                     ? 0xFFFFFFFFu
+                                     : (((smp >> d) & 1u) ? sv[d] + steps[d] : steps[d]);
                 work.lf += steps[d];
                 work.sa += (smp >> d) & 1u;
-                h[d] = give;
+                const u32 pos = k < avail ? next + k : nb + (k - avail);
+                ++k;
+                h[d] = pos;
                 steps[d] = 0;
-                if (give < wlen) row[d] = __ldg(&wrows[give]);
+                if (pos < nitems) row[d] = __ldg(&rows[pos]);
                 else live &= ~(1u << d);
-                ++give;
             } else if ((live >> d) & 1u) {
                 row[d] = lf_blk(b[d], row[d], prim, C0, C1, C2, C3);
                 ++steps[d];
             }
+        }
+        if (total > avail) {
+            next = nb + (total - avail);
+            cend = nb + CHUNK;
+        } else {
+            next += total;
         }
     }
     work.flush(wc);
@@ -1601,34 +1614,32 @@ void smem_tuning(const mb_opts *o, SmemArgs &a) {
 }
 
 template <bool COUNT, bool POW2, int D, bool CHK = false>
-int launch_locate_t(const DevIndex &I, const u32 *rows, u64 nhits, const u64 *nhits_dev, u32 *hits, u64 *wc,
-                    u32 *chk, cudaStream_t st) {
+int launch_locate_t(const DevIndex &I, const u32 *rows, u64 nhits, const u64 *nhits_dev, u32 *hits, u32 *qhead,
+                    u64 *wc, u32 *chk, cudaStream_t st) {
     const unsigned g = resident_grid((const void *)k_locate<COUNT, POW2, D, CHK>, 256, (nhits + 63) / 64 * 32);
-    const u64 warps = (u64)g * 8;
-    if ((nhits + warps - 1) / warps >= (1ull << 32) - 4096) {   // offsets within a warp's range are u32
-        mb_set_error("locate: %llu hits over %llu warps", (unsigned long long)nhits, (unsigned long long)warps);
+    if (nhits + (u64)g * 8 * 256 * D + 256 * D >= (1ull << 32)) {   // queue positions are u32
+        mb_set_error("locate: %llu hits exceed the walk queue", (unsigned long long)nhits);
         return MB_ERR_ARG;
     }
-    k_locate<COUNT, POW2, D, CHK><<<g, 256, 0, st>>>(I, rows, nhits, nhits_dev, hits, wc, chk);
+    MB_CK(cudaMemsetAsync(qhead, 0, 4, st));
+    k_locate<COUNT, POW2, D, CHK><<<g, 256, 0, st>>>(I, rows, nhits, nhits_dev, hits, qhead, wc, chk);
     MB_KCHECK();
     return MB_OK;
 }
-
-// The locate kernel: work counters, power-of-two sample rate, walks per lane (depth 1, 2, 4, 8, 16).
-int launch_locate(const DevIndex &I, const u32 *rows, u64 nhits, const u64 *nhits_dev, u32 *hits, u64 *wc,
+int launch_locate(const DevIndex &I, const u32 *rows, u64 nhits, const u64 *nhits_dev, u32 *hits, u32 *qhead, u64 *wc,
                   bool count, u32 depth, u32 *chk, cudaStream_t st) {
     const bool pow2 = (I.r & (I.r - 1)) == 0;
     if (chk)   // MB_CHECKED: one walk per lane, every row checked
-        return pow2 ? launch_locate_t<false, true, 1, true>(I, rows, nhits, nhits_dev, hits, wc, chk, st)
-                    : launch_locate_t<false, false, 1, true>(I, rows, nhits, nhits_dev, hits, wc, chk, st);
-    if (count) return pow2 ? launch_locate_t<true, true, 1>(I, rows, nhits, nhits_dev, hits, wc, chk, st)
-                           : launch_locate_t<true, false, 1>(I, rows, nhits, nhits_dev, hits, wc, chk, st);
-    if (!pow2) return launch_locate_t<false, false, 1>(I, rows, nhits, nhits_dev, hits, wc, chk, st);
-    if (depth >= 16) return launch_locate_t<false, true, 16>(I, rows, nhits, nhits_dev, hits, wc, chk, st);
-    if (depth >= 8) return launch_locate_t<false, true, 8>(I, rows, nhits, nhits_dev, hits, wc, chk, st);
-    if (depth >= 4) return launch_locate_t<false, true, 4>(I, rows, nhits, nhits_dev, hits, wc, chk, st);
-    if (depth >= 2) return launch_locate_t<false, true, 2>(I, rows, nhits, nhits_dev, hits, wc, chk, st);
-    return launch_locate_t<false, true, 1>(I, rows, nhits, nhits_dev, hits, wc, chk, st);
+        return pow2 ? launch_locate_t<false, true, 1, true>(I, rows, nhits, nhits_dev, hits, qhead, wc, chk, st)
+                    : launch_locate_t<false, false, 1, true>(I, rows, nhits, nhits_dev, hits, qhead, wc, chk, st);
+    if (count) return pow2 ? launch_locate_t<true, true, 1>(I, rows, nhits, nhits_dev, hits, qhead, wc, chk, st)
+                           : launch_locate_t<true, false, 1>(I, rows, nhits, nhits_dev, hits, qhead, wc, chk, st);
+    if (!pow2) return launch_locate_t<false, false, 1>(I, rows, nhits, nhits_dev, hits, qhead, wc, chk, st);
+    if (depth >= 16) return launch_locate_t<false, true, 16>(I, rows, nhits, nhits_dev, hits, qhead, wc, chk, st);
+    if (depth >= 8) return launch_locate_t<false, true, 8>(I, rows, nhits, nhits_dev, hits, qhead, wc, chk, st);
+    if (depth >= 4) return launch_locate_t<false, true, 4>(I, rows, nhits, nhits_dev, hits, qhead, wc, chk, st);
+    if (depth >= 2) return launch_locate_t<false, true, 2>(I, rows, nhits, nhits_dev, hits, qhead, wc, chk, st);
+    return launch_locate_t<false, true, 1>(I, rows, nhits, nhits_dev, hits, qhead, wc, chk, st);
 }
 
 // Device arrays of the shared-walk locate: per record (cap) sort keys and values with their
@@ -1640,6 +1651,7 @@ struct ShareBufs {
     u32 *vals = nullptr, *vals_alt = nullptr, *pmax = nullptr, *last = nullptr, *rows = nullptr, *rpos = nullptr;
     void *tmp = nullptr;
     u32 *err = nullptr;   // the device error word (records with rows outside the text; MB_CHECKED bounds)
+    u32 *lq = nullptr;    // the head of the plain walks' row queue
     bool checked = false; // MB_CHECKED: the locate kernel checks every row it walks
     // walks that join (k_locate_join, MB_LOCATE_JOIN): the walk blocks and coarse counts, per
     // block the walked rows before it, the not-sorted flag, and the partition of the rows by pass
@@ -1757,7 +1769,7 @@ int locate_shared(const DevIndex &I, const mb_smem *sm, u64 cap, const u64 *nsm_
             L.r = AUX_RATE;
         }
         if (kt) kt->start();
-        MB_TRY(launch_locate(L, b.rows, hits_cap, b.nrows, b.rpos, wc, count, depth, chk, st));
+        MB_TRY(launch_locate(L, b.rows, hits_cap, b.nrows, b.rpos, b.lq, wc, count, depth, chk, st));
         if (kt) kt->stop();
     }
     k_share_copy<<<G, 256, 0, st>>>(b.keys, ss, sho, b.last, b.roff, cap, b.nwalk, b.rpos, hits_cap, hits, hits_cap);
@@ -1920,7 +1932,7 @@ extern "C" int mb_seed_batch(const mb_index *idx, const uint8_t *seq, const uint
 static int share_alloc(DevBuf &bw, u64 n_smem, u64 total, u64 n, bool join, cudaStream_t st, ShareBufs &b) {
     const size_t rec_bytes = (size_t)n_smem * SHARE_BYTES_PER_RECORD, row_bytes = (size_t)total * 8;
     const size_t tmp = share_tmp_bytes(n_smem, total), jb = join ? join_bytes(n, total) : 0;
-    MB_TRY(bw.alloc(rec_bytes + row_bytes + 16 + tmp + jb + 14 * 256, st));
+    MB_TRY(bw.alloc(rec_bytes + row_bytes + 16 + tmp + jb + 15 * 256, st));
     char *m = (char *)bw.p;
     auto take = [&](size_t bytes) { void *p = m; m += (bytes + 255) & ~(size_t)255; return p; };
     b.keys = (u64 *)take(n_smem * 8);
@@ -1935,6 +1947,7 @@ static int share_alloc(DevBuf &bw, u64 n_smem, u64 total, u64 n, bool join, cuda
     b.nrows = (u64 *)take(8);
     b.nwalk = (u64 *)take(8);
     b.err = (u32 *)take(8);
+    b.lq = (u32 *)take(8);
     b.tmp = take(tmp);
     b.join = join;
     if (join) {   // the order and sizes of join_bytes
@@ -2343,6 +2356,7 @@ extern "C" int mb_plan_create(const mb_index *idx, const mb_opts *opts, uint32_t
     P->share.nwalk = P->misc + 5;
     P->share.tmp = P->tmp;
     P->share.err = plan_err(P);
+    P->share.lq = (u32 *)(P->misc + 6);
     P->share.checked = (P->flags & MB_CHECKED) != 0;
     P->share.join = plan_joins(opts, max_hits);
     P->share.aux = (P->flags & MB_LOCATE_AUX) != 0;
