@@ -636,10 +636,10 @@ def bench_bisulfite(mb, torch, dev, ref, opts, reps: int = 3):
     _, m, nh = mb.mb_seed_batch(G, seq, off, mate=mate, opts=o, out=out, cap=cap)
     hits = torch.empty(max(nh, 1), dtype=torch.int32, device=dev)
     keep = torch.empty(max(nh, 1), dtype=torch.uint8, device=dev)
-    # locate form for this batch: plain walks (16 per lane) or walks that join (4 per lane), the
+    # locate form for this batch: plain walks (16 per lane) or walks that join (2 per lane), the
     # faster of the two on one timed call each (the join's per-call setup scales with the index)
     forms = {"plain": dict(o, flags=o["flags"] & ~mb.MB_LOCATE_JOIN, prefetch_depth=16),
-             "join": dict(o, flags=o["flags"] | mb.MB_LOCATE_JOIN, prefetch_depth=4)}
+             "join": dict(o, flags=o["flags"] | mb.MB_LOCATE_JOIN, prefetch_depth=2)}
     st = torch.cuda.current_stream()
     form_ms = {}
     for name, fo in forms.items():
