@@ -92,6 +92,45 @@ def gather_ceiling(gib: float = 4, modes=((0, "indep", 2048), (1, "chain", 512),
     return out
 
 
+def locate_sweep(mb, torch, idx, out, m, hits, nh, opts, reps: int = 3):
+    """The locate forms on one step's records (plain mb_locate calls, device buffers): plain walks,
+    walks that join and walks to the rate-4 samples at several walks per lane, each timed with CUDA
+    events (kernel time from the library's own events, and the whole call), output compared with
+    the first form; one JSON line per point, then the work counts of each form."""
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    want = None
+    forms = (("plain", 0, (16, 8, 4, 2)), ("join", mb.MB_LOCATE_JOIN, (4, 2, 1)), ("aux", mb.MB_LOCATE_AUX, (16, 4, 2)))
+    for name, fl, depths in forms:
+        for depth in depths:
+            o = dict(opts, prefetch_depth=depth, flags=(opts.get("flags", 0) & ~(mb.MB_LOCATE_JOIN | mb.MB_LOCATE_AUX)) | fl)
+            mb.mb_locate(idx, out, m, opts=o, hits=hits, cap=nh)
+            torch.cuda.synchronize()
+            mb.profile_reset()
+            mb.profile_enable(True)
+            e0.record(st)
+            for _ in range(reps):
+                mb.mb_locate(idx, out, m, opts=o, hits=hits, cap=nh)
+            e1.record(st)
+            torch.cuda.synchronize()
+            mb.profile_enable(False)
+            kms, kn = mb.profile_get("locate")
+            same = None
+            if want is None:
+                want = hits[:nh].clone()
+            else:
+                same = bool(torch.equal(hits[:nh], want))
+                if not same:
+                    raise SystemExit(f"bench: locate form {name} at {depth} walks per lane disagrees")
+            print(json.dumps({"locate_form": name, "walks_per_lane": depth, "kernel_ms": kms / max(kn, 1),
+                              "call_ms": e0.elapsed_time(e1) / reps, "identical_output": same}), flush=True)
+    for name, fl, _ in forms:
+        mb.profile_reset()
+        mb.mb_locate(idx, out, m, opts=dict(opts, flags=mb.MB_COUNT | fl), hits=hits, cap=nh)
+        print(json.dumps({"locate_form": name, "work": mb.work_counters()}), flush=True)
+    return 0
+
+
 def probe_sweep():
     """Random-read rate against buffer size (L2-resident to far above L2): one JSON line per size,
     with the 32-byte rate also in reads/s."""
@@ -773,6 +812,9 @@ def run_gpu(args):
     opts["smem_wait"] = best.smem_wait
     opts["smem_warps"] = best.smem_warps
 
+    if args.locate_sweep:
+        return locate_sweep(mb, torch, idx, out, m, hits, nh, opts)
+
     # work counters of the chosen form (untimed pass with counting kernels)
     mb.profile_reset()
     copts = dict(opts, flags=mb.MB_COUNT | (best.flags & mb.MB_LOCATE_JOIN))
@@ -1081,6 +1123,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the served-form measurement")
     ap.add_argument("--no-rescue", action="store_true", help="skip the mate-rescue prefilter measurement")
     ap.add_argument("--no-aux-form", action="store_true", help="skip the graph form with MB_LOCATE_AUX")
+    ap.add_argument("--locate-sweep", action="store_true",
+                    help="only time the locate forms (plain, joined, rate-4) on one step's records, one JSON line each")
     ap.add_argument("--no-bisulfite", action="store_true", help="skip the bisulfite (3-base index) measurement")
     ap.add_argument("--rescue-pairs", type=int, default=1_000_000)
     ap.add_argument("--serve-requests", type=int, default=50_000,
