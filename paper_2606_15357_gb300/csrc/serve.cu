@@ -151,6 +151,7 @@ struct mb_server {
     std::mutex mu;
     std::condition_variable cv;
     std::deque<ReqP> pending;
+    u64 pending_short = 0;   // waiting requests without long reads
     std::unordered_map<u64, ReqP> reqs;
     std::thread worker, helper;
     std::deque<std::vector<ReqP>> outgrown;   // groups for the helper thread
@@ -299,16 +300,11 @@ void retire(mb_server *S) {
 // nothing is admitted).  Returns false if nothing was admitted.
 bool admit(mb_server *S, Slot &s, bool no_long) {
     if (S->pending.empty()) return false;
-    bool kind = S->pending.front()->long_reads;
+    bool kind = S->pending.front()->long_reads, forced = false;
     if (kind && no_long) {
-        bool any_short = false;
-        for (const ReqP &r : S->pending)
-            if (!r->long_reads) {
-                any_short = true;
-                break;
-            }
-        if (!any_short) return false;
+        if (S->pending_short == 0) return false;
         kind = false;
+        forced = true;   // a request of short reads is waiting behind long ones: find it
     }
     s.group.clear();
     s.first_read.clear();
@@ -322,7 +318,7 @@ bool admit(mb_server *S, Slot &s, bool no_long) {
         const u64 b = r->off[r->n_reads];
         if (r->long_reads != kind) {
             rest.push_back(r);
-            if (rest.size() >= 256) break;   // bounded look-ahead past the other kind
+            if (!forced && rest.size() >= 256) break;   // bounded look-ahead past the other kind
             continue;
         }
         if (!s.group.empty() && (nr + r->n_reads > SLOT_READS || nb + b > SLOT_BASES)) {
@@ -333,13 +329,14 @@ bool admit(mb_server *S, Slot &s, bool no_long) {
         s.group.push_back(r);
         nr += r->n_reads;
         nb += b;
+        if (!r->long_reads) --S->pending_short;
     }
     while (!rest.empty()) {   // the skipped requests go back in front, in their order
         S->pending.push_front(rest.back());
         rest.pop_back();
     }
     s.n_reads = nr;
-    return true;
+    return !s.group.empty();
 }
 
 // Copy the group in from the ring and run it (lock not held).
@@ -628,6 +625,7 @@ extern "C" int mb_serve_submit(mb_server *S, const uint8_t *seq, const uint64_t 
     r->ticket = S->next_ticket++;
     S->reqs[r->ticket] = r;
     S->pending.push_back(r);
+    if (!r->long_reads) ++S->pending_short;
     *ticket = r->ticket;
     S->cv.notify_all();
     return MB_OK;
