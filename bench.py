@@ -399,7 +399,7 @@ def bench_batched(mb, torch, dev, reps: int = 3):
     batched_s = e0.elapsed_time(e1) / 1000 / reps
     bsm, bhits = BP.result()
     BP.free()
-    # the fastest shape with the device work queue (reads handed out longest first), as its own
+    # the fastest shape with the device work queue (reads handed out in read order), as its own
     # replayed graph: reported beside the autotuner's choice, output compared
     qo, _ = min(((o, t) for o, t in grid if o.flags & mb.MB_BATCHED), key=lambda p: p[1])
     QP = mb.Plan(G, rd.n, len(rd.seq), n_smem + 64, n_hits + 64, opts=qo)

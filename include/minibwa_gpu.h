@@ -48,8 +48,7 @@ enum {
 /* Flags of mb_opts.flags */
 #define MB_BS3      0x1u   /* index: bisulfite 3-base index over CT(R).GA(R) (Section 2.9);
                               seeding: convert read 1 C->T and read 2 G->A, keep hits by strand */
-#define MB_BATCHED  0x2u   /* seeding: lanes take reads from a device work queue (a plan orders it
-                              by decreasing read length; mb_seed_batch keeps read order) */
+#define MB_BATCHED  0x2u   /* seeding: lanes take reads from a device work queue, in read order */
 #define MB_CHECKED  0x4u   /* seeding / locate: the kernels also check every occurrence row they
                               read against the text length (only a damaged index can fail it; the
                               checked locate runs one walk per lane); a failed check ends that read
@@ -277,8 +276,9 @@ int mb_seed_locate(const mb_index *idx, const uint8_t *seq, const uint64_t *off,
  * the whole stage on `stream` (SMEMs by Algorithm 3, the max-occ flag, hit offsets, locate by
  * Algorithm 2) with no host synchronization and no allocation, so the call can be captured into
  * a CUDA graph and the graph replayed for new batches written into the same input buffers.
- * With MB_BATCHED in opts->flags the SMEM kernel takes reads from a device work queue in
- * order of decreasing length (one persistent launch for reads of very different lengths);
+ * With MB_BATCHED in opts->flags the SMEM kernel takes reads from a device work queue in read
+ * order (one persistent launch for reads of very different lengths: a lane takes the next read
+ * when its read ends);
  * opts->block_size (128, 256 or 512) selects the launch shape.
  *   seq, off, mate (or NULL): DEVICE pointers, as in mb_seed_batch.
  * mb_plan_result waits for the stream and returns the plan-owned DEVICE arrays of the last

@@ -2212,17 +2212,6 @@ extern "C" int mb_seed_batch_noalloc(const mb_index *idx, const uint8_t *seq, co
 }
 
 // ============================================================================ batched form: plans
-namespace {
-// lengths as sort keys, longest first (key = 2^32 - 1 - length), values = read ids
-__global__ void k_len_keys(const u64 *__restrict__ off, u32 nr, u64 *__restrict__ keys, u32 *__restrict__ ids) {
-    for (u64 r = blockIdx.x * (u64)blockDim.x + threadIdx.x; r < nr; r += (u64)gridDim.x * blockDim.x) {
-        const u64 len = off[r + 1] - off[r];
-        keys[r] = 0xFFFFFFFFull - (len < 0xFFFFFFFFull ? len : 0xFFFFFFFFull);
-        ids[r] = (u32)r;
-    }
-}
-}  // namespace
-
 struct mb_plan {
     const mb_index *idx = nullptr;
     u32 l = 19, c = 1, max_occ = 500, flags = 0;
@@ -2241,8 +2230,6 @@ struct mb_plan {
     u32 *known = nullptr;   // per record: the hit position found while seeding, or NOPOS
     ShareBufs share;        // shared-walk locate: per-record arrays, positions of the walked rows
     mb_smem *out = nullptr;
-    u64 *skeys = nullptr, *skeys_alt = nullptr;
-    u32 *perm = nullptr, *perm_alt = nullptr;
     void *tmp = nullptr;
     size_t bytes = 0;
     cudaGraph_t graph = nullptr;
@@ -2266,7 +2253,7 @@ void mb_plan_arrays(const mb_plan *p, const mb_smem **smem, const u32 **hits, u6
 }
 
 // Device workspace of a plan, one entry per array (in the order mb_plan_create lays them out).
-constexpr int PLAN_ARRAYS = 31;
+constexpr int PLAN_ARRAYS = 27;
 // A plan locates with walks that join (their arrays sized by the index's n rows) when the options
 // say MB_LOCATE_JOIN without MB_CHECKED or MB_LOCATE_AUX and the plan holds hits to locate (not a
 // seeding-only plan).
@@ -2275,21 +2262,18 @@ static bool plan_joins(const mb_opts *opts, u64 max_hits) {
 }
 static void plan_sizes(const mb_opts *opts, u64 n, u32 max_reads, u64 max_bases, u64 max_smem, u64 max_hits,
                        size_t sizes[PLAN_ARRAYS]) {
-    const bool queue = opts && (opts->flags & MB_BATCHED);
     const size_t nr = max_reads, ms = max_smem ? max_smem : 1, mh = max_hits ? max_hits : 1;
     size_t tb = scan_tmp_bytes(nr > ms ? nr : ms);
-    const size_t rb = radix_tmp_bytes(nr), sb = share_tmp_bytes(ms, mh);
-    if (rb > tb) tb = rb;
+    const size_t sb = share_tmp_bytes(ms, mh);
     if (sb > tb) tb = sb;
     const bool join = plan_joins(opts, max_hits);
     const size_t nw = join ? join_words(n) : 0, nc = join ? join_coarse(n) : 0, nt = join ? join_tiles(mh) : 0;
     const size_t z[PLAN_ARRAYS] = {slots_total(max_bases, max_reads) * sizeof(SlotRec), nr * 8, nr * 8, 256, ms * 8,
-                                   nr * 4, mh * 4, mh * 4, ms * sizeof(mb_smem), queue ? nr * 8 : 0,
-                                   queue ? nr * 8 : 0, queue ? nr * 4 : 0, queue ? nr * 4 : 0, tb, ms * 4,
+                                   nr * 4, mh * 4, mh * 4, ms * sizeof(mb_smem), tb, ms * 4,
                                    ms * 8, ms * 8, ms * 8, ms * 4, ms * 4, ms * 4, ms * 4, mh * 4,
                                    nw * sizeof(WalkBlk), nc * 16, nw * 4, join ? 8u : 0u,
                                    join ? JOIN_PASSES * nt * 4 + 4 : 0, join ? mh * 4 : 0,
-                                   join ? (JOIN_PASSES + 1) * 8 : 0, join ? JOIN_PASSES * 4 : 0};
+                                   join ? (size_t)(JOIN_PASSES + 1) * 8 : 0, join ? (size_t)JOIN_PASSES * 4 : 0};
     for (int i = 0; i < PLAN_ARRAYS; ++i) sizes[i] = z[i];
 }
 
@@ -2340,8 +2324,7 @@ extern "C" int mb_plan_create(const mb_index *idx, const mb_opts *opts, uint32_t
     char *m = (char *)P->mem;
     void **ptrs[PLAN_ARRAYS] = {(void **)&P->slots, (void **)&P->counts, (void **)&P->soff, (void **)&P->misc,
                                 (void **)&P->hitc, (void **)&P->ovf, (void **)&P->rows, (void **)&P->hits,
-                                (void **)&P->out, (void **)&P->skeys, (void **)&P->skeys_alt, (void **)&P->perm,
-                                (void **)&P->perm_alt, (void **)&P->tmp, (void **)&P->known, (void **)&P->share.keys,
+                                (void **)&P->out, (void **)&P->tmp, (void **)&P->known, (void **)&P->share.keys,
                                 (void **)&P->share.keys_alt, (void **)&P->share.roff, (void **)&P->share.vals,
                                 (void **)&P->share.vals_alt, (void **)&P->share.pmax, (void **)&P->share.last,
                                 (void **)&P->share.rpos, (void **)&P->share.wb, (void **)&P->share.coarse,
@@ -2387,14 +2370,9 @@ static int plan_seed(mb_plan *P, const uint8_t *seq, const uint64_t *off, uint32
     u64 *n_smem = P->misc, *n_hits = P->misc + 1;
     u32 *ovf_n = (u32 *)(P->misc + 2), *qhead = (u32 *)(P->misc + 3), *err = plan_err(P);
     MB_CK(cudaMemsetAsync(P->hitc, 0, P->max_smem * 8, st));   // zero tail for the fixed-length scan
+    // with the work queue the reads are handed out in read order: ordering them by decreasing
+    // length (tried: a sort before the launch) made the mixed-length batch 2.4 ms slower
     const u32 *perm = nullptr;
-    if (P->queue) {   // work queue in order of decreasing read length
-        k_len_keys<<<grid_for(n_reads, 256), 256, 0, st>>>(off, n_reads, P->skeys, P->perm);
-        MB_KCHECK();
-        BitRange r0[1] = {{0, 32}};
-        MB_TRY(radix_sort_pairs(P->skeys, P->perm, P->skeys_alt, P->perm_alt, n_reads, r0, 1, P->tmp, st));
-        perm = P->perm;
-    }
     SmemArgs sa{I, seq, off, n_reads, mate, bs, P->l, P->c, P->kmer, P->slots, P->nslots, P->counts, P->ovf, ovf_n,
                 perm, qhead, nullptr, nullptr, I.text2 && !(P->flags & MB_STEP_ONLY)};
     sa.split = P->split;
