@@ -2492,11 +2492,13 @@ extern "C" int mb_plan_replay(mb_plan *P, void *stream) {
     return MB_OK;
 }
 
-// Times launch shapes on this batch (all give the same output; tests check that), in two stages:
+// Times launch shapes on this batch (all give the same output; tests check that), in stages:
 // (1) the SMEM kernel's shape, over threads per block {128, 256, 512} x work queue off/on x the
-// kernel form (the one-loop form, and the split form with block steps between service passes
-// {2, 4, 8, 16} x lanes out of the loop that call a pass early {4, 8, 16}), with 16 locate walks
-// per lane; (2) locate walks per lane {1, 2, 4, 8} with the best SMEM shape.  Each point is the
+// kernel form (the one-loop form, and the split form with memory steps between service passes
+// {2, 4, 8, 16} x lanes out of the loop that call a pass early {4, 8, 16}), with 16 plain locate
+// walks per lane; (2) for a split-form winner, reads per warp {1, 2, 4, 8, 16}; (3) with the best
+// SMEM shape, locate walks per lane {1, 2, 4, 8} plain and {1, 2, 4, 8, 16} with walks that join
+// (MB_LOCATE_JOIN).  Each point is the
 // best of two timed runs of mb_plan_run after one untimed run.  Every point tried is written to
 // points / points_ms when given (up to cap; *n_points receives the number tried).
 static int autotune_impl(const mb_index *idx, const uint8_t *seq, const uint64_t *off, uint32_t n_reads,
