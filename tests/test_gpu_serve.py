@@ -162,8 +162,13 @@ def test_served_mix_on_100mbp_index_against_oracle(mb):
     tickets = [srv.submit(r.seq, r.off) for r in reqs]
     results = [srv.wait(t) for t in tickets]
     st = srv.stats()
+    c = srv.counters()
     srv.close()
     assert st["merged"] > 0
+    # requests with reads of 1 kb or more ran in groups of their own
+    n_long = sum(1 for r in reqs if (np.diff(r.off.astype(np.int64)) >= 1000).any())
+    assert n_long > 0 and 0 < c["long_groups"] <= n_long < len(reqs)
+    assert c["groups"] > c["long_groups"]
     X = oracle.Index(ref, threads=os.cpu_count())
     for q, (r, (sm, hits, _)) in enumerate(zip(reqs, results)):
         want_sm, want_hits = mb.seed(G, r.seq, r.off)
